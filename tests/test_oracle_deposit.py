@@ -1,0 +1,189 @@
+"""Pins of the oracle's tet walk and charge-conserving deposit (Sec. IV.B.1).
+
+G_e = int over the path of W1_e . dr (times q w) and rho = -[grad]^T G, so the
+discrete continuity equation D0^T dG = dQ holds analytically.  Pinned by:
+brute-force path integration with point location on a two-tet mesh, the
+closed form of the integral on one straight piece, brute-force point location
+along the path (walk order), continuity and total charge to round-off, and the
+E x B drift carried through gather + Boris + walk over many steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_06737_gb300 import inputs as I
+import oracle as O
+
+
+def _locate_all(orc, P):
+    """Brute force: for each point the tet with the largest min barycentric (tests every tet)."""
+    nt = orc.n_tets
+    best = np.full(P.shape[0], -1)
+    bestv = np.full(P.shape[0], -np.inf)
+    for t in range(nt):
+        lam = orc.bary(np.full(P.shape[0], t, dtype=np.int32), P)
+        mn = lam.min(axis=1)
+        upd = mn > bestv
+        best[upd] = t
+        bestv[upd] = mn[upd]
+    return best, bestv
+
+
+def test_single_piece_closed_form():
+    m = I.cube_mesh(3, 1.0, 0.1, seed=7)
+    orc = O.Oracle(m.xyz, m.tets)
+    rng = np.random.default_rng(3)
+    cx = orc.cx
+    for t in rng.choice(cx.n_tets, 20, replace=False):
+        lamP, lamR = rng.dirichlet([1, 1, 1, 1], size=2)
+        x = cx.xyz[cx.tv[t]]
+        P, R = lamP @ x, lamR @ x
+        r = orc.step([t], [P], [[0, 0, 0]], np.zeros(cx.n_edges), np.zeros(cx.n_faces), 1.0, 1.0,
+                     1.0, 1.0, Xend=[R])
+        assert r["cell"][0] == t and r["ncross"][0] == 0
+        for k, (a, b) in enumerate(O.LOCAL_EDGES):
+            ref = lamP[a] * lamR[b] - lamP[b] * lamR[a]
+            got = r["dG"][cx.tet_edges[t, k]]
+            assert abs(got - ref) <= 1e-14 * max(1.0, abs(ref))
+        # W0 charge at the end point
+        assert np.allclose(r["Q"][cx.tv[t]], lamR, atol=1e-15)
+
+
+def test_two_tet_brute_force_path_integral():
+    m = I.two_tet_mesh()
+    orc = O.Oracle(m.xyz, m.tets)
+    cx = orc.cx
+    rng = np.random.default_rng(11)
+    ns = 1 << 20
+    s = (np.arange(ns) + 0.5) / ns
+    n_checked = 0
+    for _ in range(6):
+        la = rng.dirichlet([2, 2, 2, 2])
+        lb = rng.dirichlet([2, 2, 2, 2])
+        Pa = la @ cx.xyz[cx.tv[0]]
+        Pb = lb @ cx.xyz[cx.tv[1]]
+        r = orc.step([0], [Pa], [[0, 0, 0]], np.zeros(cx.n_edges), np.zeros(cx.n_faces), 1.0, 1.0, 1.0,
+                     1.0, Xend=[Pb])
+        if r["cell"][0] != 1:
+            continue      # the straight path left the two-tet domain: not a test case
+        n_checked += 1
+        # brute force: midpoint rule on the unsplit path, W1 evaluated in the tet containing each sample
+        pts = Pa[None, :] + s[:, None] * (Pb - Pa)[None, :]
+        lam0 = orc.bary(np.zeros(ns, np.int32), pts)
+        in0 = lam0.min(axis=1) >= lam0.min(axis=1) * 0 - 0.0
+        lam1 = orc.bary(np.ones(ns, np.int32), pts)
+        in0 = lam0.min(axis=1) >= lam1.min(axis=1)
+        assert (lam0.min(axis=1)[in0] > -1e-9).all() and (lam1.min(axis=1)[~in0] > -1e-9).all()
+        G = np.zeros(cx.n_edges)
+        d = (Pb - Pa) / ns
+        for t, lam, sel in ((0, lam0, in0), (1, lam1, ~in0)):
+            x = cx.xyz[cx.tv[t]]
+            J = np.stack([x[1] - x[0], x[2] - x[0], x[3] - x[0]], axis=1)
+            Gi = np.linalg.inv(J)
+            g = np.vstack([-Gi.sum(axis=0), Gi])            # rows: grad lambda_0..3
+            for k, (a, b) in enumerate(O.LOCAL_EDGES):
+                w = lam[sel, a][:, None] * g[b] - lam[sel, b][:, None] * g[a]
+                G[cx.tet_edges[t, k]] += (w @ d).sum()
+        scale = np.abs(G).max()
+        assert np.abs(r["dG"] - G).max() <= 1e-5 * scale
+    assert n_checked >= 2
+
+
+def _crossing_cloud(n_hex=4, jit=0.1, n=400, seed=5, speed=0.6):
+    m = I.cube_mesh(n_hex, 1.0, jit, seed=1)
+    orc = O.Oracle(m.xyz, m.tets)
+    sp = I.uniform_species(m, n, seed, speed, -1.0, 1.0)
+    return m, orc, sp
+
+
+def test_walk_matches_brute_force_location():
+    m, orc, sp = _crossing_cloud(n=60, speed=0.25)
+    cx = orc.cx
+    Xb = sp.X + sp.V
+    r = orc.step(sp.cell, sp.X, sp.V, np.zeros(cx.n_edges), np.zeros(cx.n_faces), 1.0, 1.0, 1.0, 1.0,
+                 Xend=Xb)
+    ns = 2000
+    s = (np.arange(ns) + 0.5) / ns
+    checked = 0
+    for p in range(sp.n):
+        end = r["X"][p]
+        pts = sp.X[p][None] + s[:, None] * (end - sp.X[p])[None]
+        cells, v = _locate_all(orc, pts)
+        seq = [cells[0]] + [c for i, c in enumerate(cells[1:], 1) if c != cells[i - 1]]
+        # one tet per interior crossing; an absorbed particle's last crossing is the wall
+        n_in = r["ncross"][p] - (1 if r["cell"][p] < 0 else 0)
+        if (v < 1e-9).any() and len(seq) != n_in + 1:
+            continue      # a sample sits on an edge/vertex within round-off: ambiguous
+        assert len(seq) == n_in + 1, p
+        if r["cell"][p] >= 0:
+            assert seq[-1] == r["cell"][p]
+        assert seq[0] == sp.cell[p]
+        checked += 1
+    assert checked >= 50
+    assert r["ncross"].max() >= 3
+
+
+@pytest.mark.parametrize("jit,seed", [(0.0, 1), (0.1, 2)])
+def test_continuity_and_total_charge(jit, seed):
+    m, orc, sp = _crossing_cloud(4, jit, 3000, seed, speed=0.5)
+    cx = orc.cx
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-1, 1, cx.n_edges)
+    b = rng.uniform(-1, 1, cx.n_faces)
+    q, mass, w, dt = -1.0, 1.0, 2.5, 0.6
+    Q0, Q0a = orc.charge(sp.cell, sp.X, q, w)
+    r = orc.step(sp.cell, sp.X, sp.V, e, b, q, mass, w, dt)
+    assert r["ncross"].sum() > sp.n          # many crossings
+    assert (r["cell"] < 0).sum() > 10        # some absorbed at the PEC walls
+    D0 = cx.D0()
+    res = D0.T @ r["dG"] - (r["Q"] - Q0)
+    scale = abs(D0.T) @ r["dG_abs"] + r["Q_abs"] + Q0a
+    assert np.abs(res).max() <= 1e-14 * scale.max()
+    # W0 is a partition of unity: all charge is on the nodes (absorbed charge stays on the wall)
+    assert abs(r["Q"].sum() - sp.n * q * w) <= 1e-12 * sp.n * w
+    # absorbed particles end on the boundary
+    dead = r["cell"] < 0
+    Xd = r["X"][dead]
+    on_wall = np.minimum(Xd, 1.0 - Xd).min(axis=1)
+    assert np.abs(on_wall).max() < 1e-12
+
+
+def test_crossing_bound():
+    m, orc, sp = _crossing_cloud(4, 0.1, 200, 9, speed=2.0)
+    cx = orc.cx
+    Q0, Q0a = orc.charge(sp.cell, sp.X, 1.0, 1.0)
+    r = orc.step(sp.cell, sp.X, sp.V, np.zeros(cx.n_edges), np.zeros(cx.n_faces), 1.0, 1.0, 1.0, 1.0,
+                 max_cross=2, Xend=sp.X + sp.V)
+    assert r["n_bound"] > 0
+    assert r["ncross"].max() <= 2
+    res = cx.D0().T @ r["dG"] - (r["Q"] - Q0)
+    assert np.abs(res).max() <= 1e-14 * (abs(cx.D0().T) @ r["dG_abs"] + r["Q_abs"] + Q0a).max()
+
+
+def test_exb_drift_through_walk():
+    """Uniform E x B fields through gather + Boris + walk: x_n = x_0 + n dt v_E to round-off."""
+    m = I.cube_mesh(6, 1.0, 0.1, seed=1)
+    orc = O.Oracle(m.xyz, m.tets)
+    cx = orc.cx
+    Bv = np.array([0.0, 0.0, 0.1])
+    Ev = np.array([0.0, 2e4, 0.0])
+    e, b = orc.project_uniform(Ev, Bv)
+    vE = np.cross(Ev, Bv) / (Bv @ Bv)                   # 2e5 m/s along x
+    q, mass = -I.Q_E, I.M_E
+    dt = 7.5e-8          # 0.015 m per step; v_E is a fixed point of the Boris map for any dt
+    sp = I.uniform_species(m, 200, 3, 0.0, q, mass)
+    keep = (sp.X[:, 0] < 0.3)
+    cell, X = sp.cell[keep], sp.X[keep]
+    V = np.tile(vE, (cell.size, 1))
+    X0 = X.copy()
+    nsteps = 40
+    tot_cross = 0
+    for _ in range(nsteps):
+        r = orc.step(cell, X, V, e, b, q, mass, 1.0, dt)
+        cell, X, V = r["cell"], r["X"], r["V"]
+        tot_cross += r["ncross"].sum()
+    assert (cell >= 0).all() and tot_cross > cell.size
+    assert np.abs(X - (X0 + nsteps * dt * vE)).max() < 1e-11   # round-off of the gathered fields
+    lam = orc.bary(cell, X)
+    assert lam.min() > -1e-12
