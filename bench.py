@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the FEM-PIC particle step on GB300 (one JSON line on rank 0).
+
+A step is one pass of the hot path over one batch of synthetic input: the periodic
+cell sort (every --sort-every steps), the particle push with gather, tet walk and
+charge-conserving deposit for every species, and the FP64 invariant residuals
+(continuity and magnetic Gauss law).  Default workload: cube 32^3 x 6 tets with
++-10% jitter, 2M electrons, Bz = 0.1 T, dt = 0.2 gyro-periods, FP32 particle path.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one independent replica per GPU (weak scaling, no collective
+on the data path; timing uses a barrier and the max over ranks).
+--impl reference times the FP64 CPU oracle on host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec at stated FP32 error; field-solve ms/step learned vs plain CG"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 5])
+    ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (tests only)")
+    ap.add_argument("--sort-every", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(gpu_index: int):
+    path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_FIELDS}",
+                              "--format=csv,noheader,nounits", "-lms", "200"], stdout=f,
+                             stderr=subprocess.DEVNULL)
+        return p, f, path
+    except Exception:
+        return None, None, path
+
+
+def clocks_stop(handle) -> dict:
+    p, f, path = handle
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, smax, reasons, busy = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        c = [x.strip() for x in line.split(",")]
+        if len(c) < 10:
+            continue
+        try:
+            mhz, mx, util = float(c[1]), float(c[2]), float(c[4])
+        except ValueError:
+            continue
+        smax.append(mx)
+        if util >= 50:
+            busy.append(mhz)
+            for k, nm in enumerate(names):
+                if c[6 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.append(mhz)
+    os.unlink(path)
+    use = busy if busy else sm
+    return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm), "samples_busy": len(busy)}
+
+
+# ------------------------------------------------------------------ workload
+
+def build_workload(args):
+    from paper_2103_06737_gb300 import inputs as I
+    return I.config(args.workload, args.scale)
+
+
+def algorithmic_bytes(n_particles, sizes, real_bytes=4):
+    """Minimal DRAM bytes of one push_deposit launch over all species (stated reading):
+    particle state read+write (cell + 3 off + 3 vel), each tet's tables once (96 B FP64
+    geometry + 80 B topology), each e and b DOF once (FP64), dG and Q read-modify-write."""
+    state = n_particles * 2 * (4 + 6 * real_bytes)
+    tets = sizes["n_tets"] * (96 + 80)
+    dofs = 8 * (sizes["n_edges"] + sizes["n_faces"])
+    dep = 2 * real_bytes * (sizes["n_edges"] + sizes["n_nodes"])
+    return state + tets + dofs + dep
+
+
+def peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2103_06737_gb300.fem_pic as F
+    from paper_2103_06737_gb300 import build as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    wl = build_workload(args)
+    lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
+    sizes = lib.sizes
+    dev = torch.device("cuda", local)
+    species = [lib.species(s.cell, s.X, s.V, s.q, s.m, s.w, device=dev) for s in wl.species]
+    spare = [s.empty_like() for s in species]
+    n_part = sum(s.n for s in species)
+    e, b = lib.fields_uniform((0.0, 0.0, 0.0), wl.B0, device=dev)
+    if wl.E_amp > 0:
+        # seeded random edge field: e_k = amp * l_k * U(-1,1) on interior edges, 0 on PEC edges
+        from paper_2103_06737_gb300 import inputs as I
+        topo = F.fem_pic_topology(lib.h)
+        rp, col, val = F.fem_pic_incidence(lib.h, 0)
+        ij = col.reshape(-1, 2)
+        length = np.linalg.norm(wl.mesh.xyz[ij[:, 1]] - wl.mesh.xyz[ij[:, 0]], axis=1)
+        u = I.random_dofs(sizes["n_edges"], 31, 1.0)
+        nb = topo["tet_neigh"]
+        bt = np.nonzero((nb < 0).any(axis=1))[0]
+        wall = np.zeros(sizes["n_edges"], bool)
+        faces_of = {0: (1, 2, 3), 1: (0, 2, 3), 2: (0, 1, 3), 3: (0, 1, 2)}
+        le = {(0, 1): 0, (0, 2): 1, (0, 3): 2, (1, 2): 3, (1, 3): 4, (2, 3): 5}
+        for t in bt:
+            for k in range(4):
+                if nb[t, k] < 0:
+                    f = faces_of[k]
+                    for a in range(3):
+                        for c in range(a + 1, 3):
+                            wall[topo["tet_edges"][t, le[(f[a], f[c])]]] = True
+        ev = wl.E_amp * length * u
+        ev[wall] = 0.0
+        e.copy_(torch.as_tensor(ev, device=dev))
+    dG = torch.empty(sizes["n_edges"], dtype=torch.float32, device=dev)
+    Qs = [torch.empty(sizes["n_nodes"], dtype=torch.float32, device=dev) for _ in range(2)]
+    res = torch.zeros(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    # initial sort and charge
+    for i in range(len(species)):
+        lib.sort(species[i], spare[i])
+        species[i], spare[i] = spare[i], species[i]
+    for i, s in enumerate(species):
+        lib.deposit_charge(s, Qs[0], flags=F.FP_ACCUMULATE if i else 0)
+    st = lib.status()
+    if st != F.FP_OK:
+        raise RuntimeError(f"setup status {st}: {F.fem_pic_last_error(lib.h)}")
+
+    state = {"i": 0, "launches": 0}
+    ev_push = []
+
+    def step(record_push=False):
+        i = state["i"]
+        if args.sort_every > 0 and i % args.sort_every == 0 and i > 0:
+            for k in range(len(species)):
+                lib.sort(species[k], spare[k])
+                species[k], spare[k] = spare[k], species[k]
+                state["launches"] += 5
+        Qn, Qo = Qs[(i + 1) % 2], Qs[i % 2]
+        if record_push:
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        for k, s in enumerate(species):
+            lib.push_deposit(e, b, s, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE if k else 0)
+            state["launches"] += 1
+        if record_push:
+            z.record(stream)
+            ev_push.append((a, z))
+        lib.residuals(dG, Qn, Qo, b, res)
+        state["launches"] += 2
+        state["i"] = i + 1
+
+    # warm-up: at least W steps and at least ~1.5 s of work so the clock sampler sees load
+    clk = clocks_start(local)
+    t0 = time.time()
+    w = 0
+    while w < args.warmup or time.time() - t0 < 1.5:
+        step()
+        if w % 20 == 0:
+            torch.cuda.synchronize()
+        w += 1
+    torch.cuda.synchronize()
+    st = lib.status()
+    if st != F.FP_OK:
+        raise RuntimeError(f"warm-up status {st}: {F.fem_pic_last_error(lib.h)}")
+
+    # timed: K steps, each bracketed by events; L2 flushed between steps (outside the events)
+    state["launches"] = 0
+    evs = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(record_push=True)
+        z.record(stream)
+        evs.append((a, z))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clocks_stop(clk)
+    launches = state["launches"]
+    step_ms = [a.elapsed_time(z) for a, z in evs]
+    push_ms = [a.elapsed_time(z) for a, z in ev_push]
+    total_ms = float(sum(step_ms))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    st = lib.status()
+    r = res.cpu().numpy()
+
+    # e2e through the public API with host buffers: H2D of the step's inputs (particle
+    # state + fields) from pinned memory, the step, D2H of the results (state + deposits)
+    e2e = None
+    if not args.no_e2e:
+        hs = [(torch.empty_like(s.cell, device="cpu").pin_memory(), torch.empty_like(s.off, device="cpu").pin_memory(),
+               torch.empty_like(s.vel, device="cpu").pin_memory()) for s in species]
+        for (hc, ho, hv), s in zip(hs, species):
+            hc.copy_(s.cell)
+            ho.copy_(s.off)
+            hv.copy_(s.vel)
+        he, hb = e.cpu().pin_memory(), b.cpu().pin_memory()
+        hdG = torch.empty_like(dG, device="cpu").pin_memory()
+        hQ = torch.empty_like(Qs[0], device="cpu").pin_memory()
+        bi = sum(x.numel() * x.element_size() for tr in hs for x in tr) + he.numel() * 8 + hb.numel() * 8
+        bo = sum(x.numel() * x.element_size() for tr in hs for x in tr) + hdG.numel() * 4 + hQ.numel() * 4
+        torch.cuda.synchronize()
+        ee = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for (hc, ho, hv), s in zip(hs, species):
+                s.cell.copy_(hc, non_blocking=True)
+                s.off.copy_(ho, non_blocking=True)
+                s.vel.copy_(hv, non_blocking=True)
+            e.copy_(he, non_blocking=True)
+            b.copy_(hb, non_blocking=True)
+            step()
+            for (hc, ho, hv), s in zip(hs, species):
+                hc.copy_(s.cell, non_blocking=True)
+                ho.copy_(s.off, non_blocking=True)
+                hv.copy_(s.vel, non_blocking=True)
+            hdG.copy_(dG, non_blocking=True)
+            hQ.copy_(Qs[state["i"] % 2], non_blocking=True)
+            z.record(stream)
+            ee.append((a, z))
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(z) for a, z in ee)
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n_part * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+
+    out = None
+    if rank == 0:
+        value = world * n_part * args.steps / (total_ms * 1e-3)
+        avg_push = statistics.mean(push_ms)
+        abytes = algorithmic_bytes(n_part, sizes, 4)
+        peak, peak_kind = peak_hbm()
+        achieved = abytes / (avg_push * 1e-3) / 1e9
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "mesh": f"cube {wl.mesh.n}^3 x 6 tets, +-10% jitter" if wl.mesh.n > 4
+                       else f"cube {wl.mesh.n}^3 x 6 tets", "n_tets": sizes["n_tets"], "n_edges": sizes["n_edges"],
+                       "particles": n_part, "species": len(species), "dt_s": wl.dt, "B0_T": list(wl.B0),
+                       "sort_every": args.sort_every, "precision": "fp32 particle path, fp64 walk test",
+                       "l2": "flushed between timed steps (256 MB write outside the step events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "step": "sort (periodic) + push/gather/walk/deposit + fp64 residuals"},
+            "roofline": {"kernel": "k_push_deposit<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": avg_push,
+                         "traffic": None},
+            "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
+            "residuals": {"continuity_max": float(r[0]), "continuity_scale": float(r[1]),
+                          "divB_max": float(r[2]), "divB_scale": float(r[3])},
+            "status": int(st),
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": e2e,
+        }
+    del lib
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out, wl
+
+
+def cpu_baseline(args, wl, budget_s):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of the workload."""
+    import oracle as O
+    orc = O.Oracle(wl.mesh.xyz, wl.mesh.tets)
+    e, b = orc.project_uniform((0.0, 0.0, 0.0), wl.B0)
+    sp = wl.species[0]
+    threads = O.nproc_threads()
+    n = min(sp.n, 20000)
+    t = time.perf_counter()
+    orc.step(sp.cell[:n], sp.X[:n], sp.V[:n], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
+    dt1 = time.perf_counter() - t
+    rate = n / max(dt1, 1e-9)
+    n2 = int(min(sp.n, max(n, rate * budget_s)))
+    done, el = 0, 0.0
+    while el < 0.5 * budget_s or done == 0:
+        t = time.perf_counter()
+        orc.step(sp.cell[:n2], sp.X[:n2], sp.V[:n2], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
+        el += time.perf_counter() - t
+        done += n2
+    return {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n2} of {sp.n} particles of species 0, {done // n2} step(s), FP64 oracle (C, OpenMP), "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = build_workload(args)
+    import oracle as O
+    orc = O.Oracle(wl.mesh.xyz, wl.mesh.tets)
+    e, b = orc.project_uniform((0.0, 0.0, 0.0), wl.B0)
+    threads = O.nproc_threads()
+    sp = wl.species[0]
+    n = min(sp.n, 20000)
+    t = time.perf_counter()
+    orc.step(sp.cell[:n], sp.X[:n], sp.V[:n], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
+    rate = n / max(time.perf_counter() - t, 1e-9)
+    # each step is a bounded sample sized so the whole run stays within a few minutes
+    per_step_s = min(4.0, 150.0 / max(1, args.steps + args.warmup))
+    ns = int(min(sp.n, max(1000, rate * per_step_s)))
+    cell, X, V = sp.cell[:ns].copy(), sp.X[:ns].copy(), sp.V[:ns].copy()
+    for _ in range(args.warmup):
+        r = orc.step(cell, X, V, e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
+        cell, X, V = r["cell"], r["X"], r["V"]
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r = orc.step(cell, X, V, e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
+        cell, X, V = r["cell"], r["X"], r["V"]
+    el = time.perf_counter() - t
+    value = ns * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": wl.name, "particles_per_step_sample": ns, "particles_full": sp.n,
+                      "step": "FP64 oracle particle step (gather, Boris, walk, deposit) on host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"{ns} of {sp.n} particles per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    out, wl = run_gpu(args)
+    rank, world, _ = dist_env()
+    if rank == 0 and out is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args, wl, args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

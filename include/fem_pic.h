@@ -1,0 +1,199 @@
+/*
+ * fem_pic.h -- C ABI of the GB300 (sm_103a) charge-conserving FEM-PIC hot path.
+ *
+ * The method (arXiv 2103.06737, "Quasi-Helmholtz Decomposition, Gauss' Laws and
+ * Charge Conservation for Finite Element Particle-in-Cell"):
+ *   - fields on an unstructured tet mesh: E in span of Whitney-1 edge functions,
+ *     B in span of Whitney-2 face functions (Sec. II.C);
+ *   - point particles moved by the Lorentz force (Sec. II.A), non-relativistic;
+ *   - the current deposit is the time-integrated current G_e = int W1_e . dr along
+ *     each particle's path, and the node charge follows from it, so the discrete
+ *     continuity equation D0^T dG = dQ holds analytically (Sec. IV.B.1);
+ *   - [grad], [curl], [div] are the signed incidence matrices D0, D1, D2 (Sec. II.C).
+ *
+ * Conventions shared by every call:
+ *   - Mesh numbering.  Tet vertices are taken in increasing global id
+ *     (v0<v1<v2<v3); local edges are (01,02,03,12,13,23); local face k is opposite
+ *     local vertex k.  Global edges are the sorted node pairs (i<j), global faces
+ *     the sorted triples (i<j<k), each numbered in lexicographic order.  Edge DOF
+ *     e_ij is the circulation of E along i->j; face DOF b_ijk the flux of B along
+ *     (x_j-x_i)x(x_k-x_i).  D0[e,i]=-1, D0[e,j]=+1; D1[f,(i,j)]=D1[f,(j,k)]=+1,
+ *     D1[f,(i,k)]=-1; D2[t,f_k]=s_t*(-1)^k with s_t the sign of the sorted tet's volume.
+ *   - Boundary faces (one tet) are PEC walls: a particle reaching one is absorbed
+ *     there and its charge stays on the wall nodes.
+ *   - Particle state (caller-owned, device memory, struct-of-arrays): cell[n]
+ *     (int32, the containing tet, -1 once absorbed), off[3*n] (planar x|y|z blocks:
+ *     position minus the position of the cell's vertex v0), vel[3*n] (planar).
+ *     off/vel are float in FP_FP32 mode and double in FP_FP64 mode.
+ *   - Field DOFs e[N_e], b[N_f] are double (device).  Deposit outputs dG[N_e],
+ *     Q[N_n] are float in FP_FP32 mode and double in FP_FP64 mode (device).
+ *   - All device work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous unless stated.  Errors found by kernels (walk
+ *     bound, invalid cell) are OR-ed into a device status word read by
+ *     fem_pic_status().  No exception crosses the ABI; every call returns fp_status.
+ *   - Ownership: the library owns the handle, its mesh tables and its scratch;
+ *     the caller owns every pointer it passes.  Host pointers are read during the
+ *     call only.
+ */
+#ifndef FEM_PIC_H
+#define FEM_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_pic fem_pic_t;
+
+typedef enum {
+    FP_OK = 0,
+    FP_EINVAL = 1,   /* bad argument, size or pointer; invalid cell id */
+    FP_ECUDA = 2,    /* a CUDA runtime call failed (text in fem_pic_last_error) */
+    FP_EWALK = 3,    /* a particle hit the crossing bound of the tet walk */
+    FP_ENOCONV = 4,  /* an iterative solve reached its iteration cap */
+    FP_EGEOM = 5     /* a tet with zero volume, or a non-manifold face */
+} fp_status;
+
+enum { FP_FP64 = 0, FP_FP32 = 1 };
+
+/* fem_pic_push_deposit flags */
+enum {
+    FP_ACCUMULATE = 1, /* add into dG and Q instead of overwriting them */
+    FP_NO_AGGREGATE = 2 /* one global atomic per contribution (no warp aggregation) */
+};
+
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_tets;
+    const double* xyz;   /* host [3*n_nodes], interleaved x,y,z per node */
+    const int32_t* tet;  /* host [4*n_tets], node ids, any order */
+} fp_mesh;
+
+/* CSR matrix with int8 values (incidence), host memory */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int32_t* row_ptr; /* [n_rows+1] */
+    const int32_t* col;     /* [nnz], increasing within a row */
+    const int8_t* val;      /* [nnz] */
+} fp_csr_i8;
+
+typedef struct {
+    int64_t n;        /* number of particles */
+    int32_t* cell;    /* device [n] */
+    void* off;        /* device [3*n], float or double per precision */
+    void* vel;        /* device [3*n], float or double per precision */
+    double q;         /* charge of one physical particle (C) */
+    double m;         /* mass of one physical particle (kg) */
+    double w;         /* macro weight: physical particles per macro-particle */
+} fp_particles;
+
+/*
+ * Build the discrete complex {N,E,F,T} of a tet mesh (Sec. II.C) and upload the
+ * per-tet tables.  D0, D1, D2 may be NULL; when given they are checked entry by
+ * entry against the library's own derivation (same numbering as above) and a
+ * mismatch returns FP_EINVAL.  precision is FP_FP64 or FP_FP32 (particle path).
+ * Uses the current CUDA device.  Synchronous.  *out is NULL on failure.
+ */
+fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_i8* D1,
+                         const fp_csr_i8* D2, int precision, fem_pic_t** out);
+
+/* Free the handle and every device buffer it owns (synchronises the device). */
+void fem_pic_destroy(fem_pic_t* ctx);
+
+/* Text of the last error on this handle (or of the last failed create if ctx is NULL). */
+const char* fem_pic_last_error(const fem_pic_t* ctx);
+
+/* sizes[0..3] = N_n, N_e, N_f, N_t; sizes[4] = precision */
+fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]);
+
+/*
+ * Copy incidence matrix `which` (0: D0, 1: D1, 2: D2) to caller host buffers.
+ * row_ptr [n_rows+1], col [nnz], val [nnz]; nnz = 2 N_e, 3 N_f, 4 N_t.  Synchronous.
+ */
+fp_status fem_pic_incidence(const fem_pic_t* ctx, int which, int32_t* row_ptr, int32_t* col,
+                            int8_t* val);
+
+/*
+ * Copy topology tables to host: tet_nodes [4 N_t] (sorted vertex ids), tet_edges
+ * [6 N_t], tet_faces [4 N_t], tet_neigh [4 N_t] (-1 = wall).  Any may be NULL.
+ */
+fp_status fem_pic_topology(const fem_pic_t* ctx, int32_t* tet_nodes, int32_t* tet_edges,
+                           int32_t* tet_faces, int32_t* tet_neigh);
+
+/*
+ * DOFs of uniform fields E0, B0 (host double[3] each): e_ij = E0.(x_j-x_i),
+ * b_ijk = B0.(x_j-x_i)x(x_k-x_i)/2, written to device e[N_e], b[N_f] (either may
+ * be NULL).  The W1/W2 interpolants of these DOFs reproduce E0 and B0 exactly.
+ */
+fp_status fem_pic_project_uniform(fem_pic_t* ctx, const double E0[3], const double B0[3], double* e,
+                                  double* b, void* stream);
+
+/*
+ * Load particles: X (device double [3*n], interleaved x,y,z) with their containing
+ * tets cell[n] (device) -> off (device [3*n] planar, float/double per precision).
+ * A cell id outside [0,N_t) sets FP_EINVAL in the status word.
+ */
+fp_status fem_pic_particles_from_global(fem_pic_t* ctx, int64_t n, const int32_t* cell,
+                                        const double* X, void* off, void* stream);
+
+/* Positions back to global coordinates: X (device double [3*n], interleaved). */
+fp_status fem_pic_particles_to_global(fem_pic_t* ctx, int64_t n, const int32_t* cell,
+                                      const void* off, double* X, void* stream);
+
+/*
+ * THE HOT PATH: one particle step of one species (Sec. II.A, II.C, IV.B.1).
+ * For each live particle: barycentric coordinates lambda in its tet; gather
+ * E = sum e_k W1_k(lambda) from e and B = sum b_f W2_f(lambda) from b; Boris push
+ * v <- v(E,B,q/m,dt); straight path x -> x + dt v walked tet to tet (exit tests in
+ * FP64); on every piece inside tet T from lambda^a to lambda^c the Whitney-1 path
+ * integral dG_ij += q w (lambda^a_i lambda^c_j - lambda^a_j lambda^c_i) on T's
+ * 6 edges; at the end point Q_n += q w lambda_n on the end tet's 4 nodes
+ * (Whitney-0 charge).  Reaching a wall absorbs the particle (cell = -1, charge at the
+ * wall point); more than max_cross crossings stops it at its last crossing point and
+ * sets FP_EWALK in the status word.  dG and Q are zeroed first unless FP_ACCUMULATE.
+ * Particle arrays are updated in place.  Asynchronous.
+ */
+fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
+                               const fp_particles* p, double dt, int max_cross, void* dG, void* Q,
+                               int flags, void* stream);
+
+/*
+ * Whitney-0 charge of the particles at their current positions:
+ * Q_n (+)= q w lambda_n (Sec. IV.B.1, the node charge the continuity equation pairs
+ * with dG).  Q is zeroed first unless FP_ACCUMULATE.  Asynchronous.
+ */
+fp_status fem_pic_deposit_charge(fem_pic_t* ctx, const fp_particles* p, void* Q, int flags,
+                                 void* stream);
+
+/*
+ * Counting sort of one species by cell (dead particles last): src -> dst, both
+ * caller-owned with the same n, q, m, w; src is not modified.  Keeps particles of a
+ * cell together so the push reads each tet's tables once per run of particles and
+ * aggregates deposits before its global atomics.  Uses library-owned scratch
+ * (grown on demand, kept until destroy).  Asynchronous.
+ */
+fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* dst, void* stream);
+
+/*
+ * Invariant residuals, FP64 (Sec. II.A continuity, Sec. IV.B.1, Sec. V item 5):
+ *   out[0] = max_n |(D0^T dG)_n - (Q_new - Q_old)_n|,  out[1] = max_n of the sum of
+ *            the absolute values of those terms (scale);
+ *   out[2] = max_t |(D2 b)_t|,  out[3] = max_t sum_f |b_f| over the tet's faces.
+ * dG, Q_new, Q_old have the particle precision; b is double.  Any input may be NULL
+ * (its entries are then 0).  out is device double[4].  Asynchronous.
+ */
+fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
+                            const double* b, double* out, void* stream);
+
+/*
+ * Synchronise `stream`, return and clear the device status word:
+ * FP_OK, FP_EWALK or FP_EINVAL (the first error class seen, EINVAL first).
+ */
+fp_status fem_pic_status(fem_pic_t* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_PIC_H */

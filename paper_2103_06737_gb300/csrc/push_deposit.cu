@@ -1,0 +1,464 @@
+// The per-particle hot path: Whitney gather, Boris push, tet walk, charge-conserving
+// Whitney-1 current deposit and Whitney-0 charge deposit (Sec. II.A, II.C, IV.B.1).
+//
+// One thread per particle, particles in struct-of-arrays, one warp = 32 consecutive
+// particles.  After a cell sort most warps hold a few runs of particles that share
+// a tet; the per-tet tables are then read once per run (broadcast loads), and the
+// deposits of particles whose path stays inside their tet are reduced per run with
+// warp shuffles before one global atomic per edge/node.  Particles that cross faces
+// deposit each piece with direct atomics.
+//
+// Precision: gather, push and deposit products in Real (float or double).  The exit
+// test of the walk (barycentric coordinates of the end point, crossing fraction,
+// argmin) is always FP64.  The piece deposit uses the factored form
+//   dG_ab = q w (l^a_a (l^c_b - l^a_b) - l^a_b (l^c_a - l^a_a)),
+// algebraically equal to q w (l^a_a l^c_b - l^a_b l^c_a), the exact line integral of
+// W1_ab along a straight piece; the differences are formed in FP64 so the Real products
+// do not cancel.
+#include "internal.cuh"
+
+namespace fempic {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Geo {
+    double o[3];
+    double g[9];
+};
+
+__device__ __forceinline__ void load_geo(const TetGeo* __restrict__ geo, int c, Geo& G) {
+    const double2* p = reinterpret_cast<const double2*>(geo + c);
+    double2 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2), e = __ldg(p + 3), f = __ldg(p + 4),
+            h = __ldg(p + 5);
+    G.o[0] = a.x;
+    G.o[1] = a.y;
+    G.o[2] = b.x;
+    G.g[0] = b.y;
+    G.g[1] = d.x;
+    G.g[2] = d.y;
+    G.g[3] = e.x;
+    G.g[4] = e.y;
+    G.g[5] = f.x;
+    G.g[6] = f.y;
+    G.g[7] = h.x;
+    G.g[8] = h.y;
+}
+
+__device__ __forceinline__ void load_topo(const TetTopo* __restrict__ topo, int c, TetTopo& T) {
+    const int4* p = reinterpret_cast<const int4*>(topo + c);
+    int4 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2), e = __ldg(p + 3), f = __ldg(p + 4);
+    T.node[0] = a.x;
+    T.node[1] = a.y;
+    T.node[2] = a.z;
+    T.node[3] = a.w;
+    T.edge[0] = b.x;
+    T.edge[1] = b.y;
+    T.edge[2] = b.z;
+    T.edge[3] = b.w;
+    T.edge[4] = d.x;
+    T.edge[5] = d.y;
+    T.face[0] = d.z;
+    T.face[1] = d.w;
+    T.face[2] = e.x;
+    T.face[3] = e.y;
+    T.nb[0] = e.z;
+    T.nb[1] = e.w;
+    T.nb[2] = f.x;
+    T.nb[3] = f.y;
+}
+
+// barycentric coordinates of a point given relative to the tet's origin (FP64)
+__device__ __forceinline__ void bary(const Geo& G, const double r[3], double l[4]) {
+    l[1] = G.g[0] * r[0] + G.g[1] * r[1] + G.g[2] * r[2];
+    l[2] = G.g[3] * r[0] + G.g[4] * r[1] + G.g[5] * r[2];
+    l[3] = G.g[6] * r[0] + G.g[7] * r[1] + G.g[8] * r[2];
+    l[0] = ((1.0 - l[1]) - l[2]) - l[3];
+}
+
+template <typename Real>
+__device__ __forceinline__ void cross(const Real a[3], const Real b[3], Real o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// E = sum_k e_k W1_k(l), B = sum_f b_f W2_f(l) in one tet (Sec. II.C)
+template <typename Real>
+__device__ __forceinline__ void gather(const Geo& G, const TetTopo& T, const double* __restrict__ e,
+                                       const double* __restrict__ b, const double la[4], Real E[3],
+                                       Real B[3]) {
+    Real g[4][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[1][i] = (Real)G.g[i];
+        g[2][i] = (Real)G.g[3 + i];
+        g[3][i] = (Real)G.g[6 + i];
+        g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+    }
+    const Real L[4] = {(Real)la[0], (Real)la[1], (Real)la[2], (Real)la[3]};
+    Real ev[6], bv[4];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ev[k] = (Real)__ldg(e + T.edge[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bv[k] = (Real)__ldg(b + T.face[k]);
+    // W1_ab = L_a g_b - L_b g_a over (01,02,03,12,13,23)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        E[i] = ev[0] * (L[0] * g[1][i] - L[1] * g[0][i]) + ev[1] * (L[0] * g[2][i] - L[2] * g[0][i]) +
+               ev[2] * (L[0] * g[3][i] - L[3] * g[0][i]) + ev[3] * (L[1] * g[2][i] - L[2] * g[1][i]) +
+               ev[4] * (L[1] * g[3][i] - L[3] * g[1][i]) + ev[5] * (L[2] * g[3][i] - L[3] * g[2][i]);
+    }
+    // W2_abc = 2 (L_a g_b x g_c + L_b g_c x g_a + L_c g_a x g_b), face k opposite vertex k
+    Real x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
+    cross(g[0], g[1], x01);
+    cross(g[0], g[2], x02);
+    cross(g[0], g[3], x03);
+    cross(g[1], g[2], x12);
+    cross(g[1], g[3], x13);
+    cross(g[2], g[3], x23);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Real f0 = L[1] * x23[i] - L[2] * x13[i] + L[3] * x12[i];  // (1,2,3)
+        Real f1 = L[0] * x23[i] - L[2] * x03[i] + L[3] * x02[i];  // (0,2,3)
+        Real f2 = L[0] * x13[i] - L[1] * x03[i] + L[3] * x01[i];  // (0,1,3)
+        Real f3 = L[0] * x12[i] - L[1] * x02[i] + L[2] * x01[i];  // (0,1,2)
+        B[i] = (Real)2 * (bv[0] * f0 + bv[1] * f1 + bv[2] * f2 + bv[3] * f3);
+    }
+}
+
+// non-relativistic Boris rotation; h = q dt / (2 m)
+template <typename Real>
+__device__ __forceinline__ void boris(Real v[3], const Real E[3], const Real B[3], Real h) {
+    Real vm[3], t[3], s[3], c[3], vp[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        vm[i] = v[i] + h * E[i];
+        t[i] = h * B[i];
+    }
+    Real tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    Real f = (Real)2 / ((Real)1 + tt);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] = f * t[i];
+    cross(vm, t, c);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vp[i] = vm[i] + c[i];
+    cross(vp, s, c);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = vm[i] + c[i] + h * E[i];
+}
+
+// end point relative to the start origin, without FMA contraction (reproducible on a CPU)
+__device__ __forceinline__ float step_pos(float x, float dt, float v) {
+    return __fadd_rn(x, __fmul_rn(dt, v));
+}
+__device__ __forceinline__ double step_pos(double x, double dt, double v) {
+    return __dadd_rn(x, __dmul_rn(dt, v));
+}
+
+template <typename Real>
+__device__ __forceinline__ void piece_values(const double la[4], const double lx[4], double qw,
+                                             Real val[6]) {
+    Real A[4], D[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = (Real)la[k];
+        D[k] = (Real)(lx[k] - la[k]);
+    }
+    const Real w = (Real)qw;
+    val[0] = w * (A[0] * D[1] - A[1] * D[0]);
+    val[1] = w * (A[0] * D[2] - A[2] * D[0]);
+    val[2] = w * (A[0] * D[3] - A[3] * D[0]);
+    val[3] = w * (A[1] * D[2] - A[2] * D[1]);
+    val[4] = w * (A[1] * D[3] - A[3] * D[1]);
+    val[5] = w * (A[2] * D[3] - A[3] * D[2]);
+}
+
+template <typename Real>
+__device__ __forceinline__ void deposit_piece(const TetTopo& T, const double la[4], const double lx[4],
+                                              double qw, Real* __restrict__ dG) {
+    Real val[6];
+    piece_values<Real>(la, lx, qw, val);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], val[k]);
+}
+
+template <typename Real>
+__device__ __forceinline__ void deposit_charge(const TetTopo& T, const double l[4], double qw,
+                                               Real* __restrict__ Q) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], (Real)qw * (Real)l[k]);
+}
+
+// Sum `v[0..NV)` over each run of equal `key` in lane order; the first lane of a run
+// (with key >= 0) issues one atomic per value.  All 32 lanes must call this.
+template <typename Real, int NV>
+__device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* heads_out, int* end_out) {
+    const int lane = threadIdx.x & 31;
+    int prev = __shfl_up_sync(kFull, key, 1);
+    bool head = lane == 0 || prev != key;
+    unsigned heads = __ballot_sync(kFull, head);
+    unsigned above = heads & ~((2u << lane) - 1u);
+    int end = above ? __ffs(above) - 1 : 32;
+    if (heads != kFull) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            Real x = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                Real u = __shfl_down_sync(kFull, x, o);
+                if (lane + o < end) x += u;
+            }
+            v[k] = x;
+        }
+    }
+    *heads_out = heads;
+    *end_out = end;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_push_deposit(
+    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ e,
+    const double* __restrict__ b, int32_t* __restrict__ cell, Real* __restrict__ off,
+    Real* __restrict__ vel, int64_t n, int32_t nt, double qmdt2, Real dt, double qw, int max_cross,
+    int aggregate, Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t p = base + lane;
+        int c = p < n ? cell[p] : -1;
+        if (c >= nt) {
+            atomicOr(status, ST_INVAL);
+            c = -1;
+        }
+        int key = -1;
+        Real agg[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) agg[k] = (Real)0;
+        TetTopo T;
+        if (c >= 0) {
+            Geo G;
+            load_geo(geo, c, G);
+            load_topo(topo, c, T);
+            Real x[3] = {off[p], off[n + p], off[2 * n + p]};
+            Real v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
+            double la[4];
+            {
+                double r[3] = {(double)x[0], (double)x[1], (double)x[2]};
+                bary(G, r, la);
+            }
+            Real E[3], B[3];
+            gather<Real>(G, T, e, b, la, E, B);
+            boris<Real>(v, E, B, (Real)qmdt2);
+            vel[p] = v[0];
+            vel[n + p] = v[1];
+            vel[2 * n + p] = v[2];
+            double db[3], ca[3], rel[3], os[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                db[i] = (double)step_pos(x[i], dt, v[i]);
+                ca[i] = (double)x[i];
+                rel[i] = db[i];
+                os[i] = G.o[i];
+            }
+            // ---- tet walk (FP64 exit test) ----
+            int t = c, entry = -1, nc = 0, end_cell = c;
+            double end_off[3];
+            TetTopo Tc = T;
+            for (;;) {
+                double lb[4];
+                bary(G, rel, lb);
+                int kx = -1;
+                double smin = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k == entry || !(lb[k] < 0.0)) continue;
+                    double den = la[k] - lb[k];
+                    double s = den > 0.0 ? la[k] / den : 0.0;
+                    s = fmin(fmax(s, 0.0), 1.0);
+                    if (kx < 0 || s < smin) {
+                        kx = k;
+                        smin = s;
+                    }
+                }
+                if (kx < 0) {
+                    if (nc == 0 && aggregate) {
+                        piece_values<Real>(la, lb, qw, agg);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) agg[6 + k] = (Real)qw * (Real)lb[k];
+                        key = c;
+                    } else {
+                        deposit_piece<Real>(Tc, la, lb, qw, dG);
+                        deposit_charge<Real>(Tc, lb, qw, Q);
+                    }
+                    end_cell = t;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) end_off[i] = rel[i];
+                    break;
+                }
+                if (nc == max_cross) {
+                    deposit_charge<Real>(Tc, la, qw, Q);
+                    atomicOr(status, ST_WALK);
+                    end_cell = t;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+                    break;
+                }
+                double lc[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
+                deposit_piece<Real>(Tc, la, lc, qw, dG);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) ca[i] = ca[i] + smin * (db[i] - ca[i]);
+                const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
+                if (tn < 0) {  // PEC wall: absorbed, charge stays at the wall point
+                    deposit_charge<Real>(Tc, lc, qw, Q);
+                    end_cell = -1;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+                    break;
+                }
+                TetTopo Tn;
+                load_topo(topo, tn, Tn);
+                int ent = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int vtx = Tn.node[a];
+                    double lv = 0.0;
+                    bool found = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (Tc.node[j] == vtx) {
+                            lv = lc[j];
+                            found = true;
+                        }
+                    la[a] = lv;
+                    if (!found) ent = a;
+                }
+                load_geo(geo, tn, G);
+                Tc = Tn;
+                t = tn;
+                entry = ent;
+                ++nc;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) rel[i] = (os[i] - G.o[i]) + db[i];
+            }
+            cell[p] = end_cell;
+            off[p] = (Real)end_off[0];
+            off[n + p] = (Real)end_off[1];
+            off[2 * n + p] = (Real)end_off[2];
+        }
+        if (aggregate) {
+            unsigned heads;
+            int end;
+            warp_run_reduce<Real, 10>(key, agg, &heads, &end);
+            const bool head = (heads >> lane) & 1u;
+            if (head && key >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], agg[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], agg[6 + k]);
+            }
+        }
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_deposit_charge(const TetGeo* __restrict__ geo,
+                                                        const TetTopo* __restrict__ topo,
+                                                        const int32_t* __restrict__ cell,
+                                                        const Real* __restrict__ off, int64_t n,
+                                                        int32_t nt, double qw, Real* __restrict__ Q,
+                                                        int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t p = base + lane;
+        int c = p < n ? cell[p] : -1;
+        if (c >= nt) {
+            atomicOr(status, ST_INVAL);
+            c = -1;
+        }
+        Real v[4] = {0, 0, 0, 0};
+        TetTopo T;
+        if (c >= 0) {
+            Geo G;
+            load_geo(geo, c, G);
+            load_topo(topo, c, T);
+            double r[3] = {(double)off[p], (double)off[n + p], (double)off[2 * n + p]}, l[4];
+            bary(G, r, l);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = (Real)qw * (Real)l[k];
+        }
+        unsigned heads;
+        int end;
+        warp_run_reduce<Real, 4>(c, v, &heads, &end);
+        if (((heads >> lane) & 1u) && c >= 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], v[k]);
+        }
+    }
+}
+
+int grid_for(int64_t n) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + 255) / 256;
+    int64_t cap = (int64_t)sms * 8;  // grid-stride beyond 8 resident 256-thread blocks per SM
+    if (blocks > cap) blocks = cap;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+
+}  // namespace
+
+fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, const fp_particles* p,
+                              double dt, int max_cross, void* dG, void* Q, int flags,
+                              cudaStream_t s) {
+    const bool f32 = ctx->precision == FP_FP32;
+    const size_t rs = f32 ? 4 : 8;
+    if (!(flags & FP_ACCUMULATE)) {
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
+    }
+    if (p->n == 0) return FP_OK;
+    const double qmdt2 = p->q * dt / (2.0 * p->m);
+    const double qw = p->q * p->w;
+    const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
+    const int grid = grid_for(p->n);
+    if (f32)
+        k_push_deposit<float><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell, (float*)p->off,
+                                                   (float*)p->vel, p->n, (int32_t)ctx->hc.nt, qmdt2,
+                                                   (float)dt, qw, max_cross, agg, (float*)dG, (float*)Q,
+                                                   ctx->d_status);
+    else
+        k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
+                                                    (double*)p->off, (double*)p->vel, p->n,
+                                                    (int32_t)ctx->hc.nt, qmdt2, dt, qw, max_cross, agg,
+                                                    (double*)dG, (double*)Q, ctx->d_status);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
+                                cudaStream_t s) {
+    const bool f32 = ctx->precision == FP_FP32;
+    if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (f32 ? 4 : 8) * ctx->hc.nn, s));
+    if (p->n == 0) return FP_OK;
+    const double qw = p->q * p->w;
+    const int grid = grid_for(p->n);
+    if (f32)
+        k_deposit_charge<float><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (const float*)p->off,
+                                                     p->n, (int32_t)ctx->hc.nt, qw, (float*)Q,
+                                                     ctx->d_status);
+    else
+        k_deposit_charge<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell,
+                                                      (const double*)p->off, p->n, (int32_t)ctx->hc.nt,
+                                                      qw, (double*)Q, ctx->d_status);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+}  // namespace fempic

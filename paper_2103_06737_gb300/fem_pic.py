@@ -1,0 +1,371 @@
+"""Thin Python binding of libfempic.so (C ABI in include/fem_pic.h).
+
+Argument marshalling only: torch tensors give device memory and streams, every
+step of the hot path runs in the library's CUDA kernels.  Function names match
+the C entry points.  If the library is missing this module raises; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FP_OK, FP_EINVAL, FP_ECUDA, FP_EWALK, FP_ENOCONV, FP_EGEOM = range(6)
+FP_FP64, FP_FP32 = 0, 1
+FP_ACCUMULATE, FP_NO_AGGREGATE = 1, 2
+_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ECUDA", 3: "FP_EWALK", 4: "FP_ENOCONV", 5: "FP_EGEOM"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FemPicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class FPMesh(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("xyz", ctypes.c_void_p),
+                ("tet", ctypes.c_void_p)]
+
+
+class FPCsr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class FPParticles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("cell", ctypes.c_void_p), ("off", ctypes.c_void_p),
+                ("vel", ctypes.c_void_p), ("q", ctypes.c_double), ("m", ctypes.c_double),
+                ("w", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def lib():
+    """Load libfempic.so (built in-tree by build.py).  Raises if it is not there."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.SO
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfempic.so not found at {path}: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        sig = {
+            "fem_pic_create": (I32, [ctypes.POINTER(FPMesh), ctypes.POINTER(FPCsr), ctypes.POINTER(FPCsr),
+                                     ctypes.POINTER(FPCsr), I32, ctypes.POINTER(P)]),
+            "fem_pic_destroy": (None, [P]),
+            "fem_pic_last_error": (ctypes.c_char_p, [P]),
+            "fem_pic_sizes": (I32, [P, P]),
+            "fem_pic_incidence": (I32, [P, I32, P, P, P]),
+            "fem_pic_topology": (I32, [P, P, P, P, P]),
+            "fem_pic_project_uniform": (I32, [P, P, P, P, P, P]),
+            "fem_pic_particles_from_global": (I32, [P, I64, P, P, P, P]),
+            "fem_pic_particles_to_global": (I32, [P, I64, P, P, P, P]),
+            "fem_pic_push_deposit": (I32, [P, P, P, ctypes.POINTER(FPParticles), D, I32, P, P, I32, P]),
+            "fem_pic_deposit_charge": (I32, [P, ctypes.POINTER(FPParticles), P, I32, P]),
+            "fem_pic_sort": (I32, [P, ctypes.POINTER(FPParticles), ctypes.POINTER(FPParticles), P]),
+            "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
+            "fem_pic_status": (I32, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _err(h) -> str:
+    s = lib().fem_pic_last_error(h)
+    return s.decode() if s else ""
+
+
+def _check(st: int, h=None):
+    if st != FP_OK:
+        raise FemPicError(st, _err(h))
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(t))
+
+
+def _need(t, dtype, numel=None, cuda=True, name="tensor"):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if cuda and not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclass
+class Species:
+    """Device particle state of one species (SoA, torch-owned)."""
+    cell: torch.Tensor   # int32 [n]
+    off: torch.Tensor    # [3, n] float32 or float64: position minus the cell's vertex-0 position
+    vel: torch.Tensor    # [3, n]
+    q: float
+    m: float
+    w: float
+
+    @property
+    def n(self) -> int:
+        return int(self.cell.numel())
+
+    def abi(self) -> FPParticles:
+        return FPParticles(self.n, self.cell.data_ptr(), self.off.data_ptr(), self.vel.data_ptr(),
+                           float(self.q), float(self.m), float(self.w))
+
+    def empty_like(self) -> "Species":
+        return Species(torch.empty_like(self.cell), torch.empty_like(self.off), torch.empty_like(self.vel),
+                       self.q, self.m, self.w)
+
+
+def _csr_struct(m):
+    if m is None:
+        return None, None
+    rp = np.ascontiguousarray(m[0], dtype=np.int32)
+    col = np.ascontiguousarray(m[1], dtype=np.int32)
+    val = np.ascontiguousarray(m[2], dtype=np.int8)
+    s = FPCsr(rp.size - 1, int(m[3]), col.size, rp.ctypes.data, col.ctypes.data, val.ctypes.data)
+    return s, (rp, col, val)
+
+
+# ---------------------------------------------------------------- C ABI wrappers
+
+def fem_pic_create(xyz, tets, D0=None, D1=None, D2=None, precision: int = FP_FP32):
+    """Build the mesh handle.  D0/D1/D2: optional (row_ptr, col, val, n_cols) CSR to validate."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    mesh = FPMesh(xyz.shape[0], tets.shape[0], xyz.ctypes.data, tets.ctypes.data)
+    keep = []
+    cs = []
+    for m in (D0, D1, D2):
+        s, k = _csr_struct(m)
+        keep.append(k)
+        cs.append(ctypes.pointer(s) if s is not None else None)
+    h = ctypes.c_void_p()
+    st = lib().fem_pic_create(ctypes.byref(mesh), cs[0], cs[1], cs[2], int(precision), ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def fem_pic_destroy(h):
+    lib().fem_pic_destroy(h)
+
+
+def fem_pic_last_error(h) -> str:
+    return _err(h)
+
+
+def fem_pic_sizes(h) -> dict:
+    s = np.zeros(5, dtype=np.int64)
+    _check(lib().fem_pic_sizes(h, _ptr(s)), h)
+    return dict(n_nodes=int(s[0]), n_edges=int(s[1]), n_faces=int(s[2]), n_tets=int(s[3]),
+                precision=int(s[4]))
+
+
+def fem_pic_incidence(h, which: int):
+    sz = fem_pic_sizes(h)
+    rows = (sz["n_edges"], sz["n_faces"], sz["n_tets"])[which]
+    per = (2, 3, 4)[which]
+    rp = np.empty(rows + 1, dtype=np.int32)
+    col = np.empty(rows * per, dtype=np.int32)
+    val = np.empty(rows * per, dtype=np.int8)
+    _check(lib().fem_pic_incidence(h, which, _ptr(rp), _ptr(col), _ptr(val)), h)
+    return rp, col, val
+
+
+def fem_pic_topology(h) -> dict:
+    nt = fem_pic_sizes(h)["n_tets"]
+    out = dict(tet_nodes=np.empty((nt, 4), np.int32), tet_edges=np.empty((nt, 6), np.int32),
+               tet_faces=np.empty((nt, 4), np.int32), tet_neigh=np.empty((nt, 4), np.int32))
+    _check(lib().fem_pic_topology(h, _ptr(out["tet_nodes"]), _ptr(out["tet_edges"]),
+                                  _ptr(out["tet_faces"]), _ptr(out["tet_neigh"])), h)
+    return out
+
+
+def fem_pic_project_uniform(h, E0, B0, e=None, b=None, stream=None):
+    E0 = np.ascontiguousarray(E0, dtype=np.float64)
+    B0 = np.ascontiguousarray(B0, dtype=np.float64)
+    sz = fem_pic_sizes(h)
+    if e is not None:
+        _need(e, torch.float64, sz["n_edges"], name="e")
+    if b is not None:
+        _need(b, torch.float64, sz["n_faces"], name="b")
+    _check(lib().fem_pic_project_uniform(h, _ptr(E0), _ptr(B0), _ptr(e), _ptr(b), _stream(stream)), h)
+
+
+def _real(h):
+    return torch.float32 if fem_pic_sizes(h)["precision"] == FP_FP32 else torch.float64
+
+
+def fem_pic_particles_from_global(h, cell, X, off, stream=None):
+    n = cell.numel()
+    _need(cell, torch.int32, n, name="cell")
+    _need(X, torch.float64, 3 * n, name="X")
+    _need(off, _real(h), 3 * n, name="off")
+    _check(lib().fem_pic_particles_from_global(h, n, _ptr(cell), _ptr(X), _ptr(off), _stream(stream)), h)
+
+
+def fem_pic_particles_to_global(h, cell, off, X, stream=None):
+    n = cell.numel()
+    _need(cell, torch.int32, n, name="cell")
+    _need(off, _real(h), 3 * n, name="off")
+    _need(X, torch.float64, 3 * n, name="X")
+    _check(lib().fem_pic_particles_to_global(h, n, _ptr(cell), _ptr(off), _ptr(X), _stream(stream)), h)
+
+
+def _check_species(h, sp: Species):
+    n = sp.n
+    _need(sp.cell, torch.int32, n, name="cell")
+    _need(sp.off, _real(h), 3 * n, name="off")
+    _need(sp.vel, _real(h), 3 * n, name="vel")
+
+
+def fem_pic_push_deposit(h, e, b, sp: Species, dt: float, dG, Q, max_cross: int = 64, flags: int = 0,
+                         stream=None):
+    sz = fem_pic_sizes(h)
+    R = _real(h)
+    _check_species(h, sp)
+    _need(e, torch.float64, sz["n_edges"], name="e")
+    _need(b, torch.float64, sz["n_faces"], name="b")
+    _need(dG, R, sz["n_edges"], name="dG")
+    _need(Q, R, sz["n_nodes"], name="Q")
+    p = sp.abi()
+    _check(lib().fem_pic_push_deposit(h, _ptr(e), _ptr(b), ctypes.byref(p), float(dt), int(max_cross),
+                                      _ptr(dG), _ptr(Q), int(flags), _stream(stream)), h)
+
+
+def fem_pic_deposit_charge(h, sp: Species, Q, flags: int = 0, stream=None):
+    _check_species(h, sp)
+    _need(Q, _real(h), fem_pic_sizes(h)["n_nodes"], name="Q")
+    p = sp.abi()
+    _check(lib().fem_pic_deposit_charge(h, ctypes.byref(p), _ptr(Q), int(flags), _stream(stream)), h)
+
+
+def fem_pic_sort(h, src: Species, dst: Species, stream=None):
+    _check_species(h, src)
+    _check_species(h, dst)
+    a, b = src.abi(), dst.abi()
+    _check(lib().fem_pic_sort(h, ctypes.byref(a), ctypes.byref(b), _stream(stream)), h)
+
+
+def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
+    _need(out, torch.float64, 4, name="out")
+    _check(lib().fem_pic_residuals(h, _ptr(dG), _ptr(Q_new), _ptr(Q_old), _ptr(b), _ptr(out),
+                                   _stream(stream)), h)
+
+
+def fem_pic_status(h, stream=None) -> int:
+    return int(lib().fem_pic_status(h, _stream(stream)))
+
+
+# ---------------------------------------------------------------- convenience layer
+
+class FemPic:
+    """Owns one library handle; methods forward to the C ABI wrappers above."""
+
+    def __init__(self, xyz, tets, precision: int = FP_FP32, D0=None, D1=None, D2=None):
+        self.h = fem_pic_create(xyz, tets, D0, D1, D2, precision)
+        self.sizes = fem_pic_sizes(self.h)
+        self.precision = precision
+        self.real = torch.float32 if precision == FP_FP32 else torch.float64
+
+    def close(self):
+        if self.h is not None:
+            fem_pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_nodes(self):
+        return self.sizes["n_nodes"]
+
+    @property
+    def n_edges(self):
+        return self.sizes["n_edges"]
+
+    @property
+    def n_faces(self):
+        return self.sizes["n_faces"]
+
+    @property
+    def n_tets(self):
+        return self.sizes["n_tets"]
+
+    def species(self, cell, X, V, q, m, w, device="cuda") -> Species:
+        """Upload one species from host arrays (cell [n], global X [n,3], V [n,3])."""
+        n = int(np.asarray(cell).shape[0])
+        c = torch.as_tensor(np.ascontiguousarray(cell, dtype=np.int32)).to(device)
+        Xd = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float64).reshape(n, 3)).to(device)
+        off = torch.empty((3, n), dtype=self.real, device=device)
+        fem_pic_particles_from_global(self.h, c, Xd, off)
+        vel = torch.as_tensor(np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(n, 3).T)).to(
+            device=device, dtype=self.real).contiguous()
+        return Species(c, off, vel, q, m, w)
+
+    def positions(self, sp: Species) -> torch.Tensor:
+        X = torch.empty((sp.n, 3), dtype=torch.float64, device=sp.cell.device)
+        fem_pic_particles_to_global(self.h, sp.cell, sp.off, X)
+        return X
+
+    def fields_uniform(self, E0, B0, device="cuda"):
+        e = torch.empty(self.n_edges, dtype=torch.float64, device=device)
+        b = torch.empty(self.n_faces, dtype=torch.float64, device=device)
+        fem_pic_project_uniform(self.h, E0, B0, e, b)
+        return e, b
+
+    def push_deposit(self, e, b, sp, dt, dG, Q, max_cross=64, flags=0, stream=None):
+        fem_pic_push_deposit(self.h, e, b, sp, dt, dG, Q, max_cross, flags, stream)
+
+    def deposit_charge(self, sp, Q, flags=0, stream=None):
+        fem_pic_deposit_charge(self.h, sp, Q, flags, stream)
+
+    def sort(self, src, dst, stream=None):
+        fem_pic_sort(self.h, src, dst, stream)
+
+    def residuals(self, dG, Q_new, Q_old, b, out, stream=None):
+        fem_pic_residuals(self.h, dG, Q_new, Q_old, b, out, stream)
+
+    def status(self, stream=None) -> int:
+        return fem_pic_status(self.h, stream)
