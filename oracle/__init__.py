@@ -127,9 +127,9 @@ class Oracle:
 
     def step(self, cell, X, V, e, b, q, m, w, dt, max_cross=64, Xend=None, nthreads=0):
         """One particle step (push if Xend is None, else walk to Xend).  Returns a dict."""
-        cell = np.array(cell, dtype=np.int32, copy=True)
-        X = np.array(X, dtype=np.float64, copy=True).reshape(-1, 3)
-        V = np.array(V, dtype=np.float64, copy=True).reshape(-1, 3)
+        cell = np.array(cell, dtype=np.int32, order="C", copy=True)
+        X = np.array(X, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
+        V = np.array(V, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
         e = _f64(e)
         b = _f64(b)
         n = cell.shape[0]
@@ -158,7 +158,7 @@ class Oracle:
 
     @staticmethod
     def boris(V, E, B, q, m, dt):
-        V = np.array(V, dtype=np.float64, copy=True).reshape(-1, 3)
+        V = np.array(V, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
         E = _f64(E, (-1, 3))
         B = _f64(B, (-1, 3))
         lib().oracle_boris(V.shape[0], _p(V), _p(E), _p(B), float(q), float(m), float(dt))

@@ -187,3 +187,15 @@ def test_exb_drift_through_walk():
     assert np.abs(X - (X0 + nsteps * dt * vE)).max() < 1e-11   # round-off of the gathered fields
     lam = orc.bary(cell, X)
     assert lam.min() > -1e-12
+
+
+def test_wrapper_accepts_any_memory_layout():
+    """Transposed (column-major) inputs give the same result as row-major ones."""
+    m = I.cube_mesh(3, 1.0, 0.1, seed=1)
+    orc = O.Oracle(m.xyz, m.tets)
+    sp = I.uniform_species(m, 50, 1, 0.1, -1.0, 1.0)
+    e = np.zeros(orc.n_edges)
+    b = np.random.default_rng(0).uniform(-1, 1, orc.n_faces)
+    r1 = orc.step(sp.cell, sp.X, sp.V, e, b, -1.0, 1.0, 1.0, 0.1)
+    r2 = orc.step(sp.cell, np.asfortranarray(sp.X), np.asfortranarray(sp.V), e, b, -1.0, 1.0, 1.0, 0.1)
+    assert np.array_equal(r1["V"], r2["V"]) and np.array_equal(r1["X"], r2["X"])
