@@ -178,11 +178,14 @@ fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* ds
 
 /*
  * Invariant residuals, FP64 (Sec. II.A continuity, Sec. IV.B.1, Sec. V item 5):
- *   out[0] = max_n |(D0^T dG)_n - (Q_new - Q_old)_n|,  out[1] = max_n of the sum of
- *            the absolute values of those terms (scale);
- *   out[2] = max_t |(D2 b)_t|,  out[3] = max_t sum_f |b_f| over the tet's faces.
+ *   out[0] = max_n |(D0^T dG)_n - (Q_new - Q_old)_n| over all nodes,  out[1] = max_n of
+ *            the sum of the absolute values of those terms (scale);
+ *   out[2] = max_t |(D2 b)_t|,  out[3] = max_t sum_f |b_f| over the tet's faces;
+ *   out[4], out[5] = as out[0], out[1] over interior nodes only (charge absorbed by a
+ *            PEC wall in an earlier step leaves the particle set, so over several
+ *            steps continuity is checked where the field solve uses it).
  * dG, Q_new, Q_old have the particle precision; b is double.  Any input may be NULL
- * (its entries are then 0).  out is device double[4].  Asynchronous.
+ * (its entries are then 0).  out is device double[6].  Asynchronous.
  */
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
                             const double* b, double* out, void* stream);

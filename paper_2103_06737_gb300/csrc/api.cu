@@ -141,6 +141,14 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
         for (int k = 0; k < 6; ++k) T.edge[k] = hc.te[6 * t + k];
         T.pad[0] = T.pad[1] = 0;
     }
+    std::vector<TetHot> hot(hc.nt);
+    for (int64_t t = 0; t < hc.nt; ++t) {
+        TetHot& H = hot[t];
+        std::memset(&H, 0, sizeof H);
+        for (int k = 0; k < 4; ++k) H.node[k] = hc.tv[4 * t + k];
+        for (int k = 0; k < 6; ++k) H.edge[k] = hc.te[6 * t + k];
+        for (int k = 0; k < 9; ++k) H.g[k] = (float)hc.geo[t].g[k];
+    }
     // node -> incident edges with the sign of D0^T
     std::vector<int32_t> n2e_ptr(hc.nn + 1, 0), n2e_col(2 * hc.ne);
     std::vector<int8_t> n2e_sgn(2 * hc.ne);
@@ -171,6 +179,19 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_n2e_col, n2e_col.data(), n2e_col.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_n2e_sgn, n2e_sgn.data(), n2e_sgn.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_orient, hc.orient.data(), hc.orient.size());
+        if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_hot, hot.data(), hot.size());
+        if (s2 == FP_OK) {
+            int32_t z4[4] = {0, 0, 0, 0};
+            s2 = upload(ctx, &ctx->d_slow_count, z4, 4);
+        }
+        if (s2 == FP_OK) {
+            // boundary flags of nodes (1 = on a PEC face), for the interior residuals
+            std::vector<uint8_t> bn(hc.nn, 0);
+            for (int64_t f = 0; f < hc.nf; ++f)
+                if (hc.bface[f])
+                    for (int k = 0; k < 3; ++k) bn[hc.faces[3 * f + k]] = 1;
+            s2 = upload(ctx, &ctx->d_node_wall, bn.data(), bn.size());
+        }
         if (s2 == FP_OK) {
             int32_t zero = 0;
             s2 = upload(ctx, &ctx->d_status, &zero, 1);
@@ -198,7 +219,8 @@ void fem_pic_destroy(fem_pic_t* ctx) {
     void* ptrs[] = {ctx->d_geo,     ctx->d_topo,    ctx->d_xyz,     ctx->d_edges,
                     ctx->d_faces,   ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn,
                     ctx->d_orient,  ctx->d_status,  ctx->d_sort_count, ctx->d_sort_block,
-                    ctx->d_sort_rank};
+                    ctx->d_sort_rank, ctx->d_hot, ctx->d_slow_idx, ctx->d_slow_count,
+                    ctx->d_node_wall};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     cudaSetDevice(prev);

@@ -31,6 +31,24 @@ struct __align__(16) TetTopo {
 };
 static_assert(sizeof(TetTopo) == 80, "TetTopo layout");
 
+// Per-tet record read by the FP32 particle kernel: one 128-byte line holding what a
+// particle that stays in its tet needs.  node/edge ids and FP32 barycentric gradients
+// are static; the affine field coefficients are rewritten from e, b at every push:
+//   E(off) = E0 + W x off          (W = sum_ab e_ab grad l_a x grad l_b, half the curl of E)
+//   B(off) = B0 + beta off         (lowest-order W2 fields: divergence 3 beta)
+// where off is the position minus the tet's vertex v0.
+struct __align__(128) TetHot {
+    int32_t node[4];
+    int32_t edge[6];
+    float g[9];
+    float E0[3];
+    float W[3];
+    float B0[3];
+    float beta;
+    float pad[3];
+};
+static_assert(sizeof(TetHot) == 128, "TetHot layout");
+
 // bits of the device status word
 enum : int32_t { ST_WALK = 1, ST_INVAL = 2 };
 
@@ -70,7 +88,13 @@ struct fem_pic {
     int32_t* d_n2e_col = nullptr;
     int8_t* d_n2e_sgn = nullptr;
     int8_t* d_orient = nullptr;       // [nt]
+    fempic::TetHot* d_hot = nullptr;  // [nt]
     int32_t* d_status = nullptr;
+    // particles deferred to the FP64 walk (near or across a face)
+    int32_t* d_slow_idx = nullptr;    // [slow_cap]
+    int32_t* d_slow_count = nullptr;  // [1]
+    int64_t slow_cap = 0;
+    uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch
     int32_t* d_sort_count = nullptr;  // [nt + 2]
     int32_t* d_sort_block = nullptr;  // block sums

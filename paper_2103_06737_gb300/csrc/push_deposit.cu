@@ -216,6 +216,109 @@ __device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* h
     *end_out = end;
 }
 
+// ---------------------------------------------------------------- FP64 walk
+// Straight path from xa to xb, both relative to the origin of the start tet c.  Every
+// piece deposits its 6 edge values, the end point its 4 node charges.  When `agg` is
+// non-null and the path stays inside c, the 10 values are returned in agg instead of
+// being added (return true) so the caller can reduce them across the warp.
+template <typename Real>
+__device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, int c,
+                          const double xa[3], const double xb[3], double qw, int max_cross,
+                          Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status,
+                          Real* agg, int* end_cell, double end_off[3]) {
+    Geo G;
+    TetTopo Tc;
+    load_geo(geo, c, G);
+    load_topo(topo, c, Tc);
+    double la[4], ca[3], rel[3], os[3];
+    bary(G, xa, la);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ca[i] = xa[i];
+        rel[i] = xb[i];
+        os[i] = G.o[i];
+    }
+    int t = c, entry = -1, nc = 0;
+    for (;;) {
+        double lb[4];
+        bary(G, rel, lb);
+        int kx = -1;
+        double smin = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k == entry || !(lb[k] < 0.0)) continue;
+            double den = la[k] - lb[k];
+            double s = den > 0.0 ? la[k] / den : 0.0;
+            s = fmin(fmax(s, 0.0), 1.0);
+            if (kx < 0 || s < smin) {
+                kx = k;
+                smin = s;
+            }
+        }
+        if (kx < 0) {
+            *end_cell = t;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) end_off[i] = rel[i];
+            if (nc == 0 && agg) {
+                piece_values<Real>(la, lb, qw, agg);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) agg[6 + k] = (Real)qw * (Real)lb[k];
+                return true;
+            }
+            deposit_piece<Real>(Tc, la, lb, qw, dG);
+            deposit_charge<Real>(Tc, lb, qw, Q);
+            return false;
+        }
+        if (nc == max_cross) {  // bound reached: stop at the last crossing point
+            deposit_charge<Real>(Tc, la, qw, Q);
+            atomicOr(status, ST_WALK);
+            *end_cell = t;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+            return false;
+        }
+        double lc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
+        deposit_piece<Real>(Tc, la, lc, qw, dG);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ca[i] = ca[i] + smin * (xb[i] - ca[i]);
+        const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
+        if (tn < 0) {  // PEC wall: absorbed, its charge stays at the wall point
+            deposit_charge<Real>(Tc, lc, qw, Q);
+            *end_cell = -1;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+            return false;
+        }
+        TetTopo Tn;
+        load_topo(topo, tn, Tn);
+        int ent = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int vtx = Tn.node[a];
+            double lv = 0.0;
+            bool found = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (Tc.node[j] == vtx) {
+                    lv = lc[j];
+                    found = true;
+                }
+            la[a] = lv;
+            if (!found) ent = a;
+        }
+        load_geo(geo, tn, G);
+        Tc = Tn;
+        t = tn;
+        entry = ent;
+        ++nc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) rel[i] = (os[i] - G.o[i]) + xb[i];
+    }
+}
+
+// ---------------------------------------------------------------- FP64 mode
 template <typename Real>
 __global__ void __launch_bounds__(256) k_push_deposit(
     const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ e,
@@ -243,107 +346,22 @@ __global__ void __launch_bounds__(256) k_push_deposit(
             load_topo(topo, c, T);
             Real x[3] = {off[p], off[n + p], off[2 * n + p]};
             Real v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
-            double la[4];
-            {
-                double r[3] = {(double)x[0], (double)x[1], (double)x[2]};
-                bary(G, r, la);
-            }
+            double xa[3] = {(double)x[0], (double)x[1], (double)x[2]}, la[4];
+            bary(G, xa, la);
             Real E[3], B[3];
             gather<Real>(G, T, e, b, la, E, B);
             boris<Real>(v, E, B, (Real)qmdt2);
             vel[p] = v[0];
             vel[n + p] = v[1];
             vel[2 * n + p] = v[2];
-            double db[3], ca[3], rel[3], os[3];
+            double xb[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                db[i] = (double)step_pos(x[i], dt, v[i]);
-                ca[i] = (double)x[i];
-                rel[i] = db[i];
-                os[i] = G.o[i];
-            }
-            // ---- tet walk (FP64 exit test) ----
-            int t = c, entry = -1, nc = 0, end_cell = c;
+            for (int i = 0; i < 3; ++i) xb[i] = (double)step_pos(x[i], dt, v[i]);
+            int end_cell;
             double end_off[3];
-            TetTopo Tc = T;
-            for (;;) {
-                double lb[4];
-                bary(G, rel, lb);
-                int kx = -1;
-                double smin = 0.0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (k == entry || !(lb[k] < 0.0)) continue;
-                    double den = la[k] - lb[k];
-                    double s = den > 0.0 ? la[k] / den : 0.0;
-                    s = fmin(fmax(s, 0.0), 1.0);
-                    if (kx < 0 || s < smin) {
-                        kx = k;
-                        smin = s;
-                    }
-                }
-                if (kx < 0) {
-                    if (nc == 0 && aggregate) {
-                        piece_values<Real>(la, lb, qw, agg);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) agg[6 + k] = (Real)qw * (Real)lb[k];
-                        key = c;
-                    } else {
-                        deposit_piece<Real>(Tc, la, lb, qw, dG);
-                        deposit_charge<Real>(Tc, lb, qw, Q);
-                    }
-                    end_cell = t;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) end_off[i] = rel[i];
-                    break;
-                }
-                if (nc == max_cross) {
-                    deposit_charge<Real>(Tc, la, qw, Q);
-                    atomicOr(status, ST_WALK);
-                    end_cell = t;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
-                    break;
-                }
-                double lc[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
-                deposit_piece<Real>(Tc, la, lc, qw, dG);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) ca[i] = ca[i] + smin * (db[i] - ca[i]);
-                const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
-                if (tn < 0) {  // PEC wall: absorbed, charge stays at the wall point
-                    deposit_charge<Real>(Tc, lc, qw, Q);
-                    end_cell = -1;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
-                    break;
-                }
-                TetTopo Tn;
-                load_topo(topo, tn, Tn);
-                int ent = 0;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int vtx = Tn.node[a];
-                    double lv = 0.0;
-                    bool found = false;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (Tc.node[j] == vtx) {
-                            lv = lc[j];
-                            found = true;
-                        }
-                    la[a] = lv;
-                    if (!found) ent = a;
-                }
-                load_geo(geo, tn, G);
-                Tc = Tn;
-                t = tn;
-                entry = ent;
-                ++nc;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) rel[i] = (os[i] - G.o[i]) + db[i];
-            }
+            if (walk_fp64<Real>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, aggregate ? agg : nullptr,
+                                &end_cell, end_off))
+                key = c;
             cell[p] = end_cell;
             off[p] = (Real)end_off[0];
             off[n + p] = (Real)end_off[1];
@@ -353,13 +371,270 @@ __global__ void __launch_bounds__(256) k_push_deposit(
             unsigned heads;
             int end;
             warp_run_reduce<Real, 10>(key, agg, &heads, &end);
-            const bool head = (heads >> lane) & 1u;
-            if (head && key >= 0) {
+            if (((heads >> lane) & 1u) && key >= 0) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], agg[k]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], agg[6 + k]);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP32 mode
+__device__ __forceinline__ void load_hot(const TetHot* __restrict__ hot, int c, TetHot& H) {
+    const float4* p = reinterpret_cast<const float4*>(hot + c);
+    float4 r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = __ldg(p + k);
+    memcpy(&H, r, sizeof(TetHot));
+}
+
+// Affine field coefficients of every tet from the edge and face DOFs (FP32):
+//   E = E0 + W x off,  E0 = sum_{b} e_0b g_b,  W = sum_{a<b} e_ab g_a x g_b;
+//   B = sum_a lambda_a K_a with K_a from the W2 functions; B0 = K_0 and
+//   beta = (1/3) sum_{a>0} (K_a - K_0) . g_a  (the field is B0 + beta off).
+// Rewrites bytes 64..127 of each record (g row 3 and the coefficients).
+__global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
+                                                      const TetTopo* __restrict__ topo,
+                                                      const double* __restrict__ e,
+                                                      const double* __restrict__ b, int64_t nt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        TetHot H;
+        load_hot(hot, (int)t, H);
+        const int4* tp = reinterpret_cast<const int4*>(topo + t);
+        int4 f01 = __ldg(tp + 2), f23 = __ldg(tp + 3);
+        const int face[4] = {f01.z, f01.w, f23.x, f23.y};
+        float g[4][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[1][i] = H.g[i];
+            g[2][i] = H.g[3 + i];
+            g[3][i] = H.g[6 + i];
+            g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+        }
+        float ev[6], bv[4];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ev[k] = (float)__ldg(e + H.edge[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bv[k] = (float)__ldg(b + face[k]);
+        float x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
+        cross<float>(g[0], g[1], x01);
+        cross<float>(g[0], g[2], x02);
+        cross<float>(g[0], g[3], x03);
+        cross<float>(g[1], g[2], x12);
+        cross<float>(g[1], g[3], x13);
+        cross<float>(g[2], g[3], x23);
+        float E0[3], W[3], K[4][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            E0[i] = ev[0] * g[1][i] + ev[1] * g[2][i] + ev[2] * g[3][i];
+            W[i] = ev[0] * x01[i] + ev[1] * x02[i] + ev[2] * x03[i] + ev[3] * x12[i] + ev[4] * x13[i] +
+                   ev[5] * x23[i];
+            // faces: 0=(1,2,3), 1=(0,2,3), 2=(0,1,3), 3=(0,1,2)
+            K[0][i] = 2.f * (bv[1] * x23[i] + bv[2] * x13[i] + bv[3] * x12[i]);
+            K[1][i] = 2.f * (bv[0] * x23[i] - bv[2] * x03[i] - bv[3] * x02[i]);
+            K[2][i] = 2.f * (-bv[0] * x13[i] - bv[1] * x03[i] + bv[3] * x01[i]);
+            K[3][i] = 2.f * (bv[0] * x12[i] + bv[1] * x02[i] + bv[2] * x01[i]);
+        }
+        float beta = 0.f;
+#pragma unroll
+        for (int a = 1; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) beta += (K[a][i] - K[0][i]) * g[a][i];
+        beta *= (1.f / 3.f);
+        float4* w = reinterpret_cast<float4*>(hot + t) + 4;
+        w[0] = make_float4(H.g[6], H.g[7], H.g[8], E0[0]);
+        w[1] = make_float4(E0[1], E0[2], W[0], W[1]);
+        w[2] = make_float4(W[2], K[0][0], K[0][1], K[0][2]);
+        w[3] = make_float4(beta, 0.f, 0.f, 0.f);
+    }
+}
+
+// Fast FP32 path: gather through the affine coefficients, Boris, and the end point's
+// barycentric coordinates l^b = l^a + G dx.  If every l^b_k clears a margin larger
+// than the FP32 rounding bound, the FP64 exit test would find no exit either, so the
+// piece stays in the tet and is deposited here (warp-reduced).  Otherwise the
+// particle index is queued for the FP64 walk (velocity already updated).
+__global__ void __launch_bounds__(256) k_push_fast32(
+    const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
+    float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
+    float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float w = (float)qw;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t p = base + lane;
+        int c = p < n ? __ldg(cell + p) : -1;
+        if (c >= nt) {
+            atomicOr(status, ST_INVAL);
+            c = -1;
+        }
+        int key = -1;
+        bool slow = false;
+        float agg[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) agg[k] = 0.f;
+        TetHot H;
+        if (c >= 0) {
+            load_hot(hot, c, H);
+            float x[3] = {off[p], off[n + p], off[2 * n + p]};
+            float v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
+            float l[4];
+            l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
+            l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
+            l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
+            l[0] = 1.f - l[1] - l[2] - l[3];
+            float E[3], B[3];
+            E[0] = H.E0[0] + (H.W[1] * x[2] - H.W[2] * x[1]);
+            E[1] = H.E0[1] + (H.W[2] * x[0] - H.W[0] * x[2]);
+            E[2] = H.E0[2] + (H.W[0] * x[1] - H.W[1] * x[0]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
+            boris<float>(v, E, B, h);
+            vel[p] = v[0];
+            vel[n + p] = v[1];
+            vel[2 * n + p] = v[2];
+            float xb[3], dx[3], d[4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                xb[i] = step_pos(x[i], dt, v[i]);
+                dx[i] = xb[i] - x[i];
+            }
+            d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
+            d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
+            d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
+            d[0] = -(d[1] + d[2] + d[3]);
+            // rounding bound of l^b in FP32 (with the FP32 copy of the gradients)
+            float S = 1.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) S += fabsf(H.g[k]) * (fabsf(x[k % 3]) + fabsf(dx[k % 3]));
+            const float margin = S * (1.f / 65536.f);
+            float lbmin = l[0] + d[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
+            if (lbmin >= margin) {
+                agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
+                agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
+                agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
+                agg[3] = w * (l[1] * d[2] - l[2] * d[1]);
+                agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
+                agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
+                off[p] = xb[0];
+                off[n + p] = xb[1];
+                off[2 * n + p] = xb[2];
+                key = c;
+                if (!aggregate) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+                }
+            } else {
+                slow = true;
+            }
+        }
+        // queue the slow particles (one atomic per warp)
+        const unsigned sm = __ballot_sync(kFull, slow);
+        if (sm) {
+            int basei = 0;
+            const int leader = __ffs(sm) - 1;
+            if (lane == leader) basei = atomicAdd(slow_count, __popc(sm));
+            basei = __shfl_sync(kFull, basei, leader);
+            if (slow) slow_idx[basei + __popc(sm & ((1u << lane) - 1u))] = (int32_t)p;
+        }
+        if (aggregate) {
+            unsigned heads;
+            int end;
+            warp_run_reduce<float, 10>(key, agg, &heads, &end);
+            if (((heads >> lane) & 1u) && key >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+            }
+        }
+    }
+}
+
+// FP64 walk of the queued particles (near or across a face).  The end point is
+// recomputed from the stored start offset and the updated velocity with the same
+// FP32 operations as in k_push_fast32.
+__global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
+                                                const TetTopo* __restrict__ topo,
+                                                int32_t* __restrict__ cell, float* __restrict__ off,
+                                                const float* __restrict__ vel, int64_t n, float dt,
+                                                double qw, int max_cross, float* __restrict__ dG,
+                                                float* __restrict__ Q,
+                                                const int32_t* __restrict__ slow_idx,
+                                                const int32_t* __restrict__ slow_count,
+                                                int32_t* __restrict__ status) {
+    const int64_t m = *slow_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int64_t p = slow_idx[i];
+        if (p < 0 || p >= n) {
+            atomicOr(status, ST_INVAL);
+            continue;
+        }
+        const int c = cell[p];
+        double xa[3], xb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float x = off[k * n + p];
+            xa[k] = (double)x;
+            xb[k] = (double)step_pos(x, dt, vel[k * n + p]);
+        }
+        int end_cell;
+        double end_off[3];
+        walk_fp64<float>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
+        cell[p] = end_cell;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) off[k * n + p] = (float)end_off[k];
+    }
+}
+
+// W0 charge at the current positions, FP32 (barycentrics from the FP32 gradients)
+__global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restrict__ hot,
+                                                          const int32_t* __restrict__ cell,
+                                                          const float* __restrict__ off, int64_t n,
+                                                          int32_t nt, double qw, float* __restrict__ Q,
+                                                          int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float w = (float)qw;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t p = base + lane;
+        int c = p < n ? cell[p] : -1;
+        if (c >= nt) {
+            atomicOr(status, ST_INVAL);
+            c = -1;
+        }
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        TetHot H;
+        if (c >= 0) {
+            load_hot(hot, c, H);
+            const float x[3] = {off[p], off[n + p], off[2 * n + p]};
+            float l1 = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
+            float l2 = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
+            float l3 = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
+            v[0] = w * (1.f - l1 - l2 - l3);
+            v[1] = w * l1;
+            v[2] = w * l2;
+            v[3] = w * l3;
+        }
+        unsigned heads;
+        int end;
+        warp_run_reduce<float, 4>(c, v, &heads, &end);
+        if (((heads >> lane) & 1u) && c >= 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], v[k]);
         }
     }
 }
@@ -428,16 +703,36 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
     const double qw = p->q * p->w;
     const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
     const int grid = grid_for(p->n);
-    if (f32)
-        k_push_deposit<float><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell, (float*)p->off,
-                                                   (float*)p->vel, p->n, (int32_t)ctx->hc.nt, qmdt2,
-                                                   (float)dt, qw, max_cross, agg, (float*)dG, (float*)Q,
-                                                   ctx->d_status);
-    else
+    const int32_t nt = (int32_t)ctx->hc.nt;
+    if (f32) {
+        if (p->n > INT32_MAX) {
+            ctx->err = "fem_pic_push_deposit: more than 2^31-1 particles in one call";
+            return FP_EINVAL;
+        }
+        if (ctx->slow_cap < p->n) {
+            if (ctx->d_slow_idx) FP_CUDA_TRY(ctx, cudaFree(ctx->d_slow_idx));
+            ctx->d_slow_idx = nullptr;
+            ctx->slow_cap = 0;
+            FP_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->d_slow_idx, p->n * sizeof(int32_t)));
+            ctx->slow_cap = p->n;
+        }
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_slow_count, 0, sizeof(int32_t), s));
+        k_field_prep32<<<grid_for(ctx->hc.nt), 256, 0, s>>>(ctx->d_hot, ctx->d_topo, e, b, ctx->hc.nt);
+        k_push_fast32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
+                                           (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+                                           ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_walk32<<<sms * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                         (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
+                                         (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+    } else {
         k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
-                                                    (double*)p->off, (double*)p->vel, p->n,
-                                                    (int32_t)ctx->hc.nt, qmdt2, dt, qw, max_cross, agg,
-                                                    (double*)dG, (double*)Q, ctx->d_status);
+                                                    (double*)p->off, (double*)p->vel, p->n, nt, qmdt2, dt,
+                                                    qw, max_cross, agg, (double*)dG, (double*)Q,
+                                                    ctx->d_status);
+    }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }
@@ -450,9 +745,8 @@ fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, in
     const double qw = p->q * p->w;
     const int grid = grid_for(p->n);
     if (f32)
-        k_deposit_charge<float><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (const float*)p->off,
-                                                     p->n, (int32_t)ctx->hc.nt, qw, (float*)Q,
-                                                     ctx->d_status);
+        k_deposit_charge32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
+                                                (int32_t)ctx->hc.nt, qw, (float*)Q, ctx->d_status);
     else
         k_deposit_charge<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell,
                                                       (const double*)p->off, p->n, (int32_t)ctx->hc.nt,

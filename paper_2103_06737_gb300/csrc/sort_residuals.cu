@@ -165,9 +165,10 @@ __global__ void __launch_bounds__(256) k_res_continuity(const int32_t* __restric
                                                         const int8_t* __restrict__ sgn, int64_t nn,
                                                         const Real* __restrict__ dG,
                                                         const Real* __restrict__ Qn,
-                                                        const Real* __restrict__ Qo, double* out) {
+                                                        const Real* __restrict__ Qo,
+                                                        const uint8_t* __restrict__ wall, double* out) {
     __shared__ double sh[32];
-    double rmax = 0.0, smax = 0.0;
+    double rmax = 0.0, smax = 0.0, imax = 0.0, ismax = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
         double r = 0.0, sc = 0.0;
@@ -182,12 +183,20 @@ __global__ void __launch_bounds__(256) k_res_continuity(const int32_t* __restric
         sc += fabs(qn) + fabs(qo);
         rmax = fmax(rmax, fabs(r));
         smax = fmax(smax, sc);
+        if (!wall[i]) {
+            imax = fmax(imax, fabs(r));
+            ismax = fmax(ismax, sc);
+        }
     }
     rmax = block_max(rmax, sh);
     smax = block_max(smax, sh);
+    imax = block_max(imax, sh);
+    ismax = block_max(ismax, sh);
     if (threadIdx.x == 0) {
         atomic_max_nonneg(out + 0, rmax);
         atomic_max_nonneg(out + 1, smax);
+        atomic_max_nonneg(out + 4, imax);
+        atomic_max_nonneg(out + 5, ismax);
     }
 }
 
@@ -258,16 +267,16 @@ fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, 
 
 fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const void* Qo,
                            const double* b, double* out, cudaStream_t s) {
-    FP_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 4 * sizeof(double), s));
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 6 * sizeof(double), s));
     const int64_t nn = ctx->hc.nn, nt = ctx->hc.nt;
     if (ctx->precision == FP_FP32)
         k_res_continuity<float><<<grid_cap(nn, 256, 4), 256, 0, s>>>(
             ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn, (const float*)dG, (const float*)Qn,
-            (const float*)Qo, out);
+            (const float*)Qo, ctx->d_node_wall, out);
     else
         k_res_continuity<double><<<grid_cap(nn, 256, 4), 256, 0, s>>>(
             ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn, (const double*)dG, (const double*)Qn,
-            (const double*)Qo, out);
+            (const double*)Qo, ctx->d_node_wall, out);
     if (b) k_res_divb<<<grid_cap(nt, 256, 4), 256, 0, s>>>(ctx->d_topo, ctx->d_orient, nt, b, out);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;

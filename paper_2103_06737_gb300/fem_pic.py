@@ -286,7 +286,7 @@ def fem_pic_sort(h, src: Species, dst: Species, stream=None):
 
 
 def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
-    _need(out, torch.float64, 4, name="out")
+    _need(out, torch.float64, 6, name="out")
     _check(lib().fem_pic_residuals(h, _ptr(dG), _ptr(Q_new), _ptr(Q_old), _ptr(b), _ptr(out),
                                    _stream(stream)), h)
 

@@ -87,7 +87,7 @@ def test_project_uniform_and_divb():
     er, br = orc.project_uniform((1.0, -2.0, 0.5), (0.1, 0.2, -0.3))
     assert np.abs(e.cpu().numpy() - er).max() <= 1e-15 * np.abs(er).max()
     assert np.abs(b.cpu().numpy() - br).max() <= 1e-15 * np.abs(br).max()
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
     lib.residuals(None, None, None, b, out)
     r = out.cpu().numpy()
     assert r[2] <= 1e-15 * r[3]
@@ -107,7 +107,7 @@ def _push_fp64(npart, speed, max_cross=64, agg=True):
     lib.deposit_charge(d, Q0)
     lib.push_deposit(ed, bd, d, dt, dG, Q, max_cross=max_cross, flags=0 if agg else F.FP_NO_AGGREGATE)
     st = lib.status()
-    res = torch.zeros(4, dtype=torch.float64, device="cuda")
+    res = torch.zeros(6, dtype=torch.float64, device="cuda")
     lib.residuals(dG, Q, Q0, bd, res)
     ref = orc.step(sp.cell, sp.X, sp.V, e, b, q, mass, w, dt, max_cross=max_cross)
     Q0r, Q0a = orc.charge(sp.cell, sp.X, q, w)
@@ -150,7 +150,7 @@ def test_push_deposit_fp32_parity():
     lib.deposit_charge(d, Q0)
     lib.push_deposit(ed, bd, d, dt, dG, Q)
     assert lib.status() == F.FP_OK
-    res = torch.zeros(4, dtype=torch.float64, device="cuda")
+    res = torch.zeros(6, dtype=torch.float64, device="cuda")
     lib.residuals(dG, Q, Q0, bd, res)
     cell1, X1, V1, off1 = _to_host(d, lib)
     # velocities vs the FP64 oracle push from the same (FP32) start state
