@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--min-warmup-s", type=float, default=1.5,
+                    help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
 
 
@@ -219,7 +221,7 @@ def run_gpu(args):
     clk = clocks_start(local)
     t0 = time.time()
     w = 0
-    while w < args.warmup or time.time() - t0 < 1.5:
+    while w < args.warmup or time.time() - t0 < args.min_warmup_s:
         step()
         if w % 20 == 0:
             torch.cuda.synchronize()
