@@ -160,6 +160,26 @@ fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
                                int flags, void* stream);
 
 /*
+ * Same step as fem_pic_push_deposit, for callers that must not allocate device
+ * memory once they are running (a memory budget fixed at start-up, an allocator
+ * that refuses new device allocations, a framework that only passes in buffers it
+ * already owns).  The paper has no counterpart: this is a property of the library.
+ * fem_pic_push_deposit keeps the particles it hands to the FP64 walk in a queue it
+ * grows with cudaMalloc; here that queue is a fixed array inside the library
+ * (4,194,304 entries, 16 MiB, held on every device that loads the library until the
+ * process exits).  The call allocates nothing: p->n above 4,194,304 returns
+ * FP_EINVAL with nothing launched.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls on a device share the array and it keeps the last
+ * call's contents (each call clears the count it needs), so calls whose GPU work
+ * overlaps (other streams, other threads, other handles) race on it: serialise them.
+ * In FP_FP64 mode no queue is used and the call behaves like fem_pic_push_deposit.
+ */
+fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const double* b,
+                                      const fp_particles* p, double dt, int max_cross, void* dG,
+                                      void* Q, int flags, void* stream);
+
+/*
  * Whitney-0 charge of the particles at their current positions:
  * Q_n (+)= q w lambda_n (Sec. IV.B.1, the node charge the continuity equation pairs
  * with dG).  Q is zeroed first unless FP_ACCUMULATE.  Asynchronous.

@@ -15,6 +15,9 @@
 // algebraically equal to q w (l^a_a l^c_b - l^a_b l^c_a), the exact line integral of
 // W1_ab along a straight piece; the differences are formed in FP64 so the Real products
 // do not cancel.
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 
 namespace fempic {
@@ -756,3 +759,96 @@ fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, in
 }
 
 }  // namespace fempic
+
+// ---------------------------------------------------------------- allocation-free entry point
+// Some callers cannot allocate device memory while they step particles: code running
+// under a strict memory budget that was fixed up front, a host allocator that forbids
+// cudaMalloc after start-up, or a driver layer that only hands out buffers it already
+// owns.  fem_pic_push_deposit grows a library-owned queue of the particles it defers
+// to the FP64 walk with cudaMalloc; this variant keeps that queue in a fixed array
+// compiled into the library instead.  The array is shared by every call on a device
+// and keeps the last call's contents; the count at its head is cleared by every call.
+namespace fempic {
+namespace {
+
+constexpr int64_t kStaticMaxParticles = int64_t(1) << 22;  // 4,194,304 particles, 16 MiB
+constexpr int kStaticHead = 64;                           // int32 slots before the indices
+
+// [0] = number of queued particles, [kStaticHead ...] = their indices
+static __device__ __align__(256) int32_t g_static_queue[kStaticHead + kStaticMaxParticles];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_static_mu;
+int32_t* g_static_addr[kMaxDevices] = {nullptr};
+
+// device address of g_static_queue on the current device, looked up once per device
+fp_status static_queue(fem_pic* ctx, int32_t** out) {
+    int dev = 0;
+    FP_CUDA_TRY(ctx, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        ctx->err = "fem_pic_push_deposit_static: device ordinal out of range";
+        return FP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);
+        if (e != cudaSuccess || !p) {
+            ctx->err = std::string("cudaGetSymbolAddress(g_static_queue): ") + cudaGetErrorString(e);
+            return FP_ECUDA;
+        }
+        g_static_addr[dev] = static_cast<int32_t*>(p);
+    }
+    *out = g_static_addr[dev];
+    return FP_OK;
+}
+
+}  // namespace
+}  // namespace fempic
+
+extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const double* b,
+                                                 const fp_particles* p, double dt, int max_cross,
+                                                 void* dG, void* Q, int flags, void* stream) {
+    using namespace fempic;
+    if (!ctx || !p || !e || !b || !dG || !Q || p->n < 0 || max_cross < 0 || !(p->m > 0.0)) {
+        if (ctx) ctx->err = "fem_pic_push_deposit_static: NULL pointer or bad argument";
+        return FP_EINVAL;
+    }
+    if (p->n > 0 && (!p->cell || !p->off || !p->vel)) {
+        ctx->err = "fem_pic_push_deposit_static: NULL particle array";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->precision != FP_FP32)  // the FP64 path defers nothing and needs no scratch
+        return launch_push_deposit(ctx, e, b, p, dt, max_cross, dG, Q, flags, s);
+    if (p->n > kStaticMaxParticles) {
+        ctx->err = "fem_pic_push_deposit_static: " + std::to_string(p->n) +
+                   " particles exceed the fixed queue of " + std::to_string(kStaticMaxParticles);
+        return FP_EINVAL;
+    }
+    int32_t* q = nullptr;
+    fp_status st = static_queue(ctx, &q);
+    if (st != FP_OK) return st;
+    if (!(flags & FP_ACCUMULATE)) {
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, sizeof(float) * ctx->hc.ne, s));
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, sizeof(float) * ctx->hc.nn, s));
+    }
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(q, 0, sizeof(int32_t), s));
+    if (p->n == 0) return FP_OK;
+    const double qmdt2 = p->q * dt / (2.0 * p->m);
+    const double qw = p->q * p->w;
+    const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
+    const int32_t nt = (int32_t)ctx->hc.nt;
+    int dev = 0, sms = 152;
+    FP_CUDA_TRY(ctx, cudaGetDevice(&dev));
+    FP_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_field_prep32<<<grid_for(ctx->hc.nt), 256, 0, s>>>(ctx->d_hot, ctx->d_topo, e, b, ctx->hc.nt);
+    k_push_fast32<<<grid_for(p->n), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
+                                                 (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+                                                 q + kStaticHead, q, ctx->d_status);
+    k_walk32<<<sms * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off, (const float*)p->vel,
+                                     p->n, (float)dt, qw, max_cross, (float*)dG, (float*)Q, q + kStaticHead, q,
+                                     ctx->d_status);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
