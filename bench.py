@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-graphs", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -125,6 +126,13 @@ def algorithmic_bytes(n_particles, sizes, real_bytes=4):
     return state + tets + dofs + dep
 
 
+def fast_kernel_bytes(n_particles, sizes):
+    """Minimal DRAM bytes of one k_push_fast32 launch: cell + off + vel read (28 B) and
+    off + vel written (24 B) per particle, each tet's 128-byte record once, dG and Q
+    read-modify-write once (FP32)."""
+    return n_particles * 52 + sizes["n_tets"] * 128 + 8 * (sizes["n_edges"] + sizes["n_nodes"])
+
+
 def peak_hbm():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -150,7 +158,6 @@ def run_gpu(args):
     sizes = lib.sizes
     dev = torch.device("cuda", local)
     species = [lib.species(s.cell, s.X, s.V, s.q, s.m, s.w, device=dev) for s in wl.species]
-    spare = [s.empty_like() for s in species]
     n_part = sum(s.n for s in species)
     e, b = lib.fields_uniform((0.0, 0.0, 0.0), wl.B0, device=dev)
     if wl.E_amp > 0:
@@ -183,46 +190,62 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     # initial sort and charge
-    for i in range(len(species)):
-        lib.sort(species[i], spare[i])
-        species[i], spare[i] = spare[i], species[i]
-    for i, s in enumerate(species):
-        lib.deposit_charge(s, Qs[0], flags=F.FP_ACCUMULATE if i else 0)
+    bufs = [[s_, s_.empty_like()] for s_ in species]     # double buffers for the sort
+    cur = [0] * len(species)
+    for k in range(len(species)):
+        lib.sort(bufs[k][0], bufs[k][1])
+        cur[k] = 1
+    for k in range(len(species)):
+        lib.deposit_charge(bufs[k][cur[k]], Qs[0], flags=F.FP_ACCUMULATE if k else 0)
     st = lib.status()
     if st != F.FP_OK:
         raise RuntimeError(f"setup status {st}: {F.fem_pic_last_error(lib.h)}")
 
-    state = {"i": 0, "launches": 0}
-    ev_push = []
+    def plan(i):
+        """(sort now?, buffer index per species before the step, Q parity) of step i"""
+        sort_now = args.sort_every > 0 and i > 0 and i % args.sort_every == 0
+        return sort_now, tuple(cur), i % 2
 
-    def step(record_push=False):
-        i = state["i"]
-        if args.sort_every > 0 and i % args.sort_every == 0 and i > 0:
-            for k in range(len(species)):
-                lib.sort(species[k], spare[k])
-                species[k], spare[k] = spare[k], species[k]
-                state["launches"] += 5
-        Qn, Qo = Qs[(i + 1) % 2], Qs[i % 2]
-        if record_push:
-            a = torch.cuda.Event(enable_timing=True)
-            z = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-        for k, s in enumerate(species):
-            lib.push_deposit(e, b, s, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE if k else 0)
-            state["launches"] += 3       # field prep, fast push, FP64 walk of the queued particles
-        if record_push:
-            z.record(stream)
-            ev_push.append((a, z))
+    def enqueue(pl):
+        """One step on the current stream; returns the number of library kernels launched."""
+        sort_now, before, par = pl
+        n_k = 0
+        use = []
+        for k in range(len(species)):
+            b_ = before[k]
+            if sort_now:
+                lib.sort(bufs[k][b_], bufs[k][1 - b_])
+                b_ = 1 - b_
+                n_k += 5
+            use.append(bufs[k][b_])
+        Qn, Qo = Qs[1 - par], Qs[par]
+        for k, s_ in enumerate(use):
+            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE if k else 0)
+            n_k += 3              # field prep, fast push, FP64 walk of the queued particles
         lib.residuals(dG, Qn, Qo, b, res)
-        state["launches"] += 2
-        state["i"] = i + 1
+        n_k += 1
+        return n_k
 
-    # warm-up: at least W steps and at least ~1.5 s of work so the clock sampler sees load
+    def advance(pl):
+        if pl[0]:
+            for k in range(len(species)):
+                cur[k] = 1 - cur[k]
+
+    state = {"i": 0}
+
+    def eager_step():
+        pl = plan(state["i"])
+        n_k = enqueue(pl)
+        advance(pl)
+        state["i"] += 1
+        return n_k
+
+    # warm-up (eager): allocates the library's scratch before any capture
     clk = clocks_start(local)
     t0 = time.time()
     w = 0
-    while w < args.warmup or time.time() - t0 < args.min_warmup_s:
-        step()
+    while w < max(args.warmup, 2 * args.sort_every + 2) or time.time() - t0 < args.min_warmup_s:
+        eager_step()
         if w % 20 == 0:
             torch.cuda.synchronize()
         w += 1
@@ -231,27 +254,50 @@ def run_gpu(args):
     if st != F.FP_OK:
         raise RuntimeError(f"warm-up status {st}: {F.fem_pic_last_error(lib.h)}")
 
+    # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
+    graphs = {}
+    use_graphs = not args.no_graphs
+
+    def graph_step():
+        pl = plan(state["i"])
+        if pl not in graphs:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                n_k = enqueue(pl)
+            graphs[pl] = (g, n_k)
+        g, n_k = graphs[pl]
+        g.replay()
+        advance(pl)
+        state["i"] += 1
+        return n_k
+
+    step = graph_step if use_graphs else eager_step
+    if use_graphs:                       # capture every shape once, outside the timed region
+        for _ in range(2 * args.sort_every + 2):
+            step()
+        torch.cuda.synchronize()
+
     # timed: K steps, each bracketed by events; L2 flushed between steps (outside the events)
-    state["launches"] = 0
+    launches = 0
     evs = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    th0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(record_push=True)
+        launches += step()
         z.record(stream)
         evs.append((a, z))
+    th1 = time.perf_counter()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = clocks_stop(clk)
-    launches = state["launches"]
     step_ms = [a.elapsed_time(z) for a, z in evs]
-    push_ms = [a.elapsed_time(z) for a, z in ev_push]
     total_ms = float(sum(step_ms))
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -260,10 +306,33 @@ def run_gpu(args):
     st = lib.status()
     r = res.cpu().numpy()
 
+    # per-kernel durations: an eager pass of the same steps with the library's event profiler
+    F.fem_pic_profile_read(lib.h, reset=True)
+    F.fem_pic_profile_enable(lib.h, True)
+    push_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        pl = plan(state["i"])
+        a.record(stream)
+        enqueue((pl[0], pl[1], pl[2]))
+        z.record(stream)
+        advance(pl)
+        state["i"] += 1
+        push_ms.append((a, z))
+    torch.cuda.synchronize()
+    F.fem_pic_profile_enable(lib.h, False)
+    phases = F.fem_pic_profile_read(lib.h, reset=True)
+    push_ms = [a.elapsed_time(z) for a, z in push_ms]
+    push_call = (phases.get("prep", (0, 1))[0] + phases.get("push_fast", (0, 1))[0] +
+                 phases.get("walk", (0, 1))[0]) / max(1, phases.get("push_fast", (0, 1))[1])
+
     # e2e through the public API with host buffers: H2D of the step's inputs (particle
     # state + fields) from pinned memory, the step, D2H of the results (state + deposits)
     e2e = None
     if not args.no_e2e:
+        species = [bufs[k][cur[k]] for k in range(len(species))]
         hs = [(torch.empty_like(s.cell, device="cpu").pin_memory(), torch.empty_like(s.off, device="cpu").pin_memory(),
                torch.empty_like(s.vel, device="cpu").pin_memory()) for s in species]
         for (hc, ho, hv), s in zip(hs, species):
@@ -288,13 +357,14 @@ def run_gpu(args):
                 s.vel.copy_(hv, non_blocking=True)
             e.copy_(he, non_blocking=True)
             b.copy_(hb, non_blocking=True)
-            step()
+            eager_step()
             for (hc, ho, hv), s in zip(hs, species):
                 hc.copy_(s.cell, non_blocking=True)
                 ho.copy_(s.off, non_blocking=True)
                 hv.copy_(s.vel, non_blocking=True)
             hdG.copy_(dG, non_blocking=True)
             hQ.copy_(Qs[state["i"] % 2], non_blocking=True)
+            species = [bufs[k][cur[k]] for k in range(len(species))]
             z.record(stream)
             ee.append((a, z))
         torch.cuda.synchronize()
@@ -308,10 +378,14 @@ def run_gpu(args):
     out = None
     if rank == 0:
         value = world * n_part * args.steps / (total_ms * 1e-3)
-        avg_push = statistics.mean(push_ms)
+        avg_push = push_call
         abytes = algorithmic_bytes(n_part, sizes, 4)
         peak, peak_kind = peak_hbm()
         achieved = abytes / (avg_push * 1e-3) / 1e9
+        fast_ms, fast_n = phases.get("push_fast", (float("nan"), 1))
+        fast_avg = fast_ms / max(1, fast_n)
+        fbytes = fast_kernel_bytes(n_part, sizes)
+        fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -323,11 +397,20 @@ def run_gpu(args):
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "sort (periodic) + push/gather/walk/deposit + fp64 residuals"},
-            "roofline": {"kernel": "push_deposit (k_field_prep32 + k_push_fast32 + k_walk32)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": avg_push,
+            "roofline": {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
+                         "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg,
                          "traffic": None},
+            "roofline_push_call": {"kernels": "k_field_prep32 + k_push_fast32 + k_walk32 (sum of kernel times)",
+                                   "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                   "frac": achieved / peak, "algorithmic_bytes_per_launch": abytes,
+                                   "avg_call_ms": avg_push},
+            "timing": ("timed steps replay one CUDA graph per step shape" if use_graphs else "eager launches") +
+                      "; per-kernel times from an eager pass of the same steps with the library's CUDA-event profiler",
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+            "host_ms_per_step": (th1 - th0) * 1e3 / args.steps,
             "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
+            "eager_ms_per_step": statistics.mean(push_ms),
             "residuals": {"continuity_interior_max": float(r[4]), "continuity_interior_scale": float(r[5]),
                           "continuity_all_nodes_max": float(r[0]), "continuity_all_nodes_scale": float(r[1]),
                           "divB_max": float(r[2]), "divB_scale": float(r[3])},

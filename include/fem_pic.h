@@ -197,10 +197,10 @@ fp_status fem_pic_deposit_charge(fem_pic_t* ctx, const fp_particles* p, void* Q,
 fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* dst, void* stream);
 
 /*
- * Invariant residuals, FP64 (Sec. II.A continuity, Sec. IV.B.1, Sec. V item 5):
+ * Invariant residuals, sums in FP64 (Sec. II.A continuity, Sec. IV.B.1, Sec. V item 5):
  *   out[0] = max_n |(D0^T dG)_n - (Q_new - Q_old)_n| over all nodes,  out[1] = max_n of
- *            the sum of the absolute values of those terms (scale);
- *   out[2] = max_t |(D2 b)_t|,  out[3] = max_t sum_f |b_f| over the tet's faces;
+ *            the sum of the absolute values of those terms (scale, accumulated in FP32);
+ *   out[2] = max_t |(D2 b)_t|,  out[3] = max_f |b_f| (scale; a row of D2 has 4 terms);
  *   out[4], out[5] = as out[0], out[1] over interior nodes only (charge absorbed by a
  *            PEC wall in an earlier step leaves the particle set, so over several
  *            steps continuity is checked where the field solve uses it).
@@ -209,6 +209,18 @@ fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* ds
  */
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
                             const double* b, double* out, void* stream);
+
+/*
+ * Optional per-phase timing (not part of the method).  When enabled, the library
+ * records a pair of CUDA events on the launch stream around each of its kernels,
+ * by phase: 0 field-coefficient prep, 1 FP32 push, 2 FP64 walk of deferred particles,
+ * 3 FP64-mode push, 4 charge deposit, 5 sort, 6 residuals, 7 field solve.
+ * fem_pic_profile_read waits for the recorded events, adds their durations to
+ * per-phase totals and returns them: ms[16] (milliseconds), count[16] (event pairs);
+ * reset != 0 clears the totals.  Either output may be NULL.
+ */
+fp_status fem_pic_profile_enable(fem_pic_t* ctx, int on);
+fp_status fem_pic_profile_read(fem_pic_t* ctx, double ms[16], int64_t count[16], int reset);
 
 /*
  * Synchronise `stream`, return and clear the device status word:

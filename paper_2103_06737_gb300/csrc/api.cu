@@ -168,6 +168,7 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
         }
     }
     cudaError_t ce = cudaGetDevice(&ctx->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (ce == cudaSuccess) {
         fp_status s2 = FP_OK;
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_geo, hc.geo.data(), hc.nt);
@@ -180,6 +181,7 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_n2e_sgn, n2e_sgn.data(), n2e_sgn.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_orient, hc.orient.data(), hc.orient.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_hot, hot.data(), hot.size());
+        if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_tet_faces, reinterpret_cast<const int4*>(hc.tf.data()), hc.nt);
         if (s2 == FP_OK) {
             int32_t z4[4] = {0, 0, 0, 0};
             s2 = upload(ctx, &ctx->d_slow_count, z4, 4);
@@ -220,9 +222,14 @@ void fem_pic_destroy(fem_pic_t* ctx) {
                     ctx->d_faces,   ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn,
                     ctx->d_orient,  ctx->d_status,  ctx->d_sort_count, ctx->d_sort_block,
                     ctx->d_sort_rank, ctx->d_hot, ctx->d_slow_idx, ctx->d_slow_count,
-                    ctx->d_node_wall};
+                    ctx->d_node_wall, ctx->d_tet_faces};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& r : ctx->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     cudaSetDevice(prev);
     delete ctx;
 }
@@ -346,6 +353,35 @@ fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, c
                             const double* b, double* out, void* stream) {
     if (!ctx || !out) return FP_EINVAL;
     return launch_residuals(ctx, dG, Q_new, Q_old, b, out, (cudaStream_t)stream);
+}
+
+fp_status fem_pic_profile_enable(fem_pic_t* ctx, int on) {
+    if (!ctx) return FP_EINVAL;
+    ctx->prof_on = on != 0;
+    return FP_OK;
+}
+
+fp_status fem_pic_profile_read(fem_pic_t* ctx, double ms[16], int64_t count[16], int reset) {
+    if (!ctx) return FP_EINVAL;
+    for (auto& r : ctx->prof_pending) {
+        FP_CUDA_TRY(ctx, cudaEventSynchronize(r.b));
+        float t = 0.f;
+        FP_CUDA_TRY(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+        ctx->prof_ms[r.phase] += t;
+        ctx->prof_n[r.phase] += 1;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    for (int i = 0; i < PH_COUNT; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (count) count[i] = ctx->prof_n[i];
+        if (reset) {
+            ctx->prof_ms[i] = 0.0;
+            ctx->prof_n[i] = 0;
+        }
+    }
+    return FP_OK;
 }
 
 fp_status fem_pic_status(fem_pic_t* ctx, void* stream) {

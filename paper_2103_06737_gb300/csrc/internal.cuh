@@ -74,8 +74,25 @@ void incidence_csr(const HostComplex& hc, int which, std::vector<int32_t>* row_p
 
 }  // namespace fempic
 
+namespace fempic {
+// phases timed by the optional profiler (fem_pic_profile_*)
+enum Phase : int { PH_PREP = 0, PH_FAST = 1, PH_WALK = 2, PH_PUSH64 = 3, PH_CHARGE = 4, PH_SORT = 5,
+                   PH_RESID = 6, PH_SOLVE = 7, PH_COUNT = 16 };
+struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+}  // namespace fempic
+
 struct fem_pic {
     int device = 0;
+    int sm_count = 152;
+    // profiler: events recorded on the launch stream around each kernel when enabled
+    bool prof_on = false;
+    std::vector<fempic::ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[fempic::PH_COUNT] = {0};
+    int64_t prof_n[fempic::PH_COUNT] = {0};
     int precision = FP_FP64;
     fempic::HostComplex hc;
     // device tables
@@ -89,6 +106,7 @@ struct fem_pic {
     int8_t* d_n2e_sgn = nullptr;
     int8_t* d_orient = nullptr;       // [nt]
     fempic::TetHot* d_hot = nullptr;  // [nt]
+    int4* d_tet_faces = nullptr;      // [nt] face ids of each tet (face k opposite vertex k)
     int32_t* d_status = nullptr;
     // particles deferred to the FP64 walk (near or across a face)
     int32_t* d_slow_idx = nullptr;    // [slow_cap]
@@ -112,8 +130,86 @@ struct fem_pic {
         }                                                                                  \
     } while (0)
 
+namespace fempic {
+#ifdef __CUDACC__
+// Conversions between float and double with integer operations only.  On GB300 the
+// FP64 pipe (which also executes F2F conversions) issues 2 thread-operations per clock
+// per SM, so the particle and residual kernels convert through the bit patterns.
+// f2d is exact for normal floats, zeros, infinities and NaN; float subnormals become
+// signed zero.  d2f rounds to nearest, ties to even, like __double2float_rn, for
+// results in the normal float range; results below it become signed zero, above it
+// signed infinity; NaN stays NaN.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + (1023u - 127u));
+    const unsigned long long bits = e == 0u ? sgn : (sgn | (ex << 52) | man);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ float d2f(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ffull);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    const int ef = e - 1023 + 127;
+    const unsigned rem = (unsigned)(m & 0x1fffffffull);  // the 29 bits dropped
+    unsigned r = ((unsigned)(ef & 0xff) << 23) | (unsigned)(m >> 29);
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;  // carry may raise the exponent
+    r = ef <= 0 ? 0u : (ef >= 255 ? 0x7f800000u : r);
+    r = e == 0x7ff ? (0x7f800000u | (m ? 0x400000u : 0u)) : r;
+    return __uint_as_float(r | sign);
+}
+
+// x < 0 strictly (and not NaN-with-sign), from the bit pattern
+__device__ __forceinline__ bool neg_strict(double x) {
+    const long long b = __double_as_longlong(x);
+    return b < 0 && b != (long long)0x8000000000000000ull;
+}
+// x > 0 strictly, from the bit pattern (NaN with a clear sign bit counts as > 0)
+__device__ __forceinline__ bool pos_strict(double x) {
+    return __double_as_longlong(x) > 0;
+}
+#endif
+}  // namespace fempic
+
 // launchers implemented in the .cu files
 namespace fempic {
+// Records an event pair around the launches in its scope when profiling is on.
+struct PhaseTimer {
+    fem_pic* c;
+    int ph;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    static cudaEvent_t get(fem_pic* c) {
+        if (!c->prof_pool.empty()) {
+            cudaEvent_t e = c->prof_pool.back();
+            c->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    PhaseTimer(fem_pic* c_, int ph_, cudaStream_t s_) : c(c_), ph(ph_), s(s_) {
+        if (c->prof_on) {
+            a = get(c);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEvent_t b = get(c);
+        if (!b) {
+            c->prof_pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        c->prof_pending.push_back({ph, a, b});
+    }
+};
 fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, const fp_particles* p,
                               double dt, int max_cross, void* dG, void* Q, int flags,
                               cudaStream_t s);

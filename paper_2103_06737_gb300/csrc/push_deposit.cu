@@ -160,15 +160,32 @@ __device__ __forceinline__ double step_pos(double x, double dt, double v) {
 }
 
 template <typename Real>
+__device__ __forceinline__ Real to_real(double x);
+template <>
+__device__ __forceinline__ float to_real<float>(double x) {
+    return d2f(x);
+}
+template <>
+__device__ __forceinline__ double to_real<double>(double x) {
+    return x;
+}
+__device__ __forceinline__ double to_f64(float x) {
+    return f2d(x);
+}
+__device__ __forceinline__ double to_f64(double x) {
+    return x;
+}
+
+template <typename Real>
 __device__ __forceinline__ void piece_values(const double la[4], const double lx[4], double qw,
                                              Real val[6]) {
     Real A[4], D[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        A[k] = (Real)la[k];
-        D[k] = (Real)(lx[k] - la[k]);
+        A[k] = to_real<Real>(la[k]);
+        D[k] = to_real<Real>(lx[k] - la[k]);
     }
-    const Real w = (Real)qw;
+    const Real w = to_real<Real>(qw);
     val[0] = w * (A[0] * D[1] - A[1] * D[0]);
     val[1] = w * (A[0] * D[2] - A[2] * D[0]);
     val[2] = w * (A[0] * D[3] - A[3] * D[0]);
@@ -190,7 +207,7 @@ template <typename Real>
 __device__ __forceinline__ void deposit_charge(const TetTopo& T, const double l[4], double qw,
                                                Real* __restrict__ Q) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], (Real)qw * (Real)l[k]);
+    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], to_real<Real>(qw) * to_real<Real>(l[k]));
 }
 
 // Sum `v[0..NV)` over each run of equal `key` in lane order; the first lane of a run
@@ -224,6 +241,12 @@ __device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* h
 // piece deposits its 6 edge values, the end point its 4 node charges.  When `agg` is
 // non-null and the path stays inside c, the 10 values are returned in agg instead of
 // being added (return true) so the caller can reduce them across the warp.
+//
+// FP64 is spent only on the exit test: the end point's barycentrics in each tet, the
+// crossing fraction and the carried crossing barycentrics.  The smallest fraction is
+// found by cross-multiplication (one division per crossing).  The deposit products are
+// in Real; the current point, needed only when the walk stops early, is tracked in
+// Real as well.
 template <typename Real>
 __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, int c,
                           const double xa[3], const double xb[3], double qw, int max_cross,
@@ -233,11 +256,13 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
     TetTopo Tc;
     load_geo(geo, c, G);
     load_topo(topo, c, Tc);
-    double la[4], ca[3], rel[3], os[3];
+    double la[4], rel[3], os[3];
     bary(G, xa, la);
+    Real ca[3], cb[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        ca[i] = xa[i];
+        ca[i] = to_real<Real>(xa[i]);
+        cb[i] = to_real<Real>(xb[i]);
         rel[i] = xb[i];
         os[i] = G.o[i];
     }
@@ -245,18 +270,39 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
     for (;;) {
         double lb[4];
         bary(G, rel, lb);
+        // exit candidates: faces other than the entry face with l^b_k < 0
+        unsigned cand = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cand |= (k != entry && neg_strict(lb[k])) ? (1u << k) : 0u;
         int kx = -1;
         double smin = 0.0;
+        if (cand != 0u && (cand & (cand - 1u)) == 0u) {
+            // one candidate (the common crossing): l^a_k > 0 > l^b_k gives s in [0,1)
+            kx = __ffs(cand) - 1;
+            const double ak = kx == 0 ? la[0] : (kx == 1 ? la[1] : (kx == 2 ? la[2] : la[3]));
+            const double bk = kx == 0 ? lb[0] : (kx == 1 ? lb[1] : (kx == 2 ? lb[2] : lb[3]));
+            smin = pos_strict(ak) ? ak / (ak - bk) : 0.0;
+        } else if (cand != 0u) {
+            // several: the smallest fraction by cross-multiplication, one division
+            double bn = 0.0, bd = 1.0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (k == entry || !(lb[k] < 0.0)) continue;
-            double den = la[k] - lb[k];
-            double s = den > 0.0 ? la[k] / den : 0.0;
-            s = fmin(fmax(s, 0.0), 1.0);
-            if (kx < 0 || s < smin) {
-                kx = k;
-                smin = s;
+            for (int k = 0; k < 4; ++k) {
+                if (!((cand >> k) & 1u)) continue;
+                double num = la[k], den = la[k] - lb[k];
+                if (!pos_strict(num) || !pos_strict(den)) {  // fraction clamps to 0
+                    num = 0.0;
+                    den = 1.0;
+                } else if (num > den) {                      // fraction clamps to 1
+                    num = 1.0;
+                    den = 1.0;
+                }
+                if (kx < 0 || num * bd < bn * den) {
+                    kx = k;
+                    bn = num;
+                    bd = den;
+                }
             }
+            smin = bn / bd;
         }
         if (kx < 0) {
             *end_cell = t;
@@ -265,7 +311,7 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
             if (nc == 0 && agg) {
                 piece_values<Real>(la, lb, qw, agg);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) agg[6 + k] = (Real)qw * (Real)lb[k];
+                for (int k = 0; k < 4; ++k) agg[6 + k] = to_real<Real>(qw) * to_real<Real>(lb[k]);
                 return true;
             }
             deposit_piece<Real>(Tc, la, lb, qw, dG);
@@ -277,21 +323,22 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
             atomicOr(status, ST_WALK);
             *end_cell = t;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+            for (int i = 0; i < 3; ++i) end_off[i] = to_f64(ca[i]) + (os[i] - G.o[i]);
             return false;
         }
         double lc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
         deposit_piece<Real>(Tc, la, lc, qw, dG);
+        const Real sr = to_real<Real>(smin);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) ca[i] = ca[i] + smin * (xb[i] - ca[i]);
+        for (int i = 0; i < 3; ++i) ca[i] = ca[i] + sr * (cb[i] - ca[i]);
         const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
         if (tn < 0) {  // PEC wall: absorbed, its charge stays at the wall point
             deposit_charge<Real>(Tc, lc, qw, Q);
             *end_cell = -1;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) end_off[i] = ca[i] + (os[i] - G.o[i]);
+            for (int i = 0; i < 3; ++i) end_off[i] = to_f64(ca[i]) + (os[i] - G.o[i]);
             return false;
         }
         TetTopo Tn;
@@ -399,29 +446,33 @@ __device__ __forceinline__ void load_hot(const TetHot* __restrict__ hot, int c, 
 //   beta = (1/3) sum_{a>0} (K_a - K_0) . g_a  (the field is B0 + beta off).
 // Rewrites bytes 64..127 of each record (g row 3 and the coefficients).
 __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
-                                                      const TetTopo* __restrict__ topo,
+                                                      const int4* __restrict__ tet_faces,
                                                       const double* __restrict__ e,
                                                       const double* __restrict__ b, int64_t nt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 2
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-        TetHot H;
-        load_hot(hot, (int)t, H);
-        const int4* tp = reinterpret_cast<const int4*>(topo + t);
-        int4 f01 = __ldg(tp + 2), f23 = __ldg(tp + 3);
-        const int face[4] = {f01.z, f01.w, f23.x, f23.y};
+        // bytes 16..79 of the record: edge ids and the FP32 gradients
+        const float4* hp = reinterpret_cast<const float4*>(hot + t);
+        const float4 r1 = __ldg(hp + 1), r2 = __ldg(hp + 2), r3 = __ldg(hp + 3), r4 = __ldg(hp + 4);
+        const int4 f = __ldg(tet_faces + t);
+        const int edge[6] = {__float_as_int(r1.x), __float_as_int(r1.y), __float_as_int(r1.z),
+                             __float_as_int(r1.w), __float_as_int(r2.x), __float_as_int(r2.y)};
+        const int face[4] = {f.x, f.y, f.z, f.w};
+        float ev[6], bv[4];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ev[k] = d2f(__ldg(e + edge[k]));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bv[k] = d2f(__ldg(b + face[k]));
+        const float hg[9] = {r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z};
         float g[4][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            g[1][i] = H.g[i];
-            g[2][i] = H.g[3 + i];
-            g[3][i] = H.g[6 + i];
+            g[1][i] = hg[i];
+            g[2][i] = hg[3 + i];
+            g[3][i] = hg[6 + i];
             g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
         }
-        float ev[6], bv[4];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) ev[k] = (float)__ldg(e + H.edge[k]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) bv[k] = (float)__ldg(b + face[k]);
         float x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
         cross<float>(g[0], g[1], x01);
         cross<float>(g[0], g[2], x02);
@@ -448,7 +499,7 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
             for (int i = 0; i < 3; ++i) beta += (K[a][i] - K[0][i]) * g[a][i];
         beta *= (1.f / 3.f);
         float4* w = reinterpret_cast<float4*>(hot + t) + 4;
-        w[0] = make_float4(H.g[6], H.g[7], H.g[8], E0[0]);
+        w[0] = make_float4(hg[6], hg[7], hg[8], E0[0]);
         w[1] = make_float4(E0[1], E0[2], W[0], W[1]);
         w[2] = make_float4(W[2], K[0][0], K[0][1], K[0][2]);
         w[3] = make_float4(beta, 0.f, 0.f, 0.f);
@@ -460,7 +511,13 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 // than the FP32 rounding bound, the FP64 exit test would find no exit either, so the
 // piece stays in the tet and is deposited here (warp-reduced).  Otherwise the
 // particle index is queued for the FP64 walk (velocity already updated).
-__global__ void __launch_bounds__(256) k_push_fast32(
+#ifndef FP_FAST_MIN_BLOCKS
+#define FP_FAST_MIN_BLOCKS 4
+#endif
+#ifndef FP_FAST_PREFETCH
+#define FP_FAST_PREFETCH 0
+#endif
+__global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
     float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
     float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
@@ -468,10 +525,40 @@ __global__ void __launch_bounds__(256) k_push_fast32(
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float w = (float)qw;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride) {
+    int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+#if FP_FAST_PREFETCH
+    // the next particle's cell and state are loaded one iteration ahead
+    int c_nx = -1;
+    float x_nx[3] = {0.f, 0.f, 0.f}, v_nx[3] = {0.f, 0.f, 0.f};
+    if (base + lane < n) {
+        const int64_t q = base + lane;
+        c_nx = __ldg(cell + q);
+        x_nx[0] = off[q], x_nx[1] = off[n + q], x_nx[2] = off[2 * n + q];
+        v_nx[0] = vel[q], v_nx[1] = vel[n + q], v_nx[2] = vel[2 * n + q];
+    }
+#endif
+    for (; base < n; base += stride) {
         const int64_t p = base + lane;
+#if FP_FAST_PREFETCH
+        int c = p < n ? c_nx : -1;
+        float x[3] = {x_nx[0], x_nx[1], x_nx[2]};
+        float v[3] = {v_nx[0], v_nx[1], v_nx[2]};
+        {
+            const int64_t q = p + stride;
+            if (q < n) {
+                c_nx = __ldg(cell + q);
+                x_nx[0] = off[q], x_nx[1] = off[n + q], x_nx[2] = off[2 * n + q];
+                v_nx[0] = vel[q], v_nx[1] = vel[n + q], v_nx[2] = vel[2 * n + q];
+            }
+        }
+#else
         int c = p < n ? __ldg(cell + p) : -1;
+        float x[3], v[3];
+        if (c >= 0 && c < nt) {
+            x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
+            v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
+        }
+#endif
         if (c >= nt) {
             atomicOr(status, ST_INVAL);
             c = -1;
@@ -484,8 +571,6 @@ __global__ void __launch_bounds__(256) k_push_fast32(
         TetHot H;
         if (c >= 0) {
             load_hot(hot, c, H);
-            float x[3] = {off[p], off[n + p], off[2 * n + p]};
-            float v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
             float l[4];
             l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
             l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
@@ -590,15 +675,15 @@ __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float x = off[k * n + p];
-            xa[k] = (double)x;
-            xb[k] = (double)step_pos(x, dt, vel[k * n + p]);
+            xa[k] = f2d(x);
+            xb[k] = f2d(step_pos(x, dt, vel[k * n + p]));
         }
         int end_cell;
         double end_off[3];
         walk_fp64<float>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
         cell[p] = end_cell;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) off[k * n + p] = (float)end_off[k];
+        for (int k = 0; k < 3; ++k) off[k * n + p] = d2f(end_off[k]);
     }
 }
 
@@ -680,10 +765,7 @@ __global__ void __launch_bounds__(256) k_deposit_charge(const TetGeo* __restrict
     }
 }
 
-int grid_for(int64_t n) {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+int grid_for(int64_t n, int sms) {
     int64_t blocks = (n + 255) / 256;
     int64_t cap = (int64_t)sms * 8;  // grid-stride beyond 8 resident 256-thread blocks per SM
     if (blocks > cap) blocks = cap;
@@ -705,7 +787,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
     const double qmdt2 = p->q * dt / (2.0 * p->m);
     const double qw = p->q * p->w;
     const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
-    const int grid = grid_for(p->n);
+    const int grid = grid_for(p->n, ctx->sm_count);
     const int32_t nt = (int32_t)ctx->hc.nt;
     if (f32) {
         if (p->n > INT32_MAX) {
@@ -720,17 +802,24 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
             ctx->slow_cap = p->n;
         }
         FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_slow_count, 0, sizeof(int32_t), s));
-        k_field_prep32<<<grid_for(ctx->hc.nt), 256, 0, s>>>(ctx->d_hot, ctx->d_topo, e, b, ctx->hc.nt);
-        k_push_fast32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
-                                           (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
-                                           ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        k_walk32<<<sms * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
-                                         (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
-                                         (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+        {
+            PhaseTimer pt(ctx, PH_PREP, s);
+            k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e, b, ctx->hc.nt);
+        }
+        {
+            PhaseTimer pt(ctx, PH_FAST, s);
+            k_push_fast32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
+                                               (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+                                               ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+        }
+        {
+            PhaseTimer pt(ctx, PH_WALK, s);
+            k_walk32<<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                             (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
+                                             (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+        }
     } else {
+        PhaseTimer pt(ctx, PH_PUSH64, s);
         k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
                                                     (double*)p->off, (double*)p->vel, p->n, nt, qmdt2, dt,
                                                     qw, max_cross, agg, (double*)dG, (double*)Q,
@@ -746,7 +835,8 @@ fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, in
     if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (f32 ? 4 : 8) * ctx->hc.nn, s));
     if (p->n == 0) return FP_OK;
     const double qw = p->q * p->w;
-    const int grid = grid_for(p->n);
+    const int grid = grid_for(p->n, ctx->sm_count);
+    PhaseTimer pt(ctx, PH_CHARGE, s);
     if (f32)
         k_deposit_charge32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
                                                 (int32_t)ctx->hc.nt, qw, (float*)Q, ctx->d_status);
@@ -842,8 +932,8 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
     int dev = 0, sms = 152;
     FP_CUDA_TRY(ctx, cudaGetDevice(&dev));
     FP_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_field_prep32<<<grid_for(ctx->hc.nt), 256, 0, s>>>(ctx->d_hot, ctx->d_topo, e, b, ctx->hc.nt);
-    k_push_fast32<<<grid_for(p->n), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
+    k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e, b, ctx->hc.nt);
+    k_push_fast32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
                                                  (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
                                                  q + kStaticHead, q, ctx->d_status);
     k_walk32<<<sms * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off, (const float*)p->vel,

@@ -7,15 +7,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScanTile = 1024;
 
-int sm_count() {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
-int grid_cap(int64_t n, int block, int per_sm) {
-    int64_t g = (n + block - 1) / block, cap = (int64_t)sm_count() * per_sm;
+int grid_cap(int64_t n, int block, int per_sm, int sms) {
+    int64_t g = (n + block - 1) / block, cap = (int64_t)sms * per_sm;
     if (g > cap) g = cap;
     return g < 1 ? 1 : (int)g;
 }
@@ -158,74 +151,126 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
     return r;
 }
 
-// r_n = (D0^T dG)_n - (Q_new - Q_old)_n  (discrete continuity, FP64)
-template <typename Real>
-__global__ void __launch_bounds__(256) k_res_continuity(const int32_t* __restrict__ ptr,
-                                                        const int32_t* __restrict__ col,
-                                                        const int8_t* __restrict__ sgn, int64_t nn,
-                                                        const Real* __restrict__ dG,
-                                                        const Real* __restrict__ Qn,
-                                                        const Real* __restrict__ Qo,
-                                                        const uint8_t* __restrict__ wall, double* out) {
-    __shared__ double sh[32];
-    double rmax = 0.0, smax = 0.0, imax = 0.0, ismax = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
-        double r = 0.0, sc = 0.0;
-        if (dG)
-            for (int j = ptr[i]; j < ptr[i + 1]; ++j) {
-                double t = (double)sgn[j] * (double)dG[col[j]];
-                r += t;
-                sc += fabs(t);
-            }
-        double qn = Qn ? (double)Qn[i] : 0.0, qo = Qo ? (double)Qo[i] : 0.0;
-        r -= (qn - qo);
-        sc += fabs(qn) + fabs(qo);
-        rmax = fmax(rmax, fabs(r));
-        smax = fmax(smax, sc);
-        if (!wall[i]) {
-            imax = fmax(imax, fabs(r));
-            ismax = fmax(ismax, sc);
-        }
-    }
-    rmax = block_max(rmax, sh);
-    smax = block_max(smax, sh);
-    imax = block_max(imax, sh);
-    ismax = block_max(ismax, sh);
-    if (threadIdx.x == 0) {
-        atomic_max_nonneg(out + 0, rmax);
-        atomic_max_nonneg(out + 1, smax);
-        atomic_max_nonneg(out + 4, imax);
-        atomic_max_nonneg(out + 5, ismax);
-    }
+__device__ __forceinline__ double as_f64(float x) { return f2d(x); }
+__device__ __forceinline__ double as_f64(double x) { return x; }
+__device__ __forceinline__ float as_f32(float x) { return x; }
+__device__ __forceinline__ float as_f32(double x) { return d2f(x); }
+
+// |x| of a double as its bit pattern: for non-negative doubles the pattern orders like the value
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// r_t = (D2 b)_t  (magnetic Gauss law, FP64)
-__global__ void __launch_bounds__(256) k_res_divb(const TetTopo* __restrict__ topo,
-                                                  const int8_t* __restrict__ orient, int64_t nt,
-                                                  const double* __restrict__ b, double* out) {
-    __shared__ double sh[32];
-    double rmax = 0.0, smax = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-        const TetTopo& T = topo[t];
-        const double s = (double)orient[t];
-        double b0 = b[T.face[0]], b1 = b[T.face[1]], b2 = b[T.face[2]], b3 = b[T.face[3]];
-        double r = s * (((b0 - b1) + b2) - b3);
-        rmax = fmax(rmax, fabs(r));
-        smax = fmax(smax, fabs(b0) + fabs(b1) + fabs(b2) + fabs(b3));
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(kFull, v, o);
+        v = u > v ? u : v;
     }
-    rmax = block_max(rmax, sh);
-    smax = block_max(smax, sh);
-    if (threadIdx.x == 0) {
-        atomic_max_nonneg(out + 2, rmax);
-        atomic_max_nonneg(out + 3, smax);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long u = __shfl_xor_sync(kFull, r, o);
+            r = u > r ? u : r;
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+// One launch for both invariants.  The residual sums are FP64; the maxima are taken
+// on bit patterns and the scales in FP32, so the FP64 pipe only does the sums.
+//   blocks [0, nb_cont): continuity r_n = (D0^T dG)_n - (Q_new - Q_old)_n, a thread per node;
+//   blocks [nb_cont, ...): magnetic Gauss law r_t = (D2 b)_t, a thread per tet.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_residuals(const int32_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ col,
+                                                   const int8_t* __restrict__ sgn, int64_t nn,
+                                                   const Real* __restrict__ dG,
+                                                   const Real* __restrict__ Qn,
+                                                   const Real* __restrict__ Qo,
+                                                   const uint8_t* __restrict__ wall,
+                                                   const int4* __restrict__ tet_faces, int64_t nt,
+                                                   const double* __restrict__ b, int nb_cont,
+                                                   double* out) {
+    __shared__ unsigned long long sh[32];
+    if ((int)blockIdx.x < nb_cont) {
+        const int64_t stride = (int64_t)nb_cont * blockDim.x;
+        unsigned long long rmax = 0, imax = 0;
+        float smax = 0.f, ismax = 0.f;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+            double r = 0.0;
+            float sc = 0.f;
+            if (dG) {
+                const int j0 = __ldg(ptr + i), j1 = __ldg(ptr + i + 1);
+                for (int j = j0; j < j1; ++j) {
+                    const Real x = __ldg(dG + __ldg(col + j));
+                    const double xd = as_f64(x);
+                    const long long flip = __ldg(sgn + j) > 0 ? 0ll : (long long)0x8000000000000000ull;
+                    r += __longlong_as_double(__double_as_longlong(xd) ^ flip);
+                    sc += fabsf(as_f32(x));
+                }
+            }
+            if (Qn) {
+                r -= as_f64(Qn[i]);
+                sc += fabsf(as_f32(Qn[i]));
+            }
+            if (Qo) {
+                r += as_f64(Qo[i]);
+                sc += fabsf(as_f32(Qo[i]));
+            }
+            const unsigned long long ar = abs_bits(r);
+            rmax = ar > rmax ? ar : rmax;
+            smax = fmaxf(smax, sc);
+            if (!wall[i]) {
+                imax = ar > imax ? ar : imax;
+                ismax = fmaxf(ismax, sc);
+            }
+        }
+        rmax = block_max_u64(rmax, sh);
+        imax = block_max_u64(imax, sh);
+        unsigned long long s1 = block_max_u64(__float_as_uint(smax), sh);
+        unsigned long long s2 = block_max_u64(__float_as_uint(ismax), sh);
+        if (threadIdx.x == 0) {
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 0), rmax);
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 4), imax);
+            atomic_max_nonneg(out + 1, f2d(__uint_as_float((unsigned)s1)));
+            atomic_max_nonneg(out + 5, f2d(__uint_as_float((unsigned)s2)));
+        }
+    } else {
+        unsigned long long rmax = 0, smax = 0;
+        if (b) {
+            const int64_t nbk = (int64_t)gridDim.x - nb_cont;
+            const int64_t stride = nbk * blockDim.x;
+            for (int64_t t = (int64_t)(blockIdx.x - nb_cont) * blockDim.x + threadIdx.x; t < nt; t += stride) {
+                const int4 f = __ldg(tet_faces + t);
+                const double b0 = __ldg(b + f.x), b1 = __ldg(b + f.y), b2 = __ldg(b + f.z), b3 = __ldg(b + f.w);
+                // D2 row: s_t (+b0 - b1 + b2 - b3); the sign s_t does not change |r|
+                const unsigned long long ar = abs_bits(((b0 - b1) + b2) - b3);
+                rmax = ar > rmax ? ar : rmax;
+                unsigned long long m01 = abs_bits(b0) > abs_bits(b1) ? abs_bits(b0) : abs_bits(b1);
+                unsigned long long m23 = abs_bits(b2) > abs_bits(b3) ? abs_bits(b2) : abs_bits(b3);
+                unsigned long long m = m01 > m23 ? m01 : m23;
+                smax = m > smax ? m : smax;
+            }
+        }
+        rmax = block_max_u64(rmax, sh);
+        smax = block_max_u64(smax, sh);
+        if (threadIdx.x == 0) {
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 2), rmax);
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 3), smax);
+        }
     }
 }
 
 template <typename Real>
 void scatter(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s) {
-    k_sort_scatter<Real><<<grid_cap(src->n, 256, 8), 256, 0, s>>>(
+    k_sort_scatter<Real><<<grid_cap(src->n, 256, 8, ctx->sm_count), 256, 0, s>>>(
         src->cell, (const Real*)src->off, (const Real*)src->vel, src->n, (int32_t)ctx->hc.nt,
         ctx->d_sort_count, ctx->d_sort_rank, dst->cell, (Real*)dst->off, (Real*)dst->vel);
 }
@@ -251,8 +296,9 @@ fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, 
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->d_sort_rank, n * sizeof(int32_t)));
         ctx->sort_cap = n;
     }
+    PhaseTimer pt(ctx, PH_SORT, s);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_sort_count, 0, (m + 1) * sizeof(int32_t), s));
-    k_sort_count<<<grid_cap(n, 256, 8), 256, 0, s>>>(src->cell, n, (int32_t)ctx->hc.nt,
+    k_sort_count<<<grid_cap(n, 256, 8, ctx->sm_count), 256, 0, s>>>(src->cell, n, (int32_t)ctx->hc.nt,
                                                      ctx->d_sort_count, ctx->d_sort_rank);
     k_scan_tiles<<<(unsigned)tiles, kScanTile, 0, s>>>(ctx->d_sort_count, m, ctx->d_sort_block);
     k_scan_sums<<<1, kScanTile, 0, s>>>(ctx->d_sort_block, tiles);
@@ -267,17 +313,22 @@ fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, 
 
 fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const void* Qo,
                            const double* b, double* out, cudaStream_t s) {
+    PhaseTimer pt(ctx, PH_RESID, s);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 6 * sizeof(double), s));
     const int64_t nn = ctx->hc.nn, nt = ctx->hc.nt;
+    const int nb_cont = grid_cap(nn, 256, 4, ctx->sm_count);
+    const int nb_div = grid_cap(nt, 256, 4, ctx->sm_count);
+    const int grid = nb_cont + nb_div;
     if (ctx->precision == FP_FP32)
-        k_res_continuity<float><<<grid_cap(nn, 256, 4), 256, 0, s>>>(
-            ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn, (const float*)dG, (const float*)Qn,
-            (const float*)Qo, ctx->d_node_wall, out);
+        k_residuals<float><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn,
+                                                (const float*)dG, (const float*)Qn, (const float*)Qo,
+                                                ctx->d_node_wall, ctx->d_tet_faces, nt, b,
+                                                nb_cont, out);
     else
-        k_res_continuity<double><<<grid_cap(nn, 256, 4), 256, 0, s>>>(
-            ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn, (const double*)dG, (const double*)Qn,
-            (const double*)Qo, ctx->d_node_wall, out);
-    if (b) k_res_divb<<<grid_cap(nt, 256, 4), 256, 0, s>>>(ctx->d_topo, ctx->d_orient, nt, b, out);
+        k_residuals<double><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn,
+                                                 (const double*)dG, (const double*)Qn, (const double*)Qo,
+                                                 ctx->d_node_wall, ctx->d_tet_faces, nt, b,
+                                                 nb_cont, out);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }

@@ -80,6 +80,8 @@ def lib():
             "fem_pic_sort": (I32, [P, ctypes.POINTER(FPParticles), ctypes.POINTER(FPParticles), P]),
             "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
             "fem_pic_status": (I32, [P, P]),
+            "fem_pic_profile_enable": (I32, [P, I32]),
+            "fem_pic_profile_read": (I32, [P, P, P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -293,6 +295,20 @@ def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
 
 def fem_pic_status(h, stream=None) -> int:
     return int(lib().fem_pic_status(h, _stream(stream)))
+
+
+PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_solve")
+
+
+def fem_pic_profile_enable(h, on: bool = True):
+    _check(lib().fem_pic_profile_enable(h, 1 if on else 0), h)
+
+
+def fem_pic_profile_read(h, reset: bool = True) -> dict:
+    ms = np.zeros(16, dtype=np.float64)
+    n = np.zeros(16, dtype=np.int64)
+    _check(lib().fem_pic_profile_read(h, _ptr(ms), _ptr(n), 1 if reset else 0), h)
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES) if n[i] > 0}
 
 
 # ---------------------------------------------------------------- convenience layer
