@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 #define FP_FAST_MIN_BLOCKS 4
 #endif
 #ifndef FP_FAST_PREFETCH
-#define FP_FAST_PREFETCH 0
+#define FP_FAST_PREFETCH 2
 #endif
 __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
@@ -526,7 +526,9 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float w = (float)qw;
     int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-#if FP_FAST_PREFETCH
+#if FP_FAST_PREFETCH == 2
+    int c_nx = base + lane < n ? __ldg(cell + base + lane) : -1;
+#elif FP_FAST_PREFETCH
     // the next particle's cell and state are loaded one iteration ahead
     int c_nx = -1;
     float x_nx[3] = {0.f, 0.f, 0.f}, v_nx[3] = {0.f, 0.f, 0.f};
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
 #endif
     for (; base < n; base += stride) {
         const int64_t p = base + lane;
-#if FP_FAST_PREFETCH
+#if FP_FAST_PREFETCH == 1
         int c = p < n ? c_nx : -1;
         float x[3] = {x_nx[0], x_nx[1], x_nx[2]};
         float v[3] = {v_nx[0], v_nx[1], v_nx[2]};
@@ -550,6 +552,18 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
                 x_nx[0] = off[q], x_nx[1] = off[n + q], x_nx[2] = off[2 * n + q];
                 v_nx[0] = vel[q], v_nx[1] = vel[n + q], v_nx[2] = vel[2 * n + q];
             }
+        }
+#elif FP_FAST_PREFETCH == 2
+        // only the next particle's cell is loaded one iteration ahead
+        int c = p < n ? c_nx : -1;
+        {
+            const int64_t q = p + stride;
+            c_nx = q < n ? __ldg(cell + q) : -1;
+        }
+        float x[3], v[3];
+        if (c >= 0 && c < nt) {
+            x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
+            v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
 #else
         int c = p < n ? __ldg(cell + p) : -1;
