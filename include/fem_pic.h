@@ -210,6 +210,79 @@ fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* ds
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
                             const double* b, double* out, void* stream);
 
+/* ------------------------------------------------------------------ implicit field step */
+
+enum { FP_SYS_NEWMARK = 0, FP_SYS_GAUSS = 1 };
+enum { FP_PC_JACOBI = 0, FP_PC_LEARNED = 1 };
+
+typedef struct {
+    int32_t iters;     /* CG iterations taken */
+    int32_t precond;   /* preconditioner used (FP_PC_*) */
+    int32_t fell_back; /* 1 if a learned solve fell back to plain Jacobi-CG */
+    int32_t pad;
+    double rel_res;    /* final ||r|| / ||reference|| (see each call) */
+    double abs_res;    /* final ||r|| */
+    double ms;         /* device time of the solve when measured, else 0 */
+} fp_solve_info;
+
+/*
+ * Assemble the FP64 field operators of Sec. II.C for time step dt, permittivity eps,
+ * permeability mu, and upload them as CSR matrices:
+ *   M = [*eps] (edge mass, <W1_i, eps W1_j>), S = [*S] = [curl]^T [*mu^-1] [curl]
+ *   (Eq. wave_cont), A = M + dt^2/4 S (Newmark beta = 1/4), L = D0^T M D0 (the discrete
+ *   Laplacian of Eq. discreteGauss).
+ * PEC walls: edges and nodes on boundary faces are fixed at zero (their rows keep a unit
+ * diagonal, their columns are removed).  Replaces any earlier setup.  Synchronous.
+ */
+fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu);
+
+/* nnz[0] = entries of the edge operators (M, S, A), nnz[1] = entries of L. */
+fp_status fem_pic_field_nnz(const fem_pic_t* ctx, int64_t nnz[2]);
+
+/*
+ * Copy operator `which` (0 M, 1 S, 2 A, 3 L) to host CSR buffers: row_ptr [rows+1],
+ * col [nnz], val [nnz] (any may be NULL).  Rows = N_e for 0..2, N_n for 3.
+ */
+fp_status fem_pic_field_matrix(const fem_pic_t* ctx, int which, int32_t* row_ptr, int32_t* col,
+                               double* val);
+
+/*
+ * Solve A x = rhs (FP_SYS_NEWMARK, edges) or L x = rhs (FP_SYS_GAUSS, nodes) with
+ * Jacobi-preconditioned CG in FP64, starting from the x passed in (device, in/out),
+ * until ||rhs - A x|| <= tol ||rhs|| or max_iter iterations.  rhs must be zero on PEC
+ * rows.  info (host, may be NULL) is filled after a stream synchronisation; with info
+ * a solve that stops at max_iter returns FP_ENOCONV, otherwise the status word records it.
+ */
+fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, double* x, double tol,
+                              int max_iter, int precond, fp_solve_info* info, void* stream);
+
+/*
+ * One implicit field step (Sec. IV.B with Newmark-beta, beta = 1/4, gamma = 1/2):
+ *   1. (M + dt^2/4 S) E^N = M(2E^n - E^{n-1}) - dt^2 S(E^n/2 + E^{n-1}/4)
+ *                            - (dG^{n+1/2} - dG^{n-1/2}),
+ *      CG from the guess 2E^n - E^{n-1}, to ||r|| <= tol ||rhs||;
+ *   2. Gauss-law projection (Eq. discreteGauss, modified projector Eq. efld_mod_proj):
+ *      L d = D0^T M E^N + Q^{n+1} on interior nodes, CG from 0 to ||r|| <= tol ||Q||
+ *      (the residual of this solve is the Gauss-law residual D0^T M E^{n+1} + Q^{n+1});
+ *      E^{n+1} = E^N - D0 d;
+ *   3. Faraday: b <- b - dt D1 (E^{n+1} + E^n)/2 (skipped if b is NULL).
+ * E_prev = E^{n-1}, E_cur = E^n (device double [N_e]); E_next receives E^{n+1} (distinct
+ * buffer); dG_half = dG^{n+1/2} (the deposit of the push that used E^n), dG_prev =
+ * dG^{n-1/2} (NULL = 0), Q_new = Q^{n+1} (particle precision).  info[2] (host, may be
+ * NULL): the Newmark and Gauss solves; with info, FP_ENOCONV if either missed tol.
+ */
+fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
+                             double* b, const void* dG_half, const void* dG_prev, const void* Q_new,
+                             double tol, int max_iter, int precond, fp_solve_info info[2],
+                             void* stream);
+
+/*
+ * Initial field: E (device double [N_e]) with D0^T M E + Q = 0 at interior nodes and no
+ * solenoidal part (the Gauss-law projection of E = 0), CG to ||r|| <= tol ||Q||.
+ */
+fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
+                                fp_solve_info* info, void* stream);
+
 /*
  * Optional per-phase timing (not part of the method).  When enabled, the library
  * records a pair of CUDA events on the launch stream around each of its kernels,

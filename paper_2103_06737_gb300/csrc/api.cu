@@ -218,6 +218,7 @@ void fem_pic_destroy(fem_pic_t* ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    field_free(ctx);
     void* ptrs[] = {ctx->d_geo,     ctx->d_topo,    ctx->d_xyz,     ctx->d_edges,
                     ctx->d_faces,   ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn,
                     ctx->d_orient,  ctx->d_status,  ctx->d_sort_count, ctx->d_sort_block,
@@ -399,6 +400,10 @@ fp_status fem_pic_status(fem_pic_t* ctx, void* stream) {
     if (h & ST_WALK) {
         ctx->err = "a particle reached the crossing bound of the tet walk";
         return FP_EWALK;
+    }
+    if (h & ST_NOCONV) {
+        ctx->err = "an iterative field solve reached its iteration cap";
+        return FP_ENOCONV;
     }
     return FP_OK;
 }

@@ -1,0 +1,527 @@
+// Implicit field step on the GPU (FP64): Newmark wave-equation update, Gauss-law
+// projection, Faraday update (Sec. II.C, IV.A-B), with a Jacobi-preconditioned CG that
+// runs as one cooperative kernel (convergence decided on the device, no host round trip).
+#include <cooperative_groups.h>
+
+#include <cstring>
+
+#include "field.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fempic {
+
+struct FieldDev {
+    double dt = 0, eps = 0, mu = 0;
+    int64_t ne = 0, nn = 0, nf = 0;
+    HostFields host;
+    int32_t *e_rp = nullptr, *e_col = nullptr, *n_rp = nullptr, *n_col = nullptr;
+    double *Mv = nullptr, *Sv = nullptr, *Av = nullptr, *Adinv = nullptr, *Lv = nullptr, *Ldinv = nullptr;
+    uint8_t *edge_fixed = nullptr, *node_fixed = nullptr;
+    int32_t* face_edges = nullptr;  // [3 nf]: (i,j), (j,k), (i,k) of face (i<j<k)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr, *tmp = nullptr,
+           *delta = nullptr, *qd = nullptr;
+    double* red = nullptr;          // reduction partials
+    double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
+    int grid = 0;                   // cooperative grid size
+};
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double as_f64(float x) { return f2d(x); }
+__device__ __forceinline__ double as_f64(double x) { return x; }
+
+__device__ __forceinline__ double csr_row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, const double* __restrict__ x,
+                                              int64_t i) {
+    double s = 0.0;
+    const int j1 = __ldg(rp + i + 1);
+    for (int j = __ldg(rp + i); j < j1; ++j) s += __ldg(val + j) * x[__ldg(col + j)];
+    return s;
+}
+
+// sum of NV values over the block, result valid in every thread
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kBlock / 32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) t += sh[k][w];
+        v[k] = t;
+    }
+}
+
+// deterministic grid-wide sum: partials of every block, summed in block order by each block
+template <int NV>
+__device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_group& g,
+                                         double (*sh)[kBlock / 32]) {
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[NV * blockIdx.x + k] = v[k];
+    g.sync();
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) t[k] += __ldcg(part + NV * b + k);
+    block_sum<NV>(t, sh);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = t[k];
+}
+
+struct PcgArgs {
+    const int32_t* rp;
+    const int32_t* col;
+    const double* val;
+    const double* dinv;
+    int64_t n;
+    const double* b;
+    double* x;
+    double *r, *z, *p, *q;
+    double* red;
+    double tol;
+    const double* scale_vec;  // non-null: stop at ||r|| <= tol ||scale_vec||, else at ||r|| <= tol ||b||
+    int max_iter;
+    double* out;     // [iterations, ||r||^2, ||b||^2]
+    int32_t* status;
+};
+
+// Jacobi-preconditioned conjugate gradients in one cooperative launch.  Every block takes
+// the same decisions from the same grid-wide sums, so all blocks run the same number of
+// grid barriers; the loop is bounded by max_iter.
+__global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
+    cg::grid_group g = cg::this_grid();
+    __shared__ double sh[4][kBlock / 32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double* part0 = a.red;
+    double* part1 = a.red + 4 * gridDim.x;
+    double* part2 = a.red + 5 * gridDim.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, b.b, s.s
+    for (int64_t i = t0; i < a.n; i += stride) {
+        const double bi = a.b[i];
+        if (a.scale_vec) v[3] += a.scale_vec[i] * a.scale_vec[i];
+        const double ri = bi - csr_row_dot(a.rp, a.col, a.val, a.x, i);
+        const double zi = a.dinv[i] * ri;
+        a.r[i] = ri;
+        a.z[i] = zi;
+        a.p[i] = zi;
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+        v[2] += bi * bi;
+    }
+    grid_sum<4>(v, part0, g, sh);
+    double rz = v[0], rr = v[1];
+    const double bb = a.scale_vec ? v[3] : v[2];
+    const double thr = a.tol * a.tol * bb;
+    int it = 0;
+    while (rr > thr && it < a.max_iter) {
+        g.sync();  // p complete
+        double w[1] = {0.0};
+        for (int64_t i = t0; i < a.n; i += stride) {
+            const double qi = csr_row_dot(a.rp, a.col, a.val, a.p, i);
+            a.q[i] = qi;
+            w[0] += a.p[i] * qi;
+        }
+        grid_sum<1>(w, part1, g, sh);
+        if (!(w[0] > 0.0)) break;  // breakdown (same decision in every block)
+        const double alpha = rz / w[0];
+        double u[2] = {0.0, 0.0};
+        for (int64_t i = t0; i < a.n; i += stride) {
+            a.x[i] += alpha * a.p[i];
+            const double ri = a.r[i] - alpha * a.q[i];
+            const double zi = a.dinv[i] * ri;
+            a.r[i] = ri;
+            a.z[i] = zi;
+            u[0] += ri * zi;
+            u[1] += ri * ri;
+        }
+        grid_sum<2>(u, part2, g, sh);
+        const double beta = u[0] / rz;
+        rz = u[0];
+        rr = u[1];
+        for (int64_t i = t0; i < a.n; i += stride) a.p[i] = a.z[i] + beta * a.p[i];
+        ++it;
+    }
+    if (t0 == 0) {
+        a.out[0] = (double)it;
+        a.out[1] = rr;
+        a.out[2] = bb;      // squared norm the residual is measured against
+        if (rr > thr) atomicOr(a.status, ST_NOCONV);
+    }
+}
+
+// Newmark right-hand side and the extrapolated initial guess 2E^n - E^{n-1}
+template <typename Real>
+__global__ void k_newmark_rhs(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const double* __restrict__ Mv, const double* __restrict__ Sv,
+                              const uint8_t* __restrict__ fixed, const double* __restrict__ En,
+                              const double* __restrict__ Em, const Real* __restrict__ dGh,
+                              const Real* __restrict__ dGp, double dt2, int64_t n, double* __restrict__ rhs,
+                              double* __restrict__ x0) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (fixed[i]) {
+            rhs[i] = 0.0;
+            x0[i] = 0.0;
+            continue;
+        }
+        double s = 0.0;
+        const int j1 = rp[i + 1];
+        for (int j = rp[i]; j < j1; ++j) {
+            const int c = col[j];
+            const double en = En[c], em = Em[c];
+            s += Mv[j] * (2.0 * en - em) - dt2 * Sv[j] * (0.5 * en + 0.25 * em);
+        }
+        const double gh = dGh ? as_f64(dGh[i]) : 0.0, gp = dGp ? as_f64(dGp[i]) : 0.0;
+        rhs[i] = s - (gh - gp);
+        x0[i] = 2.0 * En[i] - Em[i];
+    }
+}
+
+__global__ void k_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, int64_t n,
+                       double* __restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        y[i] = csr_row_dot(rp, col, val, x, i);
+}
+
+// g_n = (D0^T [*eps] E)_n + Q_n on free nodes (ME = [*eps] E), 0 on PEC nodes
+template <typename Real>
+__global__ void k_gauss_rhs(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                            const int8_t* __restrict__ sgn, const uint8_t* __restrict__ fixed,
+                            const double* __restrict__ ME, const Real* __restrict__ Q, int64_t nn,
+                            double* __restrict__ g, double* __restrict__ qd) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+        if (fixed[i]) {
+            g[i] = 0.0;
+            qd[i] = 0.0;
+            continue;
+        }
+        double s = Q ? as_f64(Q[i]) : 0.0;
+        qd[i] = s;
+        for (int j = ptr[i]; j < ptr[i + 1]; ++j) s += sgn[j] > 0 ? ME[col[j]] : -ME[col[j]];
+        g[i] = s;
+    }
+}
+
+// E_e <- E_e - (d_j - d_i) on free edges: the Gauss-law projection E - D0 d
+__global__ void k_project(const int32_t* __restrict__ edges, const uint8_t* __restrict__ fixed,
+                          const double* __restrict__ d, const double* __restrict__ EN, int64_t ne,
+                          double* __restrict__ E) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride)
+        E[e] = fixed[e] ? 0.0 : EN[e] - (d[edges[2 * e + 1]] - d[edges[2 * e]]);
+}
+
+// b <- b - dt D1 (E1 + E0)/2, face (i<j<k): +(i,j) +(j,k) -(i,k)
+__global__ void k_faraday(const int32_t* __restrict__ fe, const double* __restrict__ E1,
+                          const double* __restrict__ E0, double half_dt, int64_t nf, double* __restrict__ b) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += stride) {
+        const int ij = fe[3 * f], jk = fe[3 * f + 1], ik = fe[3 * f + 2];
+        const double c = (E1[ij] + E0[ij]) + (E1[jk] + E0[jk]) - (E1[ik] + E0[ik]);
+        b[f] -= half_dt * c;
+    }
+}
+
+int grid_of(const fem_pic* ctx, int64_t n) {
+    int64_t g = (n + kBlock - 1) / kBlock, cap = (int64_t)ctx->sm_count * 8;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+template <typename T>
+fp_status up(fem_pic* ctx, T** d, const std::vector<T>& h) {
+    FP_CUDA_TRY(ctx, cudaMalloc((void**)d, h.size() * sizeof(T) + 16));
+    if (!h.empty()) FP_CUDA_TRY(ctx, cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FP_OK;
+}
+
+fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double tol, const double* scale_vec,
+                  int max_iter, int slot, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    PcgArgs a;
+    if (system == FP_SYS_NEWMARK) {
+        a.rp = F->e_rp, a.col = F->e_col, a.val = F->Av, a.dinv = F->Adinv, a.n = F->ne;
+    } else {
+        a.rp = F->n_rp, a.col = F->n_col, a.val = F->Lv, a.dinv = F->Ldinv, a.n = F->nn;
+    }
+    a.b = rhs, a.x = x, a.r = F->r, a.z = F->z, a.p = F->p, a.q = F->q, a.red = F->red;
+    a.tol = tol, a.scale_vec = scale_vec, a.max_iter = max_iter, a.out = F->out + 4 * slot, a.status = ctx->d_status;
+    void* args[] = {&a};
+    PhaseTimer pt(ctx, PH_SOLVE, s);
+    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(F->grid), dim3(kBlock), args, 0, s));
+    return FP_OK;
+}
+
+fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s, float ms) {
+    if (!info) return FP_OK;
+    double o[4];
+    FP_CUDA_TRY(ctx, cudaMemcpyAsync(o, ctx->field->out + 4 * slot, sizeof o, cudaMemcpyDeviceToHost, s));
+    FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    info->iters = (int32_t)o[0];
+    info->rel_res = o[2] > 0 ? sqrt(o[1] / o[2]) : sqrt(o[1]);
+    info->abs_res = sqrt(o[1]);
+    info->ms = ms;
+    info->precond = FP_PC_JACOBI;
+    info->fell_back = 0;
+    return FP_OK;
+}
+
+fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
+                          double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
+                          int max_iter, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    const bool f32 = ctx->precision == FP_FP32;
+    const int ge = grid_of(ctx, F->ne), gn = grid_of(ctx, F->nn);
+    {
+        PhaseTimer pt(ctx, PH_SOLVE, s);
+        if (f32)
+            k_newmark_rhs<float><<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, F->Sv, F->edge_fixed, E_cur, E_prev,
+                                                       (const float*)dG_half, (const float*)dG_prev, F->dt * F->dt,
+                                                       F->ne, F->rhs, E_next);
+        else
+            k_newmark_rhs<double><<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, F->Sv, F->edge_fixed, E_cur,
+                                                        E_prev, (const double*)dG_half, (const double*)dG_prev,
+                                                        F->dt * F->dt, F->ne, F->rhs, E_next);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    // Newmark solve for E^N from the guess 2E^n - E^{n-1} (written into E_next above)
+    fp_status st = run_pcg(ctx, FP_SYS_NEWMARK, F->rhs, E_next, tol, nullptr, max_iter, 0, s);
+    if (st != FP_OK) return st;
+    // Gauss-law projection: L d = D0^T M E^N + Q on interior nodes, to ||r|| <= tol ||Q||
+    {
+        PhaseTimer pt(ctx, PH_SOLVE, s);
+        k_spmv<<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, E_next, F->ne, F->tmp);
+        if (f32)
+            k_gauss_rhs<float><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
+                                                     F->tmp, (const float*)Q_new, F->nn, F->rhs, F->qd);
+        else
+            k_gauss_rhs<double><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn,
+                                                      F->node_fixed, F->tmp, (const double*)Q_new, F->nn, F->rhs,
+                                                      F->qd);
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(F->delta, 0, F->nn * sizeof(double), s));
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    st = run_pcg(ctx, FP_SYS_GAUSS, F->rhs, F->delta, tol, F->qd, max_iter, 1, s);
+    if (st != FP_OK) return st;
+    {
+        PhaseTimer pt(ctx, PH_SOLVE, s);
+        FP_CUDA_TRY(ctx, cudaMemcpyAsync(F->tmp, E_next, F->ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        k_project<<<ge, kBlock, 0, s>>>(ctx->d_edges, F->edge_fixed, F->delta, F->tmp, F->ne, E_next);
+        if (b) k_faraday<<<grid_of(ctx, F->nf), kBlock, 0, s>>>(F->face_edges, E_next, E_cur, 0.5 * F->dt, F->nf, b);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return FP_OK;
+}
+
+}  // namespace
+
+void field_free(fem_pic* ctx) {
+    FieldDev* F = ctx->field;
+    if (!F) return;
+    void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
+                    F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
+                    F->delta, F->qd, F->red, F->out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete F;
+    ctx->field = nullptr;
+}
+
+}  // namespace fempic
+
+using namespace fempic;
+
+extern "C" {
+
+fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) {
+    if (!ctx || !(dt > 0.0) || !(eps > 0.0) || !(mu > 0.0)) {
+        if (ctx) ctx->err = "fem_pic_field_setup: dt, eps and mu must be positive";
+        return FP_EINVAL;
+    }
+    field_free(ctx);
+    FieldDev* F = new FieldDev();
+    ctx->field = F;
+    const HostComplex& hc = ctx->hc;
+    F->dt = dt, F->eps = eps, F->mu = mu, F->ne = hc.ne, F->nn = hc.nn, F->nf = hc.nf;
+    assemble_fields(hc, eps, mu, &F->host);
+    const HostFields& H = F->host;
+    std::vector<double> A(H.M.size()), Ad(hc.ne), Ld(hc.nn);
+    for (size_t k = 0; k < A.size(); ++k) A[k] = H.M[k] + 0.25 * dt * dt * H.S[k];
+    for (int64_t i = 0; i < hc.ne; ++i)
+        for (int32_t j = H.e_rp[i]; j < H.e_rp[i + 1]; ++j)
+            if (H.e_col[j] == i) Ad[i] = 1.0 / A[j];
+    for (int64_t i = 0; i < hc.nn; ++i)
+        for (int32_t j = H.n_rp[i]; j < H.n_rp[i + 1]; ++j)
+            if (H.n_col[j] == i) Ld[i] = 1.0 / H.L[j];
+    // face -> edges (i,j), (j,k), (i,k)
+    std::vector<int32_t> fe(3 * hc.nf);
+    {
+        std::vector<int32_t> rp, col;
+        std::vector<int8_t> val;
+        incidence_csr(hc, 1, &rp, &col, &val);  // columns sorted: (i,j) < (i,k) < (j,k)
+        for (int64_t f = 0; f < hc.nf; ++f) {
+            fe[3 * f] = col[3 * f];
+            fe[3 * f + 1] = col[3 * f + 2];
+            fe[3 * f + 2] = col[3 * f + 1];
+        }
+    }
+    fp_status st = FP_OK;
+    if (st == FP_OK) st = up(ctx, &F->e_rp, H.e_rp);
+    if (st == FP_OK) st = up(ctx, &F->e_col, H.e_col);
+    if (st == FP_OK) st = up(ctx, &F->n_rp, H.n_rp);
+    if (st == FP_OK) st = up(ctx, &F->n_col, H.n_col);
+    if (st == FP_OK) st = up(ctx, &F->Mv, H.M);
+    if (st == FP_OK) st = up(ctx, &F->Sv, H.S);
+    if (st == FP_OK) st = up(ctx, &F->Av, A);
+    if (st == FP_OK) st = up(ctx, &F->Adinv, Ad);
+    if (st == FP_OK) st = up(ctx, &F->Lv, H.L);
+    if (st == FP_OK) st = up(ctx, &F->Ldinv, Ld);
+    if (st == FP_OK) st = up(ctx, &F->edge_fixed, H.edge_fixed);
+    if (st == FP_OK) st = up(ctx, &F->node_fixed, H.node_fixed);
+    if (st == FP_OK) st = up(ctx, &F->face_edges, fe);
+    const int64_t nmax = hc.ne > hc.nn ? hc.ne : hc.nn;
+    double** vecs[] = {&F->r, &F->z, &F->p, &F->q, &F->rhs, &F->tmp, &F->delta, &F->qd};
+    for (double** v : vecs)
+        if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)v, nmax * sizeof(double)));
+    // cooperative grid: all blocks co-resident
+    int per_sm = 0;
+    if (st == FP_OK) FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
+    if (st == FP_OK) {
+        if (per_sm < 1) {
+            ctx->err = "fem_pic_field_setup: the solver kernel cannot be co-resident";
+            return FP_ECUDA;
+        }
+        int grid = ctx->sm_count * (per_sm < 2 ? per_sm : 2);
+        const int64_t need = (nmax + kBlock - 1) / kBlock;
+        if (grid > need) grid = (int)need;
+        F->grid = grid < 1 ? 1 : grid;
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 6 * (size_t)F->grid * sizeof(double)));
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
+        FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
+    }
+    return st;
+}
+
+fp_status fem_pic_field_nnz(const fem_pic_t* ctx, int64_t nnz[2]) {
+    if (!ctx || !ctx->field || !nnz) return FP_EINVAL;
+    nnz[0] = (int64_t)ctx->field->host.e_col.size();
+    nnz[1] = (int64_t)ctx->field->host.n_col.size();
+    return FP_OK;
+}
+
+fp_status fem_pic_field_matrix(const fem_pic_t* ctx, int which, int32_t* row_ptr, int32_t* col, double* val) {
+    if (!ctx || !ctx->field || which < 0 || which > 3) return FP_EINVAL;
+    const FieldDev* F = ctx->field;
+    const HostFields& H = F->host;
+    const bool node = which == 3;
+    const std::vector<int32_t>& rp = node ? H.n_rp : H.e_rp;
+    const std::vector<int32_t>& c = node ? H.n_col : H.e_col;
+    if (row_ptr) std::memcpy(row_ptr, rp.data(), rp.size() * 4);
+    if (col) std::memcpy(col, c.data(), c.size() * 4);
+    if (val) {
+        for (size_t k = 0; k < c.size(); ++k) {
+            double v = which == 0 ? H.M[k] : which == 1 ? H.S[k] : which == 2 ? H.M[k] + 0.25 * F->dt * F->dt * H.S[k]
+                                                                             : H.L[k];
+            val[k] = v;
+        }
+    }
+    return FP_OK;
+}
+
+fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, double* x, double tol,
+                              int max_iter, int precond, fp_solve_info* info, void* stream) {
+    if (!ctx || !ctx->field || !rhs || !x || (system != FP_SYS_NEWMARK && system != FP_SYS_GAUSS) ||
+        !(tol > 0.0) || max_iter < 0 || precond != FP_PC_JACOBI) {
+        if (ctx) ctx->err = "fem_pic_field_solve: bad argument (or fem_pic_field_setup not called)";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (info) {
+        FP_CUDA_TRY(ctx, cudaEventCreate(&a));
+        FP_CUDA_TRY(ctx, cudaEventCreate(&b));
+        FP_CUDA_TRY(ctx, cudaEventRecord(a, s));
+    }
+    fp_status st = run_pcg(ctx, system, rhs, x, tol, nullptr, max_iter, 0, s);
+    if (info && st == FP_OK) {
+        float ms = 0.f;
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        st = fill_info(ctx, 0, info, s, ms);
+        if (st == FP_OK && info->rel_res > tol) st = FP_ENOCONV;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return st;
+}
+
+fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
+                             double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
+                             int max_iter, int precond, fp_solve_info info[2], void* stream) {
+    if (!ctx || !ctx->field || !E_prev || !E_cur || !E_next || !Q_new || !(tol > 0.0) || max_iter < 0 ||
+        precond != FP_PC_JACOBI || E_next == E_cur || E_next == E_prev) {
+        if (ctx) ctx->err = "fem_pic_field_step: bad argument (or fem_pic_field_setup not called)";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = field_step_impl(ctx, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol, max_iter, s);
+    if (st != FP_OK || !info) return st;
+    st = fill_info(ctx, 0, &info[0], s, 0.f);
+    if (st == FP_OK) st = fill_info(ctx, 1, &info[1], s, 0.f);
+    if (st == FP_OK && (info[0].rel_res > tol || info[1].rel_res > tol)) st = FP_ENOCONV;
+    return st;
+}
+
+fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
+                                fp_solve_info* info, void* stream) {
+    if (!ctx || !ctx->field || !Q || !E || !(tol > 0.0) || max_iter < 0) {
+        if (ctx) ctx->err = "fem_pic_field_initial: bad argument (or fem_pic_field_setup not called)";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    FieldDev* F = ctx->field;
+    const bool f32 = ctx->precision == FP_FP32;
+    const int gn = grid_of(ctx, F->nn), ge = grid_of(ctx, F->ne);
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(F->tmp, 0, F->ne * sizeof(double), s));
+    if (f32)
+        k_gauss_rhs<float><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed, F->tmp,
+                                                 (const float*)Q, F->nn, F->rhs, F->qd);
+    else
+        k_gauss_rhs<double><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
+                                                  F->tmp, (const double*)Q, F->nn, F->rhs, F->qd);
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(F->delta, 0, F->nn * sizeof(double), s));
+    fp_status st = run_pcg(ctx, FP_SYS_GAUSS, F->rhs, F->delta, tol, F->qd, max_iter, 1, s);
+    if (st != FP_OK) return st;
+    k_project<<<ge, kBlock, 0, s>>>(ctx->d_edges, F->edge_fixed, F->delta, F->tmp, F->ne, E);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    if (info) {
+        st = fill_info(ctx, 1, info, s, 0.f);
+        if (st == FP_OK && info->rel_res > tol) st = FP_ENOCONV;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -50,7 +50,7 @@ struct __align__(128) TetHot {
 static_assert(sizeof(TetHot) == 128, "TetHot layout");
 
 // bits of the device status word
-enum : int32_t { ST_WALK = 1, ST_INVAL = 2 };
+enum : int32_t { ST_WALK = 1, ST_INVAL = 2, ST_NOCONV = 4 };
 
 struct HostComplex {
     int64_t nn = 0, ne = 0, nf = 0, nt = 0;
@@ -75,6 +75,8 @@ void incidence_csr(const HostComplex& hc, int which, std::vector<int32_t>* row_p
 }  // namespace fempic
 
 namespace fempic {
+struct FieldDev;
+void field_free(fem_pic* ctx);
 // phases timed by the optional profiler (fem_pic_profile_*)
 enum Phase : int { PH_PREP = 0, PH_FAST = 1, PH_WALK = 2, PH_PUSH64 = 3, PH_CHARGE = 4, PH_SORT = 5,
                    PH_RESID = 6, PH_SOLVE = 7, PH_COUNT = 16 };
@@ -87,6 +89,7 @@ struct ProfRec {
 struct fem_pic {
     int device = 0;
     int sm_count = 152;
+    fempic::FieldDev* field = nullptr;  // implicit field step (fem_pic_field_setup)
     // profiler: events recorded on the launch stream around each kernel when enabled
     bool prof_on = false;
     std::vector<fempic::ProfRec> prof_pending;

@@ -135,21 +135,6 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-__device__ __forceinline__ double block_max(double v, double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (wid == 0) {
-        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(kFull, r, o));
-    }
-    __syncthreads();
-    return r;
-}
 
 __device__ __forceinline__ double as_f64(float x) { return f2d(x); }
 __device__ __forceinline__ double as_f64(double x) { return x; }

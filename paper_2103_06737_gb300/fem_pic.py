@@ -48,6 +48,22 @@ class FPParticles(ctypes.Structure):
                 ("w", ctypes.c_double)]
 
 
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("precond", ctypes.c_int32), ("fell_back", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iters=int(self.iters), precond=int(self.precond), fell_back=int(self.fell_back),
+                    rel_res=float(self.rel_res), abs_res=float(self.abs_res), ms=float(self.ms))
+
+
+FP_SYS_NEWMARK, FP_SYS_GAUSS = 0, 1
+FP_PC_JACOBI, FP_PC_LEARNED = 0, 1
+EPS0 = 8.854_187_8128e-12
+MU0 = 1.256_637_062_12e-6
+
+
 def library_path() -> str:
     return _build.SO
 
@@ -80,6 +96,12 @@ def lib():
             "fem_pic_sort": (I32, [P, ctypes.POINTER(FPParticles), ctypes.POINTER(FPParticles), P]),
             "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
             "fem_pic_status": (I32, [P, P]),
+            "fem_pic_field_setup": (I32, [P, D, D, D]),
+            "fem_pic_field_nnz": (I32, [P, P]),
+            "fem_pic_field_matrix": (I32, [P, I32, P, P, P]),
+            "fem_pic_field_solve": (I32, [P, I32, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_field_step": (I32, [P, P, P, P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_field_initial": (I32, [P, P, P, D, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_profile_enable": (I32, [P, I32]),
             "fem_pic_profile_read": (I32, [P, P, P, I32]),
         }
@@ -295,6 +317,59 @@ def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
 
 def fem_pic_status(h, stream=None) -> int:
     return int(lib().fem_pic_status(h, _stream(stream)))
+
+
+def fem_pic_field_setup(h, dt: float, eps: float = EPS0, mu: float = MU0):
+    _check(lib().fem_pic_field_setup(h, float(dt), float(eps), float(mu)), h)
+
+
+def fem_pic_field_matrix(h, which: int):
+    """Host CSR (row_ptr, col, val) of M (0), S (1), A (2) or L (3)."""
+    nnz = np.zeros(2, dtype=np.int64)
+    _check(lib().fem_pic_field_nnz(h, _ptr(nnz)), h)
+    sz = fem_pic_sizes(h)
+    rows = sz["n_nodes"] if which == 3 else sz["n_edges"]
+    k = int(nnz[1] if which == 3 else nnz[0])
+    rp = np.empty(rows + 1, np.int32)
+    col = np.empty(k, np.int32)
+    val = np.empty(k, np.float64)
+    _check(lib().fem_pic_field_matrix(h, int(which), _ptr(rp), _ptr(col), _ptr(val)), h)
+    return rp, col, val
+
+
+def fem_pic_field_solve(h, system: int, rhs, x, tol: float = 1e-10, max_iter: int = 10000,
+                        precond: int = FP_PC_JACOBI, info: bool = True, stream=None):
+    _need(rhs, torch.float64, name="rhs")
+    _need(x, torch.float64, rhs.numel(), name="x")
+    inf = SolveInfo() if info else None
+    st = lib().fem_pic_field_solve(h, int(system), _ptr(rhs), _ptr(x), float(tol), int(max_iter), int(precond),
+                                   ctypes.byref(inf) if inf is not None else None, _stream(stream))
+    if st not in (FP_OK, FP_ENOCONV):
+        _check(st, h)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_field_step(h, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol: float = 1e-10,
+                       max_iter: int = 10000, precond: int = FP_PC_JACOBI, info: bool = True, stream=None):
+    sz = fem_pic_sizes(h)
+    for t, nm in ((E_prev, "E_prev"), (E_cur, "E_cur"), (E_next, "E_next")):
+        _need(t, torch.float64, sz["n_edges"], name=nm)
+    inf = (SolveInfo * 2)() if info else None
+    st = lib().fem_pic_field_step(h, _ptr(E_prev), _ptr(E_cur), _ptr(E_next), _ptr(b), _ptr(dG_half),
+                                  _ptr(dG_prev), _ptr(Q_new), float(tol), int(max_iter), int(precond),
+                                  inf, _stream(stream))
+    if st not in (FP_OK, FP_ENOCONV):
+        _check(st, h)
+    return st, ([inf[0].as_dict(), inf[1].as_dict()] if inf is not None else None)
+
+
+def fem_pic_field_initial(h, Q, E, tol: float = 1e-10, max_iter: int = 10000, info: bool = True, stream=None):
+    inf = SolveInfo() if info else None
+    st = lib().fem_pic_field_initial(h, _ptr(Q), _ptr(E), float(tol), int(max_iter),
+                                     ctypes.byref(inf) if inf is not None else None, _stream(stream))
+    if st not in (FP_OK, FP_ENOCONV):
+        _check(st, h)
+    return st, (inf.as_dict() if inf is not None else None)
 
 
 PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_solve")
