@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-graphs", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
+    ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -183,9 +186,23 @@ def run_gpu(args):
         ev = wl.E_amp * length * u
         ev[wall] = 0.0
         e.copy_(torch.as_tensor(ev, device=dev))
-    dG = torch.empty(sizes["n_edges"], dtype=torch.float32, device=dev)
-    Qs = [torch.empty(sizes["n_nodes"], dtype=torch.float32, device=dev) for _ in range(2)]
+    dG = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)       # dG^{n+1/2}
+    dG_prev = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)  # dG^{n-1/2}
+    Qn = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
+    Qo = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
     res = torch.zeros(6, dtype=torch.float64, device=dev)
+    # uniform immobile neutralising ion background where the workload has one:
+    # Q_ion,n = -(total electron charge) alpha^0_n / V, alpha^0_n = integral of W0_n
+    Q_ion = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
+    if wl.background_ions:
+        alpha = F.fem_pic_whitney0_integrals(lib.h)
+        qtot = sum(s_.q * s_.w * s_.n for s_ in species)
+        Q_ion.copy_(torch.as_tensor(-qtot * alpha / alpha.sum(), device=dev))
+    field = not args.no_field
+    if field:
+        F.fem_pic_field_setup(lib.h, wl.dt)
+    E_prev = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
+    E_next = torch.zeros_like(E_prev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     flush_rd = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -202,20 +219,26 @@ def run_gpu(args):
     for k in range(len(species)):
         lib.sort(bufs[k][0], bufs[k][1])
         cur[k] = 1
+    Qo.copy_(Q_ion)
     for k in range(len(species)):
-        lib.deposit_charge(bufs[k][cur[k]], Qs[0], flags=F.FP_ACCUMULATE if k else 0)
+        lib.deposit_charge(bufs[k][cur[k]], Qo, flags=F.FP_ACCUMULATE)
+    if field:   # E^0 from the Gauss law of the initial charge; E^{-1} = E^0, dG^{-1/2} = 0
+        st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
+        if st0 != F.FP_OK:
+            raise RuntimeError(f"initial field: {inf0}")
+        E_prev.copy_(e)
     st = lib.status()
     if st != F.FP_OK:
         raise RuntimeError(f"setup status {st}: {F.fem_pic_last_error(lib.h)}")
 
     def plan(i):
-        """(sort now?, buffer index per species before the step, Q parity) of step i"""
+        """(sort now?, buffer index per species before the step) of step i"""
         sort_now = args.sort_every > 0 and i > 0 and i % args.sort_every == 0
-        return sort_now, tuple(cur), i % 2
+        return sort_now, tuple(cur)
 
     def enqueue(pl):
-        """One step on the current stream; returns the number of library kernels launched."""
-        sort_now, before, par = pl
+        """One PIC step on the current stream; returns the number of library kernels launched."""
+        sort_now, before = pl
         n_k = 0
         use = []
         for k in range(len(species)):
@@ -225,12 +248,22 @@ def run_gpu(args):
                 b_ = 1 - b_
                 n_k += 5
             use.append(bufs[k][b_])
-        Qn, Qo = Qs[1 - par], Qs[par]
-        for k, s_ in enumerate(use):
-            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE if k else 0)
+        dG.zero_()
+        Qn.copy_(Q_ion)
+        for k, s_ in enumerate(use):     # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}
+            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE)
             n_k += 3              # field prep, fast push, FP64 walk of the queued particles
+        if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
+            F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
+                                 max_iter=args.max_iter, info=False)
+            n_k += 7
         lib.residuals(dG, Qn, Qo, b, res)
         n_k += 1
+        Qo.copy_(Qn)
+        if field:
+            dG_prev.copy_(dG)
+            E_prev.copy_(e)
+            e.copy_(E_next)
         return n_k
 
     def advance(pl):
@@ -272,6 +305,7 @@ def run_gpu(args):
             with torch.cuda.graph(g):
                 n_k = enqueue(pl)
             graphs[pl] = (g, n_k)
+            torch.cuda.synchronize()
         g, n_k = graphs[pl]
         g.replay()
         advance(pl)
@@ -317,17 +351,23 @@ def run_gpu(args):
     F.fem_pic_profile_read(lib.h, reset=True)
     F.fem_pic_profile_enable(lib.h, True)
     push_ms = []
+    iters_n, iters_g, relres = [], [], []
     for k in range(args.steps):
         flush_l2(k)
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
         pl = plan(state["i"])
         a.record(stream)
-        enqueue((pl[0], pl[1], pl[2]))
+        enqueue(pl)
         z.record(stream)
         advance(pl)
         state["i"] += 1
         push_ms.append((a, z))
+        if field:
+            fi = F.fem_pic_field_last_info(lib.h)
+            iters_n.append(fi[0]["iters"])
+            iters_g.append(fi[1]["iters"])
+            relres.append(max(fi[0]["rel_res"], fi[1]["rel_res"]))
     torch.cuda.synchronize()
     F.fem_pic_profile_enable(lib.h, False)
     phases = F.fem_pic_profile_read(lib.h, reset=True)
@@ -346,11 +386,16 @@ def run_gpu(args):
             hc.copy_(s.cell)
             ho.copy_(s.off)
             hv.copy_(s.vel)
-        he, hb = e.cpu().pin_memory(), b.cpu().pin_memory()
+        # the step's inputs: particle state, fields E^n, E^{n-1}, b, dG^{n-1/2}, Q^n
+        fin = [(e, e.cpu().pin_memory()), (b, b.cpu().pin_memory()), (E_prev, E_prev.cpu().pin_memory()),
+               (dG_prev, dG_prev.cpu().pin_memory()), (Qo, Qo.cpu().pin_memory())]
         hdG = torch.empty_like(dG, device="cpu").pin_memory()
-        hQ = torch.empty_like(Qs[0], device="cpu").pin_memory()
-        bi = sum(x.numel() * x.element_size() for tr in hs for x in tr) + he.numel() * 8 + hb.numel() * 8
-        bo = sum(x.numel() * x.element_size() for tr in hs for x in tr) + hdG.numel() * 4 + hQ.numel() * 4
+        hQ = torch.empty_like(Qn, device="cpu").pin_memory()
+        hE = torch.empty_like(e, device="cpu").pin_memory()
+        bi = sum(x.numel() * x.element_size() for tr in hs for x in tr) + \
+            sum(h_.numel() * h_.element_size() for _, h_ in fin)
+        bo = sum(x.numel() * x.element_size() for tr in hs for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
+            (hE.numel() * 8 if field else 0)
         torch.cuda.synchronize()
         ee = []
         for k in range(args.steps):
@@ -362,15 +407,17 @@ def run_gpu(args):
                 s.cell.copy_(hc, non_blocking=True)
                 s.off.copy_(ho, non_blocking=True)
                 s.vel.copy_(hv, non_blocking=True)
-            e.copy_(he, non_blocking=True)
-            b.copy_(hb, non_blocking=True)
+            for d_, h_ in fin:
+                d_.copy_(h_, non_blocking=True)
             eager_step()
             for (hc, ho, hv), s in zip(hs, species):
                 hc.copy_(s.cell, non_blocking=True)
                 ho.copy_(s.off, non_blocking=True)
                 hv.copy_(s.vel, non_blocking=True)
             hdG.copy_(dG, non_blocking=True)
-            hQ.copy_(Qs[state["i"] % 2], non_blocking=True)
+            hQ.copy_(Qn, non_blocking=True)
+            if field:
+                hE.copy_(e, non_blocking=True)
             species = [bufs[k][cur[k]] for k in range(len(species))]
             z.record(stream)
             ee.append((a, z))
@@ -403,7 +450,8 @@ def run_gpu(args):
                        "sort_every": args.sort_every, "precision": "fp32 particle path, fp64 walk test",
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "step": "sort (periodic) + push/gather/walk/deposit + fp64 residuals"},
+                       "step": "sort (periodic) + push/gather/walk/deposit + implicit field step "
+                               "(Newmark + Gauss-law projection + Faraday, FP64 Jacobi-CG to 1e-10) + fp64 residuals"},
             "roofline": {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
                          "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg,
@@ -417,6 +465,12 @@ def run_gpu(args):
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
             "host_ms_per_step": (th1 - th0) * 1e3 / args.steps,
             "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
+            "field_solve": None if not field else {
+                "ms_per_step": phases.get("field_solve", (0.0, 1))[0] / args.steps,
+                "precond": "jacobi", "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",
+                "tol": args.tol, "newmark_iters_mean": statistics.mean(iters_n),
+                "gauss_iters_mean": statistics.mean(iters_g), "max_rel_res": max(relres),
+                "n_edges": sizes["n_edges"], "n_nodes": sizes["n_nodes"]},
             "eager_ms_per_step": statistics.mean(push_ms),
             "residuals": {"continuity_interior_max": float(r[4]), "continuity_interior_scale": float(r[5]),
                           "continuity_all_nodes_max": float(r[0]), "continuity_all_nodes_scale": float(r[1]),

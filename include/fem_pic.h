@@ -283,6 +283,17 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
 fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
                                 fp_solve_info* info, void* stream);
 
+/* Iteration counts and residuals of the last Newmark (info[0]) and Gauss (info[1]) solves.
+ * Synchronises the stream. */
+fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* stream);
+
+/*
+ * alpha^0_n = integral over the domain of W0_n = sum over tets containing n of |T|/4
+ * (the alpha of Sec. IV.B, used for zero-mean constraints and for a uniform background
+ * charge Q_n = rho alpha^0_n).  alpha: host double [N_n].  Synchronous.
+ */
+fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha);
+
 /*
  * Optional per-phase timing (not part of the method).  When enabled, the library
  * records a pair of CUDA events on the launch stream around each of its kernels,

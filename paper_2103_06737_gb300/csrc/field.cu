@@ -3,6 +3,7 @@
 // runs as one cooperative kernel (convergence decided on the device, no host round trip).
 #include <cooperative_groups.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "field.cuh"
@@ -422,6 +423,30 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
     }
     return st;
+}
+
+fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* stream) {
+    if (!ctx || !ctx->field || !info) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = fill_info(ctx, 0, &info[0], s, 0.f);
+    if (st == FP_OK) st = fill_info(ctx, 1, &info[1], s, 0.f);
+    return st;
+}
+
+fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha) {
+    if (!ctx || !alpha) return FP_EINVAL;
+    const HostComplex& hc = ctx->hc;
+    std::vector<double> a(hc.nn, 0.0);
+    for (int64_t t = 0; t < hc.nt; ++t) {
+        const double* g = hc.geo[t].g;
+        // |T| = 1 / (6 |det G|), G = rows grad l1..3
+        const double det = g[0] * (g[4] * g[8] - g[5] * g[7]) - g[1] * (g[3] * g[8] - g[5] * g[6]) +
+                           g[2] * (g[3] * g[7] - g[4] * g[6]);
+        const double q = 1.0 / (24.0 * std::fabs(det));  // |T| / 4
+        for (int k = 0; k < 4; ++k) a[hc.tv[4 * t + k]] += q;
+    }
+    std::memcpy(alpha, a.data(), a.size() * sizeof(double));
+    return FP_OK;
 }
 
 fp_status fem_pic_field_nnz(const fem_pic_t* ctx, int64_t nnz[2]) {

@@ -102,6 +102,8 @@ def lib():
             "fem_pic_field_solve": (I32, [P, I32, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_step": (I32, [P, P, P, P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_initial": (I32, [P, P, P, D, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_field_last_info": (I32, [P, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_whitney0_integrals": (I32, [P, P]),
             "fem_pic_profile_enable": (I32, [P, I32]),
             "fem_pic_profile_read": (I32, [P, P, P, I32]),
         }
@@ -370,6 +372,18 @@ def fem_pic_field_initial(h, Q, E, tol: float = 1e-10, max_iter: int = 10000, in
     if st not in (FP_OK, FP_ENOCONV):
         _check(st, h)
     return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_field_last_info(h, stream=None):
+    inf = (SolveInfo * 2)()
+    _check(lib().fem_pic_field_last_info(h, inf, _stream(stream)), h)
+    return [inf[0].as_dict(), inf[1].as_dict()]
+
+
+def fem_pic_whitney0_integrals(h) -> np.ndarray:
+    a = np.empty(fem_pic_sizes(h)["n_nodes"], dtype=np.float64)
+    _check(lib().fem_pic_whitney0_integrals(h, _ptr(a)), h)
+    return a
 
 
 PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_solve")

@@ -189,6 +189,7 @@ class Workload:
     E_amp: float = 0.0     # amplitude of the seeded random edge field (V/m), 0 = none
     steps: int = 1
     n0: float = 1e14       # plasma density used for the macro weight
+    background_ions: bool = False   # uniform immobile neutralising ion background
 
 
 def _weight(n0: float, volume: float, n_macro: int) -> float:
@@ -210,13 +211,15 @@ def config(idx: int, scale: float = 1.0) -> Workload:
         npart = max(1, int(1000 * scale))
         B0 = 0.1
         sp = [uniform_species(mesh, npart, 0, 0.01 * C_LIGHT, -Q_E, M_E, _weight(1e14, L ** 3, npart))]
-        return Workload("cube4_e1k", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 100)
+        return Workload("cube4_e1k", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 100,
+                        background_ions=True)
     if idx == 2:
         mesh = cube_mesh(32, L, 0.1, seed=1)
         npart = max(1, int(2_000_000 * scale))
         B0 = 0.1
         sp = [uniform_species(mesh, npart, 2, 0.01 * C_LIGHT, -Q_E, M_E, _weight(1e14, L ** 3, npart))]
-        return Workload("cube32_jit_e2M", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 200)
+        return Workload("cube32_jit_e2M", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 200,
+                        background_ions=True)
     if idx == 3:
         mesh = cube_mesh(64, L, 0.1, seed=1)
         npart = max(1, int(20_000_000 * scale))
