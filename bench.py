@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--solver", default="mixed", choices=["mixed", "fp64"], help="field CG: mixed-precision refinement or plain FP64")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -199,6 +200,7 @@ def run_gpu(args):
         qtot = sum(s_.q * s_.w * s_.n for s_ in species)
         Q_ion.copy_(torch.as_tensor(-qtot * alpha / alpha.sum(), device=dev))
     field = not args.no_field
+    precond = F.FP_PC_JACOBI if args.solver == "mixed" else F.FP_PC_JACOBI_FP64
     if field:
         F.fem_pic_field_setup(lib.h, wl.dt)
     E_prev = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
@@ -255,7 +257,7 @@ def run_gpu(args):
             n_k += 3              # field prep, fast push, FP64 walk of the queued particles
         if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
             F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
-                                 max_iter=args.max_iter, info=False)
+                                 max_iter=args.max_iter, precond=precond, info=False)
             n_k += 7
         lib.residuals(dG, Qn, Qo, b, res)
         n_k += 1
@@ -351,7 +353,7 @@ def run_gpu(args):
     F.fem_pic_profile_read(lib.h, reset=True)
     F.fem_pic_profile_enable(lib.h, True)
     push_ms = []
-    iters_n, iters_g, relres = [], [], []
+    iters_n, iters_g, relres, outer_n, outer_g = [], [], [], [], []
     for k in range(args.steps):
         flush_l2(k)
         a = torch.cuda.Event(enable_timing=True)
@@ -367,6 +369,8 @@ def run_gpu(args):
             fi = F.fem_pic_field_last_info(lib.h)
             iters_n.append(fi[0]["iters"])
             iters_g.append(fi[1]["iters"])
+            outer_n.append(fi[0]["outer"])
+            outer_g.append(fi[1]["outer"])
             relres.append(max(fi[0]["rel_res"], fi[1]["rel_res"]))
     torch.cuda.synchronize()
     F.fem_pic_profile_enable(lib.h, False)
@@ -467,9 +471,12 @@ def run_gpu(args):
             "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
             "field_solve": None if not field else {
                 "ms_per_step": phases.get("field_solve", (0.0, 1))[0] / args.steps,
-                "precond": "jacobi", "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",
+                "precond": "jacobi", "solver": ("mixed-precision refinement (FP64 residual and dots, FP32 inner PCG)"
+                                                if args.solver == "mixed" else "plain FP64 PCG"),
+                "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",
                 "tol": args.tol, "newmark_iters_mean": statistics.mean(iters_n),
                 "gauss_iters_mean": statistics.mean(iters_g), "max_rel_res": max(relres),
+                "newmark_refinements_mean": statistics.mean(outer_n), "gauss_refinements_mean": statistics.mean(outer_g),
                 "n_edges": sizes["n_edges"], "n_nodes": sizes["n_nodes"]},
             "eager_ms_per_step": statistics.mean(push_ms),
             "residuals": {"continuity_interior_max": float(r[4]), "continuity_interior_scale": float(r[5]),

@@ -213,13 +213,16 @@ fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, c
 /* ------------------------------------------------------------------ implicit field step */
 
 enum { FP_SYS_NEWMARK = 0, FP_SYS_GAUSS = 1 };
-enum { FP_PC_JACOBI = 0, FP_PC_LEARNED = 1 };
+/* FP_PC_JACOBI: Jacobi-PCG by mixed-precision iterative refinement (FP64 residual and dot
+ * products, FP32 inner solves); FP_PC_JACOBI_FP64: plain Jacobi-PCG entirely in FP64;
+ * FP_PC_LEARNED: learned correction with fallback (see fem_pic_learned_*). */
+enum { FP_PC_JACOBI = 0, FP_PC_LEARNED = 1, FP_PC_JACOBI_FP64 = 2 };
 
 typedef struct {
-    int32_t iters;     /* CG iterations taken */
+    int32_t iters;     /* CG iterations taken (inner iterations for the mixed solver) */
     int32_t precond;   /* preconditioner used (FP_PC_*) */
     int32_t fell_back; /* 1 if a learned solve fell back to plain Jacobi-CG */
-    int32_t pad;
+    int32_t outer;     /* refinement steps (mixed solver), 0 for plain FP64 PCG */
     double rel_res;    /* final ||r|| / ||reference|| (see each call) */
     double abs_res;    /* final ||r|| */
     double ms;         /* device time of the solve when measured, else 0 */
@@ -248,7 +251,7 @@ fp_status fem_pic_field_matrix(const fem_pic_t* ctx, int which, int32_t* row_ptr
 
 /*
  * Solve A x = rhs (FP_SYS_NEWMARK, edges) or L x = rhs (FP_SYS_GAUSS, nodes) with
- * Jacobi-preconditioned CG in FP64, starting from the x passed in (device, in/out),
+ * Jacobi-preconditioned CG (precond, see FP_PC_*), starting from the x passed in (device, in/out),
  * until ||rhs - A x|| <= tol ||rhs|| or max_iter iterations.  rhs must be zero on PEC
  * rows.  info (host, may be NULL) is filled after a stream synchronisation; with info
  * a solve that stops at max_iter returns FP_ENOCONV, otherwise the status word records it.

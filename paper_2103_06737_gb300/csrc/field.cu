@@ -22,6 +22,8 @@ struct FieldDev {
     int32_t* face_edges = nullptr;  // [3 nf]: (i,j), (j,k), (i,k) of face (i<j<k)
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr, *tmp = nullptr,
            *delta = nullptr, *qd = nullptr;
+    float *Av32 = nullptr, *Adinv32 = nullptr, *Lv32 = nullptr, *Ldinv32 = nullptr;  // FP32 copies
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
     int grid = 0;                   // cooperative grid size
@@ -165,7 +167,182 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
         a.out[0] = (double)it;
         a.out[1] = rr;
         a.out[2] = bb;      // squared norm the residual is measured against
+        a.out[3] = 0.0;
         if (rr > thr) atomicOr(a.status, ST_NOCONV);
+    }
+}
+
+// ---------------------------------------------------------------- mixed-precision solver
+// Iterative refinement: the residual r = b - A x and every dot product are FP64; each
+// correction A c = r is solved approximately by Jacobi-PCG on FP32 copies of A and of the
+// vectors (until its own residual drops by inner_tol), then x += c in FP64.  FP64 work is
+// a few operations per row per outer step and three reductions per inner iteration; the
+// FP32 part runs on the fast pipes.  Two grid barriers per inner iteration (A p is carried
+// as q = A z + beta q).  Rows are spread over groups of 8 lanes.
+
+constexpr int kRowLanes = 8;
+
+__device__ __forceinline__ float csr_row_dot8(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const float* __restrict__ val, const float* __restrict__ x,
+                                              int64_t i, bool valid) {
+    const int sub = threadIdx.x & (kRowLanes - 1);
+    float s = 0.f;
+    if (valid) {
+        const int j1 = __ldg(rp + i + 1);
+        for (int j = __ldg(rp + i) + sub; j < j1; j += kRowLanes) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
+    }
+#pragma unroll
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return s;
+}
+
+__device__ __forceinline__ double csr_row_dot64_8(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                  const double* __restrict__ val, const double* __restrict__ x,
+                                                  int64_t i, bool valid) {
+    const int sub = threadIdx.x & (kRowLanes - 1);
+    double s = 0.0;
+    if (valid) {
+        const int j1 = __ldg(rp + i + 1);
+        for (int j = __ldg(rp + i) + sub; j < j1; j += kRowLanes) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
+    }
+#pragma unroll
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return s;
+}
+
+struct MixedArgs {
+    const int32_t* rp;
+    const int32_t* col;
+    const double* val;     // FP64 operator (outer residual)
+    const float* val32;    // FP32 copy (inner solves)
+    const float* dinv32;
+    int64_t n;
+    const double* b;
+    double* x;
+    double* r64;
+    float *r, *z, *p, *q, *c;
+    double* red;
+    double tol;            // outer: ||b - A x|| <= tol ||ref||
+    double inner_tol;      // inner: residual reduction per refinement
+    const double* scale_vec;
+    int max_iter;          // total inner iterations
+    int max_outer;
+    double* out;
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
+    cg::grid_group g = cg::this_grid();
+    __shared__ double sh[4][kBlock / 32];
+    const int groups_per_block = blockDim.x / kRowLanes;
+    const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
+    const int64_t g0 = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / kRowLanes;
+    const bool lead = (threadIdx.x & (kRowLanes - 1)) == 0;
+    const int64_t rounds = (a.n + gstride - 1) / gstride;  // uniform trip count for the shuffles
+    double* part0 = a.red;                    // 4 values
+    double* part1 = a.red + 4 * gridDim.x;    // 3 values
+    double* part2 = a.red + 7 * gridDim.x;    // 2 values
+    int total = 0, outer = 0;
+    double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
+    for (;;) {
+        // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t i = g0 + rd * gstride;
+            const bool ok = i < a.n;
+            const double ax = csr_row_dot64_8(a.rp, a.col, a.val, a.x, i, ok);
+            if (ok && lead) {
+                const double bi = a.b[i], ri = bi - ax;
+                a.r64[i] = ri;
+                a.r[i] = d2f(ri);
+                a.c[i] = 0.f;
+                v[0] += ri * ri;
+                v[1] += bi * bi;
+                if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
+            }
+        }
+        grid_sum<4>(v, part0, g, sh);
+        rr64 = v[0];
+        if (outer == 0) {
+            ref2 = a.scale_vec ? v[2] : v[1];
+            thr = a.tol * a.tol * ref2;
+        }
+        if (!(rr64 > thr) || total >= a.max_iter || outer >= a.max_outer) break;
+        ++outer;
+        // ---- inner FP32 Jacobi-PCG on A c = r (dots accumulated in FP64)
+        // z = D^-1 r; then (after a barrier) q = A z, p = z
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t i = g0 + rd * gstride;
+            if (i < a.n && lead) a.z[i] = a.dinv32[i] * a.r[i];
+        }
+        g.sync();
+        double u[3] = {0.0, 0.0, 0.0};  // r.z, p.q, r.r
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t i = g0 + rd * gstride;
+            const bool ok = i < a.n;
+            const float w = csr_row_dot8(a.rp, a.col, a.val32, a.z, i, ok);
+            if (ok && lead) {
+                const float zi = a.z[i], ri = a.r[i];
+                a.p[i] = zi;
+                a.q[i] = w;
+                u[0] += (double)(ri * zi);
+                u[1] += (double)(zi * w);
+                u[2] += (double)(ri * ri);
+            }
+        }
+        grid_sum<3>(u, part1, g, sh);
+        double rz = u[0], pq = u[1];
+        const double rr0 = u[2], ithr = a.inner_tol * a.inner_tol * rr0;
+        for (;;) {
+            if (!(pq > 0.0) || total >= a.max_iter) break;
+            const float alpha = (float)(rz / pq);
+            double w2[2] = {0.0, 0.0};  // r.z, r.r
+            for (int64_t rd = 0; rd < rounds; ++rd) {
+                const int64_t i = g0 + rd * gstride;
+                if (i < a.n && lead) {
+                    a.c[i] += alpha * a.p[i];
+                    const float ri = a.r[i] - alpha * a.q[i];
+                    const float zi = a.dinv32[i] * ri;
+                    a.r[i] = ri;
+                    a.z[i] = zi;
+                    w2[0] += (double)(ri * zi);
+                    w2[1] += (double)(ri * ri);
+                }
+            }
+            grid_sum<2>(w2, part2, g, sh);
+            ++total;
+            if (!(w2[1] > ithr)) break;
+            const float beta = (float)(w2[0] / rz);
+            rz = w2[0];
+            double u2[1] = {0.0};
+            for (int64_t rd = 0; rd < rounds; ++rd) {
+                const int64_t i = g0 + rd * gstride;
+                const bool ok = i < a.n;
+                const float w = csr_row_dot8(a.rp, a.col, a.val32, a.z, i, ok);
+                if (ok && lead) {
+                    const float pi = a.z[i] + beta * a.p[i];
+                    const float qi = w + beta * a.q[i];
+                    a.p[i] = pi;
+                    a.q[i] = qi;
+                    u2[0] += (double)(pi * qi);
+                }
+            }
+            grid_sum<1>(u2, part1, g, sh);
+            pq = u2[0];
+        }
+        // x += c (FP64)
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t i = g0 + rd * gstride;
+            if (i < a.n && lead) a.x[i] += f2d(a.c[i]);
+        }
+        g.sync();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[0] = (double)total;
+        a.out[1] = rr64;
+        a.out[2] = ref2;
+        a.out[3] = (double)outer;
+        if (rr64 > thr) atomicOr(a.status, ST_NOCONV);
     }
 }
 
@@ -261,6 +438,22 @@ fp_status up(fem_pic* ctx, T** d, const std::vector<T>& h) {
 fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double tol, const double* scale_vec,
                   int max_iter, int slot, cudaStream_t s) {
     FieldDev* F = ctx->field;
+    if (ctx->solver_fp64 == 0) {
+        MixedArgs m;
+        if (system == FP_SYS_NEWMARK) {
+            m.rp = F->e_rp, m.col = F->e_col, m.val = F->Av, m.val32 = F->Av32, m.dinv32 = F->Adinv32, m.n = F->ne;
+        } else {
+            m.rp = F->n_rp, m.col = F->n_col, m.val = F->Lv, m.val32 = F->Lv32, m.dinv32 = F->Ldinv32, m.n = F->nn;
+        }
+        m.b = rhs, m.x = x, m.r64 = F->q;
+        m.r = F->r32, m.z = F->z32, m.p = F->p32, m.q = F->q32, m.c = F->c32, m.red = F->red;
+        m.tol = tol, m.inner_tol = 1e-4, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
+        m.out = F->out + 4 * slot, m.status = ctx->d_status;
+        void* args[] = {&m};
+        PhaseTimer pt(ctx, PH_SOLVE, s);
+        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(F->grid), dim3(kBlock), args, 0, s));
+        return FP_OK;
+    }
     PcgArgs a;
     if (system == FP_SYS_NEWMARK) {
         a.rp = F->e_rp, a.col = F->e_col, a.val = F->Av, a.dinv = F->Adinv, a.n = F->ne;
@@ -281,10 +474,11 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     FP_CUDA_TRY(ctx, cudaMemcpyAsync(o, ctx->field->out + 4 * slot, sizeof o, cudaMemcpyDeviceToHost, s));
     FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     info->iters = (int32_t)o[0];
+    info->outer = (int32_t)o[3];
     info->rel_res = o[2] > 0 ? sqrt(o[1] / o[2]) : sqrt(o[1]);
     info->abs_res = sqrt(o[1]);
     info->ms = ms;
-    info->precond = FP_PC_JACOBI;
+    info->precond = ctx->solver_fp64 ? FP_PC_JACOBI_FP64 : FP_PC_JACOBI;
     info->fell_back = 0;
     return FP_OK;
 }
@@ -343,7 +537,8 @@ void field_free(fem_pic* ctx) {
     if (!F) return;
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
-                    F->delta, F->qd, F->red, F->out};
+                    F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
+                    F->z32, F->p32, F->q32, F->c32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete F;
@@ -402,13 +597,29 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
     if (st == FP_OK) st = up(ctx, &F->edge_fixed, H.edge_fixed);
     if (st == FP_OK) st = up(ctx, &F->node_fixed, H.node_fixed);
     if (st == FP_OK) st = up(ctx, &F->face_edges, fe);
+    {
+        std::vector<float> a32(A.begin(), A.end()), ad32(Ad.begin(), Ad.end()), l32(H.L.begin(), H.L.end()),
+            ld32(Ld.begin(), Ld.end());
+        if (st == FP_OK) st = up(ctx, &F->Av32, a32);
+        if (st == FP_OK) st = up(ctx, &F->Adinv32, ad32);
+        if (st == FP_OK) st = up(ctx, &F->Lv32, l32);
+        if (st == FP_OK) st = up(ctx, &F->Ldinv32, ld32);
+    }
     const int64_t nmax = hc.ne > hc.nn ? hc.ne : hc.nn;
+    float** vecs32[] = {&F->r32, &F->z32, &F->p32, &F->q32, &F->c32};
+    for (float** v : vecs32)
+        if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)v, nmax * sizeof(float)));
     double** vecs[] = {&F->r, &F->z, &F->p, &F->q, &F->rhs, &F->tmp, &F->delta, &F->qd};
     for (double** v : vecs)
         if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)v, nmax * sizeof(double)));
     // cooperative grid: all blocks co-resident
     int per_sm = 0;
-    if (st == FP_OK) FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
+    if (st == FP_OK) {
+        int per_sm2 = 0;
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_pcg_mixed, kBlock, 0));
+        if (per_sm2 < per_sm) per_sm = per_sm2;
+    }
     if (st == FP_OK) {
         if (per_sm < 1) {
             ctx->err = "fem_pic_field_setup: the solver kernel cannot be co-resident";
@@ -418,7 +629,7 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         const int64_t need = (nmax + kBlock - 1) / kBlock;
         if (grid > need) grid = (int)need;
         F->grid = grid < 1 ? 1 : grid;
-        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 6 * (size_t)F->grid * sizeof(double)));
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
     }
@@ -478,10 +689,11 @@ fp_status fem_pic_field_matrix(const fem_pic_t* ctx, int which, int32_t* row_ptr
 fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, double* x, double tol,
                               int max_iter, int precond, fp_solve_info* info, void* stream) {
     if (!ctx || !ctx->field || !rhs || !x || (system != FP_SYS_NEWMARK && system != FP_SYS_GAUSS) ||
-        !(tol > 0.0) || max_iter < 0 || precond != FP_PC_JACOBI) {
+        !(tol > 0.0) || max_iter < 0 || (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64)) {
         if (ctx) ctx->err = "fem_pic_field_solve: bad argument (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
+    ctx->solver_fp64 = precond == FP_PC_JACOBI_FP64;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a = nullptr, b = nullptr;
     if (info) {
@@ -507,10 +719,11 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
                              double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                              int max_iter, int precond, fp_solve_info info[2], void* stream) {
     if (!ctx || !ctx->field || !E_prev || !E_cur || !E_next || !Q_new || !(tol > 0.0) || max_iter < 0 ||
-        precond != FP_PC_JACOBI || E_next == E_cur || E_next == E_prev) {
+        (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64) || E_next == E_cur || E_next == E_prev) {
         if (ctx) ctx->err = "fem_pic_field_step: bad argument (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
+    ctx->solver_fp64 = precond == FP_PC_JACOBI_FP64;
     cudaStream_t s = (cudaStream_t)stream;
     fp_status st = field_step_impl(ctx, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol, max_iter, s);
     if (st != FP_OK || !info) return st;

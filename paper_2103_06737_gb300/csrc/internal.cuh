@@ -90,6 +90,7 @@ struct fem_pic {
     int device = 0;
     int sm_count = 152;
     fempic::FieldDev* field = nullptr;  // implicit field step (fem_pic_field_setup)
+    int solver_fp64 = 0;                // 1: plain FP64 PCG, 0: mixed-precision refinement
     // profiler: events recorded on the launch stream around each kernel when enabled
     bool prof_on = false;
     std::vector<fempic::ProfRec> prof_pending;

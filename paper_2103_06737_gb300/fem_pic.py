@@ -50,16 +50,17 @@ class FPParticles(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("precond", ctypes.c_int32), ("fell_back", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double),
+                ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double),
                 ("ms", ctypes.c_double)]
 
     def as_dict(self):
-        return dict(iters=int(self.iters), precond=int(self.precond), fell_back=int(self.fell_back),
-                    rel_res=float(self.rel_res), abs_res=float(self.abs_res), ms=float(self.ms))
+        return dict(iters=int(self.iters), outer=int(self.outer), precond=int(self.precond),
+                    fell_back=int(self.fell_back), rel_res=float(self.rel_res), abs_res=float(self.abs_res),
+                    ms=float(self.ms))
 
 
 FP_SYS_NEWMARK, FP_SYS_GAUSS = 0, 1
-FP_PC_JACOBI, FP_PC_LEARNED = 0, 1
+FP_PC_JACOBI, FP_PC_LEARNED, FP_PC_JACOBI_FP64 = 0, 1, 2
 EPS0 = 8.854_187_8128e-12
 MU0 = 1.256_637_062_12e-6
 

@@ -63,7 +63,8 @@ def test_operators_match_oracle(setup6, prec):
     lib.close()
 
 
-def test_newmark_solve_matches_direct(setup6):
+@pytest.mark.parametrize("precond", [F.FP_PC_JACOBI, F.FP_PC_JACOBI_FP64])
+def test_newmark_solve_matches_direct(setup6, precond):
     m, cx, dt, fo = setup6
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP64)
     F.fem_pic_field_setup(lib.h, dt)
@@ -73,15 +74,26 @@ def test_newmark_solve_matches_direct(setup6):
     x_ref = np.zeros(cx.n_edges)
     x_ref[fo.ie] = OF._solve(fo.A_II, rhs[fo.ie])
     x = torch.zeros(cx.n_edges, dtype=torch.float64, device="cuda")
-    st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_NEWMARK, torch.as_tensor(rhs, device="cuda"), x, tol=1e-10)
+    st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_NEWMARK, torch.as_tensor(rhs, device="cuda"), x, tol=1e-10,
+                                     precond=precond)
     assert st == F.FP_OK and info["rel_res"] <= 1e-10 and info["iters"] > 1
     assert np.abs(x.cpu().numpy() - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
     # an iteration cap of 1 reports non-convergence, and the status word records it
     x.zero_()
     st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_NEWMARK, torch.as_tensor(rhs, device="cuda"), x, tol=1e-10,
-                                     max_iter=1)
+                                     max_iter=1, precond=precond)
     assert st == F.FP_ENOCONV and info["iters"] == 1
     assert lib.status() == F.FP_ENOCONV
+    # the Gauss-law (node Laplacian) system
+    g = rng.uniform(-1, 1, cx.n_nodes) * 1e-20
+    g[cx.boundary_node] = 0.0
+    d_ref = np.zeros(cx.n_nodes)
+    d_ref[fo.inn] = OF._solve(fo.L_II, g[fo.inn])
+    d = torch.zeros(cx.n_nodes, dtype=torch.float64, device="cuda")
+    st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_GAUSS, torch.as_tensor(g, device="cuda"), d, tol=1e-10,
+                                     precond=precond)
+    assert st == F.FP_OK and info["rel_res"] <= 1e-10
+    assert np.abs(d.cpu().numpy() - d_ref).max() <= 1e-7 * np.abs(d_ref).max()
     lib.close()
 
 
