@@ -26,7 +26,8 @@ struct FieldDev {
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
-    int grid = 0;                   // cooperative grid size
+    int grid = 0;                   // co-resident blocks (cooperative launch limit)
+    int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
 };
 
 namespace {
@@ -89,6 +90,25 @@ __device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_gr
     for (int k = 0; k < NV; ++k) v[k] = t[k];
 }
 
+// Grid-wide sum through FP64 atomics on one of three rotating slots: reduction k adds into
+// slot k%3 while block 0 clears slot (k+1)%3, whose last readers (reduction k-2) finished
+// before the barrier of reduction k-1.  The summation order over blocks is not fixed, so
+// iterates can differ in the last bits from run to run; the slots start cleared.
+template <int NV>
+__device__ __forceinline__ void grid_sum_at(double v[NV], double* acc, int& seq, cg::grid_group& g,
+                                            double (*sh)[kBlock / 32]) {
+    block_sum<NV>(v, sh);
+    const int slot = seq % 3, next = (seq + 1) % 3;
+    if (blockIdx.x == 0 && threadIdx.x < 4) acc[4 * next + threadIdx.x] = 0.0;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) atomicAdd(acc + 4 * slot + k, v[k]);
+    g.sync();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = __ldcg(acc + 4 * slot + k);
+    ++seq;
+}
+
 struct PcgArgs {
     const int32_t* rp;
     const int32_t* col;
@@ -114,9 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
     __shared__ double sh[4][kBlock / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double* part0 = a.red;
-    double* part1 = a.red + 4 * gridDim.x;
-    double* part2 = a.red + 5 * gridDim.x;
+    int seq = 0;
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, b.b, s.s
     for (int64_t i = t0; i < a.n; i += stride) {
         const double bi = a.b[i];
@@ -130,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
         v[1] += ri * ri;
         v[2] += bi * bi;
     }
-    grid_sum<4>(v, part0, g, sh);
+    grid_sum_at<4>(v, a.red, seq, g, sh);
     double rz = v[0], rr = v[1];
     const double bb = a.scale_vec ? v[3] : v[2];
     const double thr = a.tol * a.tol * bb;
@@ -143,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
             a.q[i] = qi;
             w[0] += a.p[i] * qi;
         }
-        grid_sum<1>(w, part1, g, sh);
+        grid_sum_at<1>(w, a.red, seq, g, sh);
         if (!(w[0] > 0.0)) break;  // breakdown (same decision in every block)
         const double alpha = rz / w[0];
         double u[2] = {0.0, 0.0};
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
             u[0] += ri * zi;
             u[1] += ri * ri;
         }
-        grid_sum<2>(u, part2, g, sh);
+        grid_sum_at<2>(u, a.red, seq, g, sh);
         const double beta = u[0] / rz;
         rz = u[0];
         rr = u[1];
@@ -178,37 +196,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
 // vectors (until its own residual drops by inner_tol), then x += c in FP64.  FP64 work is
 // a few operations per row per outer step and three reductions per inner iteration; the
 // FP32 part runs on the fast pipes.  Two grid barriers per inner iteration (A p is carried
-// as q = A z + beta q).  Rows are spread over groups of 8 lanes.
-
-constexpr int kRowLanes = 8;
-
-__device__ __forceinline__ float csr_row_dot8(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                              const float* __restrict__ val, const float* __restrict__ x,
-                                              int64_t i, bool valid) {
-    const int sub = threadIdx.x & (kRowLanes - 1);
-    float s = 0.f;
-    if (valid) {
-        const int j1 = __ldg(rp + i + 1);
-        for (int j = __ldg(rp + i) + sub; j < j1; j += kRowLanes) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
-    }
-#pragma unroll
-    for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    return s;
-}
-
-__device__ __forceinline__ double csr_row_dot64_8(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                  const double* __restrict__ val, const double* __restrict__ x,
-                                                  int64_t i, bool valid) {
-    const int sub = threadIdx.x & (kRowLanes - 1);
-    double s = 0.0;
-    if (valid) {
-        const int j1 = __ldg(rp + i + 1);
-        for (int j = __ldg(rp + i) + sub; j < j1; j += kRowLanes) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
-    }
-#pragma unroll
-    for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    return s;
-}
+// as q = A z + beta q).
 
 struct MixedArgs {
     const int32_t* rp;
@@ -231,37 +219,38 @@ struct MixedArgs {
     int32_t* status;
 };
 
+__device__ __forceinline__ float csr_row_dot32(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                               const float* __restrict__ val, const float* __restrict__ x,
+                                               int64_t i) {
+    float s = 0.f;
+    const int j1 = __ldg(rp + i + 1);
+    for (int j = __ldg(rp + i); j < j1; ++j) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
+    return s;
+}
+
 __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
     __shared__ double sh[4][kBlock / 32];
-    const int groups_per_block = blockDim.x / kRowLanes;
-    const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
-    const int64_t g0 = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / kRowLanes;
-    const bool lead = (threadIdx.x & (kRowLanes - 1)) == 0;
-    const int64_t rounds = (a.n + gstride - 1) / gstride;  // uniform trip count for the shuffles
-    double* part0 = a.red;                    // 4 values
-    double* part1 = a.red + 4 * gridDim.x;    // 3 values
-    double* part2 = a.red + 7 * gridDim.x;    // 2 values
-    int total = 0, outer = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int seq = 0, total = 0, outer = 0;
     double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
     for (;;) {
         // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
         double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int64_t rd = 0; rd < rounds; ++rd) {
-            const int64_t i = g0 + rd * gstride;
-            const bool ok = i < a.n;
-            const double ax = csr_row_dot64_8(a.rp, a.col, a.val, a.x, i, ok);
-            if (ok && lead) {
-                const double bi = a.b[i], ri = bi - ax;
-                a.r64[i] = ri;
-                a.r[i] = d2f(ri);
-                a.c[i] = 0.f;
-                v[0] += ri * ri;
-                v[1] += bi * bi;
-                if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
-            }
+        for (int64_t i = t0; i < a.n; i += stride) {
+            const double bi = a.b[i];
+            double ax = 0.0;
+            const int j1 = __ldg(a.rp + i + 1);
+            for (int j = __ldg(a.rp + i); j < j1; ++j) ax += __ldg(a.val + j) * __ldcg(a.x + __ldg(a.col + j));
+            const double ri = bi - ax;
+            a.r64[i] = ri;
+            a.c[i] = 0.f;
+            v[0] += ri * ri;
+            v[1] += bi * bi;
+            if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
         }
-        grid_sum<4>(v, part0, g, sh);
+        grid_sum_at<4>(v, a.red, seq, g, sh);
         rr64 = v[0];
         if (outer == 0) {
             ref2 = a.scale_vec ? v[2] : v[1];
@@ -269,75 +258,61 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
         }
         if (!(rr64 > thr) || total >= a.max_iter || outer >= a.max_outer) break;
         ++outer;
-        // ---- inner FP32 Jacobi-PCG on A c = r (dots accumulated in FP64)
-        // z = D^-1 r; then (after a barrier) q = A z, p = z
-        for (int64_t rd = 0; rd < rounds; ++rd) {
-            const int64_t i = g0 + rd * gstride;
-            if (i < a.n && lead) a.z[i] = a.dinv32[i] * a.r[i];
+        // ---- inner FP32 Jacobi-PCG on A c = r / ||r|| (dot products accumulated in FP64)
+        const double rnorm = sqrt(rr64), rinv = 1.0 / rnorm;
+        for (int64_t i = t0; i < a.n; i += stride) {
+            const float ri = d2f(a.r64[i] * rinv);
+            a.r[i] = ri;
+            a.z[i] = a.dinv32[i] * ri;
         }
         g.sync();
         double u[3] = {0.0, 0.0, 0.0};  // r.z, p.q, r.r
-        for (int64_t rd = 0; rd < rounds; ++rd) {
-            const int64_t i = g0 + rd * gstride;
-            const bool ok = i < a.n;
-            const float w = csr_row_dot8(a.rp, a.col, a.val32, a.z, i, ok);
-            if (ok && lead) {
-                const float zi = a.z[i], ri = a.r[i];
-                a.p[i] = zi;
-                a.q[i] = w;
-                u[0] += (double)(ri * zi);
-                u[1] += (double)(zi * w);
-                u[2] += (double)(ri * ri);
-            }
+        for (int64_t i = t0; i < a.n; i += stride) {
+            const float w = csr_row_dot32(a.rp, a.col, a.val32, a.z, i);
+            const float zi = a.z[i], ri = a.r[i];
+            a.p[i] = zi;
+            a.q[i] = w;
+            u[0] += (double)(ri * zi);
+            u[1] += (double)(zi * w);
+            u[2] += (double)(ri * ri);
         }
-        grid_sum<3>(u, part1, g, sh);
+        grid_sum_at<3>(u, a.red, seq, g, sh);
         double rz = u[0], pq = u[1];
-        const double rr0 = u[2], ithr = a.inner_tol * a.inner_tol * rr0;
+        const double ithr = a.inner_tol * a.inner_tol * u[2];
         for (;;) {
             if (!(pq > 0.0) || total >= a.max_iter) break;
             const float alpha = (float)(rz / pq);
             double w2[2] = {0.0, 0.0};  // r.z, r.r
-            for (int64_t rd = 0; rd < rounds; ++rd) {
-                const int64_t i = g0 + rd * gstride;
-                if (i < a.n && lead) {
-                    a.c[i] += alpha * a.p[i];
-                    const float ri = a.r[i] - alpha * a.q[i];
-                    const float zi = a.dinv32[i] * ri;
-                    a.r[i] = ri;
-                    a.z[i] = zi;
-                    w2[0] += (double)(ri * zi);
-                    w2[1] += (double)(ri * ri);
-                }
+            for (int64_t i = t0; i < a.n; i += stride) {
+                a.c[i] += alpha * a.p[i];
+                const float ri = a.r[i] - alpha * a.q[i];
+                const float zi = a.dinv32[i] * ri;
+                a.r[i] = ri;
+                a.z[i] = zi;
+                w2[0] += (double)(ri * zi);
+                w2[1] += (double)(ri * ri);
             }
-            grid_sum<2>(w2, part2, g, sh);
+            grid_sum_at<2>(w2, a.red, seq, g, sh);
             ++total;
             if (!(w2[1] > ithr)) break;
             const float beta = (float)(w2[0] / rz);
             rz = w2[0];
             double u2[1] = {0.0};
-            for (int64_t rd = 0; rd < rounds; ++rd) {
-                const int64_t i = g0 + rd * gstride;
-                const bool ok = i < a.n;
-                const float w = csr_row_dot8(a.rp, a.col, a.val32, a.z, i, ok);
-                if (ok && lead) {
-                    const float pi = a.z[i] + beta * a.p[i];
-                    const float qi = w + beta * a.q[i];
-                    a.p[i] = pi;
-                    a.q[i] = qi;
-                    u2[0] += (double)(pi * qi);
-                }
+            for (int64_t i = t0; i < a.n; i += stride) {
+                const float w = csr_row_dot32(a.rp, a.col, a.val32, a.z, i);
+                const float pi = a.z[i] + beta * a.p[i];
+                const float qi = w + beta * a.q[i];
+                a.p[i] = pi;
+                a.q[i] = qi;
+                u2[0] += (double)(pi * qi);
             }
-            grid_sum<1>(u2, part1, g, sh);
+            grid_sum_at<1>(u2, a.red, seq, g, sh);
             pq = u2[0];
         }
-        // x += c (FP64)
-        for (int64_t rd = 0; rd < rounds; ++rd) {
-            const int64_t i = g0 + rd * gstride;
-            if (i < a.n && lead) a.x[i] += f2d(a.c[i]);
-        }
+        for (int64_t i = t0; i < a.n; i += stride) a.x[i] += rnorm * f2d(a.c[i]);
         g.sync();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (t0 == 0) {
         a.out[0] = (double)total;
         a.out[1] = rr64;
         a.out[2] = ref2;
@@ -451,7 +426,9 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
         void* args[] = {&m};
         PhaseTimer pt(ctx, PH_SOLVE, s);
-        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(F->grid), dim3(kBlock), args, 0, s));
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(F->red, 0, 12 * sizeof(double), s));
+        const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
+        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(grid), dim3(kBlock), args, 0, s));
         return FP_OK;
     }
     PcgArgs a;
@@ -464,7 +441,9 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     a.tol = tol, a.scale_vec = scale_vec, a.max_iter = max_iter, a.out = F->out + 4 * slot, a.status = ctx->d_status;
     void* args[] = {&a};
     PhaseTimer pt(ctx, PH_SOLVE, s);
-    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(F->grid), dim3(kBlock), args, 0, s));
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(F->red, 0, 12 * sizeof(double), s));
+    const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
+    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(kBlock), args, 0, s));
     return FP_OK;
 }
 
@@ -625,11 +604,14 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
             ctx->err = "fem_pic_field_setup: the solver kernel cannot be co-resident";
             return FP_ECUDA;
         }
-        int grid = ctx->sm_count * (per_sm < 2 ? per_sm : 2);
-        const int64_t need = (nmax + kBlock - 1) / kBlock;
-        if (grid > need) grid = (int)need;
-        F->grid = grid < 1 ? 1 : grid;
-        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));
+        F->grid = ctx->sm_count * per_sm;
+        auto fit = [&](int64_t rows) {
+            const int64_t need = (rows + kBlock - 1) / kBlock;
+            return (int)(need < F->grid ? (need < 1 ? 1 : need) : F->grid);
+        };
+        F->grid_e = fit(hc.ne);
+        F->grid_n = fit(hc.nn);
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
     }
