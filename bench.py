@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=2000)
-    ap.add_argument("--solver", default="mixed", choices=["mixed", "fp64"], help="field CG: mixed-precision refinement or plain FP64")
+    ap.add_argument("--solver", default="mixed,fp64",
+                    help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -200,9 +202,12 @@ def run_gpu(args):
         qtot = sum(s_.q * s_.w * s_.n for s_ in species)
         Q_ion.copy_(torch.as_tensor(-qtot * alpha / alpha.sum(), device=dev))
     field = not args.no_field
-    precond = F.FP_PC_JACOBI if args.solver == "mixed" else F.FP_PC_JACOBI_FP64
+    solv = (args.solver.split(",") + args.solver.split(","))[:2]
+    code = {"mixed": F.FP_PC_JACOBI, "fp64": F.FP_PC_JACOBI_FP64}
+    precond = F.FP_PC_JACOBI
     if field:
         F.fem_pic_field_setup(lib.h, wl.dt)
+        F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
     E_prev = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
     E_next = torch.zeros_like(E_prev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -470,9 +475,14 @@ def run_gpu(args):
             "host_ms_per_step": (th1 - th0) * 1e3 / args.steps,
             "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
             "field_solve": None if not field else {
-                "ms_per_step": phases.get("field_solve", (0.0, 1))[0] / args.steps,
-                "precond": "jacobi", "solver": ("mixed-precision refinement (FP64 residual and dots, FP32 inner PCG)"
-                                                if args.solver == "mixed" else "plain FP64 PCG"),
+                "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
+                                                                          "learned")) / args.steps,
+                "precond": "jacobi",
+                "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual and dot "
+                           "products, FP32 inner Jacobi-PCG", "fp64": "plain FP64 Jacobi-PCG",
+                           "inner_tol": args.inner_tol},
+                "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
+                "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,
                 "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",
                 "tol": args.tol, "newmark_iters_mean": statistics.mean(iters_n),
                 "gauss_iters_mean": statistics.mean(iters_g), "max_rel_res": max(relres),

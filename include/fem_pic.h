@@ -286,6 +286,14 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
 fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
                                 fp_solve_info* info, void* stream);
 
+/*
+ * Solver per system, overriding the precond argument of the solve calls: newmark_solver
+ * and gauss_solver are FP_PC_JACOBI (mixed-precision refinement), FP_PC_JACOBI_FP64, or
+ * -1 (use the precond passed to each call).  inner_tol in (0,1): residual reduction of each
+ * FP32 inner solve of the mixed solver (default 1e-4).
+ */
+fp_status fem_pic_field_options(fem_pic_t* ctx, int newmark_solver, int gauss_solver, double inner_tol);
+
 /* Iteration counts and residuals of the last Newmark (info[0]) and Gauss (info[1]) solves.
  * Synchronises the stream. */
 fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* stream);
@@ -301,7 +309,8 @@ fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha);
  * Optional per-phase timing (not part of the method).  When enabled, the library
  * records a pair of CUDA events on the launch stream around each of its kernels,
  * by phase: 0 field-coefficient prep, 1 FP32 push, 2 FP64 walk of deferred particles,
- * 3 FP64-mode push, 4 charge deposit, 5 sort, 6 residuals, 7 field solve.
+ * 3 FP64-mode push, 4 charge deposit, 5 sort, 6 residuals, 7 field-step kernels other than
+ * the solvers, 8 Newmark CG, 9 Gauss-law CG, 10 learned correction.
  * fem_pic_profile_read waits for the recorded events, adds their durations to
  * per-phase totals and returns them: ms[16] (milliseconds), count[16] (event pairs);
  * reset != 0 clears the totals.  Either output may be NULL.

@@ -28,12 +28,14 @@ struct FieldDev {
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
     int grid = 0;                   // co-resident blocks (cooperative launch limit)
     int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
+    int last_fp64[2] = {0, 0};      // solver used by the last solve in each info slot
 };
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 256;
+constexpr int kSolverBlock = 256;   // cooperative solvers: 256-thread blocks, 2 per SM
 
 __device__ __forceinline__ double as_f64(float x) { return f2d(x); }
 __device__ __forceinline__ double as_f64(double x) { return x; }
@@ -49,7 +51,7 @@ __device__ __forceinline__ double csr_row_dot(const int32_t* __restrict__ rp, co
 
 // sum of NV values over the block, result valid in every thread
 template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kBlock / 32]) {
+__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kSolverBlock / 32]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -65,7 +67,7 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kBlock / 32
     for (int k = 0; k < NV; ++k) {
         double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) t += sh[k][w];
+        for (int w = 0; w < kSolverBlock / 32; ++w) t += sh[k][w];
         v[k] = t;
     }
 }
@@ -73,7 +75,7 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kBlock / 32
 // deterministic grid-wide sum: partials of every block, summed in block order by each block
 template <int NV>
 __device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_group& g,
-                                         double (*sh)[kBlock / 32]) {
+                                         double (*sh)[kSolverBlock / 32]) {
     block_sum<NV>(v, sh);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -88,25 +90,6 @@ __device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_gr
     block_sum<NV>(t, sh);
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = t[k];
-}
-
-// Grid-wide sum through FP64 atomics on one of three rotating slots: reduction k adds into
-// slot k%3 while block 0 clears slot (k+1)%3, whose last readers (reduction k-2) finished
-// before the barrier of reduction k-1.  The summation order over blocks is not fixed, so
-// iterates can differ in the last bits from run to run; the slots start cleared.
-template <int NV>
-__device__ __forceinline__ void grid_sum_at(double v[NV], double* acc, int& seq, cg::grid_group& g,
-                                            double (*sh)[kBlock / 32]) {
-    block_sum<NV>(v, sh);
-    const int slot = seq % 3, next = (seq + 1) % 3;
-    if (blockIdx.x == 0 && threadIdx.x < 4) acc[4 * next + threadIdx.x] = 0.0;
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) atomicAdd(acc + 4 * slot + k, v[k]);
-    g.sync();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = __ldcg(acc + 4 * slot + k);
-    ++seq;
 }
 
 struct PcgArgs {
@@ -126,60 +109,84 @@ struct PcgArgs {
     int32_t* status;
 };
 
-// Jacobi-preconditioned conjugate gradients in one cooperative launch.  Every block takes
-// the same decisions from the same grid-wide sums, so all blocks run the same number of
-// grid barriers; the loop is bounded by max_iter.
-__global__ void __launch_bounds__(kBlock) k_pcg(PcgArgs a) {
+// Jacobi-preconditioned conjugate gradients in one cooperative launch (FP64).  Every
+// block takes the same decisions from the same grid-wide sums (deterministic: partials
+// summed in block order), so all blocks run the same number of grid barriers; the loop is
+// bounded by max_iter.  A p is carried as q = A z + beta q, two barriers per iteration.
+__global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
     cg::grid_group g = cg::this_grid();
-    __shared__ double sh[4][kBlock / 32];
+    __shared__ double sh[4][kSolverBlock / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int seq = 0;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, b.b, s.s
+    double* part0 = a.red;                    // 4 values per block
+    double* part1 = a.red + 4 * gridDim.x;    // 2 values per block
+    double* part2 = a.red + 6 * gridDim.x;    // 2 values per block
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.r, b.b, s.s
     for (int64_t i = t0; i < a.n; i += stride) {
         const double bi = a.b[i];
-        if (a.scale_vec) v[3] += a.scale_vec[i] * a.scale_vec[i];
-        const double ri = bi - csr_row_dot(a.rp, a.col, a.val, a.x, i);
-        const double zi = a.dinv[i] * ri;
+        double ax = 0.0;
+        const int j1 = __ldg(a.rp + i + 1);
+        for (int j = __ldg(a.rp + i); j < j1; ++j) ax += __ldg(a.val + j) * __ldcg(a.x + __ldg(a.col + j));
+        const double ri = bi - ax;
         a.r[i] = ri;
-        a.z[i] = zi;
-        a.p[i] = zi;
-        v[0] += ri * zi;
-        v[1] += ri * ri;
-        v[2] += bi * bi;
+        a.z[i] = a.dinv[i] * ri;
+        v[0] += ri * ri;
+        v[1] += bi * bi;
+        if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
     }
-    grid_sum_at<4>(v, a.red, seq, g, sh);
-    double rz = v[0], rr = v[1];
-    const double bb = a.scale_vec ? v[3] : v[2];
+    grid_sum<4>(v, part0, g, sh);  // also makes z visible to every block
+    double rr = v[0];
+    const double bb = a.scale_vec ? v[2] : v[1];
     const double thr = a.tol * a.tol * bb;
     int it = 0;
-    while (rr > thr && it < a.max_iter) {
-        g.sync();  // p complete
-        double w[1] = {0.0};
-        for (int64_t i = t0; i < a.n; i += stride) {
-            const double qi = csr_row_dot(a.rp, a.col, a.val, a.p, i);
-            a.q[i] = qi;
-            w[0] += a.p[i] * qi;
-        }
-        grid_sum_at<1>(w, a.red, seq, g, sh);
-        if (!(w[0] > 0.0)) break;  // breakdown (same decision in every block)
-        const double alpha = rz / w[0];
+    if (rr > thr && a.max_iter > 0) {
+        // p = z, q = A z; rz, pq
         double u[2] = {0.0, 0.0};
         for (int64_t i = t0; i < a.n; i += stride) {
-            a.x[i] += alpha * a.p[i];
-            const double ri = a.r[i] - alpha * a.q[i];
-            const double zi = a.dinv[i] * ri;
-            a.r[i] = ri;
-            a.z[i] = zi;
-            u[0] += ri * zi;
-            u[1] += ri * ri;
+            double w = 0.0;
+            const int j1 = __ldg(a.rp + i + 1);
+            for (int j = __ldg(a.rp + i); j < j1; ++j) w += __ldg(a.val + j) * __ldcg(a.z + __ldg(a.col + j));
+            const double zi = a.z[i];
+            a.p[i] = zi;
+            a.q[i] = w;
+            u[0] += a.r[i] * zi;
+            u[1] += zi * w;
         }
-        grid_sum_at<2>(u, a.red, seq, g, sh);
-        const double beta = u[0] / rz;
-        rz = u[0];
-        rr = u[1];
-        for (int64_t i = t0; i < a.n; i += stride) a.p[i] = a.z[i] + beta * a.p[i];
-        ++it;
+        grid_sum<2>(u, part1, g, sh);
+        double rz = u[0], pq = u[1];
+        for (;;) {
+            if (!(pq > 0.0)) break;  // breakdown (same decision in every block)
+            const double alpha = rz / pq;
+            double w2[2] = {0.0, 0.0};  // r.z, r.r
+            for (int64_t i = t0; i < a.n; i += stride) {
+                a.x[i] += alpha * a.p[i];
+                const double ri = a.r[i] - alpha * a.q[i];
+                const double zi = a.dinv[i] * ri;
+                a.r[i] = ri;
+                a.z[i] = zi;
+                w2[0] += ri * zi;
+                w2[1] += ri * ri;
+            }
+            grid_sum<2>(w2, part2, g, sh);
+            ++it;
+            rr = w2[1];
+            if (!(rr > thr) || it >= a.max_iter) break;
+            const double beta = w2[0] / rz;
+            rz = w2[0];
+            double u2[2] = {0.0, 0.0};
+            for (int64_t i = t0; i < a.n; i += stride) {
+                double w = 0.0;
+                const int j1 = __ldg(a.rp + i + 1);
+                for (int j = __ldg(a.rp + i); j < j1; ++j) w += __ldg(a.val + j) * __ldcg(a.z + __ldg(a.col + j));
+                const double pi = a.z[i] + beta * a.p[i];
+                const double qi = w + beta * a.q[i];
+                a.p[i] = pi;
+                a.q[i] = qi;
+                u2[0] += pi * qi;
+            }
+            grid_sum<2>(u2, part1, g, sh);
+            pq = u2[0];
+        }
     }
     if (t0 == 0) {
         a.out[0] = (double)it;
@@ -228,12 +235,15 @@ __device__ __forceinline__ float csr_row_dot32(const int32_t* __restrict__ rp, c
     return s;
 }
 
-__global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
-    __shared__ double sh[4][kBlock / 32];
+    __shared__ double sh[4][kSolverBlock / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int seq = 0, total = 0, outer = 0;
+    double* part0 = a.red;                    // 4 values per block
+    double* part1 = a.red + 4 * gridDim.x;    // 3 values per block
+    double* part2 = a.red + 7 * gridDim.x;    // 2 values per block
+    int total = 0, outer = 0;
     double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
     for (;;) {
         // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
             v[1] += bi * bi;
             if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
         }
-        grid_sum_at<4>(v, a.red, seq, g, sh);
+        grid_sum<4>(v, part0, g, sh);
         rr64 = v[0];
         if (outer == 0) {
             ref2 = a.scale_vec ? v[2] : v[1];
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
             u[1] += (double)(zi * w);
             u[2] += (double)(ri * ri);
         }
-        grid_sum_at<3>(u, a.red, seq, g, sh);
+        grid_sum<3>(u, part1, g, sh);
         double rz = u[0], pq = u[1];
         const double ithr = a.inner_tol * a.inner_tol * u[2];
         for (;;) {
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
                 w2[0] += (double)(ri * zi);
                 w2[1] += (double)(ri * ri);
             }
-            grid_sum_at<2>(w2, a.red, seq, g, sh);
+            grid_sum<2>(w2, part2, g, sh);
             ++total;
             if (!(w2[1] > ithr)) break;
             const float beta = (float)(w2[0] / rz);
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_mixed(MixedArgs a) {
                 a.q[i] = qi;
                 u2[0] += (double)(pi * qi);
             }
-            grid_sum_at<1>(u2, a.red, seq, g, sh);
+            grid_sum<1>(u2, part1, g, sh);
             pq = u2[0];
         }
         for (int64_t i = t0; i < a.n; i += stride) a.x[i] += rnorm * f2d(a.c[i]);
@@ -413,7 +423,11 @@ fp_status up(fem_pic* ctx, T** d, const std::vector<T>& h) {
 fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double tol, const double* scale_vec,
                   int max_iter, int slot, cudaStream_t s) {
     FieldDev* F = ctx->field;
-    if (ctx->solver_fp64 == 0) {
+    int use64 = ctx->solver_fp64;
+    if (ctx->solver_sys[system] >= 0) use64 = ctx->solver_sys[system] == FP_PC_JACOBI_FP64;
+    const int ph = system == FP_SYS_NEWMARK ? PH_CG_NEWMARK : PH_CG_GAUSS;
+    F->last_fp64[slot] = use64;
+    if (!use64) {
         MixedArgs m;
         if (system == FP_SYS_NEWMARK) {
             m.rp = F->e_rp, m.col = F->e_col, m.val = F->Av, m.val32 = F->Av32, m.dinv32 = F->Adinv32, m.n = F->ne;
@@ -422,13 +436,12 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         }
         m.b = rhs, m.x = x, m.r64 = F->q;
         m.r = F->r32, m.z = F->z32, m.p = F->p32, m.q = F->q32, m.c = F->c32, m.red = F->red;
-        m.tol = tol, m.inner_tol = 1e-4, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
+        m.tol = tol, m.inner_tol = ctx->inner_tol, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
         void* args[] = {&m};
-        PhaseTimer pt(ctx, PH_SOLVE, s);
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(F->red, 0, 12 * sizeof(double), s));
+        PhaseTimer pt(ctx, ph, s);
         const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
-        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(grid), dim3(kBlock), args, 0, s));
+        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(grid), dim3(kSolverBlock), args, 0, s));
         return FP_OK;
     }
     PcgArgs a;
@@ -440,10 +453,9 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     a.b = rhs, a.x = x, a.r = F->r, a.z = F->z, a.p = F->p, a.q = F->q, a.red = F->red;
     a.tol = tol, a.scale_vec = scale_vec, a.max_iter = max_iter, a.out = F->out + 4 * slot, a.status = ctx->d_status;
     void* args[] = {&a};
-    PhaseTimer pt(ctx, PH_SOLVE, s);
-    FP_CUDA_TRY(ctx, cudaMemsetAsync(F->red, 0, 12 * sizeof(double), s));
+    PhaseTimer pt(ctx, ph, s);
     const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
-    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(kBlock), args, 0, s));
+    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(kSolverBlock), args, 0, s));
     return FP_OK;
 }
 
@@ -457,7 +469,7 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     info->rel_res = o[2] > 0 ? sqrt(o[1] / o[2]) : sqrt(o[1]);
     info->abs_res = sqrt(o[1]);
     info->ms = ms;
-    info->precond = ctx->solver_fp64 ? FP_PC_JACOBI_FP64 : FP_PC_JACOBI;
+    info->precond = ctx->field->last_fp64[slot] ? FP_PC_JACOBI_FP64 : FP_PC_JACOBI;
     info->fell_back = 0;
     return FP_OK;
 }
@@ -595,8 +607,8 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
     int per_sm = 0;
     if (st == FP_OK) {
         int per_sm2 = 0;
-        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kBlock, 0));
-        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_pcg_mixed, kBlock, 0));
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kSolverBlock, 0));
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_pcg_mixed, kSolverBlock, 0));
         if (per_sm2 < per_sm) per_sm = per_sm2;
     }
     if (st == FP_OK) {
@@ -604,18 +616,31 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
             ctx->err = "fem_pic_field_setup: the solver kernel cannot be co-resident";
             return FP_ECUDA;
         }
-        F->grid = ctx->sm_count * per_sm;
+        F->grid = ctx->sm_count * (per_sm < 2 ? per_sm : 2);  // cheaper grid reductions than a full grid
         auto fit = [&](int64_t rows) {
-            const int64_t need = (rows + kBlock - 1) / kBlock;
+            const int64_t need = (rows + kSolverBlock - 1) / kSolverBlock;
             return (int)(need < F->grid ? (need < 1 ? 1 : need) : F->grid);
         };
         F->grid_e = fit(hc.ne);
         F->grid_n = fit(hc.nn);
-        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 16 * sizeof(double)));
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
     }
     return st;
+}
+
+fp_status fem_pic_field_options(fem_pic_t* ctx, int newmark_solver, int gauss_solver, double inner_tol) {
+    if (!ctx) return FP_EINVAL;
+    auto ok = [](int v) { return v == -1 || v == FP_PC_JACOBI || v == FP_PC_JACOBI_FP64; };
+    if (!ok(newmark_solver) || !ok(gauss_solver) || !(inner_tol > 0.0 && inner_tol < 1.0)) {
+        ctx->err = "fem_pic_field_options: bad solver code or inner tolerance";
+        return FP_EINVAL;
+    }
+    ctx->solver_sys[FP_SYS_NEWMARK] = newmark_solver;
+    ctx->solver_sys[FP_SYS_GAUSS] = gauss_solver;
+    ctx->inner_tol = inner_tol;
+    return FP_OK;
 }
 
 fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* stream) {

@@ -79,7 +79,8 @@ struct FieldDev;
 void field_free(fem_pic* ctx);
 // phases timed by the optional profiler (fem_pic_profile_*)
 enum Phase : int { PH_PREP = 0, PH_FAST = 1, PH_WALK = 2, PH_PUSH64 = 3, PH_CHARGE = 4, PH_SORT = 5,
-                   PH_RESID = 6, PH_SOLVE = 7, PH_COUNT = 16 };
+                   PH_RESID = 6, PH_SOLVE = 7, PH_CG_NEWMARK = 8, PH_CG_GAUSS = 9, PH_LEARNED = 10,
+                   PH_COUNT = 16 };
 struct ProfRec {
     int phase;
     cudaEvent_t a, b;
@@ -91,6 +92,8 @@ struct fem_pic {
     int sm_count = 152;
     fempic::FieldDev* field = nullptr;  // implicit field step (fem_pic_field_setup)
     int solver_fp64 = 0;                // 1: plain FP64 PCG, 0: mixed-precision refinement
+    int solver_sys[2] = {-1, -1};       // per-system override (FP_PC_JACOBI / _FP64), -1 = as requested
+    double inner_tol = 1e-4;            // mixed solver: residual reduction of each FP32 inner solve
     // profiler: events recorded on the launch stream around each kernel when enabled
     bool prof_on = false;
     std::vector<fempic::ProfRec> prof_pending;

@@ -104,6 +104,7 @@ def lib():
             "fem_pic_field_step": (I32, [P, P, P, P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_initial": (I32, [P, P, P, D, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_last_info": (I32, [P, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_field_options": (I32, [P, I32, I32, D]),
             "fem_pic_whitney0_integrals": (I32, [P, P]),
             "fem_pic_profile_enable": (I32, [P, I32]),
             "fem_pic_profile_read": (I32, [P, P, P, I32]),
@@ -387,7 +388,12 @@ def fem_pic_whitney0_integrals(h) -> np.ndarray:
     return a
 
 
-PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_solve")
+PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_other",
+          "cg_newmark", "cg_gauss", "learned")
+
+
+def fem_pic_field_options(h, newmark_solver: int = -1, gauss_solver: int = -1, inner_tol: float = 1e-4):
+    _check(lib().fem_pic_field_options(h, int(newmark_solver), int(gauss_solver), float(inner_tol)), h)
 
 
 def fem_pic_profile_enable(h, on: bool = True):
