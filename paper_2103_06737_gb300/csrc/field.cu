@@ -3,6 +3,7 @@
 // runs as one cooperative kernel (convergence decided on the device, no host round trip).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -23,6 +24,12 @@ struct FieldDev {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr, *tmp = nullptr,
            *delta = nullptr, *qd = nullptr;
     float *Av32 = nullptr, *Adinv32 = nullptr, *Lv32 = nullptr, *Ldinv32 = nullptr;  // FP32 copies
+    // sliced ELLPACK (slices of 32 rows, column-major inside a slice): coalesced loads of the
+    // values and columns of 32 consecutive rows
+    int32_t *se_ptr = nullptr, *se_w = nullptr, *se_col = nullptr, *sn_ptr = nullptr, *sn_w = nullptr,
+            *sn_col = nullptr;
+    double *se_M = nullptr, *se_S = nullptr, *se_A = nullptr, *sn_L = nullptr;
+    float *se_A32 = nullptr, *sn_L32 = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
@@ -40,12 +47,24 @@ constexpr int kSolverBlock = 256;   // cooperative solvers: 256-thread blocks, 2
 __device__ __forceinline__ double as_f64(float x) { return f2d(x); }
 __device__ __forceinline__ double as_f64(double x) { return x; }
 
-__device__ __forceinline__ double csr_row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                              const double* __restrict__ val, const double* __restrict__ x,
-                                              int64_t i) {
-    double s = 0.0;
-    const int j1 = __ldg(rp + i + 1);
-    for (int j = __ldg(rp + i); j < j1; ++j) s += __ldg(val + j) * x[__ldg(col + j)];
+struct Sell {
+    const int32_t* ptr;   // [slices] start of each slice
+    const int32_t* w;     // [slices] width (longest row) of each slice
+    const int32_t* col;   // padded entries point at the row itself with value 0
+};
+
+// row i of a SELL-32 matrix times x; the 32 lanes of a warp take the 32 rows of a slice
+template <typename V, typename X>
+__device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, const X* __restrict__ x,
+                                      int64_t i) {
+    const int64_t sl = i >> 5;
+    const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+    const int w = __ldg(S.w + sl);
+    X s = X(0);
+    for (int j = 0; j < w; ++j) {
+        const int64_t k = base + 32 * (int64_t)j;
+        s += (X)__ldg(val + k) * __ldcg(x + __ldg(S.col + k));
+    }
     return s;
 }
 
@@ -93,8 +112,7 @@ __device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_gr
 }
 
 struct PcgArgs {
-    const int32_t* rp;
-    const int32_t* col;
+    Sell S;
     const double* val;
     const double* dinv;
     int64_t n;
@@ -124,10 +142,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.r, b.b, s.s
     for (int64_t i = t0; i < a.n; i += stride) {
         const double bi = a.b[i];
-        double ax = 0.0;
-        const int j1 = __ldg(a.rp + i + 1);
-        for (int j = __ldg(a.rp + i); j < j1; ++j) ax += __ldg(a.val + j) * __ldcg(a.x + __ldg(a.col + j));
-        const double ri = bi - ax;
+        const double ri = bi - sell_row<double, double>(a.S, a.val, a.x, i);
         a.r[i] = ri;
         a.z[i] = a.dinv[i] * ri;
         v[0] += ri * ri;
@@ -143,9 +158,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
         // p = z, q = A z; rz, pq
         double u[2] = {0.0, 0.0};
         for (int64_t i = t0; i < a.n; i += stride) {
-            double w = 0.0;
-            const int j1 = __ldg(a.rp + i + 1);
-            for (int j = __ldg(a.rp + i); j < j1; ++j) w += __ldg(a.val + j) * __ldcg(a.z + __ldg(a.col + j));
+            const double w = sell_row<double, double>(a.S, a.val, a.z, i);
             const double zi = a.z[i];
             a.p[i] = zi;
             a.q[i] = w;
@@ -175,9 +188,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
             rz = w2[0];
             double u2[2] = {0.0, 0.0};
             for (int64_t i = t0; i < a.n; i += stride) {
-                double w = 0.0;
-                const int j1 = __ldg(a.rp + i + 1);
-                for (int j = __ldg(a.rp + i); j < j1; ++j) w += __ldg(a.val + j) * __ldcg(a.z + __ldg(a.col + j));
+                const double w = sell_row<double, double>(a.S, a.val, a.z, i);
                 const double pi = a.z[i] + beta * a.p[i];
                 const double qi = w + beta * a.q[i];
                 a.p[i] = pi;
@@ -206,8 +217,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
 // as q = A z + beta q).
 
 struct MixedArgs {
-    const int32_t* rp;
-    const int32_t* col;
+    Sell S;
     const double* val;     // FP64 operator (outer residual)
     const float* val32;    // FP32 copy (inner solves)
     const float* dinv32;
@@ -226,15 +236,6 @@ struct MixedArgs {
     int32_t* status;
 };
 
-__device__ __forceinline__ float csr_row_dot32(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                               const float* __restrict__ val, const float* __restrict__ x,
-                                               int64_t i) {
-    float s = 0.f;
-    const int j1 = __ldg(rp + i + 1);
-    for (int j = __ldg(rp + i); j < j1; ++j) s += __ldg(val + j) * __ldcg(x + __ldg(col + j));
-    return s;
-}
-
 __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
     __shared__ double sh[4][kSolverBlock / 32];
@@ -250,10 +251,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         for (int64_t i = t0; i < a.n; i += stride) {
             const double bi = a.b[i];
-            double ax = 0.0;
-            const int j1 = __ldg(a.rp + i + 1);
-            for (int j = __ldg(a.rp + i); j < j1; ++j) ax += __ldg(a.val + j) * __ldcg(a.x + __ldg(a.col + j));
-            const double ri = bi - ax;
+            const double ri = bi - sell_row<double, double>(a.S, a.val, a.x, i);
             a.r64[i] = ri;
             a.c[i] = 0.f;
             v[0] += ri * ri;
@@ -278,7 +276,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
         g.sync();
         double u[3] = {0.0, 0.0, 0.0};  // r.z, p.q, r.r
         for (int64_t i = t0; i < a.n; i += stride) {
-            const float w = csr_row_dot32(a.rp, a.col, a.val32, a.z, i);
+            const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
             const float zi = a.z[i], ri = a.r[i];
             a.p[i] = zi;
             a.q[i] = w;
@@ -309,7 +307,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
             rz = w2[0];
             double u2[1] = {0.0};
             for (int64_t i = t0; i < a.n; i += stride) {
-                const float w = csr_row_dot32(a.rp, a.col, a.val32, a.z, i);
+                const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
                 const float pi = a.z[i] + beta * a.p[i];
                 const float qi = w + beta * a.q[i];
                 a.p[i] = pi;
@@ -333,25 +331,27 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
 
 // Newmark right-hand side and the extrapolated initial guess 2E^n - E^{n-1}
 template <typename Real>
-__global__ void k_newmark_rhs(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const double* __restrict__ Mv, const double* __restrict__ Sv,
+__global__ void k_newmark_rhs(Sell Sl, const double* __restrict__ Mv, const double* __restrict__ Sv,
                               const uint8_t* __restrict__ fixed, const double* __restrict__ En,
                               const double* __restrict__ Em, const Real* __restrict__ dGh,
                               const Real* __restrict__ dGp, double dt2, int64_t n, double* __restrict__ rhs,
                               double* __restrict__ x0) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t sl = i >> 5;
+        const int64_t base = __ldg(Sl.ptr + sl) + (i & 31);
+        const int w = __ldg(Sl.w + sl);
+        double s = 0.0;
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = base + 32 * (int64_t)j;
+            const int c = __ldg(Sl.col + k);
+            const double en = En[c], em = Em[c];
+            s += __ldg(Mv + k) * (2.0 * en - em) - dt2 * __ldg(Sv + k) * (0.5 * en + 0.25 * em);
+        }
         if (fixed[i]) {
             rhs[i] = 0.0;
             x0[i] = 0.0;
             continue;
-        }
-        double s = 0.0;
-        const int j1 = rp[i + 1];
-        for (int j = rp[i]; j < j1; ++j) {
-            const int c = col[j];
-            const double en = En[c], em = Em[c];
-            s += Mv[j] * (2.0 * en - em) - dt2 * Sv[j] * (0.5 * en + 0.25 * em);
         }
         const double gh = dGh ? as_f64(dGh[i]) : 0.0, gp = dGp ? as_f64(dGp[i]) : 0.0;
         rhs[i] = s - (gh - gp);
@@ -359,12 +359,11 @@ __global__ void k_newmark_rhs(const int32_t* __restrict__ rp, const int32_t* __r
     }
 }
 
-__global__ void k_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                       const double* __restrict__ val, const double* __restrict__ x, int64_t n,
+__global__ void k_spmv(Sell Sl, const double* __restrict__ val, const double* __restrict__ x, int64_t n,
                        double* __restrict__ y) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        y[i] = csr_row_dot(rp, col, val, x, i);
+        y[i] = sell_row<double, double>(Sl, val, x, i);
 }
 
 // g_n = (D0^T [*eps] E)_n + Q_n on free nodes (ME = [*eps] E), 0 on PEC nodes
@@ -430,9 +429,11 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     if (!use64) {
         MixedArgs m;
         if (system == FP_SYS_NEWMARK) {
-            m.rp = F->e_rp, m.col = F->e_col, m.val = F->Av, m.val32 = F->Av32, m.dinv32 = F->Adinv32, m.n = F->ne;
+            m.S = Sell{F->se_ptr, F->se_w, F->se_col}, m.val = F->se_A, m.val32 = F->se_A32, m.dinv32 = F->Adinv32,
+            m.n = F->ne;
         } else {
-            m.rp = F->n_rp, m.col = F->n_col, m.val = F->Lv, m.val32 = F->Lv32, m.dinv32 = F->Ldinv32, m.n = F->nn;
+            m.S = Sell{F->sn_ptr, F->sn_w, F->sn_col}, m.val = F->sn_L, m.val32 = F->sn_L32, m.dinv32 = F->Ldinv32,
+            m.n = F->nn;
         }
         m.b = rhs, m.x = x, m.r64 = F->q;
         m.r = F->r32, m.z = F->z32, m.p = F->p32, m.q = F->q32, m.c = F->c32, m.red = F->red;
@@ -446,9 +447,9 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     }
     PcgArgs a;
     if (system == FP_SYS_NEWMARK) {
-        a.rp = F->e_rp, a.col = F->e_col, a.val = F->Av, a.dinv = F->Adinv, a.n = F->ne;
+        a.S = Sell{F->se_ptr, F->se_w, F->se_col}, a.val = F->se_A, a.dinv = F->Adinv, a.n = F->ne;
     } else {
-        a.rp = F->n_rp, a.col = F->n_col, a.val = F->Lv, a.dinv = F->Ldinv, a.n = F->nn;
+        a.S = Sell{F->sn_ptr, F->sn_w, F->sn_col}, a.val = F->sn_L, a.dinv = F->Ldinv, a.n = F->nn;
     }
     a.b = rhs, a.x = x, a.r = F->r, a.z = F->z, a.p = F->p, a.q = F->q, a.red = F->red;
     a.tol = tol, a.scale_vec = scale_vec, a.max_iter = max_iter, a.out = F->out + 4 * slot, a.status = ctx->d_status;
@@ -483,12 +484,14 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
         if (f32)
-            k_newmark_rhs<float><<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, F->Sv, F->edge_fixed, E_cur, E_prev,
+            k_newmark_rhs<float><<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, F->se_S,
+                                                       F->edge_fixed, E_cur, E_prev,
                                                        (const float*)dG_half, (const float*)dG_prev, F->dt * F->dt,
                                                        F->ne, F->rhs, E_next);
         else
-            k_newmark_rhs<double><<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, F->Sv, F->edge_fixed, E_cur,
-                                                        E_prev, (const double*)dG_half, (const double*)dG_prev,
+            k_newmark_rhs<double><<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, F->se_S,
+                                                        F->edge_fixed, E_cur, E_prev, (const double*)dG_half,
+                                                        (const double*)dG_prev,
                                                         F->dt * F->dt, F->ne, F->rhs, E_next);
         FP_CUDA_TRY(ctx, cudaGetLastError());
     }
@@ -498,7 +501,7 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
     // Gauss-law projection: L d = D0^T M E^N + Q on interior nodes, to ||r|| <= tol ||Q||
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
-        k_spmv<<<ge, kBlock, 0, s>>>(F->e_rp, F->e_col, F->Mv, E_next, F->ne, F->tmp);
+        k_spmv<<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, E_next, F->ne, F->tmp);
         if (f32)
             k_gauss_rhs<float><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
                                                      F->tmp, (const float*)Q_new, F->nn, F->rhs, F->qd);
@@ -529,7 +532,8 @@ void field_free(fem_pic* ctx) {
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
-                    F->z32, F->p32, F->q32, F->c32};
+                    F->z32, F->p32, F->q32, F->c32, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
+                    F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete F;
@@ -595,6 +599,66 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         if (st == FP_OK) st = up(ctx, &F->Adinv32, ad32);
         if (st == FP_OK) st = up(ctx, &F->Lv32, l32);
         if (st == FP_OK) st = up(ctx, &F->Ldinv32, ld32);
+    }
+    {
+        // SELL-32 copies of the operators (the CSR stays on the host for export)
+        auto sell = [](const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int64_t n,
+                       std::vector<int32_t>* ptr, std::vector<int32_t>* w, std::vector<int32_t>* scol,
+                       std::vector<int64_t>* map) {
+            const int64_t ns = (n + 31) / 32;
+            ptr->assign(ns, 0);
+            w->assign(ns, 0);
+            int64_t off = 0;
+            for (int64_t sl = 0; sl < ns; ++sl) {
+                int wmax = 0;
+                for (int64_t r = 32 * sl; r < 32 * sl + 32 && r < n; ++r) wmax = std::max(wmax, rp[r + 1] - rp[r]);
+                (*ptr)[sl] = (int32_t)off;
+                (*w)[sl] = wmax;
+                off += 32 * (int64_t)wmax;
+            }
+            scol->assign(off, 0);
+            map->assign(off, -1);
+            for (int64_t sl = 0; sl < ns; ++sl)
+                for (int64_t lane = 0; lane < 32; ++lane) {
+                    const int64_t r = 32 * sl + lane;
+                    const int64_t base = (*ptr)[sl] + lane;
+                    for (int j = 0; j < (*w)[sl]; ++j) {
+                        const int64_t k = base + 32 * (int64_t)j;
+                        if (r < n && j < rp[r + 1] - rp[r]) {
+                            (*scol)[k] = col[rp[r] + j];
+                            (*map)[k] = rp[r] + j;
+                        } else {
+                            (*scol)[k] = (int32_t)(r < n ? r : 0);  // padding: zero value
+                        }
+                    }
+                }
+        };
+        auto gather = [](const std::vector<int64_t>& map, const std::vector<double>& v) {
+            std::vector<double> o(map.size(), 0.0);
+            for (size_t k = 0; k < map.size(); ++k)
+                if (map[k] >= 0) o[k] = v[map[k]];
+            return o;
+        };
+        std::vector<int32_t> ptr, w, scol;
+        std::vector<int64_t> map;
+        sell(H.e_rp, H.e_col, hc.ne, &ptr, &w, &scol, &map);
+        std::vector<double> sM = gather(map, H.M), sS = gather(map, H.S), sA = gather(map, A);
+        std::vector<float> sA32(sA.begin(), sA.end());
+        if (st == FP_OK) st = up(ctx, &F->se_ptr, ptr);
+        if (st == FP_OK) st = up(ctx, &F->se_w, w);
+        if (st == FP_OK) st = up(ctx, &F->se_col, scol);
+        if (st == FP_OK) st = up(ctx, &F->se_M, sM);
+        if (st == FP_OK) st = up(ctx, &F->se_S, sS);
+        if (st == FP_OK) st = up(ctx, &F->se_A, sA);
+        if (st == FP_OK) st = up(ctx, &F->se_A32, sA32);
+        sell(H.n_rp, H.n_col, hc.nn, &ptr, &w, &scol, &map);
+        std::vector<double> sL = gather(map, H.L);
+        std::vector<float> sL32(sL.begin(), sL.end());
+        if (st == FP_OK) st = up(ctx, &F->sn_ptr, ptr);
+        if (st == FP_OK) st = up(ctx, &F->sn_w, w);
+        if (st == FP_OK) st = up(ctx, &F->sn_col, scol);
+        if (st == FP_OK) st = up(ctx, &F->sn_L, sL);
+        if (st == FP_OK) st = up(ctx, &F->sn_L32, sL32);
     }
     const int64_t nmax = hc.ne > hc.nn ? hc.ne : hc.nn;
     float** vecs32[] = {&F->r32, &F->z32, &F->p32, &F->q32, &F->c32};
