@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=2000)
-    ap.add_argument("--solver", default="mixed,fp64",
+    ap.add_argument("--solver", default="fp64,fp64",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
