@@ -305,6 +305,50 @@ fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* s
  */
 fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha);
 
+/* ------------------------------------------------------------------ learned correction
+ * Not in the paper (it defers its solver details).  A message-passing network on the edge
+ * graph (graph nodes: edge DOFs; graph edges: nonzeros of A), 3 layers of 64 features,
+ * BF16 weights with FP32 accumulation (tensor-core GEMMs), maps the Jacobi-scaled residual
+ * of the Newmark guess 2E^n - E^{n-1} to a correction.  With precond = FP_PC_LEARNED in
+ * fem_pic_field_step the corrected guess is used only when its residual is smaller than
+ * the plain guess's (else fell_back = 1 in info[0]); the Newmark CG then runs to the same
+ * tolerance either way.  The Gauss-law solve is not affected.  Requires
+ * fem_pic_field_setup; a new setup discards the network. */
+
+/* Allocate and initialise the network (seeded) and a store for sample_capacity training
+ * residuals.  Synchronous. */
+fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity);
+
+/* collect != 0: every fem_pic_field_step stores the residual of its plain Newmark guess
+ * (ring buffer; eager launches only: a captured graph would replay one slot).
+ * active != 0: use the network in fem_pic_field_solve-independent steps as with
+ * FP_PC_LEARNED. */
+fp_status fem_pic_learned_mode(fem_pic_t* ctx, int collect, int active);
+
+/* Number of stored samples. */
+fp_status fem_pic_learned_samples(fem_pic_t* ctx, int* count);
+
+/* Train on stored samples [first, first+count) for `epochs` passes (Adam, cosine-decayed
+ * learning rate lr, shuffled with seed).  loss (host [epochs], may be NULL): mean
+ * ||A~ c~ - r~||^2 / ||r~||^2 per epoch.  Synchronous per epoch. */
+fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs, double lr, uint64_t seed,
+                                double* loss, void* stream);
+
+/* ratio[k] = ||A~ c~ - r~||^2 / ||r~||^2 of stored sample first+k (held-out evaluation). */
+fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* ratio, void* stream);
+
+/* Parameters (FP32 master copy): get and/or set host arrays of *n_params floats. */
+fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params);
+
+/* Forward pass on one residual r (device double [N_e]): writes c~ and r~ (device float [N_e]). */
+fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out,
+                                  void* stream);
+
+/* Loss gradient for one residual r (device float [N_e]) into grad_out (host float
+ * [n_params]); the weights and optimizer state are left unchanged.  Synchronous. */
+fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_out, double* loss,
+                                   void* stream);
+
 /*
  * Optional per-phase timing (not part of the method).  When enabled, the library
  * records a pair of CUDA events on the launch stream around each of its kernels,

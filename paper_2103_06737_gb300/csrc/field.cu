@@ -13,30 +13,6 @@ namespace cg = cooperative_groups;
 
 namespace fempic {
 
-struct FieldDev {
-    double dt = 0, eps = 0, mu = 0;
-    int64_t ne = 0, nn = 0, nf = 0;
-    HostFields host;
-    int32_t *e_rp = nullptr, *e_col = nullptr, *n_rp = nullptr, *n_col = nullptr;
-    double *Mv = nullptr, *Sv = nullptr, *Av = nullptr, *Adinv = nullptr, *Lv = nullptr, *Ldinv = nullptr;
-    uint8_t *edge_fixed = nullptr, *node_fixed = nullptr;
-    int32_t* face_edges = nullptr;  // [3 nf]: (i,j), (j,k), (i,k) of face (i<j<k)
-    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr, *tmp = nullptr,
-           *delta = nullptr, *qd = nullptr;
-    float *Av32 = nullptr, *Adinv32 = nullptr, *Lv32 = nullptr, *Ldinv32 = nullptr;  // FP32 copies
-    // sliced ELLPACK (slices of 32 rows, column-major inside a slice): coalesced loads of the
-    // values and columns of 32 consecutive rows
-    int32_t *se_ptr = nullptr, *se_w = nullptr, *se_col = nullptr, *sn_ptr = nullptr, *sn_w = nullptr,
-            *sn_col = nullptr;
-    double *se_M = nullptr, *se_S = nullptr, *se_A = nullptr, *sn_L = nullptr;
-    float *se_A32 = nullptr, *sn_L32 = nullptr;
-    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
-    double* red = nullptr;          // reduction partials
-    double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
-    int grid = 0;                   // co-resident blocks (cooperative launch limit)
-    int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
-    int last_fp64[2] = {0, 0};      // solver used by the last solve in each info slot
-};
 
 namespace {
 
@@ -46,27 +22,6 @@ constexpr int kSolverBlock = 256;   // cooperative solvers: 256-thread blocks, 2
 
 __device__ __forceinline__ double as_f64(float x) { return f2d(x); }
 __device__ __forceinline__ double as_f64(double x) { return x; }
-
-struct Sell {
-    const int32_t* ptr;   // [slices] start of each slice
-    const int32_t* w;     // [slices] width (longest row) of each slice
-    const int32_t* col;   // padded entries point at the row itself with value 0
-};
-
-// row i of a SELL-32 matrix times x; the 32 lanes of a warp take the 32 rows of a slice
-template <typename V, typename X>
-__device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, const X* __restrict__ x,
-                                      int64_t i) {
-    const int64_t sl = i >> 5;
-    const int64_t base = __ldg(S.ptr + sl) + (i & 31);
-    const int w = __ldg(S.w + sl);
-    X s = X(0);
-    for (int j = 0; j < w; ++j) {
-        const int64_t k = base + 32 * (int64_t)j;
-        s += (X)__ldg(val + k) * __ldcg(x + __ldg(S.col + k));
-    }
-    return s;
-}
 
 // sum of NV values over the block, result valid in every thread
 template <int NV>
@@ -472,6 +427,13 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     info->ms = ms;
     info->precond = ctx->field->last_fp64[slot] ? FP_PC_JACOBI_FP64 : FP_PC_JACOBI;
     info->fell_back = 0;
+    if (slot == 0 && ctx->field->learned_used) {
+        int fl = 0;
+        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&fl, learned_flag(ctx->field), sizeof(int), cudaMemcpyDeviceToHost, s));
+        FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        info->precond = FP_PC_LEARNED;
+        info->fell_back = fl;
+    }
     return FP_OK;
 }
 
@@ -494,6 +456,11 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
                                                         (const double*)dG_prev,
                                                         F->dt * F->dt, F->ne, F->rhs, E_next);
         FP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    // learned correction of the guess (with fallback), and/or collection of its residual
+    if (learned_active(F)) {
+        fp_status sl = learned_newmark_guess(ctx, F->rhs, E_next, s);
+        if (sl != FP_OK) return sl;
     }
     // Newmark solve for E^N from the guess 2E^n - E^{n-1} (written into E_next above)
     fp_status st = run_pcg(ctx, FP_SYS_NEWMARK, F->rhs, E_next, tol, nullptr, max_iter, 0, s);
@@ -529,6 +496,7 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
 void field_free(fem_pic* ctx) {
     FieldDev* F = ctx->field;
     if (!F) return;
+    learned_free(F);
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
@@ -790,11 +758,18 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
                              double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                              int max_iter, int precond, fp_solve_info info[2], void* stream) {
     if (!ctx || !ctx->field || !E_prev || !E_cur || !E_next || !Q_new || !(tol > 0.0) || max_iter < 0 ||
-        (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64) || E_next == E_cur || E_next == E_prev) {
+        (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64 && precond != FP_PC_LEARNED) ||
+        E_next == E_cur || E_next == E_prev) {
         if (ctx) ctx->err = "fem_pic_field_step: bad argument (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
+    if (precond == FP_PC_LEARNED && !ctx->field->learned) {
+        ctx->err = "fem_pic_field_step: FP_PC_LEARNED needs fem_pic_learned_init";
+        return FP_EINVAL;
+    }
     ctx->solver_fp64 = precond == FP_PC_JACOBI_FP64;
+    learned_set_active(ctx->field, precond == FP_PC_LEARNED);
+    ctx->field->learned_used = precond == FP_PC_LEARNED;
     cudaStream_t s = (cudaStream_t)stream;
     fp_status st = field_step_impl(ctx, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol, max_iter, s);
     if (st != FP_OK || !info) return st;

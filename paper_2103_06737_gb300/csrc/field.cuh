@@ -15,4 +15,64 @@ struct HostFields {
 
 void assemble_fields(const HostComplex& hc, double eps, double mu, HostFields* hf);
 
+struct LearnedDev;  // learned correction (learned.cu)
+
+struct FieldDev {
+    double dt = 0, eps = 0, mu = 0;
+    int64_t ne = 0, nn = 0, nf = 0;
+    HostFields host;
+    int32_t *e_rp = nullptr, *e_col = nullptr, *n_rp = nullptr, *n_col = nullptr;
+    double *Mv = nullptr, *Sv = nullptr, *Av = nullptr, *Adinv = nullptr, *Lv = nullptr, *Ldinv = nullptr;
+    uint8_t *edge_fixed = nullptr, *node_fixed = nullptr;
+    int32_t* face_edges = nullptr;  // [3 nf]: (i,j), (j,k), (i,k) of face (i<j<k)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhs = nullptr, *tmp = nullptr,
+           *delta = nullptr, *qd = nullptr;
+    float *Av32 = nullptr, *Adinv32 = nullptr, *Lv32 = nullptr, *Ldinv32 = nullptr;  // FP32 copies
+    // sliced ELLPACK (slices of 32 rows, column-major inside a slice): coalesced loads of the
+    // values and columns of 32 consecutive rows
+    int32_t *se_ptr = nullptr, *se_w = nullptr, *se_col = nullptr, *sn_ptr = nullptr, *sn_w = nullptr,
+            *sn_col = nullptr;
+    double *se_M = nullptr, *se_S = nullptr, *se_A = nullptr, *sn_L = nullptr;
+    float *se_A32 = nullptr, *sn_L32 = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
+    double* red = nullptr;          // reduction partials
+    double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
+    int grid = 0;                   // co-resident blocks (cooperative launch limit)
+    int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
+    int last_fp64[2] = {0, 0};      // solver used by the last solve in each info slot
+    LearnedDev* learned = nullptr;
+    bool learned_used = false;      // the last field step applied the learned guess
+};
+
+#ifdef __CUDACC__
+struct Sell {
+    const int32_t* ptr;   // [slices] start of each slice
+    const int32_t* w;     // [slices] width (longest row) of each slice
+    const int32_t* col;   // padded entries point at the row itself with value 0
+};
+
+// row i of a SELL-32 matrix times x; the 32 lanes of a warp take the 32 rows of a slice
+template <typename V, typename X>
+__device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, const X* __restrict__ x,
+                                      int64_t i) {
+    const int64_t sl = i >> 5;
+    const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+    const int w = __ldg(S.w + sl);
+    X s = X(0);
+    for (int j = 0; j < w; ++j) {
+        const int64_t k = base + 32 * (int64_t)j;
+        s += (X)__ldg(val + k) * __ldcg(x + __ldg(S.col + k));
+    }
+    return s;
+}
+
+#endif
+
+// learned correction hooks (learned.cu)
+void learned_free(FieldDev* F);
+fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cudaStream_t s);
+bool learned_active(const FieldDev* F);
+int* learned_flag(FieldDev* F);
+void learned_set_active(FieldDev* F, bool on);
+
 }  // namespace fempic

@@ -1,0 +1,814 @@
+// Learned correction of the Newmark field solve's starting point (not in the paper; the
+// paper defers its solver to Newmark-beta and gives no preconditioner).
+//
+// A message-passing network on the edge graph (graph nodes: edge DOFs; graph edges: the
+// nonzeros of A = M + dt^2/4 S) maps the Jacobi-scaled residual of the extrapolated guess,
+// r~ = D^-1/2 (b - A x0) / s  (s = RMS over free rows), to a correction c~ with
+// A~ c~ ~ r~, A~ = D^-1/2 A D^-1/2; the guess becomes x0 + s D^-1/2 c~ when that lowers the
+// residual, otherwise it stays x0 (fallback).  CG to the same tolerance follows either way.
+//   h0 = relu(r~ w_e + b_e)                              (64 features)
+//   h_l = relu([h_{l-1} | A~ h_{l-1}] W_l + b_l)         l = 1..3, W_l 128 x 64
+//   c~ = r~ + h3 . w_h + b_h                              (identity = one Jacobi step)
+// Weights and activations are BF16, products accumulate in FP32 on the tensor cores
+// (mma.sync m16n8k16); the neighbour sums and the rest are FP32.  Training minimises
+// ||A~ c~ - r~||^2 / ||r~||^2 on residuals the method itself produces, with Adam on FP32
+// master weights.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "field.cuh"
+
+namespace fempic {
+
+namespace {
+
+constexpr int kH = 64;        // hidden width
+constexpr int kK = 128;       // [h | m]
+constexpr int kLayers = 3;
+constexpr int kWsz = kK * kH;  // one layer's weights
+// parameter layout (FP32 master copy)
+constexpr int kOffWe = 0, kOffBe = 64, kOffW0 = 128;
+constexpr int kLayerStride = kWsz + kH;
+constexpr int kOffWh = kOffW0 + kLayers * kLayerStride, kOffBh = kOffWh + kH;
+constexpr int kNParams = kOffBh + 1;
+constexpr unsigned kFull = 0xffffffffu;
+
+}  // namespace
+
+struct LearnedDev {
+    int64_t n = 0, n_free = 0;
+    float* a_sell = nullptr;      // A~ values in the SELL layout of A
+    float* dis = nullptr;         // D^-1/2
+    float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+    __nv_bfloat16* Wt[kLayers] = {nullptr, nullptr, nullptr};  // [64 out][128 in]
+    __nv_bfloat16* Wn[kLayers] = {nullptr, nullptr, nullptr};  // [128 in][64 out]
+    __nv_bfloat16* h[kLayers + 1] = {nullptr, nullptr, nullptr, nullptr};
+    __nv_bfloat16* m[kLayers] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16* dz = nullptr;
+    float *dh = nullptr, *dhd = nullptr, *dm = nullptr;
+    float *rt = nullptr, *ct = nullptr, *e = nullptr, *dct = nullptr;
+    float* scal = nullptr;        // [0] sum of scaled r^2, [1] loss sum, [2] rr0, [3] rr1, [4] s
+    int* flag = nullptr;          // 1: the learned guess was rejected (fallback)
+    double *r0 = nullptr, *y = nullptr;
+    float* samples = nullptr;
+    int cap = 0, count = 0, next = 0;
+    int collecting = 0, active = 0, adam_t = 0;
+};
+
+namespace {
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {  // two consecutive bf16
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// ---- scaled residual and its RMS: scal[0] += sum (D^-1/2 r)^2 over free rows
+template <typename R>
+__global__ void k_lm_sumsq(const R* __restrict__ r, const float* __restrict__ dis, const uint8_t* __restrict__ fixed,
+                           int64_t n, float* scal) {
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!fixed[i]) {
+            const float v = (float)r[i] * dis[i];
+            acc += v * v;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(scal, acc);
+}
+
+// r~ and h0 = relu(r~ w_e + b_e); thread per (row, feature pair)
+template <typename R>
+__global__ void k_lm_input(const R* __restrict__ r, const float* __restrict__ dis, const uint8_t* __restrict__ fixed,
+                           int64_t n, float n_free, const float* __restrict__ scal, const float* __restrict__ P,
+                           float* __restrict__ rt, __nv_bfloat16* __restrict__ h0, float* s_out) {
+    const float s = sqrtf(fmaxf(scal[0], 1e-30f) / n_free), inv = 1.f / s;
+    const int64_t total = n * (kH / 2);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / (kH / 2);
+        const int f = 2 * (int)(t % (kH / 2));
+        const float x = fixed[i] ? 0.f : (float)r[i] * dis[i] * inv;
+        if (f == 0) rt[i] = x;
+        const float v0 = fmaxf(x * P[kOffWe + f] + P[kOffBe + f], 0.f);
+        const float v1 = fmaxf(x * P[kOffWe + f + 1] + P[kOffBe + f + 1], 0.f);
+        reinterpret_cast<__nv_bfloat162*>(h0)[t] = __floats2bfloat162_rn(v0, v1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s_out) *s_out = s;
+}
+
+// M = A~ H (BF16 features), warp per row, two features per lane
+__global__ void k_lm_aggregate(Sell S, const float* __restrict__ a, const __nv_bfloat16* __restrict__ H, int64_t n,
+                               __nv_bfloat16* __restrict__ M) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int64_t sl = i >> 5;
+        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+        const int w = __ldg(S.w + sl);
+        float s0 = 0.f, s1 = 0.f;
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = base + 32 * (int64_t)j;
+            const int c = __ldg(S.col + k);
+            const float av = __ldg(a + k);
+            const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(H + (int64_t)c * kH)[lane];
+            s0 += av * __low2float(v);
+            s1 += av * __high2float(v);
+        }
+        reinterpret_cast<__nv_bfloat162*>(M + i * kH)[lane] = __floats2bfloat162_rn(s0, s1);
+    }
+}
+
+// dh = dhd + A~ dm (FP32 features), warp per row
+__global__ void k_lm_aggregate_f32(Sell S, const float* __restrict__ a, const float* __restrict__ dm,
+                                   const float* __restrict__ dhd, int64_t n, float* __restrict__ dh) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int64_t sl = i >> 5;
+        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+        const int w = __ldg(S.w + sl);
+        float2 acc = reinterpret_cast<const float2*>(dhd + i * kH)[lane];
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = base + 32 * (int64_t)j;
+            const int c = __ldg(S.col + k);
+            const float av = __ldg(a + k);
+            const float2 v = reinterpret_cast<const float2*>(dm + (int64_t)c * kH)[lane];
+            acc.x += av * v.x;
+            acc.y += av * v.y;
+        }
+        reinterpret_cast<float2*>(dh + i * kH)[lane] = acc;
+    }
+}
+
+// Hout = relu([Hin | M] W + b): a warp computes 16 rows x 64 outputs, K = 128
+__global__ void __launch_bounds__(128) k_lm_gemm_fwd(const __nv_bfloat16* __restrict__ Hin,
+                                                     const __nv_bfloat16* __restrict__ M,
+                                                     const __nv_bfloat16* __restrict__ Wt,
+                                                     const float* __restrict__ bias, int64_t n,
+                                                     __nv_bfloat16* __restrict__ Hout) {
+    __shared__ __align__(16) __nv_bfloat16 sW[kH * kK];  // [out][in]
+    for (int t = threadIdx.x; t < kH * kK / 8; t += blockDim.x)
+        reinterpret_cast<uint4*>(sW)[t] = reinterpret_cast<const uint4*>(Wt)[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+    const int64_t tiles = (n + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
+         tile += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        const bool ok0 = r0 < n, ok1 = r1 < n;
+        float c[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kK / 16; ++kk) {
+            const __nv_bfloat16* src = kk < 4 ? Hin : M;
+            const int kc = (kk & 3) * 16 + tg * 2;
+            uint32_t af[4];
+            af[0] = ok0 ? ld_pair(src + r0 * kH + kc) : 0u;
+            af[1] = ok1 ? ld_pair(src + r1 * kH + kc) : 0u;
+            af[2] = ok0 ? ld_pair(src + r0 * kH + kc + 8) : 0u;
+            af[3] = ok1 ? ld_pair(src + r1 * kH + kc + 8) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const __nv_bfloat16* wcol = sW + (nt * 8 + g) * kK + kk * 16 + tg * 2;
+                uint32_t bfr[2] = {ld_pair(wcol), ld_pair(wcol + 8)};
+                mma16816(c[nt], af, bfr);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + tg * 2;
+            const float b0 = bias[col], b1 = bias[col + 1];
+            if (ok0)
+                *reinterpret_cast<__nv_bfloat162*>(Hout + r0 * kH + col) =
+                    __floats2bfloat162_rn(fmaxf(c[nt][0] + b0, 0.f), fmaxf(c[nt][1] + b1, 0.f));
+            if (ok1)
+                *reinterpret_cast<__nv_bfloat162*>(Hout + r1 * kH + col) =
+                    __floats2bfloat162_rn(fmaxf(c[nt][2] + b0, 0.f), fmaxf(c[nt][3] + b1, 0.f));
+        }
+    }
+}
+
+// c~ = r~ + h3 . w_h + b_h (0 on PEC rows); warp per row
+__global__ void k_lm_head(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ P,
+                          const float* __restrict__ rt, const uint8_t* __restrict__ fixed, int64_t n,
+                          float* __restrict__ ct) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(H3 + i * kH)[lane];
+        float s = __low2float(v) * P[kOffWh + 2 * lane] + __high2float(v) * P[kOffWh + 2 * lane + 1];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) ct[i] = fixed[i] ? 0.f : rt[i] + s + P[kOffBh];
+    }
+}
+
+// y = A~ x (- sub); optional sum of squares into acc (FP32 SELL, thread per row)
+__global__ void k_lm_spmv(Sell S, const float* __restrict__ a, const float* __restrict__ x,
+                          const float* __restrict__ sub, const uint8_t* __restrict__ fixed, float scale, int64_t n,
+                          float* __restrict__ y, float* acc) {
+    float ss = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = i >> 5;
+        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+        const int w = __ldg(S.w + sl);
+        float s = 0.f;
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = base + 32 * (int64_t)j;
+            s += __ldg(a + k) * x[__ldg(S.col + k)];
+        }
+        if (sub) s -= sub[i];
+        s = fixed[i] ? 0.f : scale * s;
+        y[i] = s;
+        ss += s * s;
+    }
+    if (acc) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(acc, ss);
+    }
+}
+
+// head backward: dh = dct (x) w_h;  grads of w_h, b_h
+__global__ void k_lm_head_bwd(const float* __restrict__ dct, const __nv_bfloat16* __restrict__ H3,
+                              const float* __restrict__ P, int64_t n, float* __restrict__ dh,
+                              float* __restrict__ G) {
+    __shared__ float sg[kH + 1];
+    for (int t = threadIdx.x; t < kH + 1; t += blockDim.x) sg[t] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float gw0 = 0.f, gw1 = 0.f, gb = 0.f;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const float d = dct[i];
+        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(H3 + i * kH)[lane];
+        reinterpret_cast<float2*>(dh + i * kH)[lane] = make_float2(d * P[kOffWh + 2 * lane], d * P[kOffWh + 2 * lane + 1]);
+        gw0 += d * __low2float(v);
+        gw1 += d * __high2float(v);
+        gb += lane == 0 ? d : 0.f;
+    }
+    atomicAdd(&sg[2 * lane], gw0);
+    atomicAdd(&sg[2 * lane + 1], gw1);
+    if (lane == 0) atomicAdd(&sg[kH], gb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) atomicAdd(G + kOffWh + t, sg[t]);
+    if (threadIdx.x == 0) atomicAdd(G + kOffBh, sg[kH]);
+}
+
+// dz = bf16(dh * (H > 0)) and the bias gradient sum over rows
+__global__ void k_lm_relu_bwd(const float* __restrict__ dh, const __nv_bfloat16* __restrict__ H, int64_t n,
+                              __nv_bfloat16* __restrict__ dz, float* __restrict__ gb) {
+    __shared__ float sg[kH];
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) sg[t] = 0.f;
+    __syncthreads();
+    const int64_t total = n * (kH / 2);
+    float a0 = 0.f, a1 = 0.f;
+    int fprev = -1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int f = 2 * (int)(t % (kH / 2));
+        const float2 d = reinterpret_cast<const float2*>(dh)[t];
+        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(H)[t];
+        const float v0 = __low2float(h) > 0.f ? d.x : 0.f, v1 = __high2float(h) > 0.f ? d.y : 0.f;
+        reinterpret_cast<__nv_bfloat162*>(dz)[t] = __floats2bfloat162_rn(v0, v1);
+        if (f != fprev && fprev >= 0) {
+            atomicAdd(&sg[fprev], a0);
+            atomicAdd(&sg[fprev + 1], a1);
+            a0 = a1 = 0.f;
+        }
+        fprev = f;
+        a0 += v0;
+        a1 += v1;
+    }
+    if (fprev >= 0) {
+        atomicAdd(&sg[fprev], a0);
+        atomicAdd(&sg[fprev + 1], a1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) atomicAdd(gb + t, sg[t]);
+}
+
+// dW += [Hin | M]^T dz: warp w of 8 takes input features [16w, 16w+16); rows in chunks of 16
+__global__ void __launch_bounds__(256) k_lm_gemm_dw(const __nv_bfloat16* __restrict__ Hin,
+                                                    const __nv_bfloat16* __restrict__ M,
+                                                    const __nv_bfloat16* __restrict__ dz, int64_t n,
+                                                    int64_t rows_per_block, float* __restrict__ gW) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+    const __nv_bfloat16* X = warp < 4 ? Hin : M;
+    const int f0 = (warp & 3) * 16;  // feature offset inside X
+    const int64_t rb = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t re = rb + rows_per_block < n ? rb + rows_per_block : n;
+    float c[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int64_t k0 = rb; k0 < re; k0 += 16) {
+        // A(m = feature, k = row) = X[row][feature]
+        const int64_t ka = k0 + tg * 2, kb = ka + 1, kc = ka + 8, kd = ka + 9;
+        auto x = [&](int64_t row, int f) { return row < re ? X[row * kH + f0 + f] : zero; };
+        uint32_t af[4];
+        af[0] = pack2(x(ka, g), x(kb, g));
+        af[1] = pack2(x(ka, g + 8), x(kb, g + 8));
+        af[2] = pack2(x(kc, g), x(kd, g));
+        af[3] = pack2(x(kc, g + 8), x(kd, g + 8));
+        auto dzv = [&](int64_t row, int col) { return row < re ? dz[row * kH + col] : zero; };
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + g;
+            uint32_t bfr[2] = {pack2(dzv(ka, col), dzv(kb, col)), pack2(dzv(kc, col), dzv(kd, col))};
+            mma16816(c[nt], af, bfr);
+        }
+    }
+    // gradient layout [in 128][out 64]; input feature index = 16*warp + m
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = nt * 8 + tg * 2;
+        const int in0 = warp * 16 + g, in1 = in0 + 8;
+        atomicAdd(gW + in0 * kH + col, c[nt][0]);
+        atomicAdd(gW + in0 * kH + col + 1, c[nt][1]);
+        atomicAdd(gW + in1 * kH + col, c[nt][2]);
+        atomicAdd(gW + in1 * kH + col + 1, c[nt][3]);
+    }
+}
+
+// [dhd | dm] = dz W^T: a warp computes 16 rows x 128 columns, K = 64
+__global__ void __launch_bounds__(128) k_lm_gemm_dx(const __nv_bfloat16* __restrict__ dz,
+                                                    const __nv_bfloat16* __restrict__ Wn, int64_t n,
+                                                    float* __restrict__ dhd, float* __restrict__ dm) {
+    __shared__ __align__(16) __nv_bfloat16 sW[kK * kH];  // [in][out]
+    for (int t = threadIdx.x; t < kK * kH / 8; t += blockDim.x)
+        reinterpret_cast<uint4*>(sW)[t] = reinterpret_cast<const uint4*>(Wn)[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+    const int64_t tiles = (n + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
+         tile += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        const bool ok0 = r0 < n, ok1 = r1 < n;
+        uint32_t af[4][4];
+#pragma unroll
+        for (int kk = 0; kk < kH / 16; ++kk) {
+            const int kc = kk * 16 + tg * 2;
+            af[kk][0] = ok0 ? ld_pair(dz + r0 * kH + kc) : 0u;
+            af[kk][1] = ok1 ? ld_pair(dz + r1 * kH + kc) : 0u;
+            af[kk][2] = ok0 ? ld_pair(dz + r0 * kH + kc + 8) : 0u;
+            af[kk][3] = ok1 ? ld_pair(dz + r1 * kH + kc + 8) : 0u;
+        }
+#pragma unroll
+        for (int nt = 0; nt < kK / 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < kH / 16; ++kk) {
+                const __nv_bfloat16* wcol = sW + (nt * 8 + g) * kH + kk * 16 + tg * 2;  // B(k=out, n=in)
+                uint32_t bfr[2] = {ld_pair(wcol), ld_pair(wcol + 8)};
+                mma16816(c, af[kk], bfr);
+            }
+            const int col = (nt * 8 + tg * 2) & (kH - 1);
+            float* dst = nt < 8 ? dhd : dm;
+            if (ok0) *reinterpret_cast<float2*>(dst + r0 * kH + col) = make_float2(c[0], c[1]);
+            if (ok1) *reinterpret_cast<float2*>(dst + r1 * kH + col) = make_float2(c[2], c[3]);
+        }
+    }
+}
+
+// encoder backward: dz0 = dh0 * (h0 > 0); grads of w_e (sum dz0 r~) and b_e (sum dz0)
+__global__ void k_lm_enc_bwd(const float* __restrict__ dh, const __nv_bfloat16* __restrict__ H0,
+                             const float* __restrict__ rt, int64_t n, float* __restrict__ G) {
+    __shared__ float sw[kH], sb[kH];
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) sw[t] = sb[t] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float w0 = 0.f, w1 = 0.f, b0 = 0.f, b1 = 0.f;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const float2 d = reinterpret_cast<const float2*>(dh + i * kH)[lane];
+        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(H0 + i * kH)[lane];
+        const float v0 = __low2float(h) > 0.f ? d.x : 0.f, v1 = __high2float(h) > 0.f ? d.y : 0.f;
+        const float r = rt[i];
+        w0 += v0 * r;
+        w1 += v1 * r;
+        b0 += v0;
+        b1 += v1;
+    }
+    atomicAdd(&sw[2 * lane], w0);
+    atomicAdd(&sw[2 * lane + 1], w1);
+    atomicAdd(&sb[2 * lane], b0);
+    atomicAdd(&sb[2 * lane + 1], b1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+        atomicAdd(G + kOffWe + t, sw[t]);
+        atomicAdd(G + kOffBe + t, sb[t]);
+    }
+}
+
+__global__ void k_lm_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                          float* __restrict__ v, int np, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const float gi = G[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of the layer weights: Wt[out][in] and Wn[in][out]
+__global__ void k_lm_cast(const float* __restrict__ P, __nv_bfloat16* Wt0, __nv_bfloat16* Wt1, __nv_bfloat16* Wt2,
+                          __nv_bfloat16* Wn0, __nv_bfloat16* Wn1, __nv_bfloat16* Wn2) {
+    __nv_bfloat16* Wt[3] = {Wt0, Wt1, Wt2};
+    __nv_bfloat16* Wn[3] = {Wn0, Wn1, Wn2};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kLayers * kWsz; t += gridDim.x * blockDim.x) {
+        const int l = t / kWsz, k = t % kWsz, in = k / kH, out = k % kH;
+        const __nv_bfloat16 w = __float2bfloat16(P[kOffW0 + l * kLayerStride + k]);
+        Wn[l][k] = w;
+        Wt[l][out * kK + in] = w;
+    }
+}
+
+// FP64 residual r0 = b - A x0 (SELL, FP64), 0 on PEC rows; optional FP32 copy into a sample slot
+__global__ void k_lm_resid(Sell S, const double* __restrict__ val, const double* __restrict__ b,
+                           const double* __restrict__ x, const uint8_t* __restrict__ fixed, int64_t n,
+                           double* __restrict__ r, float* __restrict__ sample, float* rr) {
+    float ss = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = fixed[i] ? 0.0 : b[i] - sell_row<double, double>(S, val, x, i);
+        r[i] = ri;
+        if (sample) sample[i] = (float)ri;
+        const float rf = (float)ri;
+        ss += rf * rf;
+    }
+    if (rr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(rr, ss);
+    }
+}
+
+// y = x0 + s D^-1/2 c~
+__global__ void k_lm_candidate(const double* __restrict__ x0, const float* __restrict__ ct,
+                               const float* __restrict__ dis, const float* __restrict__ scal, int64_t n,
+                               double* __restrict__ y) {
+    const double s = (double)scal[4];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x0[i] + s * (double)dis[i] * (double)ct[i];
+}
+
+// keep the candidate only if its residual is smaller (the plain guess is the judge)
+__global__ void k_lm_select(double* __restrict__ x0, const double* __restrict__ y, const float* __restrict__ scal,
+                            int64_t n, int* flag) {
+    const bool take = scal[3] < scal[2];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = take ? 0 : 1;
+    if (!take) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x0[i] = y[i];
+}
+
+int blocks(const fem_pic* ctx, int64_t work, int per_block = 256, int per_sm = 8) {
+    int64_t b = (work + per_block - 1) / per_block, cap = (int64_t)ctx->sm_count * per_sm;
+    b = b < cap ? b : cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// forward pass from a residual (FP64 or FP32) to c~; scal[4] = s
+template <typename R>
+fp_status forward(fem_pic* ctx, const R* r, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    LearnedDev* L = F->learned;
+    const Sell S{F->se_ptr, F->se_w, F->se_col};
+    const int64_t n = L->n;
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal, 0, sizeof(float), s));
+    k_lm_sumsq<R><<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, L->scal);
+    k_lm_input<R><<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, (float)L->n_free, L->scal,
+                                                             L->params, L->rt, L->h[0], L->scal + 4);
+    for (int l = 0; l < kLayers; ++l) {
+        k_lm_aggregate<<<blocks(ctx, n * 32), 256, 0, s>>>(S, L->a_sell, L->h[l], n, L->m[l]);
+        k_lm_gemm_fwd<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(
+            L->h[l], L->m[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n, L->h[l + 1]);
+    }
+    k_lm_head<<<blocks(ctx, n * 32), 256, 0, s>>>(L->h[kLayers], L->params, L->rt, F->edge_fixed, n, L->ct);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+fp_status train_step(fem_pic* ctx, const float* r, float lr, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    LearnedDev* L = F->learned;
+    const Sell S{F->se_ptr, F->se_w, F->se_col};
+    const int64_t n = L->n;
+    fp_status st = forward<float>(ctx, r, s);
+    if (st != FP_OK) return st;
+    // loss = ||A~ c~ - r~||^2 / n_free;  dL/dc~ = 2/n_free A~ e
+    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, n, L->e, L->scal + 1);
+    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->e, nullptr, F->edge_fixed, 2.f / (float)L->n_free, n,
+                                             L->dct, nullptr);
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->grads, 0, kNParams * sizeof(float), s));
+    k_lm_head_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dct, L->h[kLayers], L->params, n, L->dh, L->grads);
+    const int64_t rpb = 2048;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        float* gW = L->grads + kOffW0 + l * kLayerStride;
+        k_lm_relu_bwd<<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(L->dh, L->h[l + 1], n, L->dz, gW + kWsz);
+        k_lm_gemm_dw<<<(unsigned)((n + rpb - 1) / rpb), 256, 0, s>>>(L->h[l], L->m[l], L->dz, n, rpb, gW);
+        k_lm_gemm_dx<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(L->dz, L->Wn[l], n, L->dhd, L->dm);
+        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(S, L->a_sell, L->dm, L->dhd, n, L->dh);
+    }
+    k_lm_enc_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dh, L->h[0], L->rt, n, L->grads);
+    ++L->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    k_lm_adam<<<64, 256, 0, s>>>(L->params, L->grads, L->am, L->av, kNParams, lr, b1, b2, 1e-8f,
+                                 1.f - powf(b1, (float)L->adam_t), 1.f - powf(b2, (float)L->adam_t));
+    k_lm_cast<<<96, 256, 0, s>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+template <typename T>
+fp_status alloc(fem_pic* ctx, T** p, size_t count) {
+    FP_CUDA_TRY(ctx, cudaMalloc((void**)p, count * sizeof(T) + 16));
+    return FP_OK;
+}
+
+}  // namespace
+
+bool learned_active(const FieldDev* F) { return F && F->learned && (F->learned->active || F->learned->collecting); }
+
+int* learned_flag(FieldDev* F) { return F && F->learned ? F->learned->flag : nullptr; }
+
+void learned_set_active(FieldDev* F, bool on) {
+    if (F && F->learned) F->learned->active = on ? 1 : 0;
+}
+
+void learned_free(FieldDev* F) {
+    LearnedDev* L = F ? F->learned : nullptr;
+    if (!L) return;
+    void* ptrs[] = {L->a_sell, L->dis, L->params, L->grads, L->am, L->av, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0],
+                    L->Wn[1], L->Wn[2], L->h[0], L->h[1], L->h[2], L->h[3], L->m[0], L->m[1], L->m[2], L->dz, L->dh,
+                    L->dhd, L->dm, L->rt, L->ct, L->e, L->dct, L->scal, L->flag, L->r0, L->y, L->samples};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete L;
+    F->learned = nullptr;
+}
+
+// Newmark starting point: collect the residual of the extrapolated guess as a training
+// sample and/or replace the guess by the learned one when it has the smaller residual.
+fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    LearnedDev* L = F->learned;
+    const Sell S{F->se_ptr, F->se_w, F->se_col};
+    const int64_t n = L->n;
+    float* slot = nullptr;
+    if (L->collecting && L->cap > 0) {
+        slot = L->samples + (int64_t)L->next * n;
+        L->next = (L->next + 1) % L->cap;
+        L->count = std::min(L->count + 1, L->cap);
+    }
+    PhaseTimer pt(ctx, PH_LEARNED, s);
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 2, 0, 2 * sizeof(float), s));
+    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, x0, F->edge_fixed, n, L->r0, slot, L->scal + 2);
+    if (!L->active) return FP_OK;
+    fp_status st = forward<double>(ctx, L->r0, s);
+    if (st != FP_OK) return st;
+    k_lm_candidate<<<blocks(ctx, n), 256, 0, s>>>(x0, L->ct, L->dis, L->scal, n, L->y);
+    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, L->y, F->edge_fixed, n, F->tmp, nullptr, L->scal + 3);
+    k_lm_select<<<blocks(ctx, n), 256, 0, s>>>(x0, L->y, L->scal, n, L->flag);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+}  // namespace fempic
+
+using namespace fempic;
+
+extern "C" {
+
+fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity) {
+    if (!ctx || !ctx->field || sample_capacity < 0) {
+        if (ctx) ctx->err = "fem_pic_learned_init: call fem_pic_field_setup first";
+        return FP_EINVAL;
+    }
+    FieldDev* F = ctx->field;
+    learned_free(F);
+    LearnedDev* L = new LearnedDev();
+    F->learned = L;
+    const HostFields& H = F->host;
+    const int64_t n = F->ne;
+    L->n = n;
+    int64_t nfree = 0;
+    for (int64_t i = 0; i < n; ++i) nfree += H.edge_fixed[i] ? 0 : 1;
+    L->n_free = nfree > 0 ? nfree : 1;
+    // D^-1/2 and A~ in the SELL layout of A (values gathered from the device copy)
+    std::vector<double> d(n, 1.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t j = H.e_rp[i]; j < H.e_rp[i + 1]; ++j)
+            if (H.e_col[j] == i) d[i] = H.M[j] + 0.25 * F->dt * F->dt * H.S[j];
+    std::vector<float> dis(n);
+    for (int64_t i = 0; i < n; ++i) dis[i] = (float)(1.0 / std::sqrt(d[i]));
+    const int64_t ns = (n + 31) / 32;
+    std::vector<int32_t> ptr(ns), w(ns);
+    FP_CUDA_TRY(ctx, cudaMemcpy(ptr.data(), F->se_ptr, ns * 4, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(w.data(), F->se_w, ns * 4, cudaMemcpyDeviceToHost));
+    const int64_t tot = ns ? (int64_t)ptr[ns - 1] + 32 * (int64_t)w[ns - 1] : 0;
+    std::vector<int32_t> col(tot);
+    std::vector<double> av(tot);
+    FP_CUDA_TRY(ctx, cudaMemcpy(col.data(), F->se_col, tot * 4, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(av.data(), F->se_A, tot * 8, cudaMemcpyDeviceToHost));
+    std::vector<float> at(tot);
+    for (int64_t sl = 0; sl < ns; ++sl)
+        for (int64_t lane = 0; lane < 32; ++lane) {
+            const int64_t r = 32 * sl + lane;
+            for (int j = 0; j < w[sl]; ++j) {
+                const int64_t k = ptr[sl] + lane + 32 * (int64_t)j;
+                at[k] = r < n ? (float)(av[k] * dis[r] * dis[col[k]]) : 0.f;
+            }
+        }
+    // parameters: small random layer weights, identity-like start (the head starts at 0)
+    std::vector<float> P(kNParams, 0.f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int f = 0; f < kH; ++f) {
+        P[kOffWe + f] = nd(rng);
+        P[kOffBe + f] = 0.1f * nd(rng);
+    }
+    for (int l = 0; l < kLayers; ++l)
+        for (int k = 0; k < kWsz; ++k) P[kOffW0 + l * kLayerStride + k] = nd(rng) * std::sqrt(2.f / kK);
+    fp_status st = FP_OK;
+    auto up = [&](auto** dst, const auto& src) -> fp_status {
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)dst, src.size() * sizeof(src[0]) + 16));
+        FP_CUDA_TRY(ctx, cudaMemcpy(*dst, src.data(), src.size() * sizeof(src[0]), cudaMemcpyHostToDevice));
+        return FP_OK;
+    };
+    if (st == FP_OK) st = up(&L->a_sell, at);
+    if (st == FP_OK) st = up(&L->dis, dis);
+    if (st == FP_OK) st = up(&L->params, P);
+    std::vector<float> zeros(kNParams, 0.f);
+    if (st == FP_OK) st = up(&L->grads, zeros);
+    if (st == FP_OK) st = up(&L->am, zeros);
+    if (st == FP_OK) st = up(&L->av, zeros);
+    for (int l = 0; l < kLayers && st == FP_OK; ++l) {
+        st = alloc(ctx, &L->Wt[l], kWsz);
+        if (st == FP_OK) st = alloc(ctx, &L->Wn[l], kWsz);
+    }
+    for (int l = 0; l <= kLayers && st == FP_OK; ++l) st = alloc(ctx, &L->h[l], (size_t)n * kH);
+    for (int l = 0; l < kLayers && st == FP_OK; ++l) st = alloc(ctx, &L->m[l], (size_t)n * kH);
+    if (st == FP_OK) st = alloc(ctx, &L->dz, (size_t)n * kH);
+    if (st == FP_OK) st = alloc(ctx, &L->dh, (size_t)n * kH);
+    if (st == FP_OK) st = alloc(ctx, &L->dhd, (size_t)n * kH);
+    if (st == FP_OK) st = alloc(ctx, &L->dm, (size_t)n * kH);
+    if (st == FP_OK) st = alloc(ctx, &L->rt, n);
+    if (st == FP_OK) st = alloc(ctx, &L->ct, n);
+    if (st == FP_OK) st = alloc(ctx, &L->e, n);
+    if (st == FP_OK) st = alloc(ctx, &L->dct, n);
+    if (st == FP_OK) st = alloc(ctx, &L->scal, 8);
+    if (st == FP_OK) st = alloc(ctx, &L->flag, 1);
+    if (st == FP_OK) st = alloc(ctx, &L->r0, n);
+    if (st == FP_OK) st = alloc(ctx, &L->y, n);
+    if (st == FP_OK && sample_capacity > 0) st = alloc(ctx, &L->samples, (size_t)sample_capacity * n);
+    if (st != FP_OK) return st;
+    L->cap = sample_capacity;
+    k_lm_cast<<<96, 256>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
+    FP_CUDA_TRY(ctx, cudaMemset(L->flag, 0, sizeof(int)));
+    FP_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_mode(fem_pic_t* ctx, int collect, int active) {
+    if (!ctx || !ctx->field || !ctx->field->learned) return FP_EINVAL;
+    ctx->field->learned->collecting = collect != 0;
+    ctx->field->learned->active = active != 0;
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_samples(fem_pic_t* ctx, int* count) {
+    if (!ctx || !ctx->field || !ctx->field->learned || !count) return FP_EINVAL;
+    *count = ctx->field->learned->count;
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs, double lr, uint64_t seed,
+                                double* loss, void* stream) {
+    if (!ctx || !ctx->field || !ctx->field->learned || epochs < 0 || !(lr > 0.0)) return FP_EINVAL;
+    LearnedDev* L = ctx->field->learned;
+    if (first < 0 || count < 1 || first + count > L->count) {
+        ctx->err = "fem_pic_learned_train: sample range outside the collected samples";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = first + i;
+    std::mt19937_64 rng(seed);
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(order.begin(), order.end(), rng);
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
+        for (int k : order) {
+            // cosine decay of the learning rate over the run
+            const double t = (double)(ep * count) / (double)std::max(1, epochs * count);
+            const float lr_t = (float)(lr * 0.5 * (1.0 + std::cos(3.141592653589793 * t)));
+            fp_status st = train_step(ctx, L->samples + (int64_t)k * L->n, lr_t, s);
+            if (st != FP_OK) return st;
+        }
+        if (loss) {
+            float l = 0.f;
+            FP_CUDA_TRY(ctx, cudaMemcpyAsync(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+            FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            loss[ep] = (double)l / ((double)L->n_free * count);
+        }
+    }
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* ratio, void* stream) {
+    // ratio[k] = ||A~ c~ - r~||^2 / ||r~||^2 for sample first+k (1 = no better than zero guess)
+    if (!ctx || !ctx->field || !ctx->field->learned || !ratio) return FP_EINVAL;
+    LearnedDev* L = ctx->field->learned;
+    FieldDev* F = ctx->field;
+    if (first < 0 || count < 1 || first + count > L->count) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Sell S{F->se_ptr, F->se_w, F->se_col};
+    for (int k = 0; k < count; ++k) {
+        fp_status st = forward<float>(ctx, L->samples + (int64_t)(first + k) * L->n, s);
+        if (st != FP_OK) return st;
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
+        k_lm_spmv<<<blocks(ctx, L->n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, L->n, L->e,
+                                                    L->scal + 1);
+        float l = 0.f;
+        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+        FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        ratio[k] = (double)l / (double)L->n_free;
+    }
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params) {
+    if (!ctx || !ctx->field || !ctx->field->learned) return FP_EINVAL;
+    LearnedDev* L = ctx->field->learned;
+    if (n_params) *n_params = kNParams;
+    if (get) FP_CUDA_TRY(ctx, cudaMemcpy(get, L->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    if (set) {
+        FP_CUDA_TRY(ctx, cudaMemcpy(L->params, set, kNParams * sizeof(float), cudaMemcpyHostToDevice));
+        k_lm_cast<<<96, 256>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
+        FP_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    }
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out, void* stream) {
+    // c~ and r~ of one residual (device arrays), for tests
+    if (!ctx || !ctx->field || !ctx->field->learned || !r) return FP_EINVAL;
+    LearnedDev* L = ctx->field->learned;
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = forward<double>(ctx, r, s);
+    if (st != FP_OK) return st;
+    if (ct_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(ct_out, L->ct, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (rt_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(rt_out, L->rt, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_out, double* loss, void* stream) {
+    // gradient of the loss for one residual without updating the weights, for tests
+    if (!ctx || !ctx->field || !ctx->field->learned || !r || !grad_out) return FP_EINVAL;
+    FieldDev* F = ctx->field;
+    LearnedDev* L = F->learned;
+    cudaStream_t s = (cudaStream_t)stream;
+    // run a training step with lr = 0 and read the gradients before Adam touches them
+    std::vector<float> keep(kNParams), keep_m(kNParams), keep_v(kNParams);
+    FP_CUDA_TRY(ctx, cudaMemcpy(keep.data(), L->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(keep_m.data(), L->am, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(keep_v.data(), L->av, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    const int t_keep = L->adam_t;
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
+    fp_status st = train_step(ctx, r, 0.f, s);
+    if (st != FP_OK) return st;
+    FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    FP_CUDA_TRY(ctx, cudaMemcpy(grad_out, L->grads, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss) {
+        float l = 0.f;
+        FP_CUDA_TRY(ctx, cudaMemcpy(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost));
+        *loss = (double)l / (double)L->n_free;
+    }
+    // Adam with lr = 0 left the weights but moved its moments: restore the whole state
+    FP_CUDA_TRY(ctx, cudaMemcpy(L->params, keep.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+    FP_CUDA_TRY(ctx, cudaMemcpy(L->am, keep_m.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+    FP_CUDA_TRY(ctx, cudaMemcpy(L->av, keep_v.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+    L->adam_t = t_keep;
+    k_lm_cast<<<96, 256, 0, s>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
+    FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return FP_OK;
+}
+
+}  // extern "C"

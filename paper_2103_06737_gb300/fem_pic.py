@@ -106,6 +106,14 @@ def lib():
             "fem_pic_field_last_info": (I32, [P, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_options": (I32, [P, I32, I32, D]),
             "fem_pic_whitney0_integrals": (I32, [P, P]),
+            "fem_pic_learned_init": (I32, [P, ctypes.c_uint64, I32]),
+            "fem_pic_learned_mode": (I32, [P, I32, I32]),
+            "fem_pic_learned_samples": (I32, [P, P]),
+            "fem_pic_learned_train": (I32, [P, I32, I32, I32, D, ctypes.c_uint64, P, P]),
+            "fem_pic_learned_eval": (I32, [P, I32, I32, P, P]),
+            "fem_pic_learned_params": (I32, [P, P, P, P]),
+            "fem_pic_learned_forward": (I32, [P, P, P, P, P]),
+            "fem_pic_learned_gradient": (I32, [P, P, P, P, P]),
             "fem_pic_profile_enable": (I32, [P, I32]),
             "fem_pic_profile_read": (I32, [P, P, P, I32]),
         }
@@ -374,6 +382,60 @@ def fem_pic_field_initial(h, Q, E, tol: float = 1e-10, max_iter: int = 10000, in
     if st not in (FP_OK, FP_ENOCONV):
         _check(st, h)
     return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_learned_init(h, seed: int = 0, sample_capacity: int = 64):
+    _check(lib().fem_pic_learned_init(h, int(seed), int(sample_capacity)), h)
+
+
+def fem_pic_learned_mode(h, collect: bool, active: bool):
+    _check(lib().fem_pic_learned_mode(h, 1 if collect else 0, 1 if active else 0), h)
+
+
+def fem_pic_learned_samples(h) -> int:
+    c = ctypes.c_int(0)
+    _check(lib().fem_pic_learned_samples(h, ctypes.byref(c)), h)
+    return int(c.value)
+
+
+def fem_pic_learned_train(h, first: int, count: int, epochs: int, lr: float = 1e-3, seed: int = 0, stream=None):
+    loss = np.zeros(max(1, epochs), dtype=np.float64)
+    _check(lib().fem_pic_learned_train(h, int(first), int(count), int(epochs), float(lr), int(seed), _ptr(loss),
+                                       _stream(stream)), h)
+    return loss[:epochs]
+
+
+def fem_pic_learned_eval(h, first: int, count: int, stream=None) -> np.ndarray:
+    out = np.zeros(count, dtype=np.float64)
+    _check(lib().fem_pic_learned_eval(h, int(first), int(count), _ptr(out), _stream(stream)), h)
+    return out
+
+
+def fem_pic_learned_params(h, set_values=None) -> np.ndarray:
+    n = ctypes.c_int64(0)
+    _check(lib().fem_pic_learned_params(h, None, None, ctypes.byref(n)), h)
+    out = np.zeros(int(n.value), dtype=np.float32)
+    sv = None if set_values is None else np.ascontiguousarray(set_values, dtype=np.float32)
+    _check(lib().fem_pic_learned_params(h, _ptr(out), _ptr(sv), None), h)
+    return out
+
+
+def fem_pic_learned_forward(h, r, stream=None):
+    _need(r, torch.float64, name="r")
+    ct = torch.empty(r.numel(), dtype=torch.float32, device=r.device)
+    rt = torch.empty_like(ct)
+    _check(lib().fem_pic_learned_forward(h, _ptr(r), _ptr(ct), _ptr(rt), _stream(stream)), h)
+    return ct, rt
+
+
+def fem_pic_learned_gradient(h, r, stream=None):
+    _need(r, torch.float32, name="r")
+    n = ctypes.c_int64(0)
+    _check(lib().fem_pic_learned_params(h, None, None, ctypes.byref(n)), h)
+    g = np.zeros(int(n.value), dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(lib().fem_pic_learned_gradient(h, _ptr(r), _ptr(g), ctypes.byref(loss), _stream(stream)), h)
+    return g, float(loss.value)
 
 
 def fem_pic_field_last_info(h, stream=None):
