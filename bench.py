@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--solver", default="fp64,fp64",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
+                    help="learned Newmark correction: trained during warm-up, used if it beats plain CG (auto)")
+    ap.add_argument("--learn-samples", type=int, default=48)
+    ap.add_argument("--learn-epochs", type=int, default=30)
+    ap.add_argument("--compare-steps", type=int, default=20)
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -262,8 +267,10 @@ def run_gpu(args):
             n_k += 3              # field prep, fast push, FP64 walk of the queued particles
         if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
             F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
-                                 max_iter=args.max_iter, precond=precond, info=False)
+                                 max_iter=args.max_iter, precond=state["precond"], info=False)
             n_k += 7
+            if state["precond"] == F.FP_PC_LEARNED:
+                n_k += 13         # residual, network forward (9 kernels), candidate, residual, select
         lib.residuals(dG, Qn, Qo, b, res)
         n_k += 1
         Qo.copy_(Qn)
@@ -278,7 +285,7 @@ def run_gpu(args):
             for k in range(len(species)):
                 cur[k] = 1 - cur[k]
 
-    state = {"i": 0}
+    state = {"i": 0, "precond": precond}
 
     def eager_step():
         pl = plan(state["i"])
@@ -301,19 +308,67 @@ def run_gpu(args):
     if st != F.FP_OK:
         raise RuntimeError(f"warm-up status {st}: {F.fem_pic_last_error(lib.h)}")
 
+    # learned correction: collect residuals of the method's own Newmark solves, train,
+    # then time learned vs plain Jacobi-CG on the same steps (plain CG is the judge)
+    learned = None
+    if field and args.learned != "off":
+        t_l0 = time.time()
+        F.fem_pic_learned_init(lib.h, seed=0, sample_capacity=args.learn_samples)
+        F.fem_pic_learned_mode(lib.h, collect=True, active=False)
+        for _ in range(args.learn_samples):
+            eager_step()
+        torch.cuda.synchronize()
+        F.fem_pic_learned_mode(lib.h, collect=False, active=False)
+        n_s = F.fem_pic_learned_samples(lib.h)
+        n_hold = max(1, n_s // 6)
+        before = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
+        losses = F.fem_pic_learned_train(lib.h, 0, n_s - n_hold, args.learn_epochs, lr=2e-3, seed=0)
+        after = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
+        t_train = time.time() - t_l0
+
+        def compare(pc):
+            state["precond"] = pc
+            F.fem_pic_profile_read(lib.h, reset=True)
+            F.fem_pic_profile_enable(lib.h, True)
+            its, fb = [], 0
+            for k in range(args.compare_steps):
+                flush_l2(k)
+                eager_step()
+                fi = F.fem_pic_field_last_info(lib.h)
+                its.append(fi[0]["iters"])
+                fb += fi[0]["fell_back"]
+            torch.cuda.synchronize()
+            F.fem_pic_profile_enable(lib.h, False)
+            ph = F.fem_pic_profile_read(lib.h, reset=True)
+            tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
+            return {"field_ms_per_step": tot / args.compare_steps,
+                    "newmark_cg_ms_per_step": ph.get("cg_newmark", (0.0, 1))[0] / args.compare_steps,
+                    "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
+                    "newmark_iters_mean": statistics.mean(its), "fell_back": fb}
+        plain = compare(precond)
+        learn = compare(F.FP_PC_LEARNED)
+        use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
+        state["precond"] = F.FP_PC_LEARNED if use else precond
+        learned = {"samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
+                   "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
+                   "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
+                   "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
+                   "model": "3-layer message passing on the edge graph, 64 features, BF16 weights, FP32 accum"}
+
     # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
     graphs = {}
     use_graphs = not args.no_graphs
 
     def graph_step():
         pl = plan(state["i"])
-        if pl not in graphs:
+        key = (pl, state["precond"])
+        if key not in graphs:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 n_k = enqueue(pl)
-            graphs[pl] = (g, n_k)
+            graphs[key] = (g, n_k)
             torch.cuda.synchronize()
-        g, n_k = graphs[pl]
+        g, n_k = graphs[key]
         g.replay()
         advance(pl)
         state["i"] += 1
@@ -477,7 +532,9 @@ def run_gpu(args):
             "field_solve": None if not field else {
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
-                "precond": "jacobi",
+                "ms_learned_guess": phases.get("learned", (0.0, 1))[0] / args.steps,
+                "precond": "learned correction + jacobi" if state["precond"] == F.FP_PC_LEARNED else "jacobi",
+                "learned_vs_plain": learned,
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual and dot "
                            "products, FP32 inner Jacobi-PCG", "fp64": "plain FP64 Jacobi-PCG",
                            "inner_tol": args.inner_tol},

@@ -94,7 +94,7 @@ def test_forward_and_gradient_match_reference():
     g_ref = torch.cat([we.grad, be.grad] + sum([[W[l].grad.reshape(-1), b[l].grad] for l in range(NL)], []) +
                       [wh.grad, bh.grad.reshape(1)]).numpy()
     g_gpu, loss_gpu = F.fem_pic_learned_gradient(lib.h, torch.as_tensor(r, dtype=torch.float32, device="cuda"))
-    assert abs(loss_gpu - float(loss)) <= 2e-2 * float(loss)
+    assert abs(loss_gpu - loss.item()) <= 2e-2 * loss.item()
     rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
     assert rel < 5e-2, rel
     cos = (g_gpu @ g_ref) / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref))
