@@ -144,6 +144,13 @@ def fast_kernel_bytes(n_particles, sizes):
     return n_particles * 52 + sizes["n_tets"] * 128 + 8 * (sizes["n_edges"] + sizes["n_nodes"])
 
 
+def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
+    """Minimal DRAM bytes of one Jacobi-PCG iteration (two barriers per iteration): the
+    operator once (value + column index per nonzero) and 13 passes over n-vectors
+    (update: x, r read+write, p, q, diag^-1 read, z write; search: z, p, q read, p, q write)."""
+    return nnz * (val_bytes + 4) + 13 * 8 * n_rows
+
+
 def peak_hbm():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -504,6 +511,29 @@ def run_gpu(args):
         fast_avg = fast_ms / max(1, fast_n)
         fbytes = fast_kernel_bytes(n_part, sizes)
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
+        roof_push = {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
+                     "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg, "traffic": None}
+        roof = roof_push
+        if field:
+            nnz = np.zeros(2, dtype=np.int64)
+            F.lib().fem_pic_field_nnz(lib.h, nnz.ctypes.data_as(F.ctypes.c_void_p))
+            cand = []
+            for ph, rows, nz, its in (("cg_newmark", sizes["n_edges"], int(nnz[0]), statistics.mean(iters_n)),
+                                      ("cg_gauss", sizes["n_nodes"], int(nnz[1]), statistics.mean(iters_g))):
+                t_ms, cnt = phases.get(ph, (0.0, 1))
+                if cnt and t_ms > 0:
+                    avg = t_ms / cnt
+                    byt = pcg_bytes_per_iter(rows, nz) * max(its, 1)
+                    cand.append((avg, {"kernel": "k_pcg (" + ph.split("_")[1] + " system, FP64)", "bound": "hbm",
+                                       "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
+                                       "unit": "GB/s", "frac": byt / (avg * 1e-3) / 1e9 / peak,
+                                       "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg,
+                                       "iterations_per_launch": its, "traffic": None,
+                                       "note": "operator and vectors are L2-resident across iterations; the "
+                                               "kernel is bound by barrier and gather latency, not HBM"}))
+            cand.append((fast_avg, roof_push))
+            roof = max(cand, key=lambda c: c[0])[1]
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -516,10 +546,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "sort (periodic) + push/gather/walk/deposit + implicit field step "
                                "(Newmark + Gauss-law projection + Faraday, FP64 Jacobi-CG to 1e-10) + fp64 residuals"},
-            "roofline": {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
-                         "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg,
-                         "traffic": None},
+            "roofline": roof,
+            "roofline_push": roof_push,
             "roofline_push_call": {"kernels": "k_field_prep32 + k_push_fast32 + k_walk32 (sum of kernel times)",
                                    "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                    "frac": achieved / peak, "algorithmic_bytes_per_launch": abytes,
