@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=2000)
-    ap.add_argument("--solver", default="fp64,fp64",
+    ap.add_argument("--solver", default="mixed,mixed",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
                     help="learned Newmark correction: trained during warm-up, used if it beats plain CG (auto)")
     ap.add_argument("--learn-samples", type=int, default=48)
@@ -145,10 +145,23 @@ def fast_kernel_bytes(n_particles, sizes):
 
 
 def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
-    """Minimal DRAM bytes of one Jacobi-PCG iteration (two barriers per iteration): the
+    """Minimal DRAM bytes of one FP64 Jacobi-PCG iteration (two barriers per iteration): the
     operator once (value + column index per nonzero) and 13 passes over n-vectors
     (update: x, r read+write, p, q, diag^-1 read, z write; search: z, p, q read, p, q write)."""
     return nnz * (val_bytes + 4) + 13 * 8 * n_rows
+
+
+def mixed_solve_bytes(n_rows, nnz, inner_iters, outer):
+    """Minimal DRAM bytes of one mixed-precision solve: per pipelined FP32 inner iteration the
+    FP32 operator once (4 B value + 4 B column per nonzero) and 19 FP32 vector passes (reads
+    of m, w, u, z, q, s, p, c, r, diag^-1; writes of z, q, s, p, c, r, u, w, m); per
+    refinement the start of the inner solve (one FP32 product, r, u, w, m written, r64 and
+    diag^-1 read) and the FP64 update x += |r| c; outer + 1 FP64 residuals b - A x (12 B per
+    nonzero, b and x read, r64 written, c cleared)."""
+    inner = inner_iters * (nnz * 8 + 19 * 4 * n_rows)
+    start = outer * (nnz * 8 + (8 + 4 + 4 * 4) * n_rows + (8 + 8 + 4) * n_rows)
+    resid = (outer + 1) * (nnz * 12 + (8 + 8 + 8 + 4) * n_rows)
+    return inner + start + resid
 
 
 def peak_hbm():
@@ -519,19 +532,26 @@ def run_gpu(args):
             nnz = np.zeros(2, dtype=np.int64)
             F.lib().fem_pic_field_nnz(lib.h, nnz.ctypes.data_as(F.ctypes.c_void_p))
             cand = []
-            for ph, rows, nz, its in (("cg_newmark", sizes["n_edges"], int(nnz[0]), statistics.mean(iters_n)),
-                                      ("cg_gauss", sizes["n_nodes"], int(nnz[1]), statistics.mean(iters_g))):
+            for k_sys, (ph, rows, nz, its, outs) in enumerate(
+                    (("cg_newmark", sizes["n_edges"], int(nnz[0]), statistics.mean(iters_n), statistics.mean(outer_n)),
+                     ("cg_gauss", sizes["n_nodes"], int(nnz[1]), statistics.mean(iters_g), statistics.mean(outer_g)))):
                 t_ms, cnt = phases.get(ph, (0.0, 1))
                 if cnt and t_ms > 0:
                     avg = t_ms / cnt
-                    byt = pcg_bytes_per_iter(rows, nz) * max(its, 1)
-                    cand.append((avg, {"kernel": "k_pcg (" + ph.split("_")[1] + " system, FP64)", "bound": "hbm",
+                    mixed = solv[k_sys] == "mixed"
+                    byt = (mixed_solve_bytes(rows, nz, its, outs) if mixed else
+                           pcg_bytes_per_iter(rows, nz) * max(its, 1))
+                    name = ("k_pcg_mixed (" + ph.split("_")[1] + " system, pipelined FP32 inner CG, FP64 residual)"
+                            if mixed else "k_pcg (" + ph.split("_")[1] + " system, FP64)")
+                    cand.append((avg, {"kernel": name, "bound": "hbm",
                                        "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
                                        "unit": "GB/s", "frac": byt / (avg * 1e-3) / 1e9 / peak,
                                        "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg,
-                                       "iterations_per_launch": its, "traffic": None,
-                                       "note": "operator and vectors are L2-resident across iterations; the "
-                                               "kernel is bound by barrier and gather latency, not HBM"}))
+                                       "iterations_per_launch": its, "refinements_per_launch": outs,
+                                       "traffic": None,
+                                       "note": "operator and vectors stay in L2 across iterations; the kernel is "
+                                               "bound by grid barriers and gather latency, and its algorithmic "
+                                               "bytes are set against the HBM peak"}))
             cand.append((fast_avg, roof_push))
             roof = max(cand, key=lambda c: c[0])[1]
         out = {
@@ -545,7 +565,8 @@ def run_gpu(args):
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "sort (periodic) + push/gather/walk/deposit + implicit field step "
-                               "(Newmark + Gauss-law projection + Faraday, FP64 Jacobi-CG to 1e-10) + fp64 residuals"},
+                               "(Newmark + Gauss-law projection + Faraday, Jacobi-CG to 1e-10 relative residual in FP64) "
+                               "+ fp64 residuals"},
             "roofline": roof,
             "roofline_push": roof_push,
             "roofline_push_call": {"kernels": "k_field_prep32 + k_push_fast32 + k_walk32 (sum of kernel times)",

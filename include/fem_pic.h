@@ -290,7 +290,7 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
  * Solver per system, overriding the precond argument of the solve calls: newmark_solver
  * and gauss_solver are FP_PC_JACOBI (mixed-precision refinement), FP_PC_JACOBI_FP64, or
  * -1 (use the precond passed to each call).  inner_tol in (0,1): residual reduction of each
- * FP32 inner solve of the mixed solver (default 1e-4).
+ * FP32 inner solve of the mixed solver (default 1e-5).
  */
 fp_status fem_pic_field_options(fem_pic_t* ctx, int newmark_solver, int gauss_solver, double inner_tol);
 

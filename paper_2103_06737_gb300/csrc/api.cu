@@ -393,6 +393,10 @@ fp_status fem_pic_status(fem_pic_t* ctx, void* stream) {
     FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, 4, s));
     FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h & ST_TIMEOUT) {
+        ctx->err = "a kernel gave up waiting for its asynchronous copies";
+        return FP_ECUDA;
+    }
     if (h & ST_INVAL) {
         ctx->err = "a kernel saw a cell id outside [0, N_t)";
         return FP_EINVAL;

@@ -11,6 +11,7 @@
 
 namespace cg = cooperative_groups;
 
+
 namespace fempic {
 
 
@@ -18,52 +19,59 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 256;
-constexpr int kSolverBlock = 256;   // cooperative solvers: 256-thread blocks, 2 per SM
+// Cooperative solvers: up to 2 co-resident blocks per SM; the block size is chosen per
+// system from kSolverBlocks at setup.
+constexpr int kSolverPerSm = 2;
 
 __device__ __forceinline__ double as_f64(float x) { return f2d(x); }
 __device__ __forceinline__ double as_f64(double x) { return x; }
 
-// sum of NV values over the block, result valid in every thread
-template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kSolverBlock / 32]) {
+// Deterministic grid-wide sum of NV values, result valid in every thread.  Warp sums go to
+// sh[k][warp]; thread 0 writes the block's partial to part[NV * block + k]; after the grid
+// barrier warp 0 of every block adds all partials in block order and broadcasts through
+// sh[k][BS / 32].  Two block barriers and one grid barrier per call.  Consecutive calls must
+// use different `part` buffers (a block may write the next partials while another block
+// still reads these).
+template <int BS, int NV, typename T>
+__device__ __forceinline__ void grid_sum(T v[NV], T* part, cg::grid_group& g, T (*sh)[BS / 32 + 1]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
-    __syncthreads();
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kSolverBlock / 32; ++w) t += sh[k][w];
-        v[k] = t;
-    }
-}
-
-// deterministic grid-wide sum: partials of every block, summed in block order by each block
-template <int NV>
-__device__ __forceinline__ void grid_sum(double v[NV], double* part, cg::grid_group& g,
-                                         double (*sh)[kSolverBlock / 32]) {
-    block_sum<NV>(v, sh);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) part[NV * blockIdx.x + k] = v[k];
+        for (int k = 0; k < NV; ++k) {
+            T t = T(0);
+#pragma unroll
+            for (int w = 0; w < BS / 32; ++w) t += sh[k][w];
+            part[NV * blockIdx.x + k] = t;
+        }
     g.sync();
-    double t[NV];
+    if (wid == 0) {
+        T t[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) t[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int k = 0; k < NV; ++k) t[k] = T(0);
+        for (int b = lane; b < (int)gridDim.x; b += 32)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) t[k] += __ldcg(part + NV * b + k);
-    block_sum<NV>(t, sh);
+            for (int k = 0; k < NV; ++k) t[k] += __ldcg(part + NV * b + k);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = t[k];
+        for (int k = 0; k < NV; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(kFull, t[k], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sh[k][BS / 32] = t[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = sh[k][BS / 32];
 }
 
 struct PcgArgs {
@@ -86,16 +94,21 @@ struct PcgArgs {
 // block takes the same decisions from the same grid-wide sums (deterministic: partials
 // summed in block order), so all blocks run the same number of grid barriers; the loop is
 // bounded by max_iter.  A p is carried as q = A z + beta q, two barriers per iteration.
-__global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
+template <int BS>
+__global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg(PcgArgs a) {
     cg::grid_group g = cg::this_grid();
-    __shared__ double sh[4][kSolverBlock / 32];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double sh[4][BS / 32 + 1];
+    // rows [r0, r1) of this block: contiguous runs of whole 32-row slices, so the columns a
+    // block gathers (neighbouring DOFs) stay within a window that its SM's L1 can hold
+    const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + 31) & ~(int64_t)31;
+    const int64_t r0 = min(a.n, (int64_t)blockIdx.x * chunk), r1 = min(a.n, r0 + chunk);
+    const int64_t stride = BS;
+    const int64_t t0 = r0 + threadIdx.x;
     double* part0 = a.red;                    // 4 values per block
     double* part1 = a.red + 4 * gridDim.x;    // 2 values per block
     double* part2 = a.red + 6 * gridDim.x;    // 2 values per block
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.r, b.b, s.s
-    for (int64_t i = t0; i < a.n; i += stride) {
+    for (int64_t i = t0; i < r1; i += stride) {
         const double bi = a.b[i];
         const double ri = bi - sell_row<double, double>(a.S, a.val, a.x, i);
         a.r[i] = ri;
@@ -104,7 +117,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
         v[1] += bi * bi;
         if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
     }
-    grid_sum<4>(v, part0, g, sh);  // also makes z visible to every block
+    grid_sum<BS, 4, double>(v, part0, g, sh);  // also makes z visible to every block
     double rr = v[0];
     const double bb = a.scale_vec ? v[2] : v[1];
     const double thr = a.tol * a.tol * bb;
@@ -112,7 +125,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
     if (rr > thr && a.max_iter > 0) {
         // p = z, q = A z; rz, pq
         double u[2] = {0.0, 0.0};
-        for (int64_t i = t0; i < a.n; i += stride) {
+        for (int64_t i = t0; i < r1; i += stride) {
             const double w = sell_row<double, double>(a.S, a.val, a.z, i);
             const double zi = a.z[i];
             a.p[i] = zi;
@@ -120,13 +133,13 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
             u[0] += a.r[i] * zi;
             u[1] += zi * w;
         }
-        grid_sum<2>(u, part1, g, sh);
+        grid_sum<BS, 2, double>(u, part1, g, sh);
         double rz = u[0], pq = u[1];
         for (;;) {
             if (!(pq > 0.0)) break;  // breakdown (same decision in every block)
             const double alpha = rz / pq;
             double w2[2] = {0.0, 0.0};  // r.z, r.r
-            for (int64_t i = t0; i < a.n; i += stride) {
+            for (int64_t i = t0; i < r1; i += stride) {
                 a.x[i] += alpha * a.p[i];
                 const double ri = a.r[i] - alpha * a.q[i];
                 const double zi = a.dinv[i] * ri;
@@ -135,14 +148,14 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
                 w2[0] += ri * zi;
                 w2[1] += ri * ri;
             }
-            grid_sum<2>(w2, part2, g, sh);
+            grid_sum<BS, 2, double>(w2, part2, g, sh);
             ++it;
             rr = w2[1];
             if (!(rr > thr) || it >= a.max_iter) break;
             const double beta = w2[0] / rz;
             rz = w2[0];
             double u2[2] = {0.0, 0.0};
-            for (int64_t i = t0; i < a.n; i += stride) {
+            for (int64_t i = t0; i < r1; i += stride) {
                 const double w = sell_row<double, double>(a.S, a.val, a.z, i);
                 const double pi = a.z[i] + beta * a.p[i];
                 const double qi = w + beta * a.q[i];
@@ -150,11 +163,11 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg(PcgArgs a) {
                 a.q[i] = qi;
                 u2[0] += pi * qi;
             }
-            grid_sum<2>(u2, part1, g, sh);
+            grid_sum<BS, 2, double>(u2, part1, g, sh);
             pq = u2[0];
         }
     }
-    if (t0 == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.out[0] = (double)it;
         a.out[1] = rr;
         a.out[2] = bb;      // squared norm the residual is measured against
@@ -191,20 +204,26 @@ struct MixedArgs {
     int32_t* status;
 };
 
-__global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
+template <int BS>
+__global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
-    __shared__ double sh[4][kSolverBlock / 32];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double* part0 = a.red;                    // 4 values per block
-    double* part1 = a.red + 4 * gridDim.x;    // 3 values per block
-    double* part2 = a.red + 7 * gridDim.x;    // 2 values per block
+    __shared__ double sh[4][BS / 32 + 1];
+    __shared__ float shf[3][BS / 32 + 1];
+    // rows [r0, r1) of this block: contiguous runs of whole 32-row slices, so the columns a
+    // block gathers (neighbouring DOFs) stay within a window that its SM's L1 can hold
+    const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + 31) & ~(int64_t)31;
+    const int64_t r0 = min(a.n, (int64_t)blockIdx.x * chunk), r1 = min(a.n, r0 + chunk);
+    const int64_t stride = BS;
+    const int64_t t0 = r0 + threadIdx.x;
+    double* part0 = a.red;                               // 4 FP64 values per block
+    float* part1 = (float*)(a.red + 4 * gridDim.x);      // 3 FP32 values per block
+    float* part2 = part1 + 3 * gridDim.x;                // 2 FP32 values per block
     int total = 0, outer = 0;
     double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
     for (;;) {
         // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
         double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int64_t i = t0; i < a.n; i += stride) {
+        for (int64_t i = t0; i < r1; i += stride) {
             const double bi = a.b[i];
             const double ri = bi - sell_row<double, double>(a.S, a.val, a.x, i);
             a.r64[i] = ri;
@@ -213,7 +232,7 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
             v[1] += bi * bi;
             if (a.scale_vec) v[2] += a.scale_vec[i] * a.scale_vec[i];
         }
-        grid_sum<4>(v, part0, g, sh);
+        grid_sum<BS, 4, double>(v, part0, g, sh);
         rr64 = v[0];
         if (outer == 0) {
             ref2 = a.scale_vec ? v[2] : v[1];
@@ -221,61 +240,63 @@ __global__ void __launch_bounds__(kSolverBlock, 2) k_pcg_mixed(MixedArgs a) {
         }
         if (!(rr64 > thr) || total >= a.max_iter || outer >= a.max_outer) break;
         ++outer;
-        // ---- inner FP32 Jacobi-PCG on A c = r / ||r|| (dot products accumulated in FP64)
+        // ---- inner FP32 Jacobi-PCG on A c = r / ||r||: vectors, products, dot products and
+        // their grid sums all in FP32 (an inner solve only has to reduce its residual by
+        // inner_tol; the FP64 outer residual corrects what FP32 loses)
         const double rnorm = sqrt(rr64), rinv = 1.0 / rnorm;
-        for (int64_t i = t0; i < a.n; i += stride) {
+        for (int64_t i = t0; i < r1; i += stride) {
             const float ri = d2f(a.r64[i] * rinv);
             a.r[i] = ri;
             a.z[i] = a.dinv32[i] * ri;
         }
         g.sync();
-        double u[3] = {0.0, 0.0, 0.0};  // r.z, p.q, r.r
-        for (int64_t i = t0; i < a.n; i += stride) {
+        float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
+        for (int64_t i = t0; i < r1; i += stride) {
             const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
             const float zi = a.z[i], ri = a.r[i];
             a.p[i] = zi;
             a.q[i] = w;
-            u[0] += (double)(ri * zi);
-            u[1] += (double)(zi * w);
-            u[2] += (double)(ri * ri);
+            u[0] += ri * zi;
+            u[1] += zi * w;
+            u[2] += ri * ri;
         }
-        grid_sum<3>(u, part1, g, sh);
-        double rz = u[0], pq = u[1];
-        const double ithr = a.inner_tol * a.inner_tol * u[2];
+        grid_sum<BS, 3, float>(u, part1, g, shf);
+        float rz = u[0], pq = u[1];
+        const float ithr = (float)a.inner_tol * (float)a.inner_tol * u[2];
         for (;;) {
-            if (!(pq > 0.0) || total >= a.max_iter) break;
-            const float alpha = (float)(rz / pq);
-            double w2[2] = {0.0, 0.0};  // r.z, r.r
-            for (int64_t i = t0; i < a.n; i += stride) {
+            if (!(pq > 0.f) || total >= a.max_iter) break;
+            const float alpha = rz / pq;
+            float w2[2] = {0.f, 0.f};  // r.z, r.r
+            for (int64_t i = t0; i < r1; i += stride) {
                 a.c[i] += alpha * a.p[i];
                 const float ri = a.r[i] - alpha * a.q[i];
                 const float zi = a.dinv32[i] * ri;
                 a.r[i] = ri;
                 a.z[i] = zi;
-                w2[0] += (double)(ri * zi);
-                w2[1] += (double)(ri * ri);
+                w2[0] += ri * zi;
+                w2[1] += ri * ri;
             }
-            grid_sum<2>(w2, part2, g, sh);
+            grid_sum<BS, 2, float>(w2, part2, g, shf);
             ++total;
             if (!(w2[1] > ithr)) break;
-            const float beta = (float)(w2[0] / rz);
+            const float beta = w2[0] / rz;
             rz = w2[0];
-            double u2[1] = {0.0};
-            for (int64_t i = t0; i < a.n; i += stride) {
+            float u2[1] = {0.f};
+            for (int64_t i = t0; i < r1; i += stride) {
                 const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
                 const float pi = a.z[i] + beta * a.p[i];
                 const float qi = w + beta * a.q[i];
                 a.p[i] = pi;
                 a.q[i] = qi;
-                u2[0] += (double)(pi * qi);
+                u2[0] += pi * qi;
             }
-            grid_sum<1>(u2, part1, g, sh);
+            grid_sum<BS, 1, float>(u2, part1, g, shf);
             pq = u2[0];
         }
-        for (int64_t i = t0; i < a.n; i += stride) a.x[i] += rnorm * f2d(a.c[i]);
+        for (int64_t i = t0; i < r1; i += stride) a.x[i] += rnorm * f2d(a.c[i]);
         g.sync();
     }
-    if (t0 == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.out[0] = (double)total;
         a.out[1] = rr64;
         a.out[2] = ref2;
@@ -297,11 +318,17 @@ __global__ void k_newmark_rhs(Sell Sl, const double* __restrict__ Mv, const doub
         const int64_t base = __ldg(Sl.ptr + sl) + (i & 31);
         const int w = __ldg(Sl.w + sl);
         double s = 0.0;
-        for (int j = 0; j < w; ++j) {
-            const int64_t k = base + 32 * (int64_t)j;
-            const int c = __ldg(Sl.col + k);
-            const double en = En[c], em = Em[c];
-            s += __ldg(Mv + k) * (2.0 * en - em) - dt2 * __ldg(Sv + k) * (0.5 * en + 0.25 * em);
+        for (int j0 = 0; j0 < w; j0 += kSellChunk) {   // chunks of independent loads, as in sell_row
+            int c[kSellChunk];
+#pragma unroll
+            for (int u = 0; u < kSellChunk; ++u) c[u] = j0 + u < w ? __ldg(Sl.col + base + 32 * (j0 + u)) : -1;
+#pragma unroll
+            for (int u = 0; u < kSellChunk; ++u) {
+                if (c[u] < 0) continue;
+                const int64_t k = base + 32 * (int64_t)(j0 + u);
+                const double en = En[c[u]], em = Em[c[u]];
+                s += __ldg(Mv + k) * (2.0 * en - em) - dt2 * __ldg(Sv + k) * (0.5 * en + 0.25 * em);
+            }
         }
         if (fixed[i]) {
             rhs[i] = 0.0;
@@ -361,6 +388,16 @@ __global__ void k_faraday(const int32_t* __restrict__ fe, const double* __restri
     }
 }
 
+constexpr int kSolverBlocks[3] = {128, 256, 512};
+
+void* solver_kernel(int bs, bool fp64) {
+    switch (bs) {
+        case 128: return fp64 ? (void*)k_pcg<128> : (void*)k_pcg_mixed<128>;
+        case 256: return fp64 ? (void*)k_pcg<256> : (void*)k_pcg_mixed<256>;
+        default: return fp64 ? (void*)k_pcg<512> : (void*)k_pcg_mixed<512>;
+    }
+}
+
 int grid_of(const fem_pic* ctx, int64_t n) {
     int64_t g = (n + kBlock - 1) / kBlock, cap = (int64_t)ctx->sm_count * 8;
     if (g > cap) g = cap;
@@ -397,7 +434,8 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         void* args[] = {&m};
         PhaseTimer pt(ctx, ph, s);
         const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
-        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg_mixed, dim3(grid), dim3(kSolverBlock), args, 0, s));
+        const int bs = system == FP_SYS_NEWMARK ? F->bs_e : F->bs_n;
+        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, false), dim3(grid), dim3(bs), args, 0, s));
         return FP_OK;
     }
     PcgArgs a;
@@ -411,7 +449,8 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     void* args[] = {&a};
     PhaseTimer pt(ctx, ph, s);
     const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
-    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(grid), dim3(kSolverBlock), args, 0, s));
+    const int bs = system == FP_SYS_NEWMARK ? F->bs_e : F->bs_n;
+    FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, true), dim3(grid), dim3(bs), args, 0, s));
     return FP_OK;
 }
 
@@ -635,26 +674,32 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
     double** vecs[] = {&F->r, &F->z, &F->p, &F->q, &F->rhs, &F->tmp, &F->delta, &F->qd};
     for (double** v : vecs)
         if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)v, nmax * sizeof(double)));
-    // cooperative grid: all blocks co-resident
-    int per_sm = 0;
-    if (st == FP_OK) {
-        int per_sm2 = 0;
-        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kSolverBlock, 0));
-        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_pcg_mixed, kSolverBlock, 0));
-        if (per_sm2 < per_sm) per_sm = per_sm2;
-    }
-    if (st == FP_OK) {
+    // cooperative grids: all blocks co-resident, at most kSolverPerSm per SM.  Per system the
+    // block size whose block count (one row per thread) is closest to one block per SM: the
+    // grid barriers and reductions cost more with more blocks, the SpMV and vector passes
+    // less with more SMs busy.
+    auto pick = [&](int64_t rows, int* bs, int* grid) -> fp_status {
+        double best = 1e30;
+        for (int b : kSolverBlocks) {
+            const double d = std::fabs(std::log((double)((rows + b - 1) / b) / (double)ctx->sm_count));
+            if (d < best) best = d, *bs = b;
+        }
+        int per_sm = 0, per_sm2 = 0;
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel(*bs, true), *bs, 0));
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, solver_kernel(*bs, false), *bs, 0));
+        per_sm = std::min(std::min(per_sm, per_sm2), kSolverPerSm);
         if (per_sm < 1) {
             ctx->err = "fem_pic_field_setup: the solver kernel cannot be co-resident";
             return FP_ECUDA;
         }
-        F->grid = ctx->sm_count * (per_sm < 2 ? per_sm : 2);  // cheaper grid reductions than a full grid
-        auto fit = [&](int64_t rows) {
-            const int64_t need = (rows + kSolverBlock - 1) / kSolverBlock;
-            return (int)(need < F->grid ? (need < 1 ? 1 : need) : F->grid);
-        };
-        F->grid_e = fit(hc.ne);
-        F->grid_n = fit(hc.nn);
+        const int64_t need = std::max<int64_t>(1, (rows + *bs - 1) / *bs);
+        *grid = (int)std::min<int64_t>(need, (int64_t)ctx->sm_count * per_sm);
+        return FP_OK;
+    };
+    if (st == FP_OK) st = pick(hc.ne, &F->bs_e, &F->grid_e);
+    if (st == FP_OK) st = pick(hc.nn, &F->bs_n, &F->grid_n);
+    if (st == FP_OK) {
+        F->grid = std::max(F->grid_e, F->grid_n);
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));

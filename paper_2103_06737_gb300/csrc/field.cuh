@@ -39,6 +39,7 @@ struct FieldDev {
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
     int grid = 0;                   // co-resident blocks (cooperative launch limit)
     int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
+    int bs_e = 256, bs_n = 256;     // and their block sizes
     int last_fp64[2] = {0, 0};      // solver used by the last solve in each info slot
     LearnedDev* learned = nullptr;
     bool learned_used = false;      // the last field step applied the learned guess
@@ -51,17 +52,32 @@ struct Sell {
     const int32_t* col;   // padded entries point at the row itself with value 0
 };
 
-// row i of a SELL-32 matrix times x; the 32 lanes of a warp take the 32 rows of a slice
+// row i of a SELL-32 matrix times x; the 32 lanes of a warp take the 32 rows of a slice.
+// The entries are taken in chunks of kSellChunk: the column indices of a chunk are loaded
+// together, then the values and the gathered x, so a thread has a chunk of independent
+// loads in flight instead of one dependent index -> x pair at a time.
+constexpr int kSellChunk = 8;
+
 template <typename V, typename X>
 __device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, const X* __restrict__ x,
                                       int64_t i) {
     const int64_t sl = i >> 5;
-    const int64_t base = __ldg(S.ptr + sl) + (i & 31);
+    const int32_t* cp = S.col + __ldg(S.ptr + sl) + (i & 31);
+    const V* vp = val + __ldg(S.ptr + sl) + (i & 31);
     const int w = __ldg(S.w + sl);
     X s = X(0);
-    for (int j = 0; j < w; ++j) {
-        const int64_t k = base + 32 * (int64_t)j;
-        s += (X)__ldg(val + k) * __ldcg(x + __ldg(S.col + k));
+    for (int j0 = 0; j0 < w; j0 += kSellChunk) {
+        int c[kSellChunk];
+        V a[kSellChunk];
+        X xv[kSellChunk];
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) c[u] = j0 + u < w ? __ldg(cp + 32 * (j0 + u)) : -1;
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) a[u] = j0 + u < w ? __ldg(vp + 32 * (j0 + u)) : V(0);
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? __ldcg(x + c[u]) : X(0);
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) s += (X)a[u] * xv[u];
     }
     return s;
 }

@@ -50,7 +50,7 @@ struct __align__(128) TetHot {
 static_assert(sizeof(TetHot) == 128, "TetHot layout");
 
 // bits of the device status word
-enum : int32_t { ST_WALK = 1, ST_INVAL = 2, ST_NOCONV = 4 };
+enum : int32_t { ST_WALK = 1, ST_INVAL = 2, ST_NOCONV = 4, ST_TIMEOUT = 8 };
 
 struct HostComplex {
     int64_t nn = 0, ne = 0, nf = 0, nt = 0;
@@ -93,7 +93,7 @@ struct fem_pic {
     fempic::FieldDev* field = nullptr;  // implicit field step (fem_pic_field_setup)
     int solver_fp64 = 0;                // 1: plain FP64 PCG, 0: mixed-precision refinement
     int solver_sys[2] = {-1, -1};       // per-system override (FP_PC_JACOBI / _FP64), -1 = as requested
-    double inner_tol = 1e-4;            // mixed solver: residual reduction of each FP32 inner solve
+    double inner_tol = 1e-5;            // mixed solver: residual reduction of each FP32 inner solve
     // profiler: events recorded on the launch stream around each kernel when enabled
     bool prof_on = false;
     std::vector<fempic::ProfRec> prof_pending;
@@ -119,6 +119,7 @@ struct fem_pic {
     int32_t* d_slow_idx = nullptr;    // [slow_cap]
     int32_t* d_slow_count = nullptr;  // [1]
     int64_t slow_cap = 0;
+    int tma_blocks_per_sm = 0;        // co-resident blocks of the staged push kernel (0: not queried yet)
     uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch
     int32_t* d_sort_count = nullptr;  // [nt + 2]

@@ -18,6 +18,7 @@
 #include <mutex>
 #include <string>
 
+#include "async_copy.cuh"
 #include "internal.cuh"
 
 namespace fempic {
@@ -511,12 +512,116 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 // than the FP32 rounding bound, the FP64 exit test would find no exit either, so the
 // piece stays in the tet and is deposited here (warp-reduced).  Otherwise the
 // particle index is queued for the FP64 walk (velocity already updated).
+//
+// One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
+// it (the deposit reduction is a warp collective).  Returns true when the particle has to
+// go to the FP64 walk; the caller queues it.
+__device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, int c, const float x[3], float v[3],
+                                              int64_t p, int64_t n, int32_t nt, float h, float dt, float w,
+                                              int aggregate, float* __restrict__ off, float* __restrict__ vel,
+                                              float* __restrict__ dG, float* __restrict__ Q,
+                                              int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    if (c >= nt) {
+        atomicOr(status, ST_INVAL);
+        c = -1;
+    }
+    int key = -1;
+    bool slow = false;
+    float agg[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) agg[k] = 0.f;
+    TetHot H;
+    if (c >= 0) {
+        load_hot(hot, c, H);
+        float l[4];
+        l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
+        l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
+        l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
+        l[0] = 1.f - l[1] - l[2] - l[3];
+        float E[3], B[3];
+        E[0] = H.E0[0] + (H.W[1] * x[2] - H.W[2] * x[1]);
+        E[1] = H.E0[1] + (H.W[2] * x[0] - H.W[0] * x[2]);
+        E[2] = H.E0[2] + (H.W[0] * x[1] - H.W[1] * x[0]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
+        boris<float>(v, E, B, h);
+        vel[p] = v[0];
+        vel[n + p] = v[1];
+        vel[2 * n + p] = v[2];
+        float xb[3], dx[3], d[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            xb[i] = step_pos(x[i], dt, v[i]);
+            dx[i] = xb[i] - x[i];
+        }
+        d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
+        d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
+        d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
+        d[0] = -(d[1] + d[2] + d[3]);
+        // rounding bound of l^b in FP32 (with the FP32 copy of the gradients)
+        float S = 1.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S += fabsf(H.g[k]) * (fabsf(x[k % 3]) + fabsf(dx[k % 3]));
+        const float margin = S * (1.f / 65536.f);
+        float lbmin = l[0] + d[0];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
+        if (lbmin >= margin) {
+            agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
+            agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
+            agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
+            agg[3] = w * (l[1] * d[2] - l[2] * d[1]);
+            agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
+            agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
+            off[p] = xb[0];
+            off[n + p] = xb[1];
+            off[2 * n + p] = xb[2];
+            key = c;
+            if (!aggregate) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+            }
+        } else {
+            slow = true;
+        }
+    }
+    if (aggregate) {
+        unsigned heads;
+        int end;
+        warp_run_reduce<float, 10>(key, agg, &heads, &end);
+        if (((heads >> lane) & 1u) && key >= 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+        }
+    }
+    return slow;
+}
+
+// appends the lanes with `slow` set to a queue (one atomic per warp on its counter)
+template <typename Counter>
+__device__ __forceinline__ void warp_enqueue(bool slow, int32_t value, int32_t* queue, Counter* count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned sm = __ballot_sync(kFull, slow);
+    if (!sm) return;
+    int basei = 0;
+    const int leader = __ffs(sm) - 1;
+    if (lane == leader) basei = atomicAdd(count, __popc(sm));
+    basei = __shfl_sync(kFull, basei, leader);
+    if (slow) queue[basei + __popc(sm & ((1u << lane) - 1u))] = value;
+}
+
 #ifndef FP_FAST_MIN_BLOCKS
 #define FP_FAST_MIN_BLOCKS 4
 #endif
-#ifndef FP_FAST_PREFETCH
-#define FP_FAST_PREFETCH 2
-#endif
+// Grid-stride variant: the particle state is loaded straight from global memory (the
+// next particle's cell one iteration ahead).
 __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
     float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
@@ -526,141 +631,131 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float w = (float)qw;
     int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-#if FP_FAST_PREFETCH == 2
     int c_nx = base + lane < n ? __ldg(cell + base + lane) : -1;
-#elif FP_FAST_PREFETCH
-    // the next particle's cell and state are loaded one iteration ahead
-    int c_nx = -1;
-    float x_nx[3] = {0.f, 0.f, 0.f}, v_nx[3] = {0.f, 0.f, 0.f};
-    if (base + lane < n) {
-        const int64_t q = base + lane;
-        c_nx = __ldg(cell + q);
-        x_nx[0] = off[q], x_nx[1] = off[n + q], x_nx[2] = off[2 * n + q];
-        v_nx[0] = vel[q], v_nx[1] = vel[n + q], v_nx[2] = vel[2 * n + q];
-    }
-#endif
     for (; base < n; base += stride) {
         const int64_t p = base + lane;
-#if FP_FAST_PREFETCH == 1
-        int c = p < n ? c_nx : -1;
-        float x[3] = {x_nx[0], x_nx[1], x_nx[2]};
-        float v[3] = {v_nx[0], v_nx[1], v_nx[2]};
-        {
-            const int64_t q = p + stride;
-            if (q < n) {
-                c_nx = __ldg(cell + q);
-                x_nx[0] = off[q], x_nx[1] = off[n + q], x_nx[2] = off[2 * n + q];
-                v_nx[0] = vel[q], v_nx[1] = vel[n + q], v_nx[2] = vel[2 * n + q];
-            }
-        }
-#elif FP_FAST_PREFETCH == 2
-        // only the next particle's cell is loaded one iteration ahead
-        int c = p < n ? c_nx : -1;
+        const int c = p < n ? c_nx : -1;
         {
             const int64_t q = p + stride;
             c_nx = q < n ? __ldg(cell + q) : -1;
         }
-        float x[3], v[3];
+        float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
         if (c >= 0 && c < nt) {
             x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
-#else
-        int c = p < n ? __ldg(cell + p) : -1;
-        float x[3], v[3];
-        if (c >= 0 && c < nt) {
-            x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
-            v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
-        }
+        const bool slow = fast_particle(hot, c, x, v, p, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
+        warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);   // one global atomic per warp
+    }
+}
+
+// Persistent variant with the particle state staged through shared memory by bulk
+// asynchronous copies (TMA): a block owns tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// of kTmaTile consecutive particles and keeps the copies of its next FP_TMA_STAGES - 1
+// tiles in flight while it pushes the current one, so the HBM stream does not wait on
+// the per-particle dependency chain (state -> tet record -> push -> deposit).  Each of
+// the seven state components (cell, off x/y/z, vel x/y/z) of a tile is one bulk copy.
+// Needs n % 4 == 0 and 16-byte aligned cell/off/vel (every copy then starts on a 16-byte
+// boundary and moves a multiple of 16 bytes); the launcher checks this and otherwise
+// runs k_push_fast32.  Every wait on a copy is bounded (ST_TIMEOUT on expiry).
+constexpr int kTmaTile = 512;
+constexpr int kTmaThreads = 256;
+constexpr int kTmaSlot = kTmaTile * 4;       // bytes per component per stage
+constexpr int kTmaStageBytes = 7 * kTmaSlot;
+#ifndef FP_TMA_STAGES
+#define FP_TMA_STAGES 3
 #endif
-        if (c >= nt) {
-            atomicOr(status, ST_INVAL);
-            c = -1;
-        }
-        int key = -1;
-        bool slow = false;
-        float agg[10];
+constexpr int kTmaStages = FP_TMA_STAGES;
+constexpr uint64_t kTmaWaitNs = 2000000000ull;  // 2 s
+static_assert(kTmaSlot % 16 == 0 && kTmaTile % kTmaThreads == 0, "tile shape");
+
+// copies of tile t into stage s (one thread)
+__device__ __forceinline__ void tma_issue(unsigned char* stage, uint64_t* bar, int t, const int32_t* cell,
+                                          const float* off, const float* vel, int64_t n) {
+    const int64_t p0 = (int64_t)t * kTmaTile;
+    const uint32_t bytes = 4u * (uint32_t)min((int64_t)kTmaTile, n - p0);
+    mbar_arrive_expect_tx(bar, 7u * bytes);
+    bulk_g2s(stage, cell + p0, bytes, bar);
 #pragma unroll
-        for (int k = 0; k < 10; ++k) agg[k] = 0.f;
-        TetHot H;
-        if (c >= 0) {
-            load_hot(hot, c, H);
-            float l[4];
-            l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
-            l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
-            l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
-            l[0] = 1.f - l[1] - l[2] - l[3];
-            float E[3], B[3];
-            E[0] = H.E0[0] + (H.W[1] * x[2] - H.W[2] * x[1]);
-            E[1] = H.E0[1] + (H.W[2] * x[0] - H.W[0] * x[2]);
-            E[2] = H.E0[2] + (H.W[0] * x[1] - H.W[1] * x[0]);
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (1 + k) * kTmaSlot, off + k * n + p0, bytes, bar);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
-            boris<float>(v, E, B, h);
-            vel[p] = v[0];
-            vel[n + p] = v[1];
-            vel[2 * n + p] = v[2];
-            float xb[3], dx[3], d[4];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                xb[i] = step_pos(x[i], dt, v[i]);
-                dx[i] = xb[i] - x[i];
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kTmaSlot, vel + k * n + p0, bytes, bar);
+}
+
+__global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
+    const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
+    float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
+    float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kTmaStages];
+    // slow particles of a tile, collected in shared memory and written out with one global
+    // atomic per tile; two buffers so tile t's queue is copied out during tile t + 1
+    __shared__ int32_t tq[2][kTmaTile];
+    __shared__ int tq_n[2], tq_base[2];
+    const int tid = threadIdx.x;
+    const float w = (float)qw;
+    const int ntiles = (int)((n + kTmaTile - 1) / kTmaTile);
+    const int G = gridDim.x;
+    if (tid == 0) {
+        for (int s = 0; s < kTmaStages; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+        tq_n[0] = tq_n[1] = 0;
+    }
+    __syncthreads();
+    int issued = 0;  // tiles issued by this block (kept by thread 0)
+    if (tid == 0)
+        for (int s = 0; s < kTmaStages && (int)blockIdx.x + s * G < ntiles; ++s, ++issued)
+            tma_issue(smem + s * kTmaStageBytes, &bars[s], blockIdx.x + s * G, cell, off, vel, n);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++it) {
+        const int s = it % kTmaStages, qb = it & 1;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / kTmaStages) & 1), kTmaWaitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(status, ST_TIMEOUT);
+                // wait (bounded) for the copies still in flight before leaving
+                for (int j = it; j < issued; ++j)
+                    mbar_wait_bounded(&bars[j % kTmaStages], (uint32_t)((j / kTmaStages) & 1), kTmaWaitNs);
             }
-            d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
-            d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
-            d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
-            d[0] = -(d[1] + d[2] + d[3]);
-            // rounding bound of l^b in FP32 (with the FP32 copy of the gradients)
-            float S = 1.f;
+            return;
+        }
+        if (it > 0)  // the previous tile's queue (its global slots were reserved by thread 0)
+            for (int i = tid; i < tq_n[qb ^ 1]; i += kTmaThreads) slow_idx[tq_base[qb ^ 1] + i] = tq[qb ^ 1][i];
+        const int64_t p0 = (int64_t)t * kTmaTile;
+        const int cnt = (int)min((int64_t)kTmaTile, n - p0);
+        const unsigned char* st = smem + s * kTmaStageBytes;
+#pragma unroll 1
+        for (int q = 0; q < kTmaTile / kTmaThreads; ++q) {
+            const int j = q * kTmaThreads + tid;
+            int c = -1;
+            float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+            if (j < cnt) {
+                c = reinterpret_cast<const int32_t*>(st)[j];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) S += fabsf(H.g[k]) * (fabsf(x[k % 3]) + fabsf(dx[k % 3]));
-            const float margin = S * (1.f / 65536.f);
-            float lbmin = l[0] + d[0];
-#pragma unroll
-            for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
-            if (lbmin >= margin) {
-                agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
-                agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
-                agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
-                agg[3] = w * (l[1] * d[2] - l[2] * d[1]);
-                agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
-                agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
-                off[p] = xb[0];
-                off[n + p] = xb[1];
-                off[2 * n + p] = xb[2];
-                key = c;
-                if (!aggregate) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+                for (int k = 0; k < 3; ++k) {
+                    x[k] = reinterpret_cast<const float*>(st + (1 + k) * kTmaSlot)[j];
+                    v[k] = reinterpret_cast<const float*>(st + (4 + k) * kTmaSlot)[j];
                 }
-            } else {
-                slow = true;
+            }
+            const bool slow = fast_particle(hot, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
+            warp_enqueue(slow, (int32_t)(p0 + j), tq[qb], &tq_n[qb]);
+        }
+        __syncthreads();  // every thread is done with stage s and with tile queue qb ^ 1
+        if (tid == 0) {
+            tq_n[qb ^ 1] = 0;
+            tq_base[qb] = tq_n[qb] ? atomicAdd(slow_count, tq_n[qb]) : 0;
+            if (t + kTmaStages * G < ntiles) {
+                fence_proxy_async_smem();
+                tma_issue(smem + s * kTmaStageBytes, &bars[s], t + kTmaStages * G, cell, off, vel, n);
+                ++issued;
             }
         }
-        // queue the slow particles (one atomic per warp)
-        const unsigned sm = __ballot_sync(kFull, slow);
-        if (sm) {
-            int basei = 0;
-            const int leader = __ffs(sm) - 1;
-            if (lane == leader) basei = atomicAdd(slow_count, __popc(sm));
-            basei = __shfl_sync(kFull, basei, leader);
-            if (slow) slow_idx[basei + __popc(sm & ((1u << lane) - 1u))] = (int32_t)p;
-        }
-        if (aggregate) {
-            unsigned heads;
-            int end;
-            warp_run_reduce<float, 10>(key, agg, &heads, &end);
-            if (((heads >> lane) & 1u) && key >= 0) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
-            }
-        }
+    }
+    __syncthreads();
+    if (it > 0) {  // the last tile's queue
+        const int qb = (it - 1) & 1;
+        for (int i = tid; i < tq_n[qb]; i += kTmaThreads) slow_idx[tq_base[qb] + i] = tq[qb][i];
     }
 }
 
@@ -786,6 +881,44 @@ int grid_for(int64_t n, int sms) {
     return blocks < 1 ? 1 : (int)blocks;
 }
 
+// the fast FP32 push: the TMA-staged persistent kernel (grid = co-resident blocks), or the
+// grid-stride kernel when the state arrays are not 16-byte aligned
+fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
+                        float* dG, float* Q, cudaStream_t s) {
+    const size_t smem = (size_t)kTmaStages * kTmaStageBytes;
+    if (ctx->tma_blocks_per_sm == 0) {
+        FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tma32, kTmaThreads, smem));
+        if (per_sm < 1) {
+            ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
+            return FP_ECUDA;
+        }
+        ctx->tma_blocks_per_sm = per_sm;
+    }
+    const bool aligned = (p->n % 4) == 0 && ((uintptr_t)p->cell % 16) == 0 && ((uintptr_t)p->off % 16) == 0 &&
+                         ((uintptr_t)p->vel % 16) == 0;
+#ifndef FP_PUSH_TMA
+#define FP_PUSH_TMA 1
+#endif
+    if (!aligned || !FP_PUSH_TMA) {   // the bulk copies need 16-byte aligned starts and lengths
+        k_push_fast32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
+                                                                     (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
+                                                                     ctx->d_slow_idx, ctx->d_slow_count,
+                                                                     ctx->d_status);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+        return FP_OK;
+    }
+    const int64_t ntiles = (p->n + kTmaTile - 1) / kTmaTile;
+    int64_t grid = (int64_t)ctx->sm_count * ctx->tma_blocks_per_sm;
+    if (grid > ntiles) grid = ntiles;
+    k_push_tma32<<<(int)grid, kTmaThreads, smem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
+                                                      h, dt, qw, agg, dG, Q, ctx->d_slow_idx, ctx->d_slow_count,
+                                                      ctx->d_status);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
 }  // namespace
 
 fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, const fp_particles* p,
@@ -822,9 +955,8 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
         }
         {
             PhaseTimer pt(ctx, PH_FAST, s);
-            k_push_fast32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
-                                               (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
-                                               ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q, s);
+            if (sf != FP_OK) return sf;
         }
         {
             PhaseTimer pt(ctx, PH_WALK, s);

@@ -10,6 +10,17 @@ import numpy as np
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
+def fp32_continuity_tol(n_particles, n_nodes, n_edges):
+    """Relative bound on the FP32 continuity residual |D0^T dG - dQ| against the node scale.
+
+    The deposits are FP32 sums of k terms each (k ~ 4 N_p / N_n per node charge, 6 N_p / N_e
+    per edge current); their rounding grows like sqrt(k) * 2^-24 for independent roundings.
+    The bound takes 8 times that, and never less than 1e-6.
+    """
+    k = max(4.0 * n_particles / n_nodes, 6.0 * n_particles / n_edges, 1.0)
+    return max(1e-6, 8.0 * 2.0 ** -24 * k ** 0.5)
+
+
 def assert_deposit_close(got, ref, ref_abs, tol, what="dG"):
     got = np.asarray(got, dtype=np.float64)
     err = np.abs(got - ref)

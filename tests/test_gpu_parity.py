@@ -10,7 +10,7 @@ import torch
 
 from paper_2103_06737_gb300 import inputs as I
 import oracle as O
-from helpers import TOL, assert_deposit_close, csr_tuple
+from helpers import TOL, assert_deposit_close, csr_tuple, fp32_continuity_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -135,8 +135,12 @@ def test_push_deposit_fp64_parity(agg):
     lib.close()
 
 
-def test_push_deposit_fp32_parity():
-    m, orc, lib, sp, e, b = _setup(npart=50_001, speed=0.15, prec=F.FP_FP32)
+# 50,001 particles: the grid-stride fast kernel (length not a multiple of 4); 50,000 and
+# 1,200,000: the staged (bulk-copy) kernel, the latter with several tiles per block so
+# every pipeline stage is reused
+@pytest.mark.parametrize("npart", [50_001, 50_000, 1_200_000])
+def test_push_deposit_fp32_parity(npart):
+    m, orc, lib, sp, e, b = _setup(npart=npart, speed=0.15, prec=F.FP_FP32)
     q, mass, w, dt = sp.q, sp.m, sp.w, 1.0
     d = lib.species(sp.cell, sp.X, sp.V, q, mass, w)
     cell0 = d.cell.cpu().numpy().copy()
@@ -164,7 +168,7 @@ def test_push_deposit_fp32_parity():
     end = (off0 + np.float32(dt) * v1f).astype(np.float32)   # two roundings, as on the GPU
     Xb = o + end.T.astype(np.float64)
     ref = orc.step(cell0, Xa, Va, e, b, q, mass, w, dt, Xend=Xb)
-    assert ref["ncross"].sum() > 5000
+    assert ref["ncross"].sum() > npart // 10
     assert np.array_equal(cell1, ref["cell"])
     alive = cell1 >= 0
     assert np.abs(X1[alive] - ref["X"][alive]).max() <= 1e-6
@@ -173,7 +177,8 @@ def test_push_deposit_fp32_parity():
     assert_deposit_close(dG.cpu().numpy(), ref["dG"], ref["dG_abs"], tol, "dG")
     assert_deposit_close(Q.cpu().numpy(), ref["Q"], ref["Q_abs"], tol, "Q")
     assert_deposit_close(Q0.cpu().numpy(), Q0r, Q0a, tol, "Q0")
-    assert res.cpu().numpy()[0] <= 1e-6 * res.cpu().numpy()[1]
+    ctol = fp32_continuity_tol(npart, orc.n_nodes, orc.n_edges)
+    assert res.cpu().numpy()[0] <= ctol * res.cpu().numpy()[1]
     lib.close()
 
 
