@@ -152,13 +152,13 @@ def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
 
 
 def mixed_solve_bytes(n_rows, nnz, inner_iters, outer):
-    """Minimal DRAM bytes of one mixed-precision solve: per pipelined FP32 inner iteration the
-    FP32 operator once (4 B value + 4 B column per nonzero) and 19 FP32 vector passes (reads
-    of m, w, u, z, q, s, p, c, r, diag^-1; writes of z, q, s, p, c, r, u, w, m); per
-    refinement the start of the inner solve (one FP32 product, r, u, w, m written, r64 and
-    diag^-1 read) and the FP64 update x += |r| c; outer + 1 FP64 residuals b - A x (12 B per
-    nonzero, b and x read, r64 written, c cleared)."""
-    inner = inner_iters * (nnz * 8 + 19 * 4 * n_rows)
+    """Minimal DRAM bytes of one mixed-precision solve: per FP32 inner Jacobi-PCG iteration
+    the FP32 operator once (4 B value + 4 B column per nonzero) and 13 FP32 vector passes
+    (update: c, r read+write, p, q, diag^-1 read, z written; search: z, p, q read, p, q
+    written); per refinement the start of the inner solve (one FP32 product, r64 and
+    diag^-1 read, r, z, p, q written) and the FP64 update x += |r| c; outer + 1 FP64
+    residuals b - A x (12 B per nonzero, b and x read, r64 written, c cleared)."""
+    inner = inner_iters * (nnz * 8 + 13 * 4 * n_rows)
     start = outer * (nnz * 8 + (8 + 4 + 4 * 4) * n_rows + (8 + 8 + 4) * n_rows)
     resid = (outer + 1) * (nnz * 12 + (8 + 8 + 8 + 4) * n_rows)
     return inner + start + resid
@@ -541,7 +541,7 @@ def run_gpu(args):
                     mixed = solv[k_sys] == "mixed"
                     byt = (mixed_solve_bytes(rows, nz, its, outs) if mixed else
                            pcg_bytes_per_iter(rows, nz) * max(its, 1))
-                    name = ("k_pcg_mixed (" + ph.split("_")[1] + " system, pipelined FP32 inner CG, FP64 residual)"
+                    name = ("k_pcg_mixed (" + ph.split("_")[1] + " system, FP32 inner Jacobi-PCG, FP64 residual)"
                             if mixed else "k_pcg (" + ph.split("_")[1] + " system, FP64)")
                     cand.append((avg, {"kernel": name, "bound": "hbm",
                                        "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
@@ -584,8 +584,8 @@ def run_gpu(args):
                 "ms_learned_guess": phases.get("learned", (0.0, 1))[0] / args.steps,
                 "precond": "learned correction + jacobi" if state["precond"] == F.FP_PC_LEARNED else "jacobi",
                 "learned_vs_plain": learned,
-                "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual and dot "
-                           "products, FP32 inner Jacobi-PCG", "fp64": "plain FP64 Jacobi-PCG",
+                "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
+                           "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",
                            "inner_tol": args.inner_tol},
                 "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
                 "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,

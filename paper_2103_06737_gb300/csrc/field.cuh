@@ -56,7 +56,10 @@ struct Sell {
 // The entries are taken in chunks of kSellChunk: the column indices of a chunk are loaded
 // together, then the values and the gathered x, so a thread has a chunk of independent
 // loads in flight instead of one dependent index -> x pair at a time.
-constexpr int kSellChunk = 8;
+#ifndef FP_SELL_CHUNK
+#define FP_SELL_CHUNK 8
+#endif
+constexpr int kSellChunk = FP_SELL_CHUNK;
 
 template <typename V, typename X>
 __device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, const X* __restrict__ x,

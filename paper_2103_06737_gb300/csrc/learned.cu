@@ -43,6 +43,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct LearnedDev {
     int64_t n = 0, n_free = 0;
     float* a_sell = nullptr;      // A~ values in the SELL layout of A
+    float* a_csr = nullptr;       // A~ values in the CSR order of A (warp-per-row neighbour sums)
     float* dis = nullptr;         // D^-1/2
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     __nv_bfloat16* Wt[kLayers] = {nullptr, nullptr, nullptr};  // [64 out][128 in]
@@ -112,95 +113,157 @@ __global__ void k_lm_input(const R* __restrict__ r, const float* __restrict__ di
     if (blockIdx.x == 0 && threadIdx.x == 0 && s_out) *s_out = s;
 }
 
-// M = A~ H (BF16 features), warp per row, two features per lane
-__global__ void k_lm_aggregate(Sell S, const float* __restrict__ a, const __nv_bfloat16* __restrict__ H, int64_t n,
-                               __nv_bfloat16* __restrict__ M) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const int64_t sl = i >> 5;
-        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
-        const int w = __ldg(S.w + sl);
-        float s0 = 0.f, s1 = 0.f;
-        for (int j = 0; j < w; ++j) {
-            const int64_t k = base + 32 * (int64_t)j;
-            const int c = __ldg(S.col + k);
-            const float av = __ldg(a + k);
-            const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(H + (int64_t)c * kH)[lane];
-            s0 += av * __low2float(v);
-            s1 += av * __high2float(v);
-        }
-        reinterpret_cast<__nv_bfloat162*>(M + i * kH)[lane] = __floats2bfloat162_rn(s0, s1);
-    }
-}
+// Neighbour sums over the CSR rows of A~ (k_lm_layer, k_lm_aggregate_f32), warp per row, two
+// features per lane.  The lanes first load up to 32 (column, value) pairs of the row at
+// once (consecutive, coalesced), then the neighbour feature rows are gathered kAggUnroll
+// at a time, the indices and weights broadcast by shuffles, so that several row loads are
+// in flight.
+constexpr int kAggUnroll = 4;
 
-// dh = dhd + A~ dm (FP32 features), warp per row
-__global__ void k_lm_aggregate_f32(Sell S, const float* __restrict__ a, const float* __restrict__ dm,
+// dh = dhd + A~ dm (FP32 features)
+__global__ void k_lm_aggregate_f32(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                   const float* __restrict__ a, const float* __restrict__ dm,
                                    const float* __restrict__ dhd, int64_t n, float* __restrict__ dh) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const int64_t sl = i >> 5;
-        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
-        const int w = __ldg(S.w + sl);
+        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
         float2 acc = reinterpret_cast<const float2*>(dhd + i * kH)[lane];
-        for (int j = 0; j < w; ++j) {
-            const int64_t k = base + 32 * (int64_t)j;
-            const int c = __ldg(S.col + k);
-            const float av = __ldg(a + k);
-            const float2 v = reinterpret_cast<const float2*>(dm + (int64_t)c * kH)[lane];
-            acc.x += av * v.x;
-            acc.y += av * v.y;
+        for (int j0 = rb; j0 < re; j0 += 32) {
+            const int jj = j0 + lane;
+            const int cj = jj < re ? __ldg(col + jj) : 0;
+            const float aj = jj < re ? __ldg(a + jj) : 0.f;
+            const int cnt = min(32, re - j0);
+            for (int u = 0; u < cnt; u += kAggUnroll) {
+                float2 v[kAggUnroll];
+                float w[kAggUnroll];
+#pragma unroll
+                for (int q = 0; q < kAggUnroll; ++q) {
+                    const int c = __shfl_sync(kFull, cj, u + q);
+                    w[q] = __shfl_sync(kFull, aj, u + q);
+                    v[q] = reinterpret_cast<const float2*>(dm + (int64_t)c * kH)[lane];
+                }
+#pragma unroll
+                for (int q = 0; q < kAggUnroll; ++q) {
+                    acc.x += w[q] * v[q].x;
+                    acc.y += w[q] * v[q].y;
+                }
+            }
         }
         reinterpret_cast<float2*>(dh + i * kH)[lane] = acc;
     }
 }
 
-// Hout = relu([Hin | M] W + b): a warp computes 16 rows x 64 outputs, K = 128
-__global__ void __launch_bounds__(128) k_lm_gemm_fwd(const __nv_bfloat16* __restrict__ Hin,
-                                                     const __nv_bfloat16* __restrict__ M,
-                                                     const __nv_bfloat16* __restrict__ Wt,
-                                                     const float* __restrict__ bias, int64_t n,
-                                                     __nv_bfloat16* __restrict__ Hout) {
-    __shared__ __align__(16) __nv_bfloat16 sW[kH * kK];  // [out][in]
-    for (int t = threadIdx.x; t < kH * kK / 8; t += blockDim.x)
-        reinterpret_cast<uint4*>(sW)[t] = reinterpret_cast<const uint4*>(Wt)[t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-    const int64_t tiles = (n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
-         tile += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        const bool ok0 = r0 < n, ok1 = r1 < n;
-        float c[8][4];
+// One message-passing layer fused: Hout = relu([Hin | A~ Hin] W + b) for tiles of kLT
+// rows.  Per tile the block (8 warps) copies the Hin rows into shared memory, forms the
+// neighbour sums A~ Hin of the tile's rows there (warp per row over the CSR of A~, as in
+// k_lm_aggregate_f32), multiplies the [h | m] tile by W on the tensor cores (mma.sync
+// m16n8k16, BF16 in, FP32 accumulate: each warp 16 rows x 32 outputs), applies bias and
+// relu, and writes the BF16 tile with coalesced 16-byte stores.  A~ Hin (rounded to BF16)
+// is also written to Mout when it is non-null (training needs it for the weight gradient).
+constexpr int kLT = 64;        // rows per tile
+constexpr int kAS = kK + 8;    // shared row stride of the [h | m] tile and of W^T (bf16), conflict-free
+constexpr int kOS = kH + 8;    // shared row stride of the output tile
+
+__global__ void __launch_bounds__(256) k_lm_layer(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                  const float* __restrict__ a, const __nv_bfloat16* __restrict__ Hin,
+                                                  const __nv_bfloat16* __restrict__ Wt,
+                                                  const float* __restrict__ bias, int64_t n,
+                                                  __nv_bfloat16* __restrict__ Hout, __nv_bfloat16* __restrict__ Mout) {
+    __shared__ __align__(16) __nv_bfloat16 sW[kH * kAS];   // W^T [out][in]
+    __shared__ __align__(16) __nv_bfloat16 sA[kLT * kAS];  // [h | m] rows of the tile
+    __shared__ __align__(16) __nv_bfloat16 sO[kLT * kOS];  // output rows of the tile
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tg = lane & 3;
+    for (int c = tid; c < kH * (kK / 8); c += blockDim.x) {
+        const int r = c / (kK / 8), part = c % (kK / 8);
+        *reinterpret_cast<uint4*>(sW + r * kAS + part * 8) = reinterpret_cast<const uint4*>(Wt)[c];
+    }
+    const int mt = warp & 3, nh = warp >> 2;  // this warp's 16 rows and 32 outputs of the tile
+    float bcol[4][2];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+    for (int nt = 0; nt < 4; ++nt) {
+        const int cc = nh * 32 + nt * 8 + tg * 2;
+        bcol[nt][0] = bias[cc];
+        bcol[nt][1] = bias[cc + 1];
+    }
+    const int64_t ntiles = (n + kLT - 1) / kLT;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kLT;
+        const int rows = (int)min((int64_t)kLT, n - r0);
+        // 1. the tile's h rows (16-byte loads, coalesced)
+        for (int c = tid; c < kLT * (kH / 8); c += blockDim.x) {
+            const int r = c / (kH / 8), part = c % (kH / 8);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (r < rows) v = reinterpret_cast<const uint4*>(Hin + (r0 + r) * kH)[part];
+            *reinterpret_cast<uint4*>(sA + r * kAS + part * 8) = v;
+        }
+        // 2. neighbour sums, warp per row
+        for (int rr = 0; rr < kLT / 8; ++rr) {
+            const int r = warp * (kLT / 8) + rr;
+            const int64_t i = r0 + r;
+            float s0 = 0.f, s1 = 0.f;
+            if (i < n) {
+                const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+                for (int j0 = rb; j0 < re; j0 += 32) {
+                    const int jj = j0 + lane;
+                    const int cj = jj < re ? __ldg(col + jj) : 0;
+                    const float aj = jj < re ? __ldg(a + jj) : 0.f;
+                    const int cnt = min(32, re - j0);
+                    for (int u = 0; u < cnt; u += kAggUnroll) {
+                        __nv_bfloat162 v[kAggUnroll];
+                        float w[kAggUnroll];
+#pragma unroll
+                        for (int q = 0; q < kAggUnroll; ++q) {
+                            const int c = __shfl_sync(kFull, cj, u + q);
+                            w[q] = __shfl_sync(kFull, aj, u + q);
+                            v[q] = reinterpret_cast<const __nv_bfloat162*>(Hin + (int64_t)c * kH)[lane];
+                        }
+#pragma unroll
+                        for (int q = 0; q < kAggUnroll; ++q) {
+                            s0 += w[q] * __low2float(v[q]);
+                            s1 += w[q] * __high2float(v[q]);
+                        }
+                    }
+                }
+            }
+            const __nv_bfloat162 m2 = __floats2bfloat162_rn(s0, s1);
+            *reinterpret_cast<__nv_bfloat162*>(sA + r * kAS + kH + 2 * lane) = m2;
+            if (Mout && i < n) reinterpret_cast<__nv_bfloat162*>(Mout + i * kH)[lane] = m2;
+        }
+        __syncthreads();
+        // 3. [h | m] (16 rows) x W (32 outputs) on the tensor cores
+        float c[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+        const __nv_bfloat16* arow0 = sA + (mt * 16 + g) * kAS + tg * 2;
+        const __nv_bfloat16* arow1 = arow0 + 8 * kAS;
 #pragma unroll
         for (int kk = 0; kk < kK / 16; ++kk) {
-            const __nv_bfloat16* src = kk < 4 ? Hin : M;
-            const int kc = (kk & 3) * 16 + tg * 2;
-            uint32_t af[4];
-            af[0] = ok0 ? ld_pair(src + r0 * kH + kc) : 0u;
-            af[1] = ok1 ? ld_pair(src + r1 * kH + kc) : 0u;
-            af[2] = ok0 ? ld_pair(src + r0 * kH + kc + 8) : 0u;
-            af[3] = ok1 ? ld_pair(src + r1 * kH + kc + 8) : 0u;
+            uint32_t af[4] = {ld_pair(arow0 + kk * 16), ld_pair(arow1 + kk * 16), ld_pair(arow0 + kk * 16 + 8),
+                              ld_pair(arow1 + kk * 16 + 8)};
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const __nv_bfloat16* wcol = sW + (nt * 8 + g) * kK + kk * 16 + tg * 2;
+            for (int nt = 0; nt < 4; ++nt) {
+                const __nv_bfloat16* wcol = sW + (nh * 32 + nt * 8 + g) * kAS + kk * 16 + tg * 2;
                 uint32_t bfr[2] = {ld_pair(wcol), ld_pair(wcol + 8)};
                 mma16816(c[nt], af, bfr);
             }
         }
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + tg * 2;
-            const float b0 = bias[col], b1 = bias[col + 1];
-            if (ok0)
-                *reinterpret_cast<__nv_bfloat162*>(Hout + r0 * kH + col) =
-                    __floats2bfloat162_rn(fmaxf(c[nt][0] + b0, 0.f), fmaxf(c[nt][1] + b1, 0.f));
-            if (ok1)
-                *reinterpret_cast<__nv_bfloat162*>(Hout + r1 * kH + col) =
-                    __floats2bfloat162_rn(fmaxf(c[nt][2] + b0, 0.f), fmaxf(c[nt][3] + b1, 0.f));
+        for (int nt = 0; nt < 4; ++nt) {
+            const int cc = nh * 32 + nt * 8 + tg * 2;
+            const int ra = mt * 16 + g, rb = ra + 8;
+            *reinterpret_cast<__nv_bfloat162*>(sO + ra * kOS + cc) =
+                __floats2bfloat162_rn(fmaxf(c[nt][0] + bcol[nt][0], 0.f), fmaxf(c[nt][1] + bcol[nt][1], 0.f));
+            *reinterpret_cast<__nv_bfloat162*>(sO + rb * kOS + cc) =
+                __floats2bfloat162_rn(fmaxf(c[nt][2] + bcol[nt][0], 0.f), fmaxf(c[nt][3] + bcol[nt][1], 0.f));
+        }
+        __syncthreads();
+        // 4. output rows (16-byte stores, coalesced)
+        for (int cq = tid; cq < kLT * (kH / 8); cq += blockDim.x) {
+            const int r = cq / (kH / 8), part = cq % (kH / 8);
+            if (r < rows)
+                reinterpret_cast<uint4*>(Hout + (r0 + r) * kH)[part] =
+                    *reinterpret_cast<const uint4*>(sO + r * kOS + part * 8);
         }
     }
 }
@@ -226,14 +289,7 @@ __global__ void k_lm_spmv(Sell S, const float* __restrict__ a, const float* __re
                           float* __restrict__ y, float* acc) {
     float ss = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t sl = i >> 5;
-        const int64_t base = __ldg(S.ptr + sl) + (i & 31);
-        const int w = __ldg(S.w + sl);
-        float s = 0.f;
-        for (int j = 0; j < w; ++j) {
-            const int64_t k = base + 32 * (int64_t)j;
-            s += __ldg(a + k) * x[__ldg(S.col + k)];
-        }
+        float s = sell_row<float, float>(S, a, x, i);
         if (sub) s -= sub[i];
         s = fixed[i] ? 0.f : scale * s;
         y[i] = s;
@@ -485,9 +541,10 @@ int blocks(const fem_pic* ctx, int64_t work, int per_block = 256, int per_sm = 8
     return b < 1 ? 1 : (int)b;
 }
 
-// forward pass from a residual (FP64 or FP32) to c~; scal[4] = s
+// forward pass from a residual (FP64 or FP32) to c~; scal[4] = s.  store_m keeps the
+// neighbour sums of every layer for the backward pass.
 template <typename R>
-fp_status forward(fem_pic* ctx, const R* r, cudaStream_t s) {
+fp_status forward(fem_pic* ctx, const R* r, cudaStream_t s, bool store_m) {
     FieldDev* F = ctx->field;
     LearnedDev* L = F->learned;
     const Sell S{F->se_ptr, F->se_w, F->se_col};
@@ -496,11 +553,10 @@ fp_status forward(fem_pic* ctx, const R* r, cudaStream_t s) {
     k_lm_sumsq<R><<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, L->scal);
     k_lm_input<R><<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, (float)L->n_free, L->scal,
                                                              L->params, L->rt, L->h[0], L->scal + 4);
-    for (int l = 0; l < kLayers; ++l) {
-        k_lm_aggregate<<<blocks(ctx, n * 32), 256, 0, s>>>(S, L->a_sell, L->h[l], n, L->m[l]);
-        k_lm_gemm_fwd<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(
-            L->h[l], L->m[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n, L->h[l + 1]);
-    }
+    for (int l = 0; l < kLayers; ++l)
+        k_lm_layer<<<blocks(ctx, (n + kLT - 1) / kLT * 256, 256, 4), 256, 0, s>>>(
+            F->e_rp, F->e_col, L->a_csr, L->h[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n,
+            L->h[l + 1], store_m ? L->m[l] : nullptr);
     k_lm_head<<<blocks(ctx, n * 32), 256, 0, s>>>(L->h[kLayers], L->params, L->rt, F->edge_fixed, n, L->ct);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
@@ -511,7 +567,7 @@ fp_status train_step(fem_pic* ctx, const float* r, float lr, cudaStream_t s) {
     LearnedDev* L = F->learned;
     const Sell S{F->se_ptr, F->se_w, F->se_col};
     const int64_t n = L->n;
-    fp_status st = forward<float>(ctx, r, s);
+    fp_status st = forward<float>(ctx, r, s, true);
     if (st != FP_OK) return st;
     // loss = ||A~ c~ - r~||^2 / n_free;  dL/dc~ = 2/n_free A~ e
     k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, n, L->e, L->scal + 1);
@@ -525,7 +581,7 @@ fp_status train_step(fem_pic* ctx, const float* r, float lr, cudaStream_t s) {
         k_lm_relu_bwd<<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(L->dh, L->h[l + 1], n, L->dz, gW + kWsz);
         k_lm_gemm_dw<<<(unsigned)((n + rpb - 1) / rpb), 256, 0, s>>>(L->h[l], L->m[l], L->dz, n, rpb, gW);
         k_lm_gemm_dx<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(L->dz, L->Wn[l], n, L->dhd, L->dm);
-        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(S, L->a_sell, L->dm, L->dhd, n, L->dh);
+        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(F->e_rp, F->e_col, L->a_csr, L->dm, L->dhd, n, L->dh);
     }
     k_lm_enc_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dh, L->h[0], L->rt, n, L->grads);
     ++L->adam_t;
@@ -556,7 +612,7 @@ void learned_set_active(FieldDev* F, bool on) {
 void learned_free(FieldDev* F) {
     LearnedDev* L = F ? F->learned : nullptr;
     if (!L) return;
-    void* ptrs[] = {L->a_sell, L->dis, L->params, L->grads, L->am, L->av, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0],
+    void* ptrs[] = {L->a_sell, L->a_csr, L->dis, L->params, L->grads, L->am, L->av, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0],
                     L->Wn[1], L->Wn[2], L->h[0], L->h[1], L->h[2], L->h[3], L->m[0], L->m[1], L->m[2], L->dz, L->dh,
                     L->dhd, L->dm, L->rt, L->ct, L->e, L->dct, L->scal, L->flag, L->r0, L->y, L->samples};
     for (void* p : ptrs)
@@ -582,7 +638,7 @@ fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cud
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 2, 0, 2 * sizeof(float), s));
     k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, x0, F->edge_fixed, n, L->r0, slot, L->scal + 2);
     if (!L->active) return FP_OK;
-    fp_status st = forward<double>(ctx, L->r0, s);
+    fp_status st = forward<double>(ctx, L->r0, s, false);
     if (st != FP_OK) return st;
     k_lm_candidate<<<blocks(ctx, n), 256, 0, s>>>(x0, L->ct, L->dis, L->scal, n, L->y);
     k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, L->y, F->edge_fixed, n, F->tmp, nullptr, L->scal + 3);
@@ -637,6 +693,10 @@ fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacit
                 at[k] = r < n ? (float)(av[k] * dis[r] * dis[col[k]]) : 0.f;
             }
         }
+    std::vector<float> ac(H.e_col.size());
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t j = H.e_rp[i]; j < H.e_rp[i + 1]; ++j)
+            ac[j] = (float)((H.M[j] + 0.25 * F->dt * F->dt * H.S[j]) * dis[i] * dis[H.e_col[j]]);
     // parameters: small random layer weights, identity-like start (the head starts at 0)
     std::vector<float> P(kNParams, 0.f);
     std::mt19937_64 rng(seed);
@@ -654,6 +714,7 @@ fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacit
         return FP_OK;
     };
     if (st == FP_OK) st = up(&L->a_sell, at);
+    if (st == FP_OK) st = up(&L->a_csr, ac);
     if (st == FP_OK) st = up(&L->dis, dis);
     if (st == FP_OK) st = up(&L->params, P);
     std::vector<float> zeros(kNParams, 0.f);
@@ -741,7 +802,7 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
     cudaStream_t s = (cudaStream_t)stream;
     const Sell S{F->se_ptr, F->se_w, F->se_col};
     for (int k = 0; k < count; ++k) {
-        fp_status st = forward<float>(ctx, L->samples + (int64_t)(first + k) * L->n, s);
+        fp_status st = forward<float>(ctx, L->samples + (int64_t)(first + k) * L->n, s, false);
         if (st != FP_OK) return st;
         FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
         k_lm_spmv<<<blocks(ctx, L->n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, L->n, L->e,
@@ -772,7 +833,7 @@ fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out
     if (!ctx || !ctx->field || !ctx->field->learned || !r) return FP_EINVAL;
     LearnedDev* L = ctx->field->learned;
     cudaStream_t s = (cudaStream_t)stream;
-    fp_status st = forward<double>(ctx, r, s);
+    fp_status st = forward<double>(ctx, r, s, false);
     if (st != FP_OK) return st;
     if (ct_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(ct_out, L->ct, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (rt_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(rt_out, L->rt, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));

@@ -515,10 +515,12 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 //
 // One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
 // it (the deposit reduction is a warp collective).  Returns true when the particle has to
-// go to the FP64 walk; the caller queues it.
-__device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, int c, const float x[3], float v[3],
-                                              int64_t p, int64_t n, int32_t nt, float h, float dt, float w,
-                                              int aggregate, float* __restrict__ off, float* __restrict__ vel,
+// go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
+// are read from the shared-memory copy `rec`, the others from global memory.
+__device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const TetHot* rec, int rec_lo,
+                                              int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
+                                              int32_t nt, float h, float dt, float w, int aggregate,
+                                              float* __restrict__ off, float* __restrict__ vel,
                                               float* __restrict__ dG, float* __restrict__ Q,
                                               int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
@@ -533,7 +535,15 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, in
     for (int k = 0; k < 10; ++k) agg[k] = 0.f;
     TetHot H;
     if (c >= 0) {
-        load_hot(hot, c, H);
+        if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
+            const float4* r = reinterpret_cast<const float4*>(rec + (c - rec_lo));
+            float4 t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t[k] = r[k];
+            memcpy(&H, t, sizeof(TetHot));
+        } else {
+            load_hot(hot, c, H);
+        }
         float l[4];
         l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
         l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
@@ -644,30 +654,48 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
             x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
-        const bool slow = fast_particle(hot, c, x, v, p, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
+        const bool slow =
+            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
         warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);   // one global atomic per warp
     }
 }
 
-// Persistent variant with the particle state staged through shared memory by bulk
-// asynchronous copies (TMA): a block owns tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// of kTmaTile consecutive particles and keeps the copies of its next FP_TMA_STAGES - 1
-// tiles in flight while it pushes the current one, so the HBM stream does not wait on
-// the per-particle dependency chain (state -> tet record -> push -> deposit).  Each of
-// the seven state components (cell, off x/y/z, vel x/y/z) of a tile is one bulk copy.
-// Needs n % 4 == 0 and 16-byte aligned cell/off/vel (every copy then starts on a 16-byte
-// boundary and moves a multiple of 16 bytes); the launcher checks this and otherwise
-// runs k_push_fast32.  Every wait on a copy is bounded (ST_TIMEOUT on expiry).
+// Persistent variant with the particle state and the tet records staged through shared
+// memory by bulk asynchronous copies (TMA).  A block owns tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... of kTmaTile consecutive particles:
+//  - the seven state components (cell, off x/y/z, vel x/y/z) of its next tile are copied
+//    while it pushes the current one (kTmaStages buffers);
+//  - halfway through a tile, thread 0 copies the records of a window of kRecMax cells
+//    around the median cell of the next tile (whose state has arrived by then), so a
+//    particle of a cell-sorted tile reads its 128-byte record from shared memory instead
+//    of waiting on L2 at the start of its dependency chain (record -> push -> deposit);
+//    cells outside the window are read from global memory;
+//  - the particles that need the FP64 walk are queued per tile in shared memory and
+//    written out with one global atomic per tile.
+// Needs n % 4 == 0 and 16-byte aligned cell/off/vel (every state copy then starts on a
+// 16-byte boundary and moves a multiple of 16 bytes; records are 128-byte aligned); the
+// launcher checks this and otherwise runs k_push_fast32.  Every wait on a copy is bounded
+// (ST_TIMEOUT on expiry).
 constexpr int kTmaTile = 512;
 constexpr int kTmaThreads = 256;
 constexpr int kTmaSlot = kTmaTile * 4;       // bytes per component per stage
 constexpr int kTmaStageBytes = 7 * kTmaSlot;
 #ifndef FP_TMA_STAGES
-#define FP_TMA_STAGES 3
+#define FP_TMA_STAGES 2
+#endif
+#ifndef FP_REC_MAX
+#define FP_REC_MAX 80
 #endif
 constexpr int kTmaStages = FP_TMA_STAGES;
+constexpr int kRecMax = FP_REC_MAX;           // records per window
+constexpr int kRecBytes = kRecMax * (int)sizeof(TetHot);
+// the window's records are copied as one contiguous block (128-byte stride), so records of
+// different cells read by one warp share banks; each LDS.128 of a warp touching k distinct
+// records takes k shared-memory wavefronts
+constexpr int kTmaSmem = kTmaStages * kTmaStageBytes + 2 * kRecBytes;
 constexpr uint64_t kTmaWaitNs = 2000000000ull;  // 2 s
 static_assert(kTmaSlot % 16 == 0 && kTmaTile % kTmaThreads == 0, "tile shape");
+static_assert(kTmaStageBytes % 128 == 0, "record windows stay 128-byte aligned");
 
 // copies of tile t into stage s (one thread)
 __device__ __forceinline__ void tma_issue(unsigned char* stage, uint64_t* bar, int t, const int32_t* cell,
@@ -689,18 +717,28 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
     int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kTmaStages];
+    __shared__ __align__(8) uint64_t rbars[2];
+    // record windows of the current and the next tile: first cell, count (0: none), and the
+    // number of copies issued into each window so far (its barrier's phase)
+    __shared__ int rec_lo[2], rec_n[2], rec_issued[2];
     // slow particles of a tile, collected in shared memory and written out with one global
     // atomic per tile; two buffers so tile t's queue is copied out during tile t + 1
     __shared__ int32_t tq[2][kTmaTile];
     __shared__ int tq_n[2], tq_base[2];
+    TetHot* recs = reinterpret_cast<TetHot*>(smem + kTmaStages * kTmaStageBytes);
     const int tid = threadIdx.x;
     const float w = (float)qw;
     const int ntiles = (int)((n + kTmaTile - 1) / kTmaTile);
     const int G = gridDim.x;
     if (tid == 0) {
         for (int s = 0; s < kTmaStages; ++s) mbar_init(&bars[s], 1);
+        mbar_init(&rbars[0], 1);
+        mbar_init(&rbars[1], 1);
         mbar_fence_init();
         tq_n[0] = tq_n[1] = 0;
+        rec_n[0] = rec_n[1] = 0;
+        rec_lo[0] = rec_lo[1] = 0;
+        rec_issued[0] = rec_issued[1] = 0;
     }
     __syncthreads();
     int issued = 0;  // tiles issued by this block (kept by thread 0)
@@ -708,25 +746,50 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
         for (int s = 0; s < kTmaStages && (int)blockIdx.x + s * G < ntiles; ++s, ++issued)
             tma_issue(smem + s * kTmaStageBytes, &bars[s], blockIdx.x + s * G, cell, off, vel, n);
     int it = 0;
+    bool failed = false;
     for (int t = blockIdx.x; t < ntiles; t += G, ++it) {
         const int s = it % kTmaStages, qb = it & 1;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / kTmaStages) & 1), kTmaWaitNs);
+        bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / kTmaStages) & 1), kTmaWaitNs);
+        if (ok && rec_n[qb] > 0)
+            ok = mbar_wait_bounded(&rbars[qb], (uint32_t)((rec_issued[qb] - 1) & 1), kTmaWaitNs);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(status, ST_TIMEOUT);
-                // wait (bounded) for the copies still in flight before leaving
-                for (int j = it; j < issued; ++j)
-                    mbar_wait_bounded(&bars[j % kTmaStages], (uint32_t)((j / kTmaStages) & 1), kTmaWaitNs);
-            }
-            return;
+            failed = true;
+            break;
         }
         if (it > 0)  // the previous tile's queue (its global slots were reserved by thread 0)
             for (int i = tid; i < tq_n[qb ^ 1]; i += kTmaThreads) slow_idx[tq_base[qb ^ 1] + i] = tq[qb ^ 1][i];
         const int64_t p0 = (int64_t)t * kTmaTile;
         const int cnt = (int)min((int64_t)kTmaTile, n - p0);
         const unsigned char* st = smem + s * kTmaStageBytes;
+        const TetHot* rec = recs + qb * kRecMax;
+        const int rlo = rec_lo[qb], rn = rec_n[qb];
 #pragma unroll 1
         for (int q = 0; q < kTmaTile / kTmaThreads; ++q) {
+            if (q == 1 && tid == 0) {
+                // halfway: the record window of the next tile, if its state is already here
+                // (window qb ^ 1 was last read by tile it - 1, finished before this tile began)
+                int nn = 0, lo = 0;
+                const int tn = t + G;
+                if (tn < ntiles && it + 1 < issued &&
+                    mbar_try_wait(&bars[(it + 1) % kTmaStages], (uint32_t)(((it + 1) / kTmaStages) & 1))) {
+                    const unsigned char* sn = smem + ((it + 1) % kTmaStages) * kTmaStageBytes;
+                    const int cn = (int)min((int64_t)kTmaTile, n - (int64_t)tn * kTmaTile);
+                    const int cm = reinterpret_cast<const int32_t*>(sn)[cn / 2];
+                    if (cm >= 0 && cm < nt) {
+                        nn = min(kRecMax, nt);
+                        lo = min(max(cm - kRecMax / 2, 0), nt - nn);
+                    }
+                }
+                rec_lo[qb ^ 1] = lo;
+                rec_n[qb ^ 1] = nn;
+                if (nn > 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&rbars[qb ^ 1], (uint32_t)nn * (uint32_t)sizeof(TetHot));
+                    bulk_g2s(recs + (qb ^ 1) * kRecMax, hot + lo, (uint32_t)nn * (uint32_t)sizeof(TetHot),
+                             &rbars[qb ^ 1]);
+                    ++rec_issued[qb ^ 1];
+                }
+            }
             const int j = q * kTmaThreads + tid;
             int c = -1;
             float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
@@ -738,19 +801,32 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
                     v[k] = reinterpret_cast<const float*>(st + (4 + k) * kTmaSlot)[j];
                 }
             }
-            const bool slow = fast_particle(hot, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off,
+                                            vel, dG, Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), tq[qb], &tq_n[qb]);
         }
-        __syncthreads();  // every thread is done with stage s and with tile queue qb ^ 1
+        __syncthreads();  // every thread is done with stage s, record window qb and tile queue qb ^ 1
         if (tid == 0) {
             tq_n[qb ^ 1] = 0;
             tq_base[qb] = tq_n[qb] ? atomicAdd(slow_count, tq_n[qb]) : 0;
+            rec_n[qb] = 0;  // window qb is free for tile it + 2 (set again halfway through tile it + 1)
             if (t + kTmaStages * G < ntiles) {
                 fence_proxy_async_smem();
                 tma_issue(smem + s * kTmaStageBytes, &bars[s], t + kTmaStages * G, cell, off, vel, n);
                 ++issued;
             }
         }
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, ST_TIMEOUT);
+            // wait (bounded) for the copies still in flight before leaving
+            for (int j = it; j < issued; ++j)
+                mbar_wait_bounded(&bars[j % kTmaStages], (uint32_t)((j / kTmaStages) & 1), kTmaWaitNs);
+            for (int b = 0; b < 2; ++b)
+                if (rec_issued[b] > 0) mbar_wait_bounded(&rbars[b], (uint32_t)((rec_issued[b] - 1) & 1), kTmaWaitNs);
+        }
+        return;
     }
     __syncthreads();
     if (it > 0) {  // the last tile's queue
@@ -885,7 +961,7 @@ int grid_for(int64_t n, int sms) {
 // grid-stride kernel when the state arrays are not 16-byte aligned
 fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
                         float* dG, float* Q, cudaStream_t s) {
-    const size_t smem = (size_t)kTmaStages * kTmaStageBytes;
+    const size_t smem = (size_t)kTmaSmem;
     if (ctx->tma_blocks_per_sm == 0) {
         FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;

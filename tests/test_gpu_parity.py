@@ -137,12 +137,17 @@ def test_push_deposit_fp64_parity(agg):
 
 # 50,001 particles: the grid-stride fast kernel (length not a multiple of 4); 50,000 and
 # 1,200,000: the staged (bulk-copy) kernel, the latter with several tiles per block so
-# every pipeline stage is reused
-@pytest.mark.parametrize("npart", [50_001, 50_000, 1_200_000])
-def test_push_deposit_fp32_parity(npart):
+# every pipeline stage and record window is reused; sorted by cell, most records come
+# from the shared-memory windows, unsorted most come from global memory
+@pytest.mark.parametrize("npart,sort", [(50_001, False), (50_000, False), (1_200_000, False), (1_200_000, True)])
+def test_push_deposit_fp32_parity(npart, sort):
     m, orc, lib, sp, e, b = _setup(npart=npart, speed=0.15, prec=F.FP_FP32)
     q, mass, w, dt = sp.q, sp.m, sp.w, 1.0
     d = lib.species(sp.cell, sp.X, sp.V, q, mass, w)
+    if sort:
+        d2 = d.empty_like()
+        lib.sort(d, d2)
+        d = d2
     cell0 = d.cell.cpu().numpy().copy()
     off0 = d.off.cpu().numpy().copy()                 # [3,n] float32
     v0 = d.vel.cpu().numpy().copy()
