@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--solver", default="mixed,mixed",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--poly", default="2,4",
+                    help="Chebyshev degree of the inner preconditioner, Newmark and Gauss systems (1 = Jacobi)")
+    ap.add_argument("--poly-ratio", type=float, default=30.0, help="lambda_max / lambda_low of the Chebyshev interval")
     ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
                     help="learned Newmark correction: trained during warm-up, used if it beats plain CG (auto)")
     ap.add_argument("--learn-samples", type=int, default=48)
@@ -233,6 +236,9 @@ def run_gpu(args):
     if field:
         F.fem_pic_field_setup(lib.h, wl.dt)
         F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
+        pdeg = [int(x) for x in (args.poly.split(",") + args.poly.split(","))[:2]]
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], args.poly_ratio)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], args.poly_ratio)
     E_prev = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
     E_next = torch.zeros_like(E_prev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -262,6 +268,17 @@ def run_gpu(args):
     st = lib.status()
     if st != F.FP_OK:
         raise RuntimeError(f"setup status {st}: {F.fem_pic_last_error(lib.h)}")
+
+    # The measured regions start from this initial state (particles and fields): electrons
+    # stream along B0 and are absorbed by the PEC walls, so a long warm-up would otherwise
+    # leave fewer live particles in the timed steps.  Only live particles are counted.
+    snap_cur = list(cur)
+    snap_sp = [(bufs[k][cur[k]].cell.clone(), bufs[k][cur[k]].off.clone(), bufs[k][cur[k]].vel.clone())
+               for k in range(len(species))]
+    snap_f = [(t_, t_.clone()) for t_ in (e, b, E_prev, dG_prev, Qo)]
+
+    def alive():
+        return sum(int((bufs[k][cur[k]].cell >= 0).sum()) for k in range(len(species)))
 
     def plan(i):
         """(sort now?, buffer index per species before the step) of step i"""
@@ -307,6 +324,17 @@ def run_gpu(args):
 
     state = {"i": 0, "precond": precond}
 
+    def restore():
+        for k in range(len(species)):
+            cur[k] = snap_cur[k]
+            c_, o_, v_ = snap_sp[k]
+            bufs[k][cur[k]].cell.copy_(c_)
+            bufs[k][cur[k]].off.copy_(o_)
+            bufs[k][cur[k]].vel.copy_(v_)
+        for t_, c_ in snap_f:
+            t_.copy_(c_)
+        state["i"] = 0
+
     def eager_step():
         pl = plan(state["i"])
         n_k = enqueue(pl)
@@ -348,6 +376,7 @@ def run_gpu(args):
 
         def compare(pc):
             state["precond"] = pc
+            restore()
             F.fem_pic_profile_read(lib.h, reset=True)
             F.fem_pic_profile_enable(lib.h, True)
             its, fb = [], 0
@@ -365,14 +394,19 @@ def run_gpu(args):
                     "newmark_cg_ms_per_step": ph.get("cg_newmark", (0.0, 1))[0] / args.compare_steps,
                     "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
                     "newmark_iters_mean": statistics.mean(its), "fell_back": fb}
+        # plain Jacobi-CG judges the learned correction: both runs with the Jacobi inner
+        # preconditioner on the Newmark system (the timed steps then use the configured one)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, 1, args.poly_ratio)
         plain = compare(precond)
         learn = compare(F.FP_PC_LEARNED)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], args.poly_ratio)
         use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
         state["precond"] = F.FP_PC_LEARNED if use else precond
         learned = {"samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
                    "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
                    "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
                    "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
+                   "judge": "plain Jacobi-CG (Jacobi inner preconditioner on the Newmark system in both runs)",
                    "model": "3-layer message passing on the edge graph, 64 features, BF16 weights, FP32 accum"}
 
     # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
@@ -396,9 +430,13 @@ def run_gpu(args):
 
     step = graph_step if use_graphs else eager_step
     if use_graphs:                       # capture every shape once, outside the timed region
+        restore()
         for _ in range(2 * args.sort_every + 2):
             step()
         torch.cuda.synchronize()
+    restore()
+    torch.cuda.synchronize()
+    alive0 = alive()
 
     # timed: K steps, each bracketed by events; L2 flushed between steps (outside the events)
     launches = 0
@@ -428,6 +466,9 @@ def run_gpu(args):
     total_ms = float(t.item())
     st = lib.status()
     r = res.cpu().numpy()
+    alive1 = alive()
+    alive_timed = 0.5 * (alive0 + alive1)          # absorption is gradual: mean of start and end
+    restore()
 
     # per-kernel durations: an eager pass of the same steps with the library's event profiler
     F.fem_pic_profile_read(lib.h, reset=True)
@@ -456,6 +497,7 @@ def run_gpu(args):
     F.fem_pic_profile_enable(lib.h, False)
     phases = F.fem_pic_profile_read(lib.h, reset=True)
     push_ms = [a.elapsed_time(z) for a, z in push_ms]
+    alive_eager = 0.5 * (alive0 + alive())
     push_call = (phases.get("prep", (0, 1))[0] + phases.get("push_fast", (0, 1))[0] +
                  phases.get("walk", (0, 1))[0]) / max(1, phases.get("push_fast", (0, 1))[1])
 
@@ -463,6 +505,7 @@ def run_gpu(args):
     # state + fields) from pinned memory, the step, D2H of the results (state + deposits)
     e2e = None
     if not args.no_e2e:
+        restore()
         species = [bufs[k][cur[k]] for k in range(len(species))]
         hs = [(torch.empty_like(s.cell, device="cpu").pin_memory(), torch.empty_like(s.off, device="cpu").pin_memory(),
                torch.empty_like(s.vel, device="cpu").pin_memory()) for s in species]
@@ -510,19 +553,19 @@ def run_gpu(args):
         tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n_part * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
+        e2e = {"value": world * alive0 * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
     out = None
     if rank == 0:
-        value = world * n_part * args.steps / (total_ms * 1e-3)
+        value = world * alive_timed * args.steps / (total_ms * 1e-3)
         avg_push = push_call
-        abytes = algorithmic_bytes(n_part, sizes, 4)
+        abytes = algorithmic_bytes(alive_eager, sizes, 4)
         peak, peak_kind = peak_hbm()
         achieved = abytes / (avg_push * 1e-3) / 1e9
         fast_ms, fast_n = phases.get("push_fast", (float("nan"), 1))
         fast_avg = fast_ms / max(1, fast_n)
-        fbytes = fast_kernel_bytes(n_part, sizes)
+        fbytes = fast_kernel_bytes(alive_eager, sizes)
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         roof_push = {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
@@ -560,7 +603,10 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "mesh": f"cube {wl.mesh.n}^3 x 6 tets, +-10% jitter" if wl.mesh.n > 4
                        else f"cube {wl.mesh.n}^3 x 6 tets", "n_tets": sizes["n_tets"], "n_edges": sizes["n_edges"],
-                       "particles": n_part, "species": len(species), "dt_s": wl.dt, "B0_T": list(wl.B0),
+                       "particles": n_part, "alive_in_timed_steps": alive_timed,
+                       "counted": "particle-steps of live particles only; every measured region starts from the "
+                                  "initial state (particles absorbed by the PEC walls are not counted)",
+                       "species": len(species), "dt_s": wl.dt, "B0_T": list(wl.B0),
                        "sort_every": args.sort_every, "precision": "fp32 particle path, fp64 walk test",
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -577,7 +623,7 @@ def run_gpu(args):
                       "; per-kernel times from an eager pass of the same steps with the library's CUDA-event profiler",
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
             "host_ms_per_step": (th1 - th0) * 1e3 / args.steps,
-            "push_deposit_particle_steps_per_s": n_part / (avg_push * 1e-3),
+            "push_deposit_particle_steps_per_s": alive_eager / (avg_push * 1e-3),
             "field_solve": None if not field else {
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
@@ -586,7 +632,8 @@ def run_gpu(args):
                 "learned_vs_plain": learned,
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
                            "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",
-                           "inner_tol": args.inner_tol},
+                           "inner_tol": args.inner_tol, "inner_precond_degree": {"newmark": pdeg[0], "gauss": pdeg[1]},
+                           "chebyshev_ratio": args.poly_ratio},
                 "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
                 "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,
                 "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",

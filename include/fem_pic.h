@@ -294,6 +294,17 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
  */
 fp_status fem_pic_field_options(fem_pic_t* ctx, int newmark_solver, int gauss_solver, double inner_tol);
 
+/*
+ * Preconditioner of the mixed solver's FP32 inner solves for one system (FP_SYS_NEWMARK or
+ * FP_SYS_GAUSS): degree 1 is Jacobi (the default); degree 2..16 is the Chebyshev polynomial of
+ * that degree in D^-1 A, on the interval [b / ratio, b] with b 5% above a Lanczos estimate of
+ * the largest eigenvalue of D^-1 A (made at fem_pic_field_setup).  A degree-m polynomial costs
+ * m - 1 products and grid barriers per CG iteration and no extra reductions.  Not from the
+ * paper (it defers its solver); the stopping test is unchanged.  FP_EINVAL for a degree
+ * outside [1, 16] or ratio <= 1.
+ */
+fp_status fem_pic_field_poly(fem_pic_t* ctx, int system, int degree, double ratio);
+
 /* Iteration counts and residuals of the last Newmark (info[0]) and Gauss (info[1]) solves.
  * Synchronises the stream. */
 fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* stream);

@@ -19,8 +19,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 256;
-// Cooperative solvers: up to 2 co-resident blocks per SM; the block size is chosen per
-// system from kSolverBlocks at setup.
+// Cooperative solvers: up to 2 co-resident blocks per SM (1 for 1024-thread blocks); the block
+// size is chosen per system from kSolverBlocks at setup.
 constexpr int kSolverPerSm = 2;
 // fraction of the outer threshold an inner solve aims for when that needs less than
 // inner_tol (the FP32 recurrence residual can differ slightly from the FP64 one)
@@ -98,7 +98,7 @@ struct PcgArgs {
 // summed in block order), so all blocks run the same number of grid barriers; the loop is
 // bounded by max_iter.  A p is carried as q = A z + beta q, two barriers per iteration.
 template <int BS>
-__global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg(PcgArgs a) {
+__global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg(PcgArgs a) {
     cg::grid_group g = cg::this_grid();
     __shared__ double sh[4][BS / 32 + 1];
     // rows [r0, r1) of this block: contiguous runs of whole 32-row slices, so the columns a
@@ -197,6 +197,10 @@ struct MixedArgs {
     double* x;
     double* r64;
     float *r, *z, *p, *q, *c;
+    // Chebyshev preconditioner of degree deg (1: plain Jacobi) on [theta - delta, theta + delta]
+    int deg;
+    float theta, delta;
+    float *s, *d0, *d1;    // its residual and two buffers of its step (deg > 1)
     double* red;
     double tol;            // outer: ||b - A x|| <= tol ||ref||
     double inner_tol;      // inner: residual reduction per refinement
@@ -207,8 +211,49 @@ struct MixedArgs {
     int32_t* status;
 };
 
+// z = P(r) for the rows [t0, r1) of this block, P the Chebyshev polynomial of degree deg in
+// B = D^-1 A applied to f = D^-1 r (three-term recurrence on [theta - delta, theta + delta]):
+//   d_0 = f / theta, z = d_0, s = f;
+//   k = 1..deg-1:  s <- s - B d_{k-1},  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) s,
+//                  z <- z + d_k,  rho_0 = delta / theta,  rho_k = 1 / (2 theta / delta - rho_{k-1}).
+// P is positive on (0, theta + delta] and beyond it up to 2 theta, so PCG with it stays a
+// symmetric positive definite method.  Each step's product needs the previous d of every
+// block: one grid barrier per step, d in two buffers.  z is published by the caller's next
+// grid barrier.
+__device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, int64_t t0, int64_t r1, int64_t stride,
+                                                cg::grid_group& g) {
+    const float th = a.theta, de = a.delta, sig = th / de;
+    float rho = 1.f / sig;
+    for (int64_t i = t0; i < r1; i += stride) {
+        const float f = a.dinv32[i] * a.r[i];
+        const float d = f / th;
+        a.d0[i] = d;
+        a.z[i] = d;
+        a.s[i] = f;
+    }
+    float* dc = a.d0;
+    float* dn = a.d1;
+    for (int k = 1; k < a.deg; ++k) {
+        g.sync();
+        const float rn = 1.f / (2.f * sig - rho);
+        const float c1 = rn * rho, c2 = 2.f * rn / de;
+        for (int64_t i = t0; i < r1; i += stride) {
+            const float bd = a.dinv32[i] * sell_row<float, float>(a.S, a.val32, dc, i);
+            const float sk = a.s[i] - bd;
+            const float dk = c1 * dc[i] + c2 * sk;
+            a.s[i] = sk;
+            dn[i] = dk;
+            a.z[i] += dk;
+        }
+        rho = rn;
+        float* t = dc;
+        dc = dn;
+        dn = t;
+    }
+}
+
 template <int BS>
-__global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
     __shared__ double sh[4][BS / 32 + 1];
     __shared__ float shf[3][BS / 32 + 1];
@@ -252,6 +297,7 @@ __global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg_mixed(MixedArgs a) {
             a.r[i] = ri;
             a.z[i] = a.dinv32[i] * ri;
         }
+        if (a.deg > 1) chebyshev_apply(a, t0, r1, stride, g);
         g.sync();
         float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
         for (int64_t i = t0; i < r1; i += stride) {
@@ -274,14 +320,27 @@ __global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg_mixed(MixedArgs a) {
             if (!(pq > 0.f) || total >= a.max_iter) break;
             const float alpha = rz / pq;
             float w2[2] = {0.f, 0.f};  // r.z, r.r
-            for (int64_t i = t0; i < r1; i += stride) {
-                a.c[i] += alpha * a.p[i];
-                const float ri = a.r[i] - alpha * a.q[i];
-                const float zi = a.dinv32[i] * ri;
-                a.r[i] = ri;
-                a.z[i] = zi;
-                w2[0] += ri * zi;
-                w2[1] += ri * ri;
+            if (a.deg <= 1) {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    const float ri = a.r[i] - alpha * a.q[i];
+                    const float zi = a.dinv32[i] * ri;
+                    a.r[i] = ri;
+                    a.z[i] = zi;
+                    w2[0] += ri * zi;
+                    w2[1] += ri * ri;
+                }
+            } else {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    a.r[i] -= alpha * a.q[i];
+                }
+                chebyshev_apply(a, t0, r1, stride, g);
+                for (int64_t i = t0; i < r1; i += stride) {
+                    const float ri = a.r[i];
+                    w2[0] += ri * a.z[i];
+                    w2[1] += ri * ri;
+                }
             }
             grid_sum<BS, 2, float>(w2, part2, g, shf);
             ++total;
@@ -312,13 +371,26 @@ __global__ void __launch_bounds__(BS, kSolverPerSm) k_pcg_mixed(MixedArgs a) {
     }
 }
 
-// Newmark right-hand side and the extrapolated initial guess 2E^n - E^{n-1}
+// Newmark right-hand side and the extrapolated initial guess 2E^n - E^{n-1}, in two passes
+// so that the SELL pass does two FP64 multiply-adds per stored entry:
+//   u = 2E^n - E^{n-1} (also the guess), v = -dt^2 (E^n / 2 + E^{n-1} / 4)   (per row)
+//   rhs = [*eps] u + [*S] v - (dG^{n+1/2} - dG^{n-1/2})                      (SELL)
+__global__ void k_newmark_uv(const uint8_t* __restrict__ fixed, const double* __restrict__ En,
+                             const double* __restrict__ Em, double dt2, int64_t n, double* __restrict__ u,
+                             double* __restrict__ v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double en = En[i], em = Em[i];
+        u[i] = fixed[i] ? 0.0 : 2.0 * en - em;
+        v[i] = -dt2 * (0.5 * en + 0.25 * em);
+    }
+}
+
 template <typename Real>
 __global__ void k_newmark_rhs(Sell Sl, const double* __restrict__ Mv, const double* __restrict__ Sv,
-                              const uint8_t* __restrict__ fixed, const double* __restrict__ En,
-                              const double* __restrict__ Em, const Real* __restrict__ dGh,
-                              const Real* __restrict__ dGp, double dt2, int64_t n, double* __restrict__ rhs,
-                              double* __restrict__ x0) {
+                              const uint8_t* __restrict__ fixed, const double* __restrict__ u,
+                              const double* __restrict__ v, const Real* __restrict__ dGh,
+                              const Real* __restrict__ dGp, int64_t n, double* __restrict__ rhs) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int64_t sl = i >> 5;
@@ -328,23 +400,21 @@ __global__ void k_newmark_rhs(Sell Sl, const double* __restrict__ Mv, const doub
         for (int j0 = 0; j0 < w; j0 += kSellChunk) {   // chunks of independent loads, as in sell_row
             int c[kSellChunk];
 #pragma unroll
-            for (int u = 0; u < kSellChunk; ++u) c[u] = j0 + u < w ? __ldg(Sl.col + base + 32 * (j0 + u)) : -1;
+            for (int q = 0; q < kSellChunk; ++q) c[q] = j0 + q < w ? __ldg(Sl.col + base + 32 * (j0 + q)) : -1;
 #pragma unroll
-            for (int u = 0; u < kSellChunk; ++u) {
-                if (c[u] < 0) continue;
-                const int64_t k = base + 32 * (int64_t)(j0 + u);
-                const double en = En[c[u]], em = Em[c[u]];
-                s += __ldg(Mv + k) * (2.0 * en - em) - dt2 * __ldg(Sv + k) * (0.5 * en + 0.25 * em);
+            for (int q = 0; q < kSellChunk; ++q) {
+                if (c[q] < 0) continue;
+                const int64_t k = base + 32 * (int64_t)(j0 + q);
+                s = fma(__ldg(Mv + k), u[c[q]], s);
+                s = fma(__ldg(Sv + k), v[c[q]], s);
             }
         }
         if (fixed[i]) {
             rhs[i] = 0.0;
-            x0[i] = 0.0;
             continue;
         }
         const double gh = dGh ? as_f64(dGh[i]) : 0.0, gp = dGp ? as_f64(dGp[i]) : 0.0;
         rhs[i] = s - (gh - gp);
-        x0[i] = 2.0 * En[i] - Em[i];
     }
 }
 
@@ -395,12 +465,13 @@ __global__ void k_faraday(const int32_t* __restrict__ fe, const double* __restri
     }
 }
 
-constexpr int kSolverBlocks[3] = {128, 256, 512};
+constexpr int kSolverBlocks[4] = {128, 256, 512, 1024};
 
 void* solver_kernel(int bs, bool fp64) {
     switch (bs) {
         case 128: return fp64 ? (void*)k_pcg<128> : (void*)k_pcg_mixed<128>;
         case 256: return fp64 ? (void*)k_pcg<256> : (void*)k_pcg_mixed<256>;
+        case 1024: return fp64 ? (void*)k_pcg<1024> : (void*)k_pcg_mixed<1024>;
         default: return fp64 ? (void*)k_pcg<512> : (void*)k_pcg_mixed<512>;
     }
 }
@@ -436,6 +507,14 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         }
         m.b = rhs, m.x = x, m.r64 = F->q;
         m.r = F->r32, m.z = F->z32, m.p = F->p32, m.q = F->q32, m.c = F->c32, m.red = F->red;
+        {
+            // Chebyshev interval [b / ratio, b] with b 5% above the Lanczos estimate of lambda_max
+            const double bmax = 1.05 * F->lmax[system], blo = bmax / ctx->poly_ratio[system];
+            m.deg = ctx->poly_deg[system];
+            m.theta = (float)(0.5 * (bmax + blo));
+            m.delta = (float)(0.5 * (bmax - blo));
+            m.s = F->s32, m.d0 = F->d32[0], m.d1 = F->d32[1];
+        }
         m.tol = tol, m.inner_tol = ctx->inner_tol, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
         void* args[] = {&m};
@@ -491,16 +570,16 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
     const int ge = grid_of(ctx, F->ne), gn = grid_of(ctx, F->nn);
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
+        // u = 2E^n - E^{n-1} goes straight into E_next: it is also the solver's starting guess
+        k_newmark_uv<<<ge, kBlock, 0, s>>>(F->edge_fixed, E_cur, E_prev, F->dt * F->dt, F->ne, E_next, F->tmp);
         if (f32)
             k_newmark_rhs<float><<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, F->se_S,
-                                                       F->edge_fixed, E_cur, E_prev,
-                                                       (const float*)dG_half, (const float*)dG_prev, F->dt * F->dt,
-                                                       F->ne, F->rhs, E_next);
+                                                       F->edge_fixed, E_next, F->tmp, (const float*)dG_half,
+                                                       (const float*)dG_prev, F->ne, F->rhs);
         else
             k_newmark_rhs<double><<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, F->se_S,
-                                                        F->edge_fixed, E_cur, E_prev, (const double*)dG_half,
-                                                        (const double*)dG_prev,
-                                                        F->dt * F->dt, F->ne, F->rhs, E_next);
+                                                        F->edge_fixed, E_next, F->tmp, (const double*)dG_half,
+                                                        (const double*)dG_prev, F->ne, F->rhs);
         FP_CUDA_TRY(ctx, cudaGetLastError());
     }
     // learned correction of the guess (with fallback), and/or collection of its residual
@@ -546,7 +625,7 @@ void field_free(fem_pic* ctx) {
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
-                    F->z32, F->p32, F->q32, F->c32, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
+                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
                     F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -580,6 +659,9 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
     for (int64_t i = 0; i < hc.nn; ++i)
         for (int32_t j = H.n_rp[i]; j < H.n_rp[i + 1]; ++j)
             if (H.n_col[j] == i) Ld[i] = 1.0 / H.L[j];
+    // top of the Jacobi-scaled spectra, for the Chebyshev preconditioner of the inner solves
+    F->lmax[FP_SYS_NEWMARK] = jacobi_lambda_max(H.e_rp, H.e_col, A, 40);
+    F->lmax[FP_SYS_GAUSS] = jacobi_lambda_max(H.n_rp, H.n_col, H.L, 40);
     // face -> edges (i,j), (j,k), (i,k)
     std::vector<int32_t> fe(3 * hc.nf);
     {
@@ -675,7 +757,7 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         if (st == FP_OK) st = up(ctx, &F->sn_L32, sL32);
     }
     const int64_t nmax = hc.ne > hc.nn ? hc.ne : hc.nn;
-    float** vecs32[] = {&F->r32, &F->z32, &F->p32, &F->q32, &F->c32};
+    float** vecs32[] = {&F->r32, &F->z32, &F->p32, &F->q32, &F->c32, &F->s32, &F->d32[0], &F->d32[1]};
     for (float** v : vecs32)
         if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)v, nmax * sizeof(float)));
     double** vecs[] = {&F->r, &F->z, &F->p, &F->q, &F->rhs, &F->tmp, &F->delta, &F->qd};
@@ -685,15 +767,13 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
     // block size whose block count (one row per thread) is closest to one block per SM: the
     // grid barriers and reductions cost more with more blocks, the SpMV and vector passes
     // less with more SMs busy.
-    auto pick = [&](int64_t rows, int* bs, int* grid) -> fp_status {
+    auto pick = [&](int64_t rows, int force, int* bs, int* grid) -> fp_status {
         double best = 1e30;
         for (int b : kSolverBlocks) {
             const double d = std::fabs(std::log((double)((rows + b - 1) / b) / (double)ctx->sm_count));
             if (d < best) best = d, *bs = b;
         }
-#ifdef FP_SOLVER_FORCE_BS
-        *bs = FP_SOLVER_FORCE_BS;
-#endif
+        if (force > 0) *bs = force;
         int per_sm = 0, per_sm2 = 0;
         FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel(*bs, true), *bs, 0));
         FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, solver_kernel(*bs, false), *bs, 0));
@@ -706,8 +786,14 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         *grid = (int)std::min<int64_t>(need, (int64_t)ctx->sm_count * per_sm);
         return FP_OK;
     };
-    if (st == FP_OK) st = pick(hc.ne, &F->bs_e, &F->grid_e);
-    if (st == FP_OK) st = pick(hc.nn, &F->bs_n, &F->grid_n);
+#ifndef FP_SOLVER_BS_E
+#define FP_SOLVER_BS_E 0
+#endif
+#ifndef FP_SOLVER_BS_N
+#define FP_SOLVER_BS_N 0
+#endif
+    if (st == FP_OK) st = pick(hc.ne, FP_SOLVER_BS_E, &F->bs_e, &F->grid_e);
+    if (st == FP_OK) st = pick(hc.nn, FP_SOLVER_BS_N, &F->bs_n, &F->grid_n);
     if (st == FP_OK) {
         F->grid = std::max(F->grid_e, F->grid_n);
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));
@@ -727,6 +813,17 @@ fp_status fem_pic_field_options(fem_pic_t* ctx, int newmark_solver, int gauss_so
     ctx->solver_sys[FP_SYS_NEWMARK] = newmark_solver;
     ctx->solver_sys[FP_SYS_GAUSS] = gauss_solver;
     ctx->inner_tol = inner_tol;
+    return FP_OK;
+}
+
+fp_status fem_pic_field_poly(fem_pic_t* ctx, int system, int degree, double ratio) {
+    if (!ctx || (system != FP_SYS_NEWMARK && system != FP_SYS_GAUSS) || degree < 1 || degree > 16 ||
+        !(ratio > 1.0)) {
+        if (ctx) ctx->err = "fem_pic_field_poly: system, degree in [1, 16] or ratio > 1 out of range";
+        return FP_EINVAL;
+    }
+    ctx->poly_deg[system] = degree;
+    ctx->poly_ratio[system] = ratio;
     return FP_OK;
 }
 

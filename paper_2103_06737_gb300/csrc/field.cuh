@@ -15,6 +15,12 @@ struct HostFields {
 
 void assemble_fields(const HostComplex& hc, double eps, double mu, HostFields* hf);
 
+// Largest eigenvalue of D^-1 A (A symmetric CSR with positive diagonal), estimated by
+// `steps` Lanczos steps on D^-1/2 A D^-1/2 from a fixed start vector (a lower bound that
+// converges quickly for the top of the spectrum).
+double jacobi_lambda_max(const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                         const std::vector<double>& val, int steps);
+
 struct LearnedDev;  // learned correction (learned.cu)
 
 struct FieldDev {
@@ -35,6 +41,8 @@ struct FieldDev {
     double *se_M = nullptr, *se_S = nullptr, *se_A = nullptr, *sn_L = nullptr;
     float *se_A32 = nullptr, *sn_L32 = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
+    float *s32 = nullptr, *d32[2] = {nullptr, nullptr};  // Chebyshev preconditioner scratch
+    double lmax[2] = {2.0, 2.0};    // estimated largest eigenvalue of D^-1 A, Newmark and Gauss systems
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
     int grid = 0;                   // co-resident blocks (cooperative launch limit)

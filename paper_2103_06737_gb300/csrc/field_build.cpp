@@ -138,4 +138,71 @@ void assemble_fields(const HostComplex& hc, double eps, double mu, HostFields* h
     }
 }
 
+double jacobi_lambda_max(const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                         const std::vector<double>& val, int steps) {
+    const int64_t n = (int64_t)rp.size() - 1;
+    if (n <= 0) return 1.0;
+    std::vector<double> dis(n, 1.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t j = rp[i]; j < rp[i + 1]; ++j)
+            if (col[j] == i && val[j] > 0.0) dis[i] = 1.0 / std::sqrt(val[j]);
+    std::vector<double> v(n), vp(n, 0.0), w(n), al, be;
+    // fixed start vector with all modes present: 1 + a deterministic perturbation
+    double nv = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        v[i] = 1.0 + 0.5 * std::sin(0.7 * (double)i + 0.3);
+        nv += v[i] * v[i];
+    }
+    nv = std::sqrt(nv);
+    for (double& x : v) x /= nv;
+    double bprev = 0.0;
+    for (int k = 0; k < steps && k < n; ++k) {
+        for (int64_t i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int32_t j = rp[i]; j < rp[i + 1]; ++j) t += val[j] * dis[col[j]] * v[col[j]];
+            w[i] = dis[i] * t;
+        }
+        double a = 0.0;
+        for (int64_t i = 0; i < n; ++i) a += w[i] * v[i];
+        double b = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            w[i] -= a * v[i] + bprev * vp[i];
+            b += w[i] * w[i];
+        }
+        b = std::sqrt(b);
+        al.push_back(a);
+        if (!(b > 1e-12 * std::fabs(a))) break;
+        be.push_back(b);
+        for (int64_t i = 0; i < n; ++i) {
+            vp[i] = v[i];
+            v[i] = w[i] / b;
+        }
+        bprev = b;
+    }
+    // largest eigenvalue of the tridiagonal (al, be) by bisection on Sturm counts
+    const int m = (int)al.size();
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(be[i]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    auto below = [&](double x) {  // number of eigenvalues < x
+        int cnt = 0;
+        double q = 1.0;
+        for (int i = 0; i < m; ++i) {
+            const double off = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+            q = al[i] - x - (i > 0 ? off / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0.0) ++cnt;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-12 * std::fabs(hi); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) == m) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
 }  // namespace fempic

@@ -94,6 +94,8 @@ struct fem_pic {
     int solver_fp64 = 0;                // 1: plain FP64 PCG, 0: mixed-precision refinement
     int solver_sys[2] = {-1, -1};       // per-system override (FP_PC_JACOBI / _FP64), -1 = as requested
     double inner_tol = 1e-5;            // mixed solver: residual reduction of each FP32 inner solve
+    int poly_deg[2] = {1, 1};           // mixed solver: Chebyshev degree of the Jacobi preconditioner per system
+    double poly_ratio[2] = {30.0, 30.0};  // and lambda_max / lambda_low of its interval
     // profiler: events recorded on the launch stream around each kernel when enabled
     bool prof_on = false;
     std::vector<fempic::ProfRec> prof_pending;

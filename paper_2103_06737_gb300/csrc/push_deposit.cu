@@ -222,15 +222,15 @@ __device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* h
     unsigned above = heads & ~((2u << lane) - 1u);
     int end = above ? __ffs(above) - 1 : 32;
     if (heads != kFull) {
+        // only as many shuffle steps as the longest run needs (ceil(log2(longest run)))
+        const unsigned longest = __reduce_max_sync(kFull, head ? (unsigned)(end - lane) : 0u);
+        for (int o = 1; o < (int)longest; o <<= 1) {
+            const bool take = lane + o < end;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            Real x = v[k];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                Real u = __shfl_down_sync(kFull, x, o);
-                if (lane + o < end) x += u;
+            for (int k = 0; k < NV; ++k) {
+                const Real u = __shfl_down_sync(kFull, v[k], o);
+                if (take) v[k] += u;
             }
-            v[k] = x;
         }
     }
     *heads_out = heads;
@@ -507,6 +507,11 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
     }
 }
 
+// A shared-memory window of tet records keeps them 144 bytes apart (one 128-byte bulk copy
+// each), so the same 16-byte chunk of the records of 8 consecutive cells falls on 8 different
+// bank groups when a warp reads them.
+constexpr int kRecStride = (int)sizeof(TetHot) + 16;
+
 // Fast FP32 path: gather through the affine coefficients, Boris, and the end point's
 // barycentric coordinates l^b = l^a + G dx.  If every l^b_k clears a margin larger
 // than the FP32 rounding bound, the FP64 exit test would find no exit either, so the
@@ -516,8 +521,9 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 // One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
 // it (the deposit reduction is a warp collective).  Returns true when the particle has to
 // go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
-// are read from the shared-memory copy `rec`, the others from global memory.
-__device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const TetHot* rec, int rec_lo,
+// are read from the shared-memory window `rec` (records kRecStride bytes apart), the others
+// from global memory.
+__device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
                                               int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
                                               int32_t nt, float h, float dt, float w, int aggregate,
                                               float* __restrict__ off, float* __restrict__ vel,
@@ -536,7 +542,7 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
     TetHot H;
     if (c >= 0) {
         if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
-            const float4* r = reinterpret_cast<const float4*>(rec + (c - rec_lo));
+            const float4* r = reinterpret_cast<const float4*>(rec + (c - rec_lo) * kRecStride);
             float4 t[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) t[k] = r[k];
@@ -665,7 +671,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
 // blockIdx.x + gridDim.x, ... of kTmaTile consecutive particles:
 //  - the seven state components (cell, off x/y/z, vel x/y/z) of its next tile are copied
 //    while it pushes the current one (kTmaStages buffers);
-//  - halfway through a tile, thread 0 copies the records of a window of kRecMax cells
+//  - halfway through a tile, warp 0 copies the records of a window of kRecMax cells
 //    around the median cell of the next tile (whose state has arrived by then), so a
 //    particle of a cell-sorted tile reads its 128-byte record from shared memory instead
 //    of waiting on L2 at the start of its dependency chain (record -> push -> deposit);
@@ -684,18 +690,15 @@ constexpr int kTmaStageBytes = 7 * kTmaSlot;
 #define FP_TMA_STAGES 2
 #endif
 #ifndef FP_REC_MAX
-#define FP_REC_MAX 80
+#define FP_REC_MAX 72
 #endif
 constexpr int kTmaStages = FP_TMA_STAGES;
 constexpr int kRecMax = FP_REC_MAX;           // records per window
-constexpr int kRecBytes = kRecMax * (int)sizeof(TetHot);
-// the window's records are copied as one contiguous block (128-byte stride), so records of
-// different cells read by one warp share banks; each LDS.128 of a warp touching k distinct
-// records takes k shared-memory wavefronts
+constexpr int kRecBytes = kRecMax * kRecStride;
 constexpr int kTmaSmem = kTmaStages * kTmaStageBytes + 2 * kRecBytes;
 constexpr uint64_t kTmaWaitNs = 2000000000ull;  // 2 s
 static_assert(kTmaSlot % 16 == 0 && kTmaTile % kTmaThreads == 0, "tile shape");
-static_assert(kTmaStageBytes % 128 == 0, "record windows stay 128-byte aligned");
+static_assert(kTmaStageBytes % 16 == 0 && kRecStride % 16 == 0, "bulk copy destinations 16-byte aligned");
 
 // copies of tile t into stage s (one thread)
 __device__ __forceinline__ void tma_issue(unsigned char* stage, uint64_t* bar, int t, const int32_t* cell,
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
     // atomic per tile; two buffers so tile t's queue is copied out during tile t + 1
     __shared__ int32_t tq[2][kTmaTile];
     __shared__ int tq_n[2], tq_base[2];
-    TetHot* recs = reinterpret_cast<TetHot*>(smem + kTmaStages * kTmaStageBytes);
+    unsigned char* recs = smem + kTmaStages * kTmaStageBytes;
     const int tid = threadIdx.x;
     const float w = (float)qw;
     const int ntiles = (int)((n + kTmaTile - 1) / kTmaTile);
@@ -761,33 +764,41 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
         const int64_t p0 = (int64_t)t * kTmaTile;
         const int cnt = (int)min((int64_t)kTmaTile, n - p0);
         const unsigned char* st = smem + s * kTmaStageBytes;
-        const TetHot* rec = recs + qb * kRecMax;
+        const unsigned char* rec = recs + qb * kRecBytes;
         const int rlo = rec_lo[qb], rn = rec_n[qb];
 #pragma unroll 1
         for (int q = 0; q < kTmaTile / kTmaThreads; ++q) {
-            if (q == 1 && tid == 0) {
-                // halfway: the record window of the next tile, if its state is already here
-                // (window qb ^ 1 was last read by tile it - 1, finished before this tile began)
+            if (q == 1 && tid < 32) {
+                // halfway: warp 0 copies the record window of the next tile, if its state is
+                // already here (window qb ^ 1 was last read by tile it - 1, finished before this
+                // tile began); lane 0 picks the window, every lane copies some of its records
                 int nn = 0, lo = 0;
-                const int tn = t + G;
-                if (tn < ntiles && it + 1 < issued &&
-                    mbar_try_wait(&bars[(it + 1) % kTmaStages], (uint32_t)(((it + 1) / kTmaStages) & 1))) {
-                    const unsigned char* sn = smem + ((it + 1) % kTmaStages) * kTmaStageBytes;
-                    const int cn = (int)min((int64_t)kTmaTile, n - (int64_t)tn * kTmaTile);
-                    const int cm = reinterpret_cast<const int32_t*>(sn)[cn / 2];
-                    if (cm >= 0 && cm < nt) {
-                        nn = min(kRecMax, nt);
-                        lo = min(max(cm - kRecMax / 2, 0), nt - nn);
+                if (tid == 0) {
+                    const int tn = t + G;
+                    if (tn < ntiles && it + 1 < issued &&
+                        mbar_try_wait(&bars[(it + 1) % kTmaStages], (uint32_t)(((it + 1) / kTmaStages) & 1))) {
+                        const unsigned char* sn = smem + ((it + 1) % kTmaStages) * kTmaStageBytes;
+                        const int cn = (int)min((int64_t)kTmaTile, n - (int64_t)tn * kTmaTile);
+                        const int cm = reinterpret_cast<const int32_t*>(sn)[cn / 2];
+                        if (cm >= 0 && cm < nt) {
+                            nn = min(kRecMax, nt);
+                            lo = min(max(cm - kRecMax / 2, 0), nt - nn);
+                        }
+                    }
+                    rec_lo[qb ^ 1] = lo;
+                    rec_n[qb ^ 1] = nn;
+                    if (nn > 0) {
+                        mbar_arrive_expect_tx(&rbars[qb ^ 1], (uint32_t)nn * (uint32_t)sizeof(TetHot));
+                        ++rec_issued[qb ^ 1];
                     }
                 }
-                rec_lo[qb ^ 1] = lo;
-                rec_n[qb ^ 1] = nn;
+                nn = __shfl_sync(kFull, nn, 0);
+                lo = __shfl_sync(kFull, lo, 0);
                 if (nn > 0) {
                     fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&rbars[qb ^ 1], (uint32_t)nn * (uint32_t)sizeof(TetHot));
-                    bulk_g2s(recs + (qb ^ 1) * kRecMax, hot + lo, (uint32_t)nn * (uint32_t)sizeof(TetHot),
-                             &rbars[qb ^ 1]);
-                    ++rec_issued[qb ^ 1];
+                    for (int k = tid; k < nn; k += 32)
+                        bulk_g2s(recs + (qb ^ 1) * kRecBytes + k * kRecStride, hot + lo + k,
+                                 (uint32_t)sizeof(TetHot), &rbars[qb ^ 1]);
                 }
             }
             const int j = q * kTmaThreads + tid;

@@ -105,6 +105,7 @@ def lib():
             "fem_pic_field_initial": (I32, [P, P, P, D, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_last_info": (I32, [P, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_options": (I32, [P, I32, I32, D]),
+            "fem_pic_field_poly": (I32, [P, I32, I32, D]),
             "fem_pic_whitney0_integrals": (I32, [P, P]),
             "fem_pic_learned_init": (I32, [P, ctypes.c_uint64, I32]),
             "fem_pic_learned_mode": (I32, [P, I32, I32]),
@@ -454,8 +455,13 @@ PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals
           "cg_newmark", "cg_gauss", "learned")
 
 
-def fem_pic_field_options(h, newmark_solver: int = -1, gauss_solver: int = -1, inner_tol: float = 1e-4):
+def fem_pic_field_options(h, newmark_solver: int = -1, gauss_solver: int = -1, inner_tol: float = 1e-5):
     _check(lib().fem_pic_field_options(h, int(newmark_solver), int(gauss_solver), float(inner_tol)), h)
+
+
+def fem_pic_field_poly(h, system: int, degree: int, ratio: float = 30.0):
+    """Chebyshev degree of the inner solves' preconditioner for one system (1 = Jacobi)."""
+    _check(lib().fem_pic_field_poly(h, int(system), int(degree), float(ratio)), h)
 
 
 def fem_pic_profile_enable(h, on: bool = True):

@@ -97,6 +97,42 @@ def test_newmark_solve_matches_direct(setup6, precond):
     lib.close()
 
 
+def test_chebyshev_inner_preconditioner(setup6):
+    """Mixed solver with Chebyshev-Jacobi inner preconditioning: same tolerance and solution,
+    fewer CG iterations on the node Laplacian than plain Jacobi."""
+    m, cx, dt, fo = setup6
+    lib = F.FemPic(m.xyz, m.tets, F.FP_FP64)
+    F.fem_pic_field_setup(lib.h, dt)
+    rng = np.random.default_rng(4)
+    g = rng.uniform(-1, 1, cx.n_nodes) * 1e-20
+    g[cx.boundary_node] = 0.0
+    d_ref = np.zeros(cx.n_nodes)
+    d_ref[fo.inn] = OF._solve(fo.L_II, g[fo.inn])
+    rhs = rng.uniform(-1, 1, cx.n_edges) * 1e-12
+    rhs[cx.boundary_edge] = 0.0
+    x_ref = np.zeros(cx.n_edges)
+    x_ref[fo.ie] = OF._solve(fo.A_II, rhs[fo.ie])
+    iters = {}
+    for deg in (1, 4):
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, deg, 30.0)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, deg, 30.0)
+        d = torch.zeros(cx.n_nodes, dtype=torch.float64, device="cuda")
+        st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_GAUSS, torch.as_tensor(g, device="cuda"), d, tol=1e-10,
+                                         precond=F.FP_PC_JACOBI)
+        assert st == F.FP_OK and info["rel_res"] <= 1e-10
+        assert np.abs(d.cpu().numpy() - d_ref).max() <= 1e-7 * np.abs(d_ref).max()
+        iters[deg] = info["iters"]
+        x = torch.zeros(cx.n_edges, dtype=torch.float64, device="cuda")
+        st, info = F.fem_pic_field_solve(lib.h, F.FP_SYS_NEWMARK, torch.as_tensor(rhs, device="cuda"), x,
+                                         tol=1e-10, precond=F.FP_PC_JACOBI)
+        assert st == F.FP_OK and info["rel_res"] <= 1e-10
+        assert np.abs(x.cpu().numpy() - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+    assert iters[4] < iters[1]
+    with pytest.raises(F.FemPicError):
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, 0, 30.0)
+    lib.close()
+
+
 @pytest.mark.parametrize("prec", [F.FP_FP64, F.FP_FP32])
 def test_field_steps_match_oracle(setup6, prec):
     """Particles and fields together for a few steps; the GPU field step is fed the
