@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--solver", default="mixed,mixed",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
-    ap.add_argument("--poly", default="2,4",
+    ap.add_argument("--poly", default="3,6",
                     help="Chebyshev degree of the inner preconditioner, Newmark and Gauss systems (1 = Jacobi)")
-    ap.add_argument("--poly-ratio", type=float, default=30.0, help="lambda_max / lambda_low of the Chebyshev interval")
+    ap.add_argument("--poly-ratio", default="15,100",
+                    help="lambda_max / lambda_low of the Chebyshev interval, Newmark and Gauss systems")
     ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
                     help="learned Newmark correction: trained during warm-up, used if it beats plain CG (auto)")
     ap.add_argument("--learn-samples", type=int, default=48)
@@ -237,8 +238,9 @@ def run_gpu(args):
         F.fem_pic_field_setup(lib.h, wl.dt)
         F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
         pdeg = [int(x) for x in (args.poly.split(",") + args.poly.split(","))[:2]]
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], args.poly_ratio)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], args.poly_ratio)
+        prat = [float(x) for x in (args.poly_ratio.split(",") + args.poly_ratio.split(","))[:2]]
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], prat[1])
     E_prev = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
     E_next = torch.zeros_like(E_prev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -396,10 +398,10 @@ def run_gpu(args):
                     "newmark_iters_mean": statistics.mean(its), "fell_back": fb}
         # plain Jacobi-CG judges the learned correction: both runs with the Jacobi inner
         # preconditioner on the Newmark system (the timed steps then use the configured one)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, 1, args.poly_ratio)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, 1, prat[0])
         plain = compare(precond)
         learn = compare(F.FP_PC_LEARNED)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], args.poly_ratio)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
         use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
         state["precond"] = F.FP_PC_LEARNED if use else precond
         learned = {"samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
@@ -560,12 +562,14 @@ def run_gpu(args):
     if rank == 0:
         value = world * alive_timed * args.steps / (total_ms * 1e-3)
         avg_push = push_call
-        abytes = algorithmic_bytes(alive_eager, sizes, 4)
+        abytes = algorithmic_bytes(alive_eager / len(species), sizes, 4)   # one push call (one species)
         peak, peak_kind = peak_hbm()
         achieved = abytes / (avg_push * 1e-3) / 1e9
         fast_ms, fast_n = phases.get("push_fast", (float("nan"), 1))
         fast_avg = fast_ms / max(1, fast_n)
-        fbytes = fast_kernel_bytes(alive_eager, sizes)
+        # bytes of one launch: one species' live particles (alive_eager counts all species),
+        # its tet records and deposits
+        fbytes = fast_kernel_bytes(alive_eager / len(species), sizes)
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         roof_push = {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
@@ -623,7 +627,7 @@ def run_gpu(args):
                       "; per-kernel times from an eager pass of the same steps with the library's CUDA-event profiler",
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
             "host_ms_per_step": (th1 - th0) * 1e3 / args.steps,
-            "push_deposit_particle_steps_per_s": alive_eager / (avg_push * 1e-3),
+            "push_deposit_particle_steps_per_s": alive_eager / len(species) / (avg_push * 1e-3),
             "field_solve": None if not field else {
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
@@ -633,7 +637,7 @@ def run_gpu(args):
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
                            "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",
                            "inner_tol": args.inner_tol, "inner_precond_degree": {"newmark": pdeg[0], "gauss": pdeg[1]},
-                           "chebyshev_ratio": args.poly_ratio},
+                           "chebyshev_ratio": {"newmark": prat[0], "gauss": prat[1]}},
                 "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
                 "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,
                 "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",

@@ -45,7 +45,8 @@ struct __align__(128) TetHot {
     float W[3];
     float B0[3];
     float beta;
-    float pad[3];
+    float gsum;      // sum of |g| over g[0..8] (written with the field coefficients)
+    float pad[2];
 };
 static_assert(sizeof(TetHot) == 128, "TetHot layout");
 

@@ -132,6 +132,11 @@ __device__ __forceinline__ void gather(const Geo& G, const TetTopo& T, const dou
 }
 
 // non-relativistic Boris rotation; h = q dt / (2 m)
+// 2 / (1 + tt), correctly rounded (for float via the correctly rounded reciprocal: scaling by
+// 2 commutes with rounding, so the result is the same as the division)
+__device__ __forceinline__ float two_over(float tt) { return 2.f * __frcp_rn(1.f + tt); }
+__device__ __forceinline__ double two_over(double tt) { return 2.0 / (1.0 + tt); }
+
 template <typename Real>
 __device__ __forceinline__ void boris(Real v[3], const Real E[3], const Real B[3], Real h) {
     Real vm[3], t[3], s[3], c[3], vp[3];
@@ -141,7 +146,7 @@ __device__ __forceinline__ void boris(Real v[3], const Real E[3], const Real B[3
         t[i] = h * B[i];
     }
     Real tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    Real f = (Real)2 / ((Real)1 + tt);
+    Real f = two_over(tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) s[i] = f * t[i];
     cross(vm, t, c);
@@ -503,7 +508,10 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
         w[0] = make_float4(hg[6], hg[7], hg[8], E0[0]);
         w[1] = make_float4(E0[1], E0[2], W[0], W[1]);
         w[2] = make_float4(W[2], K[0][0], K[0][1], K[0][2]);
-        w[3] = make_float4(beta, 0.f, 0.f, 0.f);
+        float gsum = 0.f;   // sum of |g| over the 9 stored gradient entries (rounding bound of the fast path)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gsum += fabsf(hg[k]);
+        w[3] = make_float4(beta, gsum, 0.f, 0.f);
     }
 }
 
@@ -575,11 +583,11 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
         d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
         d[0] = -(d[1] + d[2] + d[3]);
-        // rounding bound of l^b in FP32 (with the FP32 copy of the gradients)
-        float S = 1.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) S += fabsf(H.g[k]) * (fabsf(x[k % 3]) + fabsf(dx[k % 3]));
-        const float margin = S * (1.f / 65536.f);
+        // rounding bound of l^b in FP32 (with the FP32 copy of the gradients):
+        // 1 + sum_k |g_k| (|x_k%3| + |dx_k%3|) <= 1 + (sum |g|) max_i (|x_i| + |dx_i|)
+        const float xm = fmaxf(fmaxf(fabsf(x[0]) + fabsf(dx[0]), fabsf(x[1]) + fabsf(dx[1])),
+                               fabsf(x[2]) + fabsf(dx[2]));
+        const float margin = fmaf(H.gsum, xm, 1.f) * (1.f / 65536.f);
         float lbmin = l[0] + d[0];
 #pragma unroll
         for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
@@ -682,7 +690,10 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
 // 16-byte boundary and moves a multiple of 16 bytes; records are 128-byte aligned); the
 // launcher checks this and otherwise runs k_push_fast32.  Every wait on a copy is bounded
 // (ST_TIMEOUT on expiry).
-constexpr int kTmaTile = 512;
+#ifndef FP_TMA_TILE
+#define FP_TMA_TILE 512
+#endif
+constexpr int kTmaTile = FP_TMA_TILE;
 constexpr int kTmaThreads = 256;
 constexpr int kTmaSlot = kTmaTile * 4;       // bytes per component per stage
 constexpr int kTmaStageBytes = 7 * kTmaSlot;
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
         const int rlo = rec_lo[qb], rn = rec_n[qb];
 #pragma unroll 1
         for (int q = 0; q < kTmaTile / kTmaThreads; ++q) {
-            if (q == 1 && tid < 32) {
+            if (q == kTmaTile / kTmaThreads / 2 && tid < 32) {
                 // halfway: warp 0 copies the record window of the next tile, if its state is
                 // already here (window qb ^ 1 was last read by tile it - 1, finished before this
                 // tile began); lane 0 picks the window, every lane copies some of its records
