@@ -201,6 +201,11 @@ struct MixedArgs {
     int deg;
     float theta, delta;
     float *s, *d0, *d1;    // its residual and two buffers of its step (deg > 1)
+    // FP32 operator in shared memory: sm_slots > 0 slots per block (values, then int16
+    // column offsets), copied from val32 / d16 at the start of the launch
+    const int16_t* d16;
+    int sm_slots;
+    int64_t slots_total;
     double* red;
     double tol;            // outer: ||b - A x|| <= tol ||ref||
     double inner_tol;      // inner: residual reduction per refinement
@@ -211,6 +216,39 @@ struct MixedArgs {
     int32_t* status;
 };
 
+// This block's rows of the FP32 operator in shared memory (when the launch holds it there).
+struct SmemOp {
+    const float* v;       // values, SELL order, slots [base, base + count) of the global layout
+    const int16_t* d;     // column - row
+    int64_t base;
+};
+
+// row i of the FP32 operator times x: from shared memory (sm_slots > 0) or from the global
+// SELL copy; chunks of kSellChunk entries as in sell_row
+__device__ __forceinline__ float row_product32(const MixedArgs& a, const SmemOp& so, const float* __restrict__ x,
+                                               int64_t i) {
+    if (a.sm_slots == 0) return sell_row<float, float>(a.S, a.val32, x, i);
+    const int64_t sl = i >> 5;
+    const int64_t base = __ldg(a.S.ptr + sl) - so.base + (i & 31);
+    const int w = __ldg(a.S.w + sl);
+    float s = 0.f;
+    for (int j0 = 0; j0 < w; j0 += kSellChunk) {
+        int c[kSellChunk];
+        float av[kSellChunk], xv[kSellChunk];
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) {
+            const bool in = j0 + u < w;
+            c[u] = in ? (int)i + so.d[base + 32 * (j0 + u)] : -1;
+            av[u] = in ? so.v[base + 32 * (j0 + u)] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? __ldcg(x + c[u]) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) s += av[u] * xv[u];
+    }
+    return s;
+}
+
 // z = P(r) for the rows [t0, r1) of this block, P the Chebyshev polynomial of degree deg in
 // B = D^-1 A applied to f = D^-1 r (three-term recurrence on [theta - delta, theta + delta]):
 //   d_0 = f / theta, z = d_0, s = f;
@@ -220,8 +258,8 @@ struct MixedArgs {
 // symmetric positive definite method.  Each step's product needs the previous d of every
 // block: one grid barrier per step, d in two buffers.  z is published by the caller's next
 // grid barrier.
-__device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, int64_t t0, int64_t r1, int64_t stride,
-                                                cg::grid_group& g) {
+__device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp& so, int64_t t0, int64_t r1,
+                                                int64_t stride, cg::grid_group& g) {
     const float th = a.theta, de = a.delta, sig = th / de;
     float rho = 1.f / sig;
     for (int64_t i = t0; i < r1; i += stride) {
@@ -238,7 +276,7 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, int64_t t0, 
         const float rn = 1.f / (2.f * sig - rho);
         const float c1 = rn * rho, c2 = 2.f * rn / de;
         for (int64_t i = t0; i < r1; i += stride) {
-            const float bd = a.dinv32[i] * sell_row<float, float>(a.S, a.val32, dc, i);
+            const float bd = a.dinv32[i] * row_product32(a, so, dc, i);
             const float sk = a.s[i] - bd;
             const float dk = c1 * dc[i] + c2 * sk;
             a.s[i] = sk;
@@ -263,6 +301,23 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
     const int64_t r0 = min(a.n, (int64_t)blockIdx.x * chunk), r1 = min(a.n, r0 + chunk);
     const int64_t stride = BS;
     const int64_t t0 = r0 + threadIdx.x;
+    // this block's slots of the FP32 operator into shared memory (whole 32-row slices)
+    extern __shared__ __align__(16) unsigned char dsm[];
+    SmemOp so{reinterpret_cast<const float*>(dsm),
+              reinterpret_cast<const int16_t*>(dsm + 4 * (size_t)a.sm_slots), 0};
+    if (a.sm_slots > 0) {
+        const int64_t ns = (a.n + 31) >> 5, s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
+        const int64_t b0 = r0 < r1 ? __ldg(a.S.ptr + s0) : 0;
+        const int64_t b1 = r0 < r1 ? (s1 < ns ? __ldg(a.S.ptr + s1) : a.slots_total) : 0;
+        so.base = b0;
+        float* v = reinterpret_cast<float*>(dsm);
+        int16_t* d = reinterpret_cast<int16_t*>(dsm + 4 * (size_t)a.sm_slots);
+        for (int64_t k = threadIdx.x; k < b1 - b0; k += BS) {
+            v[k] = __ldg(a.val32 + b0 + k);
+            d[k] = __ldg(a.d16 + b0 + k);
+        }
+        __syncthreads();
+    }
     double* part0 = a.red;                               // 4 FP64 values per block
     float* part1 = (float*)(a.red + 4 * gridDim.x);      // 3 FP32 values per block
     float* part2 = part1 + 3 * gridDim.x;                // 2 FP32 values per block
@@ -297,11 +352,11 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             a.r[i] = ri;
             a.z[i] = a.dinv32[i] * ri;
         }
-        if (a.deg > 1) chebyshev_apply(a, t0, r1, stride, g);
+        if (a.deg > 1) chebyshev_apply(a, so, t0, r1, stride, g);
         g.sync();
         float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
         for (int64_t i = t0; i < r1; i += stride) {
-            const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
+            const float w = row_product32(a, so, a.z, i);
             const float zi = a.z[i], ri = a.r[i];
             a.p[i] = zi;
             a.q[i] = w;
@@ -335,7 +390,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
                     a.c[i] += alpha * a.p[i];
                     a.r[i] -= alpha * a.q[i];
                 }
-                chebyshev_apply(a, t0, r1, stride, g);
+                chebyshev_apply(a, so, t0, r1, stride, g);
                 for (int64_t i = t0; i < r1; i += stride) {
                     const float ri = a.r[i];
                     w2[0] += ri * a.z[i];
@@ -349,7 +404,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             rz = w2[0];
             float u2[1] = {0.f};
             for (int64_t i = t0; i < r1; i += stride) {
-                const float w = sell_row<float, float>(a.S, a.val32, a.z, i);
+                const float w = row_product32(a, so, a.z, i);
                 const float pi = a.z[i] + beta * a.p[i];
                 const float qi = w + beta * a.q[i];
                 a.p[i] = pi;
@@ -466,6 +521,9 @@ __global__ void k_faraday(const int32_t* __restrict__ fe, const double* __restri
 }
 
 constexpr int kSolverBlocks[4] = {128, 256, 512, 1024};
+// largest per-block share of an FP32 operator (4-byte values + 2-byte column offsets) that the
+// mixed solver keeps in shared memory
+constexpr size_t kSmemOperatorBytes = 200 * 1024;
 
 void* solver_kernel(int bs, bool fp64) {
     switch (bs) {
@@ -518,10 +576,14 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         m.tol = tol, m.inner_tol = ctx->inner_tol, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
         void* args[] = {&m};
+        m.d16 = system == FP_SYS_NEWMARK ? F->se_d16 : F->sn_d16;
+        m.sm_slots = F->sm_slots[system];
+        m.slots_total = F->slots_total[system];
         PhaseTimer pt(ctx, ph, s);
         const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
         const int bs = system == FP_SYS_NEWMARK ? F->bs_e : F->bs_n;
-        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, false), dim3(grid), dim3(bs), args, 0, s));
+        const size_t smem = (size_t)m.sm_slots * 6;
+        FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, false), dim3(grid), dim3(bs), args, smem, s));
         return FP_OK;
     }
     PcgArgs a;
@@ -625,7 +687,7 @@ void field_free(fem_pic* ctx) {
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
-                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
+                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
                     F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -737,9 +799,29 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         };
         std::vector<int32_t> ptr, w, scol;
         std::vector<int64_t> map;
+        // column offsets col - row as int16 (empty when some offset does not fit)
+        auto offsets16 = [](const std::vector<int32_t>& scol, const std::vector<int32_t>& sptr,
+                            const std::vector<int32_t>& sw) {
+            std::vector<int16_t> d(scol.size());
+            for (size_t sl = 0; sl < sptr.size(); ++sl)
+                for (int64_t j = 0; j < sw[sl]; ++j)
+                    for (int64_t lane = 0; lane < 32; ++lane) {
+                        const int64_t k = sptr[sl] + 32 * j + lane;
+                        const int64_t off = (int64_t)scol[k] - (int64_t)(32 * sl + lane);
+                        if (off < -32768 || off > 32767) return std::vector<int16_t>();
+                        d[k] = (int16_t)off;
+                    }
+            return d;
+        };
         sell(H.e_rp, H.e_col, hc.ne, &ptr, &w, &scol, &map);
         std::vector<double> sM = gather(map, H.M), sS = gather(map, H.S), sA = gather(map, A);
         std::vector<float> sA32(sA.begin(), sA.end());
+        {
+            const std::vector<int16_t> d16 = offsets16(scol, ptr, w);
+            if (!d16.empty() && st == FP_OK) st = up(ctx, &F->se_d16, d16);
+            F->hptr[FP_SYS_NEWMARK] = ptr;
+            F->slots_total[FP_SYS_NEWMARK] = (int64_t)scol.size();
+        }
         if (st == FP_OK) st = up(ctx, &F->se_ptr, ptr);
         if (st == FP_OK) st = up(ctx, &F->se_w, w);
         if (st == FP_OK) st = up(ctx, &F->se_col, scol);
@@ -750,6 +832,12 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         sell(H.n_rp, H.n_col, hc.nn, &ptr, &w, &scol, &map);
         std::vector<double> sL = gather(map, H.L);
         std::vector<float> sL32(sL.begin(), sL.end());
+        {
+            const std::vector<int16_t> d16 = offsets16(scol, ptr, w);
+            if (!d16.empty() && st == FP_OK) st = up(ctx, &F->sn_d16, d16);
+            F->hptr[FP_SYS_GAUSS] = ptr;
+            F->slots_total[FP_SYS_GAUSS] = (int64_t)scol.size();
+        }
         if (st == FP_OK) st = up(ctx, &F->sn_ptr, ptr);
         if (st == FP_OK) st = up(ctx, &F->sn_w, w);
         if (st == FP_OK) st = up(ctx, &F->sn_col, scol);
@@ -794,6 +882,46 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
 #endif
     if (st == FP_OK) st = pick(hc.ne, FP_SOLVER_BS_E, &F->bs_e, &F->grid_e);
     if (st == FP_OK) st = pick(hc.nn, FP_SOLVER_BS_N, &F->bs_n, &F->grid_n);
+    // Shared-memory residency of the FP32 operator in the mixed solver: the slots of a
+    // block's rows (its whole 32-row slices, as the kernel partitions them) must fit; the
+    // launch then stays co-resident with that much shared memory per block.
+    auto residency = [&](int sys, int64_t rows, int bs, int grid) -> fp_status {
+        F->sm_slots[sys] = 0;
+        const int16_t* d16 = sys == FP_SYS_NEWMARK ? F->se_d16 : F->sn_d16;
+        if (!d16 || grid < 1) return FP_OK;
+        const std::vector<int32_t>& ptr = F->hptr[sys];
+        const int64_t ns = (int64_t)ptr.size();
+        const int64_t chunk = ((rows + grid - 1) / grid + 31) & ~(int64_t)31;
+        int64_t most = 0;
+        for (int b = 0; b < grid; ++b) {
+            const int64_t r0 = std::min<int64_t>(rows, (int64_t)b * chunk), r1 = std::min<int64_t>(rows, r0 + chunk);
+            if (r0 >= r1) continue;
+            const int64_t s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
+            const int64_t b1 = s1 < ns ? ptr[s1] : F->slots_total[sys];
+            most = std::max<int64_t>(most, b1 - ptr[s0]);
+        }
+        const int64_t slots = (most + 7) & ~(int64_t)7;        // int16 part starts 16-byte aligned
+        const size_t bytes = (size_t)slots * 6;
+        if (bytes > kSmemOperatorBytes) return FP_OK;
+        void* k = solver_kernel(bs, false);
+        // the attribute is per kernel, shared by every context: set it to the device's limit
+        // (less room for the kernel's static shared memory) so that no context lowers it below
+        // what another one launches with
+        int optin = 0;
+        FP_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        if (bytes + 4096 > (size_t)optin) return FP_OK;
+        FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 4096));
+        int per_sm = 0;
+        FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, bytes));
+        if ((int64_t)per_sm * ctx->sm_count < grid) return FP_OK;
+        F->sm_slots[sys] = (int)slots;
+        return FP_OK;
+    };
+#ifndef FP_SMEM_OPERATOR
+#define FP_SMEM_OPERATOR 1
+#endif
+    if (FP_SMEM_OPERATOR && st == FP_OK) st = residency(FP_SYS_NEWMARK, hc.ne, F->bs_e, F->grid_e);
+    if (FP_SMEM_OPERATOR && st == FP_OK) st = residency(FP_SYS_GAUSS, hc.nn, F->bs_n, F->grid_n);
     if (st == FP_OK) {
         F->grid = std::max(F->grid_e, F->grid_n);
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->red, 9 * (size_t)F->grid * sizeof(double)));

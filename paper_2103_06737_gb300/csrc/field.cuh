@@ -43,6 +43,12 @@ struct FieldDev {
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *c32 = nullptr;
     float *s32 = nullptr, *d32[2] = {nullptr, nullptr};  // Chebyshev preconditioner scratch
     double lmax[2] = {2.0, 2.0};    // estimated largest eigenvalue of D^-1 A, Newmark and Gauss systems
+    // FP32 operators held in shared memory by the mixed solver (per system): column offsets
+    // col - row as int16 in the SELL layout, and the slots per block (0: not held)
+    int16_t *se_d16 = nullptr, *sn_d16 = nullptr;
+    int64_t slots_total[2] = {0, 0};
+    int sm_slots[2] = {0, 0};
+    std::vector<int32_t> hptr[2];   // host copies of the SELL slice starts (Newmark, Gauss)
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
     int grid = 0;                   // co-resident blocks (cooperative launch limit)
