@@ -155,15 +155,19 @@ def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
     return nnz * (val_bytes + 4) + 13 * 8 * n_rows
 
 
-def mixed_solve_bytes(n_rows, nnz, inner_iters, outer):
-    """Minimal DRAM bytes of one mixed-precision solve: per FP32 inner Jacobi-PCG iteration
-    the FP32 operator once (4 B value + 4 B column per nonzero) and 13 FP32 vector passes
-    (update: c, r read+write, p, q, diag^-1 read, z written; search: z, p, q read, p, q
-    written); per refinement the start of the inner solve (one FP32 product, r64 and
-    diag^-1 read, r, z, p, q written) and the FP64 update x += |r| c; outer + 1 FP64
-    residuals b - A x (12 B per nonzero, b and x read, r64 written, c cleared)."""
-    inner = inner_iters * (nnz * 8 + 13 * 4 * n_rows)
-    start = outer * (nnz * 8 + (8 + 4 + 4 * 4) * n_rows + (8 + 8 + 4) * n_rows)
+def mixed_solve_bytes(n_rows, nnz, inner_iters, outer, deg=1):
+    """Minimal DRAM bytes of one mixed-precision solve: per FP32 inner PCG iteration the FP32
+    operator once (4 B value + 4 B column per nonzero) and 13 FP32 vector passes (update: c,
+    r read+write, p, q, diag^-1 read, z written; search: z, p, q read, p, q written); with a
+    Chebyshev preconditioner of degree deg > 1, per application 5 vector passes to start it (r,
+    diag^-1 read; d, z, s written) and deg - 1 further products with 7 vector passes each (d,
+    s, diag^-1, z read; s, d, z written); per refinement the start of the inner solve (one
+    preconditioner application, one FP32 product, r64 and diag^-1 read, r, z, p, q written)
+    and the FP64 update x += |r| c; outer + 1 FP64 residuals b - A x (12 B per nonzero, b and x
+    read, r64 written, c cleared)."""
+    prec = 0 if deg <= 1 else 5 * 4 * n_rows + (deg - 1) * (nnz * 8 + 7 * 4 * n_rows)
+    inner = inner_iters * (nnz * 8 + 13 * 4 * n_rows + prec)
+    start = outer * (prec + nnz * 8 + (8 + 4 + 4 * 4) * n_rows + (8 + 8 + 4) * n_rows)
     resid = (outer + 1) * (nnz * 12 + (8 + 8 + 8 + 4) * n_rows)
     return inner + start + resid
 
@@ -608,9 +612,10 @@ def run_gpu(args):
                 if cnt and t_ms > 0:
                     avg = t_ms / cnt
                     mixed = solv[k_sys] == "mixed"
-                    byt = (mixed_solve_bytes(rows, nz, its, outs) if mixed else
+                    byt = (mixed_solve_bytes(rows, nz, its, outs, pdeg[k_sys]) if mixed else
                            pcg_bytes_per_iter(rows, nz) * max(its, 1))
-                    name = ("k_pcg_mixed (" + ph.split("_")[1] + " system, FP32 inner Jacobi-PCG, FP64 residual)"
+                    name = ("k_pcg_mixed (" + ph.split("_")[1] + f" system, FP32 inner PCG, Chebyshev-Jacobi degree "
+                            f"{pdeg[k_sys]}, FP64 residual)"
                             if mixed else "k_pcg (" + ph.split("_")[1] + " system, FP64)")
                     cand.append((avg, {"kernel": name, "bound": "hbm",
                                        "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
