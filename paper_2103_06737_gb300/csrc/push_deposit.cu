@@ -857,6 +857,179 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
     }
 }
 
+// Warp-specialised variant of the staged push: one producer warp and kWsConsumers consumer
+// warps per block, synchronised only through mbarriers (no block-wide barrier after set-up),
+// so a consumer warp never waits for the slowest warp of its block.  Per stage s (one tile of
+// kWsTile particles in flight per stage):
+//   full[s]  completes when the tile's seven state components have arrived (bulk copies);
+//   recb[s]  completes when the tile's record window has arrived (or at once: no window);
+//   empty[s] completes when every consumer warp is done with the tile (stage, window and
+//            queue of stage s may then be reused).
+// The producer (lane 0 of the last warp) issues the state copies, picks and copies each
+// tile's record window as soon as the tile's state is in shared memory, and after empty[s]
+// writes the tile's queue of slow particles out with one global atomic, then refills the
+// stage.  Same per-particle work as k_push_tma32; same alignment requirements.  Every wait
+// is bounded (ST_TIMEOUT on expiry; a warp that gives up leaves its loop, so the others time
+// out in turn rather than hang).
+#ifndef FP_WS_CONSUMERS
+#define FP_WS_CONSUMERS 7
+#endif
+#ifndef FP_WS_BATCHES
+#define FP_WS_BATCHES 2
+#endif
+#ifndef FP_WS_STAGES
+#define FP_WS_STAGES 2
+#endif
+constexpr int kWsConsumers = FP_WS_CONSUMERS;
+constexpr int kWsBatches = FP_WS_BATCHES;            // 32-particle batches per consumer warp per tile
+constexpr int kWsThreads = 32 * (kWsConsumers + 1);
+constexpr int kWsTile = 32 * kWsBatches * kWsConsumers;
+constexpr int kWsStages = FP_WS_STAGES;
+constexpr int kWsSlot = kWsTile * 4;
+constexpr int kWsStageBytes = 7 * kWsSlot;
+constexpr int kWsRecMax = kWsTile / 7 > 64 ? kWsTile / 7 : 64;   // about 10 particles per cell
+constexpr int kWsRecBytes = kWsRecMax * kRecStride;
+constexpr int kWsSmem = kWsStages * (kWsStageBytes + kWsRecBytes);
+static_assert(kWsSlot % 16 == 0 && kWsStageBytes % 16 == 0 && kWsRecBytes % 16 == 0, "bulk copy alignment");
+
+__device__ __forceinline__ void ws_issue(unsigned char* stage, uint64_t* bar, int t, const int32_t* cell,
+                                         const float* off, const float* vel, int64_t n) {
+    const int64_t p0 = (int64_t)t * kWsTile;
+    const uint32_t bytes = 4u * (uint32_t)min((int64_t)kWsTile, n - p0);
+    mbar_arrive_expect_tx(bar, 7u * bytes);
+    bulk_g2s(stage, cell + p0, bytes, bar);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (1 + k) * kWsSlot, off + k * n + p0, bytes, bar);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kWsSlot, vel + k * n + p0, bytes, bar);
+}
+
+__global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
+    const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
+    float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
+    float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], recb[kWsStages];
+    __shared__ int rec_lo[kWsStages], rec_n[kWsStages];
+    __shared__ int32_t queue[kWsStages][kWsTile];
+    __shared__ int qn[kWsStages];
+    unsigned char* recs = smem + kWsStages * kWsStageBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (int)((n + kWsTile - 1) / kWsTile);
+    const int G = gridDim.x;
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + G - 1) / G : 0;   // tiles of this block
+    if (tid == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kWsConsumers);
+            mbar_init(&recb[s], 1);
+            qn[s] = 0;
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == kWsConsumers) {
+        // ---------------- producer
+        if (lane != 0) return;
+        int issued = 0, recs_issued = 0;
+        bool failed = false;
+        for (int k = 0; k < kWsStages && k < mine; ++k, ++issued)
+            ws_issue(smem + k * kWsStageBytes, &full[k], blockIdx.x + k * G, cell, off, vel, n);
+        // flushes the queue of the k-th tile after its consumers are done, then refills its stage
+        auto retire = [&](int k) -> bool {
+            const int sk = k % kWsStages;
+            if (!mbar_wait_bounded(&empty[sk], (uint32_t)((k / kWsStages) & 1), kTmaWaitNs)) return false;
+            const int m = qn[sk];
+            if (m > 0) {
+                const int base = atomicAdd(slow_count, m);
+                for (int i = 0; i < m; ++i) slow_idx[base + i] = queue[sk][i];
+            }
+            qn[sk] = 0;
+            if (k + kWsStages < mine) {
+                fence_proxy_async_smem();
+                ws_issue(smem + sk * kWsStageBytes, &full[sk], blockIdx.x + (k + kWsStages) * G, cell, off, vel, n);
+                ++issued;
+            }
+            return true;
+        };
+        for (int it = 0; it < mine && !failed; ++it) {
+            const int sk = it % kWsStages;
+            // the record window of tile it, as soon as its state is here
+            if (!mbar_wait_bounded(&full[sk], (uint32_t)((it / kWsStages) & 1), kTmaWaitNs)) {
+                failed = true;
+                break;
+            }
+            const int64_t p0 = (int64_t)(blockIdx.x + it * G) * kWsTile;
+            const int cn = (int)min((int64_t)kWsTile, n - p0);
+            const int cm = reinterpret_cast<const int32_t*>(smem + sk * kWsStageBytes)[cn / 2];
+            int nn = 0, lo = 0;
+            if (cm >= 0 && cm < nt) {
+                nn = min(kWsRecMax, nt);
+                lo = min(max(cm - kWsRecMax / 2, 0), nt - nn);
+            }
+            rec_lo[sk] = lo;
+            rec_n[sk] = nn;
+            if (nn > 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&recb[sk], (uint32_t)nn * (uint32_t)sizeof(TetHot));
+                for (int k = 0; k < nn; ++k)
+                    bulk_g2s(recs + sk * kWsRecBytes + k * kRecStride, hot + lo + k, (uint32_t)sizeof(TetHot),
+                             &recb[sk]);
+            } else {
+                mbar_arrive(&recb[sk]);
+            }
+            ++recs_issued;
+            // the tile before it: retire and refill its stage
+            if (it >= 1 && !retire(it - 1)) failed = true;
+        }
+        if (!failed && mine > 0 && !retire(mine - 1)) failed = true;
+        if (failed) {
+            atomicOr(status, ST_TIMEOUT);
+            // wait (bounded) for the copies still in flight before leaving
+            for (int k = 0; k < issued; ++k)
+                mbar_wait_bounded(&full[k % kWsStages], (uint32_t)((k / kWsStages) & 1), kTmaWaitNs);
+            for (int k = 0; k < recs_issued; ++k)
+                mbar_wait_bounded(&recb[k % kWsStages], (uint32_t)((k / kWsStages) & 1), kTmaWaitNs);
+        }
+        return;
+    }
+    // ---------------- consumers
+    const float w = (float)qw;
+    for (int it = 0; it < mine; ++it) {
+        const int sk = it % kWsStages;
+        const uint32_t par = (uint32_t)((it / kWsStages) & 1);
+        if (!mbar_wait_bounded(&full[sk], par, kTmaWaitNs) || !mbar_wait_bounded(&recb[sk], par, kTmaWaitNs)) {
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        const int rlo = rec_lo[sk], rn = rec_n[sk];
+        const unsigned char* st = smem + sk * kWsStageBytes;
+        const unsigned char* rec = recs + sk * kWsRecBytes;
+        const int64_t p0 = (int64_t)(blockIdx.x + it * G) * kWsTile;
+        const int cnt = (int)min((int64_t)kWsTile, n - p0);
+#pragma unroll 1
+        for (int q = 0; q < kWsBatches; ++q) {
+            const int j = 32 * (warp + q * kWsConsumers) + lane;
+            int c = -1;
+            float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+            if (j < cnt) {
+                c = reinterpret_cast<const int32_t*>(st)[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    x[k] = reinterpret_cast<const float*>(st + (1 + k) * kWsSlot)[j];
+                    v[k] = reinterpret_cast<const float*>(st + (4 + k) * kWsSlot)[j];
+                }
+            }
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off,
+                                            vel, dG, Q, status);
+            warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+}
+
 // FP64 walk of the queued particles (near or across a face).  The end point is
 // recomputed from the stored start offset and the updated velocity with the same
 // FP32 operations as in k_push_fast32.
@@ -1004,6 +1177,29 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
                                                                      (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
                                                                      ctx->d_slow_idx, ctx->d_slow_count,
                                                                      ctx->d_status);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+        return FP_OK;
+    }
+#ifndef FP_PUSH_WS
+#define FP_PUSH_WS 1
+#endif
+    if (FP_PUSH_WS) {   // warp-specialised pipeline
+        if (ctx->ws_blocks_per_sm == 0) {
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_ws32, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+            int per_sm = 0;
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_ws32, kWsThreads, kWsSmem));
+            if (per_sm < 1) {
+                ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
+                return FP_ECUDA;
+            }
+            ctx->ws_blocks_per_sm = per_sm;
+        }
+        const int64_t wtiles = (p->n + kWsTile - 1) / kWsTile;
+        int64_t wgrid = (int64_t)ctx->sm_count * ctx->ws_blocks_per_sm;
+        if (wgrid > wtiles) wgrid = wtiles;
+        k_push_ws32<<<(int)wgrid, kWsThreads, kWsSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
+                                                             p->n, nt, h, dt, qw, agg, dG, Q, ctx->d_slow_idx,
+                                                             ctx->d_slow_count, ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
