@@ -142,7 +142,7 @@ def algorithmic_bytes(n_particles, sizes, real_bytes=4):
 
 
 def fast_kernel_bytes(n_particles, sizes):
-    """Minimal DRAM bytes of one k_push_fast32 launch: cell + off + vel read (28 B) and
+    """Minimal DRAM bytes of one fast-push launch (k_push_ws32): cell + off + vel read (28 B) and
     off + vel written (24 B) per particle, each tet's 128-byte record once, dG and Q
     read-modify-write once (FP32)."""
     return n_particles * 52 + sizes["n_tets"] * 128 + 8 * (sizes["n_edges"] + sizes["n_nodes"])
@@ -596,10 +596,10 @@ def run_gpu(args):
         # its tet records and deposits
         fbytes = fast_kernel_bytes(alive_eager / len(species), sizes)
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
-        roof_push = {"kernel": "k_push_fast32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
+        roof_push = {"kernel": "k_push_ws32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
                      "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg,
-                     "traffic": measured_traffic("k_push_tma32", wl.name)}
+                     "traffic": measured_traffic("k_push_ws32", wl.name)}
         roof = roof_push
         if field:
             nnz = np.zeros(2, dtype=np.int64)
@@ -647,7 +647,7 @@ def run_gpu(args):
                                "+ fp64 residuals"},
             "roofline": roof,
             "roofline_push": roof_push,
-            "roofline_push_call": {"kernels": "k_field_prep32 + k_push_fast32 + k_walk32 (sum of kernel times)",
+            "roofline_push_call": {"kernels": "k_field_prep32 + k_push_ws32 + k_walk32 (sum of kernel times)",
                                    "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                    "frac": achieved / peak, "algorithmic_bytes_per_launch": abytes,
                                    "avg_call_ms": avg_push},
