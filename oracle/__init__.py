@@ -11,6 +11,8 @@ Parts:
                      (Sec. II.A, II.C, IV.B.1)
   fields.py          Hodge matrices, Newmark wave-equation step, Gauss-law projection,
                      Faraday update, residuals (Sec. II.C, IV.A-B)
+  adams.py           fourth-order Adams(-Bashforth) particle mover with start-up, on the
+                     same walk and deposits (Sec. IV.B.2)
 """
 from __future__ import annotations
 
