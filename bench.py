@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--learn-samples", type=int, default=48)
     ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--compare-steps", type=int, default=20)
+    ap.add_argument("--adams-steps", type=int, default=20,
+                    help="timed calls of the fourth-order Adams particle step (0: skip that measurement)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -146,6 +148,13 @@ def fast_kernel_bytes(n_particles, sizes):
     off + vel written (24 B) per particle, each tet's 128-byte record once, dG and Q
     read-modify-write once (FP32)."""
     return n_particles * 52 + sizes["n_tets"] * 128 + 8 * (sizes["n_edges"] + sizes["n_nodes"])
+
+
+def adams_kernel_bytes(n_particles, sizes):
+    """Minimal DRAM bytes of one fourth-order Adams fast-push launch (k_push_adams32): the fast
+    Boris launch's bytes plus the derivative history, 3 slots x (v, a) read (72 B) and the new
+    slot written (24 B) per particle."""
+    return fast_kernel_bytes(n_particles, sizes) + 96 * n_particles
 
 
 def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
@@ -583,6 +592,9 @@ def run_gpu(args):
         e2e = {"value": world * alive0 * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
+    adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
+                                                             Qn, flush_l2, stream, sizes, wl, dev)
+
     out = None
     if rank == 0:
         value = world * alive_timed * args.steps / (total_ms * 1e-3)
@@ -681,12 +693,72 @@ def run_gpu(args):
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": e2e,
+            "adams": adams,
         }
     del lib
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return out, wl
+
+
+def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush_l2, stream, sizes, wl, dev):
+    """The particle step with the fourth-order Adams mover (fem_pic_push_deposit_adams) on the
+    same particles and fields, from the initial state: three start-up steps (orders 1-3), one
+    more warm-up step, then args.adams_steps timed calls at order 4 (L2 flushed between them).
+    dt is a quarter of the workload's (omega_c dt = 0.1 pi), inside the explicit method's
+    stability interval for gyration.  Particles are not re-sorted inside this short run."""
+    import torch
+    restore()
+    sps = [bufs[k][cur[k]] for k in range(len(species))]
+    hist = [torch.zeros((18, s_.n), dtype=torch.float32, device=dev) for s_ in sps]
+    dt = wl.dt / 4
+    step = 0
+
+    def call():
+        nonlocal step
+        dG.zero_()
+        Qn.zero_()
+        for s_, h_ in zip(sps, hist):
+            lib.push_deposit_adams(e, b, s_, h_, step, dt, dG, Qn, flags=F.FP_ACCUMULATE)
+        step += 1
+
+    for _ in range(4):
+        call()
+    torch.cuda.synchronize()
+    F.fem_pic_profile_read(lib.h, reset=True)
+    F.fem_pic_profile_enable(lib.h, True)
+    ev, live = [], []
+    for k in range(args.adams_steps):
+        live.append(sum(int((s_.cell >= 0).sum()) for s_ in sps))
+        flush_l2(1000 + k)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        z.record(stream)
+        ev.append((a, z))
+    torch.cuda.synchronize()
+    F.fem_pic_profile_enable(lib.h, False)
+    ph = F.fem_pic_profile_read(lib.h, reset=True)
+    st = lib.status()
+    ms = sum(a.elapsed_time(z) for a, z in ev)
+    n_live = sum(live) / len(live)
+    f_ms, f_n = ph.get("adams_push", (float("nan"), 1))
+    w_ms, _ = ph.get("adams_walk", (0.0, 1))
+    p_ms, _ = ph.get("prep", (0.0, 1))
+    f_avg = f_ms / max(1, f_n)
+    byt = adams_kernel_bytes(n_live / len(sps), sizes)
+    peak, peak_kind = peak_hbm()
+    ach = byt / (f_avg * 1e-3) / 1e9
+    return {"particle_steps_per_s": sum(live) / (ms * 1e-3), "ms_per_call": ms / args.adams_steps,
+            "order": 4, "dt_s": dt, "timed_calls": args.adams_steps, "alive_mean": n_live, "status": int(st),
+            "kernel_ms_per_call": {"k_field_prep32": p_ms / args.adams_steps, "k_push_adams32": f_avg,
+                                   "k_walk_adams32": w_ms / args.adams_steps},
+            "roofline": {"kernel": "k_push_adams32", "bound": "hbm", "achieved": ach, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes_per_launch": byt, "avg_launch_ms": f_avg,
+                         "traffic": measured_traffic("k_push_adams32", wl.name)}}
 
 
 def cpu_baseline(args, wl, budget_s):

@@ -180,6 +180,36 @@ fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const dou
                                       void* Q, int flags, void* stream);
 
 /*
+ * One particle step of one species with the fourth-order Adams mover (Sec. IV.B.2 moves
+ * the particles with a fourth-order Adams method and leaves its details to another paper;
+ * read here as explicit Adams-Bashforth on dx/dt = v, dv/dt = (q/m)(E(x) + v x B(x))).
+ * x and v are at the same time level (no leapfrog staggering).  Per live particle:
+ * E, B gathered at x^n as in fem_pic_push_deposit; a^n = (q/m)(E + v^n x B);
+ *   x^{n+1} = x^n + dt sum_{j<k} beta_{k,j} v^{n-j},  v^{n+1} = v^n + dt sum_{j<k} beta_{k,j} a^{n-j}
+ * with the k-step Adams-Bashforth coefficients, k = min(step + 1, 4) (orders 1, 2, 3 start
+ * the method); then the walk and the Whitney-1 / Whitney-0 deposits along the straight
+ * segment x^n -> x^{n+1}, exactly as in fem_pic_push_deposit (continuity holds the same way).
+ * The fields are those passed in (time level n) for the whole step.
+ *   hist: device array of 18*n reals (float in FP_FP32 mode, double in FP_FP64 mode),
+ *         caller-owned, planar: slot s (0..2) holds v at planes 6s..6s+2 and a at planes
+ *         6s+3..6s+5 (plane c is hist[c*n .. c*n+n)).  Slot (step - j) mod 3 must hold
+ *         f^{n-j} = (v^{n-j}, a^{n-j}) for j = 1..min(step, 3); the call writes f^n into slot
+ *         step mod 3 of each live particle (other slots are left alone).  Contents are
+ *         ignored on step 0 (nothing needs initialising).
+ *   step: number of earlier Adams steps of these particles (>= 0); the caller counts.
+ * The position sum is rounded operation by operation (beta_0 v^n first, then the older
+ * terms in order, then x^n + dt * sum) without fused multiply-adds.  Absorbed particles
+ * (cell -1) are left alone.  A particle's history must move with it: sort with
+ * fem_pic_sort_columns(..., hist, hist_sorted, 18, ...).  The explicit method is stable for
+ * gyration only while omega_c dt stays below about 0.43.  dG and Q are zeroed first unless
+ * FP_ACCUMULATE.  Errors and asynchrony as fem_pic_push_deposit; hist NULL with n > 0 or
+ * step < 0 returns FP_EINVAL.
+ */
+fp_status fem_pic_push_deposit_adams(fem_pic_t* ctx, const double* e, const double* b,
+                                     const fp_particles* p, void* hist, int64_t step, double dt,
+                                     int max_cross, void* dG, void* Q, int flags, void* stream);
+
+/*
  * Whitney-0 charge of the particles at their current positions:
  * Q_n (+)= q w lambda_n (Sec. IV.B.1, the node charge the continuity equation pairs
  * with dG).  Q is zeroed first unless FP_ACCUMULATE.  Asynchronous.
@@ -195,6 +225,15 @@ fp_status fem_pic_deposit_charge(fem_pic_t* ctx, const fp_particles* p, void* Q,
  * (grown on demand, kept until destroy).  Asynchronous.
  */
 fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* dst, void* stream);
+
+/*
+ * fem_pic_sort that also moves ncols planar columns of per-particle data (device,
+ * float in FP_FP32 mode and double in FP_FP64 mode, column k at cols[k*n .. k*n+n)) with
+ * the same permutation: cols_src -> cols_dst (caller-owned, not aliased).  Used for the
+ * Adams history (ncols = 18).  ncols = 0 is fem_pic_sort.  Asynchronous.
+ */
+fp_status fem_pic_sort_columns(fem_pic_t* ctx, const fp_particles* src, fp_particles* dst,
+                               const void* cols_src, void* cols_dst, int ncols, void* stream);
 
 /*
  * Invariant residuals, sums in FP64 (Sec. II.A continuity, Sec. IV.B.1, Sec. V item 5):
@@ -365,7 +404,8 @@ fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_o
  * records a pair of CUDA events on the launch stream around each of its kernels,
  * by phase: 0 field-coefficient prep, 1 FP32 push, 2 FP64 walk of deferred particles,
  * 3 FP64-mode push, 4 charge deposit, 5 sort, 6 residuals, 7 field-step kernels other than
- * the solvers, 8 Newmark CG, 9 Gauss-law CG, 10 learned correction.
+ * the solvers, 8 Newmark CG, 9 Gauss-law CG, 10 learned correction, 11 Adams push (FP32 fast
+ * path, or the whole FP64-mode step), 12 FP64 walk of deferred Adams particles.
  * fem_pic_profile_read waits for the recorded events, adds their durations to
  * per-phase totals and returns them: ms[16] (milliseconds), count[16] (event pairs);
  * reset != 0 clears the totals.  Either output may be NULL.

@@ -333,6 +333,20 @@ fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
     return launch_push_deposit(ctx, e, b, p, dt, max_cross, dG, Q, flags, (cudaStream_t)stream);
 }
 
+fp_status fem_pic_push_deposit_adams(fem_pic_t* ctx, const double* e, const double* b, const fp_particles* p,
+                                     void* hist, int64_t step, double dt, int max_cross, void* dG, void* Q,
+                                     int flags, void* stream) {
+    if (!ctx || !p || !e || !b || !dG || !Q || p->n < 0 || max_cross < 0 || step < 0 || !(p->m > 0.0)) {
+        if (ctx) ctx->err = "fem_pic_push_deposit_adams: NULL pointer or bad argument";
+        return FP_EINVAL;
+    }
+    if (p->n > 0 && (!p->cell || !p->off || !p->vel || !hist)) {
+        ctx->err = "fem_pic_push_deposit_adams: NULL particle or history array";
+        return FP_EINVAL;
+    }
+    return launch_push_adams(ctx, e, b, p, hist, step, dt, max_cross, dG, Q, flags, (cudaStream_t)stream);
+}
+
 fp_status fem_pic_deposit_charge(fem_pic_t* ctx, const fp_particles* p, void* Q, int flags,
                                  void* stream) {
     if (!ctx || !p || !Q || p->n < 0) return FP_EINVAL;
@@ -348,6 +362,18 @@ fp_status fem_pic_sort(fem_pic_t* ctx, const fp_particles* src, fp_particles* ds
         return FP_EINVAL;
     }
     return launch_sort(ctx, src, dst, (cudaStream_t)stream);
+}
+
+fp_status fem_pic_sort_columns(fem_pic_t* ctx, const fp_particles* src, fp_particles* dst, const void* cols_src,
+                               void* cols_dst, int ncols, void* stream) {
+    if (!ctx || !src || !dst || src->n != dst->n || src->n < 0 || ncols < 0) return FP_EINVAL;
+    if (src->n > 0 && (!src->cell || !src->off || !src->vel || !dst->cell || !dst->off || !dst->vel ||
+                       src->cell == dst->cell || src->off == dst->off || src->vel == dst->vel ||
+                       (ncols > 0 && (!cols_src || !cols_dst || cols_src == cols_dst)))) {
+        ctx->err = "fem_pic_sort_columns: NULL or aliased arrays";
+        return FP_EINVAL;
+    }
+    return launch_sort(ctx, src, dst, (cudaStream_t)stream, cols_src, cols_dst, ncols);
 }
 
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,

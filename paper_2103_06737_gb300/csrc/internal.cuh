@@ -81,7 +81,7 @@ void field_free(fem_pic* ctx);
 // phases timed by the optional profiler (fem_pic_profile_*)
 enum Phase : int { PH_PREP = 0, PH_FAST = 1, PH_WALK = 2, PH_PUSH64 = 3, PH_CHARGE = 4, PH_SORT = 5,
                    PH_RESID = 6, PH_SOLVE = 7, PH_CG_NEWMARK = 8, PH_CG_GAUSS = 9, PH_LEARNED = 10,
-                   PH_COUNT = 16 };
+                   PH_ADAMS = 11, PH_ADAMS_WALK = 12, PH_COUNT = 16 };
 struct ProfRec {
     int phase;
     cudaEvent_t a, b;
@@ -225,9 +225,12 @@ struct PhaseTimer {
 fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, const fp_particles* p,
                               double dt, int max_cross, void* dG, void* Q, int flags,
                               cudaStream_t s);
+fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
+                            int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s);
 fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
                                 cudaStream_t s);
-fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s);
+fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s,
+                      const void* cols_src = nullptr, void* cols_dst = nullptr, int ncols = 0);
 fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const void* Qo,
                            const double* b, double* out, cudaStream_t s);
 }  // namespace fempic

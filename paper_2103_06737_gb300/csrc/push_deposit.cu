@@ -520,6 +520,120 @@ __global__ void __launch_bounds__(256) k_field_prep32(TetHot* __restrict__ hot,
 // bank groups when a warp reads them.
 constexpr int kRecStride = (int)sizeof(TetHot) + 16;
 
+// E and B at a point x (relative to the tet's origin) from the tet's affine field coefficients
+__device__ __forceinline__ void hot_fields(const TetHot& H, const float x[3], float E[3], float B[3]) {
+    E[0] = H.E0[0] + (H.W[1] * x[2] - H.W[2] * x[1]);
+    E[1] = H.E0[1] + (H.W[2] * x[0] - H.W[0] * x[2]);
+    E[2] = H.E0[2] + (H.W[0] * x[1] - H.W[1] * x[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
+}
+
+// Particle movers of the fast path.  move() takes the particle's offset x and velocity v and
+// the fields at x, leaves the new velocity in v and the end offset in xb; commit() stores
+// what the mover keeps besides the offset once the particle is known to stay in its tet.
+//
+// Boris (leapfrog): the velocity is stored at once, since the FP64 walk of a deferred
+// particle recomputes its end point from it.
+struct BorisMover {
+    float h, dt;
+    float* __restrict__ vel;
+    int64_t n;
+    __device__ __forceinline__ void move(int64_t p, const float x[3], float v[3], const float E[3],
+                                         const float B[3], float xb[3]) {
+        boris<float>(v, E, B, h);
+        vel[p] = v[0];
+        vel[n + p] = v[1];
+        vel[2 * n + p] = v[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xb[i] = step_pos(x[i], dt, v[i]);
+    }
+    __device__ __forceinline__ void commit(int64_t) {}
+};
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// One step of the k-th order Adams-Bashforth method (k = order, 1..4) on dx/dt = v,
+// dv/dt = a = (q/m)(E + v x B) (Sec. IV.B.2 names a fourth-order Adams mover; the start-up
+// steps use orders 1..3).  hist holds the derivatives of the three previous steps as 18
+// planar components of n particles: slot s has v at planes 6s..6s+2 and a at 6s+3..6s+5.
+template <typename Real>
+struct AdamsStep {
+    Real* __restrict__ hist;
+    int64_t n;
+    int order;       // 1..4
+    int slot_new;    // slot that takes f^n
+    int slot[3];     // slots of f^{n-1}, f^{n-2}, f^{n-3}
+    Real beta[4];    // coefficients of f^n, f^{n-1}, ...
+    Real dt, qm;
+};
+
+// a^n, v^{n+1} and the end offset x^{n+1}.  The position sum is rounded operation by
+// operation without contraction, so that the end point (which decides the walk) can be
+// reproduced exactly by a CPU program:
+//   s = beta_0 v^n (+ beta_j v^{n-j} for j < k),  x^{n+1} = x^n + dt s.
+template <typename Real>
+__device__ __forceinline__ void adams_update(const AdamsStep<Real>& A, int64_t p, const Real x[3], const Real v[3],
+                                             const Real E[3], const Real B[3], Real a[3], Real v1[3], Real xb[3]) {
+    Real c[3];
+    cross<Real>(v, B, c);
+    Real sx[3], sv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        a[i] = A.qm * (E[i] + c[i]);
+        sx[i] = mul_rn(A.beta[0], v[i]);
+        sv[i] = A.beta[0] * a[i];
+    }
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        if (j >= A.order) break;
+        const int64_t base = (int64_t)6 * A.slot[j - 1] * A.n + p;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            sx[i] = add_rn(sx[i], mul_rn(A.beta[j], A.hist[base + i * A.n]));
+            sv[i] += A.beta[j] * A.hist[base + (3 + i) * A.n];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        xb[i] = add_rn(x[i], mul_rn(A.dt, sx[i]));
+        v1[i] = v[i] + A.dt * sv[i];
+    }
+}
+
+// stores v^{n+1} and f^n = (v^n, a^n) into the history slot that held f^{n-3}
+template <typename Real>
+__device__ __forceinline__ void adams_store(const AdamsStep<Real>& A, Real* __restrict__ vel, int64_t p,
+                                            const Real v0[3], const Real a[3], const Real v1[3]) {
+    const int64_t base = (int64_t)6 * A.slot_new * A.n + p;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        vel[i * A.n + p] = v1[i];
+        A.hist[base + i * A.n] = v0[i];
+        A.hist[base + (3 + i) * A.n] = a[i];
+    }
+}
+
+// Adams (multistep): nothing is stored unless the particle stays in its tet; a deferred
+// particle's whole step is redone by the walk kernel from the unchanged state.
+struct AdamsMover32 {
+    const AdamsStep<float>& A;
+    float* __restrict__ vel;
+    float v0[3], a[3], v1[3];
+    __device__ __forceinline__ void move(int64_t p, const float x[3], float v[3], const float E[3],
+                                         const float B[3], float xb[3]) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v0[i] = v[i];
+        adams_update<float>(A, p, x, v0, E, B, a, v1, xb);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i] = v1[i];
+    }
+    __device__ __forceinline__ void commit(int64_t p) { adams_store<float>(A, vel, p, v0, a, v1); }
+};
+
 // Fast FP32 path: gather through the affine coefficients, Boris, and the end point's
 // barycentric coordinates l^b = l^a + G dx.  If every l^b_k clears a margin larger
 // than the FP32 rounding bound, the FP64 exit test would find no exit either, so the
@@ -531,11 +645,11 @@ constexpr int kRecStride = (int)sizeof(TetHot) + 16;
 // go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
 // are read from the shared-memory window `rec` (records kRecStride bytes apart), the others
 // from global memory.
+template <class Mover>
 __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
                                               int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
-                                              int32_t nt, float h, float dt, float w, int aggregate,
-                                              float* __restrict__ off, float* __restrict__ vel,
-                                              float* __restrict__ dG, float* __restrict__ Q,
+                                              int32_t nt, Mover& mv, float w, int aggregate,
+                                              float* __restrict__ off, float* __restrict__ dG, float* __restrict__ Q,
                                               int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     if (c >= nt) {
@@ -564,21 +678,11 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
         l[0] = 1.f - l[1] - l[2] - l[3];
         float E[3], B[3];
-        E[0] = H.E0[0] + (H.W[1] * x[2] - H.W[2] * x[1]);
-        E[1] = H.E0[1] + (H.W[2] * x[0] - H.W[0] * x[2]);
-        E[2] = H.E0[2] + (H.W[0] * x[1] - H.W[1] * x[0]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
-        boris<float>(v, E, B, h);
-        vel[p] = v[0];
-        vel[n + p] = v[1];
-        vel[2 * n + p] = v[2];
+        hot_fields(H, x, E, B);
         float xb[3], dx[3], d[4];
+        mv.move(p, x, v, E, B, xb);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            xb[i] = step_pos(x[i], dt, v[i]);
-            dx[i] = xb[i] - x[i];
-        }
+        for (int i = 0; i < 3; ++i) dx[i] = xb[i] - x[i];
         d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
         d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
         d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
@@ -603,6 +707,7 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             off[p] = xb[0];
             off[n + p] = xb[1];
             off[2 * n + p] = xb[2];
+            mv.commit(p);
             key = c;
             if (!aggregate) {
 #pragma unroll
@@ -654,6 +759,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float w = (float)qw;
+    BorisMover bm{h, dt, vel, n};
     int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     int c_nx = base + lane < n ? __ldg(cell + base + lane) : -1;
     for (; base < n; base += stride) {
@@ -669,7 +775,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
         const bool slow =
-            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, h, dt, w, aggregate, off, vel, dG, Q, status);
+            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, bm, w, aggregate, off, dG, Q, status);
         warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);   // one global atomic per warp
     }
 }
@@ -742,6 +848,7 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
     unsigned char* recs = smem + kTmaStages * kTmaStageBytes;
     const int tid = threadIdx.x;
     const float w = (float)qw;
+    BorisMover bm{h, dt, vel, n};
     const int ntiles = (int)((n + kTmaTile - 1) / kTmaTile);
     const int G = gridDim.x;
     if (tid == 0) {
@@ -823,8 +930,8 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
                     v[k] = reinterpret_cast<const float*>(st + (4 + k) * kTmaSlot)[j];
                 }
             }
-            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off,
-                                            vel, dG, Q, status);
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, bm, w, aggregate, off, dG,
+                                            Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), tq[qb], &tq_n[qb]);
         }
         __syncthreads();  // every thread is done with stage s, record window qb and tile queue qb ^ 1
@@ -996,6 +1103,7 @@ __global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
     }
     // ---------------- consumers
     const float w = (float)qw;
+    BorisMover bm{h, dt, vel, n};
     for (int it = 0; it < mine; ++it) {
         const int sk = it % kWsStages;
         const uint32_t par = (uint32_t)((it / kWsStages) & 1);
@@ -1021,8 +1129,8 @@ __global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
                     v[k] = reinterpret_cast<const float*>(st + (4 + k) * kWsSlot)[j];
                 }
             }
-            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, h, dt, w, aggregate, off,
-                                            vel, dG, Q, status);
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, bm, w, aggregate, off, dG,
+                                            Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
         }
         __syncwarp();
@@ -1064,6 +1172,145 @@ __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
         cell[p] = end_cell;
 #pragma unroll
         for (int k = 0; k < 3; ++k) off[k * n + p] = d2f(end_off[k]);
+    }
+}
+
+// ---------------------------------------------------------------- Adams mover
+// FP32 Adams step, fast path: the Boris kernel's structure with the Adams mover.  A particle
+// whose end point clears the rounding margin is finished here (state, history, deposits);
+// the others are queued unchanged for k_walk_adams32.
+__global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_adams32(
+    const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
+    float* __restrict__ vel, AdamsStep<float> A, int32_t nt, double qw, int aggregate,
+    float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = A.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float w = (float)qw;
+    AdamsMover32 am{A, vel};
+    int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    int c_nx = base + lane < n ? __ldg(cell + base + lane) : -1;
+    for (; base < n; base += stride) {
+        const int64_t p = base + lane;
+        const int c = p < n ? c_nx : -1;
+        {
+            const int64_t q = p + stride;
+            c_nx = q < n ? __ldg(cell + q) : -1;
+        }
+        float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+        if (c >= 0 && c < nt) {
+            x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
+            v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
+        }
+        const bool slow =
+            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, am, w, aggregate, off, dG, Q, status);
+        warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);
+    }
+}
+
+// FP32 Adams step of the queued particles: the same fields and update as the fast path
+// (from the unchanged state), then the FP64 walk along x^n -> x^{n+1}.
+__global__ void __launch_bounds__(128) k_walk_adams32(const TetHot* __restrict__ hot,
+                                                      const TetGeo* __restrict__ geo,
+                                                      const TetTopo* __restrict__ topo,
+                                                      int32_t* __restrict__ cell, float* __restrict__ off,
+                                                      float* __restrict__ vel, AdamsStep<float> A, double qw,
+                                                      int max_cross, float* __restrict__ dG,
+                                                      float* __restrict__ Q,
+                                                      const int32_t* __restrict__ slow_idx,
+                                                      const int32_t* __restrict__ slow_count,
+                                                      int32_t* __restrict__ status) {
+    const int64_t n = A.n;
+    const int64_t m = *slow_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int64_t p = slow_idx[i];
+        if (p < 0 || p >= n) {
+            atomicOr(status, ST_INVAL);
+            continue;
+        }
+        const int c = cell[p];
+        TetHot H;
+        load_hot(hot, c, H);
+        float x[3], v[3], E[3], B[3], a[3], v1[3], xb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            x[k] = off[k * n + p];
+            v[k] = vel[k * n + p];
+        }
+        hot_fields(H, x, E, B);
+        adams_update<float>(A, p, x, v, E, B, a, v1, xb);
+        adams_store<float>(A, vel, p, v, a, v1);
+        double xa[3], xe[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            xa[k] = f2d(x[k]);
+            xe[k] = f2d(xb[k]);
+        }
+        int end_cell;
+        double end_off[3];
+        walk_fp64<float>(geo, topo, c, xa, xe, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
+        cell[p] = end_cell;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) off[k * n + p] = d2f(end_off[k]);
+    }
+}
+
+// FP64 Adams step: FP64 gather (Whitney-1/2 on the tet), the Adams update and the FP64 walk
+// with warp-aggregated deposits of the particles that stay in their tet.
+__global__ void __launch_bounds__(256) k_push_adams64(
+    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ e,
+    const double* __restrict__ b, int32_t* __restrict__ cell, double* __restrict__ off,
+    double* __restrict__ vel, AdamsStep<double> A, int32_t nt, double qw, int max_cross, int aggregate,
+    double* __restrict__ dG, double* __restrict__ Q, int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = A.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t p = base + lane;
+        int c = p < n ? cell[p] : -1;
+        if (c >= nt) {
+            atomicOr(status, ST_INVAL);
+            c = -1;
+        }
+        int key = -1;
+        double agg[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) agg[k] = 0.0;
+        TetTopo T;
+        if (c >= 0) {
+            Geo G;
+            load_geo(geo, c, G);
+            load_topo(topo, c, T);
+            double x[3] = {off[p], off[n + p], off[2 * n + p]};
+            double v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
+            double la[4], E[3], B[3], a[3], v1[3], xb[3];
+            bary(G, x, la);
+            gather<double>(G, T, e, b, la, E, B);
+            adams_update<double>(A, p, x, v, E, B, a, v1, xb);
+            adams_store<double>(A, vel, p, v, a, v1);
+            int end_cell;
+            double end_off[3];
+            if (walk_fp64<double>(geo, topo, c, x, xb, qw, max_cross, dG, Q, status, aggregate ? agg : nullptr,
+                                  &end_cell, end_off))
+                key = c;
+            cell[p] = end_cell;
+            off[p] = end_off[0];
+            off[n + p] = end_off[1];
+            off[2 * n + p] = end_off[2];
+        }
+        if (aggregate) {
+            unsigned heads;
+            int end;
+            warp_run_reduce<double, 10>(key, agg, &heads, &end);
+            if (((heads >> lane) & 1u) && key >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], agg[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], agg[6 + k]);
+            }
+        }
     }
 }
 
@@ -1215,6 +1462,25 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
 
 }  // namespace
 
+namespace {
+// the FP32 path's queue of particles deferred to the FP64 walk: at least n entries, count 0
+fp_status slow_queue(fem_pic* ctx, int64_t n, const char* who, cudaStream_t s) {
+    if (n > INT32_MAX) {
+        ctx->err = std::string(who) + ": more than 2^31-1 particles in one call";
+        return FP_EINVAL;
+    }
+    if (ctx->slow_cap < n) {
+        if (ctx->d_slow_idx) FP_CUDA_TRY(ctx, cudaFree(ctx->d_slow_idx));
+        ctx->d_slow_idx = nullptr;
+        ctx->slow_cap = 0;
+        FP_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->d_slow_idx, n * sizeof(int32_t)));
+        ctx->slow_cap = n;
+    }
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_slow_count, 0, sizeof(int32_t), s));
+    return FP_OK;
+}
+}  // namespace
+
 fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, const fp_particles* p,
                               double dt, int max_cross, void* dG, void* Q, int flags,
                               cudaStream_t s) {
@@ -1231,18 +1497,8 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
     const int grid = grid_for(p->n, ctx->sm_count);
     const int32_t nt = (int32_t)ctx->hc.nt;
     if (f32) {
-        if (p->n > INT32_MAX) {
-            ctx->err = "fem_pic_push_deposit: more than 2^31-1 particles in one call";
-            return FP_EINVAL;
-        }
-        if (ctx->slow_cap < p->n) {
-            if (ctx->d_slow_idx) FP_CUDA_TRY(ctx, cudaFree(ctx->d_slow_idx));
-            ctx->d_slow_idx = nullptr;
-            ctx->slow_cap = 0;
-            FP_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->d_slow_idx, p->n * sizeof(int32_t)));
-            ctx->slow_cap = p->n;
-        }
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_slow_count, 0, sizeof(int32_t), s));
+        const fp_status sq = slow_queue(ctx, p->n, "fem_pic_push_deposit", s);
+        if (sq != FP_OK) return sq;
         {
             PhaseTimer pt(ctx, PH_PREP, s);
             k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e, b, ctx->hc.nt);
@@ -1264,6 +1520,70 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                                                     (double*)p->off, (double*)p->vel, p->n, nt, qmdt2, dt,
                                                     qw, max_cross, agg, (double*)dG, (double*)Q,
                                                     ctx->d_status);
+    }
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
+                            int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s) {
+    const bool f32 = ctx->precision == FP_FP32;
+    const size_t rs = f32 ? 4 : 8;
+    if (!(flags & FP_ACCUMULATE)) {
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
+    }
+    if (p->n == 0) return FP_OK;
+    // Adams-Bashforth coefficients of f^n, f^{n-1}, ... for orders 1..4
+    static const double kBeta[4][4] = {{1.0, 0.0, 0.0, 0.0},
+                                       {3.0 / 2.0, -1.0 / 2.0, 0.0, 0.0},
+                                       {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0.0},
+                                       {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0}};
+    const int order = step < 3 ? (int)step + 1 : 4;
+    const int slot_new = (int)(step % 3);
+    int slot[3];
+    for (int j = 1; j <= 3; ++j) slot[j - 1] = (int)(((step - j) % 3 + 3) % 3);
+    const double qm = p->q / p->m, qw = p->q * p->w;
+    const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
+    const int32_t nt = (int32_t)ctx->hc.nt;
+    if (f32) {
+        AdamsStep<float> A;
+        A.hist = (float*)hist, A.n = p->n, A.order = order, A.slot_new = slot_new;
+        for (int j = 0; j < 3; ++j) A.slot[j] = slot[j];
+        for (int j = 0; j < 4; ++j) A.beta[j] = (float)kBeta[order - 1][j];
+        A.dt = (float)dt, A.qm = (float)qm;
+        const fp_status sq = slow_queue(ctx, p->n, "fem_pic_push_deposit_adams", s);
+        if (sq != FP_OK) return sq;
+        {
+            PhaseTimer pt(ctx, PH_PREP, s);
+            k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces,
+                                                                                        e, b, ctx->hc.nt);
+        }
+        {
+            PhaseTimer pt(ctx, PH_ADAMS, s);
+            k_push_adams32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
+                                                                          (float*)p->vel, A, nt, qw, agg, (float*)dG,
+                                                                          (float*)Q, ctx->d_slow_idx,
+                                                                          ctx->d_slow_count, ctx->d_status);
+        }
+        {
+            PhaseTimer pt(ctx, PH_ADAMS_WALK, s);
+            k_walk_adams32<<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_hot, ctx->d_geo, ctx->d_topo, p->cell,
+                                                             (float*)p->off, (float*)p->vel, A, qw, max_cross,
+                                                             (float*)dG, (float*)Q, ctx->d_slow_idx,
+                                                             ctx->d_slow_count, ctx->d_status);
+        }
+    } else {
+        AdamsStep<double> A;
+        A.hist = (double*)hist, A.n = p->n, A.order = order, A.slot_new = slot_new;
+        for (int j = 0; j < 3; ++j) A.slot[j] = slot[j];
+        for (int j = 0; j < 4; ++j) A.beta[j] = kBeta[order - 1][j];
+        A.dt = dt, A.qm = qm;
+        PhaseTimer pt(ctx, PH_ADAMS, s);
+        k_push_adams64<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
+                                                                      (double*)p->off, (double*)p->vel, A, nt, qw,
+                                                                      max_cross, agg, (double*)dG, (double*)Q,
+                                                                      ctx->d_status);
     }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;

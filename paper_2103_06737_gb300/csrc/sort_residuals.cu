@@ -130,6 +130,20 @@ __global__ void k_sort_scatter(const int32_t* __restrict__ cell, const Real* __r
     }
 }
 
+// extra planar columns (ncols x n) moved with the same permutation as the particle state
+template <typename Real>
+__global__ void k_sort_scatter_cols(const int32_t* __restrict__ cell, int64_t n, int32_t nt,
+                                    const int32_t* __restrict__ start, const int32_t* __restrict__ rank,
+                                    const Real* __restrict__ src, Real* __restrict__ dst, int ncols) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const int c = cell[p];
+        const int key = (c >= 0 && c < nt) ? c : nt;
+        const int64_t q = (int64_t)start[key] + rank[p];
+        for (int k = 0; k < ncols; ++k) dst[k * n + q] = src[k * n + p];
+    }
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
     // for non-negative doubles the IEEE bit pattern orders like the value
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
@@ -254,15 +268,21 @@ __global__ void __launch_bounds__(256) k_residuals(const int32_t* __restrict__ p
 }
 
 template <typename Real>
-void scatter(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s) {
+void scatter(fem_pic* ctx, const fp_particles* src, fp_particles* dst, const void* cs, void* cd, int ncols,
+             cudaStream_t s) {
     k_sort_scatter<Real><<<grid_cap(src->n, 256, 8, ctx->sm_count), 256, 0, s>>>(
         src->cell, (const Real*)src->off, (const Real*)src->vel, src->n, (int32_t)ctx->hc.nt,
         ctx->d_sort_count, ctx->d_sort_rank, dst->cell, (Real*)dst->off, (Real*)dst->vel);
+    if (ncols > 0)
+        k_sort_scatter_cols<Real><<<grid_cap(src->n, 256, 8, ctx->sm_count), 256, 0, s>>>(
+            src->cell, src->n, (int32_t)ctx->hc.nt, ctx->d_sort_count, ctx->d_sort_rank, (const Real*)cs,
+            (Real*)cd, ncols);
 }
 
 }  // namespace
 
-fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s) {
+fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s,
+                      const void* cols_src, void* cols_dst, int ncols) {
     const int64_t n = src->n, m = ctx->hc.nt + 1;
     const int64_t tiles = (m + kScanTile - 1) / kScanTile;
     if (n == 0) return FP_OK;
@@ -289,9 +309,9 @@ fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, 
     k_scan_sums<<<1, kScanTile, 0, s>>>(ctx->d_sort_block, tiles);
     k_scan_add<<<(unsigned)tiles, kScanTile, 0, s>>>(ctx->d_sort_count, m, ctx->d_sort_block);
     if (ctx->precision == FP_FP32)
-        scatter<float>(ctx, src, dst, s);
+        scatter<float>(ctx, src, dst, cols_src, cols_dst, ncols, s);
     else
-        scatter<double>(ctx, src, dst, s);
+        scatter<double>(ctx, src, dst, cols_src, cols_dst, ncols, s);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }

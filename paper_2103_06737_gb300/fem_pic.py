@@ -95,6 +95,10 @@ def lib():
             "fem_pic_push_deposit": (I32, [P, P, P, ctypes.POINTER(FPParticles), D, I32, P, P, I32, P]),
             "fem_pic_deposit_charge": (I32, [P, ctypes.POINTER(FPParticles), P, I32, P]),
             "fem_pic_sort": (I32, [P, ctypes.POINTER(FPParticles), ctypes.POINTER(FPParticles), P]),
+            "fem_pic_push_deposit_adams": (I32, [P, P, P, ctypes.POINTER(FPParticles), P, I64, D, I32, P, P, I32,
+                                                 P]),
+            "fem_pic_sort_columns": (I32, [P, ctypes.POINTER(FPParticles), ctypes.POINTER(FPParticles), P, P, I32,
+                                           P]),
             "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
             "fem_pic_status": (I32, [P, P]),
             "fem_pic_field_setup": (I32, [P, D, D, D]),
@@ -308,6 +312,23 @@ def fem_pic_push_deposit(h, e, b, sp: Species, dt: float, dG, Q, max_cross: int 
                                       _ptr(dG), _ptr(Q), int(flags), _stream(stream)), h)
 
 
+def fem_pic_push_deposit_adams(h, e, b, sp: Species, hist, step: int, dt: float, dG, Q, max_cross: int = 64,
+                               flags: int = 0, stream=None):
+    """Adams-Bashforth particle step; hist is the 18*n planar derivative history (see the header)."""
+    sz = fem_pic_sizes(h)
+    R = _real(h)
+    _check_species(h, sp)
+    _need(hist, R, 18 * sp.n, name="hist")
+    _need(e, torch.float64, sz["n_edges"], name="e")
+    _need(b, torch.float64, sz["n_faces"], name="b")
+    _need(dG, R, sz["n_edges"], name="dG")
+    _need(Q, R, sz["n_nodes"], name="Q")
+    p = sp.abi()
+    _check(lib().fem_pic_push_deposit_adams(h, _ptr(e), _ptr(b), ctypes.byref(p), _ptr(hist), int(step),
+                                            float(dt), int(max_cross), _ptr(dG), _ptr(Q), int(flags),
+                                            _stream(stream)), h)
+
+
 def fem_pic_deposit_charge(h, sp: Species, Q, flags: int = 0, stream=None):
     _check_species(h, sp)
     _need(Q, _real(h), fem_pic_sizes(h)["n_nodes"], name="Q")
@@ -320,6 +341,17 @@ def fem_pic_sort(h, src: Species, dst: Species, stream=None):
     _check_species(h, dst)
     a, b = src.abi(), dst.abi()
     _check(lib().fem_pic_sort(h, ctypes.byref(a), ctypes.byref(b), _stream(stream)), h)
+
+
+def fem_pic_sort_columns(h, src: Species, dst: Species, cols_src, cols_dst, ncols: int, stream=None):
+    _check_species(h, src)
+    _check_species(h, dst)
+    R = _real(h)
+    _need(cols_src, R, ncols * src.n, name="cols_src")
+    _need(cols_dst, R, ncols * src.n, name="cols_dst")
+    a, b = src.abi(), dst.abi()
+    _check(lib().fem_pic_sort_columns(h, ctypes.byref(a), ctypes.byref(b), _ptr(cols_src), _ptr(cols_dst),
+                                      int(ncols), _stream(stream)), h)
 
 
 def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
@@ -452,7 +484,7 @@ def fem_pic_whitney0_integrals(h) -> np.ndarray:
 
 
 PHASES = ("prep", "push_fast", "walk", "push_fp64", "charge", "sort", "residuals", "field_other",
-          "cg_newmark", "cg_gauss", "learned")
+          "cg_newmark", "cg_gauss", "learned", "adams_push", "adams_walk")
 
 
 def fem_pic_field_options(h, newmark_solver: int = -1, gauss_solver: int = -1, inner_tol: float = 1e-5):
@@ -537,6 +569,12 @@ class FemPic:
 
     def push_deposit(self, e, b, sp, dt, dG, Q, max_cross=64, flags=0, stream=None):
         fem_pic_push_deposit(self.h, e, b, sp, dt, dG, Q, max_cross, flags, stream)
+
+    def push_deposit_adams(self, e, b, sp, hist, step, dt, dG, Q, max_cross=64, flags=0, stream=None):
+        fem_pic_push_deposit_adams(self.h, e, b, sp, hist, step, dt, dG, Q, max_cross, flags, stream)
+
+    def sort_columns(self, src, dst, cols_src, cols_dst, ncols, stream=None):
+        fem_pic_sort_columns(self.h, src, dst, cols_src, cols_dst, ncols, stream)
 
     def deposit_charge(self, sp, Q, flags=0, stream=None):
         fem_pic_deposit_charge(self.h, sp, Q, flags, stream)

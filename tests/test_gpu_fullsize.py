@@ -119,3 +119,70 @@ def test_field_step_full_size(workload):
     g, sc = fo.gauss_residual(E1, Qn.double().cpu().numpy())
     assert np.abs(g).max() <= 1e-9 * sc.max()
     lib.close()
+
+
+def test_adams_step_full_size(workload):
+    """The fourth-order Adams particle step (order 4, history from earlier steps' shape) on all
+    2M sorted electrons, in the launch configuration the benchmark times it in."""
+    from oracle import adams as AD
+    wl, orc = workload
+    sp = wl.species[0]
+    lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
+    d0 = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    n = d0.n
+    rng = np.random.default_rng(12)
+    dt = wl.dt / 4
+    # history: the current velocities with a small seeded perturbation, accelerations of the
+    # size the uniform B0 gives (|q/m| v B0)
+    v = sp.V.T
+    wc = abs(sp.q / sp.m) * np.linalg.norm(wl.B0)
+    h = np.empty((18, n))
+    for s in range(3):
+        h[6 * s:6 * s + 3] = v * (1.0 + 0.01 * rng.standard_normal((3, n)))
+        h[6 * s + 3:6 * s + 6] = wc * v[[1, 0, 2]] * rng.uniform(-1, 1, (3, n))
+    hist0 = torch.as_tensor(h, device="cuda").float().contiguous()
+    d = d0.empty_like()
+    hist = torch.empty_like(hist0)
+    lib.sort_columns(d0, d, hist0, hist, 18)
+    cx = orc.cx
+    e = 1e3 * np.linalg.norm(cx.xyz[cx.edges[:, 1]] - cx.xyz[cx.edges[:, 0]], axis=1) * \
+        np.random.default_rng(11).uniform(-1.0, 1.0, cx.n_edges)
+    e[cx.boundary_edge] = 0.0
+    _, b = cx.project_uniform((0.0, 0.0, 0.0), wl.B0)
+    cell0 = d.cell.cpu().numpy().copy()
+    off0 = d.off.cpu().numpy().copy()
+    v0 = d.vel.cpu().numpy().copy()
+    h_in = hist.cpu().numpy().copy()
+    ed = torch.as_tensor(e, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    dG = torch.empty(cx.n_edges, dtype=torch.float32, device="cuda")
+    Q = torch.empty(cx.n_nodes, dtype=torch.float32, device="cuda")
+    step = 3
+    lib.push_deposit_adams(ed, bd, d, hist, step, dt, dG, Q)
+    assert lib.status() == F.FP_OK
+    # end points as the library rounds them (FP32, operation by operation)
+    beta = [np.float32(x) for x in AD.ab_coefficients(4)]
+    acc = (beta[0] * v0).astype(np.float32)
+    for j in range(1, 4):
+        sl = (step - j) % 3
+        acc = (acc + (beta[j] * h_in[6 * sl:6 * sl + 3]).astype(np.float32)).astype(np.float32)
+    end = (off0 + (np.float32(dt) * acc).astype(np.float32)).astype(np.float32)
+    o = orc.origin(cell0)
+    Xa = o + off0.T.astype(np.float64)
+    hv = np.stack([h_in[6 * s:6 * s + 3].T for s in range(3)]).astype(np.float64)
+    ha = np.stack([h_in[6 * s + 3:6 * s + 6].T for s in range(3)]).astype(np.float64)
+    ref = AD.adams_step(orc, cell0, Xa, v0.T.astype(np.float64), hv, ha, step, e, b, sp.q, sp.m, sp.w, dt,
+                        Xend=o + end.T.astype(np.float64))
+    V1 = d.vel.double().cpu().numpy().T
+    assert np.abs(V1 - ref["V"]).max() <= TOL["fp32"] * np.abs(ref["V"]).max()
+    hs = hist.cpu().numpy()
+    assert np.array_equal(hs[0:3], v0)                       # slot 3 % 3 = 0 takes v^n
+    assert np.array_equal(hs[6:18], h_in[6:18])
+    cell1 = d.cell.cpu().numpy()
+    assert np.array_equal(cell1, ref["cell"])
+    alive = cell1 >= 0
+    X1 = lib.positions(d).cpu().numpy()
+    assert np.abs(X1[alive] - ref["X"][alive]).max() <= 1e-6
+    assert_deposit_close(dG.cpu().numpy(), ref["dG"], ref["dG_abs"], TOL["fp32"], "dG")
+    assert_deposit_close(Q.cpu().numpy(), ref["Q"], ref["Q_abs"], TOL["fp32"], "Q")
+    lib.close()
