@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "field.cuh"
@@ -547,6 +548,23 @@ fp_status up(fem_pic* ctx, T** d, const std::vector<T>& h) {
     return FP_OK;
 }
 
+// b and x into the solver's row order (row r is DOF perm[r]), and the solution back
+__global__ void k_perm_gather(const int32_t* __restrict__ perm, const double* __restrict__ b,
+                              const double* __restrict__ x, double* __restrict__ pb, double* __restrict__ px,
+                              int64_t n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = __ldg(perm + r);
+        pb[r] = __ldg(b + k);
+        px[r] = __ldg(x + k);
+    }
+}
+
+__global__ void k_perm_scatter(const int32_t* __restrict__ perm, const double* __restrict__ px,
+                               double* __restrict__ x, int64_t n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        x[__ldg(perm + r)] = px[r];
+}
+
 fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double tol, const double* scale_vec,
                   int max_iter, int slot, cudaStream_t s) {
     FieldDev* F = ctx->field;
@@ -556,8 +574,8 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     F->last_fp64[slot] = use64;
     if (!use64) {
         MixedArgs m;
-        if (system == FP_SYS_NEWMARK) {
-            m.S = Sell{F->se_ptr, F->se_w, F->se_col}, m.val = F->se_A, m.val32 = F->se_A32, m.dinv32 = F->Adinv32,
+        if (system == FP_SYS_NEWMARK) {   // the solver's own row order (gathered in and scattered out below)
+            m.S = Sell{F->pe_ptr, F->pe_w, F->pe_col}, m.val = F->pe_A, m.val32 = F->pe_A32, m.dinv32 = F->pe_dinv32,
             m.n = F->ne;
         } else {
             m.S = Sell{F->sn_ptr, F->sn_w, F->sn_col}, m.val = F->sn_L, m.val32 = F->sn_L32, m.dinv32 = F->Ldinv32,
@@ -583,7 +601,13 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
         const int bs = system == FP_SYS_NEWMARK ? F->bs_e : F->bs_n;
         const size_t smem = (size_t)m.sm_slots * 6;
+        if (system == FP_SYS_NEWMARK) {
+            k_perm_gather<<<grid_of(ctx, F->ne), kBlock, 0, s>>>(F->perm_e, rhs, x, F->pb, F->px, F->ne);
+            m.b = F->pb, m.x = F->px;
+        }
         FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, false), dim3(grid), dim3(bs), args, smem, s));
+        if (system == FP_SYS_NEWMARK) k_perm_scatter<<<grid_of(ctx, F->ne), kBlock, 0, s>>>(F->perm_e, F->px, x, F->ne);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
     PcgArgs a;
@@ -687,7 +711,7 @@ void field_free(fem_pic* ctx) {
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
-                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
+                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->pe_ptr, F->pe_w, F->pe_col, F->perm_e, F->pe_A, F->pe_A32, F->pe_dinv32, F->pb, F->px, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
                     F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -816,12 +840,6 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         sell(H.e_rp, H.e_col, hc.ne, &ptr, &w, &scol, &map);
         std::vector<double> sM = gather(map, H.M), sS = gather(map, H.S), sA = gather(map, A);
         std::vector<float> sA32(sA.begin(), sA.end());
-        {
-            const std::vector<int16_t> d16 = offsets16(scol, ptr, w);
-            if (!d16.empty() && st == FP_OK) st = up(ctx, &F->se_d16, d16);
-            F->hptr[FP_SYS_NEWMARK] = ptr;
-            F->slots_total[FP_SYS_NEWMARK] = (int64_t)scol.size();
-        }
         if (st == FP_OK) st = up(ctx, &F->se_ptr, ptr);
         if (st == FP_OK) st = up(ctx, &F->se_w, w);
         if (st == FP_OK) st = up(ctx, &F->se_col, scol);
@@ -829,6 +847,113 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         if (st == FP_OK) st = up(ctx, &F->se_S, sS);
         if (st == FP_OK) st = up(ctx, &F->se_A, sA);
         if (st == FP_OK) st = up(ctx, &F->se_A32, sA32);
+        {
+            // Row order of the mixed solver's Newmark operator.  Edge ids are lexicographic in
+            // (i, j), so the edges leaving a node are consecutive and a 32-row slice mixes edges
+            // of several directions: lane l's k-th neighbour lies far from lane l+1's, and a
+            // product gathers about one useful value per 32-byte sector of x.  Renumbered by
+            // (block of kPermNodes first nodes, rank of the edge among its first node's edges,
+            // first node), a slice holds same-rank edges of consecutive nodes, whose neighbours
+            // are again consecutive.  Of the two orders the one whose products gather fewer
+            // sectors (counted over its SELL layout) is kept, so a mesh without that structure
+            // keeps the edge order; so is the edge order when the other's column offsets do
+            // not fit in 16 bits.
+            constexpr int32_t kPermNodes = 256;
+            const int64_t ne = hc.ne;
+            std::vector<int32_t> ident(ne), blocked(ne), rank(ne, 0);
+            for (int64_t k = 0; k < ne; ++k) {
+                ident[k] = (int32_t)k;
+                if (k > 0 && hc.edges[2 * k] == hc.edges[2 * (k - 1)]) rank[k] = rank[k - 1] + 1;
+            }
+            blocked = ident;
+            std::sort(blocked.begin(), blocked.end(), [&](int32_t a, int32_t b) {
+                const int32_t ia = hc.edges[2 * a], ib = hc.edges[2 * b];
+                if (ia / kPermNodes != ib / kPermNodes) return ia / kPermNodes < ib / kPermNodes;
+                if (rank[a] != rank[b]) return rank[a] < rank[b];
+                return ia != ib ? ia < ib : a < b;
+            });
+            // CSR of P A P^T (columns sorted) for perm (solver row -> edge)
+            auto permuted = [&](const std::vector<int32_t>& perm, std::vector<int32_t>* rp2, std::vector<int32_t>* col2,
+                                std::vector<double>* val2) {
+                std::vector<int32_t> inv(ne);
+                for (int64_t r = 0; r < ne; ++r) inv[perm[r]] = (int32_t)r;
+                rp2->assign(ne + 1, 0);
+                col2->resize(H.e_col.size());
+                val2->resize(H.e_col.size());
+                std::vector<std::pair<int32_t, double>> row;
+                int64_t o = 0;
+                for (int64_t r = 0; r < ne; ++r) {
+                    const int32_t e0 = perm[r];
+                    row.clear();
+                    for (int32_t j = H.e_rp[e0]; j < H.e_rp[e0 + 1]; ++j) row.emplace_back(inv[H.e_col[j]], A[j]);
+                    std::sort(row.begin(), row.end(),
+                              [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                                  return a.first < b.first;
+                              });
+                    for (const auto& pr : row) (*col2)[o] = pr.first, (*val2)[o] = pr.second, ++o;
+                    (*rp2)[r + 1] = (int32_t)o;
+                }
+            };
+            // distinct 32-byte sectors of x that the lanes of each slice gather per entry
+            auto sectors = [](const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int64_t n) {
+                int64_t total = 0;
+                int32_t sec[32];
+                for (int64_t r0 = 0; r0 < n; r0 += 32) {
+                    const int64_t r1 = std::min<int64_t>(n, r0 + 32);
+                    int w = 0;
+                    for (int64_t r = r0; r < r1; ++r) w = std::max(w, rp[r + 1] - rp[r]);
+                    for (int j = 0; j < w; ++j) {
+                        int m = 0;
+                        for (int64_t r = r0; r < r1; ++r)
+                            if (j < rp[r + 1] - rp[r]) sec[m++] = col[rp[r] + j] >> 3;
+                        std::sort(sec, sec + m);
+                        total += (int64_t)(std::unique(sec, sec + m) - sec);
+                    }
+                }
+                return total;
+            };
+            std::vector<int32_t> rp2, col2;
+            std::vector<double> val2;
+            permuted(blocked, &rp2, &col2, &val2);
+            F->sectors_e[0] = sectors(H.e_rp, H.e_col, ne);
+            F->sectors_e[1] = sectors(rp2, col2, ne);
+            const std::vector<int32_t>* perm = &blocked;
+            std::vector<int16_t> d16;
+#ifndef FP_SOLVER_ORDER
+#define FP_SOLVER_ORDER 1
+#endif
+            if (FP_SOLVER_ORDER && F->sectors_e[1] < F->sectors_e[0]) {
+                sell(rp2, col2, ne, &ptr, &w, &scol, &map);
+                d16 = offsets16(scol, ptr, w);
+            }
+            if (d16.empty()) {   // the edge order
+                perm = &ident;
+                F->sectors_e[1] = F->sectors_e[0];
+                permuted(ident, &rp2, &col2, &val2);
+                sell(rp2, col2, ne, &ptr, &w, &scol, &map);
+                d16 = offsets16(scol, ptr, w);
+            }
+            std::vector<double> pA = gather(map, val2);
+            std::vector<float> pA32(pA.begin(), pA.end()), pdinv(ne);
+            for (int64_t r = 0; r < ne; ++r) pdinv[r] = (float)Ad[(*perm)[r]];
+#ifdef FP_SMEM_REPORT
+            fprintf(stderr, "newmark solver order: %s, sectors %lld (edge order %lld), slots %lld (edge order %lld)\n",
+                    perm == &blocked ? "blocked" : "edge", (long long)F->sectors_e[1], (long long)F->sectors_e[0],
+                    (long long)scol.size(), (long long)F->slots_total[FP_SYS_GAUSS] * 0 + (long long)H.e_col.size());
+#endif
+            if (!d16.empty() && st == FP_OK) st = up(ctx, &F->se_d16, d16);
+            F->hptr[FP_SYS_NEWMARK] = ptr;
+            F->slots_total[FP_SYS_NEWMARK] = (int64_t)scol.size();
+            if (st == FP_OK) st = up(ctx, &F->perm_e, *perm);
+            if (st == FP_OK) st = up(ctx, &F->pe_ptr, ptr);
+            if (st == FP_OK) st = up(ctx, &F->pe_w, w);
+            if (st == FP_OK) st = up(ctx, &F->pe_col, scol);
+            if (st == FP_OK) st = up(ctx, &F->pe_A, pA);
+            if (st == FP_OK) st = up(ctx, &F->pe_A32, pA32);
+            if (st == FP_OK) st = up(ctx, &F->pe_dinv32, pdinv);
+            if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->pb, ne * sizeof(double)));
+            if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->px, ne * sizeof(double)));
+        }
         sell(H.n_rp, H.n_col, hc.nn, &ptr, &w, &scol, &map);
         std::vector<double> sL = gather(map, H.L);
         std::vector<float> sL32(sL.begin(), sL.end());

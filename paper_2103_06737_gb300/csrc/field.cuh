@@ -46,6 +46,15 @@ struct FieldDev {
     // FP32 operators held in shared memory by the mixed solver (per system): column offsets
     // col - row as int16 in the SELL layout, and the slots per block (0: not held)
     int16_t *se_d16 = nullptr, *sn_d16 = nullptr;
+    // The mixed solver's copy of the Newmark operator in its own row order: solver row r is
+    // edge perm_e[r] (rows and columns renumbered alike).  Right-hand side and guess are
+    // gathered into pb / px before each solve and the solution scattered back after it.
+    // se_d16 and hptr / slots_total of the Newmark system describe this copy.
+    int32_t *pe_ptr = nullptr, *pe_w = nullptr, *pe_col = nullptr, *perm_e = nullptr;
+    double* pe_A = nullptr;
+    float *pe_A32 = nullptr, *pe_dinv32 = nullptr;
+    double *pb = nullptr, *px = nullptr;
+    int64_t sectors_e[2] = {0, 0};  // gathered 32-byte sectors per product: edge order, solver order
     int64_t slots_total[2] = {0, 0};
     int sm_slots[2] = {0, 0};
     std::vector<int32_t> hptr[2];   // host copies of the SELL slice starts (Newmark, Gauss)
