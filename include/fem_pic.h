@@ -197,8 +197,9 @@ fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const dou
  *         step mod 3 of each live particle (other slots are left alone).  Contents are
  *         ignored on step 0 (nothing needs initialising).
  *   step: number of earlier Adams steps of these particles (>= 0); the caller counts.
- * The position sum is rounded operation by operation (beta_0 v^n first, then the older
- * terms in order, then x^n + dt * sum) without fused multiply-adds.  Absorbed particles
+ * The position sum is rounded operation by operation without fused multiply-adds, in
+ * this order: h = beta_1 v^{n-1}, h += beta_2 v^{n-2}, h += beta_3 v^{n-3} (the terms the
+ * order has), s = beta_0 v^n + h (s = beta_0 v^n at order 1), x^{n+1} = x^n + dt s.  Absorbed particles
  * (cell -1) are left alone.  A particle's history must move with it: sort with
  * fem_pic_sort_columns(..., hist, hist_sorted, 18, ...).  The explicit method is stable for
  * gyration only while omega_c dt stays below about 0.43.  dG and Q are zeroed first unless

@@ -571,36 +571,40 @@ struct AdamsStep {
     Real dt, qm;
 };
 
-// a^n, v^{n+1} and the end offset x^{n+1}.  The position sum is rounded operation by
-// operation without contraction, so that the end point (which decides the walk) can be
-// reproduced exactly by a CPU program:
-//   s = beta_0 v^n (+ beta_j v^{n-j} for j < k),  x^{n+1} = x^n + dt s.
+// The history part of the Adams sums, which needs no fields and can be loaded early:
+//   hx = beta_1 v^{n-1} (+ beta_2 v^{n-2} (+ beta_3 v^{n-3})),  ha likewise with a,
+// zero at order 1.  The position sum is rounded operation by operation without contraction,
+// so that the end point (which decides the walk) can be reproduced exactly by a CPU program.
 template <typename Real>
-__device__ __forceinline__ void adams_update(const AdamsStep<Real>& A, int64_t p, const Real x[3], const Real v[3],
-                                             const Real E[3], const Real B[3], Real a[3], Real v1[3], Real xb[3]) {
-    Real c[3];
-    cross<Real>(v, B, c);
-    Real sx[3], sv[3];
+__device__ __forceinline__ void adams_history(const AdamsStep<Real>& A, int64_t p, Real hx[3], Real ha[3]) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        a[i] = A.qm * (E[i] + c[i]);
-        sx[i] = mul_rn(A.beta[0], v[i]);
-        sv[i] = A.beta[0] * a[i];
-    }
+    for (int i = 0; i < 3; ++i) hx[i] = ha[i] = (Real)0;
 #pragma unroll
     for (int j = 1; j < 4; ++j) {
         if (j >= A.order) break;
         const int64_t base = (int64_t)6 * A.slot[j - 1] * A.n + p;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            sx[i] = add_rn(sx[i], mul_rn(A.beta[j], A.hist[base + i * A.n]));
-            sv[i] += A.beta[j] * A.hist[base + (3 + i) * A.n];
+            const Real t = mul_rn(A.beta[j], A.hist[base + i * A.n]);
+            hx[i] = j == 1 ? t : add_rn(hx[i], t);
+            ha[i] += A.beta[j] * A.hist[base + (3 + i) * A.n];
         }
     }
+}
+
+// a^n, v^{n+1} and the end offset x^{n+1} from the fields at x^n and the history part:
+//   x^{n+1} = x^n + dt (beta_0 v^n + hx),  v^{n+1} = v^n + dt (beta_0 a^n + ha)
+template <typename Real>
+__device__ __forceinline__ void adams_update(const AdamsStep<Real>& A, const Real x[3], const Real v[3],
+                                             const Real E[3], const Real B[3], const Real hx[3], const Real ha[3],
+                                             Real a[3], Real v1[3], Real xb[3]) {
+    Real c[3];
+    cross<Real>(v, B, c);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        xb[i] = add_rn(x[i], mul_rn(A.dt, sx[i]));
-        v1[i] = v[i] + A.dt * sv[i];
+        a[i] = A.qm * (E[i] + c[i]);
+        xb[i] = add_rn(x[i], mul_rn(A.dt, add_rn(mul_rn(A.beta[0], v[i]), hx[i])));
+        v1[i] = v[i] + A.dt * (A.beta[0] * a[i] + ha[i]);
     }
 }
 
@@ -622,12 +626,14 @@ __device__ __forceinline__ void adams_store(const AdamsStep<Real>& A, Real* __re
 struct AdamsMover32 {
     const AdamsStep<float>& A;
     float* __restrict__ vel;
-    float v0[3], a[3], v1[3];
-    __device__ __forceinline__ void move(int64_t p, const float x[3], float v[3], const float E[3],
+    float v0[3], a[3], v1[3], hx[3], ha[3];
+    // the history part, loaded before the particle's fields (its loads overlap the record's)
+    __device__ __forceinline__ void history(int64_t p) { adams_history<float>(A, p, hx, ha); }
+    __device__ __forceinline__ void move(int64_t, const float x[3], float v[3], const float E[3],
                                          const float B[3], float xb[3]) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) v0[i] = v[i];
-        adams_update<float>(A, p, x, v0, E, B, a, v1, xb);
+        adams_update<float>(A, x, v0, E, B, hx, ha, a, v1, xb);
 #pragma unroll
         for (int i = 0; i < 3; ++i) v[i] = v1[i];
     }
@@ -1179,7 +1185,10 @@ __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
 // FP32 Adams step, fast path: the Boris kernel's structure with the Adams mover.  A particle
 // whose end point clears the rounding margin is finished here (state, history, deposits);
 // the others are queued unchanged for k_walk_adams32.
-__global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_adams32(
+#ifndef FP_ADAMS_MIN_BLOCKS
+#define FP_ADAMS_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(256, FP_ADAMS_MIN_BLOCKS) k_push_adams32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
     float* __restrict__ vel, AdamsStep<float> A, int32_t nt, double qw, int aggregate,
     float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
@@ -1202,6 +1211,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_adams32(
         if (c >= 0 && c < nt) {
             x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
+            am.history(p);
         }
         const bool slow =
             fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, am, w, aggregate, off, dG, Q, status);
@@ -1233,14 +1243,15 @@ __global__ void __launch_bounds__(128) k_walk_adams32(const TetHot* __restrict__
         const int c = cell[p];
         TetHot H;
         load_hot(hot, c, H);
-        float x[3], v[3], E[3], B[3], a[3], v1[3], xb[3];
+        float x[3], v[3], E[3], B[3], a[3], v1[3], xb[3], hx[3], ha[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             x[k] = off[k * n + p];
             v[k] = vel[k * n + p];
         }
+        adams_history<float>(A, p, hx, ha);
         hot_fields(H, x, E, B);
-        adams_update<float>(A, p, x, v, E, B, a, v1, xb);
+        adams_update<float>(A, x, v, E, B, hx, ha, a, v1, xb);
         adams_store<float>(A, vel, p, v, a, v1);
         double xa[3], xe[3];
 #pragma unroll
@@ -1285,10 +1296,11 @@ __global__ void __launch_bounds__(256) k_push_adams64(
             load_topo(topo, c, T);
             double x[3] = {off[p], off[n + p], off[2 * n + p]};
             double v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
-            double la[4], E[3], B[3], a[3], v1[3], xb[3];
+            double la[4], E[3], B[3], a[3], v1[3], xb[3], hx[3], ha[3];
+            adams_history<double>(A, p, hx, ha);
             bary(G, x, la);
             gather<double>(G, T, e, b, la, E, B);
-            adams_update<double>(A, p, x, v, E, B, a, v1, xb);
+            adams_update<double>(A, x, v, E, B, hx, ha, a, v1, xb);
             adams_store<double>(A, vel, p, v, a, v1);
             int end_cell;
             double end_off[3];

@@ -60,14 +60,19 @@ def _split(h):
 
 
 def _end_points(off0, v0, h, step, dt, real):
-    """x^{n+1} offsets as the library rounds them: s = beta_0 v^n, s += beta_j v^{n-j} in
-    order, x + dt s, each operation rounded to `real` (no fused multiply-adds)."""
+    """x^{n+1} offsets as the library rounds them: h = beta_1 v^{n-1}, h += beta_j v^{n-j}
+    (j = 2, 3), s = beta_0 v^n + h, x + dt s, each operation rounded to `real` (no fused
+    multiply-adds)."""
     k = AD.order_for(step)
     beta = [real(x) for x in AD.ab_coefficients(k)]
     s = (beta[0] * v0.astype(real)).astype(real)
-    for j in range(1, k):
-        sl = (step - j) % 3
-        s = (s + (beta[j] * h[6 * sl:6 * sl + 3].astype(real)).astype(real)).astype(real)
+    if k > 1:
+        hs = None
+        for j in range(1, k):
+            sl = (step - j) % 3
+            t = (beta[j] * h[6 * sl:6 * sl + 3].astype(real)).astype(real)
+            hs = t if hs is None else (hs + t).astype(real)
+        s = (s + hs).astype(real)
     return (off0.astype(real) + (real(dt) * s).astype(real)).astype(real)
 
 

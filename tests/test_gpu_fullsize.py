@@ -162,10 +162,12 @@ def test_adams_step_full_size(workload):
     assert lib.status() == F.FP_OK
     # end points as the library rounds them (FP32, operation by operation)
     beta = [np.float32(x) for x in AD.ab_coefficients(4)]
-    acc = (beta[0] * v0).astype(np.float32)
+    hs = None
     for j in range(1, 4):
         sl = (step - j) % 3
-        acc = (acc + (beta[j] * h_in[6 * sl:6 * sl + 3]).astype(np.float32)).astype(np.float32)
+        t = (beta[j] * h_in[6 * sl:6 * sl + 3]).astype(np.float32)
+        hs = t if hs is None else (hs + t).astype(np.float32)
+    acc = ((beta[0] * v0).astype(np.float32) + hs).astype(np.float32)
     end = (off0 + (np.float32(dt) * acc).astype(np.float32)).astype(np.float32)
     o = orc.origin(cell0)
     Xa = o + off0.T.astype(np.float64)
