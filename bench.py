@@ -57,7 +57,10 @@ def parse():
     ap.add_argument("--poly-ratio", default="15,100",
                     help="lambda_max / lambda_low of the Chebyshev interval, Newmark and Gauss systems")
     ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
-                    help="learned Newmark correction: trained during warm-up, used if it beats plain CG (auto)")
+                    help="learned corrections of the Newmark and Gauss-law solves: trained during warm-up, "
+                         "each used if it beats plain CG (auto)")
+    ap.add_argument("--learned-systems", default="newmark,gauss",
+                    help="systems whose learned correction is trained and judged (newmark, gauss)")
     ap.add_argument("--learn-samples", type=int, default=48)
     ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--compare-steps", type=int, default=20)
@@ -341,9 +344,13 @@ def run_gpu(args):
         if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
             F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
                                  max_iter=args.max_iter, precond=state["precond"], info=False)
-            n_k += 7
-            if state["precond"] == F.FP_PC_LEARNED:
-                n_k += 13         # residual, network forward (9 kernels), candidate, residual, select
+            # Newmark right-hand side (2), solve (1; the mixed solver also gathers into and
+            # scatters out of its row order: 2), Gauss right-hand side (2), solve (1),
+            # projection and Faraday update (2)
+            n_k += 8 + (2 if solv[0] == "mixed" else 0)
+            for bit in (F.FP_PC_LEARNED, F.FP_PC_LEARNED_GAUSS):
+                if state["precond"] & bit:
+                    n_k += 13     # residual, network forward (9 kernels), candidate, residual, select
         lib.residuals(dG, Qn, Qo, b, res)
         n_k += 1
         Qo.copy_(Qn)
@@ -392,58 +399,71 @@ def run_gpu(args):
     if st != F.FP_OK:
         raise RuntimeError(f"warm-up status {st}: {F.fem_pic_last_error(lib.h)}")
 
-    # learned correction: collect residuals of the method's own Newmark solves, train,
-    # then time learned vs plain Jacobi-CG on the same steps (plain CG is the judge)
+    # learned corrections, per system (Newmark edge system, Gauss-law node system): collect
+    # residuals of the method's own solves, train, then time learned vs plain Jacobi-CG on the
+    # same steps (plain CG is the judge); a correction is kept only where it wins
     learned = None
     if field and args.learned != "off":
-        t_l0 = time.time()
-        F.fem_pic_learned_init(lib.h, seed=0, sample_capacity=args.learn_samples)
-        F.fem_pic_learned_mode(lib.h, collect=True, active=False)
-        for _ in range(args.learn_samples):
-            eager_step()
-        torch.cuda.synchronize()
-        F.fem_pic_learned_mode(lib.h, collect=False, active=False)
-        n_s = F.fem_pic_learned_samples(lib.h)
-        n_hold = max(1, n_s // 6)
-        before = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
-        losses = F.fem_pic_learned_train(lib.h, 0, n_s - n_hold, args.learn_epochs, lr=2e-3, seed=0)
-        after = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
-        t_train = time.time() - t_l0
-
-        def compare(pc):
-            state["precond"] = pc
-            restore()
-            F.fem_pic_profile_read(lib.h, reset=True)
-            F.fem_pic_profile_enable(lib.h, True)
-            its, fb = [], 0
-            for k in range(args.compare_steps):
-                flush_l2(k)
+        learned = {}
+        used_bits = 0
+        for sysname in [x for x in args.learned_systems.split(",") if x]:
+            sys_id = F.FP_SYS_NEWMARK if sysname == "newmark" else F.FP_SYS_GAUSS
+            bit = F.FP_PC_LEARNED if sys_id == F.FP_SYS_NEWMARK else F.FP_PC_LEARNED_GAUSS
+            ph_cg = "cg_newmark" if sys_id == F.FP_SYS_NEWMARK else "cg_gauss"
+            t_l0 = time.time()
+            state["precond"] = precond
+            F.fem_pic_learned_select(lib.h, sys_id)
+            F.fem_pic_learned_init(lib.h, seed=0, sample_capacity=args.learn_samples)
+            F.fem_pic_learned_mode(lib.h, collect=True, active=False)
+            for _ in range(args.learn_samples):
                 eager_step()
-                fi = F.fem_pic_field_last_info(lib.h)
-                its.append(fi[0]["iters"])
-                fb += fi[0]["fell_back"]
             torch.cuda.synchronize()
-            F.fem_pic_profile_enable(lib.h, False)
-            ph = F.fem_pic_profile_read(lib.h, reset=True)
-            tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
-            return {"field_ms_per_step": tot / args.compare_steps,
-                    "newmark_cg_ms_per_step": ph.get("cg_newmark", (0.0, 1))[0] / args.compare_steps,
-                    "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
-                    "newmark_iters_mean": statistics.mean(its), "fell_back": fb}
-        # plain Jacobi-CG judges the learned correction: both runs with the Jacobi inner
-        # preconditioner on the Newmark system (the timed steps then use the configured one)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, 1, prat[0])
-        plain = compare(precond)
-        learn = compare(F.FP_PC_LEARNED)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
-        use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
-        state["precond"] = F.FP_PC_LEARNED if use else precond
-        learned = {"samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
-                   "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
-                   "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
-                   "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
-                   "judge": "plain Jacobi-CG (Jacobi inner preconditioner on the Newmark system in both runs)",
-                   "model": "3-layer message passing on the edge graph, 64 features, BF16 weights, FP32 accum"}
+            F.fem_pic_learned_mode(lib.h, collect=False, active=False)
+            n_s = F.fem_pic_learned_samples(lib.h)
+            n_hold = max(1, n_s // 6)
+            before = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
+            losses = F.fem_pic_learned_train(lib.h, 0, n_s - n_hold, args.learn_epochs, lr=2e-3, seed=0)
+            after = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
+            t_train = time.time() - t_l0
+
+            def compare(pc):
+                state["precond"] = pc
+                restore()
+                F.fem_pic_profile_read(lib.h, reset=True)
+                F.fem_pic_profile_enable(lib.h, True)
+                its, fb = [], 0
+                for k in range(args.compare_steps):
+                    flush_l2(k)
+                    eager_step()
+                    fi = F.fem_pic_field_last_info(lib.h)
+                    its.append(fi[sys_id]["iters"])
+                    fb += fi[sys_id]["fell_back"]
+                torch.cuda.synchronize()
+                F.fem_pic_profile_enable(lib.h, False)
+                ph = F.fem_pic_profile_read(lib.h, reset=True)
+                tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
+                return {"field_ms_per_step": tot / args.compare_steps,
+                        ph_cg + "_ms_per_step": ph.get(ph_cg, (0.0, 1))[0] / args.compare_steps,
+                        "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
+                        "iters_mean": statistics.mean(its), "fell_back": fb}
+            # plain Jacobi-CG judges the learned correction: both runs with the Jacobi inner
+            # preconditioner on this system (the timed steps then use the configured one)
+            F.fem_pic_field_poly(lib.h, sys_id, 1, prat[sys_id])
+            plain = compare(precond)
+            learn = compare(precond | bit)
+            F.fem_pic_field_poly(lib.h, sys_id, pdeg[sys_id], prat[sys_id])
+            use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
+            if use:
+                used_bits |= bit
+            graph = "edge graph" if sys_id == F.FP_SYS_NEWMARK else "node graph"
+            learned[sysname] = {
+                "samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
+                "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
+                "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
+                "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
+                "judge": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system in both runs)",
+                "model": f"3-layer message passing on the {graph}, 64 features, BF16 weights, FP32 accum"}
+        state["precond"] = precond | used_bits
 
     # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
     graphs = {}
@@ -672,7 +692,10 @@ def run_gpu(args):
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
                 "ms_learned_guess": phases.get("learned", (0.0, 1))[0] / args.steps,
-                "precond": "learned correction + jacobi" if state["precond"] == F.FP_PC_LEARNED else "jacobi",
+                "precond": ("learned correction (" + ", ".join(
+                    nm for nm, bit in (("newmark", F.FP_PC_LEARNED), ("gauss", F.FP_PC_LEARNED_GAUSS))
+                    if state["precond"] & bit) + ") + jacobi")
+                    if state["precond"] & (F.FP_PC_LEARNED | F.FP_PC_LEARNED_GAUSS) else "jacobi",
                 "learned_vs_plain": learned,
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
                            "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",

@@ -255,8 +255,10 @@ fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, c
 enum { FP_SYS_NEWMARK = 0, FP_SYS_GAUSS = 1 };
 /* FP_PC_JACOBI: Jacobi-PCG by mixed-precision iterative refinement (FP64 residual and dot
  * products, FP32 inner solves); FP_PC_JACOBI_FP64: plain Jacobi-PCG entirely in FP64;
- * FP_PC_LEARNED: learned correction with fallback (see fem_pic_learned_*). */
-enum { FP_PC_JACOBI = 0, FP_PC_LEARNED = 1, FP_PC_JACOBI_FP64 = 2 };
+ * FP_PC_LEARNED: learned correction of the Newmark solve's starting point with fallback,
+ * FP_PC_LEARNED_GAUSS: the same for the Gauss-law projection (see fem_pic_learned_*).
+ * fem_pic_field_step takes an OR of these bits (FP_PC_JACOBI = none of them). */
+enum { FP_PC_JACOBI = 0, FP_PC_LEARNED = 1, FP_PC_JACOBI_FP64 = 2, FP_PC_LEARNED_GAUSS = 4 };
 
 typedef struct {
     int32_t iters;     /* CG iterations taken (inner iterations for the mixed solver) */
@@ -357,20 +359,27 @@ fp_status fem_pic_field_last_info(fem_pic_t* ctx, fp_solve_info info[2], void* s
 fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha);
 
 /* ------------------------------------------------------------------ learned correction
- * Not in the paper (it defers its solver details).  A message-passing network on the edge
- * graph (graph nodes: edge DOFs; graph edges: nonzeros of A), 3 layers of 64 features,
- * BF16 weights with FP32 accumulation (tensor-core GEMMs), maps the Jacobi-scaled residual
- * of the Newmark guess 2E^n - E^{n-1} to a correction.  With precond = FP_PC_LEARNED in
- * fem_pic_field_step the corrected guess is used only when its residual is smaller than
- * the plain guess's (else fell_back = 1 in info[0]); the Newmark CG then runs to the same
- * tolerance either way.  The Gauss-law solve is not affected.  Requires
- * fem_pic_field_setup; a new setup discards the network. */
+ * Not in the paper (it defers its solver details).  A message-passing network on the graph
+ * of one system's operator (Newmark: graph nodes are the edge DOFs, graph edges the
+ * nonzeros of A; Gauss-law projection: the node DOFs and the nonzeros of L), 3 layers of 64
+ * features, BF16 weights with FP32 accumulation (tensor-core GEMMs), maps the Jacobi-scaled
+ * residual of the solve's starting point (Newmark: 2E^n - E^{n-1}; projection: 0) to a
+ * correction.  With FP_PC_LEARNED (Newmark) or FP_PC_LEARNED_GAUSS (projection) in the
+ * precond bits of fem_pic_field_step the corrected start is used only when its FP64
+ * residual is smaller than the plain one's (else fell_back = 1 in that system's info); the
+ * CG then runs to the same tolerance either way.  Each system has its own network; the
+ * fem_pic_learned_* calls address the system chosen by fem_pic_learned_select (Newmark
+ * until then).  Requires fem_pic_field_setup; a new setup discards the networks.  Vectors
+ * called [N] below have N_e entries for the Newmark system and N_n for the Gauss system. */
+
+/* Choose the system (FP_SYS_NEWMARK or FP_SYS_GAUSS) later fem_pic_learned_* calls address. */
+fp_status fem_pic_learned_select(fem_pic_t* ctx, int system);
 
 /* Allocate and initialise the network (seeded) and a store for sample_capacity training
  * residuals.  Synchronous. */
 fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity);
 
-/* collect != 0: every fem_pic_field_step stores the residual of its plain Newmark guess
+/* collect != 0: every fem_pic_field_step stores the residual of the system's plain start
  * (ring buffer; eager launches only: a captured graph would replay one slot).
  * active != 0: use the network in fem_pic_field_solve-independent steps as with
  * FP_PC_LEARNED. */
@@ -391,11 +400,11 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
 /* Parameters (FP32 master copy): get and/or set host arrays of *n_params floats. */
 fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params);
 
-/* Forward pass on one residual r (device double [N_e]): writes c~ and r~ (device float [N_e]). */
+/* Forward pass on one residual r (device double [N]): writes c~ and r~ (device float [N]). */
 fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out,
                                   void* stream);
 
-/* Loss gradient for one residual r (device float [N_e]) into grad_out (host float
+/* Loss gradient for one residual r (device float [N]) into grad_out (host float
  * [n_params]); the weights and optimizer state are left unchanged.  Synchronous. */
 fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_out, double* loss,
                                    void* stream);

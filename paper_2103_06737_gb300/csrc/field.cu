@@ -638,9 +638,9 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     info->ms = ms;
     info->precond = ctx->field->last_fp64[slot] ? FP_PC_JACOBI_FP64 : FP_PC_JACOBI;
     info->fell_back = 0;
-    if (slot == 0 && ctx->field->learned_used) {
+    if (ctx->field->learned_used[slot]) {
         int fl = 0;
-        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&fl, learned_flag(ctx->field), sizeof(int), cudaMemcpyDeviceToHost, s));
+        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&fl, learned_flag(ctx->field, slot), sizeof(int), cudaMemcpyDeviceToHost, s));
         FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         info->precond = FP_PC_LEARNED;
         info->fell_back = fl;
@@ -669,8 +669,8 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
         FP_CUDA_TRY(ctx, cudaGetLastError());
     }
     // learned correction of the guess (with fallback), and/or collection of its residual
-    if (learned_active(F)) {
-        fp_status sl = learned_newmark_guess(ctx, F->rhs, E_next, s);
+    if (learned_active(F, FP_SYS_NEWMARK)) {
+        fp_status sl = learned_guess(ctx, FP_SYS_NEWMARK, F->rhs, E_next, s);
         if (sl != FP_OK) return sl;
     }
     // Newmark solve for E^N from the guess 2E^n - E^{n-1} (written into E_next above)
@@ -689,6 +689,11 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
                                                       F->qd);
         FP_CUDA_TRY(ctx, cudaMemsetAsync(F->delta, 0, F->nn * sizeof(double), s));
         FP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    // learned correction of the projection's zero starting point (node graph), with fallback
+    if (learned_active(F, FP_SYS_GAUSS)) {
+        fp_status sl = learned_guess(ctx, FP_SYS_GAUSS, F->rhs, F->delta, s);
+        if (sl != FP_OK) return sl;
     }
     st = run_pcg(ctx, FP_SYS_GAUSS, F->rhs, F->delta, tol, F->qd, max_iter, 1, s);
     if (st != FP_OK) return st;
@@ -1163,18 +1168,22 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
                              double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                              int max_iter, int precond, fp_solve_info info[2], void* stream) {
     if (!ctx || !ctx->field || !E_prev || !E_cur || !E_next || !Q_new || !(tol > 0.0) || max_iter < 0 ||
-        (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64 && precond != FP_PC_LEARNED) ||
+        (precond & ~(FP_PC_LEARNED | FP_PC_JACOBI_FP64 | FP_PC_LEARNED_GAUSS)) != 0 ||
         E_next == E_cur || E_next == E_prev) {
         if (ctx) ctx->err = "fem_pic_field_step: bad argument (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
-    if (precond == FP_PC_LEARNED && !ctx->field->learned) {
-        ctx->err = "fem_pic_field_step: FP_PC_LEARNED needs fem_pic_learned_init";
-        return FP_EINVAL;
+    const bool use[2] = {(precond & FP_PC_LEARNED) != 0, (precond & FP_PC_LEARNED_GAUSS) != 0};
+    for (int k = 0; k < 2; ++k)
+        if (use[k] && !ctx->field->learned[k]) {
+            ctx->err = "fem_pic_field_step: a learned correction needs fem_pic_learned_init for its system";
+            return FP_EINVAL;
+        }
+    ctx->solver_fp64 = (precond & FP_PC_JACOBI_FP64) != 0;
+    for (int k = 0; k < 2; ++k) {
+        learned_set_active(ctx->field, k, use[k]);
+        ctx->field->learned_used[k] = use[k];
     }
-    ctx->solver_fp64 = precond == FP_PC_JACOBI_FP64;
-    learned_set_active(ctx->field, precond == FP_PC_LEARNED);
-    ctx->field->learned_used = precond == FP_PC_LEARNED;
     cudaStream_t s = (cudaStream_t)stream;
     fp_status st = field_step_impl(ctx, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol, max_iter, s);
     if (st != FP_OK || !info) return st;

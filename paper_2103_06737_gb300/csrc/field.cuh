@@ -64,8 +64,9 @@ struct FieldDev {
     int grid_e = 0, grid_n = 0;     // grids of the edge and node systems
     int bs_e = 256, bs_n = 256;     // and their block sizes
     int last_fp64[2] = {0, 0};      // solver used by the last solve in each info slot
-    LearnedDev* learned = nullptr;
-    bool learned_used = false;      // the last field step applied the learned guess
+    LearnedDev* learned[2] = {nullptr, nullptr};  // per system (Newmark, Gauss)
+    int learned_sys = FP_SYS_NEWMARK;              // system the fem_pic_learned_* calls address
+    bool learned_used[2] = {false, false};         // the last field step applied that learned guess
 };
 
 #ifdef __CUDACC__
@@ -112,9 +113,10 @@ __device__ __forceinline__ X sell_row(const Sell& S, const V* __restrict__ val, 
 
 // learned correction hooks (learned.cu)
 void learned_free(FieldDev* F);
-fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cudaStream_t s);
-bool learned_active(const FieldDev* F);
-int* learned_flag(FieldDev* F);
-void learned_set_active(FieldDev* F, bool on);
+void learned_free(FieldDev* F, int sys);
+fp_status learned_guess(fem_pic* ctx, int sys, const double* rhs, double* x0, cudaStream_t s);
+bool learned_active(const FieldDev* F, int sys);
+int* learned_flag(FieldDev* F, int sys);
+void learned_set_active(FieldDev* F, int sys, bool on);
 
 }  // namespace fempic

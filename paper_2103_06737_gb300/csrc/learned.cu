@@ -1,10 +1,11 @@
-// Learned correction of the Newmark field solve's starting point (not in the paper; the
-// paper defers its solver to Newmark-beta and gives no preconditioner).
+// Learned correction of a field solve's starting point (not in the paper; the paper defers
+// its solver to Newmark-beta and gives no preconditioner), for either system: the Newmark
+// edge system A = M + dt^2/4 S (graph nodes: edge DOFs) or the Gauss-law node Laplacian L
+// (graph nodes: node DOFs); graph edges are the operator's nonzeros.
 //
-// A message-passing network on the edge graph (graph nodes: edge DOFs; graph edges: the
-// nonzeros of A = M + dt^2/4 S) maps the Jacobi-scaled residual of the extrapolated guess,
+// A message-passing network maps the Jacobi-scaled residual of the starting point,
 // r~ = D^-1/2 (b - A x0) / s  (s = RMS over free rows), to a correction c~ with
-// A~ c~ ~ r~, A~ = D^-1/2 A D^-1/2; the guess becomes x0 + s D^-1/2 c~ when that lowers the
+// A~ c~ ~ r~, A~ = D^-1/2 A D^-1/2; the start becomes x0 + s D^-1/2 c~ when that lowers the
 // residual, otherwise it stays x0 (fallback).  CG to the same tolerance follows either way.
 //   h0 = relu(r~ w_e + b_e)                              (64 features)
 //   h_l = relu([h_{l-1} | A~ h_{l-1}] W_l + b_l)         l = 1..3, W_l 128 x 64
@@ -41,6 +42,12 @@ constexpr unsigned kFull = 0xffffffffu;
 }  // namespace
 
 struct LearnedDev {
+    // the system: its operator in SELL (FP64 values) and CSR form, and its fixed rows
+    int sys = FP_SYS_NEWMARK;
+    Sell S{nullptr, nullptr, nullptr};
+    const double* a64 = nullptr;
+    const int32_t *rp = nullptr, *col = nullptr;
+    const uint8_t* fixed = nullptr;
     int64_t n = 0, n_free = 0;
     float* a_sell = nullptr;      // A~ values in the SELL layout of A
     float* a_csr = nullptr;       // A~ values in the CSR order of A (warp-per-row neighbour sums)
@@ -544,34 +551,29 @@ int blocks(const fem_pic* ctx, int64_t work, int per_block = 256, int per_sm = 8
 // forward pass from a residual (FP64 or FP32) to c~; scal[4] = s.  store_m keeps the
 // neighbour sums of every layer for the backward pass.
 template <typename R>
-fp_status forward(fem_pic* ctx, const R* r, cudaStream_t s, bool store_m) {
-    FieldDev* F = ctx->field;
-    LearnedDev* L = F->learned;
-    const Sell S{F->se_ptr, F->se_w, F->se_col};
+fp_status forward(fem_pic* ctx, LearnedDev* L, const R* r, cudaStream_t s, bool store_m) {
     const int64_t n = L->n;
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal, 0, sizeof(float), s));
-    k_lm_sumsq<R><<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, L->scal);
-    k_lm_input<R><<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(r, L->dis, F->edge_fixed, n, (float)L->n_free, L->scal,
+    k_lm_sumsq<R><<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, L->fixed, n, L->scal);
+    k_lm_input<R><<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(r, L->dis, L->fixed, n, (float)L->n_free, L->scal,
                                                              L->params, L->rt, L->h[0], L->scal + 4);
     for (int l = 0; l < kLayers; ++l)
         k_lm_layer<<<blocks(ctx, (n + kLT - 1) / kLT * 256, 256, 4), 256, 0, s>>>(
-            F->e_rp, F->e_col, L->a_csr, L->h[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n,
+            L->rp, L->col, L->a_csr, L->h[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n,
             L->h[l + 1], store_m ? L->m[l] : nullptr);
-    k_lm_head<<<blocks(ctx, n * 32), 256, 0, s>>>(L->h[kLayers], L->params, L->rt, F->edge_fixed, n, L->ct);
+    k_lm_head<<<blocks(ctx, n * 32), 256, 0, s>>>(L->h[kLayers], L->params, L->rt, L->fixed, n, L->ct);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }
 
-fp_status train_step(fem_pic* ctx, const float* r, float lr, cudaStream_t s) {
-    FieldDev* F = ctx->field;
-    LearnedDev* L = F->learned;
-    const Sell S{F->se_ptr, F->se_w, F->se_col};
+fp_status train_step(fem_pic* ctx, LearnedDev* L, const float* r, float lr, cudaStream_t s) {
+    const Sell S = L->S;
     const int64_t n = L->n;
-    fp_status st = forward<float>(ctx, r, s, true);
+    fp_status st = forward<float>(ctx, L, r, s, true);
     if (st != FP_OK) return st;
     // loss = ||A~ c~ - r~||^2 / n_free;  dL/dc~ = 2/n_free A~ e
-    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, n, L->e, L->scal + 1);
-    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->e, nullptr, F->edge_fixed, 2.f / (float)L->n_free, n,
+    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, L->fixed, 1.f, n, L->e, L->scal + 1);
+    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(S, L->a_sell, L->e, nullptr, L->fixed, 2.f / (float)L->n_free, n,
                                              L->dct, nullptr);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->grads, 0, kNParams * sizeof(float), s));
     k_lm_head_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dct, L->h[kLayers], L->params, n, L->dh, L->grads);
@@ -581,7 +583,7 @@ fp_status train_step(fem_pic* ctx, const float* r, float lr, cudaStream_t s) {
         k_lm_relu_bwd<<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(L->dh, L->h[l + 1], n, L->dz, gW + kWsz);
         k_lm_gemm_dw<<<(unsigned)((n + rpb - 1) / rpb), 256, 0, s>>>(L->h[l], L->m[l], L->dz, n, rpb, gW);
         k_lm_gemm_dx<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(L->dz, L->Wn[l], n, L->dhd, L->dm);
-        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(F->e_rp, F->e_col, L->a_csr, L->dm, L->dhd, n, L->dh);
+        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->a_csr, L->dm, L->dhd, n, L->dh);
     }
     k_lm_enc_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dh, L->h[0], L->rt, n, L->grads);
     ++L->adam_t;
@@ -601,16 +603,19 @@ fp_status alloc(fem_pic* ctx, T** p, size_t count) {
 
 }  // namespace
 
-bool learned_active(const FieldDev* F) { return F && F->learned && (F->learned->active || F->learned->collecting); }
-
-int* learned_flag(FieldDev* F) { return F && F->learned ? F->learned->flag : nullptr; }
-
-void learned_set_active(FieldDev* F, bool on) {
-    if (F && F->learned) F->learned->active = on ? 1 : 0;
+bool learned_active(const FieldDev* F, int sys) {
+    const LearnedDev* L = F ? F->learned[sys] : nullptr;
+    return L && (L->active || L->collecting);
 }
 
-void learned_free(FieldDev* F) {
-    LearnedDev* L = F ? F->learned : nullptr;
+int* learned_flag(FieldDev* F, int sys) { return F && F->learned[sys] ? F->learned[sys]->flag : nullptr; }
+
+void learned_set_active(FieldDev* F, int sys, bool on) {
+    if (F && F->learned[sys]) F->learned[sys]->active = on ? 1 : 0;
+}
+
+void learned_free(FieldDev* F, int sys) {
+    LearnedDev* L = F ? F->learned[sys] : nullptr;
     if (!L) return;
     void* ptrs[] = {L->a_sell, L->a_csr, L->dis, L->params, L->grads, L->am, L->av, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0],
                     L->Wn[1], L->Wn[2], L->h[0], L->h[1], L->h[2], L->h[3], L->m[0], L->m[1], L->m[2], L->dz, L->dh,
@@ -618,15 +623,19 @@ void learned_free(FieldDev* F) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete L;
-    F->learned = nullptr;
+    F->learned[sys] = nullptr;
 }
 
-// Newmark starting point: collect the residual of the extrapolated guess as a training
-// sample and/or replace the guess by the learned one when it has the smaller residual.
-fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cudaStream_t s) {
-    FieldDev* F = ctx->field;
-    LearnedDev* L = F->learned;
-    const Sell S{F->se_ptr, F->se_w, F->se_col};
+void learned_free(FieldDev* F) {
+    learned_free(F, FP_SYS_NEWMARK);
+    learned_free(F, FP_SYS_GAUSS);
+}
+
+// Starting point of one system's solve: collect the residual of the plain start as a
+// training sample and/or replace the start by the learned one when it has the smaller
+// residual.  x0 is the plain start on entry (device, the solve's x).
+fp_status learned_guess(fem_pic* ctx, int sys, const double* rhs, double* x0, cudaStream_t s) {
+    LearnedDev* L = ctx->field->learned[sys];
     const int64_t n = L->n;
     float* slot = nullptr;
     if (L->collecting && L->cap > 0) {
@@ -636,15 +645,21 @@ fp_status learned_newmark_guess(fem_pic* ctx, const double* rhs, double* x0, cud
     }
     PhaseTimer pt(ctx, PH_LEARNED, s);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 2, 0, 2 * sizeof(float), s));
-    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, x0, F->edge_fixed, n, L->r0, slot, L->scal + 2);
+    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(L->S, L->a64, rhs, x0, L->fixed, n, L->r0, slot, L->scal + 2);
     if (!L->active) return FP_OK;
-    fp_status st = forward<double>(ctx, L->r0, s, false);
+    fp_status st = forward<double>(ctx, L, L->r0, s, false);
     if (st != FP_OK) return st;
     k_lm_candidate<<<blocks(ctx, n), 256, 0, s>>>(x0, L->ct, L->dis, L->scal, n, L->y);
-    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(S, F->se_A, rhs, L->y, F->edge_fixed, n, F->tmp, nullptr, L->scal + 3);
+    k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(L->S, L->a64, rhs, L->y, L->fixed, n, ctx->field->tmp, nullptr,
+                                              L->scal + 3);
     k_lm_select<<<blocks(ctx, n), 256, 0, s>>>(x0, L->y, L->scal, n, L->flag);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
+}
+
+// the network the fem_pic_learned_* calls address (nullptr: none)
+LearnedDev* cur(fem_pic* ctx) {
+    return ctx && ctx->field ? ctx->field->learned[ctx->field->learned_sys] : nullptr;
 }
 
 }  // namespace fempic
@@ -653,37 +668,60 @@ using namespace fempic;
 
 extern "C" {
 
+fp_status fem_pic_learned_select(fem_pic_t* ctx, int system) {
+    if (!ctx || !ctx->field || (system != FP_SYS_NEWMARK && system != FP_SYS_GAUSS)) {
+        if (ctx) ctx->err = "fem_pic_learned_select: bad system (or fem_pic_field_setup not called)";
+        return FP_EINVAL;
+    }
+    ctx->field->learned_sys = system;
+    return FP_OK;
+}
+
 fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity) {
     if (!ctx || !ctx->field || sample_capacity < 0) {
         if (ctx) ctx->err = "fem_pic_learned_init: call fem_pic_field_setup first";
         return FP_EINVAL;
     }
     FieldDev* F = ctx->field;
-    learned_free(F);
+    const int sys = F->learned_sys;
+    learned_free(F, sys);
     LearnedDev* L = new LearnedDev();
-    F->learned = L;
+    F->learned[sys] = L;
     const HostFields& H = F->host;
-    const int64_t n = F->ne;
+    // the system's operator: CSR on the host (values) and device, SELL on the device
+    const bool nm = sys == FP_SYS_NEWMARK;
+    const std::vector<int32_t>& hrp = nm ? H.e_rp : H.n_rp;
+    const std::vector<int32_t>& hcol = nm ? H.e_col : H.n_col;
+    const std::vector<uint8_t>& hfixed = nm ? H.edge_fixed : H.node_fixed;
+    std::vector<double> hval(hcol.size());
+    for (size_t j = 0; j < hcol.size(); ++j) hval[j] = nm ? H.M[j] + 0.25 * F->dt * F->dt * H.S[j] : H.L[j];
+    L->sys = sys;
+    L->S = nm ? Sell{F->se_ptr, F->se_w, F->se_col} : Sell{F->sn_ptr, F->sn_w, F->sn_col};
+    L->a64 = nm ? F->se_A : F->sn_L;
+    L->rp = nm ? F->e_rp : F->n_rp;
+    L->col = nm ? F->e_col : F->n_col;
+    L->fixed = nm ? F->edge_fixed : F->node_fixed;
+    const int64_t n = nm ? F->ne : F->nn;
     L->n = n;
     int64_t nfree = 0;
-    for (int64_t i = 0; i < n; ++i) nfree += H.edge_fixed[i] ? 0 : 1;
+    for (int64_t i = 0; i < n; ++i) nfree += hfixed[i] ? 0 : 1;
     L->n_free = nfree > 0 ? nfree : 1;
     // D^-1/2 and A~ in the SELL layout of A (values gathered from the device copy)
     std::vector<double> d(n, 1.0);
     for (int64_t i = 0; i < n; ++i)
-        for (int32_t j = H.e_rp[i]; j < H.e_rp[i + 1]; ++j)
-            if (H.e_col[j] == i) d[i] = H.M[j] + 0.25 * F->dt * F->dt * H.S[j];
+        for (int32_t j = hrp[i]; j < hrp[i + 1]; ++j)
+            if (hcol[j] == i) d[i] = hval[j];
     std::vector<float> dis(n);
     for (int64_t i = 0; i < n; ++i) dis[i] = (float)(1.0 / std::sqrt(d[i]));
     const int64_t ns = (n + 31) / 32;
     std::vector<int32_t> ptr(ns), w(ns);
-    FP_CUDA_TRY(ctx, cudaMemcpy(ptr.data(), F->se_ptr, ns * 4, cudaMemcpyDeviceToHost));
-    FP_CUDA_TRY(ctx, cudaMemcpy(w.data(), F->se_w, ns * 4, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(ptr.data(), L->S.ptr, ns * 4, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(w.data(), L->S.w, ns * 4, cudaMemcpyDeviceToHost));
     const int64_t tot = ns ? (int64_t)ptr[ns - 1] + 32 * (int64_t)w[ns - 1] : 0;
     std::vector<int32_t> col(tot);
     std::vector<double> av(tot);
-    FP_CUDA_TRY(ctx, cudaMemcpy(col.data(), F->se_col, tot * 4, cudaMemcpyDeviceToHost));
-    FP_CUDA_TRY(ctx, cudaMemcpy(av.data(), F->se_A, tot * 8, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(col.data(), L->S.col, tot * 4, cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(av.data(), L->a64, tot * 8, cudaMemcpyDeviceToHost));
     std::vector<float> at(tot);
     for (int64_t sl = 0; sl < ns; ++sl)
         for (int64_t lane = 0; lane < 32; ++lane) {
@@ -693,10 +731,9 @@ fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacit
                 at[k] = r < n ? (float)(av[k] * dis[r] * dis[col[k]]) : 0.f;
             }
         }
-    std::vector<float> ac(H.e_col.size());
+    std::vector<float> ac(hcol.size());
     for (int64_t i = 0; i < n; ++i)
-        for (int32_t j = H.e_rp[i]; j < H.e_rp[i + 1]; ++j)
-            ac[j] = (float)((H.M[j] + 0.25 * F->dt * F->dt * H.S[j]) * dis[i] * dis[H.e_col[j]]);
+        for (int32_t j = hrp[i]; j < hrp[i + 1]; ++j) ac[j] = (float)(hval[j] * dis[i] * dis[hcol[j]]);
     // parameters: small random layer weights, identity-like start (the head starts at 0)
     std::vector<float> P(kNParams, 0.f);
     std::mt19937_64 rng(seed);
@@ -749,22 +786,24 @@ fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacit
 }
 
 fp_status fem_pic_learned_mode(fem_pic_t* ctx, int collect, int active) {
-    if (!ctx || !ctx->field || !ctx->field->learned) return FP_EINVAL;
-    ctx->field->learned->collecting = collect != 0;
-    ctx->field->learned->active = active != 0;
+    LearnedDev* L = cur(ctx);
+    if (!L) return FP_EINVAL;
+    L->collecting = collect != 0;
+    L->active = active != 0;
     return FP_OK;
 }
 
 fp_status fem_pic_learned_samples(fem_pic_t* ctx, int* count) {
-    if (!ctx || !ctx->field || !ctx->field->learned || !count) return FP_EINVAL;
-    *count = ctx->field->learned->count;
+    LearnedDev* L = cur(ctx);
+    if (!L || !count) return FP_EINVAL;
+    *count = L->count;
     return FP_OK;
 }
 
 fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs, double lr, uint64_t seed,
                                 double* loss, void* stream) {
-    if (!ctx || !ctx->field || !ctx->field->learned || epochs < 0 || !(lr > 0.0)) return FP_EINVAL;
-    LearnedDev* L = ctx->field->learned;
+    LearnedDev* L = cur(ctx);
+    if (!L || epochs < 0 || !(lr > 0.0)) return FP_EINVAL;
     if (first < 0 || count < 1 || first + count > L->count) {
         ctx->err = "fem_pic_learned_train: sample range outside the collected samples";
         return FP_EINVAL;
@@ -780,7 +819,7 @@ fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs
             // cosine decay of the learning rate over the run
             const double t = (double)(ep * count) / (double)std::max(1, epochs * count);
             const float lr_t = (float)(lr * 0.5 * (1.0 + std::cos(3.141592653589793 * t)));
-            fp_status st = train_step(ctx, L->samples + (int64_t)k * L->n, lr_t, s);
+            fp_status st = train_step(ctx, L, L->samples + (int64_t)k * L->n, lr_t, s);
             if (st != FP_OK) return st;
         }
         if (loss) {
@@ -795,17 +834,15 @@ fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs
 
 fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* ratio, void* stream) {
     // ratio[k] = ||A~ c~ - r~||^2 / ||r~||^2 for sample first+k (1 = no better than zero guess)
-    if (!ctx || !ctx->field || !ctx->field->learned || !ratio) return FP_EINVAL;
-    LearnedDev* L = ctx->field->learned;
-    FieldDev* F = ctx->field;
+    LearnedDev* L = cur(ctx);
+    if (!L || !ratio) return FP_EINVAL;
     if (first < 0 || count < 1 || first + count > L->count) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const Sell S{F->se_ptr, F->se_w, F->se_col};
     for (int k = 0; k < count; ++k) {
-        fp_status st = forward<float>(ctx, L->samples + (int64_t)(first + k) * L->n, s, false);
+        fp_status st = forward<float>(ctx, L, L->samples + (int64_t)(first + k) * L->n, s, false);
         if (st != FP_OK) return st;
         FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
-        k_lm_spmv<<<blocks(ctx, L->n), 256, 0, s>>>(S, L->a_sell, L->ct, L->rt, F->edge_fixed, 1.f, L->n, L->e,
+        k_lm_spmv<<<blocks(ctx, L->n), 256, 0, s>>>(L->S, L->a_sell, L->ct, L->rt, L->fixed, 1.f, L->n, L->e,
                                                     L->scal + 1);
         float l = 0.f;
         FP_CUDA_TRY(ctx, cudaMemcpyAsync(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -816,8 +853,8 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
 }
 
 fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params) {
-    if (!ctx || !ctx->field || !ctx->field->learned) return FP_EINVAL;
-    LearnedDev* L = ctx->field->learned;
+    LearnedDev* L = cur(ctx);
+    if (!L) return FP_EINVAL;
     if (n_params) *n_params = kNParams;
     if (get) FP_CUDA_TRY(ctx, cudaMemcpy(get, L->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
     if (set) {
@@ -830,10 +867,10 @@ fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, i
 
 fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out, void* stream) {
     // c~ and r~ of one residual (device arrays), for tests
-    if (!ctx || !ctx->field || !ctx->field->learned || !r) return FP_EINVAL;
-    LearnedDev* L = ctx->field->learned;
+    LearnedDev* L = cur(ctx);
+    if (!L || !r) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    fp_status st = forward<double>(ctx, r, s, false);
+    fp_status st = forward<double>(ctx, L, r, s, false);
     if (st != FP_OK) return st;
     if (ct_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(ct_out, L->ct, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (rt_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(rt_out, L->rt, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -842,9 +879,8 @@ fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out
 
 fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_out, double* loss, void* stream) {
     // gradient of the loss for one residual without updating the weights, for tests
-    if (!ctx || !ctx->field || !ctx->field->learned || !r || !grad_out) return FP_EINVAL;
-    FieldDev* F = ctx->field;
-    LearnedDev* L = F->learned;
+    LearnedDev* L = cur(ctx);
+    if (!L || !r || !grad_out) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     // run a training step with lr = 0 and read the gradients before Adam touches them
     std::vector<float> keep(kNParams), keep_m(kNParams), keep_v(kNParams);
@@ -853,7 +889,7 @@ fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_o
     FP_CUDA_TRY(ctx, cudaMemcpy(keep_v.data(), L->av, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
     const int t_keep = L->adam_t;
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
-    fp_status st = train_step(ctx, r, 0.f, s);
+    fp_status st = train_step(ctx, L, r, 0.f, s);
     if (st != FP_OK) return st;
     FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     FP_CUDA_TRY(ctx, cudaMemcpy(grad_out, L->grads, kNParams * sizeof(float), cudaMemcpyDeviceToHost));

@@ -60,7 +60,7 @@ class SolveInfo(ctypes.Structure):
 
 
 FP_SYS_NEWMARK, FP_SYS_GAUSS = 0, 1
-FP_PC_JACOBI, FP_PC_LEARNED, FP_PC_JACOBI_FP64 = 0, 1, 2
+FP_PC_JACOBI, FP_PC_LEARNED, FP_PC_JACOBI_FP64, FP_PC_LEARNED_GAUSS = 0, 1, 2, 4
 EPS0 = 8.854_187_8128e-12
 MU0 = 1.256_637_062_12e-6
 
@@ -112,6 +112,7 @@ def lib():
             "fem_pic_field_poly": (I32, [P, I32, I32, D]),
             "fem_pic_whitney0_integrals": (I32, [P, P]),
             "fem_pic_learned_init": (I32, [P, ctypes.c_uint64, I32]),
+            "fem_pic_learned_select": (I32, [P, I32]),
             "fem_pic_learned_mode": (I32, [P, I32, I32]),
             "fem_pic_learned_samples": (I32, [P, P]),
             "fem_pic_learned_train": (I32, [P, I32, I32, I32, D, ctypes.c_uint64, P, P]),
@@ -415,6 +416,11 @@ def fem_pic_field_initial(h, Q, E, tol: float = 1e-10, max_iter: int = 10000, in
     if st not in (FP_OK, FP_ENOCONV):
         _check(st, h)
     return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_learned_select(h, system: int):
+    """Choose the system (FP_SYS_NEWMARK or FP_SYS_GAUSS) the fem_pic_learned_* calls address."""
+    _check(lib().fem_pic_learned_select(h, int(system)), h)
 
 
 def fem_pic_learned_init(h, seed: int = 0, sample_capacity: int = 64):

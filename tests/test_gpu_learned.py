@@ -1,6 +1,7 @@
-"""The learned Newmark correction: forward pass and gradients against a plain PyTorch CPU
-reference of the same network (BF16 rounding emulated at the same points), training on
-residuals the method produces, and the fallback-guarded field step matching plain CG.
+"""The learned corrections (Newmark edge system and Gauss-law node system): forward pass and
+gradients against a plain PyTorch CPU reference of the same network (BF16 rounding emulated
+at the same points), training on residuals the method produces, and the fallback-guarded
+field step matching plain CG.
 """
 import numpy as np
 import pytest
@@ -56,13 +57,14 @@ def forward_loss(params, Atil, dis, fixed, r):
     return ct, rt, loss
 
 
-def _setup(n_hex=5, steps=10, seed=1):
+def _setup(n_hex=5, steps=10, seed=1, system=F.FP_SYS_NEWMARK):
     m = I.cube_mesh(n_hex, 1.0, 0.1, seed=1)
     dt = 0.2 * I.gyro_period(0.1)
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP64)
     F.fem_pic_field_setup(lib.h, dt)
-    rp, col, val = F.fem_pic_field_matrix(lib.h, 2)
-    n = lib.n_edges
+    F.fem_pic_learned_select(lib.h, system)
+    rp, col, val = F.fem_pic_field_matrix(lib.h, 2 if system == F.FP_SYS_NEWMARK else 3)
+    n = lib.n_edges if system == F.FP_SYS_NEWMARK else lib.n_nodes
     A = np.zeros((n, n))
     for i in range(n):
         A[i, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
@@ -73,12 +75,13 @@ def _setup(n_hex=5, steps=10, seed=1):
     return m, lib, torch.as_tensor(Atil), torch.as_tensor(dis.astype(np.float32)), torch.as_tensor(fixed), dt
 
 
-def test_forward_and_gradient_match_reference():
-    m, lib, Atil, dis, fixed, dt = _setup()
+@pytest.mark.parametrize("system", [F.FP_SYS_NEWMARK, F.FP_SYS_GAUSS])
+def test_forward_and_gradient_match_reference(system):
+    m, lib, Atil, dis, fixed, dt = _setup(n_hex=5 if system == F.FP_SYS_NEWMARK else 8, system=system)
     F.fem_pic_learned_init(lib.h, seed=3, sample_capacity=4)
     P = F.fem_pic_learned_params(lib.h)
     rng = np.random.default_rng(0)
-    r = rng.normal(0, 1e-12, lib.n_edges)
+    r = rng.normal(0, 1e-12, Atil.shape[0])
     r[fixed.numpy()] = 0.0
     ct_g, rt_g = F.fem_pic_learned_forward(lib.h, torch.as_tensor(r, device="cuda"))
     we, be, W, b, wh, bh = _unpack(P)
@@ -148,4 +151,31 @@ def test_training_lowers_the_loss_and_learned_steps_match_plain():
     assert all(i[0]["rel_res"] <= 1e-10 for i in info_learn)
     err = (E_learn - E_plain).abs().max() / E_plain.abs().max()
     assert float(err) < 1e-7
+    lib.close()
+
+
+def test_gauss_training_and_learned_projection_match_plain():
+    """The node-graph network on the Gauss-law projection: samples are the projection's
+    right-hand sides (zero start), training lowers the held-out loss, and field steps with
+    FP_PC_LEARNED_GAUSS reach the same tolerance and the same field as plain CG."""
+    m, lib, Atil, dis, fixed, dt = _setup(n_hex=6, system=F.FP_SYS_GAUSS)
+    F.fem_pic_learned_init(lib.h, seed=2, sample_capacity=32)
+    F.fem_pic_learned_mode(lib.h, collect=True, active=False)
+    E_plain, info_plain = _run_steps(lib, m, dt, 24, precond=F.FP_PC_JACOBI)
+    assert F.fem_pic_learned_samples(lib.h) == 24
+    before = F.fem_pic_learned_eval(lib.h, 20, 4)
+    loss = F.fem_pic_learned_train(lib.h, 0, 20, epochs=40, lr=2e-3, seed=0)
+    after = F.fem_pic_learned_eval(lib.h, 20, 4)
+    assert loss[-1] < loss[0]
+    assert after.mean() < before.mean()
+    F.fem_pic_learned_mode(lib.h, collect=False, active=False)
+    E_learn, info_learn = _run_steps(lib, m, dt, 24, precond=F.FP_PC_LEARNED_GAUSS)
+    assert all(i[1]["precond"] == F.FP_PC_LEARNED for i in info_learn)
+    assert all(i[0]["precond"] != F.FP_PC_LEARNED for i in info_learn)
+    assert all(i[0]["rel_res"] <= 1e-10 and i[1]["rel_res"] <= 1e-10 for i in info_learn)
+    err = (E_learn - E_plain).abs().max() / E_plain.abs().max()
+    assert float(err) < 1e-7
+    # both corrections at once need both networks; the Newmark one was never initialised
+    with pytest.raises(F.FemPicError):
+        _run_steps(lib, m, dt, 1, precond=F.FP_PC_LEARNED | F.FP_PC_LEARNED_GAUSS)
     lib.close()
