@@ -324,8 +324,9 @@ def run_gpu(args):
         sort_now = args.sort_every > 0 and i > 0 and i % args.sort_every == 0
         return sort_now, tuple(cur)
 
-    def enqueue(pl):
-        """One PIC step on the current stream; returns the number of library kernels launched."""
+    def enqueue_push(pl):
+        """The step's particle part on the current stream (periodic sort, push, deposits):
+        returns (library kernels launched, the species' buffers it used)."""
         sort_now, before = pl
         n_k = 0
         use = []
@@ -341,6 +342,12 @@ def run_gpu(args):
         for k, s_ in enumerate(use):     # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}
             lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE)
             n_k += 3              # field prep, fast push, FP64 walk of the queued particles
+        return n_k, use
+
+    def enqueue_field():
+        """The step's field part on the current stream (field step, residuals, leapfrog state);
+        it does not touch the particle state.  Returns the library kernels launched."""
+        n_k = 0
         if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
             F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
                                  max_iter=args.max_iter, precond=state["precond"], info=False)
@@ -359,6 +366,11 @@ def run_gpu(args):
             E_prev.copy_(e)
             e.copy_(E_next)
         return n_k
+
+    def enqueue(pl):
+        """One PIC step on the current stream; returns the number of library kernels launched."""
+        n_k, _ = enqueue_push(pl)
+        return n_k + enqueue_field()
 
     def advance(pl):
         if pl[0]:
@@ -579,12 +591,41 @@ def run_gpu(args):
             sum(h_.numel() * h_.element_size() for _, h_ in fin)
         bo = sum(x.numel() * x.element_size() for tr in hs for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
             (hE.numel() * 8 if field else 0)
+        # Each step: the inputs' host-to-device copies, the particle part (one CUDA graph per
+        # step shape), the particle state's device-to-host copy on a second stream (it overlaps
+        # the field part, which does not touch the particles), the field part (a second graph),
+        # the results' device-to-host copies, and the join of both streams.
+        copy_stream = torch.cuda.Stream(device=dev)
+        e2e_graphs = {}
+
+        def e2e_graph(pl):
+            key = (pl, state["precond"])
+            if key not in e2e_graphs:
+                ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+                with torch.cuda.graph(ga):
+                    _, use = enqueue_push(pl)
+                with torch.cuda.graph(gb):
+                    enqueue_field()
+                e2e_graphs[key] = (ga, gb, use)
+                torch.cuda.synchronize()
+            return e2e_graphs[key]
+        restore()
+        for k in range(args.steps):      # capture every shape of the run first (not timed)
+            pl = plan(k)
+            e2e_graph(pl)
+            advance(pl)
+        restore()
+        species = [bufs[k][cur[k]] for k in range(len(species))]
         torch.cuda.synchronize()
-        ee = []
+        ee, parts = [], []
         for k in range(args.steps):
             flush_l2(k)
+            pl = plan(state["i"])
+            ga, gb, use = e2e_graph(pl)
             a = torch.cuda.Event(enable_timing=True)
+            h = torch.cuda.Event(enable_timing=True)
             z = torch.cuda.Event(enable_timing=True)
+            pushed, copied = torch.cuda.Event(), torch.cuda.Event()
             a.record(stream)
             for (hc, ho, hv), s in zip(hs, species):
                 s.cell.copy_(hc, non_blocking=True)
@@ -592,25 +633,39 @@ def run_gpu(args):
                 s.vel.copy_(hv, non_blocking=True)
             for d_, h_ in fin:
                 d_.copy_(h_, non_blocking=True)
-            eager_step()
-            for (hc, ho, hv), s in zip(hs, species):
-                hc.copy_(s.cell, non_blocking=True)
-                ho.copy_(s.off, non_blocking=True)
-                hv.copy_(s.vel, non_blocking=True)
+            h.record(stream)
+            ga.replay()
+            pushed.record(stream)
+            copy_stream.wait_event(pushed)
+            with torch.cuda.stream(copy_stream):
+                for (hc, ho, hv), s in zip(hs, use):
+                    hc.copy_(s.cell, non_blocking=True)
+                    ho.copy_(s.off, non_blocking=True)
+                    hv.copy_(s.vel, non_blocking=True)
+                copied.record(copy_stream)
+            gb.replay()
             hdG.copy_(dG, non_blocking=True)
             hQ.copy_(Qn, non_blocking=True)
             if field:
                 hE.copy_(e, non_blocking=True)
-            species = [bufs[k][cur[k]] for k in range(len(species))]
+            stream.wait_event(copied)
             z.record(stream)
+            advance(pl)
+            state["i"] += 1
+            species = [bufs[k][cur[k]] for k in range(len(species))]
             ee.append((a, z))
+            parts.append((a, h))
         torch.cuda.synchronize()
         e2e_ms = sum(a.elapsed_time(z) for a, z in ee)
         tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e = {"value": world * alive0 * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+               "ms_per_step": e2e_ms / args.steps,
+               "h2d_ms_per_step": sum(a.elapsed_time(h) for a, h in parts) / args.steps,
+               "overlap": "particle state copied back on a second stream during the field step; the step's "
+                          "particle and field parts replayed as CUDA graphs"}
 
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
                                                              Qn, flush_l2, stream, sizes, wl, dev)
