@@ -13,7 +13,16 @@ The field step (the reading of Sec. IV.B with Newmark-beta, beta = 1/4, gamma = 
   2. Gauss-law projection (Eq. discreteGauss with the modified projector, Eq. efld_mod_proj):
        L d = D0^T M E^N + Q^{n+1},  L = D0^T M D0  (interior nodes);   E^{n+1} = E^N - D0 d
   3. Faraday: b^{n+1} = b^n - dt D1 (E^{n+1} + E^n)/2.
-PEC walls: edge DOFs on boundary edges and the correction d on boundary nodes are zero.
+Boundary conditions (bc):
+  "pec"      PEC walls: edge DOFs on boundary edges and the correction d on boundary nodes
+             are zero.
+  "neumann"  natural boundary: no DOF is fixed.  L is then singular (constants), and the
+             projection takes the zero-mean constraint of Eq. zero_mean_constraint: d = C_z y
+             with C_z the identity on the first n-1 nodes and the last row -alpha_i/alpha_n
+             (alpha_i the integral of W0_i), y from (C_z^T L C_z) y = C_z^T g.  Then
+             alpha^T d = 0 and L d = g - (sum g / sum alpha) alpha: a net charge is spread as a
+             uniform background (the modification the paper asks for when the net charge is
+             not zero).
 """
 from __future__ import annotations
 
@@ -109,10 +118,23 @@ def _solve(Amat, rhs, tol=1e-13):
     return x
 
 
-class FieldOracle:
-    """Implicit field step on one mesh for a fixed dt (PEC boundary)."""
+def zero_mean_constraint(alpha: np.ndarray) -> sp.csr_matrix:
+    """C_z of Eq. zero_mean_constraint, n x (n-1): identity on the first n-1 rows, last row
+    -alpha_i / alpha_n, so that alpha^T (C_z y) = 0 for every y."""
+    n = alpha.shape[0]
+    rows = np.concatenate([np.arange(n - 1), np.full(n - 1, n - 1)])
+    cols = np.concatenate([np.arange(n - 1), np.arange(n - 1)])
+    vals = np.concatenate([np.ones(n - 1), -alpha[:-1] / alpha[-1]])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n - 1))
 
-    def __init__(self, cx: Complex, dt: float, eps: float = EPS0, mu: float = MU0):
+
+class FieldOracle:
+    """Implicit field step on one mesh for a fixed dt (bc: "pec" or "neumann")."""
+
+    def __init__(self, cx: Complex, dt: float, eps: float = EPS0, mu: float = MU0, bc: str = "pec"):
+        if bc not in ("pec", "neumann"):
+            raise ValueError("bc is 'pec' or 'neumann'")
+        self.bc = bc
         self.cx = cx
         self.dt = dt
         self.M = edge_mass(cx, eps)
@@ -121,10 +143,18 @@ class FieldOracle:
         self.D1 = cx.D1().astype(np.float64).tocsr()
         self.A = (self.M + 0.25 * dt * dt * self.S).tocsr()
         self.L = (self.D0.T @ self.M @ self.D0).tocsr()
-        self.ie = np.nonzero(~cx.boundary_edge)[0]          # interior (free) edges
-        self.inn = np.nonzero(~cx.boundary_node)[0]         # interior nodes
+        if bc == "pec":
+            self.ie = np.nonzero(~cx.boundary_edge)[0]      # interior (free) edges
+            self.inn = np.nonzero(~cx.boundary_node)[0]     # interior nodes
+        else:
+            self.ie = np.arange(cx.n_edges)
+            self.inn = np.arange(cx.n_nodes)
         self.A_II = self.A[self.ie][:, self.ie].tocsr()
         self.L_II = self.L[self.inn][:, self.inn].tocsr()
+        self.alpha = cx.node_volume()
+        if bc == "neumann":
+            self.Cz = zero_mean_constraint(self.alpha)
+            self.L_z = (self.Cz.T @ self.L @ self.Cz).tocsr()
 
     def newmark_rhs(self, En, Enm1, dG_half, dG_prev):
         dt2 = self.dt * self.dt
@@ -142,7 +172,10 @@ class FieldOracle:
     def gauss_project(self, E, Q):
         g = self.gauss_rhs(E, Q)
         d = np.zeros(self.cx.n_nodes)
-        d[self.inn] = _solve(self.L_II, g[self.inn])
+        if self.bc == "pec":
+            d[self.inn] = _solve(self.L_II, g[self.inn])
+        else:
+            d = self.Cz @ _solve(self.L_z, self.Cz.T @ g)
         return E - self.D0 @ d, d
 
     def faraday(self, b, E_new, E_old):
@@ -154,10 +187,13 @@ class FieldOracle:
         return E1, self.faraday(b, E1, En)
 
     def gauss_residual(self, E, Q):
-        """Interior-node Gauss residual D0^T M E + Q and its scale."""
-        r = self.gauss_rhs(E, Q)[self.inn]
+        """Gauss residual D0^T M E + Q on the free nodes and its scale (Neumann: less the net
+        charge spread as alpha, the part the zero-mean projection leaves by construction)."""
+        r = self.gauss_rhs(E, Q)
+        if self.bc == "neumann":
+            r = r - (Q.sum() / self.alpha.sum()) * self.alpha
         sc = (np.abs(self.D0.T) @ np.abs(self.M @ E))[self.inn] + np.abs(Q[self.inn])
-        return r, sc
+        return r[self.inn], sc
 
     def initial_field(self, Q):
         """E with D0^T M E + Q = 0 at interior nodes and no solenoidal part (the start state)."""

@@ -7,7 +7,9 @@ curl W1_ab = 2 grad l_a x grad l_b (test); D0^T [*eps] D0 (oracle) equals the P1
 stiffness eps |T| grad l_a . grad l_b (test); [*S] D0 = 0 (curl grad = 0); the
 Newmark amplification matrix has its eigenvalues on the unit circle (Sec. VI.A.1);
 the sparse Gauss-law projection equals the dense modified projector of Eq.
-efld_mod_proj; Faraday keeps D2 b = 0.
+efld_mod_proj; Faraday keeps D2 b = 0.  Natural (Neumann) boundary: C_z annihilates alpha,
+the constrained projection equals the pseudo-inverse route shifted to alpha-mean zero, and
+the Gauss law holds at every node up to the net charge spread as alpha.
 """
 import numpy as np
 import pytest
@@ -150,3 +152,68 @@ def test_newmark_keeps_gauss_law_with_a_continuity_respecting_current(mesh4):
         g, sc = fo.gauss_residual(E_new, r["Q"])
         assert np.abs(g).max() <= 1e-11 * sc.max()
         E_prev, E, dG_prev = E, E_new, r["dG"]
+
+
+# ---------------------------------------------------------------- natural (Neumann) boundary
+def test_zero_mean_constraint_matrix(mesh4):
+    """C_z of Eq. zero_mean_constraint: alpha^T C_z = 0, identity on the first n-1 rows, rank n-1."""
+    a = mesh4.node_volume()
+    assert abs(a.sum() - 1.0) < 1e-13                     # the W0 integrals add up to |Omega| = 1 m^3
+    Cz = OF.zero_mean_constraint(a).toarray()
+    n = a.size
+    assert Cz.shape == (n, n - 1)
+    assert np.array_equal(Cz[:-1], np.eye(n - 1))
+    assert np.abs(a @ Cz).max() <= 1e-15
+    assert np.linalg.matrix_rank(Cz) == n - 1
+
+
+def test_neumann_laplacian_null_space_and_newmark_stability():
+    m = I.cube_mesh(3, 1.0, 0.1, seed=1)
+    cx = O.Complex(m.xyz, m.tets)
+    dt = 2.0 * (1.0 / 3.0) / I.C_LIGHT
+    fo = OF.FieldOracle(cx, dt, bc="neumann")
+    assert np.abs(fo.L @ np.ones(cx.n_nodes)).max() <= 1e-12 * abs(fo.L).max()
+    assert len(fo.ie) == cx.n_edges and len(fo.inn) == cx.n_nodes
+    mu = np.linalg.eigvals(fo.amplification_matrix())
+    assert np.abs(np.abs(mu) - 1.0).max() < 1e-7
+
+
+def test_neumann_projection_against_pseudo_inverse(mesh4):
+    """The C_z-reduced solve against an independent route: the pseudo-inverse of the singular
+    L applied to the consistent part of g, shifted to alpha-mean zero."""
+    cx = mesh4
+    fo = OF.FieldOracle(cx, 1e-10, bc="neumann")
+    rng = np.random.default_rng(3)
+    EN = rng.uniform(-1, 1, cx.n_edges)
+    Q = rng.uniform(-1e-12, 1e-12, cx.n_nodes) + 2e-13          # a net charge
+    E1, d = fo.gauss_project(EN, Q)
+    a = fo.alpha
+    g = fo.gauss_rhs(EN, Q)
+    L = fo.L.toarray()
+    dp = np.linalg.pinv(L) @ (g - g.sum() / a.sum() * a)
+    d_ref = dp - (a @ dp) / a.sum()
+    assert np.abs(d - d_ref).max() <= 1e-9 * np.abs(d_ref).max()
+    assert np.abs(E1 - (EN - fo.D0 @ d_ref)).max() <= 1e-9 * np.abs(EN).max()
+
+
+def test_neumann_gauss_law_and_zero_mean(mesh4):
+    cx = mesh4
+    fo = OF.FieldOracle(cx, 1e-10, bc="neumann")
+    rng = np.random.default_rng(4)
+    EN = rng.uniform(-1, 1, cx.n_edges)
+    Q = rng.uniform(-1e-12, 1e-12, cx.n_nodes)
+    E1, d = fo.gauss_project(EN, Q)
+    a = fo.alpha
+    assert abs(a @ d) <= 1e-12 * (a @ np.abs(d))                 # zero mean (the constraint)
+    # Gauss law at every node, less the net charge spread as alpha
+    lhs = fo.D0.T @ (fo.M @ E1) + Q
+    scale = (np.abs(fo.D0.T) @ np.abs(fo.M @ E1) + np.abs(Q)).max()
+    assert np.abs(lhs - Q.sum() / a.sum() * a).max() <= 1e-11 * scale
+    r, sc = fo.gauss_residual(E1, Q)
+    assert np.abs(r).max() <= 1e-11 * sc.max()
+    # a neutral charge satisfies the Gauss law exactly, boundary nodes included
+    Qn = Q - Q.sum() / a.sum() * a
+    E2, _ = fo.gauss_project(EN, Qn)
+    assert np.abs(fo.D0.T @ (fo.M @ E2) + Qn).max() <= 1e-11 * scale
+    # boundary edges are free under the natural boundary
+    assert np.abs(E1[cx.boundary_edge]).max() > 0
