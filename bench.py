@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--learn-samples", type=int, default=48)
     ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--compare-steps", type=int, default=20)
+    ap.add_argument("--neumann-steps", type=int, default=10,
+                    help="timed field steps with the natural (Neumann) field boundary (0: skip)")
     ap.add_argument("--adams-steps", type=int, default=20,
                     help="timed calls of the fourth-order Adams particle step (0: skip that measurement)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
@@ -669,6 +671,55 @@ def run_gpu(args):
 
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
                                                              Qn, flush_l2, stream, sizes, wl, dev)
+    def measure_neumann():
+        """The PIC step with the natural (Neumann) field boundary and the zero-mean constrained
+        Gauss-law projection: fields set up again with FP_BC_NEUMANN (this replaces the PEC
+        setup, so it runs last), the initial state restored, E^0 from its charge, then
+        args.neumann_steps timed eager steps (L2 flushed between them) with the per-phase
+        profiler on."""
+        F.fem_pic_field_setup(lib.h, wl.dt, bc=F.FP_BC_NEUMANN)
+        F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], prat[1])
+        state["precond"] = precond
+        restore()
+        st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
+        E_prev.copy_(e)
+        for _ in range(3):
+            eager_step()
+        torch.cuda.synchronize()
+        F.fem_pic_profile_read(lib.h, reset=True)
+        F.fem_pic_profile_enable(lib.h, True)
+        ev, its, rr, live = [], [], [], []
+        for k in range(args.neumann_steps):
+            live.append(alive())
+            flush_l2(2000 + k)
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eager_step()
+            z.record(stream)
+            ev.append((a, z))
+            fi = F.fem_pic_field_last_info(lib.h)
+            its.append((fi[0]["iters"], fi[1]["iters"]))
+            rr.append(max(fi[0]["rel_res"], fi[1]["rel_res"]))
+        torch.cuda.synchronize()
+        F.fem_pic_profile_enable(lib.h, False)
+        ph = F.fem_pic_profile_read(lib.h, reset=True)
+        ms = sum(a.elapsed_time(z) for a, z in ev) / len(ev)
+        nsteps = len(ev)
+        return {"ms_per_step": ms, "particle_steps_per_s": sum(live) / (ms * nsteps * 1e-3),
+                "timed_steps": nsteps, "initial_status": int(st0), "launches": "eager",
+                "field_ms_per_step": sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss"))
+                / nsteps,
+                "ms_newmark_cg": ph.get("cg_newmark", (0.0, 1))[0] / nsteps,
+                "ms_gauss_cg": ph.get("cg_gauss", (0.0, 1))[0] / nsteps,
+                "newmark_iters_mean": float(np.mean([i[0] for i in its])),
+                "gauss_iters_mean": float(np.mean([i[1] for i in its])), "max_rel_res": max(rr),
+                "status": int(lib.status()),
+                "what": "PIC step with the natural field boundary: Newmark over all edges, Gauss-law projection "
+                        "with the zero-mean constraint (a net charge spread as alpha), Faraday"}
+    neumann = None if (args.neumann_steps <= 0 or not field) else measure_neumann()
 
     out = None
     if rank == 0:
@@ -772,6 +823,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "e2e": e2e,
             "adams": adams,
+            "neumann": neumann,
         }
     del lib
     if world > 1:

@@ -281,6 +281,20 @@ typedef struct {
  */
 fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu);
 
+/* Field boundary conditions: FP_BC_PEC (the default of fem_pic_field_setup) fixes the
+ * tangential E on boundary edges and the projection's correction on boundary nodes at zero;
+ * FP_BC_NEUMANN is the natural boundary (nothing fixed).  Then the node Laplacian L is
+ * singular (its null space the constants) and the Gauss-law projection takes the zero-mean
+ * constraint of Eq. zero_mean_constraint (Sec. IV.B): d = C_z y with alpha^T d = 0 (alpha_n
+ * the integral of W0_n), which solves L d = g - (sum g / sum alpha) alpha, i.e. a net charge
+ * is spread as a uniform background, as the paper asks when the net charge is not zero.
+ * The library solves that consistent system with the same CG and shifts d to alpha^T d = 0.
+ * Particles are absorbed at the boundary under either condition. */
+enum { FP_BC_PEC = 0, FP_BC_NEUMANN = 1 };
+
+/* fem_pic_field_setup with a boundary condition bc (FP_BC_*); FP_EINVAL for another bc. */
+fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double mu, int bc);
+
 /* nnz[0] = entries of the edge operators (M, S, A), nnz[1] = entries of L. */
 fp_status fem_pic_field_nnz(const fem_pic_t* ctx, int64_t nnz[2]);
 

@@ -648,6 +648,64 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     return FP_OK;
 }
 
+// Natural boundary (Eq. zero_mean_constraint): the projection solves L d = g - (sum g / sum
+// alpha) alpha (L is singular, its null space the constants; the net charge is spread as
+// alpha) and takes the solution with alpha^T d = 0, the d = C_z y of the constrained system.
+// Both use a deterministic reduction: per-block partial sums, then every block adds the
+// partials in block order before it updates its entries.
+constexpr int kMeanBlocks = 128;
+
+// part[b] = sum over block b's entries of v (w == nullptr) or of w v
+__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ v, const double* __restrict__ w,
+                                                     int64_t n, double* __restrict__ part) {
+    __shared__ double sh[8];
+    double t = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t += w ? w[i] * v[i] : v[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < 8; ++k) u += sh[k];
+        part[blockIdx.x] = u;
+    }
+}
+
+// y -= (scale sum_b part[b]) dir  (dir == nullptr: the constant vector 1)
+__global__ void __launch_bounds__(256) k_sub_scaled(const double* __restrict__ part, int np, double scale,
+                                                    const double* __restrict__ dir, int64_t n, double* __restrict__ y) {
+    __shared__ double c;
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < np; ++k) u += part[k];
+        c = scale * u;
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] -= dir ? c * dir[i] : c;
+}
+
+// the projection's right-hand side made consistent (natural boundary only)
+fp_status neumann_rhs(fem_pic* ctx, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    if (F->bc != FP_BC_NEUMANN) return FP_OK;
+    k_dot_partial<<<kMeanBlocks, 256, 0, s>>>(F->rhs, nullptr, F->nn, F->msum);
+    k_sub_scaled<<<kMeanBlocks, 256, 0, s>>>(F->msum, kMeanBlocks, 1.0 / F->alpha_sum, F->alpha, F->nn, F->rhs);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+// the projection's solution shifted to alpha^T d = 0 (natural boundary only)
+fp_status neumann_gauge(fem_pic* ctx, cudaStream_t s) {
+    FieldDev* F = ctx->field;
+    if (F->bc != FP_BC_NEUMANN) return FP_OK;
+    k_dot_partial<<<kMeanBlocks, 256, 0, s>>>(F->delta, F->alpha, F->nn, F->msum);
+    k_sub_scaled<<<kMeanBlocks, 256, 0, s>>>(F->msum, kMeanBlocks, 1.0 / F->alpha_sum, nullptr, F->nn, F->delta);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
 fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
                           double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                           int max_iter, cudaStream_t s) {
@@ -689,6 +747,8 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
                                                       F->qd);
         FP_CUDA_TRY(ctx, cudaMemsetAsync(F->delta, 0, F->nn * sizeof(double), s));
         FP_CUDA_TRY(ctx, cudaGetLastError());
+        fp_status sn = neumann_rhs(ctx, s);
+        if (sn != FP_OK) return sn;
     }
     // learned correction of the projection's zero starting point (node graph), with fallback
     if (learned_active(F, FP_SYS_GAUSS)) {
@@ -699,6 +759,8 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
     if (st != FP_OK) return st;
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
+        st = neumann_gauge(ctx, s);
+        if (st != FP_OK) return st;
         FP_CUDA_TRY(ctx, cudaMemcpyAsync(F->tmp, E_next, F->ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
         k_project<<<ge, kBlock, 0, s>>>(ctx->d_edges, F->edge_fixed, F->delta, F->tmp, F->ne, E_next);
         if (b) k_faraday<<<grid_of(ctx, F->nf), kBlock, 0, s>>>(F->face_edges, E_next, E_cur, 0.5 * F->dt, F->nf, b);
@@ -716,7 +778,7 @@ void field_free(fem_pic* ctx) {
     void* ptrs[] = {F->e_rp, F->e_col, F->n_rp, F->n_col, F->Mv, F->Sv, F->Av, F->Adinv, F->Lv, F->Ldinv,
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
-                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->pe_ptr, F->pe_w, F->pe_col, F->perm_e, F->pe_A, F->pe_A32, F->pe_dinv32, F->pb, F->px, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
+                    F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->pe_ptr, F->pe_w, F->pe_col, F->perm_e, F->pe_A, F->pe_A32, F->pe_dinv32, F->pb, F->px, F->alpha, F->msum, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
                     F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -731,16 +793,20 @@ using namespace fempic;
 extern "C" {
 
 fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) {
-    if (!ctx || !(dt > 0.0) || !(eps > 0.0) || !(mu > 0.0)) {
-        if (ctx) ctx->err = "fem_pic_field_setup: dt, eps and mu must be positive";
+    return fem_pic_field_setup_bc(ctx, dt, eps, mu, FP_BC_PEC);
+}
+
+fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double mu, int bc) {
+    if (!ctx || !(dt > 0.0) || !(eps > 0.0) || !(mu > 0.0) || (bc != FP_BC_PEC && bc != FP_BC_NEUMANN)) {
+        if (ctx) ctx->err = "fem_pic_field_setup: dt, eps and mu must be positive, bc FP_BC_PEC or FP_BC_NEUMANN";
         return FP_EINVAL;
     }
     field_free(ctx);
     FieldDev* F = new FieldDev();
     ctx->field = F;
     const HostComplex& hc = ctx->hc;
-    F->dt = dt, F->eps = eps, F->mu = mu, F->ne = hc.ne, F->nn = hc.nn, F->nf = hc.nf;
-    assemble_fields(hc, eps, mu, &F->host);
+    F->dt = dt, F->eps = eps, F->mu = mu, F->ne = hc.ne, F->nn = hc.nn, F->nf = hc.nf, F->bc = bc;
+    assemble_fields(hc, eps, mu, bc == FP_BC_PEC, &F->host);
     const HostFields& H = F->host;
     std::vector<double> A(H.M.size()), Ad(hc.ne), Ld(hc.nn);
     for (size_t k = 0; k < A.size(); ++k) A[k] = H.M[k] + 0.25 * dt * dt * H.S[k];
@@ -1058,6 +1124,14 @@ fp_status fem_pic_field_setup(fem_pic_t* ctx, double dt, double eps, double mu) 
         FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->out, 16 * sizeof(double)));
         FP_CUDA_TRY(ctx, cudaMemset(F->out, 0, 16 * sizeof(double)));
     }
+    if (st == FP_OK && bc == FP_BC_NEUMANN) {
+        std::vector<double> a(hc.nn);
+        st = fem_pic_whitney0_integrals(ctx, a.data());
+        F->alpha_sum = 0.0;
+        for (double v : a) F->alpha_sum += v;
+        if (st == FP_OK) st = up(ctx, &F->alpha, a);
+        if (st == FP_OK) FP_CUDA_TRY(ctx, cudaMalloc((void**)&F->msum, kMeanBlocks * sizeof(double)));
+    }
     return st;
 }
 
@@ -1211,7 +1285,9 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
         k_gauss_rhs<double><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
                                                   F->tmp, (const double*)Q, F->nn, F->rhs, F->qd);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(F->delta, 0, F->nn * sizeof(double), s));
-    fp_status st = run_pcg(ctx, FP_SYS_GAUSS, F->rhs, F->delta, tol, F->qd, max_iter, 1, s);
+    fp_status st = neumann_rhs(ctx, s);
+    if (st == FP_OK) st = run_pcg(ctx, FP_SYS_GAUSS, F->rhs, F->delta, tol, F->qd, max_iter, 1, s);
+    if (st == FP_OK) st = neumann_gauge(ctx, s);
     if (st != FP_OK) return st;
     k_project<<<ge, kBlock, 0, s>>>(ctx->d_edges, F->edge_fixed, F->delta, F->tmp, F->ne, E);
     FP_CUDA_TRY(ctx, cudaGetLastError());

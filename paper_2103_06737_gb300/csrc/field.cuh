@@ -13,7 +13,8 @@ struct HostFields {
     std::vector<double> L;                         // D0^T [*eps] D0
 };
 
-void assemble_fields(const HostComplex& hc, double eps, double mu, HostFields* hf);
+// pec: boundary edges and nodes fixed at zero; else the natural boundary (nothing fixed)
+void assemble_fields(const HostComplex& hc, double eps, double mu, bool pec, HostFields* hf);
 
 // Largest eigenvalue of D^-1 A (A symmetric CSR with positive diagonal), estimated by
 // `steps` Lanczos steps on D^-1/2 A D^-1/2 from a fixed start vector (a lower bound that
@@ -25,6 +26,12 @@ struct LearnedDev;  // learned correction (learned.cu)
 
 struct FieldDev {
     double dt = 0, eps = 0, mu = 0;
+    int bc = FP_BC_PEC;             // field boundary condition
+    // natural boundary: the W0 integrals alpha (device) and their sum, for the projection's
+    // zero-mean constraint; partial sums of its two reductions
+    double* alpha = nullptr;
+    double alpha_sum = 0.0;
+    double* msum = nullptr;
     int64_t ne = 0, nn = 0, nf = 0;
     HostFields host;
     int32_t *e_rp = nullptr, *e_col = nullptr, *n_rp = nullptr, *n_col = nullptr;

@@ -69,16 +69,16 @@ int64_t find(const std::vector<int32_t>& rp, const std::vector<int32_t>& col, in
 
 }  // namespace
 
-void assemble_fields(const HostComplex& hc, double eps, double mu, HostFields* hf) {
+void assemble_fields(const HostComplex& hc, double eps, double mu, bool pec, HostFields* hf) {
     const int64_t nt = hc.nt, ne = hc.ne, nn = hc.nn;
-    // PEC: edges and nodes of boundary faces are fixed at zero
+    // PEC: edges and nodes of boundary faces are fixed at zero (natural boundary: none is)
     hf->node_fixed.assign(nn, 0);
     hf->edge_fixed.assign(ne, 0);
-    for (int64_t f = 0; f < hc.nf; ++f) {
+    for (int64_t f = 0; f < hc.nf && pec; ++f) {
         if (!hc.bface[f]) continue;
         for (int k = 0; k < 3; ++k) hf->node_fixed[hc.faces[3 * f + k]] = 1;
     }
-    for (int64_t t = 0; t < nt; ++t)
+    for (int64_t t = 0; t < nt && pec; ++t)
         for (int kf = 0; kf < 4; ++kf) {
             if (!hc.bface[hc.tf[4 * t + kf]]) continue;
             for (int a = 0; a < 6; ++a)  // the edges of face kf avoid its opposite vertex kf

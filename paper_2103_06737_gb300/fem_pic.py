@@ -61,6 +61,7 @@ class SolveInfo(ctypes.Structure):
 
 FP_SYS_NEWMARK, FP_SYS_GAUSS = 0, 1
 FP_PC_JACOBI, FP_PC_LEARNED, FP_PC_JACOBI_FP64, FP_PC_LEARNED_GAUSS = 0, 1, 2, 4
+FP_BC_PEC, FP_BC_NEUMANN = 0, 1
 EPS0 = 8.854_187_8128e-12
 MU0 = 1.256_637_062_12e-6
 
@@ -102,6 +103,7 @@ def lib():
             "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
             "fem_pic_status": (I32, [P, P]),
             "fem_pic_field_setup": (I32, [P, D, D, D]),
+            "fem_pic_field_setup_bc": (I32, [P, D, D, D, I32]),
             "fem_pic_field_nnz": (I32, [P, P]),
             "fem_pic_field_matrix": (I32, [P, I32, P, P, P]),
             "fem_pic_field_solve": (I32, [P, I32, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
@@ -365,8 +367,12 @@ def fem_pic_status(h, stream=None) -> int:
     return int(lib().fem_pic_status(h, _stream(stream)))
 
 
-def fem_pic_field_setup(h, dt: float, eps: float = EPS0, mu: float = MU0):
-    _check(lib().fem_pic_field_setup(h, float(dt), float(eps), float(mu)), h)
+def fem_pic_field_setup(h, dt: float, eps: float = EPS0, mu: float = MU0, bc: int = None):
+    """Field operators for time step dt; bc = FP_BC_PEC (default) or FP_BC_NEUMANN."""
+    if bc is None:
+        _check(lib().fem_pic_field_setup(h, float(dt), float(eps), float(mu)), h)
+    else:
+        _check(lib().fem_pic_field_setup_bc(h, float(dt), float(eps), float(mu), int(bc)), h)
 
 
 def fem_pic_field_matrix(h, which: int):
