@@ -225,7 +225,8 @@ struct SmemOp {
 };
 
 // row i of the FP32 operator times x: from shared memory (sm_slots > 0) or from the global
-// SELL copy; chunks of kSellChunk entries as in sell_row
+// SELL copy; chunks of CH independent loads (as in sell_row)
+template <int CH>
 __device__ __forceinline__ float row_product32(const MixedArgs& a, const SmemOp& so, const float* __restrict__ x,
                                                int64_t i) {
     if (a.sm_slots == 0) return sell_row<float, float>(a.S, a.val32, x, i);
@@ -233,22 +234,33 @@ __device__ __forceinline__ float row_product32(const MixedArgs& a, const SmemOp&
     const int64_t base = __ldg(a.S.ptr + sl) - so.base + (i & 31);
     const int w = __ldg(a.S.w + sl);
     float s = 0.f;
-    for (int j0 = 0; j0 < w; j0 += kSellChunk) {
-        int c[kSellChunk];
-        float av[kSellChunk], xv[kSellChunk];
+    for (int j0 = 0; j0 < w; j0 += CH) {
+        int c[CH];
+        float av[CH], xv[CH];
 #pragma unroll
-        for (int u = 0; u < kSellChunk; ++u) {
+        for (int u = 0; u < CH; ++u) {
             const bool in = j0 + u < w;
             c[u] = in ? (int)i + so.d[base + 32 * (j0 + u)] : -1;
             av[u] = in ? so.v[base + 32 * (j0 + u)] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? __ldcg(x + c[u]) : 0.f;
+        for (int u = 0; u < CH; ++u) xv[u] = c[u] >= 0 ? __ldcg(x + c[u]) : 0.f;
 #pragma unroll
-        for (int u = 0; u < kSellChunk; ++u) s += av[u] * xv[u];
+        for (int u = 0; u < CH; ++u) s += av[u] * xv[u];
     }
     return s;
 }
+
+// entries per chunk of the mixed solver's products: 16 where the block size leaves the
+// registers for them (blocks of at most 256 threads: up to 96 registers a thread), else the
+// SELL default
+#ifndef FP_SMALL_BLOCK_CHUNK
+#define FP_SMALL_BLOCK_CHUNK 16
+#endif
+template <int BS>
+struct ProductChunk {
+    static constexpr int value = BS <= 256 ? FP_SMALL_BLOCK_CHUNK : kSellChunk;
+};
 
 // z = P(r) for the rows [t0, r1) of this block, P the Chebyshev polynomial of degree deg in
 // B = D^-1 A applied to f = D^-1 r (three-term recurrence on [theta - delta, theta + delta]):
@@ -259,6 +271,7 @@ __device__ __forceinline__ float row_product32(const MixedArgs& a, const SmemOp&
 // symmetric positive definite method.  Each step's product needs the previous d of every
 // block: one grid barrier per step, d in two buffers.  z is published by the caller's next
 // grid barrier.
+template <int CH>
 __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp& so, int64_t t0, int64_t r1,
                                                 int64_t stride, cg::grid_group& g) {
     const float th = a.theta, de = a.delta, sig = th / de;
@@ -277,7 +290,7 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp
         const float rn = 1.f / (2.f * sig - rho);
         const float c1 = rn * rho, c2 = 2.f * rn / de;
         for (int64_t i = t0; i < r1; i += stride) {
-            const float bd = a.dinv32[i] * row_product32(a, so, dc, i);
+            const float bd = a.dinv32[i] * row_product32<CH>(a, so, dc, i);
             const float sk = a.s[i] - bd;
             const float dk = c1 * dc[i] + c2 * sk;
             a.s[i] = sk;
@@ -353,11 +366,11 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             a.r[i] = ri;
             a.z[i] = a.dinv32[i] * ri;
         }
-        if (a.deg > 1) chebyshev_apply(a, so, t0, r1, stride, g);
+        if (a.deg > 1) chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
         g.sync();
         float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
         for (int64_t i = t0; i < r1; i += stride) {
-            const float w = row_product32(a, so, a.z, i);
+            const float w = row_product32<ProductChunk<BS>::value>(a, so, a.z, i);
             const float zi = a.z[i], ri = a.r[i];
             a.p[i] = zi;
             a.q[i] = w;
@@ -391,7 +404,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
                     a.c[i] += alpha * a.p[i];
                     a.r[i] -= alpha * a.q[i];
                 }
-                chebyshev_apply(a, so, t0, r1, stride, g);
+                chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
                 for (int64_t i = t0; i < r1; i += stride) {
                     const float ri = a.r[i];
                     w2[0] += ri * a.z[i];
@@ -405,7 +418,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             rz = w2[0];
             float u2[1] = {0.f};
             for (int64_t i = t0; i < r1; i += stride) {
-                const float w = row_product32(a, so, a.z, i);
+                const float w = row_product32<ProductChunk<BS>::value>(a, so, a.z, i);
                 const float pi = a.z[i] + beta * a.p[i];
                 const float qi = w + beta * a.q[i];
                 a.p[i] = pi;
