@@ -156,7 +156,7 @@ def fast_kernel_bytes(n_particles, sizes):
 
 
 def adams_kernel_bytes(n_particles, sizes):
-    """Minimal DRAM bytes of one fourth-order Adams fast-push launch (k_push_adams32): the fast
+    """Minimal DRAM bytes of one fourth-order Adams fast-push launch: the fast
     Boris launch's bytes plus the derivative history, 3 slots x (v, a) read (72 B) and the new
     slot written (24 B) per particle."""
     return fast_kernel_bytes(n_particles, sizes) + 96 * n_particles
@@ -883,12 +883,14 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
     ach = byt / (f_avg * 1e-3) / 1e9
     return {"particle_steps_per_s": sum(live) / (ms * 1e-3), "ms_per_call": ms / args.adams_steps,
             "order": 4, "dt_s": dt, "timed_calls": args.adams_steps, "alive_mean": n_live, "status": int(st),
-            "kernel_ms_per_call": {"k_field_prep32": p_ms / args.adams_steps, "k_push_adams32": f_avg,
+            "kernel_ms_per_call": {"k_field_prep32": p_ms / args.adams_steps, "fast_push": f_avg,
                                    "k_walk_adams32": w_ms / args.adams_steps},
-            "roofline": {"kernel": "k_push_adams32", "bound": "hbm", "achieved": ach, "peak": peak,
+            "roofline": {"kernel": "k_push_ws32<AdamsStep<float>> (warp-specialised push with the Adams mover; "
+                                   "k_push_adams32 when the state is not 16-byte aligned)",
+                         "bound": "hbm", "achieved": ach, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes_per_launch": byt, "avg_launch_ms": f_avg,
-                         "traffic": measured_traffic("k_push_adams32", wl.name)}}
+                         "traffic": measured_traffic("k_push_ws32/adams", wl.name)}}
 
 
 def cpu_baseline(args, wl, budget_s):

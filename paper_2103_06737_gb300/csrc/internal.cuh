@@ -122,8 +122,11 @@ struct fem_pic {
     int32_t* d_slow_idx = nullptr;    // [slow_cap]
     int32_t* d_slow_count = nullptr;  // [1]
     int64_t slow_cap = 0;
+    // co-resident blocks of the staged push kernels (0: not queried yet): bulk-copy pipeline,
+    // warp-specialised Boris push, warp-specialised Adams push
     int tma_blocks_per_sm = 0;
-    int ws_blocks_per_sm = 0;         // co-resident blocks of the warp-specialised push kernel        // co-resident blocks of the staged push kernel (0: not queried yet)
+    int ws_blocks_per_sm = 0;
+    int ws_adams_blocks_per_sm = 0;
     uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch
     int32_t* d_sort_count = nullptr;  // [nt + 2]

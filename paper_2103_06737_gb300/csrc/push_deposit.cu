@@ -548,6 +548,7 @@ struct BorisMover {
 #pragma unroll
         for (int i = 0; i < 3; ++i) xb[i] = step_pos(x[i], dt, v[i]);
     }
+    __device__ __forceinline__ void history(int64_t) {}
     __device__ __forceinline__ void commit(int64_t) {}
 };
 
@@ -1017,9 +1018,33 @@ __device__ __forceinline__ void ws_issue(unsigned char* stage, uint64_t* bar, in
     for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kWsSlot, vel + k * n + p0, bytes, bar);
 }
 
-__global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
+// The consumers' particle mover: Boris (the step's leapfrog push) or the Adams mover, whose
+// history part is loaded as soon as a particle's state is read from the stage.
+struct BorisArgs {
+    float h, dt;
+};
+__device__ __forceinline__ BorisMover make_mover(const BorisArgs& a, float* vel, int64_t n) {
+    return BorisMover{a.h, a.dt, vel, n};
+}
+__device__ __forceinline__ AdamsMover32 make_mover(const AdamsStep<float>& a, float* vel, int64_t) {
+    return AdamsMover32{a, vel};
+}
+#ifndef FP_ADAMS_WS_MIN_BLOCKS
+#define FP_ADAMS_WS_MIN_BLOCKS 3
+#endif
+template <class MA>
+struct WsMinBlocks {
+    static constexpr int value = FP_FAST_MIN_BLOCKS;
+};
+template <>
+struct WsMinBlocks<AdamsStep<float>> {
+    static constexpr int value = FP_ADAMS_WS_MIN_BLOCKS;   // the Adams sums need more registers
+};
+
+template <class MA>
+__global__ void __launch_bounds__(kWsThreads, WsMinBlocks<MA>::value) k_push_ws32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
-    float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
+    float* __restrict__ vel, int64_t n, int32_t nt, MA margs, double qw, int aggregate,
     float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
     int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1109,7 +1134,7 @@ __global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
     }
     // ---------------- consumers
     const float w = (float)qw;
-    BorisMover bm{h, dt, vel, n};
+    auto mv = make_mover(margs, vel, n);
     for (int it = 0; it < mine; ++it) {
         const int sk = it % kWsStages;
         const uint32_t par = (uint32_t)((it / kWsStages) & 1);
@@ -1134,8 +1159,9 @@ __global__ void __launch_bounds__(kWsThreads, FP_FAST_MIN_BLOCKS) k_push_ws32(
                     x[k] = reinterpret_cast<const float*>(st + (1 + k) * kWsSlot)[j];
                     v[k] = reinterpret_cast<const float*>(st + (4 + k) * kWsSlot)[j];
                 }
+                if (c >= 0 && c < nt) mv.history(p0 + j);
             }
-            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, bm, w, aggregate, off, dG,
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, mv, w, aggregate, off, dG,
                                             Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
         }
@@ -1444,9 +1470,11 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
 #endif
     if (FP_PUSH_WS) {   // warp-specialised pipeline
         if (ctx->ws_blocks_per_sm == 0) {
-            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_ws32, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_ws32<BorisArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kWsSmem));
             int per_sm = 0;
-            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_ws32, kWsThreads, kWsSmem));
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_ws32<BorisArgs>, kWsThreads,
+                                                                           kWsSmem));
             if (per_sm < 1) {
                 ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
                 return FP_ECUDA;
@@ -1456,9 +1484,9 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
         const int64_t wtiles = (p->n + kWsTile - 1) / kWsTile;
         int64_t wgrid = (int64_t)ctx->sm_count * ctx->ws_blocks_per_sm;
         if (wgrid > wtiles) wgrid = wtiles;
-        k_push_ws32<<<(int)wgrid, kWsThreads, kWsSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
-                                                             p->n, nt, h, dt, qw, agg, dG, Q, ctx->d_slow_idx,
-                                                             ctx->d_slow_count, ctx->d_status);
+        k_push_ws32<BorisArgs><<<(int)wgrid, kWsThreads, kWsSmem, s>>>(
+            ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt, BorisArgs{h, dt}, qw, agg, dG, Q,
+            ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
@@ -1571,12 +1599,38 @@ fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, cons
             k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces,
                                                                                         e, b, ctx->hc.nt);
         }
+        const bool aligned = (p->n % 4) == 0 && ((uintptr_t)p->cell % 16) == 0 && ((uintptr_t)p->off % 16) == 0 &&
+                             ((uintptr_t)p->vel % 16) == 0;
+#ifndef FP_ADAMS_WS
+#define FP_ADAMS_WS 1
+#endif
+        if (aligned && FP_ADAMS_WS && ctx->ws_adams_blocks_per_sm == 0) {
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_ws32<AdamsStep<float>>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+            int per_sm = 0;
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_ws32<AdamsStep<float>>,
+                                                                           kWsThreads, kWsSmem));
+            if (per_sm < 1) {
+                ctx->err = "fem_pic_push_deposit_adams: the staged push kernel does not fit on an SM";
+                return FP_ECUDA;
+            }
+            ctx->ws_adams_blocks_per_sm = per_sm;
+        }
         {
             PhaseTimer pt(ctx, PH_ADAMS, s);
-            k_push_adams32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
-                                                                          (float*)p->vel, A, nt, qw, agg, (float*)dG,
-                                                                          (float*)Q, ctx->d_slow_idx,
-                                                                          ctx->d_slow_count, ctx->d_status);
+            if (aligned && FP_ADAMS_WS) {   // the state staged by bulk copies, as in the Boris push
+                const int64_t wtiles = (p->n + kWsTile - 1) / kWsTile;
+                int64_t wgrid = (int64_t)ctx->sm_count * ctx->ws_adams_blocks_per_sm;
+                if (wgrid > wtiles) wgrid = wtiles;
+                k_push_ws32<AdamsStep<float>><<<(int)wgrid, kWsThreads, kWsSmem, s>>>(
+                    ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt, A, qw, agg, (float*)dG, (float*)Q,
+                    ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+            } else {
+                k_push_adams32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
+                                                                              (float*)p->vel, A, nt, qw, agg,
+                                                                              (float*)dG, (float*)Q, ctx->d_slow_idx,
+                                                                              ctx->d_slow_count, ctx->d_status);
+            }
         }
         {
             PhaseTimer pt(ctx, PH_ADAMS_WALK, s);
