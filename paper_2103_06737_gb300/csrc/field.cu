@@ -1021,9 +1021,9 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
             std::vector<float> pA32(pA.begin(), pA.end()), pdinv(ne);
             for (int64_t r = 0; r < ne; ++r) pdinv[r] = (float)Ad[(*perm)[r]];
 #ifdef FP_SMEM_REPORT
-            fprintf(stderr, "newmark solver order: %s, sectors %lld (edge order %lld), slots %lld (edge order %lld)\n",
+            fprintf(stderr, "newmark solver order: %s, sectors %lld (edge order %lld), SELL slots %lld, nonzeros %lld\n",
                     perm == &blocked ? "blocked" : "edge", (long long)F->sectors_e[1], (long long)F->sectors_e[0],
-                    (long long)scol.size(), (long long)F->slots_total[FP_SYS_GAUSS] * 0 + (long long)H.e_col.size());
+                    (long long)scol.size(), (long long)H.e_col.size());
 #endif
             if (!d16.empty() && st == FP_OK) st = up(ctx, &F->se_d16, d16);
             F->hptr[FP_SYS_NEWMARK] = ptr;
