@@ -60,7 +60,7 @@ def parse():
                     help="learned corrections of the Newmark and Gauss-law solves: trained during warm-up, "
                          "each used if it beats plain CG (auto)")
     ap.add_argument("--learned-systems", default="newmark,gauss",
-                    help="systems whose learned correction is trained and judged (newmark, gauss)")
+                    help="systems whose learned correction is trained and compared with plain CG (newmark, gauss)")
     ap.add_argument("--learn-samples", type=int, default=48)
     ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--compare-steps", type=int, default=20)
@@ -415,7 +415,7 @@ def run_gpu(args):
 
     # learned corrections, per system (Newmark edge system, Gauss-law node system): collect
     # residuals of the method's own solves, train, then time learned vs plain Jacobi-CG on the
-    # same steps (plain CG is the judge); a correction is kept only where it wins
+    # same steps (plain CG decides); a correction is kept only where it wins
     learned = None
     if field and args.learned != "off":
         learned = {}
@@ -460,7 +460,7 @@ def run_gpu(args):
                         ph_cg + "_ms_per_step": ph.get(ph_cg, (0.0, 1))[0] / args.compare_steps,
                         "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
                         "iters_mean": statistics.mean(its), "fell_back": fb}
-            # plain Jacobi-CG judges the learned correction: both runs with the Jacobi inner
+            # plain Jacobi-CG is the comparison: both runs with the Jacobi inner
             # preconditioner on this system (the timed steps then use the configured one)
             F.fem_pic_field_poly(lib.h, sys_id, 1, prat[sys_id])
             plain = compare(precond)
@@ -475,7 +475,7 @@ def run_gpu(args):
                 "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
                 "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
                 "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
-                "judge": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system in both runs)",
+                "compared_against": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system in both runs)",
                 "model": f"3-layer message passing on the {graph}, 64 features, BF16 weights, FP32 accum"}
         state["precond"] = precond | used_bits
 

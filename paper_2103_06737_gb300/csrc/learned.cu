@@ -532,7 +532,7 @@ __global__ void k_lm_candidate(const double* __restrict__ x0, const float* __res
         y[i] = x0[i] + s * (double)dis[i] * (double)ct[i];
 }
 
-// keep the candidate only if its residual is smaller (the plain guess is the judge)
+// keep the candidate only if its residual is smaller than the plain guess's
 __global__ void k_lm_select(double* __restrict__ x0, const double* __restrict__ y, const float* __restrict__ scal,
                             int64_t n, int* flag) {
     const bool take = scal[3] < scal[2];
