@@ -78,6 +78,33 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (the whole job's), on every rank; ms itself for one rank."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(units: float, world: int, device) -> float:
+    """The units all ranks processed, on every rank."""
+    if world <= 1:
+        return float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_all_ranks: float, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_all_ranks / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
@@ -529,15 +556,12 @@ def run_gpu(args):
         dist.barrier()
     clocks = clocks_stop(clk)
     step_ms = [a.elapsed_time(z) for a, z in evs]
-    total_ms = float(sum(step_ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     st = lib.status()
     r = res.cpu().numpy()
     alive1 = alive()
     alive_timed = 0.5 * (alive0 + alive1)          # absorption is gradual: mean of start and end
+    units_all = sum_over_ranks(alive_timed * args.steps, world, dev)
     restore()
 
     # per-kernel durations: an eager pass of the same steps with the library's event profiler
@@ -659,10 +683,8 @@ def run_gpu(args):
             parts.append((a, h))
         torch.cuda.synchronize()
         e2e_ms = sum(a.elapsed_time(z) for a, z in ee)
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * alive0 * args.steps / (float(tt.item()) * 1e-3), "unit": UNIT,
+        e2e_max = max_over_ranks(e2e_ms, world, dev)
+        e2e = {"value": whole_job_rate(sum_over_ranks(alive0 * args.steps, world, dev), e2e_max), "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                "ms_per_step": e2e_ms / args.steps,
                "h2d_ms_per_step": sum(a.elapsed_time(h) for a, h in parts) / args.steps,
@@ -723,7 +745,7 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
-        value = world * alive_timed * args.steps / (total_ms * 1e-3)
+        value = whole_job_rate(units_all, total_ms)
         avg_push = push_call
         abytes = algorithmic_bytes(alive_eager / len(species), sizes, 4)   # one push call (one species)
         peak, peak_kind = peak_hbm()
