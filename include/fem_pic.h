@@ -438,6 +438,16 @@ fp_status fem_pic_profile_enable(fem_pic_t* ctx, int on);
 fp_status fem_pic_profile_read(fem_pic_t* ctx, double ms[16], int64_t count[16], int reset);
 
 /*
+ * Self-test of the failure path of the library's bounded waits (not part of the method; the
+ * paper has no counterpart): a one-thread kernel waits on a barrier that nothing completes,
+ * gives up after limit_s seconds (0 < limit_s <= 10, else FP_EINVAL) and sets the time-out
+ * bit of the status word, exactly as a push kernel does when a bulk copy never lands; the
+ * next fem_pic_status returns FP_ECUDA and clears it, and the context stays usable.  Nothing
+ * faults or hangs.  Asynchronous.
+ */
+fp_status fem_pic_selftest_wait(fem_pic_t* ctx, double limit_s, void* stream);
+
+/*
  * Synchronise `stream`, return and clear the device status word:
  * FP_OK, FP_EWALK or FP_EINVAL (the first error class seen, EINVAL first).
  */

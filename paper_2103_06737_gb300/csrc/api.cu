@@ -411,6 +411,14 @@ fp_status fem_pic_profile_read(fem_pic_t* ctx, double ms[16], int64_t count[16],
     return FP_OK;
 }
 
+fp_status fem_pic_selftest_wait(fem_pic_t* ctx, double limit_s, void* stream) {
+    if (!ctx || !(limit_s > 0.0) || limit_s > 10.0) {
+        if (ctx) ctx->err = "fem_pic_selftest_wait: limit outside (0, 10] s";
+        return FP_EINVAL;
+    }
+    return launch_wait_selftest(ctx, limit_s, (cudaStream_t)stream);
+}
+
 fp_status fem_pic_status(fem_pic_t* ctx, void* stream) {
     if (!ctx) return FP_EINVAL;
     int32_t h = 0;

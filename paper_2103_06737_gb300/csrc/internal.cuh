@@ -230,6 +230,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                               cudaStream_t s);
 fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
                             int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s);
+fp_status launch_wait_selftest(fem_pic* ctx, double limit_s, cudaStream_t s);
 fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
                                 cudaStream_t s);
 fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, cudaStream_t s,

@@ -1352,6 +1352,17 @@ __global__ void __launch_bounds__(256) k_push_adams64(
     }
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing arrives at,
+// gives up after limit_ns and reports ST_TIMEOUT, as the push kernels do when a copy never
+// completes.  No copy is issued, so nothing is in flight when it returns.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(status, ST_TIMEOUT);
+}
+
 // W0 charge at the current positions, FP32 (barycentrics from the FP32 gradients)
 __global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restrict__ hot,
                                                           const int32_t* __restrict__ cell,
@@ -1651,6 +1662,12 @@ fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, cons
                                                                       max_cross, agg, (double*)dG, (double*)Q,
                                                                       ctx->d_status);
     }
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+fp_status launch_wait_selftest(fem_pic* ctx, double limit_s, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>((uint64_t)(limit_s * 1e9), ctx->d_status);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }

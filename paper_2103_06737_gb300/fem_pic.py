@@ -102,6 +102,7 @@ def lib():
                                            P]),
             "fem_pic_residuals": (I32, [P, P, P, P, P, P, P]),
             "fem_pic_status": (I32, [P, P]),
+            "fem_pic_selftest_wait": (I32, [P, D, P]),
             "fem_pic_field_setup": (I32, [P, D, D, D]),
             "fem_pic_field_setup_bc": (I32, [P, D, D, D, I32]),
             "fem_pic_field_nnz": (I32, [P, P]),
@@ -365,6 +366,11 @@ def fem_pic_residuals(h, dG, Q_new, Q_old, b, out, stream=None):
 
 def fem_pic_status(h, stream=None) -> int:
     return int(lib().fem_pic_status(h, _stream(stream)))
+
+
+def fem_pic_selftest_wait(h, limit_s: float = 1e-3, stream=None):
+    """A bounded wait that runs out on the GPU (see the header); read the result with fem_pic_status."""
+    _check(lib().fem_pic_selftest_wait(h, float(limit_s), _stream(stream)), h)
 
 
 def fem_pic_field_setup(h, dt: float, eps: float = EPS0, mu: float = MU0, bc: int = None):

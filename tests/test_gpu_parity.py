@@ -221,6 +221,25 @@ def test_invalid_cell_and_empty_input():
     lib.close()
 
 
+def test_bounded_wait_runs_out_and_reports():
+    """A wait that nothing completes gives up after its limit (1 ms) and sets the time-out
+    status; fem_pic_status reports it once, and the context keeps working (a push follows)."""
+    m, orc, lib, sp, e, b = _setup(npart=2000, prec=F.FP_FP32)
+    F.fem_pic_selftest_wait(lib.h, 1e-3)
+    assert lib.status() == F.FP_ECUDA
+    assert "gave up waiting" in F.fem_pic_last_error(lib.h)
+    assert lib.status() == F.FP_OK            # cleared
+    with pytest.raises(F.FemPicError):
+        F.fem_pic_selftest_wait(lib.h, 0.0)   # the limit must be positive
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    dG = torch.empty(orc.n_edges, dtype=torch.float32, device="cuda")
+    Q = torch.empty(orc.n_nodes, dtype=torch.float32, device="cuda")
+    lib.push_deposit(torch.as_tensor(e, device="cuda"), torch.as_tensor(b, device="cuda"), d, 1.0, dG, Q)
+    assert lib.status() == F.FP_OK
+    assert abs(float(Q.double().sum()) - sp.n * sp.q * sp.w) <= 1e-4 * sp.n * abs(sp.w)
+    lib.close()
+
+
 @pytest.mark.parametrize("prec", [F.FP_FP32, F.FP_FP64])
 def test_sort_is_a_permutation_by_cell(prec):
     m, orc, lib, sp, e, b = _setup(npart=30_001, prec=prec, speed=0.3)
