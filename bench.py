@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--learn-samples", type=int, default=48)
     ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--compare-steps", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="timed particle steps of the FP64 mode in a context of its own (0: skip)")
     ap.add_argument("--neumann-steps", type=int, default=10,
                     help="timed field steps with the natural (Neumann) field boundary (0: skip)")
     ap.add_argument("--adams-steps", type=int, default=20,
@@ -691,6 +693,7 @@ def run_gpu(args):
                "overlap": "particle state copied back on a second stream during the field step; the step's "
                           "particle and field parts replayed as CUDA graphs"}
 
+    fp64 = None if args.fp64_steps <= 0 else measure_fp64(args, F, wl, dev, flush_l2, stream)
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
                                                              Qn, flush_l2, stream, sizes, wl, dev)
     def measure_neumann():
@@ -846,6 +849,7 @@ def run_gpu(args):
             "e2e": e2e,
             "adams": adams,
             "neumann": neumann,
+            "fp64_mode": fp64,
         }
     del lib
     if world > 1:
@@ -915,6 +919,64 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
                          "traffic": measured_traffic("k_push_ws32/adams", wl.name)}}
 
 
+def measure_fp64(args, F, wl, dev, flush_l2, stream):
+    """The particle step in FP64 mode (FP64 state, gather, Boris, walk and deposits: one kernel,
+    k_push_deposit<double>) on the same particles and B0, in a context of its own: cell-sorted
+    state, 3 warm-up calls, then args.fp64_steps timed calls (L2 flushed between them)."""
+    import torch
+    lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP64)
+    sizes = lib.sizes
+    sps = []
+    for s in wl.species:
+        d0 = lib.species(s.cell, s.X, s.V, s.q, s.m, s.w, device=dev)
+        d1 = d0.empty_like()
+        lib.sort(d0, d1)
+        sps.append(d1)
+    e, b = lib.fields_uniform((0.0, 0.0, 0.0), wl.B0, device=dev)
+    dG = torch.zeros(sizes["n_edges"], dtype=torch.float64, device=dev)
+    Q = torch.zeros(sizes["n_nodes"], dtype=torch.float64, device=dev)
+
+    def call():
+        dG.zero_()
+        Q.zero_()
+        for s_ in sps:
+            lib.push_deposit(e, b, s_, wl.dt, dG, Q, flags=F.FP_ACCUMULATE)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    F.fem_pic_profile_read(lib.h, reset=True)
+    F.fem_pic_profile_enable(lib.h, True)
+    ev, live = [], []
+    for k in range(args.fp64_steps):
+        live.append(sum(int((s_.cell >= 0).sum()) for s_ in sps))
+        flush_l2(3000 + k)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        z.record(stream)
+        ev.append((a, z))
+    torch.cuda.synchronize()
+    F.fem_pic_profile_enable(lib.h, False)
+    ph = F.fem_pic_profile_read(lib.h, reset=True)
+    st = lib.status()
+    ms = sum(a.elapsed_time(z) for a, z in ev) / len(ev)
+    k_ms, k_n = ph.get("push_fp64", (float("nan"), 1))
+    k_avg = k_ms / max(1, k_n)
+    n_live = sum(live) / len(live)
+    byt = algorithmic_bytes(n_live / len(sps), sizes, 8)
+    peak, peak_kind = peak_hbm()
+    ach = byt / (k_avg * 1e-3) / 1e9
+    lib.close()
+    return {"particle_steps_per_s": sum(live) / (ms * 1e-3 * len(ev)), "ms_per_call": ms, "status": int(st),
+            "timed_calls": len(ev), "alive_mean": n_live,
+            "kernel": "k_push_deposit<double>", "avg_launch_ms": k_avg,
+            "bound": "FP64 pipe: every particle takes the FP64 gather, push, exit test and walk (GB300 issues "
+                     "2 FP64 operations per clock per SM), not HBM",
+            "algorithmic_bytes_per_launch": byt, "hbm_achieved_gbs": ach, "hbm_frac": ach / peak,
+            "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind}
+
+
 def cpu_baseline(args, wl, budget_s):
     """The FP64 oracle as it stands, on the host cores, over a bounded sample of the workload."""
     import oracle as O
@@ -934,9 +996,15 @@ def cpu_baseline(args, wl, budget_s):
         orc.step(sp.cell[:n2], sp.X[:n2], sp.V[:n2], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
         el += time.perf_counter() - t
         done += n2
+    # the same oracle on one host thread, over a smaller sample
+    n1 = min(sp.n, 20000)
+    t = time.perf_counter()
+    orc.step(sp.cell[:n1], sp.X[:n1], sp.V[:n1], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=1)
+    el1 = time.perf_counter() - t
     return {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n2} of {sp.n} particles of species 0, {done // n2} step(s), FP64 oracle (C, OpenMP), "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s",
+            "value_1_thread": n1 / max(el1, 1e-9), "sample_1_thread": f"{n1} particles, 1 step, 1 thread"}
 
 
 def run_reference(args):
