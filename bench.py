@@ -920,8 +920,8 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
 
 
 def measure_fp64(args, F, wl, dev, flush_l2, stream):
-    """The particle step in FP64 mode (FP64 state, gather, Boris, walk and deposits: one kernel,
-    k_push_deposit<double>) on the same particles and B0, in a context of its own: cell-sorted
+    """The particle step in FP64 mode (FP64 state, fields, Boris, walk and deposits: the per-tet
+    field records, then k_push_deposit<double>) on the same particles and B0, in a context of its own: cell-sorted
     state, 3 warm-up calls, then args.fp64_steps timed calls (L2 flushed between them)."""
     import torch
     lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP64)
@@ -971,8 +971,8 @@ def measure_fp64(args, F, wl, dev, flush_l2, stream):
     return {"particle_steps_per_s": sum(live) / (ms * 1e-3 * len(ev)), "ms_per_call": ms, "status": int(st),
             "timed_calls": len(ev), "alive_mean": n_live,
             "kernel": "k_push_deposit<double>", "avg_launch_ms": k_avg,
-            "bound": "FP64 pipe: every particle takes the FP64 gather, push, exit test and walk (GB300 issues "
-                     "2 FP64 operations per clock per SM), not HBM",
+            "bound": "FP64 pipe: every particle takes the FP64 fields (per-tet affine records), push, exit test "
+                     "and walk (GB300 issues 2 FP64 operations per clock per SM), not HBM",
             "algorithmic_bytes_per_launch": byt, "hbm_achieved_gbs": ach, "hbm_frac": ach / peak,
             "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind}
 

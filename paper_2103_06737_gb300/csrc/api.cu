@@ -181,6 +181,13 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_n2e_sgn, n2e_sgn.data(), n2e_sgn.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_orient, hc.orient.data(), hc.orient.size());
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_hot, hot.data(), hot.size());
+        if (s2 == FP_OK && precision == FP_FP64) {   // the FP64 path's per-tet field records
+            ce = cudaMalloc((void**)&ctx->d_field64, (size_t)10 * hc.nt * sizeof(double));
+            if (ce != cudaSuccess) {
+                ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(ce);
+                s2 = FP_ECUDA;
+            }
+        }
         if (s2 == FP_OK) s2 = upload(ctx, &ctx->d_tet_faces, reinterpret_cast<const int4*>(hc.tf.data()), hc.nt);
         if (s2 == FP_OK) {
             int32_t z4[4] = {0, 0, 0, 0};
@@ -222,7 +229,7 @@ void fem_pic_destroy(fem_pic_t* ctx) {
     void* ptrs[] = {ctx->d_geo,     ctx->d_topo,    ctx->d_xyz,     ctx->d_edges,
                     ctx->d_faces,   ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn,
                     ctx->d_orient,  ctx->d_status,  ctx->d_sort_count, ctx->d_sort_block,
-                    ctx->d_sort_rank, ctx->d_hot, ctx->d_slow_idx, ctx->d_slow_count,
+                    ctx->d_sort_rank, ctx->d_hot, ctx->d_field64, ctx->d_slow_idx, ctx->d_slow_count,
                     ctx->d_node_wall, ctx->d_tet_faces};
     for (void* p : ptrs)
         if (p) cudaFree(p);

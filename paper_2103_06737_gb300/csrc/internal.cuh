@@ -116,6 +116,7 @@ struct fem_pic {
     int8_t* d_n2e_sgn = nullptr;
     int8_t* d_orient = nullptr;       // [nt]
     fempic::TetHot* d_hot = nullptr;  // [nt]
+    double* d_field64 = nullptr;      // [10 nt] FP64 mode: per tet E0, W, B0, beta (affine fields)
     int4* d_tet_faces = nullptr;      // [nt] face ids of each tet (face k opposite vertex k)
     int32_t* d_status = nullptr;
     // particles deferred to the FP64 walk (near or across a face)

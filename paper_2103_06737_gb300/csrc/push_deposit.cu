@@ -87,50 +87,6 @@ __device__ __forceinline__ void cross(const Real a[3], const Real b[3], Real o[3
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// E = sum_k e_k W1_k(l), B = sum_f b_f W2_f(l) in one tet (Sec. II.C)
-template <typename Real>
-__device__ __forceinline__ void gather(const Geo& G, const TetTopo& T, const double* __restrict__ e,
-                                       const double* __restrict__ b, const double la[4], Real E[3],
-                                       Real B[3]) {
-    Real g[4][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        g[1][i] = (Real)G.g[i];
-        g[2][i] = (Real)G.g[3 + i];
-        g[3][i] = (Real)G.g[6 + i];
-        g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
-    }
-    const Real L[4] = {(Real)la[0], (Real)la[1], (Real)la[2], (Real)la[3]};
-    Real ev[6], bv[4];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) ev[k] = (Real)__ldg(e + T.edge[k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) bv[k] = (Real)__ldg(b + T.face[k]);
-    // W1_ab = L_a g_b - L_b g_a over (01,02,03,12,13,23)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        E[i] = ev[0] * (L[0] * g[1][i] - L[1] * g[0][i]) + ev[1] * (L[0] * g[2][i] - L[2] * g[0][i]) +
-               ev[2] * (L[0] * g[3][i] - L[3] * g[0][i]) + ev[3] * (L[1] * g[2][i] - L[2] * g[1][i]) +
-               ev[4] * (L[1] * g[3][i] - L[3] * g[1][i]) + ev[5] * (L[2] * g[3][i] - L[3] * g[2][i]);
-    }
-    // W2_abc = 2 (L_a g_b x g_c + L_b g_c x g_a + L_c g_a x g_b), face k opposite vertex k
-    Real x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
-    cross(g[0], g[1], x01);
-    cross(g[0], g[2], x02);
-    cross(g[0], g[3], x03);
-    cross(g[1], g[2], x12);
-    cross(g[1], g[3], x13);
-    cross(g[2], g[3], x23);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Real f0 = L[1] * x23[i] - L[2] * x13[i] + L[3] * x12[i];  // (1,2,3)
-        Real f1 = L[0] * x23[i] - L[2] * x03[i] + L[3] * x02[i];  // (0,2,3)
-        Real f2 = L[0] * x13[i] - L[1] * x03[i] + L[3] * x01[i];  // (0,1,3)
-        Real f3 = L[0] * x12[i] - L[1] * x02[i] + L[2] * x01[i];  // (0,1,2)
-        B[i] = (Real)2 * (bv[0] * f0 + bv[1] * f1 + bv[2] * f2 + bv[3] * f3);
-    }
-}
-
 // non-relativistic Boris rotation; h = q dt / (2 m)
 // 2 / (1 + tt), correctly rounded (for float via the correctly rounded reciprocal: scaling by
 // 2 commutes with rounding, so the result is the same as the division)
@@ -374,11 +330,87 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
     }
 }
 
+// FP64 mode: the affine field coefficients of k_field_prep32 (below) in FP64, from the FP64
+// gradients, 10 doubles per tet:
+// rec = E0 (3), W (3), B0 (3), beta, with E = E0 + W x off and B = B0 + beta off in the tet
+// (off relative to its vertex 0) equal to the Whitney-1 / Whitney-2 sums (Sec. II.C).
+__global__ void __launch_bounds__(256) k_field_prep64(const TetGeo* __restrict__ geo,
+                                                      const TetTopo* __restrict__ topo,
+                                                      const double* __restrict__ e, const double* __restrict__ b,
+                                                      int64_t nt, double* __restrict__ rec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        Geo G;
+        TetTopo T;
+        load_geo(geo, (int)t, G);
+        load_topo(topo, (int)t, T);
+        double g[4][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[1][i] = G.g[i];
+            g[2][i] = G.g[3 + i];
+            g[3][i] = G.g[6 + i];
+            g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+        }
+        double ev[6], bv[4];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ev[k] = __ldg(e + T.edge[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bv[k] = __ldg(b + T.face[k]);
+        double x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
+        cross<double>(g[0], g[1], x01);
+        cross<double>(g[0], g[2], x02);
+        cross<double>(g[0], g[3], x03);
+        cross<double>(g[1], g[2], x12);
+        cross<double>(g[1], g[3], x13);
+        cross<double>(g[2], g[3], x23);
+        double E0[3], W[3], K[4][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            E0[i] = ev[0] * g[1][i] + ev[1] * g[2][i] + ev[2] * g[3][i];
+            W[i] = ev[0] * x01[i] + ev[1] * x02[i] + ev[2] * x03[i] + ev[3] * x12[i] + ev[4] * x13[i] +
+                   ev[5] * x23[i];
+            // faces: 0=(1,2,3), 1=(0,2,3), 2=(0,1,3), 3=(0,1,2)
+            K[0][i] = 2.0 * (bv[1] * x23[i] + bv[2] * x13[i] + bv[3] * x12[i]);
+            K[1][i] = 2.0 * (bv[0] * x23[i] - bv[2] * x03[i] - bv[3] * x02[i]);
+            K[2][i] = 2.0 * (-bv[0] * x13[i] - bv[1] * x03[i] + bv[3] * x01[i]);
+            K[3][i] = 2.0 * (bv[0] * x12[i] + bv[1] * x02[i] + bv[2] * x01[i]);
+        }
+        double beta = 0.0;
+#pragma unroll
+        for (int a = 1; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) beta += (K[a][i] - K[0][i]) * g[a][i];
+        double* r = rec + 10 * t;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            r[i] = E0[i];
+            r[3 + i] = W[i];
+            r[6 + i] = K[0][i];
+        }
+        r[9] = beta * (1.0 / 3.0);
+    }
+}
+
+// E and B at offset x in tet c from its FP64 record
+__device__ __forceinline__ void fields64(const double* __restrict__ rec, int c, const double x[3], double E[3],
+                                         double B[3]) {
+    const double2* p = reinterpret_cast<const double2*>(rec + 10 * (int64_t)c);
+    const double2 a = __ldg(p), bb = __ldg(p + 1), d = __ldg(p + 2), f = __ldg(p + 3), h = __ldg(p + 4);
+    const double E0[3] = {a.x, a.y, bb.x}, W[3] = {bb.y, d.x, d.y}, B0[3] = {f.x, f.y, h.x};
+    const double beta = h.y;
+    E[0] = E0[0] + (W[1] * x[2] - W[2] * x[1]);
+    E[1] = E0[1] + (W[2] * x[0] - W[0] * x[2]);
+    E[2] = E0[2] + (W[0] * x[1] - W[1] * x[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) B[i] = B0[i] + beta * x[i];
+}
+
 // ---------------------------------------------------------------- FP64 mode
 template <typename Real>
 __global__ void __launch_bounds__(256) k_push_deposit(
-    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ e,
-    const double* __restrict__ b, int32_t* __restrict__ cell, Real* __restrict__ off,
+    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ f64,
+    int32_t* __restrict__ cell, Real* __restrict__ off,
     Real* __restrict__ vel, int64_t n, int32_t nt, double qmdt2, Real dt, double qw, int max_cross,
     int aggregate, Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
@@ -397,15 +429,12 @@ __global__ void __launch_bounds__(256) k_push_deposit(
         for (int k = 0; k < 10; ++k) agg[k] = (Real)0;
         TetTopo T;
         if (c >= 0) {
-            Geo G;
-            load_geo(geo, c, G);
             load_topo(topo, c, T);
             Real x[3] = {off[p], off[n + p], off[2 * n + p]};
             Real v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
-            double xa[3] = {(double)x[0], (double)x[1], (double)x[2]}, la[4];
-            bary(G, xa, la);
+            double xa[3] = {(double)x[0], (double)x[1], (double)x[2]};
             Real E[3], B[3];
-            gather<Real>(G, T, e, b, la, E, B);
+            fields64(f64, c, xa, E, B);
             boris<Real>(v, E, B, (Real)qmdt2);
             vel[p] = v[0];
             vel[n + p] = v[1];
@@ -1297,8 +1326,8 @@ __global__ void __launch_bounds__(128) k_walk_adams32(const TetHot* __restrict__
 // FP64 Adams step: FP64 gather (Whitney-1/2 on the tet), the Adams update and the FP64 walk
 // with warp-aggregated deposits of the particles that stay in their tet.
 __global__ void __launch_bounds__(256) k_push_adams64(
-    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ e,
-    const double* __restrict__ b, int32_t* __restrict__ cell, double* __restrict__ off,
+    const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ f64,
+    int32_t* __restrict__ cell, double* __restrict__ off,
     double* __restrict__ vel, AdamsStep<double> A, int32_t nt, double qw, int max_cross, int aggregate,
     double* __restrict__ dG, double* __restrict__ Q, int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
@@ -1317,15 +1346,12 @@ __global__ void __launch_bounds__(256) k_push_adams64(
         for (int k = 0; k < 10; ++k) agg[k] = 0.0;
         TetTopo T;
         if (c >= 0) {
-            Geo G;
-            load_geo(geo, c, G);
             load_topo(topo, c, T);
             double x[3] = {off[p], off[n + p], off[2 * n + p]};
             double v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
-            double la[4], E[3], B[3], a[3], v1[3], xb[3], hx[3], ha[3];
+            double E[3], B[3], a[3], v1[3], xb[3], hx[3], ha[3];
             adams_history<double>(A, p, hx, ha);
-            bary(G, x, la);
-            gather<double>(G, T, e, b, la, E, B);
+            fields64(f64, c, x, E, B);
             adams_update<double>(A, x, v, E, B, hx, ha, a, v1, xb);
             adams_store<double>(A, vel, p, v, a, v1);
             int end_cell;
@@ -1566,8 +1592,13 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                                              (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
         }
     } else {
+        {
+            PhaseTimer pt(ctx, PH_PREP, s);
+            k_field_prep64<<<grid_for(ctx->hc.nt, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b,
+                                                                               ctx->hc.nt, ctx->d_field64);
+        }
         PhaseTimer pt(ctx, PH_PUSH64, s);
-        k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
+        k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, ctx->d_field64, p->cell,
                                                     (double*)p->off, (double*)p->vel, p->n, nt, qmdt2, dt,
                                                     qw, max_cross, agg, (double*)dG, (double*)Q,
                                                     ctx->d_status);
@@ -1656,11 +1687,16 @@ fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, cons
         for (int j = 0; j < 3; ++j) A.slot[j] = slot[j];
         for (int j = 0; j < 4; ++j) A.beta[j] = kBeta[order - 1][j];
         A.dt = dt, A.qm = qm;
+        {
+            PhaseTimer pt(ctx, PH_PREP, s);
+            k_field_prep64<<<grid_for(ctx->hc.nt, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b,
+                                                                               ctx->hc.nt, ctx->d_field64);
+        }
         PhaseTimer pt(ctx, PH_ADAMS, s);
-        k_push_adams64<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b, p->cell,
-                                                                      (double*)p->off, (double*)p->vel, A, nt, qw,
-                                                                      max_cross, agg, (double*)dG, (double*)Q,
-                                                                      ctx->d_status);
+        k_push_adams64<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, ctx->d_field64,
+                                                                      p->cell, (double*)p->off, (double*)p->vel, A,
+                                                                      nt, qw, max_cross, agg, (double*)dG,
+                                                                      (double*)Q, ctx->d_status);
     }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
