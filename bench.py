@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-field", action="store_true", help="skip timing the oracle's field step")
     ap.add_argument("--no-graphs", action="store_true", help="launch eagerly instead of replaying CUDA graphs")
     ap.add_argument("--no-field", action="store_true", help="particle step only (no implicit field solve)")
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -996,6 +997,27 @@ def cpu_baseline(args, wl, budget_s):
         orc.step(sp.cell[:n2], sp.X[:n2], sp.V[:n2], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
         el += time.perf_counter() - t
         done += n2
+    # the field step of the oracle (scipy: direct solve of the Gauss-law projection, CG on the
+    # Newmark system to 1e-13), one step on the same mesh with a continuity-respecting current
+    field = None
+    if not args.no_field and not args.no_cpu_field:
+        import numpy as np
+        from oracle import fields as OF
+        t = time.perf_counter()
+        fo = OF.FieldOracle(orc.cx, wl.dt)
+        t_setup = time.perf_counter() - t
+        rng = np.random.default_rng(0)
+        cx = orc.cx
+        E0 = 1e3 * rng.uniform(-1.0, 1.0, cx.n_edges)
+        E0[cx.boundary_edge] = 0.0
+        dG = 1e-12 * rng.uniform(-1.0, 1.0, cx.n_edges)
+        dG[cx.boundary_edge] = 0.0
+        Q = cx.D0().T @ dG
+        t = time.perf_counter()
+        fo.step(E0, E0, b, dG, np.zeros_like(dG), Q)
+        field = {"ms_per_field_step": (time.perf_counter() - t) * 1e3, "setup_s": t_setup, "threads": 1,
+                 "what": "oracle field step (Newmark CG + Gauss-law projection by a direct solve + Faraday), "
+                         "scipy on one host thread"}
     # the same oracle on one host thread, over a smaller sample
     n1 = min(sp.n, 20000)
     t = time.perf_counter()
@@ -1004,7 +1026,8 @@ def cpu_baseline(args, wl, budget_s):
     return {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n2} of {sp.n} particles of species 0, {done // n2} step(s), FP64 oracle (C, OpenMP), "
                       f"{el:.1f} s",
-            "value_1_thread": n1 / max(el1, 1e-9), "sample_1_thread": f"{n1} particles, 1 step, 1 thread"}
+            "value_1_thread": n1 / max(el1, 1e-9), "sample_1_thread": f"{n1} particles, 1 step, 1 thread",
+            "field_step": field}
 
 
 def run_reference(args):
