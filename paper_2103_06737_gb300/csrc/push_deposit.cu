@@ -8,7 +8,11 @@
 // warp shuffles before one global atomic per edge/node.  Particles that cross faces
 // deposit each piece with direct atomics.
 //
-// Precision: gather, push and deposit products in Real (float or double).  The exit
+// The gather goes through per-tet affine field records (E = E0 + W x off, B = B0 + beta off
+// in the tet, equal to the Whitney-1 / Whitney-2 sums), made once per call from e and b by
+// k_field_prep32 (FP32 records) or k_field_prep64 (FP64 mode).
+//
+// Precision: fields, push and deposit products in Real (float or double).  The exit
 // test of the walk (barycentric coordinates of the end point, crossing fraction,
 // argmin) is always FP64.  The piece deposit uses the factored form
 //   dG_ab = q w (l^a_a (l^c_b - l^a_b) - l^a_b (l^c_a - l^a_a)),
