@@ -383,10 +383,10 @@ def run_gpu(args):
         if field:                 # fields: Newmark, Gauss-law projection, Faraday -> E^{n+1}, b^{n+1}
             F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dG_prev, Qn, tol=args.tol,
                                  max_iter=args.max_iter, precond=state["precond"], info=False)
-            # Newmark right-hand side (2), solve (1; the mixed solver also gathers into and
-            # scatters out of its row order: 2), Gauss right-hand side (2), solve (1),
-            # projection and Faraday update (2)
-            n_k += 8 + (2 if solv[0] == "mixed" else 0)
+            # Newmark right-hand side (2) and solve (mixed: gather into its row order, solve,
+            # scatter out with A E^N: 3; FP64: the solve, then M E^N: 2), Gauss right-hand side
+            # (1), solve (1), projection and Faraday update (2)
+            n_k += 9 if solv[0] == "mixed" else 8
             for bit in (F.FP_PC_LEARNED, F.FP_PC_LEARNED_GAUSS):
                 if state["precond"] & bit:
                     n_k += 13     # residual, network forward (9 kernels), candidate, residual, select

@@ -572,14 +572,22 @@ __global__ void k_perm_gather(const int32_t* __restrict__ perm, const double* __
     }
 }
 
+// ... and, when ax is given, A x = b - r from the solve's last FP64 residual r (the mixed
+// solver stops right after computing it for the final x), back in DOF order as well
 __global__ void k_perm_scatter(const int32_t* __restrict__ perm, const double* __restrict__ px,
-                               double* __restrict__ x, int64_t n) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        x[__ldg(perm + r)] = px[r];
+                               double* __restrict__ x, const double* __restrict__ pb,
+                               const double* __restrict__ r64, double* __restrict__ ax, int64_t n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = __ldg(perm + r);
+        x[k] = px[r];
+        if (ax) ax[k] = pb[r] - r64[r];
+    }
 }
 
+// ax (Newmark system only, may be null): also A x for the final x, in DOF order, when the
+// mixed solver ran (F->last_fp64[slot] == 0 afterwards); the FP64 solver leaves it alone
 fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double tol, const double* scale_vec,
-                  int max_iter, int slot, cudaStream_t s) {
+                  int max_iter, int slot, cudaStream_t s, double* ax = nullptr) {
     FieldDev* F = ctx->field;
     int use64 = ctx->solver_fp64;
     if (ctx->solver_sys[system] >= 0) use64 = ctx->solver_sys[system] == FP_PC_JACOBI_FP64;
@@ -619,7 +627,8 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
             m.b = F->pb, m.x = F->px;
         }
         FP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(solver_kernel(bs, false), dim3(grid), dim3(bs), args, smem, s));
-        if (system == FP_SYS_NEWMARK) k_perm_scatter<<<grid_of(ctx, F->ne), kBlock, 0, s>>>(F->perm_e, F->px, x, F->ne);
+        if (system == FP_SYS_NEWMARK)
+            k_perm_scatter<<<grid_of(ctx, F->ne), kBlock, 0, s>>>(F->perm_e, F->px, x, F->pb, F->q, ax, F->ne);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
@@ -745,12 +754,16 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
         if (sl != FP_OK) return sl;
     }
     // Newmark solve for E^N from the guess 2E^n - E^{n-1} (written into E_next above)
-    fp_status st = run_pcg(ctx, FP_SYS_NEWMARK, F->rhs, E_next, tol, nullptr, max_iter, 0, s);
+    fp_status st = run_pcg(ctx, FP_SYS_NEWMARK, F->rhs, E_next, tol, nullptr, max_iter, 0, s, F->tmp);
     if (st != FP_OK) return st;
-    // Gauss-law projection: L d = D0^T M E^N + Q on interior nodes, to ||r|| <= tol ||Q||
+    // Gauss-law projection: L d = D0^T M E^N + Q on interior nodes, to ||r|| <= tol ||Q||.
+    // D0^T M E^N = D0^T A E^N, since D0^T S = (S D0)^T = 0 (curl grad = 0) on the rows the
+    // interior nodes touch; the mixed solver hands back A E^N = b - r from its last residual,
+    // so M E^N needs its own product only after the FP64 solver.
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
-        k_spmv<<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, E_next, F->ne, F->tmp);
+        if (F->last_fp64[0])
+            k_spmv<<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, E_next, F->ne, F->tmp);
         if (f32)
             k_gauss_rhs<float><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
                                                      F->tmp, (const float*)Q_new, F->nn, F->rhs, F->qd);
