@@ -921,14 +921,16 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
         std::vector<int32_t> ptr, w, scol;
         std::vector<int64_t> map;
         // column offsets col - row as int16 (empty when some offset does not fit)
+        // (the lanes past the last row of a partial slice are never computed: offset 0)
         auto offsets16 = [](const std::vector<int32_t>& scol, const std::vector<int32_t>& sptr,
-                            const std::vector<int32_t>& sw) {
+                            const std::vector<int32_t>& sw, int64_t n) {
             std::vector<int16_t> d(scol.size());
             for (size_t sl = 0; sl < sptr.size(); ++sl)
                 for (int64_t j = 0; j < sw[sl]; ++j)
                     for (int64_t lane = 0; lane < 32; ++lane) {
                         const int64_t k = sptr[sl] + 32 * j + lane;
-                        const int64_t off = (int64_t)scol[k] - (int64_t)(32 * sl + lane);
+                        const int64_t row = (int64_t)(32 * sl + lane);
+                        const int64_t off = row < n ? (int64_t)scol[k] - row : 0;
                         if (off < -32768 || off > 32767) return std::vector<int16_t>();
                         d[k] = (int16_t)off;
                     }
@@ -1021,14 +1023,14 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
 #endif
             if (FP_SOLVER_ORDER && F->sectors_e[1] < F->sectors_e[0]) {
                 sell(rp2, col2, ne, &ptr, &w, &scol, &map);
-                d16 = offsets16(scol, ptr, w);
+                d16 = offsets16(scol, ptr, w, ne);
             }
             if (d16.empty()) {   // the edge order
                 perm = &ident;
                 F->sectors_e[1] = F->sectors_e[0];
                 permuted(ident, &rp2, &col2, &val2);
                 sell(rp2, col2, ne, &ptr, &w, &scol, &map);
-                d16 = offsets16(scol, ptr, w);
+                d16 = offsets16(scol, ptr, w, ne);
             }
             std::vector<double> pA = gather(map, val2);
             std::vector<float> pA32(pA.begin(), pA.end()), pdinv(ne);
@@ -1055,7 +1057,7 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
         std::vector<double> sL = gather(map, H.L);
         std::vector<float> sL32(sL.begin(), sL.end());
         {
-            const std::vector<int16_t> d16 = offsets16(scol, ptr, w);
+            const std::vector<int16_t> d16 = offsets16(scol, ptr, w, hc.nn);
             if (!d16.empty() && st == FP_OK) st = up(ctx, &F->sn_d16, d16);
             F->hptr[FP_SYS_GAUSS] = ptr;
             F->slots_total[FP_SYS_GAUSS] = (int64_t)scol.size();
