@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--solver", default="mixed,mixed",
                     help="field CG for the Newmark and Gauss systems: mixed (refinement) or fp64, e.g. mixed,fp64")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
-    ap.add_argument("--poly", default="3,6",
+    ap.add_argument("--poly", default="3,8",
                     help="Chebyshev degree of the inner preconditioner, Newmark and Gauss systems (1 = Jacobi)")
     ap.add_argument("--poly-ratio", default="15,100",
                     help="lambda_max / lambda_low of the Chebyshev interval, Newmark and Gauss systems")
