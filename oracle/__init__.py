@@ -13,6 +13,8 @@ Parts:
                      Faraday update, residuals (Sec. II.C, IV.A-B)
   adams.py           fourth-order Adams(-Bashforth) particle mover with start-up, on the
                      same walk and deposits (Sec. IV.B.2)
+  cotree.py          tree / co-tree reduced field system (Z-matrices, Eq. reduceMEs and
+                     reducedWaveEqn) and the first-order mixed FEM, dense (Sec. IV.B, V, VI.A.1)
 """
 from __future__ import annotations
 

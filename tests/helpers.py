@@ -1,4 +1,4 @@
-"""Shared helpers for the GPU parity tests (tolerances follow the stated reading).
+"""Shared helpers for the tests (tolerances follow the stated reading).
 
 Deposit tolerance (per entry, relative to the sum of absolute contributions):
   |G_gpu - G_ref|_e <= tol * sum_p |g_{p,e}|   and   max|G_gpu - G_ref| <= tol * max|G_ref|
@@ -36,3 +36,36 @@ def csr_tuple(m, n_cols):
     m = m.tocsr()
     m.sort_indices()
     return (m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.int8), n_cols)
+
+
+def continuity_run(m, cx, fo, dt, n_steps, seed, q_sign=-1.0):
+    """Deposits from the oracle's own particle steps on the library reading's fields.
+
+    The reduced system rests on continuity at every free node.  A particle absorbed by the
+    wall leaves the particle set after its step, so the next step's node charge no longer
+    holds its wall charge; under the natural boundary those wall nodes are free.  The run
+    therefore keeps absorbed charge on the wall: Q^{n+1} = Q^n + D0^T dG^{n+1/2}, which
+    equals the particles' own W0 charge wherever no particle was absorbed."""
+    from paper_2103_06737_gb300 import inputs as I
+    import oracle as O
+
+    orc = O.Oracle(m.xyz, m.tets)
+    sp_ = I.uniform_species(m, 800, seed, 0.02 * I.C_LIGHT, q_sign * I.Q_E, I.M_E, 1e6)
+    _, b0 = cx.project_uniform((0, 0, 0), (0, 0, 0.1))
+    Q0, _ = orc.charge(sp_.cell, sp_.X, sp_.q, sp_.w)
+    E0 = fo.initial_field(Q0)
+    E_prev, E, b = E0.copy(), E0.copy(), b0.copy()
+    dG_prev = np.zeros(cx.n_edges)
+    cell, X, V = sp_.cell, sp_.X, sp_.V
+    D0T = cx.D0().T.astype(np.float64)
+    Q = Q0.copy()
+    out = []
+    for _ in range(n_steps):
+        r = orc.step(cell, X, V, E, b, sp_.q, sp_.m, sp_.w, dt)
+        cell, X, V = r["cell"], r["X"], r["V"]
+        Q = Q + D0T @ r["dG"]
+        assert np.abs(Q - r["Q"])[~cx.boundary_node].max() <= 1e-13 * np.abs(Q).max()
+        E1, b1 = fo.step(E, E_prev, b, r["dG"], dG_prev, Q)
+        out.append(dict(dG=r["dG"], dG_prev=dG_prev, Q=Q.copy(), E=E1, b=b1))
+        E_prev, E, b, dG_prev = E, E1, b1, r["dG"]
+    return Q0, E0, b0, out
