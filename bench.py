@@ -71,6 +71,12 @@ def parse():
                     help="timed field steps with the natural (Neumann) field boundary (0: skip)")
     ap.add_argument("--adams-steps", type=int, default=20,
                     help="timed calls of the fourth-order Adams particle step (0: skip that measurement)")
+    ap.add_argument("--drift-steps", type=int, default=200,
+                    help="steps of the Gauss-law comparison of the projected step with the unprojected "
+                         "first-order mixed FEM and wave-equation FEM (0: skip)")
+    ap.add_argument("--drift-tol", type=float, default=1e-6,
+                    help="second run of the Gauss-law comparison with this solver tolerance for the two "
+                         "unprojected systems (the projected step keeps --tol; 0: skip)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up at least this long (clock sampling under load)")
     return ap.parse_args()
@@ -745,6 +751,85 @@ def run_gpu(args):
                 "status": int(lib.status()),
                 "what": "PIC step with the natural field boundary: Newmark over all edges, Gauss-law projection "
                         "with the zero-mean constraint (a net charge spread as alpha), Faraday"}
+    def measure_gauss_drift():
+        """The Gauss-law comparison of Sec. V and VI.B on this workload: the projected step (the
+        product path) against the first-order mixed FEM and the wave-equation FEM without the
+        projection.  All three are fed the deposits of the same particle steps, pushed with the
+        projected step's fields, from the same initial state (E^0 from the Gauss law, b^0 the
+        uniform B0, which drives no interior edge).  Per step: max |D0^T [*eps] E + Q| over
+        interior nodes divided by its scale, for each; the two comparison steps are timed with
+        CUDA events, L2 flushed before each step (outside the events).  Run once with every
+        solve at --tol, and once with the unprojected systems' solves at --drift-tol: the
+        excitation of their gradient null space follows the solves' errors (Sec. V)."""
+        mh = F.fem_pic_mfem_create(lib.h)
+        names = ("projected", "mfem", "wave")
+        solver = code[solv[0]]
+
+        def run(tol_cmp):
+            state["precond"] = precond
+            restore()
+            torch.cuda.synchronize()
+            E_m, E_m2, b_m = e.clone(), torch.empty_like(e), b.clone()
+            E_wp, E_w, E_w2, b_w = e.clone(), e.clone(), torch.empty_like(e), b.clone()
+            K = args.drift_steps
+            hist = torch.zeros(K, 3, 2, dtype=torch.float64, device=dev)
+            ev = []
+            for k in range(K):
+                pl = plan(state["i"])
+                flush_l2(3000 + k)
+                enqueue_push(pl)
+                ta, tb, tc = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                ta.record(stream)
+                F.fem_pic_mfem_step(lib.h, mh, E_m, E_m2, b_m, dG, tol=tol_cmp, max_iter=args.max_iter,
+                                    precond=solver, info=False)
+                tb.record(stream)
+                F.fem_pic_wave_step(lib.h, mh, E_wp, E_w, E_w2, b_w, dG, dG_prev, tol=tol_cmp,
+                                    max_iter=args.max_iter, precond=solver, info=False)
+                tc.record(stream)
+                ev.append((ta, tb, tc))
+                enqueue_field()          # the projected step: e <- E^{n+1}, dG_prev <- dG, Qo <- Qn
+                F.fem_pic_mfem_gauss_residual(lib.h, mh, e, Qn, hist[k, 0])
+                F.fem_pic_mfem_gauss_residual(lib.h, mh, E_m2, Qn, hist[k, 1])
+                F.fem_pic_mfem_gauss_residual(lib.h, mh, E_w2, Qn, hist[k, 2])
+                E_m, E_m2 = E_m2, E_m
+                E_wp, E_w, E_w2 = E_w, E_w2, E_wp
+                advance(pl)
+                state["i"] += 1
+            torch.cuda.synchronize()
+            h = hist.cpu().numpy()
+            rel = h[:, :, 0] / np.maximum(h[:, :, 1], 1e-300)
+            at = [n for n in (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000) if n <= K]
+
+            def slope(j):
+                # least-squares exponent of the relative residual against the step number (second half)
+                n = np.arange(1, K + 1)[K // 2:]
+                y = np.maximum(rel[K // 2:, j], 1e-300)
+                return float(np.polyfit(np.log(n), np.log(y), 1)[0]) if K >= 8 else None
+            return {
+                "tol_projected": args.tol, "tol_unprojected": tol_cmp, "steps": K, "status": int(lib.status()),
+                "rel_residual_at_step": {nm: {str(n): float(rel[n - 1, j]) for n in at} for j, nm in enumerate(names)},
+                "rel_residual_max": {nm: float(rel[:, j].max()) for j, nm in enumerate(names)},
+                "growth_exponent_second_half": {nm: slope(j) for j, nm in enumerate(names)},
+                "ms_mfem_step": float(np.mean([a.elapsed_time(b_) for a, b_, _ in ev])),
+                "ms_wave_step": float(np.mean([b_.elapsed_time(c) for _, b_, c in ev])),
+            }
+        try:
+            out = {"what": "Gauss-law residual max|D0^T M E + Q| / scale over interior nodes: the projected step "
+                           "against the first-order mixed FEM (trapezoidal Newmark on the E-b system) and Newmark "
+                           "on the wave equation, both without the projection, fed the same deposits",
+                   "solver": solv[0], "same_tol": run(args.tol)}
+            if args.drift_tol > 0:
+                out["loose_unprojected"] = run(args.drift_tol)
+            return out
+        finally:
+            F.fem_pic_mfem_destroy(mh)
+
+    drift = None
+    if args.drift_steps > 0 and field:
+        try:
+            drift = measure_gauss_drift()
+        except Exception as ex:   # the comparison never takes the main measurement down with it
+            drift = {"error": f"{type(ex).__name__}: {ex}"}
     neumann = None if (args.neumann_steps <= 0 or not field) else measure_neumann()
 
     out = None
@@ -850,6 +935,7 @@ def run_gpu(args):
             "e2e": e2e,
             "adams": adams,
             "neumann": neumann,
+            "gauss_drift": drift,
             "fp64_mode": fp64,
         }
     del lib

@@ -342,6 +342,61 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
 fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
                                 fp_solve_info* info, void* stream);
 
+/* ------------------------------------------- comparison systems of the field solve (Sec. V, VI) */
+
+/*
+ * Handle for the systems the paper compares the quasi-Helmholtz step with, and for the
+ * Gauss-law residual.  Made from the field setup of ctx (fem_pic_field_setup first); it
+ * holds the face mass [*mu^-1]_fg = integral of W2_f . mu^-1 W2_g (Sec. II.C, every face
+ * free), the transpose of [curl] = D1, and scratch.  Owned by the library: destroy it
+ * before ctx.  Calls made after a new fem_pic_field_setup return FP_EINVAL.
+ */
+typedef struct fem_pic_mfem fem_pic_mfem_t;
+fp_status fem_pic_mfem_create(fem_pic_t* ctx, fem_pic_mfem_t** out);
+void fem_pic_mfem_destroy(fem_pic_mfem_t* m);
+
+/* Host copy of the face mass in CSR (rows N_f, sorted columns): nnz, row_ptr [N_f+1], col
+ * [nnz], val [nnz]; any may be NULL (call with NULL arrays first to size them). */
+fp_status fem_pic_mfem_face_mass(const fem_pic_mfem_t* m, int64_t* nnz, int32_t* row_ptr, int32_t* col,
+                                 double* val);
+
+/*
+ * One step of the first-order mixed FEM (MFEM) of Eq. maxwell_semi with Newmark (beta = 1/4,
+ * gamma = 1/2), the trapezoidal rule for a first-order system, and NO Gauss-law projection:
+ *   (M + dt^2/4 S) E^{n+1} = (M - dt^2/4 S) E^n + dt [curl]^T [*mu^-1] b^n - dG^{n+1/2}
+ *   b^{n+1} = b^n - dt [curl] (E^{n+1} + E^n)/2
+ * with M = [*eps], S = [*S] and dt of the field setup.  E_cur = E^n, E_next receives E^{n+1}
+ * (device double [N_e], distinct buffers); b (device double [N_f], all faces) is updated in
+ * place; dG_half (particle precision [N_e], NULL = 0) is the step's deposit.  The Newmark
+ * system is solved by fem_pic_field_solve from the start E^n (precond: FP_PC_JACOBI or
+ * FP_PC_JACOBI_FP64; tol, max_iter and info as there, FP_ENOCONV after a finished step whose
+ * solve missed tol).  With E^0 a gradient and the same deposits it gives the E of
+ * fem_pic_wave_step; unlike it, a gradient error in E stays constant instead of growing (Sec. V).
+ */
+fp_status fem_pic_mfem_step(fem_pic_mfem_t* m, const double* E_cur, double* E_next, double* b,
+                            const void* dG_half, double tol, int max_iter, int precond, fp_solve_info* info,
+                            void* stream);
+
+/*
+ * Newmark on the wave equation (Eq. wave_cont) without the Gauss-law projection: steps 1 and 3
+ * of fem_pic_field_step (the wave-equation FEM of Sec. V, whose gradient null space grows
+ * linearly in time).  Arguments as there (b may be NULL: no Faraday update); solved by
+ * fem_pic_field_solve from 2E^n - E^{n-1}, precond and errors as fem_pic_mfem_step.
+ */
+fp_status fem_pic_wave_step(fem_pic_mfem_t* m, const double* E_prev, const double* E_cur, double* E_next,
+                            double* b, const void* dG_half, const void* dG_prev, double tol, int max_iter,
+                            int precond, fp_solve_info* info, void* stream);
+
+/*
+ * Gauss-law residual g = D0^T [*eps] E + Q (Eq. discreteGauss) on the free nodes, in FP64:
+ * out[0] = max |g_n|, out[1] = max over the same nodes of |Q_n| + sum over incident edges of
+ * |([*eps] E)_e| (the scale).  Natural boundary: g less (sum Q / sum alpha) alpha, the net
+ * charge the zero-mean constraint spreads.  E device double [N_e], Q particle precision [N_n]
+ * (NULL = 0), out device double [2].  Asynchronous.
+ */
+fp_status fem_pic_mfem_gauss_residual(fem_pic_mfem_t* m, const double* E, const void* Q, double* out,
+                                      void* stream);
+
 /*
  * Solver per system, overriding the precond argument of the solve calls: newmark_solver
  * and gauss_solver are FP_PC_JACOBI (mixed-precision refinement), FP_PC_JACOBI_FP64, or

@@ -110,6 +110,12 @@ def lib():
             "fem_pic_field_solve": (I32, [P, I32, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_step": (I32, [P, P, P, P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_initial": (I32, [P, P, P, D, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_mfem_create": (I32, [P, ctypes.POINTER(P)]),
+            "fem_pic_mfem_destroy": (None, [P]),
+            "fem_pic_mfem_face_mass": (I32, [P, P, P, P, P]),
+            "fem_pic_mfem_step": (I32, [P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_wave_step": (I32, [P, P, P, P, P, P, P, D, I32, I32, ctypes.POINTER(SolveInfo), P]),
+            "fem_pic_mfem_gauss_residual": (I32, [P, P, P, P, P]),
             "fem_pic_field_last_info": (I32, [P, ctypes.POINTER(SolveInfo), P]),
             "fem_pic_field_options": (I32, [P, I32, I32, D]),
             "fem_pic_field_poly": (I32, [P, I32, I32, D]),
@@ -419,6 +425,65 @@ def fem_pic_field_step(h, E_prev, E_cur, E_next, b, dG_half, dG_prev, Q_new, tol
     if st not in (FP_OK, FP_ENOCONV):
         _check(st, h)
     return st, ([inf[0].as_dict(), inf[1].as_dict()] if inf is not None else None)
+
+
+def fem_pic_mfem_create(h):
+    """Handle of the comparison systems (MFEM, unprojected wave equation) for h's field setup."""
+    m = ctypes.c_void_p()
+    _check(lib().fem_pic_mfem_create(h, ctypes.byref(m)), h)
+    return m
+
+
+def fem_pic_mfem_destroy(m):
+    lib().fem_pic_mfem_destroy(m)
+
+
+def fem_pic_mfem_face_mass(h, m):
+    """Host CSR (row_ptr, col, val) of the face mass [*mu^-1] over all faces."""
+    nnz = np.zeros(1, dtype=np.int64)
+    _check(lib().fem_pic_mfem_face_mass(m, _ptr(nnz), None, None, None), h)
+    nf = fem_pic_sizes(h)["n_faces"]
+    rp = np.zeros(nf + 1, dtype=np.int32)
+    col = np.zeros(int(nnz[0]), dtype=np.int32)
+    val = np.zeros(int(nnz[0]), dtype=np.float64)
+    _check(lib().fem_pic_mfem_face_mass(m, None, _ptr(rp), _ptr(col), _ptr(val)), h)
+    return rp, col, val
+
+
+def fem_pic_mfem_step(h, m, E_cur, E_next, b, dG_half, tol: float = 1e-10, max_iter: int = 10000,
+                      precond: int = FP_PC_JACOBI, info: bool = True, stream=None):
+    sz = fem_pic_sizes(h)
+    for t, nm in ((E_cur, "E_cur"), (E_next, "E_next")):
+        _need(t, torch.float64, sz["n_edges"], name=nm)
+    _need(b, torch.float64, sz["n_faces"], name="b")
+    inf = SolveInfo() if info else None
+    st = lib().fem_pic_mfem_step(m, _ptr(E_cur), _ptr(E_next), _ptr(b), _ptr(dG_half), float(tol), int(max_iter),
+                                 int(precond), ctypes.byref(inf) if inf is not None else None, _stream(stream))
+    if st not in (FP_OK, FP_ENOCONV):
+        _check(st, h)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_wave_step(h, m, E_prev, E_cur, E_next, b, dG_half, dG_prev, tol: float = 1e-10, max_iter: int = 10000,
+                      precond: int = FP_PC_JACOBI, info: bool = True, stream=None):
+    sz = fem_pic_sizes(h)
+    for t, nm in ((E_prev, "E_prev"), (E_cur, "E_cur"), (E_next, "E_next")):
+        _need(t, torch.float64, sz["n_edges"], name=nm)
+    if b is not None:
+        _need(b, torch.float64, sz["n_faces"], name="b")
+    inf = SolveInfo() if info else None
+    st = lib().fem_pic_wave_step(m, _ptr(E_prev), _ptr(E_cur), _ptr(E_next), _ptr(b), _ptr(dG_half),
+                                 _ptr(dG_prev), float(tol), int(max_iter), int(precond),
+                                 ctypes.byref(inf) if inf is not None else None, _stream(stream))
+    if st not in (FP_OK, FP_ENOCONV):
+        _check(st, h)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def fem_pic_mfem_gauss_residual(h, m, E, Q, out, stream=None):
+    """out (device double[2]) <- max |D0^T [*eps] E + Q| over free nodes and its scale."""
+    _need(out, torch.float64, 2, name="out")
+    _check(lib().fem_pic_mfem_gauss_residual(m, _ptr(E), _ptr(Q), _ptr(out), _stream(stream)), h)
 
 
 def fem_pic_field_initial(h, Q, E, tol: float = 1e-10, max_iter: int = 10000, info: bool = True, stream=None):
