@@ -221,6 +221,27 @@ def test_eigenvalues_and_null_spaces(mesh3):
     assert rw1 == G_w.shape[0] - nn and rw2 == G_w.shape[0] - 2 * nn
 
 
+def test_eigenvalue_experiment_at_the_papers_resolution():
+    """Sec. VI.A.1: a PEC box of side 1 m, average edge about 0.214 m (here the jittered 6^3
+    cube, 0.209 m), Newmark far beyond any explicit limit (dt = 10 h / c): every eigenvalue of
+    the full MFEM and of the reduced first-order system lies on the unit circle, and the reduced
+    system keeps exactly MFEM's dynamic spectrum (units with eps = mu = 1)."""
+    m = I.cube_mesh(6, 1.0, 0.1, seed=1)
+    cx = O.Complex(m.xyz, m.tets)
+    edge = np.linalg.norm(cx.xyz[cx.edges[:, 1]] - cx.xyz[cx.edges[:, 0]], axis=1).mean()
+    assert 0.2 < edge < 0.22
+    ct = OC.CoTree(cx, "pec", eps=1.0, mu=1.0)
+    dt = 10.0 / 6.0
+    mu_m = np.linalg.eigvals(ct.mfem_amplification(dt))
+    mu_r = np.linalg.eigvals(ct.reduced_amplification(dt))
+    assert np.abs(np.abs(mu_m) - 1.0).max() < 1e-10
+    assert np.abs(np.abs(mu_r) - 1.0).max() < 1e-10
+    static = np.abs(mu_m - 1.0) < 1e-6
+    assert static.sum() == len(ct.inn) + cx.n_tets - 1
+    assert not (np.abs(mu_r - 1.0) < 1e-6).any()
+    assert np.abs(np.sort(np.angle(mu_m[~static])) - np.sort(np.angle(mu_r))).max() < 1e-8
+
+
 def test_gauss_error_grows_in_we_fem_only(mesh4, trees4):
     """A gradient error left by one inexact solve: WE-FEM's Gauss residual grows linearly,
     MFEM's stays where it was, and the projection removes it."""
