@@ -102,6 +102,14 @@ def test_projectors_and_z_matrices(mesh4, trees4, bc):
     assert np.abs(Pe @ Pe - Pe).max() <= 1e-10
     assert np.abs(ct.div @ Pb).max() <= 1e-12
     assert np.abs(Pb @ Pb - Pb).max() <= 1e-12
+    # the pseudo-inverse projector of Eq. proj_es has the same range (the gradient fluxes) but
+    # projects along ker(Sigma^T), so its complement is not divergence-free: the projector of
+    # Eq. efld_mod_proj is the one that imposes the discrete Gauss law
+    S = ct.Sigma
+    P_pinv = S @ np.linalg.pinv(S.T @ S) @ S.T
+    assert np.abs(P_pinv @ ct.P_sigma_e - ct.P_sigma_e).max() <= 1e-12
+    assert np.abs(S.T @ (np.eye(len(ct.ie)) - P_pinv)).max() <= 1e-12 * np.abs(S).max()
+    assert np.abs(ct.grad.T @ (np.eye(len(ct.ie)) - P_pinv)).max() > 0.1
     # Z13 = 0 (Sec. IV.B)
     assert np.abs(ct.Z13).max() <= 1e-10 * np.abs(ct.Z12).max()
     # Z21 and the reduced stiffness are symmetric positive definite: no null space in the
