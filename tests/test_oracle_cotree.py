@@ -106,7 +106,7 @@ def test_projectors_and_z_matrices(mesh4, trees4, bc):
     # projects along ker(Sigma^T), so its complement is not divergence-free: the projector of
     # Eq. efld_mod_proj is the one that imposes the discrete Gauss law
     S = ct.Sigma
-    P_pinv = S @ np.linalg.pinv(S.T @ S) @ S.T
+    P_pinv = S @ np.linalg.pinv(S.T @ S, rcond=1e-10, hermitian=True) @ S.T
     assert np.abs(P_pinv @ ct.P_sigma_e - ct.P_sigma_e).max() <= 1e-12
     assert np.abs(S.T @ (np.eye(len(ct.ie)) - P_pinv)).max() <= 1e-12 * np.abs(S).max()
     assert np.abs(ct.grad.T @ (np.eye(len(ct.ie)) - P_pinv)).max() > 0.1
