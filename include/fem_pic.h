@@ -349,7 +349,9 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
  * Gauss-law residual.  Made from the field setup of ctx (fem_pic_field_setup first); it
  * holds the face mass [*mu^-1]_fg = integral of W2_f . mu^-1 W2_g (Sec. II.C, every face
  * free), the transpose of [curl] = D1, and scratch.  Owned by the library: destroy it
- * before ctx.  Calls made after a new fem_pic_field_setup return FP_EINVAL.
+ * before ctx.  Calls made after a new fem_pic_field_setup return FP_EINVAL.  Create returns
+ * FP_EINVAL without a field setup or when host memory runs out, FP_ECUDA when a device
+ * allocation fails (*out is then NULL).
  */
 typedef struct fem_pic_mfem fem_pic_mfem_t;
 fp_status fem_pic_mfem_create(fem_pic_t* ctx, fem_pic_mfem_t** out);

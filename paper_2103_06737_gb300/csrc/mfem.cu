@@ -168,6 +168,12 @@ fp_status upload(fem_pic* ctx, T** d, const std::vector<T>& v) {
     return FP_OK;
 }
 
+fp_status scratch(fem_pic* ctx, double** d, int64_t n) {
+    FP_CUDA_TRY(ctx, cudaMalloc((void**)d, (size_t)n * sizeof(double) + 16));
+    FP_CUDA_TRY(ctx, cudaMemset(*d, 0, (size_t)n * sizeof(double)));
+    return FP_OK;
+}
+
 fp_status check(fem_pic_mfem* m, const char* who) {
     if (!m) return FP_EINVAL;
     const FieldDev* F = m->ctx->field;
@@ -232,17 +238,23 @@ fp_status fem_pic_mfem_create(fem_pic_t* ctx, fem_pic_mfem_t** out) {
     m->F = F;
     m->dt = F->dt, m->eps = F->eps, m->mu = F->mu, m->bc = F->bc;
     m->ne = F->ne, m->nn = F->nn, m->nf = F->nf;
-    assemble_mfem(ctx->hc, F->mu, &m->host);
+    try {
+        assemble_mfem(ctx->hc, F->mu, &m->host);
+    } catch (const std::bad_alloc&) {   // no exception crosses the C ABI
+        delete m;
+        ctx->err = "fem_pic_mfem_create: out of host memory";
+        return FP_EINVAL;
+    }
     fp_status st = upload(ctx, &m->f_rp, m->host.f_rp);
     if (st == FP_OK) st = upload(ctx, &m->f_col, m->host.f_col);
     if (st == FP_OK) st = upload(ctx, &m->f_val, m->host.Fm);
     if (st == FP_OK) st = upload(ctx, &m->ef_rp, m->host.ef_rp);
     if (st == FP_OK) st = upload(ctx, &m->ef_col, m->host.ef_col);
     if (st == FP_OK) st = upload(ctx, &m->ef_sgn, m->host.ef_sgn);
-    if (st == FP_OK) st = upload(ctx, &m->h, std::vector<double>(m->nf, 0.0));
-    if (st == FP_OK) st = upload(ctx, &m->rhs, std::vector<double>(m->ne, 0.0));
-    if (st == FP_OK) st = upload(ctx, &m->me, std::vector<double>(m->ne, 0.0));
-    if (st == FP_OK) st = upload(ctx, &m->qsum, std::vector<double>(1, 0.0));
+    if (st == FP_OK) st = scratch(ctx, &m->h, m->nf);
+    if (st == FP_OK) st = scratch(ctx, &m->rhs, m->ne);
+    if (st == FP_OK) st = scratch(ctx, &m->me, m->ne);
+    if (st == FP_OK) st = scratch(ctx, &m->qsum, 1);
     if (st != FP_OK) {
         fem_pic_mfem_destroy(m);
         return st;
