@@ -173,6 +173,11 @@ def test_reduced_systems_reproduce_the_projected_step(mesh4, trees4, bc):
         assert np.abs(ct.compose(y_new, s_new) - E_ref).max() <= tol, k
         assert np.abs(ct.compose(y_new, s1) - E_ref).max() <= tol, k
         assert np.abs(Em - E_ref).max() <= tol, k
+        # Sec. VI.A.2's comparison by components: MFEM's E split by Eq. efld_decomp_flux
+        # against the E_ns of Eq. discreteGauss and the E_s of Eq. reducedWaveEqn
+        y_m, s_m = ct.decompose(Em)
+        assert np.abs(y_m - y_new).max() <= 1e-9 * np.abs(y_new).max(), k
+        assert np.abs(s_m - s_new).max() <= 1e-9 * Escale, k
         # db_ref = b - b0 carries the rounding of the 0.1 T background flux b0
         btol = 1e-8 * np.abs(db_ref).max() + (k + 2) * 2.3e-16 * np.abs(b0).max()
         assert np.abs(ct.Lam_b @ Bs - db_ref).max() <= btol, k
