@@ -188,23 +188,28 @@ def test_reduced_systems_reproduce_the_projected_step(mesh4, trees4, bc):
     assert np.abs(ct.Lam_e @ s).max() > 1e-4 * Escale
 
 
-def test_eigenvalues_and_null_spaces(mesh3):
-    """Sec. VI.A.1 and Sec. V on a PEC box (units with eps = mu = 1, dt = 2 h)."""
+@pytest.mark.parametrize("bc", ["pec", "neumann"])
+def test_eigenvalues_and_null_spaces(mesh3, bc):
+    """Sec. VI.A.1 and Sec. V on a box with PEC or natural walls (units with eps = mu = 1,
+    dt = 2 h).  Static modes of MFEM: the gradients of node potentials (PEC: one per interior
+    node; natural: N_n - 1, constants map to zero) and the non-solenoidal fluxes (PEC: N_t - 1
+    over the interior faces; natural: N_t), by Euler's relation."""
     cx = mesh3
     h = 1.0 / 3.0
     dt = 2.0 * h
-    ct = OC.CoTree(cx, "pec", eps=1.0, mu=1.0)
-    fo = OF.FieldOracle(cx, dt, eps=1.0, mu=1.0)
+    ct = OC.CoTree(cx, bc, eps=1.0, mu=1.0)
+    fo = OF.FieldOracle(cx, dt, eps=1.0, mu=1.0, bc=bc)
     nn, nt = len(ct.inn), cx.n_tets
+    n_grad = nn if bc == "pec" else nn - 1
+    n_div = nt - 1 if bc == "pec" else nt
     G_m = ct.mfem_amplification(dt)
     G_r = ct.reduced_amplification(dt)
     mu_m = np.linalg.eigvals(G_m)
     mu_r = np.linalg.eigvals(G_r)
     assert np.abs(np.abs(mu_m) - 1.0).max() < 1e-8
     assert np.abs(np.abs(mu_r) - 1.0).max() < 1e-8
-    # MFEM's static modes: gradients of node potentials and the N_t - 1 non-solenoidal fluxes
     static = np.abs(mu_m - 1.0) < 1e-6
-    assert static.sum() == nn + nt - 1
+    assert static.sum() == n_grad + n_div
     assert not (np.abs(mu_r - 1.0) < 1e-6).any()
     # the reduced system keeps exactly MFEM's dynamic spectrum
     ang_m = np.sort(np.angle(mu_m[~static]))
@@ -220,7 +225,7 @@ def test_eigenvalues_and_null_spaces(mesh3):
     Im = np.eye(G_m.shape[0])
     r1 = np.linalg.matrix_rank(G_m - Im, tol=1e-8)
     r2 = np.linalg.matrix_rank((G_m - Im) @ (G_m - Im), tol=1e-8)
-    assert r1 == r2 == G_m.shape[0] - (nn + nt - 1)
+    assert r1 == r2 == G_m.shape[0] - (n_grad + n_div)
     # WE-FEM (state E^n, E^{n-1}): the gradient modes form Jordan chains, E^n = (n+1) grad phi
     G_w = fo.amplification_matrix()
     assert np.abs(np.abs(np.linalg.eigvals(G_w)) - 1.0).max() < 1e-6
@@ -231,7 +236,7 @@ def test_eigenvalues_and_null_spaces(mesh3):
     Iw = np.eye(G_w.shape[0])
     rw1 = np.linalg.matrix_rank(G_w - Iw, tol=1e-8)
     rw2 = np.linalg.matrix_rank((G_w - Iw) @ (G_w - Iw), tol=1e-8)
-    assert rw1 == G_w.shape[0] - nn and rw2 == G_w.shape[0] - 2 * nn
+    assert rw1 == G_w.shape[0] - n_grad and rw2 == G_w.shape[0] - 2 * n_grad
 
 
 def test_eigenvalue_experiment_at_the_papers_resolution():
