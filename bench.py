@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/sec at stated FP32 error; field-solve ms/step learned vs plain CG"
 UNIT = "particle-steps/s"
+# nominal HBM3e bandwidth of one GB300, for fractions quoted beside the measured copy peak
+NOMINAL_HBM_GBS = 7900.0
 
 
 def parse():
@@ -847,6 +849,7 @@ def run_gpu(args):
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         roof_push = {"kernel": "k_push_ws32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
+                     "frac_of_nominal": fast_achieved / NOMINAL_HBM_GBS,
                      "algorithmic_bytes_per_launch": fbytes, "avg_launch_ms": fast_avg,
                      "traffic": measured_traffic("k_push_ws32", wl.name)}
         roof = roof_push
@@ -869,6 +872,7 @@ def run_gpu(args):
                     cand.append((avg, {"kernel": name, "bound": "hbm",
                                        "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
                                        "unit": "GB/s", "frac": byt / (avg * 1e-3) / 1e9 / peak,
+                                       "frac_of_nominal": byt / (avg * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
                                        "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg,
                                        "iterations_per_launch": its, "refinements_per_launch": outs,
                                        "traffic": measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph,
@@ -898,7 +902,8 @@ def run_gpu(args):
             "roofline_push": roof_push,
             "roofline_push_call": {"kernels": "k_field_prep32 + k_push_ws32 + k_walk32 (sum of kernel times)",
                                    "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                   "frac": achieved / peak, "algorithmic_bytes_per_launch": abytes,
+                                   "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                                   "algorithmic_bytes_per_launch": abytes,
                                    "avg_call_ms": avg_push},
             "timing": ("timed steps replay one CUDA graph per step shape" if use_graphs else "eager launches") +
                       "; per-kernel times from an eager pass of the same steps with the library's CUDA-event profiler",
@@ -1002,6 +1007,7 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
                                    "k_push_adams32 when the state is not 16-byte aligned)",
                          "bound": "hbm", "achieved": ach, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                         "frac_of_nominal": ach / NOMINAL_HBM_GBS,
                          "algorithmic_bytes_per_launch": byt, "avg_launch_ms": f_avg,
                          "traffic": measured_traffic("k_push_ws32/adams", wl.name)}}
 
