@@ -1,0 +1,86 @@
+// The library's host-side assembly (discrete complex, field operators, face mass and [curl]^T)
+// compiled without CUDA, with a small C interface, so that the CPU tests can hold it against
+// the oracle.  Test infrastructure: built by tests/test_host_assembly.py with g++.
+#include <algorithm>
+#include <cstring>
+
+#include "../paper_2103_06737_gb300/csrc/field.cuh"
+#include "../paper_2103_06737_gb300/csrc/mfem.cuh"
+
+using namespace fempic;
+
+namespace {
+HostComplex g_hc;
+HostFields g_hf;
+HostMfem g_hm;
+std::string g_err;
+
+template <typename T>
+void put(const std::vector<T>& v, T* out) {
+    if (out) std::copy(v.begin(), v.end(), out);
+}
+}  // namespace
+
+extern "C" {
+
+// Build the complex of a mesh and assemble every host operator; returns the fp_status.
+int hh_build(int64_t nn, int64_t nt, const double* xyz, const int32_t* tet, double eps, double mu, int pec) {
+    fp_mesh m{};
+    m.n_nodes = nn;
+    m.n_tets = nt;
+    m.xyz = xyz;
+    m.tet = tet;
+    g_hc = HostComplex();
+    g_hf = HostFields();
+    g_hm = HostMfem();
+    const fp_status st = build_complex(&m, &g_hc, &g_err);
+    if (st != FP_OK) return (int)st;
+    assemble_fields(g_hc, eps, mu, pec != 0, &g_hf);
+    assemble_mfem(g_hc, mu, &g_hm);
+    return 0;
+}
+
+const char* hh_error() { return g_err.c_str(); }
+
+// N_n, N_e, N_f, N_t, nnz of the edge pattern, of the node pattern, of the face mass, of [curl]^T
+void hh_sizes(int64_t* s) {
+    s[0] = g_hc.nn;
+    s[1] = g_hc.ne;
+    s[2] = g_hc.nf;
+    s[3] = g_hc.nt;
+    s[4] = (int64_t)g_hf.e_col.size();
+    s[5] = (int64_t)g_hf.n_col.size();
+    s[6] = (int64_t)g_hm.f_col.size();
+    s[7] = (int64_t)g_hm.ef_col.size();
+}
+
+void hh_complex(int32_t* edges, int32_t* faces, int32_t* tet_faces, uint8_t* bface) {
+    put(g_hc.edges, edges);
+    put(g_hc.faces, faces);
+    put(g_hc.tf, tet_faces);
+    put(g_hc.bface, bface);
+}
+
+void hh_fields(int32_t* e_rp, int32_t* e_col, double* M, double* S, int32_t* n_rp, int32_t* n_col, double* L,
+               uint8_t* edge_fixed, uint8_t* node_fixed) {
+    put(g_hf.e_rp, e_rp);
+    put(g_hf.e_col, e_col);
+    put(g_hf.M, M);
+    put(g_hf.S, S);
+    put(g_hf.n_rp, n_rp);
+    put(g_hf.n_col, n_col);
+    put(g_hf.L, L);
+    put(g_hf.edge_fixed, edge_fixed);
+    put(g_hf.node_fixed, node_fixed);
+}
+
+void hh_mfem(int32_t* f_rp, int32_t* f_col, double* Fm, int32_t* ef_rp, int32_t* ef_col, int8_t* ef_sgn) {
+    put(g_hm.f_rp, f_rp);
+    put(g_hm.f_col, f_col);
+    put(g_hm.Fm, Fm);
+    put(g_hm.ef_rp, ef_rp);
+    put(g_hm.ef_col, ef_col);
+    put(g_hm.ef_sgn, ef_sgn);
+}
+
+}  // extern "C"

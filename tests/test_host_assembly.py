@@ -1,0 +1,133 @@
+"""The library's host-side assembly against the oracle, on the CPU (no GPU, no CUDA runtime).
+
+tests/host_harness.cpp compiles the library's own host sources (mesh_build.cpp,
+field_build.cpp, mfem_build.cpp) with g++ and exposes what they build.  Checked here:
+the discrete complex's numbering and boundary faces; the edge mass [*eps], the curl-curl
+matrix [*S] and the node Laplacian L (closed-form element matrices in the library, quadrature
+and the paper's products D1^T [*mu^-1] D1, D0^T [*eps] D0 in the oracle) on the free DOFs, with
+unit rows on PEC DOFs; the face mass [*mu^-1] and the transposed curl of the comparison
+systems.  Both field boundaries.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2103_06737_gb300 import inputs as I
+import oracle as O
+from oracle import fields as OF
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2103_06737_gb300", "csrc")
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def hh(tmp_path_factory):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if not cxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    out = str(tmp_path_factory.mktemp("hh") / "libhh.so")
+    srcs = [os.path.join(HERE, "host_harness.cpp")] + [os.path.join(CSRC, f) for f in
+                                                        ("mesh_build.cpp", "field_build.cpp", "mfem_build.cpp")]
+    cmd = [cxx, "-O1", "-std=c++17", "-shared", "-fPIC", "-I" + inc, "-I" + os.path.join(ROOT, "include"),
+           *srcs, "-Wl,--no-undefined", "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lib = ctypes.CDLL(out)
+    lib.hh_error.restype = ctypes.c_char_p
+    lib.hh_build.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _build(hh, m, pec):
+    xyz = np.ascontiguousarray(m.xyz, np.float64)
+    tet = np.ascontiguousarray(m.tets, np.int32)
+    st = hh.hh_build(xyz.shape[0], tet.shape[0], _p(xyz), _p(tet), OF.EPS0, OF.MU0, 1 if pec else 0)
+    assert st == 0, hh.hh_error()
+    s = np.zeros(8, np.int64)
+    hh.hh_sizes(_p(s))
+    return [int(x) for x in s]
+
+
+@pytest.fixture(scope="module")
+def mesh4():
+    m = I.cube_mesh(4, 1.0, 0.1, seed=1)
+    return m, O.Complex(m.xyz, m.tets)
+
+
+def _close(a, b, rel=1e-12):
+    a, b = sp.csr_matrix(a), sp.csr_matrix(b)
+    scale = abs(b).max()
+    return abs(a - b).max() <= rel * scale
+
+
+@pytest.mark.parametrize("bc", ["pec", "neumann"])
+def test_field_operators_match_oracle(hh, mesh4, bc):
+    m, cx = mesh4
+    nn, ne, nf, nt, enz, nnz_n, fnz, efnz = _build(hh, m, bc == "pec")
+    assert (nn, ne, nf, nt) == (cx.n_nodes, cx.n_edges, cx.n_faces, cx.n_tets)
+    edges = np.zeros(2 * ne, np.int32)
+    faces = np.zeros(3 * nf, np.int32)
+    tf = np.zeros(4 * nt, np.int32)
+    bface = np.zeros(nf, np.uint8)
+    hh.hh_complex(_p(edges), _p(faces), _p(tf), _p(bface))
+    assert np.array_equal(edges.reshape(-1, 2), cx.edges)
+    assert np.array_equal(faces.reshape(-1, 3), cx.faces)
+    assert np.array_equal(tf.reshape(-1, 4), cx.tet_faces)
+    assert np.array_equal(bface.astype(bool), cx.boundary_face)
+
+    e_rp, e_col = np.zeros(ne + 1, np.int32), np.zeros(enz, np.int32)
+    M, S = np.zeros(enz), np.zeros(enz)
+    n_rp, n_col, L = np.zeros(nn + 1, np.int32), np.zeros(nnz_n, np.int32), np.zeros(nnz_n)
+    efix, nfix = np.zeros(ne, np.uint8), np.zeros(nn, np.uint8)
+    hh.hh_fields(_p(e_rp), _p(e_col), _p(M), _p(S), _p(n_rp), _p(n_col), _p(L), _p(efix), _p(nfix))
+    if bc == "pec":
+        assert np.array_equal(efix.astype(bool), cx.boundary_edge)
+        assert np.array_equal(nfix.astype(bool), cx.boundary_node)
+    else:
+        assert not efix.any() and not nfix.any()
+    fe, fn = np.nonzero(efix == 0)[0], np.nonzero(nfix == 0)[0]
+    Mh = sp.csr_matrix((M, e_col, e_rp), shape=(ne, ne))
+    Sh = sp.csr_matrix((S, e_col, e_rp), shape=(ne, ne))
+    Lh = sp.csr_matrix((L, n_col, n_rp), shape=(nn, nn))
+    assert _close(Mh[fe][:, fe], OF.edge_mass(cx)[fe][:, fe])
+    assert _close(Sh[fe][:, fe], OF.curl_curl(cx)[fe][:, fe])
+    assert _close(Lh[fn][:, fn], OF.node_laplacian(cx)[fn][:, fn])
+    # PEC rows: a unit diagonal and nothing else (M, L); no entry in S
+    for A, fixed in ((Mh, np.nonzero(efix)[0]), (Lh, np.nonzero(nfix)[0])):
+        blk = A[fixed]
+        assert abs(blk).sum() == fixed.size
+        assert np.array_equal(blk.toarray()[np.arange(fixed.size), fixed], np.ones(fixed.size))
+    assert Sh[np.nonzero(efix)[0]].count_nonzero() == 0
+
+
+def test_face_mass_and_curl_transpose_match_oracle(hh, mesh4):
+    m, cx = mesh4
+    nn, ne, nf, nt, enz, nnz_n, fnz, efnz = _build(hh, m, True)
+    f_rp, f_col, Fm = np.zeros(nf + 1, np.int32), np.zeros(fnz, np.int32), np.zeros(fnz)
+    ef_rp, ef_col, ef_sgn = np.zeros(ne + 1, np.int32), np.zeros(efnz, np.int32), np.zeros(efnz, np.int8)
+    hh.hh_mfem(_p(f_rp), _p(f_col), _p(Fm), _p(ef_rp), _p(ef_col), _p(ef_sgn))
+    Fh = sp.csr_matrix((Fm, f_col, f_rp), shape=(nf, nf))
+    assert _close(Fh, OF.face_mass(cx))
+    CT = sp.csr_matrix((ef_sgn.astype(np.float64), ef_col, ef_rp), shape=(ne, nf))
+    assert abs(CT - cx.D1().T.astype(np.float64)).max() == 0
+    # [curl]^T [*mu^-1] [curl] = [*S] (Eq. wave_cont), here from the library's two halves
+    assert _close(CT @ Fh @ CT.T, OF.curl_curl(cx))
