@@ -83,4 +83,15 @@ void hh_mfem(int32_t* f_rp, int32_t* f_col, double* Fm, int32_t* ef_rp, int32_t*
     put(g_hm.ef_sgn, ef_sgn);
 }
 
+// The Lanczos estimate of the largest eigenvalue of D^-1 A that sets the Chebyshev interval of
+// the inner solves: which = 0 the Newmark operator [*eps] + dt^2/4 [*S], 1 the node Laplacian.
+double hh_lambda_max(int which, double dt, int steps) {
+    if (which == 0) {
+        std::vector<double> A(g_hf.M.size());
+        for (size_t k = 0; k < A.size(); ++k) A[k] = g_hf.M[k] + 0.25 * dt * dt * g_hf.S[k];
+        return jacobi_lambda_max(g_hf.e_rp, g_hf.e_col, A, steps);
+    }
+    return jacobi_lambda_max(g_hf.n_rp, g_hf.n_col, g_hf.L, steps);
+}
+
 }  // extern "C"

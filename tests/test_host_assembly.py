@@ -6,7 +6,7 @@ the discrete complex's numbering and boundary faces; the edge mass [*eps], the c
 matrix [*S] and the node Laplacian L (closed-form element matrices in the library, quadrature
 and the paper's products D1^T [*mu^-1] D1, D0^T [*eps] D0 in the oracle) on the free DOFs, with
 unit rows on PEC DOFs; the face mass [*mu^-1] and the transposed curl of the comparison
-systems.  Both field boundaries.
+systems; the Lanczos estimate of the top of the Jacobi-scaled spectra.  Both field boundaries.
 """
 import ctypes
 import os
@@ -50,6 +50,8 @@ def hh(tmp_path_factory):
     lib.hh_error.restype = ctypes.c_char_p
     lib.hh_build.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int]
+    lib.hh_lambda_max.restype = ctypes.c_double
+    lib.hh_lambda_max.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
     return lib
 
 
@@ -131,3 +133,25 @@ def test_face_mass_and_curl_transpose_match_oracle(hh, mesh4):
     assert abs(CT - cx.D1().T.astype(np.float64)).max() == 0
     # [curl]^T [*mu^-1] [curl] = [*S] (Eq. wave_cont), here from the library's two halves
     assert _close(CT @ Fh @ CT.T, OF.curl_curl(cx))
+
+
+@pytest.mark.parametrize("bc", ["pec", "neumann"])
+def test_lanczos_estimate_of_the_jacobi_spectrum(hh, mesh4, bc):
+    """The top of the Jacobi-scaled spectra (the Chebyshev interval's upper end): 40 Lanczos
+    steps from the library's fixed start give a lower bound within 1% of the exact largest
+    eigenvalue of D^-1 A (numpy, symmetric form D^-1/2 A D^-1/2) for both systems."""
+    m, cx = mesh4
+    nn, ne, nf, nt, enz, nnz_n, fnz, efnz = _build(hh, m, bc == "pec")
+    dt = 0.2 * I.gyro_period(0.1)
+    e_rp, e_col = np.zeros(ne + 1, np.int32), np.zeros(enz, np.int32)
+    M, S = np.zeros(enz), np.zeros(enz)
+    n_rp, n_col, L = np.zeros(nn + 1, np.int32), np.zeros(nnz_n, np.int32), np.zeros(nnz_n)
+    efix, nfix = np.zeros(ne, np.uint8), np.zeros(nn, np.uint8)
+    hh.hh_fields(_p(e_rp), _p(e_col), _p(M), _p(S), _p(n_rp), _p(n_col), _p(L), _p(efix), _p(nfix))
+    for which, A in ((0, sp.csr_matrix((M + 0.25 * dt * dt * S, e_col, e_rp), shape=(ne, ne))),
+                     (1, sp.csr_matrix((L, n_col, n_rp), shape=(nn, nn)))):
+        d = 1.0 / np.sqrt(A.diagonal())
+        lam = np.linalg.eigvalsh((sp.diags(d) @ A @ sp.diags(d)).toarray()).max()
+        est = hh.hh_lambda_max(which, dt, 40)
+        assert est <= lam * (1 + 1e-9), (which, est, lam)
+        assert est >= 0.99 * lam, (which, est, lam)
