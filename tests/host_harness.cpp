@@ -83,6 +83,27 @@ void hh_mfem(int32_t* f_rp, int32_t* f_col, double* Fm, int32_t* ef_rp, int32_t*
     put(g_hm.ef_sgn, ef_sgn);
 }
 
+// D0 (which 0), D1 (1) or D2 (2) in CSR; returns nnz (arrays may be NULL to size them)
+int64_t hh_incidence(int which, int32_t* row_ptr, int32_t* col, int8_t* val) {
+    std::vector<int32_t> rp, c;
+    std::vector<int8_t> v;
+    incidence_csr(g_hc, which, &rp, &c, &v);
+    put(rp, row_ptr);
+    put(c, col);
+    put(v, val);
+    return (int64_t)c.size();
+}
+
+// per tet: neighbours across faces 0..3 (-1 wall), the gradients of lambda_1..3 (rows) and the
+// origin (the lowest-id vertex)
+void hh_tets(int32_t* nb, double* grad, double* origin) {
+    put(g_hc.nb, nb);
+    for (size_t t = 0; t < g_hc.geo.size(); ++t) {
+        if (grad) std::memcpy(grad + 9 * t, g_hc.geo[t].g, 9 * sizeof(double));
+        if (origin) std::memcpy(origin + 3 * t, g_hc.geo[t].o, 3 * sizeof(double));
+    }
+}
+
 // The Lanczos estimate of the largest eigenvalue of D^-1 A that sets the Chebyshev interval of
 // the inner solves: which = 0 the Newmark operator [*eps] + dt^2/4 [*S], 1 the node Laplacian.
 double hh_lambda_max(int which, double dt, int steps) {

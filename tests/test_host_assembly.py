@@ -50,6 +50,7 @@ def hh(tmp_path_factory):
     lib.hh_error.restype = ctypes.c_char_p
     lib.hh_build.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int]
+    lib.hh_incidence.restype = ctypes.c_int64
     lib.hh_lambda_max.restype = ctypes.c_double
     lib.hh_lambda_max.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
     return lib
@@ -63,7 +64,7 @@ def _build(hh, m, pec):
     xyz = np.ascontiguousarray(m.xyz, np.float64)
     tet = np.ascontiguousarray(m.tets, np.int32)
     st = hh.hh_build(xyz.shape[0], tet.shape[0], _p(xyz), _p(tet), OF.EPS0, OF.MU0, 1 if pec else 0)
-    assert st == 0, hh.hh_error()
+    assert st == 0, hh.hh_error().decode()
     s = np.zeros(8, np.int64)
     hh.hh_sizes(_p(s))
     return [int(x) for x in s]
@@ -155,3 +156,43 @@ def test_lanczos_estimate_of_the_jacobi_spectrum(hh, mesh4, bc):
         est = hh.hh_lambda_max(which, dt, 40)
         assert est <= lam * (1 + 1e-9), (which, est, lam)
         assert est >= 0.99 * lam, (which, est, lam)
+
+
+def test_incidence_neighbours_and_geometry_match_oracle(hh, mesh4):
+    """D0, D1, D2 bit-exact, the neighbour table exact, the barycentric gradients and tet
+    origins to round-off."""
+    m, cx = mesh4
+    nn, ne, nf, nt = _build(hh, m, True)[:4]
+    for which, ref, rows in ((0, cx.D0(), ne), (1, cx.D1(), nf), (2, cx.D2(), nt)):
+        k = int(hh.hh_incidence(which, None, None, None))
+        rp, col, val = np.zeros(rows + 1, np.int32), np.zeros(k, np.int32), np.zeros(k, np.int8)
+        hh.hh_incidence(which, _p(rp), _p(col), _p(val))
+        got = sp.csr_matrix((val.astype(np.int64), col, rp), shape=ref.shape)
+        assert (got != ref).nnz == 0, which
+    nb = np.zeros(4 * nt, np.int32)
+    grad, origin = np.zeros(9 * nt), np.zeros(3 * nt)
+    hh.hh_tets(_p(nb), _p(grad), _p(origin))
+    assert np.array_equal(nb.reshape(-1, 4), cx.neigh)
+    g_ref = OF.grads(cx)[:, 1:, :].reshape(nt, 9)
+    assert np.abs(grad.reshape(nt, 9) - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+    assert np.array_equal(origin.reshape(nt, 3), cx.xyz[cx.tv[:, 0]])
+
+
+def test_build_rejects_bad_meshes(hh):
+    """Host-side validation: a node id out of range (FP_EINVAL), a repeated node or a flat tet
+    (FP_EGEOM), a face shared by three tets (FP_EGEOM)."""
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [0.3, 0.3, 0.0], [0.2, 0.2, -1.0]],
+                   np.float64)
+
+    def build(tets, pts=xyz):
+        t = np.ascontiguousarray(np.array(tets, np.int32))
+        x = np.ascontiguousarray(pts)
+        return hh.hh_build(x.shape[0], t.shape[0], _p(x), _p(t), OF.EPS0, OF.MU0, 1)
+
+    assert build([[0, 1, 2, 3]]) == 0
+    assert build([[0, 1, 2, 9]]) == 1                      # FP_EINVAL
+    assert build([[0, 1, 2, 2]]) == 5                      # FP_EGEOM: repeated node
+    assert build([[0, 1, 2, 5]]) == 5                      # FP_EGEOM: node 5 lies in the plane z = 0
+    assert build([[0, 1, 2, 3], [0, 1, 2, 6]]) == 0
+    assert build([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 6]]) == 5   # face (0,1,2) in three tets
+    assert b"more than two" in hh.hh_error()
