@@ -724,7 +724,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         F.fem_pic_profile_read(lib.h, reset=True)
         F.fem_pic_profile_enable(lib.h, True)
-        ev, its, rr, live = [], [], [], []
+        ev, its, outs, rr, live = [], [], [], [], []
         for k in range(args.neumann_steps):
             live.append(alive())
             flush_l2(2000 + k)
@@ -736,6 +736,7 @@ def run_gpu(args):
             ev.append((a, z))
             fi = F.fem_pic_field_last_info(lib.h)
             its.append((fi[0]["iters"], fi[1]["iters"]))
+            outs.append((fi[0]["outer"], fi[1]["outer"]))
             rr.append(max(fi[0]["rel_res"], fi[1]["rel_res"]))
         torch.cuda.synchronize()
         F.fem_pic_profile_enable(lib.h, False)
@@ -750,6 +751,8 @@ def run_gpu(args):
                 "ms_gauss_cg": ph.get("cg_gauss", (0.0, 1))[0] / nsteps,
                 "newmark_iters_mean": float(np.mean([i[0] for i in its])),
                 "gauss_iters_mean": float(np.mean([i[1] for i in its])), "max_rel_res": max(rr),
+                "newmark_refinements_mean": float(np.mean([o[0] for o in outs])),
+                "gauss_refinements_mean": float(np.mean([o[1] for o in outs])),
                 "status": int(lib.status()),
                 "what": "PIC step with the natural field boundary: Newmark over all edges, Gauss-law projection "
                         "with the zero-mean constraint (a net charge spread as alpha), Faraday"}
