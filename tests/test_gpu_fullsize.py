@@ -98,7 +98,7 @@ def test_field_step_full_size(workload):
     _, b0 = cx.project_uniform((0.0, 0.0, 0.0), wl.B0)
     Q0, _ = orc.charge(sp.cell, sp.X, sp.q, sp.w)
     alpha = F.fem_pic_whitney0_integrals(lib.h)
-    Q_ion = -alpha * Q0.sum() / alpha.sum()          # neutralising immobile ions (reading 12)
+    Q_ion = -alpha * Q0.sum() / alpha.sum()          # immobile ions, node charge proportional to the W0 integrals
     E0 = fo.initial_field(Q0 + Q_ion)
     r = orc.step(sp.cell, sp.X, sp.V, E0, b0, sp.q, sp.m, sp.w, wl.dt)
     Q1 = r["Q"] + Q_ion

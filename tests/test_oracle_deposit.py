@@ -71,7 +71,6 @@ def test_two_tet_brute_force_path_integral():
         # brute force: midpoint rule on the unsplit path, W1 evaluated in the tet containing each sample
         pts = Pa[None, :] + s[:, None] * (Pb - Pa)[None, :]
         lam0 = orc.bary(np.zeros(ns, np.int32), pts)
-        in0 = lam0.min(axis=1) >= lam0.min(axis=1) * 0 - 0.0
         lam1 = orc.bary(np.ones(ns, np.int32), pts)
         in0 = lam0.min(axis=1) >= lam1.min(axis=1)
         assert (lam0.min(axis=1)[in0] > -1e-9).all() and (lam1.min(axis=1)[~in0] > -1e-9).all()
