@@ -67,6 +67,8 @@ def lib():
             _lib.oracle_bary.argtypes = [P, P, i64, P, P, P]
             _lib.oracle_boris.restype = None
             _lib.oracle_boris.argtypes = [i64, P, P, P, d, d, d]
+            _lib.oracle_walk_trace.restype = i
+            _lib.oracle_walk_trace.argtypes = [i64, i64, P, P, P, P, P, i, P, P, d, i, i, P, P, P, P, P, P, P, P]
             _lib.oracle_charge.restype = None
             _lib.oracle_charge.argtypes = [P, P, i64, i64, P, P, d, P, P]
     return _lib
@@ -150,6 +152,25 @@ class Oracle:
                                _p(dG), _p(dGa), _p(Q), _p(Qa), _p(ncross), int(nthreads))
         return dict(cell=cell, X=X, V=V, dG=dG, dG_abs=dGa, Q=Q, Q_abs=Qa, ncross=ncross,
                     n_bound=int(nb))
+
+    def walk_trace(self, cell, Xa, Xb, qw=1.0, max_cross=64, cap=256):
+        """The pieces of one walk: (cells [k], piece start points [k,3], stop point, end cell, dG, Q)."""
+        Xa = _f64(Xa, (3,))
+        Xb = _f64(Xb, (3,))
+        cells = np.zeros(cap, dtype=np.int32)
+        start = np.zeros((cap, 3))
+        stop = np.zeros(3)
+        end = np.zeros(1, dtype=np.int32)
+        dG = np.zeros(self.n_edges)
+        dGa = np.zeros(self.n_edges)
+        Q = np.zeros(self.n_nodes)
+        Qa = np.zeros(self.n_nodes)
+        k = lib().oracle_walk_trace(self.n_edges, self.n_nodes, _p(self.xyz), _p(self.tv32), _p(self.te32),
+                                    _p(self.tf32), _p(self.nb32), int(cell), _p(Xa), _p(Xb), float(qw),
+                                    int(max_cross), cap, _p(cells), _p(start), _p(stop), _p(end), _p(dG),
+                                    _p(dGa), _p(Q), _p(Qa))
+        assert k <= cap
+        return cells[:k].copy(), start[:k].copy(), stop, int(end[0]), dG, Q
 
     def charge(self, cell, X, q, w):
         cell = np.ascontiguousarray(cell, dtype=np.int32)

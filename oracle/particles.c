@@ -198,9 +198,25 @@ static void deposit_charge(const mesh_t* M, int t, const double X[3], double qw,
     }
 }
 
+/* optional record of the walk's pieces: the tet and start point of each piece */
+typedef struct {
+    int32_t* cell;
+    double* start;
+    int cap, n;
+} trace_t;
+
+static void trace_piece(trace_t* tr, int t, const double P[3]) {
+    if (!tr) return;
+    if (tr->n < tr->cap) {
+        tr->cell[tr->n] = t;
+        for (int i = 0; i < 3; ++i) tr->start[3 * tr->n + i] = P[i];
+    }
+    tr->n++;
+}
+
 /* walk X_a -> X_b from tet t; returns the final tet (-1 = absorbed), writes the stop point */
 static int walk(const mesh_t* M, int t, const double Xa[3], const double Xb[3], double qw,
-                int max_cross, acc_t* A, double Xstop[3], int* ncross, int* bound_hit) {
+                int max_cross, acc_t* A, double Xstop[3], int* ncross, int* bound_hit, trace_t* tr) {
     double cur[3] = {Xa[0], Xa[1], Xa[2]};
     double la[4], lb[4];
     int entry = -1;
@@ -223,6 +239,7 @@ static int walk(const mesh_t* M, int t, const double Xa[3], const double Xb[3], 
             }
         }
         if (kx < 0) {
+            trace_piece(tr, t, cur);
             deposit_segment(M, t, cur, Xb, qw, A);
             deposit_charge(M, t, Xb, qw, A);
             Xstop[0] = Xb[0];
@@ -241,6 +258,7 @@ static int walk(const mesh_t* M, int t, const double Xa[3], const double Xb[3], 
         }
         double Xc[3];
         for (int i = 0; i < 3; ++i) Xc[i] = cur[i] + smin * (Xb[i] - cur[i]);
+        trace_piece(tr, t, cur);
         deposit_segment(M, t, cur, Xc, qw, A);
         int nt = M->nb[4 * (int64_t)t + kx];
         if (nt < 0) {
@@ -327,7 +345,7 @@ int64_t oracle_step(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv
         }
         double Xs[3];
         int nc = 0, hit = 0;
-        int tn = walk(&M, t, Xa, Xb, qw, max_cross, &A, Xs, &nc, &hit);
+        int tn = walk(&M, t, Xa, Xb, qw, max_cross, &A, Xs, &nc, &hit, NULL);
         cell[p] = tn;
         for (int i = 0; i < 3; ++i) X[3 * p + i] = Xs[i];
         if (ncross) ncross[p] = nc;
@@ -379,4 +397,25 @@ void oracle_charge(const double* xyz, const int32_t* tv, int64_t nn, int64_t np,
     (void)nn;
     for (int64_t p = 0; p < np; ++p)
         if (cell[p] >= 0) deposit_charge(&M, cell[p], X + 3 * p, qw, &A);
+}
+
+/*
+ * The pieces of one particle's walk from Xa (in tet t) to Xb, for tests: cells[k] and
+ * start[3k..3k+2] are the tet and the start point of piece k (at most cap are stored);
+ * the stop point (Xb, the wall point or the point where the crossing bound stopped the
+ * walk) goes to stop[3] and the final tet (-1 = absorbed) to *end_cell.  Deposits go to
+ * dG, dGabs, Q, Qabs as in oracle_step.  Returns the number of pieces.
+ */
+int oracle_walk_trace(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv, const int32_t* te,
+                      const int32_t* tf, const int32_t* nb, int t, const double* Xa, const double* Xb, double qw,
+                      int max_cross, int cap, int32_t* cells, double* start, double* stop, int32_t* end_cell,
+                      double* dG, double* dGabs, double* Q, double* Qabs) {
+    mesh_t M = {xyz, tv, te, tf, nb, NULL, NULL};
+    acc_t A = {dG, dGabs, Q, Qabs};
+    trace_t tr = {cells, start, cap, 0};
+    int nc = 0, hit = 0;
+    (void)ne;
+    (void)nn;
+    *end_cell = walk(&M, t, Xa, Xb, qw, max_cross, &A, stop, &nc, &hit, &tr);
+    return tr.n;
 }

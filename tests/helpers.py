@@ -1,9 +1,14 @@
 """Shared helpers for the tests (tolerances follow the stated reading).
 
 Deposit tolerance (per entry, relative to the sum of absolute contributions):
-  |G_gpu - G_ref|_e <= tol * sum_p |g_{p,e}|   and   max|G_gpu - G_ref| <= tol * max|G_ref|
-with tol = 1e-12 in FP64 mode and 1e-5 in FP32 mode.  A plain relative bound per
-entry is ill-posed where thermal contributions cancel.
+  |G_gpu - G_ref|_e <= tol * sum_p |g_{p,e}| + 64 eps max|G_ref|
+  and   max|G_gpu - G_ref| <= tol * max|G_ref|
+with tol = 1e-12 in FP64 mode and 1e-5 in FP32 mode, eps = 2^-52.  A plain relative
+bound per entry is ill-posed where thermal contributions cancel.  The 64 eps term is
+the oracle's own FP64 rounding floor: its 2-point Gauss-Legendre nodes are not dyadic,
+so an entry whose exact value is zero (a piece on which the edge's two barycentric
+coordinates stay proportional, e.g. one of them zero throughout) comes out as rounding
+noise of order eps there.
 """
 import numpy as np
 
@@ -25,7 +30,8 @@ def assert_deposit_close(got, ref, ref_abs, tol, what="dG"):
     got = np.asarray(got, dtype=np.float64)
     err = np.abs(got - ref)
     scale = np.maximum(ref_abs, np.finfo(np.float64).tiny)
-    bad = err > tol * scale + 1e-300
+    floor = 64.0 * np.finfo(np.float64).eps * np.abs(ref).max()
+    bad = err > tol * scale + floor + 1e-300
     assert not bad.any(), (f"{what}: {bad.sum()} entries beyond {tol} * sum|contrib| "
                            f"(worst ratio {np.max(err / scale):.3e})")
     assert err.max() <= tol * max(np.abs(ref).max(), np.finfo(np.float64).tiny) + 1e-300, \
