@@ -49,7 +49,7 @@ typedef struct fem_pic fem_pic_t;
 
 typedef enum {
     FP_OK = 0,
-    FP_EINVAL = 1,   /* bad argument, size or pointer; invalid cell id */
+    FP_EINVAL = 1,   /* bad argument, size or pointer; invalid cell id; non-finite particle state */
     FP_ECUDA = 2,    /* a CUDA runtime call failed (text in fem_pic_last_error) */
     FP_EWALK = 3,    /* a particle hit the crossing bound of the tet walk */
     FP_ENOCONV = 4,  /* an iterative solve reached its iteration cap */
@@ -152,7 +152,10 @@ fp_status fem_pic_particles_to_global(fem_pic_t* ctx, int64_t n, const int32_t* 
  * 6 edges; at the end point Q_n += q w lambda_n on the end tet's 4 nodes
  * (Whitney-0 charge).  Reaching a wall absorbs the particle (cell = -1, charge at the
  * wall point); more than max_cross crossings stops it at its last crossing point and
- * sets FP_EWALK in the status word.  dG and Q are zeroed first unless FP_ACCUMULATE.
+ * sets FP_EWALK in the status word.  A particle whose position or velocity, given or
+ * pushed, is not finite (NaN or Inf, e.g. from a non-finite field DOF) is removed
+ * (cell = -1) with nothing deposited and sets FP_EINVAL in the status word, so dG and Q
+ * stay finite.  dG and Q are zeroed first unless FP_ACCUMULATE.
  * Particle arrays are updated in place.  Asynchronous.
  */
 fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
@@ -168,12 +171,14 @@ fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
  * grows with cudaMalloc; here that queue is a fixed array inside the library
  * (4,194,304 entries, 16 MiB, held on every device that loads the library until the
  * process exits).  The call allocates nothing: p->n above 4,194,304 returns
- * FP_EINVAL with nothing launched.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  All calls on a device share the array and it keeps the last
- * call's contents (each call clears the count it needs), so calls whose GPU work
- * overlaps (other streams, other threads, other handles) race on it: serialise them.
- * In FP_FP64 mode no queue is used and the call behaves like fem_pic_push_deposit.
+ * FP_EINVAL with nothing launched.  fem_pic_create (FP_FP32) looks up the array's
+ * device address in the handle's context (cudaGetSymbolAddress) and keeps it in the
+ * handle.  All calls on a device share the array and it keeps the last call's contents
+ * (each call clears the count it needs), so calls whose GPU work overlaps (other
+ * streams, other threads, other handles) race on it: serialise them.  It runs the same
+ * kernels as fem_pic_push_deposit (the staged pipeline when n is a multiple of 4 and the
+ * state arrays are 16-byte aligned, the grid-stride kernel otherwise).  In FP_FP64 mode no
+ * queue is used and the call behaves like fem_pic_push_deposit.
  */
 fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const double* b,
                                       const fp_particles* p, double dt, int max_cross, void* dG,
@@ -505,8 +510,10 @@ fp_status fem_pic_profile_read(fem_pic_t* ctx, double ms[16], int64_t count[16],
 fp_status fem_pic_selftest_wait(fem_pic_t* ctx, double limit_s, void* stream);
 
 /*
- * Synchronise `stream`, return and clear the device status word:
- * FP_OK, FP_EWALK or FP_EINVAL (the first error class seen, EINVAL first).
+ * Synchronise `stream`, return and clear the device status word: FP_OK, or the first
+ * error class seen in this order: FP_ECUDA (a bounded wait gave up), FP_EINVAL (a
+ * non-finite particle state, or a cell id outside [0, N_t)), FP_EWALK, FP_ENOCONV.
+ * fem_pic_last_error names the cause.
  */
 fp_status fem_pic_status(fem_pic_t* ctx, void* stream);
 

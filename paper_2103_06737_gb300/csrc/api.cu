@@ -205,6 +205,7 @@ fp_status fem_pic_create(const fp_mesh* mesh, const fp_csr_i8* D0, const fp_csr_
             int32_t zero = 0;
             s2 = upload(ctx, &ctx->d_status, &zero, 1);
         }
+        if (s2 == FP_OK && precision == FP_FP32) s2 = static_queue_lookup(ctx);
         if (s2 != FP_OK) {
             g_create_err = ctx->err;
             fem_pic_destroy(ctx);
@@ -437,6 +438,11 @@ fp_status fem_pic_status(fem_pic_t* ctx, void* stream) {
     if (h & ST_TIMEOUT) {
         ctx->err = "a kernel gave up waiting for its asynchronous copies";
         return FP_ECUDA;
+    }
+    if (h & ST_NONFINITE) {
+        ctx->err = "a particle's position or velocity was not finite (NaN or Inf): it was removed "
+                   "(cell -1) with nothing deposited";
+        return FP_EINVAL;
     }
     if (h & ST_INVAL) {
         ctx->err = "a kernel saw a cell id outside [0, N_t)";

@@ -51,7 +51,9 @@ struct __align__(128) TetHot {
 static_assert(sizeof(TetHot) == 128, "TetHot layout");
 
 // bits of the device status word
-enum : int32_t { ST_WALK = 1, ST_INVAL = 2, ST_NOCONV = 4, ST_TIMEOUT = 8 };
+// ST_NONFINITE: a particle's position or velocity (given, or after its push) was not finite;
+// the particle was removed (cell -1) with nothing deposited
+enum : int32_t { ST_WALK = 1, ST_INVAL = 2, ST_NOCONV = 4, ST_TIMEOUT = 8, ST_NONFINITE = 16 };
 
 struct HostComplex {
     int64_t nn = 0, ne = 0, nf = 0, nt = 0;
@@ -123,6 +125,8 @@ struct fem_pic {
     int32_t* d_slow_idx = nullptr;    // [slow_cap]
     int32_t* d_slow_count = nullptr;  // [1]
     int64_t slow_cap = 0;
+    // device address of the allocation-free push's fixed queue in this handle's context
+    int32_t* d_static_queue = nullptr;
     // co-resident blocks of the staged push kernels (0: not queried yet): bulk-copy pipeline,
     // warp-specialised Boris push, warp-specialised Adams push
     int tma_blocks_per_sm = 0;
@@ -184,6 +188,13 @@ __device__ __forceinline__ bool neg_strict(double x) {
     const long long b = __double_as_longlong(x);
     return b < 0 && b != (long long)0x8000000000000000ull;
 }
+// x is neither infinite nor NaN (exponent field not all ones), from the bit pattern
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool finite_bits(float x) {
+    return ((__float_as_uint(x) >> 23) & 0xffu) != 0xffu;
+}
 // x > 0 strictly, from the bit pattern (NaN with a clear sign bit counts as > 0)
 __device__ __forceinline__ bool pos_strict(double x) {
     return __double_as_longlong(x) > 0;
@@ -231,6 +242,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                               cudaStream_t s);
 fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
                             int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s);
+fp_status static_queue_lookup(fem_pic* ctx);
 fp_status launch_wait_selftest(fem_pic* ctx, double limit_s, cudaStream_t s);
 fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
                                 cudaStream_t s);

@@ -19,7 +19,6 @@
 // algebraically equal to q w (l^a_a l^c_b - l^a_b l^c_a), the exact line integral of
 // W1_ab along a straight piece; the differences are formed in FP64 so the Real products
 // do not cancel.
-#include <mutex>
 #include <string>
 
 #include "async_copy.cuh"
@@ -218,6 +217,15 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
                           const double xa[3], const double xb[3], double qw, int max_cross,
                           Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status,
                           Real* agg, int* end_cell, double end_off[3]) {
+    if (!(finite_bits(xa[0]) && finite_bits(xa[1]) && finite_bits(xa[2]) && finite_bits(xb[0]) &&
+          finite_bits(xb[1]) && finite_bits(xb[2]))) {
+        // a non-finite start or end point has no path: the particle is removed, nothing deposited
+        atomicOr(status, ST_NONFINITE);
+        *end_cell = -1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) end_off[i] = xa[i];
+        return false;
+    }
     Geo G;
     TetTopo Tc;
     load_geo(geo, c, G);
@@ -688,7 +696,7 @@ struct AdamsMover32 {
 template <class Mover>
 __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
                                               int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
-                                              int32_t nt, Mover& mv, float w, int aggregate,
+                                              int32_t nt, Mover& mv, float w, int aggregate, int32_t* __restrict__ cell,
                                               float* __restrict__ off, float* __restrict__ dG, float* __restrict__ Q,
                                               int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
@@ -721,6 +729,8 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         hot_fields(H, x, E, B);
         float xb[3], dx[3], d[4];
         mv.move(p, x, v, E, B, xb);
+        const bool finite = finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]) && finite_bits(xb[0]) &&
+                            finite_bits(xb[1]) && finite_bits(xb[2]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) dx[i] = xb[i] - x[i];
         d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
@@ -735,7 +745,12 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         float lbmin = l[0] + d[0];
 #pragma unroll
         for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
-        if (lbmin >= margin) {
+        if (!finite) {
+            // a non-finite state or push (NaN/Inf velocity, offset or field): the particle is
+            // removed with nothing deposited, and the status word says so
+            atomicOr(status, ST_NONFINITE);
+            cell[p] = -1;
+        } else if (lbmin >= margin) {
             agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
             agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
             agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
@@ -815,7 +830,7 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
         const bool slow =
-            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, bm, w, aggregate, off, dG, Q, status);
+            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, bm, w, aggregate, cell, off, dG, Q, status);
         warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);   // one global atomic per warp
     }
 }
@@ -970,7 +985,7 @@ __global__ void __launch_bounds__(kTmaThreads, FP_FAST_MIN_BLOCKS) k_push_tma32(
                     v[k] = reinterpret_cast<const float*>(st + (4 + k) * kTmaSlot)[j];
                 }
             }
-            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, bm, w, aggregate, off, dG,
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, bm, w, aggregate, cell, off, dG,
                                             Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), tq[qb], &tq_n[qb]);
         }
@@ -1194,7 +1209,7 @@ __global__ void __launch_bounds__(kWsThreads, WsMinBlocks<MA>::value) k_push_ws3
                 }
                 if (c >= 0 && c < nt) mv.history(p0 + j);
             }
-            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, mv, w, aggregate, off, dG,
+            const bool slow = fast_particle(hot, rec, rlo, rn, c, x, v, p0 + j, n, nt, mv, w, aggregate, cell, off, dG,
                                             Q, status);
             warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
         }
@@ -1273,7 +1288,7 @@ __global__ void __launch_bounds__(256, FP_ADAMS_MIN_BLOCKS) k_push_adams32(
             am.history(p);
         }
         const bool slow =
-            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, am, w, aggregate, off, dG, Q, status);
+            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, am, w, aggregate, cell, off, dG, Q, status);
         warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);
     }
 }
@@ -1412,6 +1427,10 @@ __global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restri
         }
         float v[4] = {0.f, 0.f, 0.f, 0.f};
         TetHot H;
+        if (c >= 0 && !(finite_bits(off[p]) && finite_bits(off[n + p]) && finite_bits(off[2 * n + p]))) {
+            atomicOr(status, ST_NONFINITE);   // no charge for a particle without a position
+            c = -1;
+        }
         if (c >= 0) {
             load_hot(hot, c, H);
             const float x[3] = {off[p], off[n + p], off[2 * n + p]};
@@ -1450,6 +1469,10 @@ __global__ void __launch_bounds__(256) k_deposit_charge(const TetGeo* __restrict
             atomicOr(status, ST_INVAL);
             c = -1;
         }
+        if (c >= 0 && !(finite_bits(off[p]) && finite_bits(off[n + p]) && finite_bits(off[2 * n + p]))) {
+            atomicOr(status, ST_NONFINITE);   // no charge for a particle without a position
+            c = -1;
+        }
         Real v[4] = {0, 0, 0, 0};
         TetTopo T;
         if (c >= 0) {
@@ -1481,7 +1504,7 @@ int grid_for(int64_t n, int sms) {
 // the fast FP32 push: the TMA-staged persistent kernel (grid = co-resident blocks), or the
 // grid-stride kernel when the state arrays are not 16-byte aligned
 fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
-                        float* dG, float* Q, cudaStream_t s) {
+                        float* dG, float* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
     const size_t smem = (size_t)kTmaSmem;
     if (ctx->tma_blocks_per_sm == 0) {
         FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1501,7 +1524,7 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
     if (!aligned || !FP_PUSH_TMA) {   // the bulk copies need 16-byte aligned starts and lengths
         k_push_fast32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
                                                                      (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
-                                                                     ctx->d_slow_idx, ctx->d_slow_count,
+                                                                     slow_idx, slow_count,
                                                                      ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
@@ -1527,7 +1550,7 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
         if (wgrid > wtiles) wgrid = wtiles;
         k_push_ws32<BorisArgs><<<(int)wgrid, kWsThreads, kWsSmem, s>>>(
             ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt, BorisArgs{h, dt}, qw, agg, dG, Q,
-            ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+            slow_idx, slow_count, ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
@@ -1535,7 +1558,7 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
     int64_t grid = (int64_t)ctx->sm_count * ctx->tma_blocks_per_sm;
     if (grid > ntiles) grid = ntiles;
     k_push_tma32<<<(int)grid, kTmaThreads, smem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
-                                                      h, dt, qw, agg, dG, Q, ctx->d_slow_idx, ctx->d_slow_count,
+                                                      h, dt, qw, agg, dG, Q, slow_idx, slow_count,
                                                       ctx->d_status);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
@@ -1586,7 +1609,8 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
         }
         {
             PhaseTimer pt(ctx, PH_FAST, s);
-            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q, s);
+            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+                                         ctx->d_slow_idx, ctx->d_slow_count, s);
             if (sf != FP_OK) return sf;
         }
         {
@@ -1750,33 +1774,23 @@ constexpr int kStaticHead = 64;                           // int32 slots before 
 // [0] = number of queued particles, [kStaticHead ...] = their indices
 static __device__ __align__(256) int32_t g_static_queue[kStaticHead + kStaticMaxParticles];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_static_mu;
-int32_t* g_static_addr[kMaxDevices] = {nullptr};
+}  // namespace
 
-// device address of g_static_queue on the current device, looked up once per device
-fp_status static_queue(fem_pic* ctx, int32_t** out) {
-    int dev = 0;
-    FP_CUDA_TRY(ctx, cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        ctx->err = "fem_pic_push_deposit_static: device ordinal out of range";
-        return FP_EINVAL;
+// Device address of g_static_queue in the handle's context.  Called by fem_pic_create with
+// the handle's device current, so the address lives exactly as long as the handle (a context
+// rebuilt after cudaDeviceReset gets a new handle and a new lookup).  In host code the
+// array's name is only a stand-in: kernels must be given this address.
+fp_status static_queue_lookup(fem_pic* ctx) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);
+    if (e != cudaSuccess || !p) {
+        ctx->err = std::string("cudaGetSymbolAddress(g_static_queue): ") + cudaGetErrorString(e);
+        return FP_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);
-        if (e != cudaSuccess || !p) {
-            ctx->err = std::string("cudaGetSymbolAddress(g_static_queue): ") + cudaGetErrorString(e);
-            return FP_ECUDA;
-        }
-        g_static_addr[dev] = static_cast<int32_t*>(p);
-    }
-    *out = g_static_addr[dev];
+    ctx->d_static_queue = static_cast<int32_t*>(p);
     return FP_OK;
 }
 
-}  // namespace
 }  // namespace fempic
 
 extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const double* b,
@@ -1799,9 +1813,11 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
                    " particles exceed the fixed queue of " + std::to_string(kStaticMaxParticles);
         return FP_EINVAL;
     }
-    int32_t* q = nullptr;
-    fp_status st = static_queue(ctx, &q);
-    if (st != FP_OK) return st;
+    int32_t* q = ctx->d_static_queue;
+    if (!q) {
+        ctx->err = "fem_pic_push_deposit_static: the fixed queue's device address is unknown";
+        return FP_ECUDA;
+    }
     if (!(flags & FP_ACCUMULATE)) {
         FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, sizeof(float) * ctx->hc.ne, s));
         FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, sizeof(float) * ctx->hc.nn, s));
@@ -1812,16 +1828,24 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
     const double qw = p->q * p->w;
     const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
     const int32_t nt = (int32_t)ctx->hc.nt;
-    int dev = 0, sms = 152;
-    FP_CUDA_TRY(ctx, cudaGetDevice(&dev));
-    FP_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e, b, ctx->hc.nt);
-    k_push_fast32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt,
-                                                 (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
-                                                 q + kStaticHead, q, ctx->d_status);
-    k_walk32<<<sms * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off, (const float*)p->vel,
-                                     p->n, (float)dt, qw, max_cross, (float*)dG, (float*)Q, q + kStaticHead, q,
-                                     ctx->d_status);
+    {
+        PhaseTimer pt(ctx, PH_PREP, s);
+        k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e,
+                                                                                    b, ctx->hc.nt);
+    }
+    {
+        // the same kernel choice as fem_pic_push_deposit (staged pipeline for aligned state)
+        PhaseTimer pt(ctx, PH_FAST, s);
+        const fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+                                           q + kStaticHead, q, s);
+        if (sf != FP_OK) return sf;
+    }
+    {
+        PhaseTimer pt(ctx, PH_WALK, s);
+        k_walk32<<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                                   (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
+                                                   (float*)Q, q + kStaticHead, q, ctx->d_status);
+    }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }

@@ -281,3 +281,63 @@ def test_sorted_and_unsorted_push_agree():
         assert_deposit_close(dG, ref["dG"], ref["dG_abs"], TOL["fp64"], "dG")
         assert_deposit_close(Q, ref["Q"], ref["Q_abs"], TOL["fp64"], "Q")
     lib.close()
+
+
+# n = 50,000 (staged pipeline), 50,001 (grid-stride kernel) in FP32; FP64 mode
+@pytest.mark.parametrize("prec,npart", [(F.FP_FP32, 50_000), (F.FP_FP32, 50_001), (F.FP_FP64, 50_001)])
+def test_nonfinite_state_is_flagged_and_not_deposited(prec, npart):
+    """NaN and Inf written on the host into some velocities and offsets: those particles are
+    removed (cell -1) with nothing deposited, the status word reports FP_EINVAL, and the other
+    particles' steps and the deposits equal those of the same push with the bad particles
+    already absent.  The charge call drops (and reports) the particles whose offsets are not
+    finite."""
+    m, orc, lib, sp, e, b = _setup(npart=npart, speed=0.15, prec=prec)
+    ed = torch.as_tensor(e, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    bad = np.array([3, 1000, 20_001, 33_333, npart - 1])
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    d.vel[0, 3] = float("nan")
+    d.vel[1, 1000] = float("inf")
+    d.off[2, 20_001] = float("nan")
+    d.off[0, 33_333] = float("-inf")
+    d.vel[2, npart - 1] = float("-inf")
+    clean = F.Species(d.cell.clone(), d.off.clone(), d.vel.clone(), d.q, d.m, d.w)
+    clean.cell[torch.as_tensor(bad, device="cuda")] = -1
+    # the charge call needs only positions: it drops the two particles without one
+    clean_pos = F.Species(d.cell.clone(), d.off.clone(), d.vel.clone(), d.q, d.m, d.w)
+    clean_pos.cell[torch.as_tensor([20_001, 33_333], device="cuda")] = -1
+    R = lib.real
+    out = {}
+    for name, sp_, sp_q in (("bad", d, d), ("clean", clean, clean_pos)):
+        Q0 = torch.empty(lib.n_nodes, dtype=R, device="cuda")
+        lib.deposit_charge(sp_q, Q0)
+        st0 = lib.status()
+        dG = torch.empty(lib.n_edges, dtype=R, device="cuda")
+        Q = torch.empty(lib.n_nodes, dtype=R, device="cuda")
+        lib.push_deposit(ed, bd, sp_, 1.0, dG, Q)
+        st = lib.status()
+        err = F.fem_pic_last_error(lib.h)
+        out[name] = (st0, st, err, Q0.double().cpu().numpy(), dG.double().cpu().numpy(), Q.double().cpu().numpy())
+    st0, st, err, Q0, dG, Q = out["bad"]
+    assert st0 == F.FP_EINVAL                       # the charge call flags the non-finite offsets
+    assert st == F.FP_EINVAL and "not finite" in err
+    assert out["clean"][0] == F.FP_OK and out["clean"][1] == F.FP_OK
+    assert np.isfinite(Q0).all() and np.isfinite(dG).all() and np.isfinite(Q).all()
+    cb = d.cell.cpu().numpy()
+    assert (cb[bad] == -1).all()
+    assert np.array_equal(cb, clean.cell.cpu().numpy())
+    good = np.ones(npart, bool)
+    good[bad] = False
+    for a, c in ((d.off, clean.off), (d.vel, clean.vel)):
+        assert np.array_equal(a.cpu().numpy()[:, good], c.cpu().numpy()[:, good])
+    tol = 1e-12 if prec == F.FP_FP64 else TOL["fp32"]
+    for x, y in zip(out["bad"][3:], out["clean"][3:]):
+        assert np.abs(x - y).max() <= tol * np.abs(y).max()
+    if prec == F.FP_FP64:                           # and the clean step is the oracle's
+        cell0 = sp.cell.copy()
+        cell0[bad] = -1
+        ref = orc.step(cell0, sp.X, sp.V, e, b, sp.q, sp.m, sp.w, 1.0)
+        assert np.array_equal(cb, ref["cell"])
+        assert_deposit_close(dG, ref["dG"], ref["dG_abs"], TOL["fp64"], "dG")
+        assert_deposit_close(Q, ref["Q"], ref["Q_abs"], TOL["fp64"], "Q")
+    lib.close()

@@ -35,10 +35,13 @@ def _entry():
     return F, f
 
 
-def test_static_push_matches_allocating_push_on_two_calls():
+# 50,001 particles: the grid-stride kernel (n not a multiple of 4); 50,000: the staged
+# pipeline, which both entry points pick for aligned state
+@pytest.mark.parametrize("npart", [50_001, 50_000])
+def test_static_push_matches_allocating_push_on_two_calls(npart):
     F, push_static = _entry()
     m = I.cube_mesh(8, 1.0, 0.1, seed=1)
-    sp = I.uniform_species(m, 50_001, 3, 0.15, -1.0, 1.0, 0.7)
+    sp = I.uniform_species(m, npart, 3, 0.15, -1.0, 1.0, 0.7)
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP32)
     rng = np.random.default_rng(7)
     e = torch.as_tensor(rng.uniform(-0.2, 0.2, lib.n_edges), device="cuda")
@@ -73,15 +76,20 @@ def test_static_push_matches_allocating_push_on_two_calls():
 def test_static_push_rejects_more_particles_than_its_array():
     F, push_static = _entry()
     m = I.cube_mesh(2, 1.0, 0.0)
-    sp = I.uniform_species(m, 64, 1, 0.1, -1.0, 1.0)
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP32)
-    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    n = STATIC_MAX + 1
+    # arrays of the full length, every particle already absorbed (cell -1): should the size
+    # check ever let the call through, the kernels skip every particle and the assertion
+    # below fails instead of any access leaving the arrays
+    d = F.Species(torch.full((n,), -1, dtype=torch.int32, device="cuda"),
+                  torch.zeros((3, n), dtype=torch.float32, device="cuda"),
+                  torch.zeros((3, n), dtype=torch.float32, device="cuda"), -1.0, 1.0, 1.0)
     e = torch.zeros(lib.n_edges, dtype=torch.float64, device="cuda")
     b = torch.zeros(lib.n_faces, dtype=torch.float64, device="cuda")
     dG = torch.zeros(lib.n_edges, dtype=torch.float32, device="cuda")
     Q = torch.zeros(lib.n_nodes, dtype=torch.float32, device="cuda")
     pa = d.abi()
-    pa.n = STATIC_MAX + 1                           # rejected before anything is launched
+    assert pa.n == STATIC_MAX + 1                   # rejected before anything is launched
     st = push_static(lib.h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(b.data_ptr()), ctypes.byref(pa), 1e-3,
                      64, ctypes.c_void_p(dG.data_ptr()), ctypes.c_void_p(Q.data_ptr()), 0, None)
     assert st == F.FP_EINVAL
