@@ -3,9 +3,13 @@
 
 A step is one pass of the hot path over one batch of synthetic input: the periodic
 cell sort (every --sort-every steps), the particle push with gather, tet walk and
-charge-conserving deposit for every species, and the FP64 invariant residuals
-(continuity and magnetic Gauss law).  Default workload: cube 32^3 x 6 tets with
-+-10% jitter, 2M electrons, Bz = 0.1 T, dt = 0.2 gyro-periods, FP32 particle path.
+charge-conserving deposit for every species, the implicit field step (Newmark,
+Gauss-law projection, Faraday) and the FP64 invariant residuals (continuity and
+magnetic Gauss law, logged every timed step).  Default workload (the largest that fits
+one GPU): cube 96^3 x 6 tets with +-10% jitter, 50M electrons + 50M ions (mass ratio
+1836), Bx = 0.2 T, dt = 0.2 electron gyro-periods, FP32 particle path, 50 timed steps.
+The 32^3 / 2M-electron workload is measured after it in the same run (--also) and
+reported under "workloads".
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run, one independent replica per GPU (weak scaling, no collective
@@ -41,7 +45,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 3, 5])
+    ap.add_argument("--also", default="2",
+                    help="further workloads measured after the headline one in the same run (timed steps and "
+                         "per-kernel times only), comma-separated; empty: none")
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (tests only)")
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -73,9 +80,10 @@ def parse():
                     help="timed field steps with the natural (Neumann) field boundary (0: skip)")
     ap.add_argument("--adams-steps", type=int, default=20,
                     help="timed calls of the fourth-order Adams particle step (0: skip that measurement)")
-    ap.add_argument("--drift-steps", type=int, default=200,
+    ap.add_argument("--drift-steps", type=int, default=-1,
                     help="steps of the Gauss-law comparison of the projected step with the unprojected "
-                         "first-order mixed FEM and wave-equation FEM (0: skip)")
+                         "first-order mixed FEM and wave-equation FEM (0: skip; -1: 200 on the 32^3 and "
+                         "smaller workloads, 0 on the larger ones)")
     ap.add_argument("--drift-tol", type=float, default=1e-6,
                     help="second run of the Gauss-law comparison with this solver tolerance for the two "
                          "unprojected systems (the projected step keeps --tol; 0: skip)")
@@ -200,6 +208,23 @@ def adams_kernel_bytes(n_particles, sizes):
     return fast_kernel_bytes(n_particles, sizes) + 96 * n_particles
 
 
+def cg_iter_bytes(n_rows, nnz):
+    """Algorithmic DRAM bytes of one Jacobi-PCG iteration as the hot-path table states them:
+    the FP64 SpMV (8 B value + 4 B column per nonzero; per row 8 B in, 8 B out, 4 B row
+    pointer) and the PCG vector traffic (7 FP64 passes), 12 B per nonzero + 76 B per row."""
+    return 12 * nnz + 76 * n_rows
+
+
+def push_call_bytes(n_particles, n_tets):
+    """Algorithmic DRAM bytes of one push call (FP32) as the hot-path table states them: 56 B
+    of particle state per particle (28 B read, 28 B written) and about 230 B per tet (its
+    record, its e and b values and the read-modify-write of its 10 deposit targets)."""
+    return 56 * n_particles + 230 * n_tets
+
+
+L2_BYTES = 129e6
+
+
 def pcg_bytes_per_iter(n_rows, nnz, val_bytes=8):
     """Minimal DRAM bytes of one FP64 Jacobi-PCG iteration (two barriers per iteration): the
     operator once (value + column index per nonzero) and 13 passes over n-vectors
@@ -266,6 +291,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     wl = build_workload(args)
+    if args.drift_steps < 0:
+        args.drift_steps = 200 if wl.mesh.n <= 32 else 0
     lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
     sizes = lib.sizes
     dev = torch.device("cuda", local)
@@ -380,8 +407,9 @@ def run_gpu(args):
         dG.zero_()
         Qn.copy_(Q_ion)
         for k, s_ in enumerate(use):     # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}
-            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE)
-            n_k += 3              # field prep, fast push, FP64 walk of the queued particles
+            # the field records are made once per step (the first species' call)
+            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
+            n_k += 3 if k == 0 else 2     # field prep (first species), fast push, FP64 walk of the queue
         return n_k, use
 
     def enqueue_field():
@@ -546,9 +574,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     alive0 = alive()
 
-    # timed: K steps, each bracketed by events; L2 flushed between steps (outside the events)
+    # timed: K steps, each bracketed by events; L2 flushed between steps (outside the events);
+    # each step's FP64 residuals (continuity, D2 b) are kept, copied after its end event
     launches = 0
     evs = []
+    res_log = torch.zeros((args.steps, 6), dtype=torch.float64, device=dev)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -560,6 +590,7 @@ def run_gpu(args):
         a.record(stream)
         launches += step()
         z.record(stream)
+        res_log[k].copy_(res)
         evs.append((a, z))
     th1 = time.perf_counter()
     torch.cuda.synchronize()
@@ -570,6 +601,7 @@ def run_gpu(args):
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     st = lib.status()
     r = res.cpu().numpy()
+    rlog = res_log.cpu().numpy()
     alive1 = alive()
     alive_timed = 0.5 * (alive0 + alive1)          # absorption is gradual: mean of start and end
     units_all = sum_over_ranks(alive_timed * args.steps, world, dev)
@@ -618,6 +650,9 @@ def run_gpu(args):
             hc.copy_(s.cell)
             ho.copy_(s.off)
             hv.copy_(s.vel)
+        # results go to pinned buffers of their own: a device-to-host copy into the pinned pages a
+        # host-to-device copy of the same step has just read ran at less than half the rate
+        hs_out = [tuple(torch.empty_like(x).pin_memory() for x in tr) for tr in hs]
         # the step's inputs: particle state, fields E^n, E^{n-1}, b, dG^{n-1/2}, Q^n
         fin = [(e, e.cpu().pin_memory()), (b, b.cpu().pin_memory()), (E_prev, E_prev.cpu().pin_memory()),
                (dG_prev, dG_prev.cpu().pin_memory()), (Qo, Qo.cpu().pin_memory())]
@@ -626,7 +661,7 @@ def run_gpu(args):
         hE = torch.empty_like(e, device="cpu").pin_memory()
         bi = sum(x.numel() * x.element_size() for tr in hs for x in tr) + \
             sum(h_.numel() * h_.element_size() for _, h_ in fin)
-        bo = sum(x.numel() * x.element_size() for tr in hs for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
+        bo = sum(x.numel() * x.element_size() for tr in hs_out for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
             (hE.numel() * 8 if field else 0)
         # Each step: the inputs' host-to-device copies, the particle part (one CUDA graph per
         # step shape), the particle state's device-to-host copy on a second stream (it overlaps
@@ -675,7 +710,7 @@ def run_gpu(args):
             pushed.record(stream)
             copy_stream.wait_event(pushed)
             with torch.cuda.stream(copy_stream):
-                for (hc, ho, hv), s in zip(hs, use):
+                for (hc, ho, hv), s in zip(hs_out, use):
                     hc.copy_(s.cell, non_blocking=True)
                     ho.copy_(s.off, non_blocking=True)
                     hv.copy_(s.vel, non_blocking=True)
@@ -699,8 +734,8 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                "ms_per_step": e2e_ms / args.steps,
                "h2d_ms_per_step": sum(a.elapsed_time(h) for a, h in parts) / args.steps,
-               "overlap": "particle state copied back on a second stream during the field step; the step's "
-                          "particle and field parts replayed as CUDA graphs"}
+               "overlap": "particle state copied back on a second stream during the field step into pinned "
+                          "buffers of its own; the step's particle and field parts replayed as CUDA graphs"}
 
     fp64 = None if args.fp64_steps <= 0 else measure_fp64(args, F, wl, dev, flush_l2, stream)
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
@@ -841,7 +876,7 @@ def run_gpu(args):
     if rank == 0:
         value = whole_job_rate(units_all, total_ms)
         avg_push = push_call
-        abytes = algorithmic_bytes(alive_eager / len(species), sizes, 4)   # one push call (one species)
+        abytes = push_call_bytes(alive_eager / len(species), sizes["n_tets"])   # one push call (one species)
         peak, peak_kind = peak_hbm()
         achieved = abytes / (avg_push * 1e-3) / 1e9
         fast_ms, fast_n = phases.get("push_fast", (float("nan"), 1))
@@ -867,22 +902,40 @@ def run_gpu(args):
                 if cnt and t_ms > 0:
                     avg = t_ms / cnt
                     mixed = solv[k_sys] == "mixed"
-                    byt = (mixed_solve_bytes(rows, nz, its, outs, pdeg[k_sys]) if mixed else
-                           pcg_bytes_per_iter(rows, nz) * max(its, 1))
+                    # algorithmic bytes: 12 B per nonzero + 76 B per row per CG iteration, times the
+                    # solve's (inner) CG iterations
+                    byt = cg_iter_bytes(rows, nz) * max(its, 1)
+                    model = (mixed_solve_bytes(rows, nz, its, outs, pdeg[k_sys]) if mixed else
+                             pcg_bytes_per_iter(rows, nz) * max(its, 1))
+                    op_bytes = nz * 8 * 1.2          # FP32 SELL operator (value + column), ~1.2x padding
+                    on_chip = op_bytes < L2_BYTES
+                    traffic = measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph, wl.name)
                     name = ("k_pcg_mixed (" + ph.split("_")[1] + f" system, FP32 inner PCG, Chebyshev-Jacobi degree "
                             f"{pdeg[k_sys]}, FP64 residual)"
                             if mixed else "k_pcg (" + ph.split("_")[1] + " system, FP64)")
-                    cand.append((avg, {"kernel": name, "bound": "hbm",
-                                       "achieved": byt / (avg * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
-                                       "unit": "GB/s", "frac": byt / (avg * 1e-3) / 1e9 / peak,
-                                       "frac_of_nominal": byt / (avg * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
-                                       "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg,
-                                       "iterations_per_launch": its, "refinements_per_launch": outs,
-                                       "traffic": measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph,
-                                                                   wl.name),
-                                       "note": "operator and vectors stay in L2 across iterations; the kernel is "
-                                               "bound by grid barriers and gather latency, and its algorithmic "
-                                               "bytes are set against the HBM peak"}))
+                    ach = byt / (avg * 1e-3) / 1e9
+                    cand.append((avg, {
+                        "kernel": name,
+                        "bound": "latency" if on_chip else "hbm",
+                        "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                        "frac_of_nominal": ach / NOMINAL_HBM_GBS,
+                        "algorithmic_bytes_per_launch": byt,
+                        "algorithmic_bytes_rule": "12 B per nonzero + 76 B per row per CG iteration (FP64 SpMV + "
+                                                  "PCG vectors) x CG iterations per launch",
+                        "avg_launch_ms": avg, "iterations_per_launch": its, "refinements_per_launch": outs,
+                        "rows": rows, "nnz": nz,
+                        "model_bytes_per_launch": model,
+                        "model_frac": model / (avg * 1e-3) / 1e9 / peak,
+                        "model_rule": ("what the mixed solver moves: the FP32 operator (8 B per nonzero) once per "
+                                       "product, deg products per inner iteration, FP32 vector passes, FP64 "
+                                       "residuals per refinement" if mixed else "FP64 PCG, 12 B per nonzero + "
+                                       "13 FP64 vector passes per iteration"),
+                        "traffic": traffic,
+                        "traffic_frac": None if traffic is None else traffic / (avg * 1e-3) / 1e9 / peak,
+                        "note": ("the FP32 operator fits on chip (shared memory / L2): DRAM traffic is about one "
+                                 "read of it per launch and the kernel is bound by its grid barriers and gather "
+                                 "latency, not by HBM" if on_chip else
+                                 "the FP32 operator is larger than L2: every product streams it from HBM")}))
             cand.append((fast_avg, roof_push))
             roof = max(cand, key=lambda c: c[0])[1]
         out = {
@@ -907,6 +960,7 @@ def run_gpu(args):
                                    "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                    "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                                    "algorithmic_bytes_per_launch": abytes,
+                                   "algorithmic_bytes_rule": "56 B per particle + 230 B per tet",
                                    "avg_call_ms": avg_push},
             "timing": ("timed steps replay one CUDA graph per step shape" if use_graphs else "eager launches") +
                       "; per-kernel times from an eager pass of the same steps with the library's CUDA-event profiler",
@@ -936,7 +990,15 @@ def run_gpu(args):
             "eager_ms_per_step": statistics.mean(push_ms),
             "residuals": {"continuity_interior_max": float(r[4]), "continuity_interior_scale": float(r[5]),
                           "continuity_all_nodes_max": float(r[0]), "continuity_all_nodes_scale": float(r[1]),
-                          "divB_max": float(r[2]), "divB_scale": float(r[3])},
+                          "divB_max": float(r[2]), "divB_scale": float(r[3]),
+                          "per_step": {
+                              "what": "every timed step: max|D0^T dG - (Q^{n+1} - Q^n)| over interior nodes and "
+                                      "max|D2 b| over tets, each over its scale (FP64 residual kernel)",
+                              "continuity_interior_rel_max": float(np.max(rlog[:, 4] / np.maximum(rlog[:, 5], 1e-300))),
+                              "divB_rel_max": float(np.max(rlog[:, 2] / np.maximum(rlog[:, 3], 1e-300))),
+                              "continuity_interior_rel": [float(f"{x:.3e}") for x in
+                                                          rlog[:, 4] / np.maximum(rlog[:, 5], 1e-300)],
+                              "divB_rel": [float(f"{x:.3e}") for x in rlog[:, 2] / np.maximum(rlog[:, 3], 1e-300)]}},
             "status": int(st),
             "clocks": clocks,
             "gpu_launches": launches,
@@ -970,8 +1032,9 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
         nonlocal step
         dG.zero_()
         Qn.zero_()
-        for s_, h_ in zip(sps, hist):
-            lib.push_deposit_adams(e, b, s_, h_, step, dt, dG, Qn, flags=F.FP_ACCUMULATE)
+        for k, (s_, h_) in enumerate(zip(sps, hist)):
+            lib.push_deposit_adams(e, b, s_, h_, step, dt, dG, Qn,
+                                   flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
         step += 1
 
     for _ in range(4):
@@ -1035,8 +1098,8 @@ def measure_fp64(args, F, wl, dev, flush_l2, stream):
     def call():
         dG.zero_()
         Q.zero_()
-        for s_ in sps:
-            lib.push_deposit(e, b, s_, wl.dt, dG, Q, flags=F.FP_ACCUMULATE)
+        for k, s_ in enumerate(sps):
+            lib.push_deposit(e, b, s_, wl.dt, dG, Q, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
     for _ in range(3):
         call()
     torch.cuda.synchronize()
@@ -1073,6 +1136,21 @@ def measure_fp64(args, F, wl, dev, flush_l2, stream):
             "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind}
 
 
+def oracle_sample_size(orc, sp, e, b, dt, threads, step_s):
+    """Particles per oracle call such that one call takes about step_s seconds: the sample grows
+    by 4x from 20,000 until a call takes at least a quarter of that (each call also pays a
+    fixed cost per mesh entity, its thread-private deposit arrays), then scales linearly."""
+    n = min(sp.n, 20000)
+    while True:
+        t = time.perf_counter()
+        orc.step(sp.cell[:n], sp.X[:n], sp.V[:n], e, b, sp.q, sp.m, sp.w, dt, nthreads=threads)
+        el = time.perf_counter() - t
+        if el >= 0.25 * step_s or n >= sp.n:
+            break
+        n = min(sp.n, 4 * n)
+    return int(min(sp.n, max(1000, n * step_s / max(el, 1e-9))))
+
+
 def cpu_baseline(args, wl, budget_s):
     """The FP64 oracle as it stands, on the host cores, over a bounded sample of the workload."""
     import oracle as O
@@ -1080,12 +1158,7 @@ def cpu_baseline(args, wl, budget_s):
     e, b = orc.project_uniform((0.0, 0.0, 0.0), wl.B0)
     sp = wl.species[0]
     threads = O.nproc_threads()
-    n = min(sp.n, 20000)
-    t = time.perf_counter()
-    orc.step(sp.cell[:n], sp.X[:n], sp.V[:n], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
-    dt1 = time.perf_counter() - t
-    rate = n / max(dt1, 1e-9)
-    n2 = int(min(sp.n, max(n, rate * budget_s)))
+    n2 = oracle_sample_size(orc, sp, e, b, wl.dt, threads, 0.25 * budget_s)
     done, el = 0, 0.0
     while el < 0.5 * budget_s or done == 0:
         t = time.perf_counter()
@@ -1095,7 +1168,10 @@ def cpu_baseline(args, wl, budget_s):
     # the field step of the oracle (scipy: direct solve of the Gauss-law projection, CG on the
     # Newmark system to 1e-13), one step on the same mesh with a continuity-respecting current
     field = None
-    if not args.no_field and not args.no_cpu_field:
+    if wl.mesh.n > 32 and not args.no_field:
+        field = {"skipped": "the oracle's scipy field step is timed on the 32^3 and smaller meshes only (at this "
+                            "size one step takes minutes on one host thread)"}
+    elif not args.no_field and not args.no_cpu_field:
         import numpy as np
         from oracle import fields as OF
         t = time.perf_counter()
@@ -1135,13 +1211,9 @@ def run_reference(args):
     e, b = orc.project_uniform((0.0, 0.0, 0.0), wl.B0)
     threads = O.nproc_threads()
     sp = wl.species[0]
-    n = min(sp.n, 20000)
-    t = time.perf_counter()
-    orc.step(sp.cell[:n], sp.X[:n], sp.V[:n], e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
-    rate = n / max(time.perf_counter() - t, 1e-9)
     # each step is a bounded sample sized so the whole run stays within a few minutes
     per_step_s = min(4.0, 150.0 / max(1, args.steps + args.warmup))
-    ns = int(min(sp.n, max(1000, rate * per_step_s)))
+    ns = oracle_sample_size(orc, sp, e, b, wl.dt, threads, per_step_s)
     cell, X, V = sp.cell[:ns].copy(), sp.X[:ns].copy(), sp.V[:ns].copy()
     for _ in range(args.warmup):
         r = orc.step(cell, X, V, e, b, sp.q, sp.m, sp.w, wl.dt, nthreads=threads)
@@ -1164,6 +1236,36 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_also(args):
+    """The further workloads of --also: the same timed PIC steps (and per-kernel pass), without
+    the side measurements; returns {workload name: its main numbers}."""
+    import copy
+    import gc
+    import torch
+    res = {}
+    for tok in [x for x in args.also.split(",") if x.strip()]:
+        idx = int(tok)
+        if idx == args.workload:
+            continue
+        a = copy.copy(args)
+        a.workload, a.also, a.learned = idx, "", "off"
+        a.no_e2e, a.fp64_steps, a.adams_steps, a.neumann_steps, a.drift_steps = True, 0, 0, 0, 0
+        a.steps = max(args.steps, 20)
+        o, wl2 = run_gpu(a)
+        gc.collect()
+        torch.cuda.empty_cache()
+        if o is None:
+            continue
+        fs = o.get("field_solve") or {}
+        res[wl2.name] = {k: o[k] for k in ("value", "unit", "ms_per_step", "steps", "roofline", "roofline_push",
+                                           "roofline_push_call", "phases_ms_per_step", "residuals", "clocks",
+                                           "gpu_launches", "status")}
+        res[wl2.name]["config"] = o["config"]
+        res[wl2.name]["field_solve"] = {k: fs.get(k) for k in ("ms_per_step", "newmark_iters_mean",
+                                                                 "gauss_iters_mean", "max_rel_res")}
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1171,7 +1273,10 @@ def main():
         return
     out, wl = run_gpu(args)
     rank, world, _ = dist_env()
+    also = run_also(args) if world == 1 and args.also else None
     if rank == 0 and out is not None:
+        if also:
+            out["workloads"] = also
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args, wl, args.cpu_seconds)
         print(json.dumps(out), flush=True)

@@ -61,7 +61,9 @@ enum { FP_FP64 = 0, FP_FP32 = 1 };
 /* fem_pic_push_deposit flags */
 enum {
     FP_ACCUMULATE = 1, /* add into dG and Q instead of overwriting them */
-    FP_NO_AGGREGATE = 2 /* one global atomic per contribution (no warp aggregation) */
+    FP_NO_AGGREGATE = 2, /* one global atomic per contribution (no warp aggregation) */
+    FP_SAME_FIELDS = 4 /* e and b are those of this handle's previous push call, unchanged since:
+                          its per-tet field records are reused (e.g. the second species of a step) */
 };
 
 typedef struct {

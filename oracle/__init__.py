@@ -60,7 +60,7 @@ def lib():
             i = ctypes.c_int
             _lib.oracle_step.restype = i64
             _lib.oracle_step.argtypes = [i64, i64, P, P, P, P, P, P, P, i64, P, P, P, d, d, d, d, i, i, P,
-                                         P, P, P, P, P, i]
+                                         P, P, P, P, P, i, P, P]
             _lib.oracle_gather.restype = None
             _lib.oracle_gather.argtypes = [P, P, P, P, P, P, i64, P, P, P, P]
             _lib.oracle_bary.restype = None
@@ -131,8 +131,10 @@ class Oracle:
                             cell.shape[0], _p(cell), _p(X), _p(E), _p(B))
         return E, B
 
-    def step(self, cell, X, V, e, b, q, m, w, dt, max_cross=64, Xend=None, nthreads=0):
-        """One particle step (push if Xend is None, else walk to Xend).  Returns a dict."""
+    def step(self, cell, X, V, e, b, q, m, w, dt, max_cross=64, Xend=None, nthreads=0, touch=False):
+        """One particle step (push if Xend is None, else walk to Xend).  Returns a dict; with
+        touch=True it also holds dG_touch / Q_touch, the sum of |q w| over the pieces / end
+        points that touch each edge / node."""
         cell = np.array(cell, dtype=np.int32, order="C", copy=True)
         X = np.array(X, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
         V = np.array(V, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
@@ -144,14 +146,19 @@ class Oracle:
         Q = np.zeros(self.n_nodes)
         Qa = np.zeros(self.n_nodes)
         ncross = np.zeros(n, dtype=np.int32)
+        Gt = np.zeros(self.n_edges) if touch else None
+        Qt = np.zeros(self.n_nodes) if touch else None
         push = 1 if Xend is None else 0
         Xe = _f64(Xend, (-1, 3)) if Xend is not None else np.zeros((1, 3))
         nb = lib().oracle_step(self.n_edges, self.n_nodes, _p(self.xyz), _p(self.tv32), _p(self.te32),
                                _p(self.tf32), _p(self.nb32), _p(e), _p(b), n, _p(cell), _p(X), _p(V),
                                float(q), float(m), float(w), float(dt), int(max_cross), push, _p(Xe),
-                               _p(dG), _p(dGa), _p(Q), _p(Qa), _p(ncross), int(nthreads))
-        return dict(cell=cell, X=X, V=V, dG=dG, dG_abs=dGa, Q=Q, Q_abs=Qa, ncross=ncross,
-                    n_bound=int(nb))
+                               _p(dG), _p(dGa), _p(Q), _p(Qa), _p(ncross), int(nthreads),
+                               _p(Gt) if touch else None, _p(Qt) if touch else None)
+        out = dict(cell=cell, X=X, V=V, dG=dG, dG_abs=dGa, Q=Q, Q_abs=Qa, ncross=ncross, n_bound=int(nb))
+        if touch:
+            out["dG_touch"], out["Q_touch"] = Gt, Qt
+        return out
 
     def walk_trace(self, cell, Xa, Xb, qw=1.0, max_cross=64, cap=256):
         """The pieces of one walk: (cells [k], piece start points [k,3], stop point, end cell, dG, Q)."""

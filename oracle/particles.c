@@ -162,6 +162,10 @@ typedef struct {
     double* Gabs;
     double* Q;
     double* Qabs;
+    /* optional (NULL: not kept): sum of |q w| over the pieces / end points touching each entry,
+     * the scale of the rounding a deposit computed in a given precision can carry there */
+    double* Gtouch;
+    double* Qtouch;
 } acc_t;
 
 /* G_e += qw * int_P^R W1_e . dr on a straight piece inside tet t (2-pt Gauss-Legendre) */
@@ -185,6 +189,7 @@ static void deposit_segment(const mesh_t* M, int t, const double P[3], const dou
         int64_t ed = M->te[6 * (int64_t)t + k];
         A->G[ed] += qw * val[k];
         A->Gabs[ed] += fabs(qw * val[k]);
+        if (A->Gtouch) A->Gtouch[ed] += fabs(qw);
     }
 }
 
@@ -195,6 +200,7 @@ static void deposit_charge(const mesh_t* M, int t, const double X[3], double qw,
         int64_t n = M->tv[4 * (int64_t)t + k];
         A->Q[n] += qw * lam[k];
         A->Qabs[n] += fabs(qw * lam[k]);
+        if (A->Qtouch) A->Qtouch[n] += fabs(qw);
     }
 }
 
@@ -288,20 +294,21 @@ static int walk(const mesh_t* M, int t, const double Xa[3], const double Xb[3], 
 
 typedef struct {
     int64_t ne, nn;
-    double *G, *Gabs, *Q, *Qabs;
+    double *G, *Gabs, *Q, *Qabs, *Gt, *Qt;
 } thr_acc;
 
 /*
  * One step for np particles of one species.  push=1: gather at X, Boris, X_b = X + dt v.
  * push=0: only walk from X to the given Xend (velocities untouched).
- * cell/X/V are updated in place; dG, dGabs, Q, Qabs are accumulated.
+ * cell/X/V are updated in place; dG, dGabs, Q, Qabs are accumulated (dGtouch, Qtouch too
+ * when not NULL).
  * Returns the number of particles that hit the crossing bound.
  */
 int64_t oracle_step(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv, const int32_t* te,
                     const int32_t* tf, const int32_t* nb, const double* e, const double* b, int64_t np,
                     int32_t* cell, double* X, double* V, double q, double m, double w, double dt,
                     int max_cross, int push, const double* Xend, double* dG, double* dGabs, double* Q,
-                    double* Qabs, int32_t* ncross, int nthreads) {
+                    double* Qabs, int32_t* ncross, int nthreads, double* dGtouch, double* Qtouch) {
     mesh_t M = {xyz, tv, te, tf, nb, e, b};
     double qw = q * w;
     int64_t nbound = 0;
@@ -316,6 +323,8 @@ int64_t oracle_step(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv
         acc[i].Gabs = (double*)calloc((size_t)ne, sizeof(double));
         acc[i].Q = (double*)calloc((size_t)nn, sizeof(double));
         acc[i].Qabs = (double*)calloc((size_t)nn, sizeof(double));
+        acc[i].Gt = dGtouch ? (double*)calloc((size_t)ne, sizeof(double)) : NULL;
+        acc[i].Qt = Qtouch ? (double*)calloc((size_t)nn, sizeof(double)) : NULL;
     }
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(T) schedule(static) reduction(+ : nbound)
@@ -325,7 +334,7 @@ int64_t oracle_step(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        acc_t A = {acc[tid].G, acc[tid].Gabs, acc[tid].Q, acc[tid].Qabs};
+        acc_t A = {acc[tid].G, acc[tid].Gabs, acc[tid].Q, acc[tid].Qabs, acc[tid].Gt, acc[tid].Qt};
         int t = cell[p];
         if (t < 0) {
             if (ncross) ncross[p] = 0;
@@ -355,15 +364,19 @@ int64_t oracle_step(int64_t ne, int64_t nn, const double* xyz, const int32_t* tv
         for (int64_t k = 0; k < ne; ++k) {
             dG[k] += acc[i].G[k];
             dGabs[k] += acc[i].Gabs[k];
+            if (dGtouch) dGtouch[k] += acc[i].Gt[k];
         }
         for (int64_t k = 0; k < nn; ++k) {
             Q[k] += acc[i].Q[k];
             Qabs[k] += acc[i].Qabs[k];
+            if (Qtouch) Qtouch[k] += acc[i].Qt[k];
         }
         free(acc[i].G);
         free(acc[i].Gabs);
         free(acc[i].Q);
         free(acc[i].Qabs);
+        free(acc[i].Gt);
+        free(acc[i].Qt);
     }
     free(acc);
     return nbound;
@@ -393,7 +406,7 @@ void oracle_boris(int64_t np, double* V, const double* E, const double* B, doubl
 void oracle_charge(const double* xyz, const int32_t* tv, int64_t nn, int64_t np, const int32_t* cell,
                    const double* X, double qw, double* Q, double* Qabs) {
     mesh_t M = {xyz, tv, NULL, NULL, NULL, NULL, NULL};
-    acc_t A = {NULL, NULL, Q, Qabs};
+    acc_t A = {NULL, NULL, Q, Qabs, NULL, NULL};
     (void)nn;
     for (int64_t p = 0; p < np; ++p)
         if (cell[p] >= 0) deposit_charge(&M, cell[p], X + 3 * p, qw, &A);
@@ -411,7 +424,7 @@ int oracle_walk_trace(int64_t ne, int64_t nn, const double* xyz, const int32_t* 
                       int max_cross, int cap, int32_t* cells, double* start, double* stop, int32_t* end_cell,
                       double* dG, double* dGabs, double* Q, double* Qabs) {
     mesh_t M = {xyz, tv, te, tf, nb, NULL, NULL};
-    acc_t A = {dG, dGabs, Q, Qabs};
+    acc_t A = {dG, dGabs, Q, Qabs, NULL, NULL};
     trace_t tr = {cells, start, cap, 0};
     int nc = 0, hit = 0;
     (void)ne;

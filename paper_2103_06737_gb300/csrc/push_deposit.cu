@@ -1603,7 +1603,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
     if (f32) {
         const fp_status sq = slow_queue(ctx, p->n, "fem_pic_push_deposit", s);
         if (sq != FP_OK) return sq;
-        {
+        if (!(flags & FP_SAME_FIELDS)) {
             PhaseTimer pt(ctx, PH_PREP, s);
             k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e, b, ctx->hc.nt);
         }
@@ -1620,7 +1620,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                                              (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
         }
     } else {
-        {
+        if (!(flags & FP_SAME_FIELDS)) {
             PhaseTimer pt(ctx, PH_PREP, s);
             k_field_prep64<<<grid_for(ctx->hc.nt, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b,
                                                                                ctx->hc.nt, ctx->d_field64);
@@ -1664,7 +1664,7 @@ fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, cons
         A.dt = (float)dt, A.qm = (float)qm;
         const fp_status sq = slow_queue(ctx, p->n, "fem_pic_push_deposit_adams", s);
         if (sq != FP_OK) return sq;
-        {
+        if (!(flags & FP_SAME_FIELDS)) {
             PhaseTimer pt(ctx, PH_PREP, s);
             k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces,
                                                                                         e, b, ctx->hc.nt);
@@ -1715,7 +1715,7 @@ fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, cons
         for (int j = 0; j < 3; ++j) A.slot[j] = slot[j];
         for (int j = 0; j < 4; ++j) A.beta[j] = kBeta[order - 1][j];
         A.dt = dt, A.qm = qm;
-        {
+        if (!(flags & FP_SAME_FIELDS)) {
             PhaseTimer pt(ctx, PH_PREP, s);
             k_field_prep64<<<grid_for(ctx->hc.nt, ctx->sm_count), 256, 0, s>>>(ctx->d_geo, ctx->d_topo, e, b,
                                                                                ctx->hc.nt, ctx->d_field64);
@@ -1828,7 +1828,7 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
     const double qw = p->q * p->w;
     const int agg = (flags & FP_NO_AGGREGATE) ? 0 : 1;
     const int32_t nt = (int32_t)ctx->hc.nt;
-    {
+    if (!(flags & FP_SAME_FIELDS)) {
         PhaseTimer pt(ctx, PH_PREP, s);
         k_field_prep32<<<grid_for((ctx->hc.nt + 1) / 2, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, ctx->d_tet_faces, e,
                                                                                     b, ctx->hc.nt);

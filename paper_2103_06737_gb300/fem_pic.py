@@ -19,7 +19,7 @@ from . import build as _build
 
 FP_OK, FP_EINVAL, FP_ECUDA, FP_EWALK, FP_ENOCONV, FP_EGEOM = range(6)
 FP_FP64, FP_FP32 = 0, 1
-FP_ACCUMULATE, FP_NO_AGGREGATE = 1, 2
+FP_ACCUMULATE, FP_NO_AGGREGATE, FP_SAME_FIELDS = 1, 2, 4
 _STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ECUDA", 3: "FP_EWALK", 4: "FP_ENOCONV", 5: "FP_EGEOM"}
 
 _lock = threading.Lock()

@@ -13,6 +13,7 @@ noise of order eps there.
 import numpy as np
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
+EPS = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
 
 
 def fp32_continuity_tol(n_particles, n_nodes, n_edges):
@@ -26,11 +27,21 @@ def fp32_continuity_tol(n_particles, n_nodes, n_edges):
     return max(1e-6, 8.0 * 2.0 ** -24 * k ** 0.5)
 
 
-def assert_deposit_close(got, ref, ref_abs, tol, what="dG"):
+def assert_deposit_close(got, ref, ref_abs, tol, what="dG", touch=None, eps=None):
+    """Per-entry and max-norm deposit bound.  With touch (the oracle's sum of |q w| over the
+    pieces / end points touching each entry) and eps (the unit roundoff of the precision the
+    deposits were computed in) the per-entry floor is 4 eps touch instead of 64 eps_64 max|ref|:
+    barycentric coordinates in [0, 1] carry an absolute rounding of order eps, so an entry
+    formed from near-zero contributions (a particle near the opposite face, a start point that
+    rounding put a hair outside its tet and that the walk first moves onto the face) is held
+    to that absolute scale per touching particle, not to its own tiny value."""
     got = np.asarray(got, dtype=np.float64)
     err = np.abs(got - ref)
     scale = np.maximum(ref_abs, np.finfo(np.float64).tiny)
-    floor = 64.0 * np.finfo(np.float64).eps * np.abs(ref).max()
+    if touch is not None:
+        floor = 4.0 * eps * np.asarray(touch)
+    else:
+        floor = 64.0 * np.finfo(np.float64).eps * np.abs(ref).max()
     bad = err > tol * scale + floor + 1e-300
     assert not bad.any(), (f"{what}: {bad.sum()} entries beyond {tol} * sum|contrib| "
                            f"(worst ratio {np.max(err / scale):.3e})")
