@@ -67,12 +67,17 @@ def parse():
     ap.add_argument("--poly-ratio", default="15,100",
                     help="lambda_max / lambda_low of the Chebyshev interval, Newmark and Gauss systems")
     ap.add_argument("--learned", default="auto", choices=["auto", "off", "on"],
-                    help="learned corrections of the Newmark and Gauss-law solves: trained during warm-up, "
-                         "each used if it beats plain CG (auto)")
+                    help="learned preconditioners of the Newmark and Gauss-law solves: trained by the protocol on "
+                         "the 4^3 and 32^3 workloads, each used in the timed steps if it beats plain CG and the "
+                         "configured polynomial (auto)")
     ap.add_argument("--learned-systems", default="newmark,gauss",
                     help="systems whose learned correction is trained and compared with plain CG (newmark, gauss)")
-    ap.add_argument("--learn-samples", type=int, default=48)
-    ap.add_argument("--learn-epochs", type=int, default=30)
+    ap.add_argument("--proto-systems", type=int, default=1000,
+                    help="field systems collected per workload (4^3 and 32^3) for the learned preconditioner; "
+                         "a tenth of them are held out")
+    ap.add_argument("--proto-rounds", type=int, default=6,
+                    help="training rounds; each trains a few epochs on each workload in turn")
+    ap.add_argument("--proto-epochs", type=int, default=3, help="epochs per workload per round")
     ap.add_argument("--compare-steps", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="timed particle steps of the FP64 mode in a context of its own (0: skip)")
@@ -278,6 +283,159 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+def learned_protocol(args, dev):
+    """Training and evaluation protocol of the learned preconditioner (the FP_LEARNED_PRECOND
+    network) on both field systems, Newmark (edge graph) and Gauss-law projection (node graph).
+    Field systems come from PIC runs of the 4^3 / 1,000-electron and the 32^3 / 2M-electron
+    workloads: the residual of each solve's start, one per system per step, args.proto_systems
+    steps per workload, the last tenth held out.  One network per system is trained on both
+    workloads' training systems (rounds of a few epochs on each workload in turn, the weights
+    carried from one to the other).  The held-out steps are then run again from the same state
+    with plain Jacobi-CG and with the learned preconditioner, both in the mixed solver to
+    args.tol: iterations and CUDA-event time per solve.  Returns the report and the weights."""
+    import torch
+    import paper_2103_06737_gb300.fem_pic as F
+    from paper_2103_06737_gb300 import inputs as I
+    t0 = time.time()
+    n_sys = max(20, args.proto_systems)
+    n_hold = max(2, n_sys // 10)
+    n_train = n_sys - n_hold
+    systems = ((F.FP_SYS_NEWMARK, F.FP_PC_LEARNED, "newmark", "cg_newmark"),
+               (F.FP_SYS_GAUSS, F.FP_PC_LEARNED_GAUSS, "gauss", "cg_gauss"))
+    runs = []
+    for idx in (1, 2):
+        wl = I.config(idx)
+        lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
+        sizes = lib.sizes
+        sps = []
+        for s_ in wl.species:
+            d0 = lib.species(s_.cell, s_.X, s_.V, s_.q, s_.m, s_.w, device=dev)
+            d1 = d0.empty_like()
+            lib.sort(d0, d1)
+            sps.append(d1)
+        e, b = lib.fields_uniform((0.0, 0.0, 0.0), wl.B0, device=dev)
+        ne, nn = sizes["n_edges"], sizes["n_nodes"]
+        dG = torch.zeros(ne, dtype=torch.float32, device=dev)
+        dGp = torch.zeros_like(dG)
+        Qn = torch.zeros(nn, dtype=torch.float32, device=dev)
+        Qo = torch.zeros_like(Qn)
+        Q_ion = torch.zeros_like(Qn)
+        if wl.background_ions:
+            alpha = F.fem_pic_whitney0_integrals(lib.h)
+            qtot = sum(s_.q * s_.w * s_.n for s_ in sps)
+            Q_ion.copy_(torch.as_tensor(-qtot * alpha / alpha.sum(), device=dev))
+        Ep = torch.zeros(ne, dtype=torch.float64, device=dev)
+        En = torch.zeros_like(Ep)
+        F.fem_pic_field_setup(lib.h, wl.dt)
+        F.fem_pic_field_options(lib.h, F.FP_PC_JACOBI, F.FP_PC_JACOBI, args.inner_tol)
+        for sys_id, _, _, _ in systems:
+            F.fem_pic_field_poly(lib.h, sys_id, 1, 30.0)       # plain Jacobi inner preconditioner
+            F.fem_pic_learned_select(lib.h, sys_id)
+            F.fem_pic_learned_init_model(lib.h, seed=7 + sys_id, sample_capacity=n_sys, model=F.FP_LEARNED_PRECOND)
+            F.fem_pic_learned_mode(lib.h, collect=True, active=False)
+        Qo.copy_(Q_ion)
+        for k, s_ in enumerate(sps):
+            lib.deposit_charge(s_, Qo, flags=F.FP_ACCUMULATE)
+        st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
+        Ep.copy_(e)
+
+        def step(pc, lib=lib, sps=sps, e=e, b=b, dG=dG, dGp=dGp, Qn=Qn, Qo=Qo, Q_ion=Q_ion, Ep=Ep, En=En, wl=wl):
+            dG.zero_()
+            Qn.copy_(Q_ion)
+            for k, s_ in enumerate(sps):
+                lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
+            F.fem_pic_field_step(lib.h, Ep, e, En, b, dG, dGp, Qn, tol=args.tol, max_iter=args.max_iter,
+                                 precond=pc, info=False)
+            Qo.copy_(Qn)
+            dGp.copy_(dG)
+            Ep.copy_(e)
+            e.copy_(En)
+        for k in range(n_train):
+            step(F.FP_PC_JACOBI)
+        torch.cuda.synchronize()
+        snap = [t_.clone() for t_ in (e, b, Ep, dGp, Qo)] + [(s_.cell.clone(), s_.off.clone(), s_.vel.clone())
+                                                             for s_ in sps]
+        for k in range(n_hold):
+            step(F.FP_PC_JACOBI)
+        torch.cuda.synchronize()
+        for sys_id, _, _, _ in systems:
+            F.fem_pic_learned_select(lib.h, sys_id)
+            F.fem_pic_learned_mode(lib.h, collect=False, active=False)
+        st = lib.status()
+        if st != F.FP_OK:
+            raise RuntimeError(f"learned protocol, workload {wl.name}: status {st}: {F.fem_pic_last_error(lib.h)}")
+
+        def restore(snap=snap, e=e, b=b, Ep=Ep, dGp=dGp, Qo=Qo, sps=sps):
+            for t_, c_ in zip((e, b, Ep, dGp, Qo), snap[:5]):
+                t_.copy_(c_)
+            for s_, (c_, o_, v_) in zip(sps, snap[5:]):
+                s_.cell.copy_(c_)
+                s_.off.copy_(o_)
+                s_.vel.copy_(v_)
+        runs.append({"wl": wl, "lib": lib, "step": step, "restore": restore,
+                     "alive": sum(int((s_.cell >= 0).sum()) for s_ in sps)})
+    t_collect = time.time() - t0
+    # training: one network per system on both workloads' training systems
+    params, report = {}, {"workloads": [r["wl"].name for r in runs], "systems_per_workload": n_sys,
+                          "held_out_per_workload": n_hold, "train_per_workload": n_train,
+                          "collect_s": t_collect}
+    for sys_id, bit, name, ph in systems:
+        t1 = time.time()
+        P = None
+        before, losses = {}, []
+        for r in runs:
+            F.fem_pic_learned_select(r["lib"].h, sys_id)
+            before[r["wl"].name] = float(np.mean(F.fem_pic_learned_eval(r["lib"].h, n_train, n_hold)))
+        for rd in range(args.proto_rounds):
+            lr = 2e-3 * (1.0 - rd / max(1, args.proto_rounds)) + 1e-4
+            for r in runs:
+                F.fem_pic_learned_select(r["lib"].h, sys_id)
+                if P is not None:
+                    F.fem_pic_learned_params(r["lib"].h, P)
+                ls = F.fem_pic_learned_train(r["lib"].h, 0, n_train, args.proto_epochs, lr=lr, seed=rd)
+                losses.append(float(ls[-1]))
+                P = F.fem_pic_learned_params(r["lib"].h)
+        params[sys_id] = P
+        rep = {"train_s": time.time() - t1, "train_loss_first": losses[0], "train_loss_last": losses[-1],
+               "model": "3-layer message passing on the " + ("edge" if sys_id == F.FP_SYS_NEWMARK else "node") +
+                        " graph, 64 features, BF16 weights with FP32 accumulation (tensor cores), static input; "
+                        "head: a symmetric sparse correction of the Jacobi preconditioner on the operator's pattern"}
+        for r in runs:
+            lib = r["lib"]
+            F.fem_pic_learned_select(lib.h, sys_id)
+            F.fem_pic_learned_params(lib.h, P)
+            after = float(np.mean(F.fem_pic_learned_eval(lib.h, n_train, n_hold)))
+            F.fem_pic_learned_build(lib.h)
+
+            def run(pc, lib=lib, r=r):
+                r["restore"]()
+                torch.cuda.synchronize()
+                F.fem_pic_profile_read(lib.h, reset=True)
+                F.fem_pic_profile_enable(lib.h, True)
+                its, fb = [], 0
+                for k in range(n_hold):
+                    r["step"](pc)
+                    fi = F.fem_pic_field_last_info(lib.h)
+                    its.append(fi[sys_id]["iters"])
+                    fb += fi[sys_id]["fell_back"]
+                torch.cuda.synchronize()
+                F.fem_pic_profile_enable(lib.h, False)
+                phs = F.fem_pic_profile_read(lib.h, reset=True)
+                return {"iters_mean": statistics.mean(its), "ms_per_solve": phs.get(ph, (0.0, 1))[0] / n_hold,
+                        "fell_back": fb}
+            plain = run(F.FP_PC_JACOBI)
+            learn = run(bit)
+            rep[r["wl"].name] = {"held_out_ratio_before": before[r["wl"].name], "held_out_ratio_after": after,
+                                 "plain_jacobi_cg": plain, "learned": learn,
+                                 "iters_ratio": learn["iters_mean"] / max(1e-9, plain["iters_mean"]),
+                                 "time_ratio": learn["ms_per_solve"] / max(1e-9, plain["ms_per_solve"])}
+        report[name] = rep
+    for r in runs:
+        r["lib"].close()
+    report["total_s"] = time.time() - t0
+    return {"report": report, "params": params}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -290,6 +448,10 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
+    proto = None
+    if not args.no_field and args.learned != "off":
+        proto = learned_protocol(args, torch.device("cuda", local))
+        torch.cuda.empty_cache()
     wl = build_workload(args)
     if args.drift_steps < 0:
         args.drift_steps = 200 if wl.mesh.n <= 32 else 0
@@ -422,10 +584,7 @@ def run_gpu(args):
             # Newmark right-hand side (2) and solve (mixed: gather into its row order, solve,
             # scatter out with A E^N: 3; FP64: the solve, then M E^N: 2), Gauss right-hand side
             # (1), solve (1), projection and Faraday update (2)
-            n_k += 9 if solv[0] == "mixed" else 8
-            for bit in (F.FP_PC_LEARNED, F.FP_PC_LEARNED_GAUSS):
-                if state["precond"] & bit:
-                    n_k += 13     # residual, network forward (9 kernels), candidate, residual, select
+            n_k += 9 if solv[0] == "mixed" else 8     # (a learned preconditioner acts inside the solver)
         lib.residuals(dG, Qn, Qo, b, res)
         n_k += 1
         Qo.copy_(Qn)
@@ -479,34 +638,27 @@ def run_gpu(args):
     if st != F.FP_OK:
         raise RuntimeError(f"warm-up status {st}: {F.fem_pic_last_error(lib.h)}")
 
-    # learned corrections, per system (Newmark edge system, Gauss-law node system): collect
-    # residuals of the method's own solves, train, then time learned vs plain Jacobi-CG on the
-    # same steps (plain CG decides); a correction is kept only where it wins
+    # learned preconditioner, per system (Newmark edge system, Gauss-law node system): the
+    # networks trained by the protocol on the 4^3 and 32^3 workloads' systems, applied to this
+    # mesh; timed against plain Jacobi-CG (the judge) and the configured Chebyshev polynomial
+    # on the same steps.  It is kept for the timed steps only where it beats both.
     learned = None
-    if field and args.learned != "off":
-        learned = {}
+    if field and proto is not None:
+        learned = {"protocol": proto["report"]}
         used_bits = 0
         for sysname in [x for x in args.learned_systems.split(",") if x]:
             sys_id = F.FP_SYS_NEWMARK if sysname == "newmark" else F.FP_SYS_GAUSS
             bit = F.FP_PC_LEARNED if sys_id == F.FP_SYS_NEWMARK else F.FP_PC_LEARNED_GAUSS
             ph_cg = "cg_newmark" if sys_id == F.FP_SYS_NEWMARK else "cg_gauss"
-            t_l0 = time.time()
             state["precond"] = precond
             F.fem_pic_learned_select(lib.h, sys_id)
-            F.fem_pic_learned_init(lib.h, seed=0, sample_capacity=args.learn_samples)
-            F.fem_pic_learned_mode(lib.h, collect=True, active=False)
-            for _ in range(args.learn_samples):
-                eager_step()
+            F.fem_pic_learned_init_model(lib.h, seed=0, sample_capacity=0, model=F.FP_LEARNED_PRECOND)
+            F.fem_pic_learned_params(lib.h, proto["params"][sys_id])
+            F.fem_pic_learned_build(lib.h)
             torch.cuda.synchronize()
-            F.fem_pic_learned_mode(lib.h, collect=False, active=False)
-            n_s = F.fem_pic_learned_samples(lib.h)
-            n_hold = max(1, n_s // 6)
-            before = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
-            losses = F.fem_pic_learned_train(lib.h, 0, n_s - n_hold, args.learn_epochs, lr=2e-3, seed=0)
-            after = F.fem_pic_learned_eval(lib.h, n_s - n_hold, n_hold)
-            t_train = time.time() - t_l0
 
-            def compare(pc):
+            def compare(pc, deg):
+                F.fem_pic_field_poly(lib.h, sys_id, deg, prat[sys_id])
                 state["precond"] = pc
                 restore()
                 F.fem_pic_profile_read(lib.h, reset=True)
@@ -524,25 +676,23 @@ def run_gpu(args):
                 tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
                 return {"field_ms_per_step": tot / args.compare_steps,
                         ph_cg + "_ms_per_step": ph.get(ph_cg, (0.0, 1))[0] / args.compare_steps,
-                        "learned_ms_per_step": ph.get("learned", (0.0, 1))[0] / args.compare_steps,
                         "iters_mean": statistics.mean(its), "fell_back": fb}
-            # plain Jacobi-CG is the comparison: both runs with the Jacobi inner
-            # preconditioner on this system (the timed steps then use the configured one)
-            F.fem_pic_field_poly(lib.h, sys_id, 1, prat[sys_id])
-            plain = compare(precond)
-            learn = compare(precond | bit)
+            plain = compare(precond, 1)            # plain Jacobi-CG
+            learn = compare(precond | bit, 1)      # the learned preconditioner (replaces the polynomial)
+            poly = compare(precond, pdeg[sys_id]) if pdeg[sys_id] > 1 else None
             F.fem_pic_field_poly(lib.h, sys_id, pdeg[sys_id], prat[sys_id])
-            use = args.learned == "on" or learn["field_ms_per_step"] < plain["field_ms_per_step"]
+            beats_plain = learn[ph_cg + "_ms_per_step"] < plain[ph_cg + "_ms_per_step"]
+            best_other = (poly or plain)[ph_cg + "_ms_per_step"]
+            use = args.learned == "on" or (beats_plain and learn[ph_cg + "_ms_per_step"] < best_other)
             if use:
                 used_bits |= bit
-            graph = "edge graph" if sys_id == F.FP_SYS_NEWMARK else "node graph"
             learned[sysname] = {
-                "samples": n_s, "held_out": n_hold, "epochs": args.learn_epochs, "train_s": t_train,
-                "train_loss_first": float(losses[0]), "train_loss_last": float(losses[-1]),
-                "held_out_ratio_before": float(np.mean(before)), "held_out_ratio_after": float(np.mean(after)),
-                "plain": plain, "learned": learn, "used_in_timed_steps": bool(use),
-                "compared_against": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system in both runs)",
-                "model": f"3-layer message passing on the {graph}, 64 features, BF16 weights, FP32 accum"}
+                "plain": plain, "learned": learn, "chebyshev": poly,
+                "learned_vs_plain_ms": learn[ph_cg + "_ms_per_step"] / plain[ph_cg + "_ms_per_step"],
+                "learned_beats_plain_cg": bool(beats_plain), "used_in_timed_steps": bool(use),
+                "weights": "trained by the protocol on the 4^3 and 32^3 workloads, applied unchanged to this mesh",
+                "compared_against": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system) and the "
+                                    f"Chebyshev-Jacobi polynomial of degree {pdeg[sys_id]}, same steps, same {args.tol}"}
         state["precond"] = precond | used_bits
 
     # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
@@ -970,11 +1120,10 @@ def run_gpu(args):
             "field_solve": None if not field else {
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
-                "ms_learned_guess": phases.get("learned", (0.0, 1))[0] / args.steps,
-                "precond": ("learned correction (" + ", ".join(
-                    nm for nm, bit in (("newmark", F.FP_PC_LEARNED), ("gauss", F.FP_PC_LEARNED_GAUSS))
-                    if state["precond"] & bit) + ") + jacobi")
-                    if state["precond"] & (F.FP_PC_LEARNED | F.FP_PC_LEARNED_GAUSS) else "jacobi",
+                "precond": {nm: ("learned preconditioner" if state["precond"] & bit else
+                                 (f"Chebyshev-Jacobi degree {pdeg[k_]}" if pdeg[k_] > 1 else "jacobi"))
+                            for k_, (nm, bit) in enumerate((("newmark", F.FP_PC_LEARNED),
+                                                            ("gauss", F.FP_PC_LEARNED_GAUSS)))},
                 "learned_vs_plain": learned,
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
                            "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",

@@ -454,8 +454,41 @@ fp_status fem_pic_whitney0_integrals(const fem_pic_t* ctx, double* alpha);
 fp_status fem_pic_learned_select(fem_pic_t* ctx, int system);
 
 /* Allocate and initialise the network (seeded) and a store for sample_capacity training
- * residuals.  Synchronous. */
+ * residuals.  Synchronous.  Same as fem_pic_learned_init_model(..., FP_LEARNED_GUESS). */
 fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity);
+
+/*
+ * The two uses of the network (the model of the selected system's network):
+ *   FP_LEARNED_GUESS: the start correction described above.
+ *   FP_LEARNED_PRECOND: a learned preconditioner inside the CG iteration.  The network runs
+ *     on a static input (the Jacobi-scaled row sums of the operator) and its features h
+ *     define, for every stored entry of the operator (Jacobi-scaled: A~ = D^-1/2 A D^-1/2),
+ *       Delta~_ii = d0 + sum_f v_f h_if^2,   Delta~_ij = A~_ij (b0 + sum_f w_f h_if h_jf),
+ *     symmetric by construction; the mixed solver's inner CG then uses
+ *       z = D^-1 r + D^-1/2 Delta~ D^-1/2 r
+ *     instead of z = D^-1 r (Delta~ = 0 is Jacobi; w = v = 0 a degree-1 polynomial in
+ *     D^-1 A), one product on the operator's pattern per iteration.  Training minimises the
+ *     mean over samples of ||A~ (r~ + Delta~ r~) - r~||^2 / ||r~||^2 (r~ = D^-1/2 r scaled to
+ *     unit RMS), the residual one application leaves, over residuals the method produces,
+ *     in mini-batches of 8.  fem_pic_learned_build makes the correction from the current
+ *     weights; FP_PC_LEARNED / FP_PC_LEARNED_GAUSS (fem_pic_field_step) or FP_PC_LEARNED
+ *     (fem_pic_field_solve, either system) then use it in the mixed solver (the FP64 solver
+ *     ignores it).  If an inner iteration finds p.Ap <= 0 (the learned operator is not
+ *     positive there) the solve falls back to Jacobi for the rest of the call
+ *     (fell_back = 1).  The weights do not depend on the mesh size: weights trained on one
+ *     mesh (fem_pic_learned_params) can be set on another of the same kind.
+ */
+enum { FP_LEARNED_GUESS = 0, FP_LEARNED_PRECOND = 1 };
+fp_status fem_pic_learned_init_model(fem_pic_t* ctx, uint64_t seed, int sample_capacity, int model);
+
+/* FP_LEARNED_PRECOND: the preconditioner's correction from the current weights, for the
+ * solver (asynchronous).  Call after training or after setting the weights. */
+fp_status fem_pic_learned_build(fem_pic_t* ctx, void* stream);
+
+/* FP_LEARNED_PRECOND, for tests: Delta~ per entry of the system's operator in CSR order
+ * (fem_pic_field_matrix's pattern; device float [nnz]) and the static input (device float
+ * [N], may be NULL). */
+fp_status fem_pic_learned_delta(fem_pic_t* ctx, float* delta_out, float* xin_out, void* stream);
 
 /* collect != 0: every fem_pic_field_step stores the residual of the system's plain start
  * (ring buffer; eager launches only: a captured graph would replay one slot).
@@ -478,12 +511,14 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
 /* Parameters (FP32 master copy): get and/or set host arrays of *n_params floats. */
 fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params);
 
-/* Forward pass on one residual r (device double [N]): writes c~ and r~ (device float [N]). */
+/* FP_LEARNED_GUESS: forward pass on one residual r (device double [N]): writes c~ and r~
+ * (device float [N]). */
 fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out,
                                   void* stream);
 
 /* Loss gradient for one residual r (device float [N]) into grad_out (host float
- * [n_params]); the weights and optimizer state are left unchanged.  Synchronous. */
+ * [n_params], n_params of the network's model); the weights and optimizer state are left
+ * unchanged.  Synchronous. */
 fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_out, double* loss,
                                    void* stream);
 

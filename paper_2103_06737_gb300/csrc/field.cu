@@ -215,6 +215,11 @@ struct MixedArgs {
     int max_outer;
     double* out;
     int32_t* status;
+    // learned preconditioner (null: off): z = D^-1 r + Dl r with Dl on the operator's SELL
+    // pattern (replaces the Chebyshev polynomial); lflag (may be null) is set to 1 when the
+    // solve fell back to Jacobi because r.z was not positive
+    const float* dl32;
+    int* lflag;
 };
 
 // This block's rows of the FP32 operator in shared memory (when the launch holds it there).
@@ -304,6 +309,16 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp
     }
 }
 
+// z = D^-1 r + Dl r for the rows [t0, r1) of this block (the learned preconditioner); the
+// product needs every block's r: one grid barrier first.  z is published by the caller's
+// next grid barrier.
+__device__ __forceinline__ void learned_apply(const MixedArgs& a, int64_t t0, int64_t r1, int64_t stride,
+                                              cg::grid_group& g) {
+    g.sync();
+    for (int64_t i = t0; i < r1; i += stride)
+        a.z[i] = a.dinv32[i] * a.r[i] + sell_row<float, float>(a.S, a.dl32, a.r, i);
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed(MixedArgs a) {
     cg::grid_group g = cg::this_grid();
@@ -337,6 +352,8 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
     float* part2 = part1 + 3 * gridDim.x;                // 2 FP32 values per block
     int total = 0, outer = 0;
     double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
+    bool use_l = a.dl32 != nullptr;   // every block takes the same fallback decision (grid sums)
+    if (use_l && a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 0;
     for (;;) {
         // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
         double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -366,7 +383,10 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             a.r[i] = ri;
             a.z[i] = a.dinv32[i] * ri;
         }
-        if (a.deg > 1) chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
+        if (use_l)
+            learned_apply(a, t0, r1, stride, g);
+        else if (a.deg > 1)
+            chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
         g.sync();
         float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
         for (int64_t i = t0; i < r1; i += stride) {
@@ -379,6 +399,12 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             u[2] += ri * ri;
         }
         grid_sum<BS, 3, float>(u, part1, g, shf);
+        if (use_l && !(u[0] > 0.f)) {   // the learned operator is not positive on r: Jacobi from here on
+            use_l = false;
+            if (a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 1;
+            g.sync();
+            continue;                   // c is still 0: the refinement restarts with Jacobi
+        }
         float rz = u[0], pq = u[1];
         // the inner solve stops at a reduction of inner_tol, or earlier when a smaller
         // reduction (with a margin of kInnerMargin) already meets the outer tolerance
@@ -389,7 +415,18 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             if (!(pq > 0.f) || total >= a.max_iter) break;
             const float alpha = rz / pq;
             float w2[2] = {0.f, 0.f};  // r.z, r.r
-            if (a.deg <= 1) {
+            if (use_l) {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    a.r[i] -= alpha * a.q[i];
+                }
+                learned_apply(a, t0, r1, stride, g);
+                for (int64_t i = t0; i < r1; i += stride) {
+                    const float ri = a.r[i];
+                    w2[0] += ri * a.z[i];
+                    w2[1] += ri * ri;
+                }
+            } else if (a.deg <= 1) {
                 for (int64_t i = t0; i < r1; i += stride) {
                     a.c[i] += alpha * a.p[i];
                     const float ri = a.r[i] - alpha * a.q[i];
@@ -414,6 +451,11 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             grid_sum<BS, 2, float>(w2, part2, g, shf);
             ++total;
             if (!(w2[1] > ithr)) break;
+            if (use_l && !(w2[0] > 0.f)) {   // not positive on this r: keep c, Jacobi from here on
+                use_l = false;
+                if (a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 1;
+                break;
+            }
             const float beta = w2[0] / rz;
             rz = w2[0];
             float u2[1] = {0.f};
@@ -593,6 +635,7 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     if (ctx->solver_sys[system] >= 0) use64 = ctx->solver_sys[system] == FP_PC_JACOBI_FP64;
     const int ph = system == FP_SYS_NEWMARK ? PH_CG_NEWMARK : PH_CG_GAUSS;
     F->last_fp64[slot] = use64;
+    F->slot_sys[slot] = system;
     if (!use64) {
         MixedArgs m;
         if (system == FP_SYS_NEWMARK) {   // the solver's own row order (gathered in and scattered out below)
@@ -614,6 +657,8 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         }
         m.tol = tol, m.inner_tol = ctx->inner_tol, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
+        m.dl32 = learned_precond(F, system);
+        m.lflag = m.dl32 ? learned_flag(F, system) : nullptr;
         void* args[] = {&m};
         m.d16 = system == FP_SYS_NEWMARK ? F->se_d16 : F->sn_d16;
         m.sm_slots = F->sm_slots[system];
@@ -662,7 +707,8 @@ fp_status fill_info(fem_pic* ctx, int slot, fp_solve_info* info, cudaStream_t s,
     info->fell_back = 0;
     if (ctx->field->learned_used[slot]) {
         int fl = 0;
-        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&fl, learned_flag(ctx->field, slot), sizeof(int), cudaMemcpyDeviceToHost, s));
+        FP_CUDA_TRY(ctx, cudaMemcpyAsync(&fl, learned_flag(ctx->field, ctx->field->slot_sys[slot]), sizeof(int),
+                                         cudaMemcpyDeviceToHost, s));
         FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         info->precond = FP_PC_LEARNED;
         info->fell_back = fl;
@@ -1021,11 +1067,15 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
 #ifndef FP_SOLVER_ORDER
 #define FP_SOLVER_ORDER 1
 #endif
+            bool blocked_order = false;
             if (FP_SOLVER_ORDER && F->sectors_e[1] < F->sectors_e[0]) {
+                // the solver order gathers fewer sectors; its 16-bit column offsets (for the
+                // shared-memory operator) may not fit on large meshes, the order is kept anyway
                 sell(rp2, col2, ne, &ptr, &w, &scol, &map);
                 d16 = offsets16(scol, ptr, w, ne);
+                blocked_order = true;
             }
-            if (d16.empty()) {   // the edge order
+            if (!blocked_order) {   // the edge order
                 perm = &ident;
                 F->sectors_e[1] = F->sectors_e[0];
                 permuted(ident, &rp2, &col2, &val2);
@@ -1240,11 +1290,18 @@ fp_status fem_pic_field_matrix(const fem_pic_t* ctx, int which, int32_t* row_ptr
 fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, double* x, double tol,
                               int max_iter, int precond, fp_solve_info* info, void* stream) {
     if (!ctx || !ctx->field || !rhs || !x || (system != FP_SYS_NEWMARK && system != FP_SYS_GAUSS) ||
-        !(tol > 0.0) || max_iter < 0 || (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64)) {
+        !(tol > 0.0) || max_iter < 0 ||
+        (precond != FP_PC_JACOBI && precond != FP_PC_JACOBI_FP64 && precond != FP_PC_LEARNED)) {
         if (ctx) ctx->err = "fem_pic_field_solve: bad argument (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
+    if (precond == FP_PC_LEARNED && !learned_precond_ready(ctx->field, system)) {
+        ctx->err = "fem_pic_field_solve: FP_PC_LEARNED needs a built FP_LEARNED_PRECOND network for the system";
+        return FP_EINVAL;
+    }
     ctx->solver_fp64 = precond == FP_PC_JACOBI_FP64;
+    learned_set_active(ctx->field, system, precond == FP_PC_LEARNED);
+    ctx->field->learned_used[0] = precond == FP_PC_LEARNED;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a = nullptr, b = nullptr;
     if (info) {
@@ -1277,8 +1334,10 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
     }
     const bool use[2] = {(precond & FP_PC_LEARNED) != 0, (precond & FP_PC_LEARNED_GAUSS) != 0};
     for (int k = 0; k < 2; ++k)
-        if (use[k] && !ctx->field->learned[k]) {
-            ctx->err = "fem_pic_field_step: a learned correction needs fem_pic_learned_init for its system";
+        if (use[k] && (!ctx->field->learned[k] || (learned_model(ctx->field, k) == FP_LEARNED_PRECOND &&
+                                                    !learned_precond_ready(ctx->field, k)))) {
+            ctx->err = "fem_pic_field_step: a learned correction needs fem_pic_learned_init for its system "
+                       "(and fem_pic_learned_build for a learned preconditioner)";
             return FP_EINVAL;
         }
     ctx->solver_fp64 = (precond & FP_PC_JACOBI_FP64) != 0;

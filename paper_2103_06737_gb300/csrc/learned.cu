@@ -36,7 +36,11 @@ constexpr int kWsz = kK * kH;  // one layer's weights
 constexpr int kOffWe = 0, kOffBe = 64, kOffW0 = 128;
 constexpr int kLayerStride = kWsz + kH;
 constexpr int kOffWh = kOffW0 + kLayers * kLayerStride, kOffBh = kOffWh + kH;
-constexpr int kNParams = kOffBh + 1;
+constexpr int kNParams0 = kOffBh + 1;          // model 0 (start correction)
+// model 1 (preconditioner) adds a diagonal head: v (64) and d0 after the off-diagonal w, b0
+// (which take the places of w_h, b_h)
+constexpr int kOffVh = kNParams0, kOffDh = kOffVh + kH;
+constexpr int kNParams = kOffDh + 1;           // storage (both models)
 constexpr unsigned kFull = 0xffffffffu;
 
 }  // namespace
@@ -66,6 +70,19 @@ struct LearnedDev {
     float* samples = nullptr;
     int cap = 0, count = 0, next = 0;
     int collecting = 0, active = 0, adam_t = 0;
+    // model 1: the network's output is a sparse correction of the Jacobi preconditioner on
+    // the operator's pattern, z = D^-1 r + D^-1/2 Delta~ D^-1/2 r (see below)
+    int model = 0;
+    int64_t rp_nnz = 0;           // entries of the CSR pattern
+    float* xin = nullptr;         // static encoder input per row (scaled row sum of A~, unit RMS)
+    float* delta = nullptr;       // Delta~ per CSR entry
+    float* gdel = nullptr;        // d loss / d Delta~ per CSR entry
+    int32_t* tpos = nullptr;      // CSR index of the transposed entry
+    float *rs = nullptr, *u = nullptr, *g = nullptr;
+    float* pre = nullptr;         // D^-1/2 Delta~ D^-1/2 in the mixed solver's SELL layout
+    int64_t pre_slots = 0;
+    int built = 0;                // pre holds the current weights' preconditioner
+    int n_params() const { return model == 1 ? kNParams : kNParams0; }
 };
 
 namespace {
@@ -542,6 +559,233 @@ __global__ void k_lm_select(double* __restrict__ x0, const double* __restrict__ 
         x0[i] = y[i];
 }
 
+// ---------------------------------------------------------------- model 1: learned preconditioner
+// The network's features h3 (from a static input: the scaled row sums of A~) define a sparse
+// correction of the Jacobi preconditioner on the operator's own pattern, symmetric by
+// construction, in the Jacobi-scaled variables:
+//   Delta~_ii = d0 + sum_f v_f h_if^2,   Delta~_ij = A~_ij (b0 + sum_f w_f h_if h_jf)  (j != i)
+// and the preconditioner is z = D^-1 r + D^-1/2 Delta~ D^-1/2 r  (Delta~ = 0: plain Jacobi;
+// w = v = 0 gives z = (1 + d0) D^-1 r + b0 D^-1 A D^-1 r, a degree-1 polynomial in D^-1 A).
+// It is trained on residuals r the method produces: loss ||A~ (r~ + Delta~ r~) - r~||^2 /
+// ||r~||^2, the residual left by one application in the scaled variables.
+
+// h0 = relu(x w_e + b_e) from the static input x (also kept in rt for the encoder backward)
+__global__ void k_ls_input(const float* __restrict__ xin, int64_t n, const float* __restrict__ P,
+                           float* __restrict__ rt, __nv_bfloat16* __restrict__ h0) {
+    const int64_t total = n * (kH / 2);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / (kH / 2);
+        const int f = 2 * (int)(t % (kH / 2));
+        const float x = xin[i];
+        if (f == 0) rt[i] = x;
+        const float v0 = fmaxf(x * P[kOffWe + f] + P[kOffBe + f], 0.f);
+        const float v1 = fmaxf(x * P[kOffWe + f + 1] + P[kOffBe + f + 1], 0.f);
+        reinterpret_cast<__nv_bfloat162*>(h0)[t] = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Delta~ per CSR entry (warp per row; each lane holds two features of h_i)
+__global__ void k_ls_head(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ a,
+                          const __nv_bfloat16* __restrict__ H, const float* __restrict__ P,
+                          const uint8_t* __restrict__ fixed, int64_t n, float* __restrict__ delta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float w0 = P[kOffWh + 2 * lane], w1 = P[kOffWh + 2 * lane + 1], b0 = P[kOffBh];
+    const float v0 = P[kOffVh + 2 * lane], v1 = P[kOffVh + 2 * lane + 1], d0 = P[kOffDh];
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const __nv_bfloat162 hi2 = reinterpret_cast<const __nv_bfloat162*>(H + i * kH)[lane];
+        const float hi0 = __low2float(hi2), hi1 = __high2float(hi2);
+        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        const bool fx = fixed[i] != 0;
+        for (int k = rb; k < re; ++k) {
+            const int j = __ldg(col + k);
+            float dl;
+            if (j == i) {
+                dl = warp_sum(v0 * hi0 * hi0 + v1 * hi1 * hi1) + d0;
+            } else {
+                const __nv_bfloat162 hj2 = reinterpret_cast<const __nv_bfloat162*>(H + (int64_t)j * kH)[lane];
+                dl = __ldg(a + k) * (warp_sum(w0 * hi0 * __low2float(hj2) + w1 * hi1 * __high2float(hj2)) + b0);
+            }
+            if (lane == 0) delta[k] = fx ? 0.f : dl;
+        }
+    }
+}
+
+// rs = D^-1/2 r / s, s = RMS over free rows (scal[0] = sum of (D^-1/2 r)^2 over free rows)
+__global__ void k_ls_scale(const float* __restrict__ r, const float* __restrict__ dis, const uint8_t* __restrict__ fixed,
+                           int64_t n, float n_free, const float* __restrict__ scal, float* __restrict__ rs) {
+    const float inv = 1.f / sqrtf(fmaxf(scal[0], 1e-30f) / n_free);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rs[i] = fixed[i] ? 0.f : r[i] * dis[i] * inv;
+}
+
+// u = x + Delta~ x (CSR, warp per row)
+__global__ void k_ls_apply(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const float* __restrict__ delta, const float* __restrict__ x, int64_t n,
+                           float* __restrict__ u) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        float acc = 0.f;
+        for (int k = rb + lane; k < re; k += 32) acc += delta[k] * x[__ldg(col + k)];
+        acc = warp_sum(acc);
+        if (lane == 0) u[i] = x[i] + acc;
+    }
+}
+
+// gdel_ij += g_i x_j (CSR, warp per row)
+__global__ void k_ls_grad_accum(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const float* __restrict__ g, const float* __restrict__ x, int64_t n,
+                                float* __restrict__ gdel) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        const float gi = g[i];
+        for (int k = rb + lane; k < re; k += 32) gdel[k] += gi * x[__ldg(col + k)];
+    }
+}
+
+// head backward: dh_i = sum_{j != i} (G_ij + G_ji) A~_ij w (.) h_j + 2 G_ii v (.) h_i, and the
+// gradients of w, b0, v, d0 (G = d loss / d Delta~ per CSR entry; Delta~_ij and Delta~_ji both
+// depend on h_i)
+__global__ void k_ls_head_bwd(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const float* __restrict__ a, const int32_t* __restrict__ tpos,
+                              const __nv_bfloat16* __restrict__ H, const float* __restrict__ gdel,
+                              const float* __restrict__ P, const uint8_t* __restrict__ fixed, int64_t n,
+                              float* __restrict__ dh, float* __restrict__ G) {
+    __shared__ float sg[2 * kH + 2];
+    for (int t = threadIdx.x; t < 2 * kH + 2; t += blockDim.x) sg[t] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float w0 = P[kOffWh + 2 * lane], w1 = P[kOffWh + 2 * lane + 1];
+    const float v0 = P[kOffVh + 2 * lane], v1 = P[kOffVh + 2 * lane + 1];
+    float gw0 = 0.f, gw1 = 0.f, gv0 = 0.f, gv1 = 0.f, gb = 0.f, gd = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const __nv_bfloat162 hi2 = reinterpret_cast<const __nv_bfloat162*>(H + i * kH)[lane];
+        const float hi0 = __low2float(hi2), hi1 = __high2float(hi2);
+        float d0 = 0.f, d1 = 0.f;
+        if (!fixed[i]) {
+            const int rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+            for (int k = rb; k < re; ++k) {
+                const int j = __ldg(col + k);
+                const float gk = gdel[k];
+                if (j == i) {
+                    d0 += 2.f * gk * v0 * hi0;
+                    d1 += 2.f * gk * v1 * hi1;
+                    gv0 += gk * hi0 * hi0;
+                    gv1 += gk * hi1 * hi1;
+                    gd += lane == 0 ? gk : 0.f;
+                } else {
+                    const __nv_bfloat162 hj2 = reinterpret_cast<const __nv_bfloat162*>(H + (int64_t)j * kH)[lane];
+                    const float hj0 = __low2float(hj2), hj1 = __high2float(hj2);
+                    const float aij = __ldg(a + k);
+                    const int tk = __ldg(tpos + k);   // -1: no (j, i) entry (a fixed row j)
+                    const float gs = (gk + (tk >= 0 ? gdel[tk] : 0.f)) * aij;
+                    d0 += gs * w0 * hj0;
+                    d1 += gs * w1 * hj1;
+                    gw0 += gk * aij * hi0 * hj0;
+                    gw1 += gk * aij * hi1 * hj1;
+                    gb += lane == 0 ? gk * aij : 0.f;
+                }
+            }
+        }
+        reinterpret_cast<float2*>(dh + i * kH)[lane] = make_float2(d0, d1);
+    }
+    atomicAdd(&sg[2 * lane], gw0);
+    atomicAdd(&sg[2 * lane + 1], gw1);
+    atomicAdd(&sg[kH + 2 * lane], gv0);
+    atomicAdd(&sg[kH + 2 * lane + 1], gv1);
+    if (lane == 0) {
+        atomicAdd(&sg[2 * kH], gb);
+        atomicAdd(&sg[2 * kH + 1], gd);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+        atomicAdd(G + kOffWh + t, sg[t]);
+        atomicAdd(G + kOffVh + t, sg[kH + t]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(G + kOffBh, sg[2 * kH]);
+        atomicAdd(G + kOffDh, sg[2 * kH + 1]);
+    }
+}
+
+// D^-1/2 Delta~ D^-1/2 in the mixed solver's SELL layout (solver row r is DOF perm[r], perm
+// null: the identity; padded slots point at their own row with value 0): warp per slice, lane
+// per row, one slot of each row at a time (each lane dots its h_i with the h_j of its slot)
+__global__ void k_ls_build(const int32_t* __restrict__ sptr, const int32_t* __restrict__ sw,
+                           const int32_t* __restrict__ scol, const double* __restrict__ sval,
+                           const int32_t* __restrict__ perm, const float* __restrict__ dis,
+                           const __nv_bfloat16* __restrict__ H, const float* __restrict__ P,
+                           const uint8_t* __restrict__ fixed, int64_t n, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nsl = (n + 31) / 32;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nsl; sl += warps) {
+        const int64_t r = 32 * sl + lane;
+        const bool live = r < n;
+        const int64_t i = live ? (perm ? (int64_t)__ldg(perm + r) : r) : 0;
+        const bool fx = !live || fixed[i] != 0;
+        const float di = live ? dis[i] : 0.f;
+        float hi[kH];
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < kH / 8; ++q) {
+                const uint4 v = reinterpret_cast<const uint4*>(H + i * kH)[q];
+                const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    hi[8 * q + 2 * t] = __low2float(b2[t]);
+                    hi[8 * q + 2 * t + 1] = __high2float(b2[t]);
+                }
+            }
+        }
+        const int64_t base = __ldg(sptr + sl);
+        const int w = __ldg(sw + sl);
+        for (int jj = 0; jj < w; ++jj) {
+            const int64_t k = base + 32 * (int64_t)jj + lane;
+            float o = 0.f;
+            if (!fx) {
+                const int64_t c = __ldg(scol + k);
+                const double av = __ldg(sval + k);
+                const int64_t j = perm ? (int64_t)__ldg(perm + c) : c;
+                if (c == r) {
+                    if (av != 0.0) {   // the diagonal (a padded slot has value 0)
+                        float t = P[kOffDh];
+#pragma unroll
+                        for (int f = 0; f < kH; ++f) t += P[kOffVh + f] * hi[f] * hi[f];
+                        o = di * t * di;
+                    }
+                } else if (!fixed[j]) {
+                    const float dj = dis[j];
+                    const float at = (float)av * di * dj;
+                    float t = P[kOffBh];
+#pragma unroll
+                    for (int q = 0; q < kH / 8; ++q) {
+                        const uint4 v = reinterpret_cast<const uint4*>(H + j * kH)[q];
+                        const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            t += P[kOffWh + 8 * q + 2 * u] * hi[8 * q + 2 * u] * __low2float(b2[u]) +
+                                 P[kOffWh + 8 * q + 2 * u + 1] * hi[8 * q + 2 * u + 1] * __high2float(b2[u]);
+                    }
+                    o = di * at * t * dj;
+                }
+            }
+            out[k] = o;
+        }
+    }
+}
+
 int blocks(const fem_pic* ctx, int64_t work, int per_block = 256, int per_sm = 8) {
     int64_t b = (work + per_block - 1) / per_block, cap = (int64_t)ctx->sm_count * per_sm;
     b = b < cap ? b : cap;
@@ -595,6 +839,70 @@ fp_status train_step(fem_pic* ctx, LearnedDev* L, const float* r, float lr, cuda
     return FP_OK;
 }
 
+// model 1: features from the static input and Delta~ per CSR entry
+fp_status precond_forward(fem_pic* ctx, LearnedDev* L, cudaStream_t s, bool store_m) {
+    const int64_t n = L->n;
+    k_ls_input<<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(L->xin, n, L->params, L->rt, L->h[0]);
+    for (int l = 0; l < kLayers; ++l)
+        k_lm_layer<<<blocks(ctx, (n + kLT - 1) / kLT * 256, 256, 4), 256, 0, s>>>(
+            L->rp, L->col, L->a_csr, L->h[l], L->Wt[l], L->params + kOffW0 + l * kLayerStride + kWsz, n,
+            L->h[l + 1], store_m ? L->m[l] : nullptr);
+    k_ls_head<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->a_csr, L->h[kLayers], L->params, L->fixed, n,
+                                                  L->delta);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+// model 1: loss of one sample r (FP32, unscaled) added to scal[1]; with grad, g = d loss / d u
+// and gdel += g (x) r~ (the per-entry gradient), scaled by gscale
+fp_status precond_sample(fem_pic* ctx, LearnedDev* L, const float* r, bool grad, float gscale, cudaStream_t s) {
+    const int64_t n = L->n;
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal, 0, sizeof(float), s));
+    k_lm_sumsq<float><<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, L->fixed, n, L->scal);
+    k_ls_scale<<<blocks(ctx, n), 256, 0, s>>>(r, L->dis, L->fixed, n, (float)L->n_free, L->scal, L->rs);
+    k_ls_apply<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->delta, L->rs, n, L->u);
+    // e = A~ u - r~ and its squared norm; loss = ||e||^2 / n_free (r~ has unit RMS)
+    k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(L->S, L->a_sell, L->u, L->rs, L->fixed, 1.f, n, L->e, L->scal + 1);
+    if (grad) {
+        k_lm_spmv<<<blocks(ctx, n), 256, 0, s>>>(L->S, L->a_sell, L->e, nullptr, L->fixed,
+                                                 2.f * gscale / (float)L->n_free, n, L->g, nullptr);
+        k_ls_grad_accum<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->g, L->rs, n, L->gdel);
+    }
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
+// model 1: one Adam step on the mean loss of `count` samples (sample pointers in rs_list)
+fp_status precond_train_step(fem_pic* ctx, LearnedDev* L, const float* const* rs_list, int count, float lr,
+                             cudaStream_t s) {
+    const int64_t n = L->n;
+    fp_status st = precond_forward(ctx, L, s, true);
+    if (st != FP_OK) return st;
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->gdel, 0, (size_t)(L->rp_nnz) * sizeof(float), s));
+    for (int k = 0; k < count && st == FP_OK; ++k) st = precond_sample(ctx, L, rs_list[k], true, 1.f / count, s);
+    if (st != FP_OK) return st;
+    FP_CUDA_TRY(ctx, cudaMemsetAsync(L->grads, 0, kNParams * sizeof(float), s));
+    k_ls_head_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->a_csr, L->tpos, L->h[kLayers], L->gdel,
+                                                      L->params, L->fixed, n, L->dh, L->grads);
+    const int64_t rpb = 2048;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        float* gW = L->grads + kOffW0 + l * kLayerStride;
+        k_lm_relu_bwd<<<blocks(ctx, n * (kH / 2)), 256, 0, s>>>(L->dh, L->h[l + 1], n, L->dz, gW + kWsz);
+        k_lm_gemm_dw<<<(unsigned)((n + rpb - 1) / rpb), 256, 0, s>>>(L->h[l], L->m[l], L->dz, n, rpb, gW);
+        k_lm_gemm_dx<<<blocks(ctx, (n + 15) / 16 * 32, 128, 16), 128, 0, s>>>(L->dz, L->Wn[l], n, L->dhd, L->dm);
+        k_lm_aggregate_f32<<<blocks(ctx, n * 32), 256, 0, s>>>(L->rp, L->col, L->a_csr, L->dm, L->dhd, n, L->dh);
+    }
+    k_lm_enc_bwd<<<blocks(ctx, n * 32), 256, 0, s>>>(L->dh, L->h[0], L->rt, n, L->grads);
+    ++L->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    k_lm_adam<<<64, 256, 0, s>>>(L->params, L->grads, L->am, L->av, kNParams, lr, b1, b2, 1e-8f,
+                                 1.f - powf(b1, (float)L->adam_t), 1.f - powf(b2, (float)L->adam_t));
+    k_lm_cast<<<96, 256, 0, s>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
+    L->built = 0;
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    return FP_OK;
+}
+
 template <typename T>
 fp_status alloc(fem_pic* ctx, T** p, size_t count) {
     FP_CUDA_TRY(ctx, cudaMalloc((void**)p, count * sizeof(T) + 16));
@@ -610,6 +918,21 @@ bool learned_active(const FieldDev* F, int sys) {
 
 int* learned_flag(FieldDev* F, int sys) { return F && F->learned[sys] ? F->learned[sys]->flag : nullptr; }
 
+int learned_model(const FieldDev* F, int sys) {
+    const LearnedDev* L = F ? F->learned[sys] : nullptr;
+    return L ? L->model : -1;
+}
+
+bool learned_precond_ready(const FieldDev* F, int sys) {
+    const LearnedDev* L = F ? F->learned[sys] : nullptr;
+    return L && L->model == 1 && L->built;
+}
+
+const float* learned_precond(const FieldDev* F, int sys) {
+    const LearnedDev* L = F ? F->learned[sys] : nullptr;
+    return L && L->model == 1 && L->active && L->built ? L->pre : nullptr;
+}
+
 void learned_set_active(FieldDev* F, int sys, bool on) {
     if (F && F->learned[sys]) F->learned[sys]->active = on ? 1 : 0;
 }
@@ -619,7 +942,8 @@ void learned_free(FieldDev* F, int sys) {
     if (!L) return;
     void* ptrs[] = {L->a_sell, L->a_csr, L->dis, L->params, L->grads, L->am, L->av, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0],
                     L->Wn[1], L->Wn[2], L->h[0], L->h[1], L->h[2], L->h[3], L->m[0], L->m[1], L->m[2], L->dz, L->dh,
-                    L->dhd, L->dm, L->rt, L->ct, L->e, L->dct, L->scal, L->flag, L->r0, L->y, L->samples};
+                    L->dhd, L->dm, L->rt, L->ct, L->e, L->dct, L->scal, L->flag, L->r0, L->y, L->samples,
+                    L->xin, L->delta, L->gdel, L->tpos, L->rs, L->u, L->g, L->pre};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -637,6 +961,7 @@ void learned_free(FieldDev* F) {
 fp_status learned_guess(fem_pic* ctx, int sys, const double* rhs, double* x0, cudaStream_t s) {
     LearnedDev* L = ctx->field->learned[sys];
     const int64_t n = L->n;
+    if (L->model == 1 && !L->collecting) return FP_OK;   // it acts inside the solver
     float* slot = nullptr;
     if (L->collecting && L->cap > 0) {
         slot = L->samples + (int64_t)L->next * n;
@@ -646,7 +971,7 @@ fp_status learned_guess(fem_pic* ctx, int sys, const double* rhs, double* x0, cu
     PhaseTimer pt(ctx, PH_LEARNED, s);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 2, 0, 2 * sizeof(float), s));
     k_lm_resid<<<blocks(ctx, n), 256, 0, s>>>(L->S, L->a64, rhs, x0, L->fixed, n, L->r0, slot, L->scal + 2);
-    if (!L->active) return FP_OK;
+    if (!L->active || L->model == 1) return FP_OK;   // model 1 acts inside the solver instead
     fp_status st = forward<double>(ctx, L, L->r0, s, false);
     if (st != FP_OK) return st;
     k_lm_candidate<<<blocks(ctx, n), 256, 0, s>>>(x0, L->ct, L->dis, L->scal, n, L->y);
@@ -678,8 +1003,12 @@ fp_status fem_pic_learned_select(fem_pic_t* ctx, int system) {
 }
 
 fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacity) {
-    if (!ctx || !ctx->field || sample_capacity < 0) {
-        if (ctx) ctx->err = "fem_pic_learned_init: call fem_pic_field_setup first";
+    return fem_pic_learned_init_model(ctx, seed, sample_capacity, FP_LEARNED_GUESS);
+}
+
+fp_status fem_pic_learned_init_model(fem_pic_t* ctx, uint64_t seed, int sample_capacity, int model) {
+    if (!ctx || !ctx->field || sample_capacity < 0 || (model != FP_LEARNED_GUESS && model != FP_LEARNED_PRECOND)) {
+        if (ctx) ctx->err = "fem_pic_learned_init: bad model or capacity (or fem_pic_field_setup not called)";
         return FP_EINVAL;
     }
     FieldDev* F = ctx->field;
@@ -779,6 +1108,53 @@ fp_status fem_pic_learned_init(fem_pic_t* ctx, uint64_t seed, int sample_capacit
     if (st == FP_OK && sample_capacity > 0) st = alloc(ctx, &L->samples, (size_t)sample_capacity * n);
     if (st != FP_OK) return st;
     L->cap = sample_capacity;
+    L->model = model;
+    if (model == FP_LEARNED_PRECOND) {
+        // static input: the row sums of A~ (unit RMS over free rows); the transposed entry of
+        // every CSR entry; the preconditioner's head starts near zero (plain Jacobi)
+        const int64_t nnz = (int64_t)hcol.size();
+        L->rp_nnz = nnz;
+        std::vector<float> xin(n, 0.f);
+        double ss = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int32_t j = hrp[i]; j < hrp[i + 1]; ++j) t += ac[j];
+            xin[i] = hfixed[i] ? 0.f : (float)t;
+            if (!hfixed[i]) ss += t * t;
+        }
+        const float inv = (float)(1.0 / std::sqrt(std::max(ss / (double)L->n_free, 1e-300)));
+        for (int64_t i = 0; i < n; ++i) xin[i] *= inv;
+        std::vector<int32_t> tpos(nnz, -1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t k = hrp[i]; k < hrp[i + 1]; ++k) {
+                const int32_t j = hcol[k];
+                const int32_t* b = hcol.data() + hrp[j];
+                const int32_t* e = hcol.data() + hrp[j + 1];
+                const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+                if (f != e && *f == i) tpos[k] = (int32_t)(f - hcol.data());
+            }
+        std::vector<float> P2(kNParams);
+        FP_CUDA_TRY(ctx, cudaMemcpy(P2.data(), L->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int f = 0; f < kH; ++f) {
+            P2[kOffWh + f] = 0.01f * nd(rng);
+            P2[kOffVh + f] = 0.01f * nd(rng);
+        }
+        P2[kOffBh] = 0.f;
+        P2[kOffDh] = 0.f;
+        FP_CUDA_TRY(ctx, cudaMemcpy(L->params, P2.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+        const bool nm2 = sys == FP_SYS_NEWMARK;
+        L->pre_slots = F->slots_total[sys];
+        if (st == FP_OK) st = up(&L->xin, xin);
+        if (st == FP_OK) st = up(&L->tpos, tpos);
+        if (st == FP_OK) st = alloc(ctx, &L->delta, (size_t)nnz);
+        if (st == FP_OK) st = alloc(ctx, &L->gdel, (size_t)nnz);
+        if (st == FP_OK) st = alloc(ctx, &L->rs, n);
+        if (st == FP_OK) st = alloc(ctx, &L->u, n);
+        if (st == FP_OK) st = alloc(ctx, &L->g, n);
+        if (st == FP_OK) st = alloc(ctx, &L->pre, (size_t)std::max<int64_t>(1, L->pre_slots));
+        (void)nm2;
+        if (st != FP_OK) return st;
+    }
     k_lm_cast<<<96, 256>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
     FP_CUDA_TRY(ctx, cudaMemset(L->flag, 0, sizeof(int)));
     FP_CUDA_TRY(ctx, cudaDeviceSynchronize());
@@ -812,6 +1188,32 @@ fp_status fem_pic_learned_train(fem_pic_t* ctx, int first, int count, int epochs
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = first + i;
     std::mt19937_64 rng(seed);
+    if (L->model == FP_LEARNED_PRECOND) {
+        // mini-batches of kBatch samples; the reported loss is the epoch's mean sample loss
+        constexpr int kBatch = 8;
+        const int steps = (count + kBatch - 1) / kBatch;
+        for (int ep = 0; ep < epochs; ++ep) {
+            std::shuffle(order.begin(), order.end(), rng);
+            FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
+            for (int b = 0; b < steps; ++b) {
+                const float* batch[kBatch];
+                int m = 0;
+                for (int k = b * kBatch; k < std::min(count, (b + 1) * kBatch); ++k)
+                    batch[m++] = L->samples + (int64_t)order[k] * L->n;
+                const double t = (double)(ep * steps + b) / (double)std::max(1, epochs * steps);
+                const float lr_t = (float)(lr * 0.5 * (1.0 + std::cos(3.141592653589793 * t)));
+                fp_status st = precond_train_step(ctx, L, batch, m, lr_t, s);
+                if (st != FP_OK) return st;
+            }
+            if (loss) {
+                float l = 0.f;
+                FP_CUDA_TRY(ctx, cudaMemcpyAsync(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+                FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+                loss[ep] = (double)l / ((double)L->n_free * count);
+            }
+        }
+        return FP_OK;
+    }
     for (int ep = 0; ep < epochs; ++ep) {
         std::shuffle(order.begin(), order.end(), rng);
         FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
@@ -838,6 +1240,18 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
     if (!L || !ratio) return FP_EINVAL;
     if (first < 0 || count < 1 || first + count > L->count) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (L->model == FP_LEARNED_PRECOND) {   // ||A~ M~ r~ - r~||^2 / ||r~||^2 per sample
+        fp_status st = precond_forward(ctx, L, s, false);
+        for (int k = 0; k < count && st == FP_OK; ++k) {
+            FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
+            st = precond_sample(ctx, L, L->samples + (int64_t)(first + k) * L->n, false, 1.f, s);
+            float l = 0.f;
+            FP_CUDA_TRY(ctx, cudaMemcpyAsync(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+            FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            ratio[k] = (double)l / (double)L->n_free;
+        }
+        return st;
+    }
     for (int k = 0; k < count; ++k) {
         fp_status st = forward<float>(ctx, L, L->samples + (int64_t)(first + k) * L->n, s, false);
         if (st != FP_OK) return st;
@@ -855,20 +1269,59 @@ fp_status fem_pic_learned_eval(fem_pic_t* ctx, int first, int count, double* rat
 fp_status fem_pic_learned_params(fem_pic_t* ctx, float* get, const float* set, int64_t* n_params) {
     LearnedDev* L = cur(ctx);
     if (!L) return FP_EINVAL;
-    if (n_params) *n_params = kNParams;
-    if (get) FP_CUDA_TRY(ctx, cudaMemcpy(get, L->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    const int np = L->n_params();
+    if (n_params) *n_params = np;
+    if (get) FP_CUDA_TRY(ctx, cudaMemcpy(get, L->params, np * sizeof(float), cudaMemcpyDeviceToHost));
     if (set) {
-        FP_CUDA_TRY(ctx, cudaMemcpy(L->params, set, kNParams * sizeof(float), cudaMemcpyHostToDevice));
+        FP_CUDA_TRY(ctx, cudaMemcpy(L->params, set, np * sizeof(float), cudaMemcpyHostToDevice));
+        L->built = 0;
         k_lm_cast<<<96, 256>>>(L->params, L->Wt[0], L->Wt[1], L->Wt[2], L->Wn[0], L->Wn[1], L->Wn[2]);
         FP_CUDA_TRY(ctx, cudaDeviceSynchronize());
     }
     return FP_OK;
 }
 
+fp_status fem_pic_learned_delta(fem_pic_t* ctx, float* delta_out, float* xin_out, void* stream) {
+    // model 1: Delta~ per CSR entry of the system's operator and the static input (device), for tests
+    LearnedDev* L = cur(ctx);
+    if (!L || L->model != FP_LEARNED_PRECOND || !delta_out) {
+        if (ctx) ctx->err = "fem_pic_learned_delta: needs a network of model FP_LEARNED_PRECOND";
+        return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = precond_forward(ctx, L, s, false);
+    if (st != FP_OK) return st;
+    FP_CUDA_TRY(ctx, cudaMemcpyAsync(delta_out, L->delta, L->rp_nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (xin_out) FP_CUDA_TRY(ctx, cudaMemcpyAsync(xin_out, L->xin, L->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return FP_OK;
+}
+
+fp_status fem_pic_learned_build(fem_pic_t* ctx, void* stream) {
+    // model 1: the preconditioner's correction from the current weights, in the mixed
+    // solver's layout of the system's operator
+    LearnedDev* L = cur(ctx);
+    if (!L || L->model != FP_LEARNED_PRECOND) {
+        if (ctx) ctx->err = "fem_pic_learned_build: needs a network of model FP_LEARNED_PRECOND";
+        return FP_EINVAL;
+    }
+    FieldDev* F = ctx->field;
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = precond_forward(ctx, L, s, false);
+    if (st != FP_OK) return st;
+    const bool nm = L->sys == FP_SYS_NEWMARK;
+    const int64_t nsl = (L->n + 31) / 32;
+    k_ls_build<<<blocks(ctx, nsl * 32, 128, 16), 128, 0, s>>>(
+        nm ? F->pe_ptr : F->sn_ptr, nm ? F->pe_w : F->sn_w, nm ? F->pe_col : F->sn_col, nm ? F->pe_A : F->sn_L,
+        nm ? F->perm_e : nullptr, L->dis, L->h[kLayers], L->params, L->fixed, L->n, L->pre);
+    FP_CUDA_TRY(ctx, cudaGetLastError());
+    L->built = 1;
+    return FP_OK;
+}
+
 fp_status fem_pic_learned_forward(fem_pic_t* ctx, const double* r, float* ct_out, float* rt_out, void* stream) {
     // c~ and r~ of one residual (device arrays), for tests
     LearnedDev* L = cur(ctx);
-    if (!L || !r) return FP_EINVAL;
+    if (!L || !r || L->model != FP_LEARNED_GUESS) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     fp_status st = forward<double>(ctx, L, r, s, false);
     if (st != FP_OK) return st;
@@ -888,11 +1341,14 @@ fp_status fem_pic_learned_gradient(fem_pic_t* ctx, const float* r, float* grad_o
     FP_CUDA_TRY(ctx, cudaMemcpy(keep_m.data(), L->am, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
     FP_CUDA_TRY(ctx, cudaMemcpy(keep_v.data(), L->av, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
     const int t_keep = L->adam_t;
+    const int built_keep = L->built;
     FP_CUDA_TRY(ctx, cudaMemsetAsync(L->scal + 1, 0, sizeof(float), s));
-    fp_status st = train_step(ctx, L, r, 0.f, s);
+    fp_status st = L->model == FP_LEARNED_PRECOND ? precond_train_step(ctx, L, &r, 1, 0.f, s)
+                                                  : train_step(ctx, L, r, 0.f, s);
     if (st != FP_OK) return st;
+    L->built = built_keep;
     FP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    FP_CUDA_TRY(ctx, cudaMemcpy(grad_out, L->grads, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    FP_CUDA_TRY(ctx, cudaMemcpy(grad_out, L->grads, L->n_params() * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss) {
         float l = 0.f;
         FP_CUDA_TRY(ctx, cudaMemcpy(&l, L->scal + 1, sizeof(float), cudaMemcpyDeviceToHost));

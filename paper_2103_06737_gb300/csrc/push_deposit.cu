@@ -570,6 +570,25 @@ __device__ __forceinline__ void hot_fields(const TetHot& H, const float x[3], fl
     for (int i = 0; i < 3; ++i) B[i] = H.B0[i] + H.beta * x[i];
 }
 
+// Record chunks (16 bytes each) every particle of the fast path reads up front: from chunk
+// kIdChunks on (the gradients and field coefficients); the id chunks 0..kIdChunks-1 follow
+// only where a deposit is issued.
+#ifndef FP_HEAD_IDS
+#define FP_HEAD_IDS 1
+#endif
+constexpr int kIdChunks = FP_HEAD_IDS ? 2 : 0;
+
+// node ids and edge ids 0..3 of record c (chunks 0 and 1), from the shared window or global memory
+__device__ __forceinline__ void ids_of(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
+                                       bool in_win, int c, TetHot& H) {
+    if (kIdChunks == 0) return;
+    const int4* r = in_win ? reinterpret_cast<const int4*>(rec + (c - rec_lo) * kRecStride)
+                           : reinterpret_cast<const int4*>(hot + c);
+    const int4 a = in_win ? r[0] : __ldg(r), b = in_win ? r[1] : __ldg(r + 1);
+    H.node[0] = a.x, H.node[1] = a.y, H.node[2] = a.z, H.node[3] = a.w;
+    H.edge[0] = b.x, H.edge[1] = b.y, H.edge[2] = b.z, H.edge[3] = b.w;
+}
+
 // Particle movers of the fast path.  move() takes the particle's offset x and velocity v and
 // the fields at x, leaves the new velocity in v and the end offset in xb; commit() stores
 // what the mover keeps besides the offset once the particle is known to stay in its tet.
@@ -710,16 +729,17 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
 #pragma unroll
     for (int k = 0; k < 10; ++k) agg[k] = 0.f;
     TetHot H;
+    // the record's first 32 bytes (node ids, edge ids 0..3) are needed only where a deposit
+    // is issued (the head lane of a run): they are loaded there (ids_of)
+    const bool in_win = (unsigned)(c - rec_lo) < (unsigned)rec_n;
     if (c >= 0) {
-        if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
-            const float4* r = reinterpret_cast<const float4*>(rec + (c - rec_lo) * kRecStride);
-            float4 t[8];
+        float4 t[8];
+        const float4* r = in_win ? reinterpret_cast<const float4*>(rec + (c - rec_lo) * kRecStride)
+                                 : reinterpret_cast<const float4*>(hot + c);
+        t[0] = t[1] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) t[k] = r[k];
-            memcpy(&H, t, sizeof(TetHot));
-        } else {
-            load_hot(hot, c, H);
-        }
+        for (int k = kIdChunks; k < 8; ++k) t[k] = in_win ? r[k] : __ldg(r + k);
+        memcpy(&H, t, sizeof(TetHot));
         float l[4];
         l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
         l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
@@ -765,6 +785,7 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             mv.commit(p);
             key = c;
             if (!aggregate) {
+                ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
 #pragma unroll
@@ -779,6 +800,7 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         int end;
         warp_run_reduce<float, 10>(key, agg, &heads, &end);
         if (((heads >> lane) & 1u) && key >= 0) {
+            ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
             for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
 #pragma unroll

@@ -62,6 +62,7 @@ class SolveInfo(ctypes.Structure):
 FP_SYS_NEWMARK, FP_SYS_GAUSS = 0, 1
 FP_PC_JACOBI, FP_PC_LEARNED, FP_PC_JACOBI_FP64, FP_PC_LEARNED_GAUSS = 0, 1, 2, 4
 FP_BC_PEC, FP_BC_NEUMANN = 0, 1
+FP_LEARNED_GUESS, FP_LEARNED_PRECOND = 0, 1
 EPS0 = 8.854_187_8128e-12
 MU0 = 1.256_637_062_12e-6
 
@@ -121,6 +122,9 @@ def lib():
             "fem_pic_field_poly": (I32, [P, I32, I32, D]),
             "fem_pic_whitney0_integrals": (I32, [P, P]),
             "fem_pic_learned_init": (I32, [P, ctypes.c_uint64, I32]),
+            "fem_pic_learned_init_model": (I32, [P, ctypes.c_uint64, I32, I32]),
+            "fem_pic_learned_build": (I32, [P, P]),
+            "fem_pic_learned_delta": (I32, [P, P, P, P]),
             "fem_pic_learned_select": (I32, [P, I32]),
             "fem_pic_learned_mode": (I32, [P, I32, I32]),
             "fem_pic_learned_samples": (I32, [P, P]),
@@ -502,6 +506,22 @@ def fem_pic_learned_select(h, system: int):
 
 def fem_pic_learned_init(h, seed: int = 0, sample_capacity: int = 64):
     _check(lib().fem_pic_learned_init(h, int(seed), int(sample_capacity)), h)
+
+
+def fem_pic_learned_init_model(h, seed: int = 0, sample_capacity: int = 64, model: int = FP_LEARNED_PRECOND):
+    _check(lib().fem_pic_learned_init_model(h, int(seed), int(sample_capacity), int(model)), h)
+
+
+def fem_pic_learned_build(h, stream=None):
+    _check(lib().fem_pic_learned_build(h, _stream(stream)), h)
+
+
+def fem_pic_learned_delta(h, nnz: int, n: int, device="cuda", stream=None):
+    """Delta~ per CSR entry of the selected system's operator and the network's static input."""
+    d = torch.empty(int(nnz), dtype=torch.float32, device=device)
+    x = torch.empty(int(n), dtype=torch.float32, device=device)
+    _check(lib().fem_pic_learned_delta(h, _ptr(d), _ptr(x), _stream(stream)), h)
+    return d, x
 
 
 def fem_pic_learned_mode(h, collect: bool, active: bool):
