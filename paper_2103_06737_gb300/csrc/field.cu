@@ -216,9 +216,11 @@ struct MixedArgs {
     double* out;
     int32_t* status;
     // learned preconditioner (null: off): z = D^-1 r + Dl r with Dl on the operator's SELL
-    // pattern (replaces the Chebyshev polynomial); lflag (may be null) is set to 1 when the
+    // pattern, BF16 (replaces the Chebyshev polynomial); with sm_l the block's slots of Dl are
+    // held in shared memory after the operator's; lflag (may be null) is set to 1 when the
     // solve fell back to Jacobi because r.z was not positive
-    const float* dl32;
+    const __nv_bfloat16* dl16;
+    int sm_l;
     int* lflag;
 };
 
@@ -227,6 +229,7 @@ struct SmemOp {
     const float* v;       // values, SELL order, slots [base, base + count) of the global layout
     const int16_t* d;     // column - row
     int64_t base;
+    const __nv_bfloat16* l;   // the learned preconditioner's values of the same slots (or null)
 };
 
 // row i of the FP32 operator times x: from shared memory (sm_slots > 0) or from the global
@@ -312,12 +315,41 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp
 // z = D^-1 r + Dl r for the rows [t0, r1) of this block (the learned preconditioner); the
 // product needs every block's r: one grid barrier first.  z is published by the caller's
 // next grid barrier.
-__device__ __forceinline__ void learned_apply(const MixedArgs& a, int64_t t0, int64_t r1, int64_t stride,
-                                              cg::grid_group& g) {
+__device__ __forceinline__ void learned_apply(const MixedArgs& a, const SmemOp& so, int64_t t0, int64_t r1,
+                                              int64_t stride, cg::grid_group& g) {
     g.sync();
+    if (so.l) {   // Dl and the column offsets from shared memory
+        for (int64_t i = t0; i < r1; i += stride) {
+            const int64_t sl = i >> 5;
+            const int64_t base = __ldg(a.S.ptr + sl) - so.base + (i & 31);
+            const int w = __ldg(a.S.w + sl);
+            float t = 0.f;
+            for (int j0 = 0; j0 < w; j0 += kSellChunk) {
+                int c[kSellChunk];
+                float lv[kSellChunk], xv[kSellChunk];
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) {
+                    const bool in = j0 + u < w;
+                    c[u] = in ? (int)i + so.d[base + 32 * (j0 + u)] : -1;
+                    lv[u] = in ? __bfloat162float(so.l[base + 32 * (j0 + u)]) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? __ldcg(a.r + c[u]) : 0.f;
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) t += lv[u] * xv[u];
+            }
+            a.z[i] = a.dinv32[i] * a.r[i] + t;
+        }
+        return;
+    }
     for (int64_t i = t0; i < r1; i += stride)
-        a.z[i] = a.dinv32[i] * a.r[i] + sell_row<float, float>(a.S, a.dl32, a.r, i);
+        a.z[i] = a.dinv32[i] * a.r[i] + sell_row<__nv_bfloat16, float>(a.S, a.dl16, a.r, i);
 }
+
+// Inner CG in the Chronopoulos-Gear form (one grid sum per iteration instead of two)
+#ifndef FP_CG_ONE_SUM
+#define FP_CG_ONE_SUM 0
+#endif
 
 template <int BS>
 __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed(MixedArgs a) {
@@ -333,7 +365,8 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
     // this block's slots of the FP32 operator into shared memory (whole 32-row slices)
     extern __shared__ __align__(16) unsigned char dsm[];
     SmemOp so{reinterpret_cast<const float*>(dsm),
-              reinterpret_cast<const int16_t*>(dsm + 4 * (size_t)a.sm_slots), 0};
+              reinterpret_cast<const int16_t*>(dsm + 4 * (size_t)a.sm_slots), 0,
+              a.sm_l && a.dl16 ? reinterpret_cast<const __nv_bfloat16*>(dsm + 6 * (size_t)a.sm_slots) : nullptr};
     if (a.sm_slots > 0) {
         const int64_t ns = (a.n + 31) >> 5, s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
         const int64_t b0 = r0 < r1 ? __ldg(a.S.ptr + s0) : 0;
@@ -341,9 +374,11 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
         so.base = b0;
         float* v = reinterpret_cast<float*>(dsm);
         int16_t* d = reinterpret_cast<int16_t*>(dsm + 4 * (size_t)a.sm_slots);
+        __nv_bfloat16* l = so.l ? reinterpret_cast<__nv_bfloat16*>(dsm + 6 * (size_t)a.sm_slots) : nullptr;
         for (int64_t k = threadIdx.x; k < b1 - b0; k += BS) {
             v[k] = __ldg(a.val32 + b0 + k);
             d[k] = __ldg(a.d16 + b0 + k);
+            if (l) l[k] = a.dl16[b0 + k];
         }
         __syncthreads();
     }
@@ -352,7 +387,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
     float* part2 = part1 + 3 * gridDim.x;                // 2 FP32 values per block
     int total = 0, outer = 0;
     double rr64 = 0.0, ref2 = 0.0, thr = 0.0;
-    bool use_l = a.dl32 != nullptr;   // every block takes the same fallback decision (grid sums)
+    bool use_l = a.dl16 != nullptr;   // every block takes the same fallback decision (grid sums)
     if (use_l && a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 0;
     for (;;) {
         // ---- outer residual in FP64: r = b - A x; its norm and the reference norm
@@ -384,7 +419,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             a.z[i] = a.dinv32[i] * ri;
         }
         if (use_l)
-            learned_apply(a, t0, r1, stride, g);
+            learned_apply(a, so, t0, r1, stride, g);
         else if (a.deg > 1)
             chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
         g.sync();
@@ -411,6 +446,63 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
         const double need = kInnerMargin * sqrt(thr / rr64);
         const float red = (float)(need > a.inner_tol ? need : a.inner_tol);
         const float ithr = red * red * u[2];
+#if FP_CG_ONE_SUM
+        // Chronopoulos-Gear form: one grid sum per iteration.  After the update of c and r
+        // and z = P(r), w = A z is formed behind a plain grid barrier, then r.z, r.r and z.w
+        // are summed together; beta = (r.z)/(r.z)_old, p.q = z.w - beta (r.z) / alpha_old
+        // (= p.A p), p = z + beta p, q = w + beta q (= A p).  w is kept in s (free between
+        // applications of the preconditioner).
+        float alpha = pq > 0.f ? rz / pq : 0.f;
+        for (;;) {
+            if (!(pq > 0.f) || total >= a.max_iter) break;
+            float v3[3] = {0.f, 0.f, 0.f};  // r.z, r.r, z.w
+            if (use_l) {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    a.r[i] -= alpha * a.q[i];
+                }
+                learned_apply(a, so, t0, r1, stride, g);
+            } else if (a.deg <= 1) {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    const float ri = a.r[i] - alpha * a.q[i];
+                    a.r[i] = ri;
+                    a.z[i] = a.dinv32[i] * ri;
+                }
+            } else {
+                for (int64_t i = t0; i < r1; i += stride) {
+                    a.c[i] += alpha * a.p[i];
+                    a.r[i] -= alpha * a.q[i];
+                }
+                chebyshev_apply<ProductChunk<BS>::value>(a, so, t0, r1, stride, g);
+            }
+            g.sync();   // z of every block before its product
+            for (int64_t i = t0; i < r1; i += stride) {
+                const float zi = a.z[i], ri = a.r[i];
+                const float w = row_product32<ProductChunk<BS>::value>(a, so, a.z, i);
+                a.s[i] = w;
+                v3[0] += ri * zi;
+                v3[1] += ri * ri;
+                v3[2] += zi * w;
+            }
+            grid_sum<BS, 3, float>(v3, part1, g, shf);
+            ++total;
+            if (!(v3[1] > ithr)) break;
+            if (use_l && !(v3[0] > 0.f)) {   // not positive on this r: keep c, Jacobi from here on
+                use_l = false;
+                if (a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 1;
+                break;
+            }
+            const float beta = v3[0] / rz;
+            pq = v3[2] - beta * v3[0] / alpha;
+            rz = v3[0];
+            alpha = pq > 0.f ? rz / pq : 0.f;
+            for (int64_t i = t0; i < r1; i += stride) {
+                a.p[i] = a.z[i] + beta * a.p[i];
+                a.q[i] = a.s[i] + beta * a.q[i];
+            }
+        }
+#else
         for (;;) {
             if (!(pq > 0.f) || total >= a.max_iter) break;
             const float alpha = rz / pq;
@@ -420,7 +512,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
                     a.c[i] += alpha * a.p[i];
                     a.r[i] -= alpha * a.q[i];
                 }
-                learned_apply(a, t0, r1, stride, g);
+                learned_apply(a, so, t0, r1, stride, g);
                 for (int64_t i = t0; i < r1; i += stride) {
                     const float ri = a.r[i];
                     w2[0] += ri * a.z[i];
@@ -470,6 +562,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             grid_sum<BS, 1, float>(u2, part1, g, shf);
             pq = u2[0];
         }
+#endif
         for (int64_t i = t0; i < r1; i += stride) a.x[i] += rnorm * f2d(a.c[i]);
         g.sync();
     }
@@ -657,16 +750,20 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
         }
         m.tol = tol, m.inner_tol = ctx->inner_tol, m.scale_vec = scale_vec, m.max_iter = max_iter, m.max_outer = 12;
         m.out = F->out + 4 * slot, m.status = ctx->d_status;
-        m.dl32 = learned_precond(F, system);
-        m.lflag = m.dl32 ? learned_flag(F, system) : nullptr;
+        m.dl16 = learned_precond(F, system);
+        m.lflag = m.dl16 ? learned_flag(F, system) : nullptr;
+        m.sm_l = 0;
         void* args[] = {&m};
         m.d16 = system == FP_SYS_NEWMARK ? F->se_d16 : F->sn_d16;
         m.sm_slots = F->sm_slots[system];
         m.slots_total = F->slots_total[system];
+        // the learned preconditioner's BF16 values join the operator in shared memory when
+        // the block's slots still fit (8 bytes per slot in all) with the launch co-resident
+        if (m.dl16 && m.sm_slots > 0) m.sm_l = F->sm_learned[system];
         PhaseTimer pt(ctx, ph, s);
         const int grid = system == FP_SYS_NEWMARK ? F->grid_e : F->grid_n;
         const int bs = system == FP_SYS_NEWMARK ? F->bs_e : F->bs_n;
-        const size_t smem = (size_t)m.sm_slots * 6;
+        const size_t smem = (size_t)m.sm_slots * (m.sm_l ? 8 : 6);
         if (system == FP_SYS_NEWMARK) {
             k_perm_gather<<<grid_of(ctx, F->ne), kBlock, 0, s>>>(F->perm_e, rhs, x, F->pb, F->px, F->ne);
             m.b = F->pb, m.x = F->px;
@@ -1189,6 +1286,13 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
         FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, bytes));
         if ((int64_t)per_sm * ctx->sm_count < grid) return FP_OK;
         F->sm_slots[sys] = (int)slots;
+        // room for the learned preconditioner's BF16 values beside them (8 bytes per slot)?
+        F->sm_learned[sys] = 0;
+        if ((size_t)slots * 8 <= kSmemOperatorBytes + 24 * 1024 && (size_t)slots * 8 + 4096 <= (size_t)optin) {
+            int per_sm8 = 0;
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k, bs, (size_t)slots * 8));
+            F->sm_learned[sys] = (int64_t)per_sm8 * ctx->sm_count >= grid ? 1 : 0;
+        }
         return FP_OK;
     };
 #ifndef FP_SMEM_OPERATOR

@@ -1,6 +1,8 @@
 // Internal declarations of the implicit field step (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace fempic {
@@ -64,6 +66,7 @@ struct FieldDev {
     int64_t sectors_e[2] = {0, 0};  // gathered 32-byte sectors per product: edge order, solver order
     int64_t slots_total[2] = {0, 0};
     int sm_slots[2] = {0, 0};
+    int sm_learned[2] = {0, 0};     // the learned preconditioner's values fit in shared memory too
     std::vector<int32_t> hptr[2];   // host copies of the SELL slice starts (Newmark, Gauss)
     double* red = nullptr;          // reduction partials
     double* out = nullptr;          // [8] solver outputs (iterations, rr, bb) of the last two solves
@@ -141,7 +144,7 @@ fp_status learned_guess(fem_pic* ctx, int sys, const double* rhs, double* x0, cu
 bool learned_active(const FieldDev* F, int sys);
 int* learned_flag(FieldDev* F, int sys);
 // the learned preconditioner's correction (solver SELL layout) when it is active and built, else null
-const float* learned_precond(const FieldDev* F, int sys);
+const __nv_bfloat16* learned_precond(const FieldDev* F, int sys);
 bool learned_precond_ready(const FieldDev* F, int sys);   // model FP_LEARNED_PRECOND, built
 int learned_model(const FieldDev* F, int sys);            // -1: no network
 void learned_set_active(FieldDev* F, int sys, bool on);

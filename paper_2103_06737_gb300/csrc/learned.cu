@@ -79,7 +79,8 @@ struct LearnedDev {
     float* gdel = nullptr;        // d loss / d Delta~ per CSR entry
     int32_t* tpos = nullptr;      // CSR index of the transposed entry
     float *rs = nullptr, *u = nullptr, *g = nullptr;
-    float* pre = nullptr;         // D^-1/2 Delta~ D^-1/2 in the mixed solver's SELL layout
+    __nv_bfloat16* pre = nullptr; // D^-1/2 Delta~ D^-1/2 in the mixed solver's SELL layout (BF16: the
+                                  // preconditioner need not be exact, and symmetric entries round alike)
     int64_t pre_slots = 0;
     int built = 0;                // pre holds the current weights' preconditioner
     int n_params() const { return model == 1 ? kNParams : kNParams0; }
@@ -726,7 +727,7 @@ __global__ void k_ls_build(const int32_t* __restrict__ sptr, const int32_t* __re
                            const int32_t* __restrict__ scol, const double* __restrict__ sval,
                            const int32_t* __restrict__ perm, const float* __restrict__ dis,
                            const __nv_bfloat16* __restrict__ H, const float* __restrict__ P,
-                           const uint8_t* __restrict__ fixed, int64_t n, float* __restrict__ out) {
+                           const uint8_t* __restrict__ fixed, int64_t n, __nv_bfloat16* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t nsl = (n + 31) / 32;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -781,7 +782,7 @@ __global__ void k_ls_build(const int32_t* __restrict__ sptr, const int32_t* __re
                     o = di * at * t * dj;
                 }
             }
-            out[k] = o;
+            out[k] = __float2bfloat16(o);
         }
     }
 }
@@ -928,7 +929,7 @@ bool learned_precond_ready(const FieldDev* F, int sys) {
     return L && L->model == 1 && L->built;
 }
 
-const float* learned_precond(const FieldDev* F, int sys) {
+const __nv_bfloat16* learned_precond(const FieldDev* F, int sys) {
     const LearnedDev* L = F ? F->learned[sys] : nullptr;
     return L && L->model == 1 && L->active && L->built ? L->pre : nullptr;
 }
