@@ -257,10 +257,12 @@ def mixed_solve_bytes(n_rows, nnz, inner_iters, outer, deg=1):
     return inner + start + resid
 
 
-def measured_traffic(kernel: str, workload: str):
+def measured_traffic(kernel: str, workload: str, iterations=None):
     """DRAM bytes per launch (read + write) of `kernel` from the ncu capture recorded in
     profiles/traffic.json, or None when there is none for this workload or any source file
-    the kernel is built from has changed since the capture (sha256 recorded with it)."""
+    the kernel is built from has changed since the capture (sha256 recorded with it).  A solver
+    record holds bytes per inner iteration (its launches' bytes over their iterations), scaled
+    here by this run's iterations per launch."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
@@ -275,6 +277,8 @@ def measured_traffic(kernel: str, workload: str):
                     return None
         except OSError:
             return None
+    if "dram_bytes_per_iteration" in rec:
+        return None if iterations is None else float(rec["dram_bytes_per_iteration"]) * float(iterations)
     return float(rec["dram_bytes_per_launch"])
 
 
@@ -507,6 +511,7 @@ def run_gpu(args):
         F.fem_pic_field_setup(lib.h, wl.dt)
         F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
         pdeg = [int(x) for x in (args.poly.split(",") + args.poly.split(","))[:2]]
+        pdeg_cfg = list(pdeg)     # as configured (the learned comparison may set a system to 1)
         prat = [float(x) for x in (args.poly_ratio.split(",") + args.poly_ratio.split(","))[:2]]
         F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
         F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], prat[1])
@@ -763,9 +768,11 @@ def run_gpu(args):
         flush_l2(k)
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")      # marks the timed steps for profilers
         a.record(stream)
         launches += step()
         z.record(stream)
+        torch.cuda.nvtx.range_pop()
         res_log[k].copy_(res)
         evs.append((a, z))
     th1 = time.perf_counter()
@@ -793,9 +800,11 @@ def run_gpu(args):
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
         pl = plan(state["i"])
+        torch.cuda.nvtx.range_push("eager_step")      # the per-kernel pass, for profilers
         a.record(stream)
         enqueue(pl)
         z.record(stream)
+        torch.cuda.nvtx.range_pop()
         advance(pl)
         state["i"] += 1
         push_ms.append((a, z))
@@ -924,8 +933,9 @@ def run_gpu(args):
         profiler on."""
         F.fem_pic_field_setup(lib.h, wl.dt, bc=F.FP_BC_NEUMANN)
         F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg[0], prat[0])
-        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg[1], prat[1])
+        # the learned networks belong to the PEC setup: this boundary runs the configured polynomials
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg_cfg[0], prat[0])
+        F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg_cfg[1], prat[1])
         state["precond"] = precond
         restore()
         st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
@@ -1088,7 +1098,8 @@ def run_gpu(args):
                         model += its * nz * 6
                     op_bytes = nz * 8 * 1.2          # FP32 SELL operator (value + column), ~1.2x padding
                     on_chip = op_bytes < L2_BYTES
-                    traffic = measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph, wl.name)
+                    traffic = measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph +
+                                               ("/learned" if lrn else ""), wl.name, its)
                     pc_name = ("learned preconditioner" if lrn else
                                f"Chebyshev-Jacobi degree {pdeg[k_sys]}" if pdeg[k_sys] > 1 else "Jacobi")
                     name = ("k_pcg_mixed (" + ph.split("_")[1] + f" system, FP32 inner PCG, {pc_name}, FP64 residual)"
@@ -1162,7 +1173,8 @@ def run_gpu(args):
                 "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
                 "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,
                 "initial_guess": "2E^n - E^(n-1) (Newmark), 0 (Gauss)",
-                "tol": args.tol, "newmark_iters_mean": statistics.mean(iters_n),
+                "tol": args.tol, "newmark_iters": iters_n, "gauss_iters": iters_g,
+                "newmark_iters_mean": statistics.mean(iters_n),
                 "gauss_iters_mean": statistics.mean(iters_g), "max_rel_res": max(relres),
                 "newmark_refinements_mean": statistics.mean(outer_n), "gauss_refinements_mean": statistics.mean(outer_g),
                 "n_edges": sizes["n_edges"], "n_nodes": sizes["n_nodes"]},
