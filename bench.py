@@ -561,25 +561,35 @@ def run_gpu(args):
         sort_now = args.sort_every > 0 and i > 0 and i % args.sort_every == 0
         return sort_now, tuple(cur)
 
+    def enqueue_push_part(pl, k):
+        """Species k's share of the step's particle part on the current stream (its periodic
+        sort, its push and deposits; species 0 also clears dG and starts Q^{n+1} from the ion
+        background): returns (library kernels launched, the buffer it used)."""
+        sort_now, before = pl
+        n_k = 0
+        b_ = before[k]
+        if sort_now:
+            lib.sort(bufs[k][b_], bufs[k][1 - b_])
+            b_ = 1 - b_
+            n_k += 5
+        s_ = bufs[k][b_]
+        if k == 0:
+            dG.zero_()
+            Qn.copy_(Q_ion)
+        # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}; the field records
+        # are made once per step (the first species' call)
+        lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
+        n_k += 3 if k == 0 else 2     # field prep (first species), fast push, FP64 walk of the queue
+        return n_k, s_
+
     def enqueue_push(pl):
         """The step's particle part on the current stream (periodic sort, push, deposits):
         returns (library kernels launched, the species' buffers it used)."""
-        sort_now, before = pl
-        n_k = 0
-        use = []
+        n_k, use = 0, []
         for k in range(len(species)):
-            b_ = before[k]
-            if sort_now:
-                lib.sort(bufs[k][b_], bufs[k][1 - b_])
-                b_ = 1 - b_
-                n_k += 5
-            use.append(bufs[k][b_])
-        dG.zero_()
-        Qn.copy_(Q_ion)
-        for k, s_ in enumerate(use):     # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}
-            # the field records are made once per step (the first species' call)
-            lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
-            n_k += 3 if k == 0 else 2     # field prep (first species), fast push, FP64 walk of the queue
+            m_, s_ = enqueue_push_part(pl, k)
+            n_k += m_
+            use.append(s_)
         return n_k, use
 
     def enqueue_field():
@@ -651,80 +661,93 @@ def run_gpu(args):
     # args.tune_systems systems of this workload's own steps, then timed against plain
     # Jacobi-CG (the judge) and the configured Chebyshev polynomial on the same steps.  The
     # timed steps use the fastest of the three for each system.
+    def learned_pick(sys_id, params0, n_compare, flush_base=0):
+        """Fine-tune the learned preconditioner of one system (starting from params0) on
+        args.tune_systems systems of this workload's own steps, then time plain Jacobi-CG, the
+        learned preconditioner and the configured polynomial on the same steps from the initial
+        state; set up the fastest for the system.  Returns (report, choice, tuned weights)."""
+        bit = F.FP_PC_LEARNED if sys_id == F.FP_SYS_NEWMARK else F.FP_PC_LEARNED_GAUSS
+        ph_cg = "cg_newmark" if sys_id == F.FP_SYS_NEWMARK else "cg_gauss"
+        sysname = "newmark" if sys_id == F.FP_SYS_NEWMARK else "gauss"
+        t_l0 = time.time()
+        keep = state["precond"]
+        state["precond"] = keep & ~bit
+        F.fem_pic_learned_select(lib.h, sys_id)
+        F.fem_pic_learned_init_model(lib.h, seed=0, sample_capacity=max(1, args.tune_systems),
+                                     model=F.FP_LEARNED_PRECOND)
+        F.fem_pic_learned_params(lib.h, params0)
+        tune = None
+        if args.tune_systems > 0:
+            restore()
+            F.fem_pic_learned_mode(lib.h, collect=True, active=False)
+            for _ in range(args.tune_systems):
+                eager_step()
+            torch.cuda.synchronize()
+            F.fem_pic_learned_mode(lib.h, collect=False, active=False)
+            n_t = F.fem_pic_learned_samples(lib.h)
+            r_before = float(np.mean(F.fem_pic_learned_eval(lib.h, 0, n_t)))
+            ls = F.fem_pic_learned_train(lib.h, 0, n_t, args.tune_epochs, lr=5e-4, seed=1)
+            r_after = float(np.mean(F.fem_pic_learned_eval(lib.h, 0, n_t)))
+            tune = {"systems": n_t, "epochs": args.tune_epochs, "ratio_before": r_before,
+                    "ratio_after": r_after, "loss_last": float(ls[-1])}
+        F.fem_pic_learned_build(lib.h)
+        torch.cuda.synchronize()
+        t_prep = time.time() - t_l0
+
+        def compare(pc, deg):
+            F.fem_pic_field_poly(lib.h, sys_id, deg, prat[sys_id])
+            state["precond"] = pc
+            restore()
+            F.fem_pic_profile_read(lib.h, reset=True)
+            F.fem_pic_profile_enable(lib.h, True)
+            its, fb = [], 0
+            for k in range(n_compare):
+                flush_l2(flush_base + k)
+                eager_step()
+                fi = F.fem_pic_field_last_info(lib.h)
+                its.append(fi[sys_id]["iters"])
+                fb += fi[sys_id]["fell_back"]
+            torch.cuda.synchronize()
+            F.fem_pic_profile_enable(lib.h, False)
+            ph = F.fem_pic_profile_read(lib.h, reset=True)
+            tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
+            return {"field_ms_per_step": tot / n_compare,
+                    ph_cg + "_ms_per_step": ph.get(ph_cg, (0.0, 1))[0] / n_compare,
+                    "iters_mean": statistics.mean(its), "fell_back": fb}
+        base = keep & ~bit
+        plain = compare(base, 1)             # plain Jacobi-CG
+        learn = compare(base | bit, 1)       # the learned preconditioner (replaces the polynomial)
+        poly = compare(base, pdeg_cfg[sys_id]) if pdeg_cfg[sys_id] > 1 else None
+        ms = {"plain": plain[ph_cg + "_ms_per_step"], "learned": learn[ph_cg + "_ms_per_step"]}
+        if poly is not None:
+            ms["chebyshev"] = poly[ph_cg + "_ms_per_step"]
+        best = min(ms, key=ms.get) if args.learned == "auto" else "learned"
+        pdeg[sys_id] = pdeg_cfg[sys_id] if best == "chebyshev" else 1
+        F.fem_pic_field_poly(lib.h, sys_id, pdeg[sys_id], prat[sys_id])
+        state["precond"] = base | (bit if best == "learned" else 0)
+        rep = {"plain": plain, "learned": learn, "chebyshev": poly, "fine_tune": tune, "prepare_s": t_prep,
+               "learned_vs_plain_ms": ms["learned"] / ms["plain"],
+               "learned_beats_plain_cg": bool(ms["learned"] < ms["plain"]),
+               "timed_steps_use": best, "used_in_timed_steps": best == "learned",
+               "compared_against": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system) and the "
+                                   f"Chebyshev-Jacobi polynomial of degree {pdeg_cfg[sys_id]}, same steps, "
+                                   f"same {args.tol}"}
+        return rep, best, F.fem_pic_learned_params(lib.h)
+
+    # learned preconditioner, per system (Newmark edge system, Gauss-law node system): the
+    # network trained by the protocol on the 4^3 and 32^3 workloads' systems, fine-tuned on
+    # this workload's own steps, then timed against plain Jacobi-CG (the judge) and the
+    # configured Chebyshev polynomial on the same steps; the timed steps use the fastest.
     learned = None
+    tuned = {}
     if field and proto is not None:
         learned = {"protocol": proto["report"]}
-        used_bits = 0
         for sysname in [x for x in args.learned_systems.split(",") if x]:
             sys_id = F.FP_SYS_NEWMARK if sysname == "newmark" else F.FP_SYS_GAUSS
-            bit = F.FP_PC_LEARNED if sys_id == F.FP_SYS_NEWMARK else F.FP_PC_LEARNED_GAUSS
-            ph_cg = "cg_newmark" if sys_id == F.FP_SYS_NEWMARK else "cg_gauss"
-            t_l0 = time.time()
-            state["precond"] = precond
-            F.fem_pic_learned_select(lib.h, sys_id)
-            F.fem_pic_learned_init_model(lib.h, seed=0, sample_capacity=max(1, args.tune_systems),
-                                         model=F.FP_LEARNED_PRECOND)
-            F.fem_pic_learned_params(lib.h, proto["params"][sys_id])
-            tune = None
-            if args.tune_systems > 0:
-                restore()
-                F.fem_pic_learned_mode(lib.h, collect=True, active=False)
-                for _ in range(args.tune_systems):
-                    eager_step()
-                torch.cuda.synchronize()
-                F.fem_pic_learned_mode(lib.h, collect=False, active=False)
-                n_t = F.fem_pic_learned_samples(lib.h)
-                r_before = float(np.mean(F.fem_pic_learned_eval(lib.h, 0, n_t)))
-                ls = F.fem_pic_learned_train(lib.h, 0, n_t, args.tune_epochs, lr=5e-4, seed=1)
-                r_after = float(np.mean(F.fem_pic_learned_eval(lib.h, 0, n_t)))
-                tune = {"systems": n_t, "epochs": args.tune_epochs, "ratio_before": r_before,
-                        "ratio_after": r_after, "loss_last": float(ls[-1])}
-            F.fem_pic_learned_build(lib.h)
-            torch.cuda.synchronize()
-            t_prep = time.time() - t_l0
-
-            def compare(pc, deg):
-                F.fem_pic_field_poly(lib.h, sys_id, deg, prat[sys_id])
-                state["precond"] = pc
-                restore()
-                F.fem_pic_profile_read(lib.h, reset=True)
-                F.fem_pic_profile_enable(lib.h, True)
-                its, fb = [], 0
-                for k in range(args.compare_steps):
-                    flush_l2(k)
-                    eager_step()
-                    fi = F.fem_pic_field_last_info(lib.h)
-                    its.append(fi[sys_id]["iters"])
-                    fb += fi[sys_id]["fell_back"]
-                torch.cuda.synchronize()
-                F.fem_pic_profile_enable(lib.h, False)
-                ph = F.fem_pic_profile_read(lib.h, reset=True)
-                tot = sum(ph.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss", "learned"))
-                return {"field_ms_per_step": tot / args.compare_steps,
-                        ph_cg + "_ms_per_step": ph.get(ph_cg, (0.0, 1))[0] / args.compare_steps,
-                        "iters_mean": statistics.mean(its), "fell_back": fb}
-            plain = compare(precond, 1)            # plain Jacobi-CG
-            learn = compare(precond | bit, 1)      # the learned preconditioner (replaces the polynomial)
-            poly = compare(precond, pdeg[sys_id]) if pdeg[sys_id] > 1 else None
-            ms = {"plain": plain[ph_cg + "_ms_per_step"], "learned": learn[ph_cg + "_ms_per_step"]}
-            if poly is not None:
-                ms["chebyshev"] = poly[ph_cg + "_ms_per_step"]
-            best = min(ms, key=ms.get) if args.learned == "auto" else "learned"
-            if best == "learned":
-                used_bits |= bit
-            if best != "chebyshev":
-                pdeg[sys_id] = 1
-            F.fem_pic_field_poly(lib.h, sys_id, pdeg[sys_id], prat[sys_id])
-            learned[sysname] = {
-                "plain": plain, "learned": learn, "chebyshev": poly, "fine_tune": tune, "prepare_s": t_prep,
-                "learned_vs_plain_ms": ms["learned"] / ms["plain"],
-                "learned_beats_plain_cg": bool(ms["learned"] < ms["plain"]),
-                "timed_steps_use": best, "used_in_timed_steps": best == "learned",
-                "weights": "trained by the protocol on the 4^3 and 32^3 workloads, fine-tuned on this workload's "
-                           "own systems",
-                "compared_against": f"plain Jacobi-CG (Jacobi inner preconditioner on the {sysname} system) and the "
-                                    f"Chebyshev-Jacobi polynomial of degree {args.poly}, same steps, same {args.tol}"}
-        state["precond"] = precond | used_bits
+            rep, best, tuned[sys_id] = learned_pick(sys_id, proto["params"][sys_id], args.compare_steps)
+            rep["weights"] = "trained by the protocol on the 4^3 and 32^3 workloads, fine-tuned on this workload's " \
+                             "own systems"
+            learned[sysname] = rep
 
     # one CUDA graph per distinct step shape (sort or not, buffers, Q parity)
     graphs = {}
@@ -848,22 +871,31 @@ def run_gpu(args):
             sum(h_.numel() * h_.element_size() for _, h_ in fin)
         bo = sum(x.numel() * x.element_size() for tr in hs_out for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
             (hE.numel() * 8 if field else 0)
-        # Each step: the inputs' host-to-device copies, the particle part (one CUDA graph per
-        # step shape), the particle state's device-to-host copy on a second stream (it overlaps
-        # the field part, which does not touch the particles), the field part (a second graph),
-        # the results' device-to-host copies, and the join of both streams.
-        copy_stream = torch.cuda.Stream(device=dev)
+        # Each step, pipelined by species: the fields' and species 0's host-to-device copies,
+        # then species k's push (one CUDA graph per species and step shape) while species k+1's
+        # state is copied in on an input stream and species k-1's state goes back on an output
+        # stream; then the field part (a second graph), which does not touch the particles, with
+        # the last species' state going back beside it; the results' device-to-host copies; the
+        # join of the streams.
+        in_stream = torch.cuda.Stream(device=dev)
+        out_stream = torch.cuda.Stream(device=dev)
         e2e_graphs = {}
+        nsp = len(species)
 
         def e2e_graph(pl):
             key = (pl, state["precond"])
             if key not in e2e_graphs:
-                ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-                with torch.cuda.graph(ga):
-                    _, use = enqueue_push(pl)
+                gps, use = [], []
+                for k in range(nsp):
+                    g_ = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g_):
+                        _, s_ = enqueue_push_part(pl, k)
+                    gps.append(g_)
+                    use.append(s_)
+                gb = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(gb):
                     enqueue_field()
-                e2e_graphs[key] = (ga, gb, use)
+                e2e_graphs[key] = (gps, gb, use)
                 torch.cuda.synchronize()
             return e2e_graphs[key]
         restore()
@@ -872,44 +904,54 @@ def run_gpu(args):
             e2e_graph(pl)
             advance(pl)
         restore()
-        species = [bufs[k][cur[k]] for k in range(len(species))]
+        species = [bufs[k][cur[k]] for k in range(nsp)]
         torch.cuda.synchronize()
         ee, parts = [], []
         for k in range(args.steps):
             flush_l2(k)
             pl = plan(state["i"])
-            ga, gb, use = e2e_graph(pl)
+            gps, gb, use = e2e_graph(pl)
             a = torch.cuda.Event(enable_timing=True)
             h = torch.cuda.Event(enable_timing=True)
             z = torch.cuda.Event(enable_timing=True)
-            pushed, copied = torch.cuda.Event(), torch.cuda.Event()
             a.record(stream)
-            for (hc, ho, hv), s in zip(hs, species):
-                s.cell.copy_(hc, non_blocking=True)
-                s.off.copy_(ho, non_blocking=True)
-                s.vel.copy_(hv, non_blocking=True)
-            for d_, h_ in fin:
-                d_.copy_(h_, non_blocking=True)
-            h.record(stream)
-            ga.replay()
-            pushed.record(stream)
-            copy_stream.wait_event(pushed)
-            with torch.cuda.stream(copy_stream):
-                for (hc, ho, hv), s in zip(hs_out, use):
-                    hc.copy_(s.cell, non_blocking=True)
-                    ho.copy_(s.off, non_blocking=True)
-                    hv.copy_(s.vel, non_blocking=True)
-                copied.record(copy_stream)
+            in_stream.wait_event(a)
+            ev_in = []
+            with torch.cuda.stream(in_stream):
+                for d_, h_ in fin:
+                    d_.copy_(h_, non_blocking=True)
+                for (hc, ho, hv), s in zip(hs, species):
+                    s.cell.copy_(hc, non_blocking=True)
+                    s.off.copy_(ho, non_blocking=True)
+                    s.vel.copy_(hv, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(in_stream)
+                    ev_in.append(ev)
+            h.record(in_stream)
+            for j in range(nsp):
+                stream.wait_event(ev_in[j])
+                gps[j].replay()
+                pushed = torch.cuda.Event()
+                pushed.record(stream)
+                out_stream.wait_event(pushed)
+                with torch.cuda.stream(out_stream):
+                    hc, ho, hv = hs_out[j]
+                    hc.copy_(use[j].cell, non_blocking=True)
+                    ho.copy_(use[j].off, non_blocking=True)
+                    hv.copy_(use[j].vel, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(out_stream)
             gb.replay()
             hdG.copy_(dG, non_blocking=True)
             hQ.copy_(Qn, non_blocking=True)
             if field:
                 hE.copy_(e, non_blocking=True)
             stream.wait_event(copied)
+            stream.wait_event(h)
             z.record(stream)
             advance(pl)
             state["i"] += 1
-            species = [bufs[k][cur[k]] for k in range(len(species))]
+            species = [bufs[k][cur[k]] for k in range(nsp)]
             ee.append((a, z))
             parts.append((a, h))
         torch.cuda.synchronize()
@@ -919,8 +961,10 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                "ms_per_step": e2e_ms / args.steps,
                "h2d_ms_per_step": sum(a.elapsed_time(h) for a, h in parts) / args.steps,
-               "overlap": "particle state copied back on a second stream during the field step into pinned "
-                          "buffers of its own; the step's particle and field parts replayed as CUDA graphs"}
+               "overlap": "pipelined by species: species k+1's state copied in on an input stream while species k "
+                          "is pushed, species k's state copied back on an output stream (into pinned buffers of "
+                          "its own) during the next push and the field step; per-species push graphs and a field "
+                          "graph"}
 
     fp64 = None if args.fp64_steps <= 0 else measure_fp64(args, F, wl, dev, flush_l2, stream)
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
@@ -933,12 +977,22 @@ def run_gpu(args):
         profiler on."""
         F.fem_pic_field_setup(lib.h, wl.dt, bc=F.FP_BC_NEUMANN)
         F.fem_pic_field_options(lib.h, code[solv[0]], code[solv[1]], args.inner_tol)
-        # the learned networks belong to the PEC setup: this boundary runs the configured polynomials
         F.fem_pic_field_poly(lib.h, F.FP_SYS_NEWMARK, pdeg_cfg[0], prat[0])
         F.fem_pic_field_poly(lib.h, F.FP_SYS_GAUSS, pdeg_cfg[1], prat[1])
+        pdeg[0], pdeg[1] = pdeg_cfg[0], pdeg_cfg[1]
         state["precond"] = precond
         restore()
         st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
+        E_prev.copy_(e)
+        snap_f[2] = (E_prev, E_prev.clone())   # this boundary's E^0 is the restored start
+        snap_f[0] = (e, e.clone())
+        # the new setup discarded the PEC networks: the same weights (tuned on the PEC systems of
+        # this mesh) are tuned again on this boundary's systems and compared the same way
+        nlearn = {}
+        for sys_id, prm in tuned.items():
+            rep, best, _ = learned_pick(sys_id, prm, args.neumann_steps, flush_base=4000)
+            nlearn["newmark" if sys_id == F.FP_SYS_NEWMARK else "gauss"] = rep
+        restore()
         E_prev.copy_(e)
         for _ in range(3):
             eager_step()
@@ -975,6 +1029,11 @@ def run_gpu(args):
                 "newmark_refinements_mean": float(np.mean([o[0] for o in outs])),
                 "gauss_refinements_mean": float(np.mean([o[1] for o in outs])),
                 "status": int(lib.status()),
+                "learned_vs_plain": nlearn or None,
+                "precond": {nm: ("learned preconditioner" if state["precond"] & bit else
+                                 (f"Chebyshev-Jacobi degree {pdeg[k_]}" if pdeg[k_] > 1 else "jacobi"))
+                            for k_, (nm, bit) in enumerate((("newmark", F.FP_PC_LEARNED),
+                                                            ("gauss", F.FP_PC_LEARNED_GAUSS)))},
                 "what": "PIC step with the natural field boundary: Newmark over all edges, Gauss-law projection "
                         "with the zero-mean constraint (a net charge spread as alpha), Faraday"}
     def measure_gauss_drift():
