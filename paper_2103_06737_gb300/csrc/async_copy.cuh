@@ -1,5 +1,6 @@
-// Bulk asynchronous copies (the TMA engine's non-tensor mode) into shared memory, completed
-// on an mbarrier, with bounded waits.  sm_90 and later; written for sm_103a.
+// Bulk asynchronous copies (the TMA engine's non-tensor mode): into shared memory, completed
+// on an mbarrier, with bounded waits; out of shared memory, completed through bulk
+// async-groups.  sm_90 and later; written for sm_103a.
 #pragma once
 
 #include <cstdint>
@@ -42,6 +43,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+
+// shared -> global bulk copy, completed through the issuing thread's bulk async-groups;
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// closes the bulk async-group of the copies issued since the last commit
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// waits until every committed bulk group has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// waits until every committed bulk group has completed (its writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;

@@ -131,6 +131,7 @@ struct fem_pic {
     // warp-specialised Boris push, warp-specialised Adams push
     int tma_blocks_per_sm = 0;
     int ws_blocks_per_sm = 0;
+    int run_blocks_per_sm = 0;
     int ws_adams_blocks_per_sm = 0;
     uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch

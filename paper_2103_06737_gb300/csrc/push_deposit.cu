@@ -707,6 +707,54 @@ struct AdamsMover32 {
 // piece stays in the tet and is deposited here (warp-reduced).  Otherwise the
 // particle index is queued for the FP64 walk (velocity already updated).
 //
+// fast_core is the per-particle arithmetic: it moves the particle (the mover stores what it
+// keeps) and returns kFastStay with the end offset xb and the 10 deposit values (6 W1 edge
+// values, 4 W0 node charges) when the piece stays in the tet, kFastWalk when the FP64 walk
+// has to decide, kFastNonFinite when the state or the push is not finite.
+enum { kFastStay = 0, kFastWalk = 1, kFastNonFinite = 2 };
+
+template <class Mover>
+__device__ __forceinline__ int fast_core(const TetHot& H, const float x[3], float v[3], int64_t p, Mover& mv,
+                                         float w, float xb[3], float agg[10]) {
+    float l[4];
+    l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
+    l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
+    l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
+    l[0] = 1.f - l[1] - l[2] - l[3];
+    float E[3], B[3];
+    hot_fields(H, x, E, B);
+    float dx[3], d[4];
+    mv.move(p, x, v, E, B, xb);
+    const bool finite = finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]) && finite_bits(xb[0]) &&
+                        finite_bits(xb[1]) && finite_bits(xb[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dx[i] = xb[i] - x[i];
+    d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
+    d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
+    d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
+    d[0] = -(d[1] + d[2] + d[3]);
+    // rounding bound of l^b in FP32 (with the FP32 copy of the gradients):
+    // 1 + sum_k |g_k| (|x_k%3| + |dx_k%3|) <= 1 + (sum |g|) max_i (|x_i| + |dx_i|)
+    const float xm = fmaxf(fmaxf(fabsf(x[0]) + fabsf(dx[0]), fabsf(x[1]) + fabsf(dx[1])),
+                           fabsf(x[2]) + fabsf(dx[2]));
+    const float margin = fmaf(H.gsum, xm, 1.f) * (1.f / 65536.f);
+    float lbmin = l[0] + d[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
+    // a non-finite state or push (NaN/Inf velocity, offset or field) removes the particle
+    if (!finite) return kFastNonFinite;
+    if (!(lbmin >= margin)) return kFastWalk;
+    agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
+    agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
+    agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
+    agg[3] = w * (l[1] * d[2] - l[2] * d[1]);
+    agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
+    agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
+    return kFastStay;
+}
+
 // One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
 // it (the deposit reduction is a warp collective).  Returns true when the particle has to
 // go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
@@ -740,45 +788,13 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
 #pragma unroll
         for (int k = kIdChunks; k < 8; ++k) t[k] = in_win ? r[k] : __ldg(r + k);
         memcpy(&H, t, sizeof(TetHot));
-        float l[4];
-        l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
-        l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
-        l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
-        l[0] = 1.f - l[1] - l[2] - l[3];
-        float E[3], B[3];
-        hot_fields(H, x, E, B);
-        float xb[3], dx[3], d[4];
-        mv.move(p, x, v, E, B, xb);
-        const bool finite = finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]) && finite_bits(xb[0]) &&
-                            finite_bits(xb[1]) && finite_bits(xb[2]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dx[i] = xb[i] - x[i];
-        d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
-        d[2] = H.g[3] * dx[0] + H.g[4] * dx[1] + H.g[5] * dx[2];
-        d[3] = H.g[6] * dx[0] + H.g[7] * dx[1] + H.g[8] * dx[2];
-        d[0] = -(d[1] + d[2] + d[3]);
-        // rounding bound of l^b in FP32 (with the FP32 copy of the gradients):
-        // 1 + sum_k |g_k| (|x_k%3| + |dx_k%3|) <= 1 + (sum |g|) max_i (|x_i| + |dx_i|)
-        const float xm = fmaxf(fmaxf(fabsf(x[0]) + fabsf(dx[0]), fabsf(x[1]) + fabsf(dx[1])),
-                               fabsf(x[2]) + fabsf(dx[2]));
-        const float margin = fmaf(H.gsum, xm, 1.f) * (1.f / 65536.f);
-        float lbmin = l[0] + d[0];
-#pragma unroll
-        for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
-        if (!finite) {
-            // a non-finite state or push (NaN/Inf velocity, offset or field): the particle is
-            // removed with nothing deposited, and the status word says so
+        float xb[3];
+        const int r3 = fast_core(H, x, v, p, mv, w, xb, agg);
+        if (r3 == kFastNonFinite) {
+            // the particle is removed with nothing deposited, and the status word says so
             atomicOr(status, ST_NONFINITE);
             cell[p] = -1;
-        } else if (lbmin >= margin) {
-            agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
-            agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
-            agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
-            agg[3] = w * (l[1] * d[2] - l[2] * d[1]);
-            agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
-            agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
+        } else if (r3 == kFastStay) {
             off[p] = xb[0];
             off[n + p] = xb[1];
             off[2 * n + p] = xb[2];
@@ -1240,6 +1256,342 @@ __global__ void __launch_bounds__(kWsThreads, WsMinBlocks<MA>::value) k_push_ws3
     }
 }
 
+// ------------------------------------------------------------------ run-summing push
+// Boris variant of k_push_ws32 in which each consumer lane takes kRunK consecutive particles
+// of the tile (lane l of consumer warp w: tile positions (32 w + l) kRunK + i, i < kRunK)
+// instead of one particle in 32.  In cell-sorted order consecutive particles mostly share a
+// tet, so a lane sums its deposit values in registers, re-reads the tet's record only where
+// the tet changes, and issues the 10 atomics of a run once; the warp joins the runs that
+// cross lane boundaries once per chunk (lane l+1's first run into lane l's last, then the
+// runs of equal tets over consecutive lanes), not once per particle.  The deposits are the
+// same sums, grouped differently (FP32 atomics: the order of addition is not fixed anyway).
+// kRunK is odd, so the lanes' strided shared-memory accesses hit 32 distinct banks.  The new
+// offsets and velocities are written back into the staged tile, which the producer copies
+// out with bulk copies after the consumers are done.  Stage layout, barriers, bounded waits
+// and the queue of deferred particles are those of k_push_ws32.
+#ifndef FP_RUN_K
+#define FP_RUN_K 3
+#endif
+#ifndef FP_RUN_CONSUMERS
+#define FP_RUN_CONSUMERS 7
+#endif
+#ifndef FP_RUN_REC
+#define FP_RUN_REC 96
+#endif
+#ifndef FP_RUN_MIN_BLOCKS
+#define FP_RUN_MIN_BLOCKS 3
+#endif
+#ifndef FP_RUN_STAGES
+#define FP_RUN_STAGES 2
+#endif
+constexpr int kRunK = FP_RUN_K;
+static_assert(kRunK % 2 == 1, "an odd chunk keeps the strided shared-memory accesses free of bank conflicts");
+constexpr int kRunConsumers = FP_RUN_CONSUMERS;
+constexpr int kRunThreads = 32 * (kRunConsumers + 1);
+constexpr int kRunTile = 32 * kRunK * kRunConsumers;
+constexpr int kRunStages = FP_RUN_STAGES;
+constexpr int kRunSlot = kRunTile * 4;
+constexpr int kRunStageBytes = 7 * kRunSlot;
+constexpr int kRunRecMax = FP_RUN_REC;
+constexpr int kRunRecBytes = kRunRecMax * kRecStride;
+constexpr int kRunSmem = kRunStages * (kRunStageBytes + kRunRecBytes);
+static_assert(kRunSlot % 16 == 0 && kRunStageBytes % 16 == 0 && kRunRecBytes % 16 == 0, "bulk copy alignment");
+
+// the 10 atomics of one run: node ids and edge ids from record c (shared window or global)
+__device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
+                                          int rec_n, int c, const float a[10], float* __restrict__ dG,
+                                          float* __restrict__ Q) {
+    int4 nd, e03, e45;
+    if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
+        const int4* r = reinterpret_cast<const int4*>(rec + (c - rec_lo) * kRecStride);
+        nd = r[0];
+        e03 = r[1];
+        e45 = r[2];
+    } else {
+        const int4* r = reinterpret_cast<const int4*>(hot + c);
+        nd = __ldg(r);
+        e03 = __ldg(r + 1);
+        e45 = __ldg(r + 2);
+    }
+    atomicAdd(dG + e03.x, a[0]);
+    atomicAdd(dG + e03.y, a[1]);
+    atomicAdd(dG + e03.z, a[2]);
+    atomicAdd(dG + e03.w, a[3]);
+    atomicAdd(dG + e45.x, a[4]);
+    atomicAdd(dG + e45.y, a[5]);
+    atomicAdd(Q + nd.x, a[6]);
+    atomicAdd(Q + nd.y, a[7]);
+    atomicAdd(Q + nd.z, a[8]);
+    atomicAdd(Q + nd.w, a[9]);
+}
+
+// Boris with the new velocity stored into the staged tile (position j of its planes)
+struct BorisStaged {
+    float h, dt;
+    float* v0;
+    float* v1;
+    float* v2;
+    __device__ __forceinline__ void move(int64_t j, const float x[3], float v[3], const float E[3],
+                                         const float B[3], float xb[3]) {
+        boris<float>(v, E, B, h);
+        v0[j] = v[0];
+        v1[j] = v[1];
+        v2[j] = v[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xb[i] = step_pos(x[i], dt, v[i]);
+    }
+};
+
+template <int Tile>
+__device__ __forceinline__ void stage_issue(unsigned char* stage, uint64_t* bar, int t, const int32_t* cell,
+                                            const float* off, const float* vel, int64_t n) {
+    constexpr int kSlot = Tile * 4;
+    const int64_t p0 = (int64_t)t * Tile;
+    const uint32_t bytes = 4u * (uint32_t)min((int64_t)Tile, n - p0);
+    mbar_arrive_expect_tx(bar, 7u * bytes);
+    bulk_g2s(stage, cell + p0, bytes, bar);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (1 + k) * kSlot, off + k * n + p0, bytes, bar);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kSlot, vel + k * n + p0, bytes, bar);
+}
+
+__global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
+    const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off, float* __restrict__ vel,
+    int64_t n, int32_t nt, float h, float dt, double qw, int aggregate, float* __restrict__ dG,
+    float* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
+    int32_t* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kRunStages], empty[kRunStages], recb[kRunStages];
+    __shared__ int rec_lo[kRunStages], rec_n[kRunStages];
+    __shared__ int32_t queue[kRunStages][kRunTile];
+    __shared__ int qn[kRunStages];
+    unsigned char* recs = smem + kRunStages * kRunStageBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (int)((n + kRunTile - 1) / kRunTile);
+    const int G = gridDim.x;
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + G - 1) / G : 0;   // tiles of this block
+    if (tid == 0) {
+        for (int s = 0; s < kRunStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kRunConsumers);
+            mbar_init(&recb[s], 1);
+            qn[s] = 0;
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == kRunConsumers) {
+        // ---------------- producer
+        if (lane != 0) return;
+        int issued = 0, recs_issued = 0;
+        bool failed = false;
+        for (int k = 0; k < kRunStages && k < mine; ++k, ++issued)
+            stage_issue<kRunTile>(smem + k * kRunStageBytes, &full[k], blockIdx.x + k * G, cell, off, vel, n);
+        // after the consumers of tile k are done: its new offsets and velocities out, its queue
+        // flushed, its stage refilled once the copies out have read it
+        auto retire = [&](int k) -> bool {
+            const int sk = k % kRunStages;
+            if (!mbar_wait_bounded(&empty[sk], (uint32_t)((k / kRunStages) & 1), kTmaWaitNs)) return false;
+            unsigned char* stg = smem + sk * kRunStageBytes;
+            const int64_t p0 = (int64_t)(blockIdx.x + k * G) * kRunTile;
+            const uint32_t bytes = 4u * (uint32_t)min((int64_t)kRunTile, n - p0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) bulk_s2g(off + c * n + p0, stg + (1 + c) * kRunSlot, bytes);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) bulk_s2g(vel + c * n + p0, stg + (4 + c) * kRunSlot, bytes);
+            bulk_commit();
+            const int m = qn[sk];
+            if (m > 0) {
+                const int base = atomicAdd(slow_count, m);
+                for (int i = 0; i < m; ++i) slow_idx[base + i] = queue[sk][i];
+            }
+            qn[sk] = 0;
+            if (k + kRunStages < mine) {
+                bulk_wait_read_all();
+                fence_proxy_async_smem();
+                stage_issue<kRunTile>(stg, &full[sk], blockIdx.x + (k + kRunStages) * G, cell, off, vel, n);
+                ++issued;
+            }
+            return true;
+        };
+        for (int it = 0; it < mine && !failed; ++it) {
+            const int sk = it % kRunStages;
+            if (!mbar_wait_bounded(&full[sk], (uint32_t)((it / kRunStages) & 1), kTmaWaitNs)) {
+                failed = true;
+                break;
+            }
+            // record window: the tile's tets from first to last when they fit (cell-sorted
+            // tiles), else kRunRecMax tets around the middle particle's
+            const int64_t p0 = (int64_t)(blockIdx.x + it * G) * kRunTile;
+            const int cn = (int)min((int64_t)kRunTile, n - p0);
+            const int32_t* sc = reinterpret_cast<const int32_t*>(smem + sk * kRunStageBytes);
+            const int c0 = sc[0], c1 = sc[cn - 1], cm = sc[cn / 2];
+            int nn = 0, lo = 0;
+            if (c0 >= 0 && c1 < nt && c0 <= c1 && c1 - c0 < kRunRecMax) {
+                lo = c0;
+                nn = c1 - c0 + 1;
+            } else if (cm >= 0 && cm < nt) {
+                nn = min(kRunRecMax, nt);
+                lo = min(max(cm - kRunRecMax / 2, 0), nt - nn);
+            }
+            rec_lo[sk] = lo;
+            rec_n[sk] = nn;
+            if (nn > 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&recb[sk], (uint32_t)nn * (uint32_t)sizeof(TetHot));
+                for (int k = 0; k < nn; ++k)
+                    bulk_g2s(recs + sk * kRunRecBytes + k * kRecStride, hot + lo + k, (uint32_t)sizeof(TetHot),
+                             &recb[sk]);
+            } else {
+                mbar_arrive(&recb[sk]);
+            }
+            ++recs_issued;
+            if (it >= 1 && !retire(it - 1)) failed = true;
+        }
+        if (!failed && mine > 0 && !retire(mine - 1)) failed = true;
+        if (failed) {
+            atomicOr(status, ST_TIMEOUT);
+            // wait (bounded) for the copies still in flight before leaving
+            for (int k = 0; k < issued; ++k)
+                mbar_wait_bounded(&full[k % kRunStages], (uint32_t)((k / kRunStages) & 1), kTmaWaitNs);
+            for (int k = 0; k < recs_issued; ++k)
+                mbar_wait_bounded(&recb[k % kRunStages], (uint32_t)((k / kRunStages) & 1), kTmaWaitNs);
+        }
+        bulk_wait_all();
+        return;
+    }
+    // ---------------- consumers
+    const float w = (float)qw;
+    const int jb = (warp * 32 + lane) * kRunK;
+    for (int it = 0; it < mine; ++it) {
+        const int sk = it % kRunStages;
+        const uint32_t par = (uint32_t)((it / kRunStages) & 1);
+        if (!mbar_wait_bounded(&full[sk], par, kTmaWaitNs) || !mbar_wait_bounded(&recb[sk], par, kTmaWaitNs)) {
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        const int rlo = rec_lo[sk], rn = rec_n[sk];
+        unsigned char* st = smem + sk * kRunStageBytes;
+        const unsigned char* rec = recs + sk * kRunRecBytes;
+        const int32_t* sc = reinterpret_cast<const int32_t*>(st);
+        float* sx[3];
+        float* sv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sx[k] = reinterpret_cast<float*>(st + (1 + k) * kRunSlot);
+            sv[k] = reinterpret_cast<float*>(st + (4 + k) * kRunSlot);
+        }
+        BorisStaged mv{h, dt, sv[0], sv[1], sv[2]};
+        const int64_t p0 = (int64_t)(blockIdx.x + it * G) * kRunTile;
+        const int cnt = (int)min((int64_t)kRunTile, n - p0);
+        // the run being summed (tet cur; live once a particle of it stayed in its tet), the
+        // lane's first run once it has ended (tet hcell), and the tet whose record is in H
+        int cur = -1, hcell = -1, hc = -1;
+        bool first = true, live = false;
+        float acc[10], head[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = head[k] = 0.f;
+        TetHot H;
+#pragma unroll 1
+        for (int i = 0; i < kRunK; ++i) {
+            const int j = jb + i;
+            int c = -1;
+            float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+            if (j < cnt) {
+                c = sc[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    x[k] = sx[k][j];
+                    v[k] = sv[k][j];
+                }
+            }
+            if (c >= nt) {
+                atomicOr(status, ST_INVAL);
+                c = -1;
+            }
+            bool slow = false;
+            if (c >= 0) {
+                if (c != hc) {
+                    // gradients and field coefficients (record chunks 2..7); the ids are read
+                    // where a run is flushed
+                    float4 t[8];
+                    t[0] = t[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if ((unsigned)(c - rlo) < (unsigned)rn) {
+                        const float4* r = reinterpret_cast<const float4*>(rec + (c - rlo) * kRecStride);
+#pragma unroll
+                        for (int k = 2; k < 8; ++k) t[k] = r[k];
+                    } else {
+                        const float4* r = reinterpret_cast<const float4*>(hot + c);
+#pragma unroll
+                        for (int k = 2; k < 8; ++k) t[k] = __ldg(r + k);
+                    }
+                    memcpy(&H, t, sizeof(TetHot));
+                    hc = c;
+                }
+                if (aggregate && c != cur) {
+                    // a new run: the previous one is kept (the lane's first) or flushed
+                    if (live) {
+                        if (first) {
+#pragma unroll
+                            for (int k = 0; k < 10; ++k) head[k] = acc[k];
+                            hcell = cur;
+                        } else {
+                            run_flush(hot, rec, rlo, rn, cur, acc, dG, Q);
+                        }
+                    }
+                    if (cur >= 0) first = false;
+                    cur = c;
+                    live = false;
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) acc[k] = 0.f;
+                }
+                float xb[3], agg[10];
+                const int r3 = fast_core(H, x, v, j, mv, w, xb, agg);
+                if (r3 == kFastNonFinite) {
+                    atomicOr(status, ST_NONFINITE);
+                    cell[p0 + j] = -1;
+                } else if (r3 == kFastWalk) {
+                    slow = true;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) sx[k][j] = xb[k];
+                    if (aggregate) {
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) acc[k] += agg[k];
+                        live = true;
+                    } else {
+                        run_flush(hot, rec, rlo, rn, c, agg, dG, Q);
+                    }
+                }
+            }
+            warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
+        }
+        if (aggregate) {
+            if (!live) cur = -1;   // a last run without a particle that stayed: nothing to add
+            // lane l+1's first run continues lane l's last one when their tets agree
+            const int nh = __shfl_down_sync(kFull, hcell, 1);
+            const int pc = __shfl_up_sync(kFull, cur, 1);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                const float u = __shfl_down_sync(kFull, head[k], 1);
+                if (lane < 31 && nh >= 0 && nh == cur) acc[k] += u;
+            }
+            const bool taken = lane > 0 && hcell >= 0 && hcell == pc;
+            if (hcell >= 0 && !taken) run_flush(hot, rec, rlo, rn, hcell, head, dG, Q);
+            // the last runs of consecutive lanes with the same tet (lanes spanned by one run)
+            unsigned heads;
+            int end;
+            warp_run_reduce<float, 10>(cur, acc, &heads, &end);
+            if (((heads >> lane) & 1u) && cur >= 0) run_flush(hot, rec, rlo, rn, cur, acc, dG, Q);
+        }
+        // the producer's bulk copies read the written tile through the async proxy
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sk]);
+    }
+}
+
 // FP64 walk of the queued particles (near or across a face).  The end point is
 // recomputed from the stored start offset and the updated velocity with the same
 // FP32 operations as in k_push_fast32.
@@ -1548,6 +1900,29 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
                                                                      (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
                                                                      slow_idx, slow_count,
                                                                      ctx->d_status);
+        FP_CUDA_TRY(ctx, cudaGetLastError());
+        return FP_OK;
+    }
+#ifndef FP_PUSH_RUN
+#define FP_PUSH_RUN 1
+#endif
+    if (FP_PUSH_RUN) {   // warp-specialised pipeline, runs summed per lane
+        if (ctx->run_blocks_per_sm == 0) {
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_run32, cudaFuncAttributeMaxDynamicSharedMemorySize, kRunSmem));
+            int per_sm = 0;
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_run32, kRunThreads, kRunSmem));
+            if (per_sm < 1) {
+                ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
+                return FP_ECUDA;
+            }
+            ctx->run_blocks_per_sm = per_sm;
+        }
+        const int64_t rtiles = (p->n + kRunTile - 1) / kRunTile;
+        int64_t rgrid = (int64_t)ctx->sm_count * ctx->run_blocks_per_sm;
+        if (rgrid > rtiles) rgrid = rtiles;
+        k_push_run32<<<(int)rgrid, kRunThreads, kRunSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
+                                                               p->n, nt, h, dt, qw, agg, dG, Q, slow_idx, slow_count,
+                                                               ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
