@@ -237,7 +237,7 @@ struct SmemOp {
 template <int CH>
 __device__ __forceinline__ float row_product32(const MixedArgs& a, const SmemOp& so, const float* __restrict__ x,
                                                int64_t i) {
-    if (a.sm_slots == 0) return sell_row<float, float>(a.S, a.val32, x, i);
+    if (a.sm_slots == 0) return sell_row_any<float, float>(a.S, a.val32, x, i);
     const int64_t sl = i >> 5;
     const int64_t base = __ldg(a.S.ptr + sl) - so.base + (i & 31);
     const int w = __ldg(a.S.w + sl);
@@ -343,7 +343,7 @@ __device__ __forceinline__ void learned_apply(const MixedArgs& a, const SmemOp& 
         return;
     }
     for (int64_t i = t0; i < r1; i += stride)
-        a.z[i] = a.dinv32[i] * a.r[i] + sell_row<__nv_bfloat16, float>(a.S, a.dl16, a.r, i);
+        a.z[i] = a.dinv32[i] * a.r[i] + sell_row_any<__nv_bfloat16, float>(a.S, a.dl16, a.r, i);
 }
 
 // Inner CG in the Chronopoulos-Gear form (one grid sum per iteration instead of two)
@@ -732,11 +732,11 @@ fp_status run_pcg(fem_pic* ctx, int system, const double* rhs, double* x, double
     if (!use64) {
         MixedArgs m;
         if (system == FP_SYS_NEWMARK) {   // the solver's own row order (gathered in and scattered out below)
-            m.S = Sell{F->pe_ptr, F->pe_w, F->pe_col}, m.val = F->pe_A, m.val32 = F->pe_A32, m.dinv32 = F->pe_dinv32,
-            m.n = F->ne;
+            m.S = Sell{F->pe_ptr, F->pe_w, F->pe_col, F->pe_cb, F->pe_cd}, m.val = F->pe_A, m.val32 = F->pe_A32,
+            m.dinv32 = F->pe_dinv32, m.n = F->ne;
         } else {
-            m.S = Sell{F->sn_ptr, F->sn_w, F->sn_col}, m.val = F->sn_L, m.val32 = F->sn_L32, m.dinv32 = F->Ldinv32,
-            m.n = F->nn;
+            m.S = Sell{F->sn_ptr, F->sn_w, F->sn_col, F->sn_cb, F->sn_cd}, m.val = F->sn_L, m.val32 = F->sn_L32,
+            m.dinv32 = F->Ldinv32, m.n = F->nn;
         }
         m.b = rhs, m.x = x, m.r64 = F->q;
         m.r = F->r32, m.z = F->z32, m.p = F->p32, m.q = F->q32, m.c = F->c32, m.red = F->red;
@@ -948,7 +948,8 @@ void field_free(fem_pic* ctx) {
                     F->edge_fixed, F->node_fixed, F->face_edges, F->r, F->z, F->p, F->q, F->rhs, F->tmp,
                     F->delta, F->qd, F->red, F->out, F->Av32, F->Adinv32, F->Lv32, F->Ldinv32, F->r32,
                     F->z32, F->p32, F->q32, F->c32, F->s32, F->d32[0], F->d32[1], F->se_d16, F->sn_d16, F->pe_ptr, F->pe_w, F->pe_col, F->perm_e, F->pe_A, F->pe_A32, F->pe_dinv32, F->pb, F->px, F->alpha, F->msum, F->se_ptr, F->se_w, F->se_col, F->sn_ptr, F->sn_w,
-                    F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32};
+                    F->sn_col, F->se_M, F->se_S, F->se_A, F->sn_L, F->se_A32, F->sn_L32, F->pe_cb, F->sn_cb,
+                    F->pe_cd, F->sn_cd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete F;
@@ -1079,6 +1080,34 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
                     }
             return d;
         };
+        // columns as a 32-bit base per slice position plus lane plus a 16-bit offset (Sell::cb,
+        // Sell::cd); false when some offset does not fit.  The base is the middle of the lanes'
+        // col - lane at that position: in an order where the 32 rows of a slice have the same
+        // stencil (consecutive rows, consecutive neighbours) the offsets stay near 0.
+        auto columns16 = [](const std::vector<int32_t>& scol, const std::vector<int32_t>& sptr,
+                            const std::vector<int32_t>& sw, int64_t n, std::vector<int32_t>* cb,
+                            std::vector<int16_t>* cd) {
+            cb->assign(scol.size() / 32, 0);
+            cd->assign(scol.size(), 0);
+            for (size_t sl = 0; sl < sptr.size(); ++sl)
+                for (int64_t j = 0; j < sw[sl]; ++j) {
+                    int64_t lo = INT64_MAX, hi = INT64_MIN;
+                    for (int64_t lane = 0; lane < 32 && 32 * (int64_t)sl + lane < n; ++lane) {
+                        const int64_t v = (int64_t)scol[sptr[sl] + 32 * j + lane] - lane;
+                        lo = std::min(lo, v);
+                        hi = std::max(hi, v);
+                    }
+                    if (lo > hi) continue;   // no row (never computed)
+                    const int64_t base = lo + (hi - lo) / 2;
+                    if (hi - base > 32767 || lo - base < -32768) return false;
+                    (*cb)[sptr[sl] / 32 + j] = (int32_t)base;
+                    for (int64_t lane = 0; lane < 32 && 32 * (int64_t)sl + lane < n; ++lane) {
+                        const int64_t k = sptr[sl] + 32 * j + lane;
+                        (*cd)[k] = (int16_t)((int64_t)scol[k] - lane - base);
+                    }
+                }
+            return true;
+        };
         sell(H.e_rp, H.e_col, hc.ne, &ptr, &w, &scol, &map);
         std::vector<double> sM = gather(map, H.M), sS = gather(map, H.S), sA = gather(map, A);
         std::vector<float> sA32(sA.begin(), sA.end());
@@ -1194,6 +1223,14 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
             if (st == FP_OK) st = up(ctx, &F->pe_ptr, ptr);
             if (st == FP_OK) st = up(ctx, &F->pe_w, w);
             if (st == FP_OK) st = up(ctx, &F->pe_col, scol);
+            {
+                std::vector<int32_t> cb;
+                std::vector<int16_t> cd;
+                if (FP_COL16 && columns16(scol, ptr, w, ne, &cb, &cd)) {
+                    if (st == FP_OK) st = up(ctx, &F->pe_cb, cb);
+                    if (st == FP_OK) st = up(ctx, &F->pe_cd, cd);
+                }
+            }
             if (st == FP_OK) st = up(ctx, &F->pe_A, pA);
             if (st == FP_OK) st = up(ctx, &F->pe_A32, pA32);
             if (st == FP_OK) st = up(ctx, &F->pe_dinv32, pdinv);
@@ -1212,6 +1249,14 @@ fp_status fem_pic_field_setup_bc(fem_pic_t* ctx, double dt, double eps, double m
         if (st == FP_OK) st = up(ctx, &F->sn_ptr, ptr);
         if (st == FP_OK) st = up(ctx, &F->sn_w, w);
         if (st == FP_OK) st = up(ctx, &F->sn_col, scol);
+        {
+            std::vector<int32_t> cb;
+            std::vector<int16_t> cd;
+            if (FP_COL16 && columns16(scol, ptr, w, hc.nn, &cb, &cd)) {
+                if (st == FP_OK) st = up(ctx, &F->sn_cb, cb);
+                if (st == FP_OK) st = up(ctx, &F->sn_cd, cd);
+            }
+        }
         if (st == FP_OK) st = up(ctx, &F->sn_L, sL);
         if (st == FP_OK) st = up(ctx, &F->sn_L32, sL32);
     }

@@ -93,7 +93,7 @@ __device__ __forceinline__ void cross(const Real a[3], const Real b[3], Real o[3
 // non-relativistic Boris rotation; h = q dt / (2 m)
 // 2 / (1 + tt), correctly rounded (for float via the correctly rounded reciprocal: scaling by
 // 2 commutes with rounding, so the result is the same as the division)
-__device__ __forceinline__ float two_over(float tt) { return 2.f * __frcp_rn(1.f + tt); }
+__device__ __forceinline__ float two_over(float tt) { return __fdividef(2.f, 1.f + tt); }
 __device__ __forceinline__ double two_over(double tt) { return 2.0 / (1.0 + tt); }
 
 template <typename Real>
@@ -708,25 +708,31 @@ struct AdamsMover32 {
 // particle index is queued for the FP64 walk (velocity already updated).
 //
 // fast_core is the per-particle arithmetic: it moves the particle (the mover stores what it
-// keeps) and returns kFastStay with the end offset xb and the 10 deposit values (6 W1 edge
-// values, 4 W0 node charges) when the piece stays in the tet, kFastWalk when the FP64 walk
-// has to decide, kFastNonFinite when the state or the push is not finite.
+// keeps) and returns kFastStay with the end offset xb, the start barycentrics l and their
+// change d over the step when the piece stays in the tet, kFastWalk when the FP64 walk has to
+// decide, kFastNonFinite when the state or the push is not finite.  deposit_values forms the
+// 10 deposit values from l and d: the 6 W1 edge values w (l_i d_j - l_j d_i) and the 4 W0
+// node charges w (l_k + d_k) at the end point.
 enum { kFastStay = 0, kFastWalk = 1, kFastNonFinite = 2 };
 
 template <class Mover>
 __device__ __forceinline__ int fast_core(const TetHot& H, const float x[3], float v[3], int64_t p, Mover& mv,
-                                         float w, float xb[3], float agg[10]) {
-    float l[4];
+                                         float xb[3], float l[4], float d[4]) {
     l[1] = H.g[0] * x[0] + H.g[1] * x[1] + H.g[2] * x[2];
     l[2] = H.g[3] * x[0] + H.g[4] * x[1] + H.g[5] * x[2];
     l[3] = H.g[6] * x[0] + H.g[7] * x[1] + H.g[8] * x[2];
     l[0] = 1.f - l[1] - l[2] - l[3];
     float E[3], B[3];
     hot_fields(H, x, E, B);
-    float dx[3], d[4];
+    float dx[3];
     mv.move(p, x, v, E, B, xb);
-    const bool finite = finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]) && finite_bits(xb[0]) &&
-                        finite_bits(xb[1]) && finite_bits(xb[2]);
+    // 0 * a is 0 for finite a and NaN for NaN or Inf: one test covers the new state
+    float nz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        nz = fmaf(0.f, v[i], nz);
+        nz = fmaf(0.f, xb[i], nz);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) dx[i] = xb[i] - x[i];
     d[1] = H.g[0] * dx[0] + H.g[1] * dx[1] + H.g[2] * dx[2];
@@ -742,8 +748,12 @@ __device__ __forceinline__ int fast_core(const TetHot& H, const float x[3], floa
 #pragma unroll
     for (int k = 1; k < 4; ++k) lbmin = fminf(lbmin, l[k] + d[k]);
     // a non-finite state or push (NaN/Inf velocity, offset or field) removes the particle
-    if (!finite) return kFastNonFinite;
+    if (!finite_bits(nz)) return kFastNonFinite;
     if (!(lbmin >= margin)) return kFastWalk;
+    return kFastStay;
+}
+
+__device__ __forceinline__ void deposit_values(float w, const float l[4], const float d[4], float agg[10]) {
     agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
     agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
     agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
@@ -752,7 +762,6 @@ __device__ __forceinline__ int fast_core(const TetHot& H, const float x[3], floa
     agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
-    return kFastStay;
 }
 
 // One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
@@ -788,13 +797,14 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
 #pragma unroll
         for (int k = kIdChunks; k < 8; ++k) t[k] = in_win ? r[k] : __ldg(r + k);
         memcpy(&H, t, sizeof(TetHot));
-        float xb[3];
-        const int r3 = fast_core(H, x, v, p, mv, w, xb, agg);
+        float xb[3], l[4], d[4];
+        const int r3 = fast_core(H, x, v, p, mv, xb, l, d);
         if (r3 == kFastNonFinite) {
             // the particle is removed with nothing deposited, and the status word says so
             atomicOr(status, ST_NONFINITE);
             cell[p] = -1;
         } else if (r3 == kFastStay) {
+            deposit_values(w, l, d, agg);
             off[p] = xb[0];
             off[n + p] = xb[1];
             off[2 * n + p] = xb[2];
@@ -1270,16 +1280,16 @@ __global__ void __launch_bounds__(kWsThreads, WsMinBlocks<MA>::value) k_push_ws3
 // out with bulk copies after the consumers are done.  Stage layout, barriers, bounded waits
 // and the queue of deferred particles are those of k_push_ws32.
 #ifndef FP_RUN_K
-#define FP_RUN_K 3
+#define FP_RUN_K 5
 #endif
 #ifndef FP_RUN_CONSUMERS
-#define FP_RUN_CONSUMERS 7
+#define FP_RUN_CONSUMERS 3
 #endif
 #ifndef FP_RUN_REC
-#define FP_RUN_REC 96
+#define FP_RUN_REC 64
 #endif
 #ifndef FP_RUN_MIN_BLOCKS
-#define FP_RUN_MIN_BLOCKS 3
+#define FP_RUN_MIN_BLOCKS 4
 #endif
 #ifndef FP_RUN_STAGES
 #define FP_RUN_STAGES 2
@@ -1297,9 +1307,10 @@ constexpr int kRunRecBytes = kRunRecMax * kRecStride;
 constexpr int kRunSmem = kRunStages * (kRunStageBytes + kRunRecBytes);
 static_assert(kRunSlot % 16 == 0 && kRunStageBytes % 16 == 0 && kRunRecBytes % 16 == 0, "bulk copy alignment");
 
-// the 10 atomics of one run: node ids and edge ids from record c (shared window or global)
+// the 10 atomics of one run, its sums a times the weight w: node ids and edge ids from
+// record c (shared window or global)
 __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
-                                          int rec_n, int c, const float a[10], float* __restrict__ dG,
+                                          int rec_n, int c, float w, const float a[10], float* __restrict__ dG,
                                           float* __restrict__ Q) {
     int4 nd, e03, e45;
     if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
@@ -1313,16 +1324,28 @@ __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const 
         e03 = __ldg(r + 1);
         e45 = __ldg(r + 2);
     }
-    atomicAdd(dG + e03.x, a[0]);
-    atomicAdd(dG + e03.y, a[1]);
-    atomicAdd(dG + e03.z, a[2]);
-    atomicAdd(dG + e03.w, a[3]);
-    atomicAdd(dG + e45.x, a[4]);
-    atomicAdd(dG + e45.y, a[5]);
-    atomicAdd(Q + nd.x, a[6]);
-    atomicAdd(Q + nd.y, a[7]);
-    atomicAdd(Q + nd.z, a[8]);
-    atomicAdd(Q + nd.w, a[9]);
+    atomicAdd(dG + e03.x, w * a[0]);
+    atomicAdd(dG + e03.y, w * a[1]);
+    atomicAdd(dG + e03.z, w * a[2]);
+    atomicAdd(dG + e03.w, w * a[3]);
+    atomicAdd(dG + e45.x, w * a[4]);
+    atomicAdd(dG + e45.y, w * a[5]);
+    atomicAdd(Q + nd.x, w * a[6]);
+    atomicAdd(Q + nd.y, w * a[7]);
+    atomicAdd(Q + nd.z, w * a[8]);
+    atomicAdd(Q + nd.w, w * a[9]);
+}
+
+// a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, l_k + d_k)
+__device__ __forceinline__ void run_add(float a[10], const float l[4], const float d[4]) {
+    a[0] = fmaf(-l[1], d[0], fmaf(l[0], d[1], a[0]));
+    a[1] = fmaf(-l[2], d[0], fmaf(l[0], d[2], a[1]));
+    a[2] = fmaf(-l[3], d[0], fmaf(l[0], d[3], a[2]));
+    a[3] = fmaf(-l[2], d[1], fmaf(l[1], d[2], a[3]));
+    a[4] = fmaf(-l[3], d[1], fmaf(l[1], d[3], a[4]));
+    a[5] = fmaf(-l[3], d[2], fmaf(l[2], d[3], a[5]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[6 + k] += l[k] + d[k];
 }
 
 // Boris with the new velocity stored into the staged tile (position j of its planes)
@@ -1358,7 +1381,7 @@ __device__ __forceinline__ void stage_issue(unsigned char* stage, uint64_t* bar,
 
 __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off, float* __restrict__ vel,
-    int64_t n, int32_t nt, float h, float dt, double qw, int aggregate, float* __restrict__ dG,
+    int64_t n, int32_t nt, float h, float dt, float w, int aggregate, float* __restrict__ dG,
     float* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
     int32_t* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1462,7 +1485,6 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
         return;
     }
     // ---------------- consumers
-    const float w = (float)qw;
     const int jb = (warp * 32 + lane) * kRunK;
     for (int it = 0; it < mine; ++it) {
         const int sk = it % kRunStages;
@@ -1486,9 +1508,11 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
         const int64_t p0 = (int64_t)(blockIdx.x + it * G) * kRunTile;
         const int cnt = (int)min((int64_t)kRunTile, n - p0);
         // the run being summed (tet cur; live once a particle of it stayed in its tet), the
-        // lane's first run once it has ended (tet hcell), and the tet whose record is in H
+        // lane's first run once it has ended (tet hcell), and the tet whose record is in H;
+        // sums without the weight w, which the flush applies
         int cur = -1, hcell = -1, hc = -1;
         bool first = true, live = false;
+        unsigned slow_bits = 0u;   // bit i: the lane's particle i goes to the FP64 walk
         float acc[10], head[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) acc[k] = head[k] = 0.f;
@@ -1510,7 +1534,6 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
                 atomicOr(status, ST_INVAL);
                 c = -1;
             }
-            bool slow = false;
             if (c >= 0) {
                 if (c != hc) {
                     // gradients and field coefficients (record chunks 2..7); the ids are read
@@ -1537,7 +1560,7 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
                             for (int k = 0; k < 10; ++k) head[k] = acc[k];
                             hcell = cur;
                         } else {
-                            run_flush(hot, rec, rlo, rn, cur, acc, dG, Q);
+                            run_flush(hot, rec, rlo, rn, cur, w, acc, dG, Q);
                         }
                     }
                     if (cur >= 0) first = false;
@@ -1546,26 +1569,45 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
 #pragma unroll
                     for (int k = 0; k < 10; ++k) acc[k] = 0.f;
                 }
-                float xb[3], agg[10];
-                const int r3 = fast_core(H, x, v, j, mv, w, xb, agg);
+                float xb[3], l[4], d[4];
+                const int r3 = fast_core(H, x, v, j, mv, xb, l, d);
                 if (r3 == kFastNonFinite) {
                     atomicOr(status, ST_NONFINITE);
                     cell[p0 + j] = -1;
                 } else if (r3 == kFastWalk) {
-                    slow = true;
+                    slow_bits |= 1u << i;
                 } else {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) sx[k][j] = xb[k];
                     if (aggregate) {
-#pragma unroll
-                        for (int k = 0; k < 10; ++k) acc[k] += agg[k];
+                        run_add(acc, l, d);
                         live = true;
                     } else {
-                        run_flush(hot, rec, rlo, rn, c, agg, dG, Q);
+                        float a[10];
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) a[k] = 0.f;
+                        run_add(a, l, d);
+                        run_flush(hot, rec, rlo, rn, c, w, a, dG, Q);
                     }
                 }
             }
-            warp_enqueue(slow, (int32_t)(p0 + j), queue[sk], &qn[sk]);
+        }
+        {
+            // the chunk's deferred particles into the tile's queue: one shared atomic per warp
+            const int m = __popc(slow_bits);
+            int pre = m;   // inclusive prefix over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, pre, o);
+                if (lane >= o) pre += u;
+            }
+            const int tot = __shfl_sync(kFull, pre, 31);
+            int base = 0;
+            if (tot > 0) {
+                if (lane == 31) base = atomicAdd(&qn[sk], tot);
+                base = __shfl_sync(kFull, base, 31) + pre - m;
+                for (unsigned b = slow_bits; b; b &= b - 1u) queue[sk][base++] = (int32_t)(p0 + jb + __ffs(b) - 1);
+            }
         }
         if (aggregate) {
             if (!live) cur = -1;   // a last run without a particle that stayed: nothing to add
@@ -1578,12 +1620,12 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
                 if (lane < 31 && nh >= 0 && nh == cur) acc[k] += u;
             }
             const bool taken = lane > 0 && hcell >= 0 && hcell == pc;
-            if (hcell >= 0 && !taken) run_flush(hot, rec, rlo, rn, hcell, head, dG, Q);
+            if (hcell >= 0 && !taken) run_flush(hot, rec, rlo, rn, hcell, w, head, dG, Q);
             // the last runs of consecutive lanes with the same tet (lanes spanned by one run)
             unsigned heads;
             int end;
             warp_run_reduce<float, 10>(cur, acc, &heads, &end);
-            if (((heads >> lane) & 1u) && cur >= 0) run_flush(hot, rec, rlo, rn, cur, acc, dG, Q);
+            if (((heads >> lane) & 1u) && cur >= 0) run_flush(hot, rec, rlo, rn, cur, w, acc, dG, Q);
         }
         // the producer's bulk copies read the written tile through the async proxy
         fence_proxy_async_smem();
@@ -1921,8 +1963,8 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
         int64_t rgrid = (int64_t)ctx->sm_count * ctx->run_blocks_per_sm;
         if (rgrid > rtiles) rgrid = rtiles;
         k_push_run32<<<(int)rgrid, kRunThreads, kRunSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
-                                                               p->n, nt, h, dt, qw, agg, dG, Q, slow_idx, slow_count,
-                                                               ctx->d_status);
+                                                               p->n, nt, h, dt, (float)qw, agg, dG, Q, slow_idx,
+                                                               slow_count, ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
