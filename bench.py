@@ -50,6 +50,9 @@ def parse():
                     help="further workloads measured after the headline one in the same run (timed steps and "
                          "per-kernel times only), comma-separated; empty: none")
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (tests only)")
+    ap.add_argument("--mesh", type=int, default=0,
+                    help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
+                         "particles per tet and displacement per step in cells (profiling cases)")
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -188,7 +191,7 @@ def clocks_stop(handle) -> dict:
 
 def build_workload(args):
     from paper_2103_06737_gb300 import inputs as I
-    return I.config(args.workload, args.scale)
+    return I.config(args.workload, args.scale, mesh_n=args.mesh)
 
 
 def algorithmic_bytes(n_particles, sizes, real_bytes=4):
@@ -259,16 +262,15 @@ def mixed_solve_bytes(n_rows, nnz, inner_iters, outer, deg=1):
 
 def measured_traffic(kernel: str, workload: str, iterations=None):
     """DRAM bytes per launch (read + write) of `kernel` from the ncu capture recorded in
-    profiles/traffic.json, or None when there is none for this workload or any source file
-    the kernel is built from has changed since the capture (sha256 recorded with it).  A solver
+    profiles/traffic.json (key kernel@workload), or None when there is none for this workload
+    or any source file the kernel is built from has changed since the capture (sha256 recorded
+    with it).  A solver
     record holds bytes per inner iteration (its launches' bytes over their iterations), scaled
     here by this run's iterations per launch."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[f"{kernel}@{workload}"]
     except Exception:
-        return None
-    if rec.get("workload") != workload:
         return None
     for path, digest in rec.get("sources", {}).items():
         try:
@@ -993,6 +995,8 @@ def run_gpu(args):
                           "step's particle state copied in during this step's field step; fields in and deposits/E "
                           "out on the compute stream; one timed region over all steps"}
 
+    # the main measurement's preconditioners (the side legs below choose their own)
+    main_pc, main_pdeg = state["precond"], list(pdeg)
     fp64 = None if args.fp64_steps <= 0 else measure_fp64(args, F, wl, dev, flush_l2, stream)
     adams = None if args.adams_steps <= 0 else measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG,
                                                              Qn, flush_l2, stream, sizes, wl, dev)
@@ -1177,8 +1181,8 @@ def run_gpu(args):
                     # algorithmic bytes: 12 B per nonzero + 76 B per row per CG iteration, times the
                     # solve's (inner) CG iterations
                     byt = cg_iter_bytes(rows, nz) * max(its, 1)
-                    lrn = bool(state["precond"] & (F.FP_PC_LEARNED if k_sys == 0 else F.FP_PC_LEARNED_GAUSS))
-                    model = (mixed_solve_bytes(rows, nz, its, outs, 1 if lrn else pdeg[k_sys]) if mixed else
+                    lrn = bool(main_pc & (F.FP_PC_LEARNED if k_sys == 0 else F.FP_PC_LEARNED_GAUSS))
+                    model = (mixed_solve_bytes(rows, nz, its, outs, 1 if lrn else main_pdeg[k_sys]) if mixed else
                              pcg_bytes_per_iter(rows, nz) * max(its, 1))
                     if lrn:   # one product with the BF16 learned correction per inner iteration
                         model += its * nz * 6
@@ -1187,7 +1191,7 @@ def run_gpu(args):
                     traffic = measured_traffic(("k_pcg_mixed/" if mixed else "k_pcg/") + ph +
                                                ("/learned" if lrn else ""), wl.name, its)
                     pc_name = ("learned preconditioner" if lrn else
-                               f"Chebyshev-Jacobi degree {pdeg[k_sys]}" if pdeg[k_sys] > 1 else "Jacobi")
+                               f"Chebyshev-Jacobi degree {main_pdeg[k_sys]}" if main_pdeg[k_sys] > 1 else "Jacobi")
                     name = ("k_pcg_mixed (" + ph.split("_")[1] + f" system, FP32 inner PCG, {pc_name}, FP64 residual)"
                             if mixed else "k_pcg (" + ph.split("_")[1] + " system, FP64)")
                     ach = byt / (avg * 1e-3) / 1e9
@@ -1247,14 +1251,15 @@ def run_gpu(args):
             "field_solve": None if not field else {
                 "ms_per_step": sum(phases.get(k, (0.0, 1))[0] for k in ("field_other", "cg_newmark", "cg_gauss",
                                                                           "learned")) / args.steps,
-                "precond": {nm: ("learned preconditioner" if state["precond"] & bit else
-                                 (f"Chebyshev-Jacobi degree {pdeg[k_]}" if pdeg[k_] > 1 else "jacobi"))
+                "precond": {nm: ("learned preconditioner" if main_pc & bit else
+                                 (f"Chebyshev-Jacobi degree {main_pdeg[k_]}" if main_pdeg[k_] > 1 else "jacobi"))
                             for k_, (nm, bit) in enumerate((("newmark", F.FP_PC_LEARNED),
                                                             ("gauss", F.FP_PC_LEARNED_GAUSS)))},
                 "learned_vs_plain": learned,
                 "solver": {"newmark": solv[0], "gauss": solv[1], "mixed": "refinement: FP64 residual, FP32 "
                            "inner Jacobi-PCG (FP32 products, dot products and grid sums)", "fp64": "plain FP64 Jacobi-PCG",
-                           "inner_tol": args.inner_tol, "inner_precond_degree": {"newmark": pdeg[0], "gauss": pdeg[1]},
+                           "inner_tol": args.inner_tol,
+                           "inner_precond_degree": {"newmark": main_pdeg[0], "gauss": main_pdeg[1]},
                            "chebyshev_ratio": {"newmark": prat[0], "gauss": prat[1]}},
                 "ms_newmark_cg": phases.get("cg_newmark", (0.0, 1))[0] / args.steps,
                 "ms_gauss_cg": phases.get("cg_gauss", (0.0, 1))[0] / args.steps,

@@ -196,7 +196,7 @@ def _weight(n0: float, volume: float, n_macro: int) -> float:
     return n0 * volume / max(1, n_macro)
 
 
-def config(idx: int, scale: float = 1.0) -> Workload:
+def config(idx: int, scale: float = 1.0, mesh_n: int = 0) -> Workload:
     """The five synthetic workloads (1-based index).  `scale` < 1 shrinks particle counts.
 
     1: 4^3x6 tets, no jitter, 1,000 e-, v_th=0.01c, seed 0, Bz=0.1 T, dt=0.2*T_ce, 100 steps
@@ -204,41 +204,56 @@ def config(idx: int, scale: float = 1.0) -> Workload:
     3: 64^3x6, jitter, 20M e- beam r=0.2L drifting 0.1c along z, v_th=0.005c, Bz=0.5 T,
        random edge field amplitude 1e3 V/m, 100 steps
     5: 96^3x6, jitter, 50M e- + 50M ions, v_th_e=0.02c, Bx=0.2 T, 50 steps
+
+    mesh_n > 0 replaces the workload's mesh resolution n by mesh_n with the same particles per
+    tet (counts times (mesh_n / n)^3) and the same displacement per step in cells (dt times
+    n / mesh_n): a smaller case of the same character, named after its sizes.
     """
     L = 1.0
+    base_n = {1: 4, 2: 32, 3: 64, 5: 96}.get(idx)
+    if base_n is None:
+        raise ValueError(f"unknown workload {idx}")
+    n = mesh_n if mesh_n > 0 else base_n
+    f = (n / base_n) ** 3 if mesh_n > 0 else 1.0
+    tdt = base_n / n
+
+    def count(c):
+        return max(1, int(c * scale * f))
+
+    def named(default, parts):
+        return default if mesh_n <= 0 else f"cube{n}" + parts
     if idx == 1:
-        mesh = cube_mesh(4, L, 0.0)
-        npart = max(1, int(1000 * scale))
+        mesh = cube_mesh(n, L, 0.0)
+        npart = count(1000)
         B0 = 0.1
         sp = [uniform_species(mesh, npart, 0, 0.01 * C_LIGHT, -Q_E, M_E, _weight(1e14, L ** 3, npart))]
-        return Workload("cube4_e1k", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 100,
-                        background_ions=True)
+        return Workload(named("cube4_e1k", f"_e{npart}"), mesh, sp, 0.2 * gyro_period(B0) * tdt, (0.0, 0.0, B0),
+                        0.0, 100, background_ions=True)
     if idx == 2:
-        mesh = cube_mesh(32, L, 0.1, seed=1)
-        npart = max(1, int(2_000_000 * scale))
+        mesh = cube_mesh(n, L, 0.1, seed=1)
+        npart = count(2_000_000)
         B0 = 0.1
         sp = [uniform_species(mesh, npart, 2, 0.01 * C_LIGHT, -Q_E, M_E, _weight(1e14, L ** 3, npart))]
-        return Workload("cube32_jit_e2M", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 0.0, 200,
-                        background_ions=True)
+        return Workload(named("cube32_jit_e2M", f"_jit_e{npart}"), mesh, sp, 0.2 * gyro_period(B0) * tdt,
+                        (0.0, 0.0, B0), 0.0, 200, background_ions=True)
     if idx == 3:
-        mesh = cube_mesh(64, L, 0.1, seed=1)
-        npart = max(1, int(20_000_000 * scale))
+        mesh = cube_mesh(n, L, 0.1, seed=1)
+        npart = count(20_000_000)
         B0 = 0.5
         r = 0.2 * L
         sp = [beam_species(mesh, npart, 3, r, 0.005 * C_LIGHT, (0.0, 0.0, 0.1 * C_LIGHT), -Q_E, M_E,
                            _weight(1e14, math.pi * r * r * L, npart))]
-        return Workload("cube64_jit_beam20M", mesh, sp, 0.2 * gyro_period(B0), (0.0, 0.0, B0), 1e3, 100)
-    if idx == 5:
-        mesh = cube_mesh(96, L, 0.1, seed=1)
-        npart = max(1, int(50_000_000 * scale))
-        B0 = 0.2
-        vte = 0.02 * C_LIGHT
-        w = _weight(1e14, L ** 3, npart)
-        sp = [uniform_species(mesh, npart, 5, vte, -Q_E, M_E, w),
-              uniform_species(mesh, npart, 55, vte / math.sqrt(MASS_RATIO_ION), Q_E,
-                              MASS_RATIO_ION * M_E, w)]
-        return Workload("cube96_jit_e50M_i50M", mesh, sp, 0.2 * gyro_period(B0), (B0, 0.0, 0.0), 0.0, 50)
-    raise ValueError(f"unknown workload {idx}")
+        return Workload(named("cube64_jit_beam20M", f"_jit_beam{npart}"), mesh, sp, 0.2 * gyro_period(B0) * tdt,
+                        (0.0, 0.0, B0), 1e3, 100)
+    mesh = cube_mesh(n, L, 0.1, seed=1)
+    npart = count(50_000_000)
+    B0 = 0.2
+    vte = 0.02 * C_LIGHT
+    w = _weight(1e14, L ** 3, npart)
+    sp = [uniform_species(mesh, npart, 5, vte, -Q_E, M_E, w),
+          uniform_species(mesh, npart, 55, vte / math.sqrt(MASS_RATIO_ION), Q_E, MASS_RATIO_ION * M_E, w)]
+    return Workload(named("cube96_jit_e50M_i50M", f"_jit_e{npart}_i{npart}"), mesh, sp,
+                    0.2 * gyro_period(B0) * tdt, (B0, 0.0, 0.0), 0.0, 50)
 
 
 def two_tet_mesh() -> Mesh:
