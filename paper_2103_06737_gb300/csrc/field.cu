@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "async_copy.cuh"
 #include "field.cuh"
 
 namespace cg = cooperative_groups;
@@ -232,6 +233,30 @@ struct SmemOp {
     const __nv_bfloat16* l;   // the learned preconditioner's values of the same slots (or null)
 };
 
+// A block's streamed product runs through its rows in steps of BS rows (thread 0 holds each
+// step's first row).  With FP_SELL_PREFETCH = D > 0, thread 0 asks the TMA engine at every step
+// to bring the SELL entries (columns and values) of the step D steps ahead into L2, so that the
+// dependent column -> x gathers of the rows wait on L2 rather than HBM latency.  Rows of a step
+// are whole 32-row slices; a slice's entries are 32 w slots from ptr, so the range is
+// 128-byte aligned.
+#ifndef FP_SELL_PREFETCH
+#define FP_SELL_PREFETCH 1
+#endif
+__device__ __forceinline__ void sell_prefetch(const Sell& S, const void* val, int vbytes, int64_t i, int64_t r1,
+                                              int64_t stride) {
+#if FP_SELL_PREFETCH
+    if (threadIdx.x != 0) return;
+    const int64_t r0 = i + FP_SELL_PREFETCH * stride;
+    if (r0 >= r1) return;
+    const int64_t re = r0 + stride < r1 ? r0 + stride : r1;
+    const int64_t s0 = r0 >> 5, s1 = (re - 1) >> 5;
+    const int64_t k0 = __ldg(S.ptr + s0), k1 = (int64_t)__ldg(S.ptr + s1) + 32 * (int64_t)__ldg(S.w + s1);
+    if (k1 <= k0) return;
+    bulk_prefetch_l2(S.col + k0, (uint32_t)((k1 - k0) * 4));
+    bulk_prefetch_l2(static_cast<const char*>(val) + k0 * vbytes, (uint32_t)((k1 - k0) * vbytes));
+#endif
+}
+
 // row i of the FP32 operator times x: from shared memory (sm_slots > 0) or from the global
 // SELL copy; chunks of CH independent loads (as in sell_row)
 template <int CH>
@@ -298,6 +323,7 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp
         const float rn = 1.f / (2.f * sig - rho);
         const float c1 = rn * rho, c2 = 2.f * rn / de;
         for (int64_t i = t0; i < r1; i += stride) {
+            if (a.sm_slots == 0) sell_prefetch(a.S, a.val32, 4, i, r1, stride);
             const float bd = a.dinv32[i] * row_product32<CH>(a, so, dc, i);
             const float sk = a.s[i] - bd;
             const float dk = c1 * dc[i] + c2 * sk;
@@ -314,9 +340,9 @@ __device__ __forceinline__ void chebyshev_apply(const MixedArgs& a, const SmemOp
 
 // z = D^-1 r + Dl r for the rows [t0, r1) of this block (the learned preconditioner); the
 // product needs every block's r: one grid barrier first.  z is published by the caller's
-// next grid barrier.
+// next grid barrier.  With rz_rr, r.z and r.r of these rows are added to rz_rr[0], rz_rr[1].
 __device__ __forceinline__ void learned_apply(const MixedArgs& a, const SmemOp& so, int64_t t0, int64_t r1,
-                                              int64_t stride, cg::grid_group& g) {
+                                              int64_t stride, cg::grid_group& g, float* rz_rr = nullptr) {
     g.sync();
     if (so.l) {   // Dl and the column offsets from shared memory
         for (int64_t i = t0; i < r1; i += stride) {
@@ -338,12 +364,24 @@ __device__ __forceinline__ void learned_apply(const MixedArgs& a, const SmemOp& 
 #pragma unroll
                 for (int u = 0; u < kSellChunk; ++u) t += lv[u] * xv[u];
             }
-            a.z[i] = a.dinv32[i] * a.r[i] + t;
+            const float ri = a.r[i], zi = a.dinv32[i] * ri + t;
+            a.z[i] = zi;
+            if (rz_rr) {
+                rz_rr[0] += ri * zi;
+                rz_rr[1] += ri * ri;
+            }
         }
         return;
     }
-    for (int64_t i = t0; i < r1; i += stride)
-        a.z[i] = a.dinv32[i] * a.r[i] + sell_row_any<__nv_bfloat16, float>(a.S, a.dl16, a.r, i);
+    for (int64_t i = t0; i < r1; i += stride) {
+        sell_prefetch(a.S, a.dl16, 2, i, r1, stride);
+        const float ri = a.r[i], zi = a.dinv32[i] * ri + sell_row_any<__nv_bfloat16, float>(a.S, a.dl16, a.r, i);
+        a.z[i] = zi;
+        if (rz_rr) {
+            rz_rr[0] += ri * zi;
+            rz_rr[1] += ri * ri;
+        }
+    }
 }
 
 // Inner CG in the Chronopoulos-Gear form (one grid sum per iteration instead of two)
@@ -425,6 +463,7 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
         g.sync();
         float u[3] = {0.f, 0.f, 0.f};  // r.z, p.q, r.r
         for (int64_t i = t0; i < r1; i += stride) {
+            if (a.sm_slots == 0) sell_prefetch(a.S, a.val32, 4, i, r1, stride);
             const float w = row_product32<ProductChunk<BS>::value>(a, so, a.z, i);
             const float zi = a.z[i], ri = a.r[i];
             a.p[i] = zi;
@@ -508,16 +547,10 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             const float alpha = rz / pq;
             float w2[2] = {0.f, 0.f};  // r.z, r.r
             if (use_l) {
-                for (int64_t i = t0; i < r1; i += stride) {
-                    a.c[i] += alpha * a.p[i];
-                    a.r[i] -= alpha * a.q[i];
-                }
-                learned_apply(a, so, t0, r1, stride, g);
-                for (int64_t i = t0; i < r1; i += stride) {
-                    const float ri = a.r[i];
-                    w2[0] += ri * a.z[i];
-                    w2[1] += ri * ri;
-                }
+                // r.z and r.r come with z; c += alpha p waits for the product loop, which
+                // reads p anyway (or for the exit below)
+                for (int64_t i = t0; i < r1; i += stride) a.r[i] -= alpha * a.q[i];
+                learned_apply(a, so, t0, r1, stride, g, w2);
             } else if (a.deg <= 1) {
                 for (int64_t i = t0; i < r1; i += stride) {
                     a.c[i] += alpha * a.p[i];
@@ -542,17 +575,23 @@ __global__ void __launch_bounds__(BS, BS >= 1024 ? 1 : kSolverPerSm) k_pcg_mixed
             }
             grid_sum<BS, 2, float>(w2, part2, g, shf);
             ++total;
-            if (!(w2[1] > ithr)) break;
-            if (use_l && !(w2[0] > 0.f)) {   // not positive on this r: keep c, Jacobi from here on
-                use_l = false;
-                if (a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 1;
+            const bool l_step = use_l;   // this iteration deferred c += alpha p
+            if (!(w2[1] > ithr) || (use_l && !(w2[0] > 0.f))) {
+                if (use_l && !(w2[0] > 0.f)) {   // not positive on this r: keep c, Jacobi from here on
+                    use_l = false;
+                    if (a.lflag && blockIdx.x == 0 && threadIdx.x == 0) *a.lflag = 1;
+                }
+                if (l_step)
+                    for (int64_t i = t0; i < r1; i += stride) a.c[i] += alpha * a.p[i];
                 break;
             }
             const float beta = w2[0] / rz;
             rz = w2[0];
             float u2[1] = {0.f};
             for (int64_t i = t0; i < r1; i += stride) {
+                if (a.sm_slots == 0) sell_prefetch(a.S, a.val32, 4, i, r1, stride);
                 const float w = row_product32<ProductChunk<BS>::value>(a, so, a.z, i);
+                if (l_step) a.c[i] += alpha * a.p[i];
                 const float pi = a.z[i] + beta * a.p[i];
                 const float qi = w + beta * a.q[i];
                 a.p[i] = pi;
