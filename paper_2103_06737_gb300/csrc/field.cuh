@@ -7,10 +7,10 @@
 
 // FP_COL16=1: the mixed solver's streamed FP32 operators read their columns as 16-bit offsets
 // from a per-slice-position base (Sell::cb, Sell::cd) where every offset fits, a quarter fewer
-// operator bytes per product.  Measured on the 96^3 mesh (both operators streamed): Newmark
-// 17.8 -> 18.1 ms and Gauss-law 6.3 -> 6.8 ms per solve with plain Jacobi-CG, so the products
-// there are bound by the latency of the dependent column -> x gathers, not by the operator's
-// bytes; off by default.
+// operator bytes per product.  Measured on the 96^3 mesh (both operators streamed), Jacobi-CG
+// per solve: Newmark 17.8 -> 18.1 ms and Gauss-law 6.3 -> 6.8 ms in the bench; with the L2
+// prefetch of the operator, field-only, Newmark 19.5 -> 19.6 ms and Gauss-law 3.7 -> 4.2 ms.
+// The extra base load per entry costs more than the bytes it saves; off by default.
 #ifndef FP_COL16
 #define FP_COL16 0
 #endif
