@@ -669,7 +669,7 @@ def run_gpu(args):
     # learned preconditioner, per system (Newmark edge system, Gauss-law node system): the
     # network trained by the protocol on the 4^3 and 32^3 workloads' systems, fine-tuned on
     # args.tune_systems systems of this workload's own steps, then timed against plain
-    # Jacobi-CG (the judge) and the configured Chebyshev polynomial on the same steps.  The
+    # Jacobi-CG (the reference solver) and the configured Chebyshev polynomial on the same steps.  The
     # timed steps use the fastest of the three for each system.
     def learned_pick(sys_id, params0, n_compare, flush_base=0):
         """Fine-tune the learned preconditioner of one system (starting from params0) on
@@ -762,7 +762,7 @@ def run_gpu(args):
 
     # learned preconditioner, per system (Newmark edge system, Gauss-law node system): the
     # network trained by the protocol on the 4^3 and 32^3 workloads' systems, fine-tuned on
-    # this workload's own steps, then timed against plain Jacobi-CG (the judge) and the
+    # this workload's own steps, then timed against plain Jacobi-CG (the reference solver) and the
     # configured Chebyshev polynomial on the same steps; the timed steps use the fastest.
     learned = None
     tuned = {}
