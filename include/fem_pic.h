@@ -26,7 +26,8 @@
  *     position minus the position of the cell's vertex v0), vel[3*n] (planar).
  *     off/vel are float in FP_FP32 mode and double in FP_FP64 mode.
  *   - Field DOFs e[N_e], b[N_f] are double (device).  Deposit outputs dG[N_e],
- *     Q[N_n] are float in FP_FP32 mode and double in FP_FP64 mode (device).
+ *     Q[N_n] are float in FP_FP32 mode and double in FP_FP64 mode (device), or double in
+ *     FP_FP32 mode after fem_pic_set_deposit_precision(ctx, FP_FP64).
  *   - All device work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and is asynchronous unless stated.  Errors found by kernels (walk
  *     bound, invalid cell) are OR-ed into a device status word read by
@@ -109,6 +110,28 @@ const char* fem_pic_last_error(const fem_pic_t* ctx);
 
 /* sizes[0..3] = N_n, N_e, N_f, N_t; sizes[4] = precision */
 fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]);
+
+/*
+ * Element type of the deposit arrays of an FP32 context: the W1 current dG and the W0 charge Q
+ * of Sec. IV.B.1 (Eq. for Gbar and rhobar) as fem_pic_push_deposit, fem_pic_push_deposit_static
+ * and fem_pic_deposit_charge write them, and as fem_pic_field_step, fem_pic_field_initial,
+ * fem_pic_residuals and the comparison steps (fem_pic_mfem_*, fem_pic_wave_step) read them.
+ *   FP_FP32 (the default of an FP32 context): float arrays, accumulated with FP32 atomics.
+ *   FP_FP64: double arrays.  The particle arithmetic stays FP32: each particle's
+ *            contributions, and the fast push's sums over a run of particles in one tet, are
+ *            formed in FP32 and added into the arrays with FP64 atomics.  The arrays then keep
+ *            charge continuity (D0^T dG against the change of Q) about a hundred times closer
+ *            than FP32 arrays, whose atomic sums round at the scale of each entry's total,
+ *            and the Gauss-law projection of the field step, which corrects exactly that
+ *            residual, needs correspondingly fewer iterations.
+ * An FP64 context always deposits in FP64 (FP_FP64 accepted, FP_FP32 -> FP_EINVAL).  The FP32
+ * Adams mover (fem_pic_push_deposit_adams) takes FP32 deposits only (FP_EINVAL otherwise).
+ * The setting applies to calls made after it; arrays already passed keep their type.
+ */
+fp_status fem_pic_set_deposit_precision(fem_pic_t* ctx, int precision);
+
+/* FP_FP32 or FP_FP64: the element type of this context's dG and Q arrays (-1 for NULL). */
+int fem_pic_deposit_precision(const fem_pic_t* ctx);
 
 /*
  * Copy incidence matrix `which` (0: D0, 1: D1, 2: D2) to caller host buffers.
@@ -251,8 +274,8 @@ fp_status fem_pic_sort_columns(fem_pic_t* ctx, const fp_particles* src, fp_parti
  *   out[4], out[5] = as out[0], out[1] over interior nodes only (charge absorbed by a
  *            PEC wall in an earlier step leaves the particle set, so over several
  *            steps continuity is checked where the field solve uses it).
- * dG, Q_new, Q_old have the particle precision; b is double.  Any input may be NULL
- * (its entries are then 0).  out is device double[6].  Asynchronous.
+ * dG, Q_new, Q_old have the deposit precision (fem_pic_deposit_precision); b is double.  Any
+ * input may be NULL (its entries are then 0).  out is device double[6].  Asynchronous.
  */
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
                             const double* b, double* out, void* stream);
@@ -334,7 +357,7 @@ fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, dou
  *   3. Faraday: b <- b - dt D1 (E^{n+1} + E^n)/2 (skipped if b is NULL).
  * E_prev = E^{n-1}, E_cur = E^n (device double [N_e]); E_next receives E^{n+1} (distinct
  * buffer); dG_half = dG^{n+1/2} (the deposit of the push that used E^n), dG_prev =
- * dG^{n-1/2} (NULL = 0), Q_new = Q^{n+1} (particle precision).  info[2] (host, may be
+ * dG^{n-1/2} (NULL = 0), Q_new = Q^{n+1} (deposit precision).  info[2] (host, may be
  * NULL): the Newmark and Gauss solves; with info, FP_ENOCONV if either missed tol.
  */
 fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
@@ -376,7 +399,7 @@ fp_status fem_pic_mfem_face_mass(const fem_pic_mfem_t* m, int64_t* nnz, int32_t*
  *   b^{n+1} = b^n - dt [curl] (E^{n+1} + E^n)/2
  * with M = [*eps], S = [*S] and dt of the field setup.  E_cur = E^n, E_next receives E^{n+1}
  * (device double [N_e], distinct buffers); b (device double [N_f], all faces) is updated in
- * place; dG_half (particle precision [N_e], NULL = 0) is the step's deposit.  The Newmark
+ * place; dG_half (deposit precision [N_e], NULL = 0) is the step's deposit.  The Newmark
  * system is solved by fem_pic_field_solve from the start E^n (precond: FP_PC_JACOBI or
  * FP_PC_JACOBI_FP64; tol, max_iter and info as there, FP_ENOCONV after a finished step whose
  * solve missed tol).  With E^0 a gradient and the same deposits it gives the E of
@@ -400,7 +423,7 @@ fp_status fem_pic_wave_step(fem_pic_mfem_t* m, const double* E_prev, const doubl
  * Gauss-law residual g = D0^T [*eps] E + Q (Eq. discreteGauss) on the free nodes, in FP64:
  * out[0] = max |g_n|, out[1] = max over the same nodes of |Q_n| + sum over incident edges of
  * |([*eps] E)_e| (the scale).  Natural boundary: g less (sum Q / sum alpha) alpha, the net
- * charge the zero-mean constraint spreads.  E device double [N_e], Q particle precision [N_n]
+ * charge the zero-mean constraint spreads.  E device double [N_e], Q deposit precision [N_n]
  * (NULL = 0), out device double [2].  Asynchronous.
  */
 fp_status fem_pic_mfem_gauss_residual(fem_pic_mfem_t* m, const double* E, const void* Q, double* out,

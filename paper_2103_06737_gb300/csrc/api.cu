@@ -257,6 +257,28 @@ fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]) {
     return FP_OK;
 }
 
+fp_status fem_pic_set_deposit_precision(fem_pic_t* ctx, int precision) {
+    if (!ctx) return FP_EINVAL;
+    if (precision != FP_FP32 && precision != FP_FP64) {
+        ctx->err = "fem_pic_set_deposit_precision: precision must be FP_FP32 or FP_FP64";
+        return FP_EINVAL;
+    }
+    if (ctx->precision == FP_FP64) {
+        if (precision != FP_FP64) {
+            ctx->err = "fem_pic_set_deposit_precision: an FP64 context deposits in FP64";
+            return FP_EINVAL;
+        }
+        return FP_OK;
+    }
+    ctx->deposit64 = precision == FP_FP64 ? 1 : 0;
+    return FP_OK;
+}
+
+int fem_pic_deposit_precision(const fem_pic_t* ctx) {
+    if (!ctx) return -1;
+    return ctx->precision == FP_FP64 || ctx->deposit64 ? FP_FP64 : FP_FP32;
+}
+
 fp_status fem_pic_incidence(const fem_pic_t* ctx, int which, int32_t* row_ptr, int32_t* col,
                             int8_t* val) {
     if (!ctx || which < 0 || which > 2 || !row_ptr || !col || !val) return FP_EINVAL;

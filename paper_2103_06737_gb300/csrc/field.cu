@@ -914,7 +914,7 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
                           double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                           int max_iter, cudaStream_t s) {
     FieldDev* F = ctx->field;
-    const bool f32 = ctx->precision == FP_FP32;
+    const bool f32 = deposits_f32(ctx);   // dG and Q are float arrays
     const int ge = grid_of(ctx, F->ne), gn = grid_of(ctx, F->nn);
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
@@ -1550,7 +1550,7 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
     }
     cudaStream_t s = (cudaStream_t)stream;
     FieldDev* F = ctx->field;
-    const bool f32 = ctx->precision == FP_FP32;
+    const bool f32 = deposits_f32(ctx);   // dG and Q are float arrays
     const int gn = grid_of(ctx, F->nn), ge = grid_of(ctx, F->ne);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(F->tmp, 0, F->ne * sizeof(double), s));
     if (f32)

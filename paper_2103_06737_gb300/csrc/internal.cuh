@@ -106,6 +106,7 @@ struct fem_pic {
     double prof_ms[fempic::PH_COUNT] = {0};
     int64_t prof_n[fempic::PH_COUNT] = {0};
     int precision = FP_FP64;
+    int deposit64 = 0;  // FP32 mode: dG and Q are double arrays (fem_pic_set_deposit_precision)
     fempic::HostComplex hc;
     // device tables
     fempic::TetGeo* d_geo = nullptr;
@@ -132,6 +133,7 @@ struct fem_pic {
     int tma_blocks_per_sm = 0;
     int ws_blocks_per_sm = 0;
     int run_blocks_per_sm = 0;
+    int run_blocks_per_sm64 = 0;
     int ws_adams_blocks_per_sm = 0;
     uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch
@@ -141,6 +143,9 @@ struct fem_pic {
     int64_t sort_cap = 0;
     std::string err;
 };
+
+// dG and Q are float arrays (FP32 mode with FP32 deposits), else double
+inline bool deposits_f32(const fem_pic* ctx) { return ctx->precision == FP_FP32 && !ctx->deposit64; }
 
 #define FP_CUDA_TRY(ctx, call)                                                             \
     do {                                                                                   \

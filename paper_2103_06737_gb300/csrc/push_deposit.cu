@@ -159,20 +159,22 @@ __device__ __forceinline__ void piece_values(const double la[4], const double lx
     val[5] = w * (A[2] * D[3] - A[3] * D[2]);
 }
 
-template <typename Real>
+// values computed in Real, added into deposit arrays of type D (D = double with FP32
+// arithmetic: FP64 deposits of an FP32-mode context)
+template <typename Real, typename D = Real>
 __device__ __forceinline__ void deposit_piece(const TetTopo& T, const double la[4], const double lx[4],
-                                              double qw, Real* __restrict__ dG) {
+                                              double qw, D* __restrict__ dG) {
     Real val[6];
     piece_values<Real>(la, lx, qw, val);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], val[k]);
+    for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], (D)val[k]);
 }
 
-template <typename Real>
+template <typename Real, typename D = Real>
 __device__ __forceinline__ void deposit_charge(const TetTopo& T, const double l[4], double qw,
-                                               Real* __restrict__ Q) {
+                                               D* __restrict__ Q) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], to_real<Real>(qw) * to_real<Real>(l[k]));
+    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], (D)(to_real<Real>(qw) * to_real<Real>(l[k])));
 }
 
 // Sum `v[0..NV)` over each run of equal `key` in lane order; the first lane of a run
@@ -212,10 +214,10 @@ __device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* h
 // found by cross-multiplication (one division per crossing).  The deposit products are
 // in Real; the current point, needed only when the walk stops early, is tracked in
 // Real as well.
-template <typename Real>
+template <typename Real, typename D = Real>
 __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, int c,
                           const double xa[3], const double xb[3], double qw, int max_cross,
-                          Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status,
+                          D* __restrict__ dG, D* __restrict__ Q, int32_t* __restrict__ status,
                           Real* agg, int* end_cell, double end_off[3]) {
     if (!(finite_bits(xa[0]) && finite_bits(xa[1]) && finite_bits(xa[2]) && finite_bits(xb[0]) &&
           finite_bits(xb[1]) && finite_bits(xb[2]))) {
@@ -288,12 +290,12 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
                 for (int k = 0; k < 4; ++k) agg[6 + k] = to_real<Real>(qw) * to_real<Real>(lb[k]);
                 return true;
             }
-            deposit_piece<Real>(Tc, la, lb, qw, dG);
-            deposit_charge<Real>(Tc, lb, qw, Q);
+            deposit_piece<Real, D>(Tc, la, lb, qw, dG);
+            deposit_charge<Real, D>(Tc, lb, qw, Q);
             return false;
         }
         if (nc == max_cross) {  // bound reached: stop at the last crossing point
-            deposit_charge<Real>(Tc, la, qw, Q);
+            deposit_charge<Real, D>(Tc, la, qw, Q);
             atomicOr(status, ST_WALK);
             *end_cell = t;
 #pragma unroll
@@ -303,13 +305,13 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
         double lc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
-        deposit_piece<Real>(Tc, la, lc, qw, dG);
+        deposit_piece<Real, D>(Tc, la, lc, qw, dG);
         const Real sr = to_real<Real>(smin);
 #pragma unroll
         for (int i = 0; i < 3; ++i) ca[i] = ca[i] + sr * (cb[i] - ca[i]);
         const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
         if (tn < 0) {  // PEC wall: absorbed, its charge stays at the wall point
-            deposit_charge<Real>(Tc, lc, qw, Q);
+            deposit_charge<Real, D>(Tc, lc, qw, Q);
             *end_cell = -1;
 #pragma unroll
             for (int i = 0; i < 3; ++i) end_off[i] = to_f64(ca[i]) + (os[i] - G.o[i]);
@@ -769,11 +771,11 @@ __device__ __forceinline__ void deposit_values(float w, const float l[4], const 
 // go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
 // are read from the shared-memory window `rec` (records kRecStride bytes apart), the others
 // from global memory.
-template <class Mover>
+template <class Mover, typename D = float>
 __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
                                               int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
                                               int32_t nt, Mover& mv, float w, int aggregate, int32_t* __restrict__ cell,
-                                              float* __restrict__ off, float* __restrict__ dG, float* __restrict__ Q,
+                                              float* __restrict__ off, D* __restrict__ dG, D* __restrict__ Q,
                                               int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     if (c >= nt) {
@@ -813,9 +815,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             if (!aggregate) {
                 ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (D)agg[k]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)agg[6 + k]);
             }
         } else {
             slow = true;
@@ -828,9 +830,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         if (((heads >> lane) & 1u) && key >= 0) {
             ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], agg[k]);
+            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (D)agg[k]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], agg[6 + k]);
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)agg[6 + k]);
         }
     }
     return slow;
@@ -854,10 +856,11 @@ __device__ __forceinline__ void warp_enqueue(bool slow, int32_t value, int32_t* 
 #endif
 // Grid-stride variant: the particle state is loaded straight from global memory (the
 // next particle's cell one iteration ahead).
+template <typename D>
 __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
     float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
-    float* __restrict__ dG, float* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    D* __restrict__ dG, D* __restrict__ Q, int32_t* __restrict__ slow_idx,
     int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1309,9 +1312,10 @@ static_assert(kRunSlot % 16 == 0 && kRunStageBytes % 16 == 0 && kRunRecBytes % 1
 
 // the 10 atomics of one run, its sums a times the weight w: node ids and edge ids from
 // record c (shared window or global)
+template <typename D>
 __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
-                                          int rec_n, int c, float w, const float a[10], float* __restrict__ dG,
-                                          float* __restrict__ Q) {
+                                          int rec_n, int c, float w, const float a[10], D* __restrict__ dG,
+                                          D* __restrict__ Q) {
     int4 nd, e03, e45;
     if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
         const int4* r = reinterpret_cast<const int4*>(rec + (c - rec_lo) * kRecStride);
@@ -1324,16 +1328,16 @@ __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const 
         e03 = __ldg(r + 1);
         e45 = __ldg(r + 2);
     }
-    atomicAdd(dG + e03.x, w * a[0]);
-    atomicAdd(dG + e03.y, w * a[1]);
-    atomicAdd(dG + e03.z, w * a[2]);
-    atomicAdd(dG + e03.w, w * a[3]);
-    atomicAdd(dG + e45.x, w * a[4]);
-    atomicAdd(dG + e45.y, w * a[5]);
-    atomicAdd(Q + nd.x, w * a[6]);
-    atomicAdd(Q + nd.y, w * a[7]);
-    atomicAdd(Q + nd.z, w * a[8]);
-    atomicAdd(Q + nd.w, w * a[9]);
+    atomicAdd(dG + e03.x, (D)(w * a[0]));
+    atomicAdd(dG + e03.y, (D)(w * a[1]));
+    atomicAdd(dG + e03.z, (D)(w * a[2]));
+    atomicAdd(dG + e03.w, (D)(w * a[3]));
+    atomicAdd(dG + e45.x, (D)(w * a[4]));
+    atomicAdd(dG + e45.y, (D)(w * a[5]));
+    atomicAdd(Q + nd.x, (D)(w * a[6]));
+    atomicAdd(Q + nd.y, (D)(w * a[7]));
+    atomicAdd(Q + nd.z, (D)(w * a[8]));
+    atomicAdd(Q + nd.w, (D)(w * a[9]));
 }
 
 // a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, l_k + d_k)
@@ -1379,10 +1383,11 @@ __device__ __forceinline__ void stage_issue(unsigned char* stage, uint64_t* bar,
     for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kSlot, vel + k * n + p0, bytes, bar);
 }
 
+template <typename D>
 __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off, float* __restrict__ vel,
-    int64_t n, int32_t nt, float h, float dt, float w, int aggregate, float* __restrict__ dG,
-    float* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
+    int64_t n, int32_t nt, float h, float dt, float w, int aggregate, D* __restrict__ dG,
+    D* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
     int32_t* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kRunStages], empty[kRunStages], recb[kRunStages];
@@ -1637,12 +1642,13 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
 // FP64 walk of the queued particles (near or across a face).  The end point is
 // recomputed from the stored start offset and the updated velocity with the same
 // FP32 operations as in k_push_fast32.
+template <typename D>
 __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
                                                 const TetTopo* __restrict__ topo,
                                                 int32_t* __restrict__ cell, float* __restrict__ off,
                                                 const float* __restrict__ vel, int64_t n, float dt,
-                                                double qw, int max_cross, float* __restrict__ dG,
-                                                float* __restrict__ Q,
+                                                double qw, int max_cross, D* __restrict__ dG,
+                                                D* __restrict__ Q,
                                                 const int32_t* __restrict__ slow_idx,
                                                 const int32_t* __restrict__ slow_count,
                                                 int32_t* __restrict__ status) {
@@ -1664,7 +1670,7 @@ __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
         }
         int end_cell;
         double end_off[3];
-        walk_fp64<float>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
+        walk_fp64<float, D>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
         cell[p] = end_cell;
 #pragma unroll
         for (int k = 0; k < 3; ++k) off[k * n + p] = d2f(end_off[k]);
@@ -1825,10 +1831,11 @@ __global__ void k_wait_selftest(uint64_t limit_ns, int32_t* __restrict__ status)
 }
 
 // W0 charge at the current positions, FP32 (barycentrics from the FP32 gradients)
+template <typename D>
 __global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restrict__ hot,
                                                           const int32_t* __restrict__ cell,
                                                           const float* __restrict__ off, int64_t n,
-                                                          int32_t nt, double qw, float* __restrict__ Q,
+                                                          int32_t nt, double qw, D* __restrict__ Q,
                                                           int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1863,7 +1870,7 @@ __global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restri
         warp_run_reduce<float, 4>(c, v, &heads, &end);
         if (((heads >> lane) & 1u) && c >= 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], v[k]);
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)v[k]);
         }
     }
 }
@@ -1919,8 +1926,10 @@ int grid_for(int64_t n, int sms) {
 
 // the fast FP32 push: the TMA-staged persistent kernel (grid = co-resident blocks), or the
 // grid-stride kernel when the state arrays are not 16-byte aligned
-fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
-                        float* dG, float* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
+template <typename D>
+fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
+                          D* dG, D* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
+    constexpr bool d64 = sizeof(D) == 8;   // FP64 deposits: the run-summing or the grid-stride kernel
     const size_t smem = (size_t)kTmaSmem;
     if (ctx->tma_blocks_per_sm == 0) {
         FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1937,8 +1946,8 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
 #ifndef FP_PUSH_TMA
 #define FP_PUSH_TMA 1
 #endif
-    if (!aligned || !FP_PUSH_TMA) {   // the bulk copies need 16-byte aligned starts and lengths
-        k_push_fast32<<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
+    if (!aligned || (!FP_PUSH_TMA && !d64)) {   // the bulk copies need 16-byte aligned starts and lengths
+        k_push_fast32<D><<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
                                                                      (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
                                                                      slow_idx, slow_count,
                                                                      ctx->d_status);
@@ -1948,21 +1957,24 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
 #ifndef FP_PUSH_RUN
 #define FP_PUSH_RUN 1
 #endif
-    if (FP_PUSH_RUN) {   // warp-specialised pipeline, runs summed per lane
-        if (ctx->run_blocks_per_sm == 0) {
-            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_run32, cudaFuncAttributeMaxDynamicSharedMemorySize, kRunSmem));
+    if (FP_PUSH_RUN || d64) {   // warp-specialised pipeline, runs summed per lane
+        int& per_sm_cached = d64 ? ctx->run_blocks_per_sm64 : ctx->run_blocks_per_sm;
+        if (per_sm_cached == 0) {
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_run32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kRunSmem));
             int per_sm = 0;
-            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_run32, kRunThreads, kRunSmem));
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_run32<D>, kRunThreads,
+                                                                           kRunSmem));
             if (per_sm < 1) {
                 ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
                 return FP_ECUDA;
             }
-            ctx->run_blocks_per_sm = per_sm;
+            per_sm_cached = per_sm;
         }
         const int64_t rtiles = (p->n + kRunTile - 1) / kRunTile;
-        int64_t rgrid = (int64_t)ctx->sm_count * ctx->run_blocks_per_sm;
+        int64_t rgrid = (int64_t)ctx->sm_count * per_sm_cached;
         if (rgrid > rtiles) rgrid = rtiles;
-        k_push_run32<<<(int)rgrid, kRunThreads, kRunSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
+        k_push_run32<D><<<(int)rgrid, kRunThreads, kRunSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
                                                                p->n, nt, h, dt, (float)qw, agg, dG, Q, slow_idx,
                                                                slow_count, ctx->d_status);
         FP_CUDA_TRY(ctx, cudaGetLastError());
@@ -1971,6 +1983,9 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
 #ifndef FP_PUSH_WS
 #define FP_PUSH_WS 1
 #endif
+    if constexpr (d64) {
+        return FP_OK;   // not reached: FP64 deposits take the run-summing kernel above
+    } else {
     if (FP_PUSH_WS) {   // warp-specialised pipeline
         if (ctx->ws_blocks_per_sm == 0) {
             FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_ws32<BorisArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2001,6 +2016,30 @@ fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h
                                                       ctx->d_status);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
+    }
+}
+
+// the FP64 walk of the queued particles, with the deposit arrays' element type
+void launch_walk32(fem_pic* ctx, const fp_particles* p, float dt, double qw, int max_cross, void* dG, void* Q,
+                   const int32_t* slow_idx, const int32_t* slow_count, cudaStream_t s) {
+    if (ctx->deposit64)
+        k_walk32<double><<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                                           (const float*)p->vel, p->n, dt, qw, max_cross,
+                                                           (double*)dG, (double*)Q, slow_idx, slow_count,
+                                                           ctx->d_status);
+    else
+        k_walk32<float><<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                                          (const float*)p->vel, p->n, dt, qw, max_cross,
+                                                          (float*)dG, (float*)Q, slow_idx, slow_count,
+                                                          ctx->d_status);
+}
+
+// the fast FP32 push with the deposit arrays' element type
+fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
+                        void* dG, void* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
+    if (ctx->deposit64)
+        return launch_fast32_t<double>(ctx, p, nt, h, dt, qw, agg, (double*)dG, (double*)Q, slow_idx, slow_count, s);
+    return launch_fast32_t<float>(ctx, p, nt, h, dt, qw, agg, (float*)dG, (float*)Q, slow_idx, slow_count, s);
 }
 
 }  // namespace
@@ -2028,7 +2067,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                               double dt, int max_cross, void* dG, void* Q, int flags,
                               cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
-    const size_t rs = f32 ? 4 : 8;
+    const size_t rs = deposits_f32(ctx) ? 4 : 8;
     if (!(flags & FP_ACCUMULATE)) {
         FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
         FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
@@ -2048,15 +2087,13 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
         }
         {
             PhaseTimer pt(ctx, PH_FAST, s);
-            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, dG, Q,
                                          ctx->d_slow_idx, ctx->d_slow_count, s);
             if (sf != FP_OK) return sf;
         }
         {
             PhaseTimer pt(ctx, PH_WALK, s);
-            k_walk32<<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
-                                             (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
-                                             (float*)Q, ctx->d_slow_idx, ctx->d_slow_count, ctx->d_status);
+            launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, ctx->d_slow_idx, ctx->d_slow_count, s);
         }
     } else {
         if (!(flags & FP_SAME_FIELDS)) {
@@ -2077,6 +2114,10 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
 fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
                             int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
+    if (f32 && ctx->deposit64) {
+        ctx->err = "fem_pic_push_deposit_adams: FP64 deposits are not available for the Adams mover in FP32 mode";
+        return FP_EINVAL;
+    }
     const size_t rs = f32 ? 4 : 8;
     if (!(flags & FP_ACCUMULATE)) {
         FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
@@ -2178,14 +2219,17 @@ fp_status launch_wait_selftest(fem_pic* ctx, double limit_s, cudaStream_t s) {
 fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
                                 cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
-    if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (f32 ? 4 : 8) * ctx->hc.nn, s));
+    if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (deposits_f32(ctx) ? 4 : 8) * ctx->hc.nn, s));
     if (p->n == 0) return FP_OK;
     const double qw = p->q * p->w;
     const int grid = grid_for(p->n, ctx->sm_count);
     PhaseTimer pt(ctx, PH_CHARGE, s);
-    if (f32)
-        k_deposit_charge32<<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
-                                                (int32_t)ctx->hc.nt, qw, (float*)Q, ctx->d_status);
+    if (f32 && ctx->deposit64)
+        k_deposit_charge32<double><<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
+                                                        (int32_t)ctx->hc.nt, qw, (double*)Q, ctx->d_status);
+    else if (f32)
+        k_deposit_charge32<float><<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
+                                                       (int32_t)ctx->hc.nt, qw, (float*)Q, ctx->d_status);
     else
         k_deposit_charge<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell,
                                                       (const double*)p->off, p->n, (int32_t)ctx->hc.nt,
@@ -2258,8 +2302,9 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
         return FP_ECUDA;
     }
     if (!(flags & FP_ACCUMULATE)) {
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, sizeof(float) * ctx->hc.ne, s));
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, sizeof(float) * ctx->hc.nn, s));
+        const size_t rs = ctx->deposit64 ? sizeof(double) : sizeof(float);
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
     }
     FP_CUDA_TRY(ctx, cudaMemsetAsync(q, 0, sizeof(int32_t), s));
     if (p->n == 0) return FP_OK;
@@ -2275,15 +2320,13 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
     {
         // the same kernel choice as fem_pic_push_deposit (staged pipeline for aligned state)
         PhaseTimer pt(ctx, PH_FAST, s);
-        const fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, (float*)dG, (float*)Q,
+        const fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, dG, Q,
                                            q + kStaticHead, q, s);
         if (sf != FP_OK) return sf;
     }
     {
         PhaseTimer pt(ctx, PH_WALK, s);
-        k_walk32<<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
-                                                   (const float*)p->vel, p->n, (float)dt, qw, max_cross, (float*)dG,
-                                                   (float*)Q, q + kStaticHead, q, ctx->d_status);
+        launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, q + kStaticHead, q, s);
     }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;

@@ -324,7 +324,7 @@ fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const v
     const int nb_cont = grid_cap(nn, 256, 4, ctx->sm_count);
     const int nb_div = grid_cap(nt, 256, 4, ctx->sm_count);
     const int grid = nb_cont + nb_div;
-    if (ctx->precision == FP_FP32)
+    if (deposits_f32(ctx))
         k_residuals<float><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn,
                                                 (const float*)dG, (const float*)Qn, (const float*)Qo,
                                                 ctx->d_node_wall, ctx->d_tet_faces, nt, b,

@@ -89,6 +89,8 @@ def lib():
             "fem_pic_destroy": (None, [P]),
             "fem_pic_last_error": (ctypes.c_char_p, [P]),
             "fem_pic_sizes": (I32, [P, P]),
+            "fem_pic_set_deposit_precision": (I32, [P, I32]),
+            "fem_pic_deposit_precision": (I32, [P]),
             "fem_pic_incidence": (I32, [P, I32, P, P, P]),
             "fem_pic_topology": (I32, [P, P, P, P, P]),
             "fem_pic_project_uniform": (I32, [P, P, P, P, P, P]),
@@ -289,6 +291,20 @@ def _real(h):
     return torch.float32 if fem_pic_sizes(h)["precision"] == FP_FP32 else torch.float64
 
 
+def _dep(h):
+    """dtype of the deposit arrays (dG, Q)."""
+    return torch.float32 if int(lib().fem_pic_deposit_precision(h)) == FP_FP32 else torch.float64
+
+
+def fem_pic_set_deposit_precision(h, precision: int):
+    """FP_FP32 or FP_FP64 deposit arrays (dG, Q) of an FP32 context (see the header)."""
+    _check(lib().fem_pic_set_deposit_precision(h, int(precision)), h)
+
+
+def fem_pic_deposit_precision(h) -> int:
+    return int(lib().fem_pic_deposit_precision(h))
+
+
 def fem_pic_particles_from_global(h, cell, X, off, stream=None):
     n = cell.numel()
     _need(cell, torch.int32, n, name="cell")
@@ -315,7 +331,7 @@ def _check_species(h, sp: Species):
 def fem_pic_push_deposit(h, e, b, sp: Species, dt: float, dG, Q, max_cross: int = 64, flags: int = 0,
                          stream=None):
     sz = fem_pic_sizes(h)
-    R = _real(h)
+    R = _dep(h)
     _check_species(h, sp)
     _need(e, torch.float64, sz["n_edges"], name="e")
     _need(b, torch.float64, sz["n_faces"], name="b")
@@ -345,7 +361,7 @@ def fem_pic_push_deposit_adams(h, e, b, sp: Species, hist, step: int, dt: float,
 
 def fem_pic_deposit_charge(h, sp: Species, Q, flags: int = 0, stream=None):
     _check_species(h, sp)
-    _need(Q, _real(h), fem_pic_sizes(h)["n_nodes"], name="Q")
+    _need(Q, _dep(h), fem_pic_sizes(h)["n_nodes"], name="Q")
     p = sp.abi()
     _check(lib().fem_pic_deposit_charge(h, ctypes.byref(p), _ptr(Q), int(flags), _stream(stream)), h)
 
@@ -681,6 +697,13 @@ class FemPic:
 
     def deposit_charge(self, sp, Q, flags=0, stream=None):
         fem_pic_deposit_charge(self.h, sp, Q, flags, stream)
+
+    def set_deposit_precision(self, precision: int):
+        fem_pic_set_deposit_precision(self.h, precision)
+
+    @property
+    def deposit_dtype(self):
+        return _dep(self.h)
 
     def sort(self, src, dst, stream=None):
         fem_pic_sort(self.h, src, dst, stream)

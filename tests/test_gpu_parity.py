@@ -341,3 +341,71 @@ def test_nonfinite_state_is_flagged_and_not_deposited(prec, npart):
         assert_deposit_close(dG, ref["dG"], ref["dG_abs"], TOL["fp64"], "dG")
         assert_deposit_close(Q, ref["Q"], ref["Q_abs"], TOL["fp64"], "Q")
     lib.close()
+
+
+def test_fp32_staged_push_without_aggregation_matches():
+    """The staged FP32 push with FP_NO_AGGREGATE (one atomic per contribution) gives the same
+    particles bit for bit and the same deposits within the FP32 tolerance as the run-summed
+    push, on a cell-sorted state of 50,000 particles (the last tile partial)."""
+    m, orc, lib, sp, e, b = _setup(npart=50_000, speed=0.15, prec=F.FP_FP32)
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    s = d.empty_like()
+    lib.sort(d, s)
+    ed = torch.as_tensor(e, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    runs = []
+    for flags in (0, F.FP_NO_AGGREGATE):
+        t = s.empty_like()
+        t.cell.copy_(s.cell)
+        t.off.copy_(s.off)
+        t.vel.copy_(s.vel)
+        dG = torch.empty(orc.n_edges, dtype=torch.float32, device="cuda")
+        Q = torch.empty(orc.n_nodes, dtype=torch.float32, device="cuda")
+        lib.push_deposit(ed, bd, t, 1.0, dG, Q, flags=flags)
+        assert lib.status() == F.FP_OK
+        runs.append((t, dG.double().cpu().numpy(), Q.double().cpu().numpy()))
+    (a, dGa, Qa), (c, dGc, Qc) = runs
+    assert torch.equal(a.cell, c.cell) and torch.equal(a.off, c.off) and torch.equal(a.vel, c.vel)
+    for x, y in ((dGa, dGc), (Qa, Qc)):
+        assert np.abs(x - y).max() <= TOL["fp32"] * np.abs(x).max()
+    lib.close()
+
+
+def test_fp32_staged_push_skips_dead_and_invalid_particles():
+    """Absorbed particles (cell -1) in the middle of a cell-sorted state, and one particle with
+    an out-of-range cell, through the staged FP32 push: the status word reports FP_EINVAL, the
+    skipped particles keep their state, and the others give the same particles and deposits
+    as a push of the state without them."""
+    m, orc, lib, sp, e, b = _setup(npart=40_000, speed=0.15, prec=F.FP_FP32)
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    s = d.empty_like()
+    lib.sort(d, s)
+    n = s.n
+    rng = np.random.default_rng(11)
+    dead = np.sort(rng.choice(n, 900, replace=False))
+    bad = int(dead[450])
+    cell = s.cell.clone()
+    cell[torch.as_tensor(dead, device="cuda")] = -1
+    cell[bad] = orc.n_tets + 3
+    keep = np.setdiff1d(np.arange(n), dead)
+    kt = torch.as_tensor(keep, device="cuda")
+    # the reference: only the live particles (n - 900, a multiple of 4: the same staged kernel)
+    r = F.Species(s.cell[kt].contiguous(), s.off[:, kt].contiguous(), s.vel[:, kt].contiguous(), s.q, s.m, s.w)
+    assert r.n % 4 == 0
+    t = F.Species(cell, s.off.clone(), s.vel.clone(), s.q, s.m, s.w)
+    ed = torch.as_tensor(e, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    out = []
+    for sp_ in (t, r):
+        dG = torch.empty(orc.n_edges, dtype=torch.float32, device="cuda")
+        Q = torch.empty(orc.n_nodes, dtype=torch.float32, device="cuda")
+        lib.push_deposit(ed, bd, sp_, 1.0, dG, Q)
+        out.append((dG.double().cpu().numpy(), Q.double().cpu().numpy(), lib.status()))
+    assert out[0][2] == F.FP_EINVAL and out[1][2] == F.FP_OK
+    dt_ = torch.as_tensor(dead, device="cuda")
+    assert torch.equal(t.off[:, dt_], s.off[:, dt_]) and torch.equal(t.vel[:, dt_], s.vel[:, dt_])
+    assert int(t.cell[bad]) == orc.n_tets + 3
+    assert torch.equal(t.cell[kt], r.cell) and torch.equal(t.off[:, kt], r.off) and torch.equal(t.vel[:, kt], r.vel)
+    for x, y in ((out[0][0], out[1][0]), (out[0][1], out[1][1])):
+        assert np.abs(x - y).max() <= TOL["fp32"] * np.abs(y).max()
+    lib.close()
