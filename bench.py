@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--mesh", type=int, default=0,
                     help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
                          "particles per tet and displacement per step in cells (profiling cases)")
+    ap.add_argument("--deposits", default="fp64", choices=["fp32", "fp64"],
+                    help="element type of the deposit arrays dG and Q (the FP32 particle path adds its FP32 "
+                         "contributions into them with atomics of this type)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="steps between cell sorts (0: the workload's own: 2 for the drifting beam, whose cell "
                          "order decays fastest, 10 otherwise; negative: never)")
@@ -208,11 +211,11 @@ def algorithmic_bytes(n_particles, sizes, real_bytes=4):
     return state + tets + dofs + dep
 
 
-def fast_kernel_bytes(n_particles, sizes):
+def fast_kernel_bytes(n_particles, sizes, dep_bytes=4):
     """Minimal DRAM bytes of one fast-push launch (k_push_run32): cell + off + vel read (28 B) and
     off + vel written (24 B) per particle, each tet's 128-byte record once, dG and Q
-    read-modify-write once (FP32)."""
-    return n_particles * 52 + sizes["n_tets"] * 128 + 8 * (sizes["n_edges"] + sizes["n_nodes"])
+    read-modify-write once (dep_bytes per element: 4 for float, 8 for double deposit arrays)."""
+    return n_particles * 52 + sizes["n_tets"] * 128 + 2 * dep_bytes * (sizes["n_edges"] + sizes["n_nodes"])
 
 
 def adams_kernel_bytes(n_particles, sizes):
@@ -318,6 +321,8 @@ def learned_protocol(args, dev):
     for idx in (1, 2):
         wl = I.config(idx)
         lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
+        if args.deposits == "fp64":
+            lib.set_deposit_precision(F.FP_FP64)
         sizes = lib.sizes
         sps = []
         for s_ in wl.species:
@@ -327,9 +332,9 @@ def learned_protocol(args, dev):
             sps.append(d1)
         e, b = lib.fields_uniform((0.0, 0.0, 0.0), wl.B0, device=dev)
         ne, nn = sizes["n_edges"], sizes["n_nodes"]
-        dG = torch.zeros(ne, dtype=torch.float32, device=dev)
+        dG = torch.zeros(ne, dtype=lib.deposit_dtype, device=dev)
         dGp = torch.zeros_like(dG)
-        Qn = torch.zeros(nn, dtype=torch.float32, device=dev)
+        Qn = torch.zeros(nn, dtype=lib.deposit_dtype, device=dev)
         Qo = torch.zeros_like(Qn)
         Q_ion = torch.zeros_like(Qn)
         if wl.background_ions:
@@ -501,14 +506,17 @@ def run_gpu(args):
         ev = wl.E_amp * length * u
         ev[wall] = 0.0
         e.copy_(torch.as_tensor(ev, device=dev))
-    dG = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)       # dG^{n+1/2}
-    dG_prev = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)  # dG^{n-1/2}
-    Qn = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
-    Qo = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
+    if args.deposits == "fp64":
+        lib.set_deposit_precision(F.FP_FP64)
+    DEP = lib.deposit_dtype
+    dG = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)       # dG^{n+1/2}
+    dG_prev = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)  # dG^{n-1/2}
+    Qn = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
+    Qo = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
     res = torch.zeros(6, dtype=torch.float64, device=dev)
     # uniform immobile neutralising ion background where the workload has one:
     # Q_ion,n = -(total electron charge) alpha^0_n / V, alpha^0_n = integral of W0_n
-    Q_ion = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
+    Q_ion = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
     if wl.background_ions:
         alpha = F.fem_pic_whitney0_integrals(lib.h)
         qtot = sum(s_.q * s_.w * s_.n for s_ in species)
@@ -895,7 +903,8 @@ def run_gpu(args):
         hE = torch.empty_like(e, device="cpu").pin_memory()
         bi = sum(x.numel() * x.element_size() for tr in hs for x in tr) + \
             sum(h_.numel() * h_.element_size() for _, h_ in fin)
-        bo = sum(x.numel() * x.element_size() for tr in hs_out for x in tr) + hdG.numel() * 4 + hQ.numel() * 4 + \
+        bo = sum(x.numel() * x.element_size() for tr in hs_out for x in tr) + hdG.numel() * hdG.element_size() + \
+            hQ.numel() * hQ.element_size() + \
             (hE.numel() * 8 if field else 0)
         # Pipelined by species and across steps: each species is pushed (one CUDA graph per species
         # and step shape) as soon as its state has been copied in, and its new state goes back on an
@@ -1167,7 +1176,7 @@ def run_gpu(args):
         fast_avg = fast_ms / max(1, fast_n)
         # bytes of one launch: one species' live particles (alive_eager counts all species),
         # its tet records and deposits
-        fbytes = fast_kernel_bytes(alive_eager / len(species), sizes)
+        fbytes = fast_kernel_bytes(alive_eager / len(species), sizes, torch.empty(0, dtype=DEP).element_size())
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         roof_push = {"kernel": "k_push_run32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
@@ -1238,6 +1247,8 @@ def run_gpu(args):
                                   "initial state (particles absorbed by the PEC walls are not counted)",
                        "species": len(species), "dt_s": wl.dt, "B0_T": list(wl.B0),
                        "sort_every": args.sort_every, "precision": "fp32 particle path, fp64 walk test",
+                       "deposits": ("double dG and Q (FP32 contributions added with FP64 atomics)"
+                                    if DEP == torch.float64 else "float dG and Q (FP32 atomics)"),
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "sort (periodic) + push/gather/walk/deposit + implicit field step "
@@ -1318,6 +1329,12 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
     dt = wl.dt / 4
     step = 0
 
+    # the Adams mover takes FP32 deposits: arrays of its own while it runs, the context's setting
+    # restored after
+    dep_keep = F.fem_pic_deposit_precision(lib.h)
+    lib.set_deposit_precision(F.FP_FP32)
+    dG = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)
+    Qn = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
     def call():
         nonlocal step
         dG.zero_()
@@ -1346,6 +1363,7 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
     F.fem_pic_profile_enable(lib.h, False)
     ph = F.fem_pic_profile_read(lib.h, reset=True)
     st = lib.status()
+    lib.set_deposit_precision(dep_keep)
     ms = sum(a.elapsed_time(z) for a, z in ev)
     n_live = sum(live) / len(live)
     f_ms, f_n = ph.get("adams_push", (float("nan"), 1))
