@@ -28,12 +28,21 @@ def _built():
     build.build()
 
 
-def _push(lib, orc, sp, e, b, dtype, sort):
+def _state(lib, sp, sort):
     d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
     if sort:
         s = d.empty_like()
         lib.sort(d, s)
         d = s
+    return d
+
+
+def _push(lib, orc, d0, e, b, dtype):
+    """One push of a copy of the state d0 into deposit arrays of the given dtype."""
+    d = d0.empty_like()
+    d.cell.copy_(d0.cell)
+    d.off.copy_(d0.off)
+    d.vel.copy_(d0.vel)
     cell0 = d.cell.cpu().numpy().copy()
     off0 = d.off.cpu().numpy().copy()
     v0 = d.vel.cpu().numpy().copy()
@@ -62,10 +71,11 @@ def test_fp64_deposits_match_oracle_and_tighten_continuity(npart, sort):
     b = rng.uniform(-0.5, 0.5, orc.n_faces)
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP32)
     assert F.fem_pic_deposit_precision(lib.h) == F.FP_FP32
-    r32 = _push(lib, orc, sp, e, b, torch.float32, sort)
+    d0 = _state(lib, sp, sort)      # one state (the sort orders equal cells arbitrarily)
+    r32 = _push(lib, orc, d0, e, b, torch.float32)
     lib.set_deposit_precision(F.FP_FP64)
     assert lib.deposit_dtype == torch.float64
-    d, cell0, off0, v0, dG, Q, Q0, res = _push(lib, orc, sp, e, b, torch.float64, sort)
+    d, cell0, off0, v0, dG, Q, Q0, res = _push(lib, orc, d0, e, b, torch.float64)
     # the particles are those of the FP32-deposit push, bit for bit
     assert torch.equal(d.cell, r32[0].cell) and torch.equal(d.off, r32[0].off) and torch.equal(d.vel, r32[0].vel)
     # deposits against the oracle walk on the GPU's own end points
