@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--mesh", type=int, default=0,
                     help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
                          "particles per tet and displacement per step in cells (profiling cases)")
-    ap.add_argument("--deposits", default="fp64", choices=["fp32", "fp64"],
+    ap.add_argument("--deposits", default="fp32", choices=["fp32", "fp64"],
                     help="element type of the deposit arrays dG and Q (the FP32 particle path adds its FP32 "
-                         "contributions into them with atomics of this type)")
+                         "contributions into them with atomics of this type); at 96^3 fp64 cut the Gauss-law "
+                         "projection from 121 to 104 inner iterations (5.2 -> 4.5 ms) but slowed the push and "
+                         "walk by 0.6 ms (FP64 atomics), no gain per step")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="steps between cell sorts (0: the workload's own: 2 for the drifting beam, whose cell "
                          "order decays fastest, 10 otherwise; negative: never)")
