@@ -1,18 +1,21 @@
 // The per-particle hot path: Whitney gather, Boris push, tet walk, charge-conserving
 // Whitney-1 current deposit and Whitney-0 charge deposit (Sec. II.A, II.C, IV.B.1).
 //
-// One thread per particle, particles in struct-of-arrays, one warp = 32 consecutive
-// particles.  After a cell sort most warps hold a few runs of particles that share
-// a tet; the per-tet tables are then read once per run (broadcast loads), and the
-// deposits of particles whose path stays inside their tet are reduced per run with
-// warp shuffles before one global atomic per edge/node.  Particles that cross faces
-// deposit each piece with direct atomics.
+// Particles in struct-of-arrays.  After a cell sort consecutive particles mostly share a
+// tet.  The default FP32 push (k_push_run32) gives each lane a few consecutive particles:
+// a lane re-reads the tet's record only where the tet changes and sums the deposits of a
+// run of particles in one tet in registers, the warp joins the runs that cross lane
+// boundaries, and one global atomic per edge/node is issued per run.  The other kernels
+// take one particle per lane and reduce runs with warp shuffles.  Particles whose path
+// leaves (or may leave) their tet are deferred to the FP64 walk, which deposits each piece
+// with direct atomics.
 //
 // The gather goes through per-tet affine field records (E = E0 + W x off, B = B0 + beta off
 // in the tet, equal to the Whitney-1 / Whitney-2 sums), made once per call from e and b by
 // k_field_prep32 (FP32 records) or k_field_prep64 (FP64 mode).
 //
-// Precision: fields, push and deposit products in Real (float or double).  The exit
+// Precision: fields, push and deposit products in Real (float or double); the deposit
+// arrays are Real or, for an FP32 context with FP64 deposits, double.  The exit
 // test of the walk (barycentric coordinates of the end point, crossing fraction,
 // argmin) is always FP64.  The piece deposit uses the factored form
 //   dG_ab = q w (l^a_a (l^c_b - l^a_b) - l^a_b (l^c_a - l^a_a)),
