@@ -961,18 +961,44 @@ def run_gpu(args):
                     ev.record(in_stream)
                     evs.append(ev)
             return evs
+        # the fields' copies in and the results' copies out go through device staging buffers:
+        # the next step's fields are copied from host memory into staging on the input stream
+        # during this step, and this step's results are copied to staging on the compute stream
+        # (device-to-device) and from there to host memory on the output stream, so only the
+        # device-to-device copies sit on the compute stream
+        stg_in = [torch.empty_like(d_) for d_, _ in fin]
+        res_dev = [dG, Qn] + ([e] if field else [])
+        res_host = [hdG, hQ] + ([hE] if field else [])
+        stg_out = [torch.empty_like(x) for x in res_dev]
+
+        def fields_in(after):
+            with torch.cuda.stream(in_stream):
+                if after is not None:
+                    in_stream.wait_event(after)
+                for (_, h_), g_ in zip(fin, stg_in):
+                    g_.copy_(h_, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(in_stream)
+            return ev
         t_a = torch.cuda.Event(enable_timing=True)
         t_z = torch.cuda.Event(enable_timing=True)
         t_a.record(stream)
         in_stream.wait_event(t_a)
         out_stream.wait_event(t_a)
+        ev_f = fields_in(None)
         ev_in = copy_in(species, [None] * nsp)
         out_done = [None] * nsp
+        res_done = None
         for k in range(args.steps):
             pl = plan(state["i"])
             gps, gb, use = e2e_graph(pl)
-            for d_, h_ in fin:
-                d_.copy_(h_, non_blocking=True)
+            stream.wait_event(ev_f)
+            for (d_, _), g_ in zip(fin, stg_in):
+                d_.copy_(g_, non_blocking=True)
+            if k + 1 < args.steps:
+                staged = torch.cuda.Event()
+                staged.record(stream)
+                ev_f = fields_in(staged)
             for j in range(nsp):
                 stream.wait_event(ev_in[j])
                 gps[j].replay()
@@ -988,16 +1014,24 @@ def run_gpu(args):
                     ev.record(out_stream)
                     out_done[j] = ev
             gb.replay()
-            hdG.copy_(dG, non_blocking=True)
-            hQ.copy_(Qn, non_blocking=True)
-            if field:
-                hE.copy_(e, non_blocking=True)
+            if res_done is not None:
+                stream.wait_event(res_done)   # the previous step's results have left staging
+            for x, g_ in zip(res_dev, stg_out):
+                g_.copy_(x, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(stream)
+            out_stream.wait_event(copied)
+            with torch.cuda.stream(out_stream):
+                for g_, h_ in zip(stg_out, res_host):
+                    h_.copy_(g_, non_blocking=True)
+                res_done = torch.cuda.Event()
+                res_done.record(out_stream)
             advance(pl)
             state["i"] += 1
             species = [bufs[j][cur[j]] for j in range(nsp)]
             if k + 1 < args.steps:
                 ev_in = copy_in(species, out_done)
-        for ev in out_done:
+        for ev in out_done + [res_done]:
             stream.wait_event(ev)
         t_z.record(stream)
         torch.cuda.synchronize()
@@ -1011,8 +1045,9 @@ def run_gpu(args):
                "overlap": "pipelined by species and across steps: species k pushed once its state is in while "
                           "species k+1's state is copied in, species k's new state copied back on an output stream "
                           "(into pinned buffers of its own) during the next push and the field step, the next "
-                          "step's particle state copied in during this step's field step; fields in and deposits/E "
-                          "out on the compute stream; one timed region over all steps"}
+                          "step's particle state and fields copied in during this step (the fields through device "
+                          "staging buffers), deposits and E copied out through staging on the output stream; one "
+                          "timed region over all steps"}
 
     # the main measurement's preconditioners (the side legs below choose their own)
     main_pc, main_pdeg = state["precond"], list(pdeg)
