@@ -53,11 +53,12 @@ def parse():
     ap.add_argument("--mesh", type=int, default=0,
                     help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
                          "particles per tet and displacement per step in cells (profiling cases)")
-    ap.add_argument("--deposits", default="fp32", choices=["fp32", "fp64"],
-                    help="element type of the deposit arrays dG and Q (the FP32 particle path adds its FP32 "
-                         "contributions into them with atomics of this type); at 96^3 fp64 cut the Gauss-law "
-                         "projection from 121 to 104 inner iterations (5.2 -> 4.5 ms) but slowed the push and "
-                         "walk by 0.6 ms (FP64 atomics), no gain per step")
+    ap.add_argument("--deposits", default="fp32", choices=["fp32", "fp64", "change"],
+                    help="deposit arrays: fp32 (float dG and Q, the end-point charge), fp64 (double dG and Q: "
+                         "the FP32 contributions added with FP64 atomics; at 96^3 it cut the Gauss-law "
+                         "projection from 121 to 104 inner iterations but slowed the push and walk by 0.6 ms) "
+                         "or change (float dG, double Q carried from step to step by the charge change of "
+                         "each particle, FP_CHARGE_CHANGE)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="steps between cell sorts (0: the workload's own: 2 for the drifting beam, whose cell "
                          "order decays fastest, 10 otherwise; negative: never)")
@@ -213,11 +214,12 @@ def algorithmic_bytes(n_particles, sizes, real_bytes=4):
     return state + tets + dofs + dep
 
 
-def fast_kernel_bytes(n_particles, sizes, dep_bytes=4):
+def fast_kernel_bytes(n_particles, sizes, dep_bytes=4, q_bytes=None):
     """Minimal DRAM bytes of one fast-push launch (k_push_run32): cell + off + vel read (28 B) and
     off + vel written (24 B) per particle, each tet's 128-byte record once, dG and Q
     read-modify-write once (dep_bytes per element: 4 for float, 8 for double deposit arrays)."""
-    return n_particles * 52 + sizes["n_tets"] * 128 + 2 * dep_bytes * (sizes["n_edges"] + sizes["n_nodes"])
+    q_bytes = dep_bytes if q_bytes is None else q_bytes
+    return n_particles * 52 + sizes["n_tets"] * 128 + 2 * (dep_bytes * sizes["n_edges"] + q_bytes * sizes["n_nodes"])
 
 
 def adams_kernel_bytes(n_particles, sizes):
@@ -300,6 +302,14 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+def set_deposits(args, lib, F):
+    """The deposit arrays' element types for the --deposits choice."""
+    if args.deposits == "fp64":
+        lib.set_deposit_precision(F.FP_FP64)
+    elif args.deposits == "change":
+        lib.set_charge_precision(F.FP_FP64)
+
+
 def learned_protocol(args, dev):
     """Training and evaluation protocol of the learned preconditioner (the FP_LEARNED_PRECOND
     network) on both field systems, Newmark (edge graph) and Gauss-law projection (node graph).
@@ -323,8 +333,8 @@ def learned_protocol(args, dev):
     for idx in (1, 2):
         wl = I.config(idx)
         lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
-        if args.deposits == "fp64":
-            lib.set_deposit_precision(F.FP_FP64)
+        set_deposits(args, lib, F)
+        cflag = F.FP_CHARGE_CHANGE if args.deposits == "change" else 0
         sizes = lib.sizes
         sps = []
         for s_ in wl.species:
@@ -336,7 +346,7 @@ def learned_protocol(args, dev):
         ne, nn = sizes["n_edges"], sizes["n_nodes"]
         dG = torch.zeros(ne, dtype=lib.deposit_dtype, device=dev)
         dGp = torch.zeros_like(dG)
-        Qn = torch.zeros(nn, dtype=lib.deposit_dtype, device=dev)
+        Qn = torch.zeros(nn, dtype=lib.charge_dtype, device=dev)
         Qo = torch.zeros_like(Qn)
         Q_ion = torch.zeros_like(Qn)
         if wl.background_ions:
@@ -358,11 +368,13 @@ def learned_protocol(args, dev):
         st0, inf0 = F.fem_pic_field_initial(lib.h, Qo, e, tol=args.tol)
         Ep.copy_(e)
 
-        def step(pc, lib=lib, sps=sps, e=e, b=b, dG=dG, dGp=dGp, Qn=Qn, Qo=Qo, Q_ion=Q_ion, Ep=Ep, En=En, wl=wl):
+        def step(pc, lib=lib, sps=sps, e=e, b=b, dG=dG, dGp=dGp, Qn=Qn, Qo=Qo, Q_ion=Q_ion, Ep=Ep, En=En, wl=wl,
+                 cflag=cflag):
             dG.zero_()
-            Qn.copy_(Q_ion)
+            Qn.copy_(Qo if cflag else Q_ion)     # the charge change is added onto Q^n
             for k, s_ in enumerate(sps):
-                lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
+                lib.push_deposit(e, b, s_, wl.dt, dG, Qn,
+                                 flags=F.FP_ACCUMULATE | cflag | (F.FP_SAME_FIELDS if k else 0))
             F.fem_pic_field_step(lib.h, Ep, e, En, b, dG, dGp, Qn, tol=args.tol, max_iter=args.max_iter,
                                  precond=pc, info=False)
             Qo.copy_(Qn)
@@ -508,17 +520,17 @@ def run_gpu(args):
         ev = wl.E_amp * length * u
         ev[wall] = 0.0
         e.copy_(torch.as_tensor(ev, device=dev))
-    if args.deposits == "fp64":
-        lib.set_deposit_precision(F.FP_FP64)
-    DEP = lib.deposit_dtype
+    set_deposits(args, lib, F)
+    cflag = F.FP_CHARGE_CHANGE if args.deposits == "change" else 0
+    DEP, DQ = lib.deposit_dtype, lib.charge_dtype
     dG = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)       # dG^{n+1/2}
     dG_prev = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)  # dG^{n-1/2}
-    Qn = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
-    Qo = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
+    Qn = torch.zeros(sizes["n_nodes"], dtype=DQ, device=dev)
+    Qo = torch.zeros(sizes["n_nodes"], dtype=DQ, device=dev)
     res = torch.zeros(6, dtype=torch.float64, device=dev)
     # uniform immobile neutralising ion background where the workload has one:
     # Q_ion,n = -(total electron charge) alpha^0_n / V, alpha^0_n = integral of W0_n
-    Q_ion = torch.zeros(sizes["n_nodes"], dtype=DEP, device=dev)
+    Q_ion = torch.zeros(sizes["n_nodes"], dtype=DQ, device=dev)
     if wl.background_ions:
         alpha = F.fem_pic_whitney0_integrals(lib.h)
         qtot = sum(s_.q * s_.w * s_.n for s_ in species)
@@ -595,10 +607,10 @@ def run_gpu(args):
         s_ = bufs[k][b_]
         if k == 0:
             dG.zero_()
-            Qn.copy_(Q_ion)
+            Qn.copy_(Qo if cflag else Q_ion)     # the charge change is added onto Q^n
         # particles: gather at E^n, push, walk, deposit dG^{n+1/2}, Q^{n+1}; the field records
         # are made once per step (the first species' call)
-        lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | (F.FP_SAME_FIELDS if k else 0))
+        lib.push_deposit(e, b, s_, wl.dt, dG, Qn, flags=F.FP_ACCUMULATE | cflag | (F.FP_SAME_FIELDS if k else 0))
         n_k += 3 if k == 0 else 2     # field prep (first species), fast push, FP64 walk of the queue
         return n_k, s_
 
@@ -1213,7 +1225,8 @@ def run_gpu(args):
         fast_avg = fast_ms / max(1, fast_n)
         # bytes of one launch: one species' live particles (alive_eager counts all species),
         # its tet records and deposits
-        fbytes = fast_kernel_bytes(alive_eager / len(species), sizes, torch.empty(0, dtype=DEP).element_size())
+        fbytes = fast_kernel_bytes(alive_eager / len(species), sizes, torch.empty(0, dtype=DEP).element_size(),
+                                   torch.empty(0, dtype=DQ).element_size())
         fast_achieved = fbytes / (fast_avg * 1e-3) / 1e9
         roof_push = {"kernel": "k_push_run32", "bound": "hbm", "achieved": fast_achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": fast_achieved / peak,
@@ -1284,8 +1297,10 @@ def run_gpu(args):
                                   "initial state (particles absorbed by the PEC walls are not counted)",
                        "species": len(species), "dt_s": wl.dt, "B0_T": list(wl.B0),
                        "sort_every": args.sort_every, "precision": "fp32 particle path, fp64 walk test",
-                       "deposits": ("double dG and Q (FP32 contributions added with FP64 atomics)"
-                                    if DEP == torch.float64 else "float dG and Q (FP32 atomics)"),
+                       "deposits": {"fp64": "double dG and Q (FP32 contributions added with FP64 atomics)",
+                                    "change": "float dG (FP32 atomics); double Q carried from step to step, each "
+                                              "particle's FP32 charge change added with FP64 atomics",
+                                    "fp32": "float dG and Q (FP32 atomics)"}[args.deposits],
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "sort (periodic) + push/gather/walk/deposit + implicit field step "
@@ -1368,7 +1383,7 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
 
     # the Adams mover takes FP32 deposits: arrays of its own while it runs, the context's setting
     # restored after
-    dep_keep = F.fem_pic_deposit_precision(lib.h)
+    dep_keep = F.fem_pic_deposit_precision(lib.h), F.fem_pic_charge_precision(lib.h)
     lib.set_deposit_precision(F.FP_FP32)
     dG = torch.zeros(sizes["n_edges"], dtype=torch.float32, device=dev)
     Qn = torch.zeros(sizes["n_nodes"], dtype=torch.float32, device=dev)
@@ -1400,7 +1415,8 @@ def measure_adams(args, lib, F, species, restore, bufs, cur, e, b, dG, Qn, flush
     F.fem_pic_profile_enable(lib.h, False)
     ph = F.fem_pic_profile_read(lib.h, reset=True)
     st = lib.status()
-    lib.set_deposit_precision(dep_keep)
+    lib.set_deposit_precision(dep_keep[0])
+    lib.set_charge_precision(dep_keep[1])
     ms = sum(a.elapsed_time(z) for a, z in ev)
     n_live = sum(live) / len(live)
     f_ms, f_n = ph.get("adams_push", (float("nan"), 1))

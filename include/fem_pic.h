@@ -63,8 +63,10 @@ enum { FP_FP64 = 0, FP_FP32 = 1 };
 enum {
     FP_ACCUMULATE = 1, /* add into dG and Q instead of overwriting them */
     FP_NO_AGGREGATE = 2, /* one global atomic per contribution (no warp aggregation) */
-    FP_SAME_FIELDS = 4 /* e and b are those of this handle's previous push call, unchanged since:
-                          its per-tet field records are reused (e.g. the second species of a step) */
+    FP_SAME_FIELDS = 4, /* e and b are those of this handle's previous push call, unchanged since:
+                           its per-tet field records are reused (e.g. the second species of a step) */
+    FP_CHARGE_CHANGE = 8 /* Q receives the change of the W0 charge over the step (see
+                            fem_pic_push_deposit) instead of the charge at the end point */
 };
 
 typedef struct {
@@ -126,12 +128,30 @@ fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]);
  *            residual, needs correspondingly fewer iterations.
  * An FP64 context always deposits in FP64 (FP_FP64 accepted, FP_FP32 -> FP_EINVAL).  The FP32
  * Adams mover (fem_pic_push_deposit_adams) takes FP32 deposits only (FP_EINVAL otherwise).
+ * FP_FP32 sets Q back to float as well (see fem_pic_set_charge_precision).
  * The setting applies to calls made after it; arrays already passed keep their type.
  */
 fp_status fem_pic_set_deposit_precision(fem_pic_t* ctx, int precision);
 
-/* FP_FP32 or FP_FP64: the element type of this context's dG and Q arrays (-1 for NULL). */
+/* FP_FP32 or FP_FP64: the element type of this context's dG array, and of Q unless
+ * fem_pic_set_charge_precision changed it (-1 for NULL). */
 int fem_pic_deposit_precision(const fem_pic_t* ctx);
+
+/*
+ * Element type of the charge array Q alone (fem_pic_set_deposit_precision sets dG and Q
+ * together).  FP_FP64 with float dG suits FP_CHARGE_CHANGE: the step's charge change
+ * q w (lambda^end - lambda^start) is added onto the previous step's Q in FP64, so Q^{n+1}
+ * keeps continuity with D0^T dG to the rounding of the FP32 per-particle terms instead of
+ * the rounding of the FP32 sums of whole node charges.  FP_FP32 while dG is double, or in
+ * an FP64 context, is FP_EINVAL.  Applies to calls made after it.  Q's element type is
+ * what fem_pic_charge_precision returns, for every call that takes Q (the push calls,
+ * fem_pic_deposit_charge, fem_pic_field_step, fem_pic_field_initial, fem_pic_residuals
+ * and the comparison steps).
+ */
+fp_status fem_pic_set_charge_precision(fem_pic_t* ctx, int precision);
+
+/* FP_FP32 or FP_FP64: the element type of this context's Q array (-1 for NULL). */
+int fem_pic_charge_precision(const fem_pic_t* ctx);
 
 /*
  * Copy incidence matrix `which` (0: D0, 1: D1, 2: D2) to caller host buffers.
@@ -181,6 +201,14 @@ fp_status fem_pic_particles_to_global(fem_pic_t* ctx, int64_t n, const int32_t* 
  * pushed, is not finite (NaN or Inf, e.g. from a non-finite field DOF) is removed
  * (cell = -1) with nothing deposited and sets FP_EINVAL in the status word, so dG and Q
  * stay finite.  dG and Q are zeroed first unless FP_ACCUMULATE.
+ * With FP_CHARGE_CHANGE, Q is never zeroed and receives q w (lambda^end_n - lambda^start_n)
+ * per particle instead (the start charge subtracted on the start tet's nodes, the end charge
+ * added on the end tet's; a particle that stays in its tet adds the difference once; a
+ * removed particle with a finite start subtracts its start charge): a Q that holds the
+ * charge of the start positions (fem_pic_deposit_charge, or the previous step) becomes the
+ * charge of the end positions.  dG is zeroed unless FP_ACCUMULATE, as without the flag.
+ * The change equals D0^T dG exactly in real arithmetic (the continuity equation of
+ * Sec. II.A), so FP32 rounding touches only the change, not the node charges.
  * Particle arrays are updated in place.  Asynchronous.
  */
 fp_status fem_pic_push_deposit(fem_pic_t* ctx, const double* e, const double* b,
@@ -233,8 +261,8 @@ fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e, const dou
  * (cell -1) are left alone.  A particle's history must move with it: sort with
  * fem_pic_sort_columns(..., hist, hist_sorted, 18, ...).  The explicit method is stable for
  * gyration only while omega_c dt stays below about 0.43.  dG and Q are zeroed first unless
- * FP_ACCUMULATE.  Errors and asynchrony as fem_pic_push_deposit; hist NULL with n > 0 or
- * step < 0 returns FP_EINVAL.
+ * FP_ACCUMULATE.  Errors and asynchrony as fem_pic_push_deposit; hist NULL with n > 0,
+ * step < 0, FP_CHARGE_CHANGE, or double dG or Q in FP_FP32 mode return FP_EINVAL.
  */
 fp_status fem_pic_push_deposit_adams(fem_pic_t* ctx, const double* e, const double* b,
                                      const fp_particles* p, void* hist, int64_t step, double dt,

@@ -270,13 +270,32 @@ fp_status fem_pic_set_deposit_precision(fem_pic_t* ctx, int precision) {
         }
         return FP_OK;
     }
-    ctx->deposit64 = precision == FP_FP64 ? 1 : 0;
+    ctx->dG64 = ctx->Q64 = precision == FP_FP64 ? 1 : 0;
     return FP_OK;
 }
 
 int fem_pic_deposit_precision(const fem_pic_t* ctx) {
     if (!ctx) return -1;
-    return ctx->precision == FP_FP64 || ctx->deposit64 ? FP_FP64 : FP_FP32;
+    return ctx->precision == FP_FP64 || ctx->dG64 ? FP_FP64 : FP_FP32;
+}
+
+fp_status fem_pic_set_charge_precision(fem_pic_t* ctx, int precision) {
+    if (!ctx) return FP_EINVAL;
+    if (precision != FP_FP32 && precision != FP_FP64) {
+        ctx->err = "fem_pic_set_charge_precision: precision must be FP_FP32 or FP_FP64";
+        return FP_EINVAL;
+    }
+    if (precision == FP_FP32 && (ctx->precision == FP_FP64 || ctx->dG64)) {
+        ctx->err = "fem_pic_set_charge_precision: with double dG arrays Q is double too";
+        return FP_EINVAL;
+    }
+    if (ctx->precision == FP_FP32) ctx->Q64 = precision == FP_FP64 ? 1 : 0;
+    return FP_OK;
+}
+
+int fem_pic_charge_precision(const fem_pic_t* ctx) {
+    if (!ctx) return -1;
+    return ctx->precision == FP_FP64 || ctx->Q64 ? FP_FP64 : FP_FP32;
 }
 
 fp_status fem_pic_incidence(const fem_pic_t* ctx, int which, int32_t* row_ptr, int32_t* col,

@@ -914,7 +914,7 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
                           double* b, const void* dG_half, const void* dG_prev, const void* Q_new, double tol,
                           int max_iter, cudaStream_t s) {
     FieldDev* F = ctx->field;
-    const bool f32 = deposits_f32(ctx);   // dG and Q are float arrays
+    const bool f32 = dG_f32(ctx), q32 = Q_f32(ctx);   // dG, Q are float arrays
     const int ge = grid_of(ctx, F->ne), gn = grid_of(ctx, F->nn);
     {
         PhaseTimer pt(ctx, PH_SOLVE, s);
@@ -946,7 +946,7 @@ fp_status field_step_impl(fem_pic_t* ctx, const double* E_prev, const double* E_
         PhaseTimer pt(ctx, PH_SOLVE, s);
         if (F->last_fp64[0])
             k_spmv<<<ge, kBlock, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, E_next, F->ne, F->tmp);
-        if (f32)
+        if (q32)
             k_gauss_rhs<float><<<gn, kBlock, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, F->node_fixed,
                                                      F->tmp, (const float*)Q_new, F->nn, F->rhs, F->qd);
         else
@@ -1550,7 +1550,7 @@ fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double
     }
     cudaStream_t s = (cudaStream_t)stream;
     FieldDev* F = ctx->field;
-    const bool f32 = deposits_f32(ctx);   // dG and Q are float arrays
+    const bool f32 = Q_f32(ctx);   // Q is a float array
     const int gn = grid_of(ctx, F->nn), ge = grid_of(ctx, F->ne);
     FP_CUDA_TRY(ctx, cudaMemsetAsync(F->tmp, 0, F->ne * sizeof(double), s));
     if (f32)

@@ -106,7 +106,8 @@ struct fem_pic {
     double prof_ms[fempic::PH_COUNT] = {0};
     int64_t prof_n[fempic::PH_COUNT] = {0};
     int precision = FP_FP64;
-    int deposit64 = 0;  // FP32 mode: dG and Q are double arrays (fem_pic_set_deposit_precision)
+    int dG64 = 0;  // FP32 mode: dG is a double array (fem_pic_set_deposit_precision)
+    int Q64 = 0;   // FP32 mode: Q is a double array (fem_pic_set_deposit_precision, _charge_precision)
     fempic::HostComplex hc;
     // device tables
     fempic::TetGeo* d_geo = nullptr;
@@ -132,8 +133,7 @@ struct fem_pic {
     // warp-specialised Boris push, warp-specialised Adams push
     int tma_blocks_per_sm = 0;
     int ws_blocks_per_sm = 0;
-    int run_blocks_per_sm = 0;
-    int run_blocks_per_sm64 = 0;
+    int run_blocks_per_sm[4] = {0, 0, 0, 0};  // per (dG double) + 2 (Q double)
     int ws_adams_blocks_per_sm = 0;
     uint8_t* d_node_wall = nullptr;   // [nn] 1 = node on the PEC boundary
     // sort scratch
@@ -144,8 +144,9 @@ struct fem_pic {
     std::string err;
 };
 
-// dG and Q are float arrays (FP32 mode with FP32 deposits), else double
-inline bool deposits_f32(const fem_pic* ctx) { return ctx->precision == FP_FP32 && !ctx->deposit64; }
+// dG / Q are float arrays (FP32 mode with FP32 deposits), else double
+inline bool dG_f32(const fem_pic* ctx) { return ctx->precision == FP_FP32 && !ctx->dG64; }
+inline bool Q_f32(const fem_pic* ctx) { return ctx->precision == FP_FP32 && !ctx->Q64; }
 
 #define FP_CUDA_TRY(ctx, call)                                                             \
     do {                                                                                   \

@@ -191,7 +191,7 @@ fp_status launch_rhs(fem_pic_mfem* m, const double* x, const double* y, double a
     const FieldDev* F = ctx->field;
     const Sell Sl{F->se_ptr, F->se_w, F->se_col};
     const int g = grid_for(ctx, m->ne);
-    if (deposits_f32(ctx))
+    if (dG_f32(ctx))
         k_rhs<float><<<g, kThreads, 0, s>>>(Sl, F->se_M, F->se_S, F->edge_fixed, x, y, a1, a2, b1, b2, m->ef_rp,
                                             m->ef_col, m->ef_sgn, h, c, (const float*)gh, (const float*)gp, m->ne,
                                             m->rhs);
@@ -337,7 +337,7 @@ fp_status fem_pic_mfem_gauss_residual(fem_pic_mfem_t* m, const double* E, const 
     }
     const FieldDev* F = ctx->field;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool f32 = deposits_f32(ctx);   // dG and Q are float arrays
+    const bool f32 = Q_f32(ctx);   // Q is a float array
     const bool natural = F->bc == FP_BC_NEUMANN && Q != nullptr;
     k_mass<<<grid_for(ctx, m->ne), kThreads, 0, s>>>(Sell{F->se_ptr, F->se_w, F->se_col}, F->se_M, E, m->ne, m->me);
     if (natural) {

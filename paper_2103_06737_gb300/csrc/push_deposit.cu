@@ -217,25 +217,36 @@ __device__ __forceinline__ void warp_run_reduce(int key, Real v[NV], unsigned* h
 // found by cross-multiplication (one division per crossing).  The deposit products are
 // in Real; the current point, needed only when the walk stops early, is tracked in
 // Real as well.
-template <typename Real, typename D = Real>
+//
+// cc (charge change): Q receives the change of the particle's W0 charge over the step, its
+// end point's charge minus its start point's (the start's, where a particle is removed for a
+// non-finite push), instead of the end point's charge.
+template <typename Real, typename DG = Real, typename DQ = DG>
 __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, int c,
                           const double xa[3], const double xb[3], double qw, int max_cross,
-                          D* __restrict__ dG, D* __restrict__ Q, int32_t* __restrict__ status,
-                          Real* agg, int* end_cell, double end_off[3]) {
-    if (!(finite_bits(xa[0]) && finite_bits(xa[1]) && finite_bits(xa[2]) && finite_bits(xb[0]) &&
-          finite_bits(xb[1]) && finite_bits(xb[2]))) {
+                          DG* __restrict__ dG, DQ* __restrict__ Q, int32_t* __restrict__ status,
+                          Real* agg, int* end_cell, double end_off[3], bool cc = false) {
+    Geo G;
+    TetTopo Tc;
+    double la[4], rel[3], os[3];
+    const bool start_finite = finite_bits(xa[0]) && finite_bits(xa[1]) && finite_bits(xa[2]);
+    if (!(start_finite && finite_bits(xb[0]) && finite_bits(xb[1]) && finite_bits(xb[2]))) {
         // a non-finite start or end point has no path: the particle is removed, nothing deposited
+        // (with cc, its start point's charge leaves Q where the start is finite)
         atomicOr(status, ST_NONFINITE);
         *end_cell = -1;
 #pragma unroll
         for (int i = 0; i < 3; ++i) end_off[i] = xa[i];
+        if (cc && start_finite) {
+            load_geo(geo, c, G);
+            load_topo(topo, c, Tc);
+            bary(G, xa, la);
+            deposit_charge<Real, DQ>(Tc, la, -qw, Q);
+        }
         return false;
     }
-    Geo G;
-    TetTopo Tc;
     load_geo(geo, c, G);
     load_topo(topo, c, Tc);
-    double la[4], rel[3], os[3];
     bary(G, xa, la);
     Real ca[3], cb[3];
 #pragma unroll
@@ -290,15 +301,23 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
             if (nc == 0 && agg) {
                 piece_values<Real>(la, lb, qw, agg);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) agg[6 + k] = to_real<Real>(qw) * to_real<Real>(lb[k]);
+                for (int k = 0; k < 4; ++k)
+                    agg[6 + k] = to_real<Real>(qw) * to_real<Real>(cc ? lb[k] - la[k] : lb[k]);
                 return true;
             }
-            deposit_piece<Real, D>(Tc, la, lb, qw, dG);
-            deposit_charge<Real, D>(Tc, lb, qw, Q);
+            deposit_piece<Real, DG>(Tc, la, lb, qw, dG);
+            if (cc && nc == 0) {   // still in the start tet: the change of its nodes' charge
+                double lq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) lq[k] = lb[k] - la[k];
+                deposit_charge<Real, DQ>(Tc, lq, qw, Q);
+            } else {
+                deposit_charge<Real, DQ>(Tc, lb, qw, Q);
+            }
             return false;
         }
         if (nc == max_cross) {  // bound reached: stop at the last crossing point
-            deposit_charge<Real, D>(Tc, la, qw, Q);
+            if (!cc || nc > 0) deposit_charge<Real, DQ>(Tc, la, qw, Q);   // (cc, no crossing: no change)
             atomicOr(status, ST_WALK);
             *end_cell = t;
 #pragma unroll
@@ -308,13 +327,14 @@ __device__ bool walk_fp64(const TetGeo* __restrict__ geo, const TetTopo* __restr
         double lc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) lc[k] = (k == kx) ? 0.0 : la[k] + smin * (lb[k] - la[k]);
-        deposit_piece<Real, D>(Tc, la, lc, qw, dG);
+        if (cc && nc == 0) deposit_charge<Real, DQ>(Tc, la, -qw, Q);   // the start point's charge leaves
+        deposit_piece<Real, DG>(Tc, la, lc, qw, dG);
         const Real sr = to_real<Real>(smin);
 #pragma unroll
         for (int i = 0; i < 3; ++i) ca[i] = ca[i] + sr * (cb[i] - ca[i]);
         const int tn = kx == 0 ? Tc.nb[0] : (kx == 1 ? Tc.nb[1] : (kx == 2 ? Tc.nb[2] : Tc.nb[3]));
         if (tn < 0) {  // PEC wall: absorbed, its charge stays at the wall point
-            deposit_charge<Real, D>(Tc, lc, qw, Q);
+            deposit_charge<Real, DQ>(Tc, lc, qw, Q);
             *end_cell = -1;
 #pragma unroll
             for (int i = 0; i < 3; ++i) end_off[i] = to_f64(ca[i]) + (os[i] - G.o[i]);
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(256) k_push_deposit(
     const TetGeo* __restrict__ geo, const TetTopo* __restrict__ topo, const double* __restrict__ f64,
     int32_t* __restrict__ cell, Real* __restrict__ off,
     Real* __restrict__ vel, int64_t n, int32_t nt, double qmdt2, Real dt, double qw, int max_cross,
-    int aggregate, Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status) {
+    int aggregate, Real* __restrict__ dG, Real* __restrict__ Q, int32_t* __restrict__ status, int cc) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(256) k_push_deposit(
             int end_cell;
             double end_off[3];
             if (walk_fp64<Real>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, aggregate ? agg : nullptr,
-                                &end_cell, end_off))
+                                &end_cell, end_off, cc != 0))
                 key = c;
             cell[p] = end_cell;
             off[p] = (Real)end_off[0];
@@ -758,7 +778,8 @@ __device__ __forceinline__ int fast_core(const TetHot& H, const float x[3], floa
     return kFastStay;
 }
 
-__device__ __forceinline__ void deposit_values(float w, const float l[4], const float d[4], float agg[10]) {
+__device__ __forceinline__ void deposit_values(float w, const float l[4], const float d[4], float agg[10],
+                                               bool cc = false) {
     agg[0] = w * (l[0] * d[1] - l[1] * d[0]);
     agg[1] = w * (l[0] * d[2] - l[2] * d[0]);
     agg[2] = w * (l[0] * d[3] - l[3] * d[0]);
@@ -766,7 +787,7 @@ __device__ __forceinline__ void deposit_values(float w, const float l[4], const 
     agg[4] = w * (l[1] * d[3] - l[3] * d[1]);
     agg[5] = w * (l[2] * d[3] - l[3] * d[2]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) agg[6 + k] = w * (l[k] + d[k]);
+    for (int k = 0; k < 4; ++k) agg[6 + k] = w * (cc ? d[k] : l[k] + d[k]);   // cc: the charge change
 }
 
 // One particle per lane; c < 0 means no particle.  All 32 lanes of the warp must call
@@ -774,12 +795,12 @@ __device__ __forceinline__ void deposit_values(float w, const float l[4], const 
 // go to the FP64 walk; the caller queues it.  Records of cells [rec_lo, rec_lo + rec_n)
 // are read from the shared-memory window `rec` (records kRecStride bytes apart), the others
 // from global memory.
-template <class Mover, typename D = float>
+template <class Mover, typename DG = float, typename DQ = DG>
 __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
                                               int rec_n, int c, const float x[3], float v[3], int64_t p, int64_t n,
                                               int32_t nt, Mover& mv, float w, int aggregate, int32_t* __restrict__ cell,
-                                              float* __restrict__ off, D* __restrict__ dG, D* __restrict__ Q,
-                                              int32_t* __restrict__ status) {
+                                              float* __restrict__ off, DG* __restrict__ dG, DQ* __restrict__ Q,
+                                              int32_t* __restrict__ status, bool cc = false) {
     const int lane = threadIdx.x & 31;
     if (c >= nt) {
         atomicOr(status, ST_INVAL);
@@ -806,10 +827,16 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         const int r3 = fast_core(H, x, v, p, mv, xb, l, d);
         if (r3 == kFastNonFinite) {
             // the particle is removed with nothing deposited, and the status word says so
+            // (with cc, its start point's charge leaves Q where the start is finite)
             atomicOr(status, ST_NONFINITE);
             cell[p] = -1;
+            if (cc && finite_bits(l[0]) && finite_bits(l[1]) && finite_bits(l[2]) && finite_bits(l[3])) {
+                ids_of(hot, rec, rec_lo, in_win, c, H);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)(-w * l[k]));
+            }
         } else if (r3 == kFastStay) {
-            deposit_values(w, l, d, agg);
+            deposit_values(w, l, d, agg, cc);
             off[p] = xb[0];
             off[n + p] = xb[1];
             off[2 * n + p] = xb[2];
@@ -818,9 +845,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             if (!aggregate) {
                 ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (D)agg[k]);
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (DG)agg[k]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)agg[6 + k]);
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)agg[6 + k]);
             }
         } else {
             slow = true;
@@ -833,9 +860,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         if (((heads >> lane) & 1u) && key >= 0) {
             ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (D)agg[k]);
+            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (DG)agg[k]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)agg[6 + k]);
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)agg[6 + k]);
         }
     }
     return slow;
@@ -859,12 +886,12 @@ __device__ __forceinline__ void warp_enqueue(bool slow, int32_t value, int32_t* 
 #endif
 // Grid-stride variant: the particle state is loaded straight from global memory (the
 // next particle's cell one iteration ahead).
-template <typename D>
+template <typename DG, typename DQ>
 __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off,
     float* __restrict__ vel, int64_t n, int32_t nt, float h, float dt, double qw, int aggregate,
-    D* __restrict__ dG, D* __restrict__ Q, int32_t* __restrict__ slow_idx,
-    int32_t* __restrict__ slow_count, int32_t* __restrict__ status) {
+    DG* __restrict__ dG, DQ* __restrict__ Q, int32_t* __restrict__ slow_idx,
+    int32_t* __restrict__ slow_count, int32_t* __restrict__ status, int cc) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float w = (float)qw;
@@ -883,8 +910,8 @@ __global__ void __launch_bounds__(256, FP_FAST_MIN_BLOCKS) k_push_fast32(
             x[0] = off[p], x[1] = off[n + p], x[2] = off[2 * n + p];
             v[0] = vel[p], v[1] = vel[n + p], v[2] = vel[2 * n + p];
         }
-        const bool slow =
-            fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, bm, w, aggregate, cell, off, dG, Q, status);
+        const bool slow = fast_particle(hot, nullptr, 0, 0, c, x, v, p, n, nt, bm, w, aggregate, cell, off, dG, Q,
+                                        status, cc != 0);
         warp_enqueue(slow, (int32_t)p, slow_idx, slow_count);   // one global atomic per warp
     }
 }
@@ -1315,10 +1342,10 @@ static_assert(kRunSlot % 16 == 0 && kRunStageBytes % 16 == 0 && kRunRecBytes % 1
 
 // the 10 atomics of one run, its sums a times the weight w: node ids and edge ids from
 // record c (shared window or global)
-template <typename D>
+template <typename DG, typename DQ>
 __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const unsigned char* rec, int rec_lo,
-                                          int rec_n, int c, float w, const float a[10], D* __restrict__ dG,
-                                          D* __restrict__ Q) {
+                                          int rec_n, int c, float w, const float a[10], DG* __restrict__ dG,
+                                          DQ* __restrict__ Q) {
     int4 nd, e03, e45;
     if ((unsigned)(c - rec_lo) < (unsigned)rec_n) {
         const int4* r = reinterpret_cast<const int4*>(rec + (c - rec_lo) * kRecStride);
@@ -1331,20 +1358,21 @@ __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const 
         e03 = __ldg(r + 1);
         e45 = __ldg(r + 2);
     }
-    atomicAdd(dG + e03.x, (D)(w * a[0]));
-    atomicAdd(dG + e03.y, (D)(w * a[1]));
-    atomicAdd(dG + e03.z, (D)(w * a[2]));
-    atomicAdd(dG + e03.w, (D)(w * a[3]));
-    atomicAdd(dG + e45.x, (D)(w * a[4]));
-    atomicAdd(dG + e45.y, (D)(w * a[5]));
-    atomicAdd(Q + nd.x, (D)(w * a[6]));
-    atomicAdd(Q + nd.y, (D)(w * a[7]));
-    atomicAdd(Q + nd.z, (D)(w * a[8]));
-    atomicAdd(Q + nd.w, (D)(w * a[9]));
+    atomicAdd(dG + e03.x, (DG)(w * a[0]));
+    atomicAdd(dG + e03.y, (DG)(w * a[1]));
+    atomicAdd(dG + e03.z, (DG)(w * a[2]));
+    atomicAdd(dG + e03.w, (DG)(w * a[3]));
+    atomicAdd(dG + e45.x, (DG)(w * a[4]));
+    atomicAdd(dG + e45.y, (DG)(w * a[5]));
+    atomicAdd(Q + nd.x, (DQ)(w * a[6]));
+    atomicAdd(Q + nd.y, (DQ)(w * a[7]));
+    atomicAdd(Q + nd.z, (DQ)(w * a[8]));
+    atomicAdd(Q + nd.w, (DQ)(w * a[9]));
 }
 
-// a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, l_k + d_k)
-__device__ __forceinline__ void run_add(float a[10], const float l[4], const float d[4]) {
+// a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, and l_k + d_k,
+// or d_k for the charge change)
+__device__ __forceinline__ void run_add(float a[10], const float l[4], const float d[4], bool cc) {
     a[0] = fmaf(-l[1], d[0], fmaf(l[0], d[1], a[0]));
     a[1] = fmaf(-l[2], d[0], fmaf(l[0], d[2], a[1]));
     a[2] = fmaf(-l[3], d[0], fmaf(l[0], d[3], a[2]));
@@ -1352,7 +1380,7 @@ __device__ __forceinline__ void run_add(float a[10], const float l[4], const flo
     a[4] = fmaf(-l[3], d[1], fmaf(l[1], d[3], a[4]));
     a[5] = fmaf(-l[3], d[2], fmaf(l[2], d[3], a[5]));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a[6 + k] += l[k] + d[k];
+    for (int k = 0; k < 4; ++k) a[6 + k] += cc ? d[k] : l[k] + d[k];
 }
 
 // Boris with the new velocity stored into the staged tile (position j of its planes)
@@ -1386,12 +1414,12 @@ __device__ __forceinline__ void stage_issue(unsigned char* stage, uint64_t* bar,
     for (int k = 0; k < 3; ++k) bulk_g2s(stage + (4 + k) * kSlot, vel + k * n + p0, bytes, bar);
 }
 
-template <typename D>
+template <typename DG, typename DQ>
 __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
     const TetHot* __restrict__ hot, int32_t* __restrict__ cell, float* __restrict__ off, float* __restrict__ vel,
-    int64_t n, int32_t nt, float h, float dt, float w, int aggregate, D* __restrict__ dG,
-    D* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
-    int32_t* __restrict__ status) {
+    int64_t n, int32_t nt, float h, float dt, float w, int aggregate, DG* __restrict__ dG,
+    DQ* __restrict__ Q, int32_t* __restrict__ slow_idx, int32_t* __restrict__ slow_count,
+    int32_t* __restrict__ status, int cc_) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kRunStages], empty[kRunStages], recb[kRunStages];
     __shared__ int rec_lo[kRunStages], rec_n[kRunStages];
@@ -1494,6 +1522,7 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
     }
     // ---------------- consumers
     const int jb = (warp * 32 + lane) * kRunK;
+    const bool cc = cc_ != 0;   // Q takes the charge change over the step (the end's minus the start's)
     for (int it = 0; it < mine; ++it) {
         const int sk = it % kRunStages;
         const uint32_t par = (uint32_t)((it / kRunStages) & 1);
@@ -1582,19 +1611,28 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
                 if (r3 == kFastNonFinite) {
                     atomicOr(status, ST_NONFINITE);
                     cell[p0 + j] = -1;
+                    if (cc && finite_bits(l[0]) && finite_bits(l[1]) && finite_bits(l[2]) && finite_bits(l[3])) {
+                        // the removed particle's start charge leaves Q
+                        float a[10];
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) a[k] = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) a[6 + k] = -l[k];
+                        run_flush(hot, rec, rlo, rn, c, w, a, dG, Q);
+                    }
                 } else if (r3 == kFastWalk) {
                     slow_bits |= 1u << i;
                 } else {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) sx[k][j] = xb[k];
                     if (aggregate) {
-                        run_add(acc, l, d);
+                        run_add(acc, l, d, cc);
                         live = true;
                     } else {
                         float a[10];
 #pragma unroll
                         for (int k = 0; k < 10; ++k) a[k] = 0.f;
-                        run_add(a, l, d);
+                        run_add(a, l, d, cc);
                         run_flush(hot, rec, rlo, rn, c, w, a, dG, Q);
                     }
                 }
@@ -1645,16 +1683,16 @@ __global__ void __launch_bounds__(kRunThreads, FP_RUN_MIN_BLOCKS) k_push_run32(
 // FP64 walk of the queued particles (near or across a face).  The end point is
 // recomputed from the stored start offset and the updated velocity with the same
 // FP32 operations as in k_push_fast32.
-template <typename D>
+template <typename DG, typename DQ>
 __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
                                                 const TetTopo* __restrict__ topo,
                                                 int32_t* __restrict__ cell, float* __restrict__ off,
                                                 const float* __restrict__ vel, int64_t n, float dt,
-                                                double qw, int max_cross, D* __restrict__ dG,
-                                                D* __restrict__ Q,
+                                                double qw, int max_cross, DG* __restrict__ dG,
+                                                DQ* __restrict__ Q,
                                                 const int32_t* __restrict__ slow_idx,
                                                 const int32_t* __restrict__ slow_count,
-                                                int32_t* __restrict__ status) {
+                                                int32_t* __restrict__ status, int cc) {
     const int64_t m = *slow_count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
@@ -1673,7 +1711,8 @@ __global__ void __launch_bounds__(128) k_walk32(const TetGeo* __restrict__ geo,
         }
         int end_cell;
         double end_off[3];
-        walk_fp64<float, D>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off);
+        walk_fp64<float, DG, DQ>(geo, topo, c, xa, xb, qw, max_cross, dG, Q, status, nullptr, &end_cell, end_off,
+                                 cc != 0);
         cell[p] = end_cell;
 #pragma unroll
         for (int k = 0; k < 3; ++k) off[k * n + p] = d2f(end_off[k]);
@@ -1929,10 +1968,12 @@ int grid_for(int64_t n, int sms) {
 
 // the fast FP32 push: the TMA-staged persistent kernel (grid = co-resident blocks), or the
 // grid-stride kernel when the state arrays are not 16-byte aligned
-template <typename D>
+template <typename DG, typename DQ>
 fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
-                          D* dG, D* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
-    constexpr bool d64 = sizeof(D) == 8;   // FP64 deposits: the run-summing or the grid-stride kernel
+                          DG* dG, DQ* Q, int cc, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
+    // FP64 deposit arrays or the charge change: the run-summing or the grid-stride kernel
+    constexpr int kind = (sizeof(DG) == 8 ? 1 : 0) + (sizeof(DQ) == 8 ? 2 : 0);
+    const bool d64 = kind != 0 || cc != 0;
     const size_t smem = (size_t)kTmaSmem;
     if (ctx->tma_blocks_per_sm == 0) {
         FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1950,10 +1991,9 @@ fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float
 #define FP_PUSH_TMA 1
 #endif
     if (!aligned || (!FP_PUSH_TMA && !d64)) {   // the bulk copies need 16-byte aligned starts and lengths
-        k_push_fast32<D><<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(ctx->d_hot, p->cell, (float*)p->off,
-                                                                     (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q,
-                                                                     slow_idx, slow_count,
-                                                                     ctx->d_status);
+        k_push_fast32<DG, DQ><<<grid_for(p->n, ctx->sm_count), 256, 0, s>>>(
+            ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt, h, dt, qw, agg, dG, Q, slow_idx,
+            slow_count, ctx->d_status, cc);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
@@ -1961,13 +2001,13 @@ fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float
 #define FP_PUSH_RUN 1
 #endif
     if (FP_PUSH_RUN || d64) {   // warp-specialised pipeline, runs summed per lane
-        int& per_sm_cached = d64 ? ctx->run_blocks_per_sm64 : ctx->run_blocks_per_sm;
+        int& per_sm_cached = ctx->run_blocks_per_sm[kind];
         if (per_sm_cached == 0) {
-            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_run32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            FP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_push_run32<DG, DQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   kRunSmem));
             int per_sm = 0;
-            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_run32<D>, kRunThreads,
-                                                                           kRunSmem));
+            FP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_run32<DG, DQ>,
+                                                                           kRunThreads, kRunSmem));
             if (per_sm < 1) {
                 ctx->err = "fem_pic_push_deposit: the staged push kernel does not fit on an SM";
                 return FP_ECUDA;
@@ -1977,16 +2017,16 @@ fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float
         const int64_t rtiles = (p->n + kRunTile - 1) / kRunTile;
         int64_t rgrid = (int64_t)ctx->sm_count * per_sm_cached;
         if (rgrid > rtiles) rgrid = rtiles;
-        k_push_run32<D><<<(int)rgrid, kRunThreads, kRunSmem, s>>>(ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel,
-                                                               p->n, nt, h, dt, (float)qw, agg, dG, Q, slow_idx,
-                                                               slow_count, ctx->d_status);
+        k_push_run32<DG, DQ><<<(int)rgrid, kRunThreads, kRunSmem, s>>>(
+            ctx->d_hot, p->cell, (float*)p->off, (float*)p->vel, p->n, nt, h, dt, (float)qw, agg, dG, Q, slow_idx,
+            slow_count, ctx->d_status, cc);
         FP_CUDA_TRY(ctx, cudaGetLastError());
         return FP_OK;
     }
 #ifndef FP_PUSH_WS
 #define FP_PUSH_WS 1
 #endif
-    if constexpr (d64) {
+    if constexpr (kind != 0) {
         return FP_OK;   // not reached: FP64 deposits take the run-summing kernel above
     } else {
     if (FP_PUSH_WS) {   // warp-specialised pipeline
@@ -2023,26 +2063,35 @@ fp_status launch_fast32_t(fem_pic* ctx, const fp_particles* p, int32_t nt, float
 }
 
 // the FP64 walk of the queued particles, with the deposit arrays' element type
+template <typename DG, typename DQ>
+void launch_walk32_t(fem_pic* ctx, const fp_particles* p, float dt, double qw, int max_cross, void* dG, void* Q,
+                     int cc, const int32_t* slow_idx, const int32_t* slow_count, cudaStream_t s) {
+    k_walk32<DG, DQ><<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
+                                                       (const float*)p->vel, p->n, dt, qw, max_cross, (DG*)dG,
+                                                       (DQ*)Q, slow_idx, slow_count, ctx->d_status, cc);
+}
+
 void launch_walk32(fem_pic* ctx, const fp_particles* p, float dt, double qw, int max_cross, void* dG, void* Q,
-                   const int32_t* slow_idx, const int32_t* slow_count, cudaStream_t s) {
-    if (ctx->deposit64)
-        k_walk32<double><<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
-                                                           (const float*)p->vel, p->n, dt, qw, max_cross,
-                                                           (double*)dG, (double*)Q, slow_idx, slow_count,
-                                                           ctx->d_status);
+                   int cc, const int32_t* slow_idx, const int32_t* slow_count, cudaStream_t s) {
+    if (ctx->dG64)
+        launch_walk32_t<double, double>(ctx, p, dt, qw, max_cross, dG, Q, cc, slow_idx, slow_count, s);
+    else if (ctx->Q64)
+        launch_walk32_t<float, double>(ctx, p, dt, qw, max_cross, dG, Q, cc, slow_idx, slow_count, s);
     else
-        k_walk32<float><<<ctx->sm_count * 4, 128, 0, s>>>(ctx->d_geo, ctx->d_topo, p->cell, (float*)p->off,
-                                                          (const float*)p->vel, p->n, dt, qw, max_cross,
-                                                          (float*)dG, (float*)Q, slow_idx, slow_count,
-                                                          ctx->d_status);
+        launch_walk32_t<float, float>(ctx, p, dt, qw, max_cross, dG, Q, cc, slow_idx, slow_count, s);
 }
 
 // the fast FP32 push with the deposit arrays' element type
 fp_status launch_fast32(fem_pic* ctx, const fp_particles* p, int32_t nt, float h, float dt, double qw, int agg,
-                        void* dG, void* Q, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
-    if (ctx->deposit64)
-        return launch_fast32_t<double>(ctx, p, nt, h, dt, qw, agg, (double*)dG, (double*)Q, slow_idx, slow_count, s);
-    return launch_fast32_t<float>(ctx, p, nt, h, dt, qw, agg, (float*)dG, (float*)Q, slow_idx, slow_count, s);
+                        void* dG, void* Q, int cc, int32_t* slow_idx, int32_t* slow_count, cudaStream_t s) {
+    if (ctx->dG64)
+        return launch_fast32_t<double, double>(ctx, p, nt, h, dt, qw, agg, (double*)dG, (double*)Q, cc, slow_idx,
+                                               slow_count, s);
+    if (ctx->Q64)
+        return launch_fast32_t<float, double>(ctx, p, nt, h, dt, qw, agg, (float*)dG, (double*)Q, cc, slow_idx,
+                                              slow_count, s);
+    return launch_fast32_t<float, float>(ctx, p, nt, h, dt, qw, agg, (float*)dG, (float*)Q, cc, slow_idx,
+                                         slow_count, s);
 }
 
 }  // namespace
@@ -2070,11 +2119,12 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
                               double dt, int max_cross, void* dG, void* Q, int flags,
                               cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
-    const size_t rs = deposits_f32(ctx) ? 4 : 8;
-    if (!(flags & FP_ACCUMULATE)) {
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
+    if (!(flags & FP_ACCUMULATE)) {   // the charge change is always added onto Q
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, (dG_f32(ctx) ? 4 : 8) * ctx->hc.ne, s));
+        if (!(flags & FP_CHARGE_CHANGE))
+            FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (Q_f32(ctx) ? 4 : 8) * ctx->hc.nn, s));
     }
+    const int cc = (flags & FP_CHARGE_CHANGE) ? 1 : 0;
     if (p->n == 0) return FP_OK;
     const double qmdt2 = p->q * dt / (2.0 * p->m);
     const double qw = p->q * p->w;
@@ -2090,13 +2140,13 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
         }
         {
             PhaseTimer pt(ctx, PH_FAST, s);
-            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, dG, Q,
+            fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, dG, Q, cc,
                                          ctx->d_slow_idx, ctx->d_slow_count, s);
             if (sf != FP_OK) return sf;
         }
         {
             PhaseTimer pt(ctx, PH_WALK, s);
-            launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, ctx->d_slow_idx, ctx->d_slow_count, s);
+            launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, cc, ctx->d_slow_idx, ctx->d_slow_count, s);
         }
     } else {
         if (!(flags & FP_SAME_FIELDS)) {
@@ -2108,7 +2158,7 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
         k_push_deposit<double><<<grid, 256, 0, s>>>(ctx->d_geo, ctx->d_topo, ctx->d_field64, p->cell,
                                                     (double*)p->off, (double*)p->vel, p->n, nt, qmdt2, dt,
                                                     qw, max_cross, agg, (double*)dG, (double*)Q,
-                                                    ctx->d_status);
+                                                    ctx->d_status, cc);
     }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
@@ -2117,8 +2167,12 @@ fp_status launch_push_deposit(fem_pic* ctx, const double* e, const double* b, co
 fp_status launch_push_adams(fem_pic* ctx, const double* e, const double* b, const fp_particles* p, void* hist,
                             int64_t step, double dt, int max_cross, void* dG, void* Q, int flags, cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
-    if (f32 && ctx->deposit64) {
+    if (f32 && (ctx->dG64 || ctx->Q64)) {
         ctx->err = "fem_pic_push_deposit_adams: FP64 deposits are not available for the Adams mover in FP32 mode";
+        return FP_EINVAL;
+    }
+    if (flags & FP_CHARGE_CHANGE) {
+        ctx->err = "fem_pic_push_deposit_adams: the charge-change deposit is not available for the Adams mover";
         return FP_EINVAL;
     }
     const size_t rs = f32 ? 4 : 8;
@@ -2222,12 +2276,12 @@ fp_status launch_wait_selftest(fem_pic* ctx, double limit_s, cudaStream_t s) {
 fp_status launch_deposit_charge(fem_pic* ctx, const fp_particles* p, void* Q, int flags,
                                 cudaStream_t s) {
     const bool f32 = ctx->precision == FP_FP32;
-    if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (deposits_f32(ctx) ? 4 : 8) * ctx->hc.nn, s));
+    if (!(flags & FP_ACCUMULATE)) FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (Q_f32(ctx) ? 4 : 8) * ctx->hc.nn, s));
     if (p->n == 0) return FP_OK;
     const double qw = p->q * p->w;
     const int grid = grid_for(p->n, ctx->sm_count);
     PhaseTimer pt(ctx, PH_CHARGE, s);
-    if (f32 && ctx->deposit64)
+    if (f32 && ctx->Q64)
         k_deposit_charge32<double><<<grid, 256, 0, s>>>(ctx->d_hot, p->cell, (const float*)p->off, p->n,
                                                         (int32_t)ctx->hc.nt, qw, (double*)Q, ctx->d_status);
     else if (f32)
@@ -2304,10 +2358,10 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
         ctx->err = "fem_pic_push_deposit_static: the fixed queue's device address is unknown";
         return FP_ECUDA;
     }
-    if (!(flags & FP_ACCUMULATE)) {
-        const size_t rs = ctx->deposit64 ? sizeof(double) : sizeof(float);
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, rs * ctx->hc.ne, s));
-        FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, rs * ctx->hc.nn, s));
+    if (!(flags & FP_ACCUMULATE)) {   // the charge change is always added onto Q
+        FP_CUDA_TRY(ctx, cudaMemsetAsync(dG, 0, (dG_f32(ctx) ? 4 : 8) * ctx->hc.ne, s));
+        if (!(flags & FP_CHARGE_CHANGE))
+            FP_CUDA_TRY(ctx, cudaMemsetAsync(Q, 0, (Q_f32(ctx) ? 4 : 8) * ctx->hc.nn, s));
     }
     FP_CUDA_TRY(ctx, cudaMemsetAsync(q, 0, sizeof(int32_t), s));
     if (p->n == 0) return FP_OK;
@@ -2324,12 +2378,13 @@ extern "C" fp_status fem_pic_push_deposit_static(fem_pic_t* ctx, const double* e
         // the same kernel choice as fem_pic_push_deposit (staged pipeline for aligned state)
         PhaseTimer pt(ctx, PH_FAST, s);
         const fp_status sf = launch_fast32(ctx, p, nt, (float)qmdt2, (float)dt, qw, agg, dG, Q,
-                                           q + kStaticHead, q, s);
+                                           (flags & FP_CHARGE_CHANGE) ? 1 : 0, q + kStaticHead, q, s);
         if (sf != FP_OK) return sf;
     }
     {
         PhaseTimer pt(ctx, PH_WALK, s);
-        launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, q + kStaticHead, q, s);
+        launch_walk32(ctx, p, (float)dt, qw, max_cross, dG, Q, (flags & FP_CHARGE_CHANGE) ? 1 : 0, q + kStaticHead,
+                      q, s);
     }
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;

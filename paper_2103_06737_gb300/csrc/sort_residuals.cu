@@ -186,13 +186,13 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 // on bit patterns and the scales in FP32, so the FP64 pipe only does the sums.
 //   blocks [0, nb_cont): continuity r_n = (D0^T dG)_n - (Q_new - Q_old)_n, a thread per node;
 //   blocks [nb_cont, ...): magnetic Gauss law r_t = (D2 b)_t, a thread per tet.
-template <typename Real>
+template <typename Real, typename RealQ>
 __global__ void __launch_bounds__(256) k_residuals(const int32_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ col,
                                                    const int8_t* __restrict__ sgn, int64_t nn,
                                                    const Real* __restrict__ dG,
-                                                   const Real* __restrict__ Qn,
-                                                   const Real* __restrict__ Qo,
+                                                   const RealQ* __restrict__ Qn,
+                                                   const RealQ* __restrict__ Qo,
                                                    const uint8_t* __restrict__ wall,
                                                    const int4* __restrict__ tet_faces, int64_t nt,
                                                    const double* __restrict__ b, int nb_cont,
@@ -316,6 +316,14 @@ fp_status launch_sort(fem_pic* ctx, const fp_particles* src, fp_particles* dst, 
     return FP_OK;
 }
 
+template <typename DG, typename DQ>
+void residuals_t(fem_pic* ctx, const void* dG, const void* Qn, const void* Qo, const double* b, int nb_cont,
+                 int grid, double* out, cudaStream_t s) {
+    k_residuals<DG, DQ><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, ctx->hc.nn,
+                                             (const DG*)dG, (const DQ*)Qn, (const DQ*)Qo, ctx->d_node_wall,
+                                             ctx->d_tet_faces, ctx->hc.nt, b, nb_cont, out);
+}
+
 fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const void* Qo,
                            const double* b, double* out, cudaStream_t s) {
     PhaseTimer pt(ctx, PH_RESID, s);
@@ -324,16 +332,12 @@ fp_status launch_residuals(fem_pic* ctx, const void* dG, const void* Qn, const v
     const int nb_cont = grid_cap(nn, 256, 4, ctx->sm_count);
     const int nb_div = grid_cap(nt, 256, 4, ctx->sm_count);
     const int grid = nb_cont + nb_div;
-    if (deposits_f32(ctx))
-        k_residuals<float><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn,
-                                                (const float*)dG, (const float*)Qn, (const float*)Qo,
-                                                ctx->d_node_wall, ctx->d_tet_faces, nt, b,
-                                                nb_cont, out);
+    if (dG_f32(ctx) && Q_f32(ctx))
+        residuals_t<float, float>(ctx, dG, Qn, Qo, b, nb_cont, grid, out, s);
+    else if (dG_f32(ctx))
+        residuals_t<float, double>(ctx, dG, Qn, Qo, b, nb_cont, grid, out, s);
     else
-        k_residuals<double><<<grid, 256, 0, s>>>(ctx->d_n2e_ptr, ctx->d_n2e_col, ctx->d_n2e_sgn, nn,
-                                                 (const double*)dG, (const double*)Qn, (const double*)Qo,
-                                                 ctx->d_node_wall, ctx->d_tet_faces, nt, b,
-                                                 nb_cont, out);
+        residuals_t<double, double>(ctx, dG, Qn, Qo, b, nb_cont, grid, out, s);
     FP_CUDA_TRY(ctx, cudaGetLastError());
     return FP_OK;
 }

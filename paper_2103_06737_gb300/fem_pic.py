@@ -19,7 +19,7 @@ from . import build as _build
 
 FP_OK, FP_EINVAL, FP_ECUDA, FP_EWALK, FP_ENOCONV, FP_EGEOM = range(6)
 FP_FP64, FP_FP32 = 0, 1
-FP_ACCUMULATE, FP_NO_AGGREGATE, FP_SAME_FIELDS = 1, 2, 4
+FP_ACCUMULATE, FP_NO_AGGREGATE, FP_SAME_FIELDS, FP_CHARGE_CHANGE = 1, 2, 4, 8
 _STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ECUDA", 3: "FP_EWALK", 4: "FP_ENOCONV", 5: "FP_EGEOM"}
 
 _lock = threading.Lock()
@@ -91,6 +91,8 @@ def lib():
             "fem_pic_sizes": (I32, [P, P]),
             "fem_pic_set_deposit_precision": (I32, [P, I32]),
             "fem_pic_deposit_precision": (I32, [P]),
+            "fem_pic_set_charge_precision": (I32, [P, I32]),
+            "fem_pic_charge_precision": (I32, [P]),
             "fem_pic_incidence": (I32, [P, I32, P, P, P]),
             "fem_pic_topology": (I32, [P, P, P, P, P]),
             "fem_pic_project_uniform": (I32, [P, P, P, P, P, P]),
@@ -292,17 +294,31 @@ def _real(h):
 
 
 def _dep(h):
-    """dtype of the deposit arrays (dG, Q)."""
+    """dtype of the current array dG."""
     return torch.float32 if int(lib().fem_pic_deposit_precision(h)) == FP_FP32 else torch.float64
 
 
+def _chg(h):
+    """dtype of the charge array Q."""
+    return torch.float32 if int(lib().fem_pic_charge_precision(h)) == FP_FP32 else torch.float64
+
+
 def fem_pic_set_deposit_precision(h, precision: int):
-    """FP_FP32 or FP_FP64 deposit arrays (dG, Q) of an FP32 context (see the header)."""
+    """FP_FP32 or FP_FP64 deposit arrays (dG and Q) of an FP32 context (see the header)."""
     _check(lib().fem_pic_set_deposit_precision(h, int(precision)), h)
 
 
 def fem_pic_deposit_precision(h) -> int:
     return int(lib().fem_pic_deposit_precision(h))
+
+
+def fem_pic_set_charge_precision(h, precision: int):
+    """FP_FP32 or FP_FP64 charge array Q alone (see the header)."""
+    _check(lib().fem_pic_set_charge_precision(h, int(precision)), h)
+
+
+def fem_pic_charge_precision(h) -> int:
+    return int(lib().fem_pic_charge_precision(h))
 
 
 def fem_pic_particles_from_global(h, cell, X, off, stream=None):
@@ -331,12 +347,11 @@ def _check_species(h, sp: Species):
 def fem_pic_push_deposit(h, e, b, sp: Species, dt: float, dG, Q, max_cross: int = 64, flags: int = 0,
                          stream=None):
     sz = fem_pic_sizes(h)
-    R = _dep(h)
     _check_species(h, sp)
     _need(e, torch.float64, sz["n_edges"], name="e")
     _need(b, torch.float64, sz["n_faces"], name="b")
-    _need(dG, R, sz["n_edges"], name="dG")
-    _need(Q, R, sz["n_nodes"], name="Q")
+    _need(dG, _dep(h), sz["n_edges"], name="dG")
+    _need(Q, _chg(h), sz["n_nodes"], name="Q")
     p = sp.abi()
     _check(lib().fem_pic_push_deposit(h, _ptr(e), _ptr(b), ctypes.byref(p), float(dt), int(max_cross),
                                       _ptr(dG), _ptr(Q), int(flags), _stream(stream)), h)
@@ -361,7 +376,7 @@ def fem_pic_push_deposit_adams(h, e, b, sp: Species, hist, step: int, dt: float,
 
 def fem_pic_deposit_charge(h, sp: Species, Q, flags: int = 0, stream=None):
     _check_species(h, sp)
-    _need(Q, _dep(h), fem_pic_sizes(h)["n_nodes"], name="Q")
+    _need(Q, _chg(h), fem_pic_sizes(h)["n_nodes"], name="Q")
     p = sp.abi()
     _check(lib().fem_pic_deposit_charge(h, ctypes.byref(p), _ptr(Q), int(flags), _stream(stream)), h)
 
@@ -703,7 +718,15 @@ class FemPic:
 
     @property
     def deposit_dtype(self):
+        """dtype of dG (and of Q unless set_charge_precision changed it)."""
         return _dep(self.h)
+
+    def set_charge_precision(self, precision: int):
+        fem_pic_set_charge_precision(self.h, precision)
+
+    @property
+    def charge_dtype(self):
+        return _chg(self.h)
 
     def sort(self, src, dst, stream=None):
         fem_pic_sort(self.h, src, dst, stream)

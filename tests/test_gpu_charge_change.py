@@ -1,0 +1,282 @@
+"""Charge-change deposits (FP_CHARGE_CHANGE) and double charge arrays (fem_pic_set_charge_precision).
+
+The continuity equation of Sec. II.A ties a step's Whitney-1 current to the change of the
+Whitney-0 charge: D0^T dG = Q^{n+1} - Q^n.  With FP_CHARGE_CHANGE the push adds each
+particle's change q w (lambda^end - lambda^start) onto Q instead of writing its end charge,
+so a double Q holding Q^n becomes Q^{n+1} while FP32 rounding touches only the change.
+Checked here, for every kernel that takes the flag (the run-summing staged push, the
+grid-stride push, the FP64 walk of the particles that cross faces or reach a wall, the FP64
+context's push):
+  - the change and the updated Q against the FP64 oracle's charge at the start and end points,
+    and the particles bit for bit those of the plain push;
+  - the continuity residual against that of float arrays;
+  - particles removed for a non-finite state (their start charge leaves Q);
+  - the refusals (Adams mover, float Q beside double dG, an FP64 context);
+  - the Gauss-law projection's iterations over several field steps.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2103_06737_gb300 import inputs as I
+import oracle as O
+from helpers import TOL, assert_deposit_close
+
+pytestmark = pytest.mark.gpu
+
+F = pytest.importorskip("paper_2103_06737_gb300.fem_pic")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2103_06737_gb300 import build
+    build.build()
+
+
+def _copy(d0):
+    d = d0.empty_like()
+    d.cell.copy_(d0.cell)
+    d.off.copy_(d0.off)
+    d.vel.copy_(d0.vel)
+    return d
+
+
+def _state(lib, sp, sort):
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    if sort:
+        s = d.empty_like()
+        lib.sort(d, s)
+        d = s
+    return d
+
+
+def _resid(lib, dG, Qn, Qo, bd):
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    lib.residuals(dG, Qn, Qo, bd, out)
+    return out.cpu().numpy()
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+# 1,200,000 sorted: the run-summing staged kernel; 50,001: the grid-stride kernel; 50,000
+# sorted with float Q: the staged kernel with float arrays; FP64: the FP64 context's push.
+# At |v| dt = 0.15 on an 8^3 cube (cells 0.125 wide) most particles cross faces (the FP64
+# walk) and some reach the walls.
+@pytest.mark.parametrize("prec,npart,sort,q64", [(F.FP_FP32, 1_200_000, True, True),
+                                                 (F.FP_FP32, 50_001, False, True),
+                                                 (F.FP_FP32, 50_000, True, False),
+                                                 (F.FP_FP64, 50_001, False, True)])
+def test_charge_change_matches_oracle(prec, npart, sort, q64):
+    m = I.cube_mesh(8, 1.0, 0.1, seed=1)
+    orc = O.Oracle(m.xyz, m.tets)
+    sp = I.uniform_species(m, npart, 3, 0.15, -1.0, 1.0, 0.7)
+    rng = np.random.default_rng(7)
+    e = rng.uniform(-0.2, 0.2, orc.n_edges)
+    b = rng.uniform(-0.5, 0.5, orc.n_faces)
+    ed = torch.as_tensor(e, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    lib = F.FemPic(m.xyz, m.tets, prec)
+    if prec == F.FP_FP32 and q64:
+        lib.set_charge_precision(F.FP_FP64)
+    RG, RQ = lib.deposit_dtype, lib.charge_dtype
+    assert RG == lib.real
+    assert RQ == (torch.float64 if q64 else torch.float32)
+    d0 = _state(lib, sp, sort)
+    cell0 = d0.cell.cpu().numpy().copy()
+    off0 = d0.off.cpu().numpy().copy()
+    v0 = d0.vel.cpu().numpy().copy()
+    Q0 = torch.empty(orc.n_nodes, dtype=RQ, device="cuda")
+    lib.deposit_charge(d0, Q0)
+    # the plain push (end-point charge) for the particles
+    dp = _copy(d0)
+    dGp = torch.empty(orc.n_edges, dtype=RG, device="cuda")
+    Qp = torch.empty(orc.n_nodes, dtype=RQ, device="cuda")
+    lib.push_deposit(ed, bd, dp, 1.0, dGp, Qp)
+    assert lib.status() == F.FP_OK
+    runs = []
+    for start in (Q0, torch.zeros_like(Q0)):     # onto Q^n, and onto zeros: the change alone
+        d = _copy(d0)
+        dG = torch.full((orc.n_edges,), 7.0, dtype=RG, device="cuda")   # zeroed by the call
+        Q = start.clone()
+        lib.push_deposit(ed, bd, d, 1.0, dG, Q, flags=F.FP_CHARGE_CHANGE)
+        assert lib.status() == F.FP_OK
+        assert torch.equal(d.cell, dp.cell) and torch.equal(d.off, dp.off) and torch.equal(d.vel, dp.vel)
+        runs.append((dG, Q))
+    (dG1, Q1), (dG2, dQ) = runs
+    cb = dp.cell.cpu().numpy()
+    assert (cb == -1).any() and (cb != cell0).mean() > 0.3     # walls reached, faces crossed
+    o = orc.origin(cell0)
+    Xa = o + off0.T.astype(np.float64)
+    Va = v0.T.astype(np.float64)
+    if prec == F.FP_FP32:      # the oracle walk on the GPU's own end points
+        end = (off0 + np.float32(1.0) * dp.vel.cpu().numpy()).astype(np.float32)
+        ref = orc.step(cell0, Xa, Va, e, b, sp.q, sp.m, sp.w, 1.0, Xend=o + end.T.astype(np.float64))
+        tol = TOL["fp32"]
+    else:
+        ref = orc.step(cell0, Xa, Va, e, b, sp.q, sp.m, sp.w, 1.0)
+        assert np.array_equal(cb, ref["cell"])
+        tol = TOL["fp64"]
+    Q0r, Q0a = orc.charge(cell0, Xa, sp.q, sp.w)
+    for g in (dG1, dG2):
+        assert_deposit_close(_np(g), ref["dG"], ref["dG_abs"], tol, "dG")
+    assert_deposit_close(_np(Q1), ref["Q"], ref["Q_abs"], tol, "Q^{n+1}")
+    assert_deposit_close(_np(dQ), ref["Q"] - Q0r, ref["Q_abs"] + Q0a, tol, "Q^{n+1} - Q^n")
+    res = _resid(lib, dG1, Q1, Q0, bd)
+    if prec == F.FP_FP64:
+        assert res[0] <= 1e-12 * res[1]
+    elif q64:
+        # against float arrays: the end-point charge summed in FP32 (the default)
+        lib.set_charge_precision(F.FP_FP32)
+        assert lib.charge_dtype == torch.float32
+        Q0f = torch.empty(orc.n_nodes, dtype=torch.float32, device="cuda")
+        lib.deposit_charge(d0, Q0f)
+        df = _copy(d0)
+        dGf = torch.empty_like(dGp)
+        Qf = torch.empty_like(Q0f)
+        lib.push_deposit(ed, bd, df, 1.0, dGf, Qf)
+        assert lib.status() == F.FP_OK
+        rf = _resid(lib, dGf, Qf, Q0f, bd)
+        assert res[0] <= 1e-6 * res[1]
+        assert res[0] * 10.0 <= rf[0], (res[0], rf[0])
+    lib.close()
+
+
+# n = 50,000 (staged pipeline) and 50,001 (grid-stride kernel) in FP32 with double Q; FP64 mode
+@pytest.mark.parametrize("prec,npart", [(F.FP_FP32, 50_000), (F.FP_FP32, 50_001), (F.FP_FP64, 50_001)])
+def test_charge_change_removes_the_start_charge_of_nonfinite_particles(prec, npart):
+    """NaN and Inf written into some velocities and offsets.  A particle with a finite start and
+    a non-finite velocity is removed, and its start charge leaves Q; one without a finite start
+    has no charge in Q^n to remove (fem_pic_deposit_charge drops it).  Q^n plus the change then
+    equals the end charge of the push of the state with the bad particles already absent."""
+    m = I.cube_mesh(8, 1.0, 0.1, seed=1)
+    sp = I.uniform_species(m, npart, 3, 0.15, -1.0, 1.0, 0.7)
+    rng = np.random.default_rng(7)
+    lib = F.FemPic(m.xyz, m.tets, prec)
+    if prec == F.FP_FP32:
+        lib.set_charge_precision(F.FP_FP64)
+    ed = torch.as_tensor(rng.uniform(-0.2, 0.2, lib.n_edges), device="cuda")
+    bd = torch.as_tensor(rng.uniform(-0.5, 0.5, F.fem_pic_sizes(lib.h)["n_faces"]), device="cuda")
+    bad = np.array([3, 1000, 20_001, 33_333, npart - 1])
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    d.vel[0, 3] = float("nan")
+    d.vel[1, 1000] = float("inf")
+    d.off[2, 20_001] = float("nan")
+    d.off[0, 33_333] = float("-inf")
+    d.vel[2, npart - 1] = float("-inf")
+    clean = F.Species(d.cell.clone(), d.off.clone(), d.vel.clone(), d.q, d.m, d.w)
+    clean.cell[torch.as_tensor(bad, device="cuda")] = -1
+    has_start = F.Species(d.cell.clone(), d.off.clone(), d.vel.clone(), d.q, d.m, d.w)
+    has_start.cell[torch.as_tensor([20_001, 33_333], device="cuda")] = -1
+    RG, RQ = lib.deposit_dtype, lib.charge_dtype
+    Q = torch.empty(lib.n_nodes, dtype=RQ, device="cuda")
+    lib.deposit_charge(has_start, Q)
+    assert lib.status() == F.FP_OK
+    dG = torch.empty(lib.n_edges, dtype=RG, device="cuda")
+    lib.push_deposit(ed, bd, d, 1.0, dG, Q, flags=F.FP_CHARGE_CHANGE)
+    assert lib.status() == F.FP_EINVAL and "not finite" in F.fem_pic_last_error(lib.h)
+    dGc = torch.empty_like(dG)
+    Qc = torch.empty_like(Q)
+    lib.push_deposit(ed, bd, clean, 1.0, dGc, Qc)
+    assert lib.status() == F.FP_OK
+    assert (d.cell.cpu().numpy()[bad] == -1).all() and torch.equal(d.cell, clean.cell)
+    tol = 1e-12 if prec == F.FP_FP64 else TOL["fp32"]
+    for x, y in ((_np(dG), _np(dGc)), (_np(Q), _np(Qc))):
+        assert np.isfinite(x).all()
+        assert np.abs(x - y).max() <= tol * np.abs(y).max()
+    lib.close()
+
+
+def _adams_status(lib, e, b, d, dG, Q, flags):
+    hist = torch.zeros(18 * d.n, dtype=lib.real, device="cuda")
+    p = d.abi()
+    f = F.lib().fem_pic_push_deposit_adams
+    return int(f(lib.h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(b.data_ptr()), ctypes.byref(p),
+                 ctypes.c_void_p(hist.data_ptr()), 0, ctypes.c_double(0.1), 64, ctypes.c_void_p(dG.data_ptr()),
+                 ctypes.c_void_p(Q.data_ptr()), int(flags), None))
+
+
+def test_charge_precision_settings_and_refusals():
+    m = I.cube_mesh(4, 1.0, 0.1, seed=1)
+    sp = I.uniform_species(m, 1000, 3, 0.05, -1.0, 1.0, 0.7)
+    lib = F.FemPic(m.xyz, m.tets, F.FP_FP32)
+    assert (lib.deposit_dtype, lib.charge_dtype) == (torch.float32, torch.float32)
+    lib.set_charge_precision(F.FP_FP64)
+    assert (lib.deposit_dtype, lib.charge_dtype) == (torch.float32, torch.float64)
+    assert F.fem_pic_charge_precision(lib.h) == F.FP_FP64 and F.fem_pic_deposit_precision(lib.h) == F.FP_FP32
+    with pytest.raises(F.FemPicError):
+        lib.set_charge_precision(7)
+    lib.set_deposit_precision(F.FP_FP64)            # dG and Q together
+    assert (lib.deposit_dtype, lib.charge_dtype) == (torch.float64, torch.float64)
+    with pytest.raises(F.FemPicError):              # float Q beside double dG
+        lib.set_charge_precision(F.FP_FP32)
+    lib.set_deposit_precision(F.FP_FP32)
+    assert (lib.deposit_dtype, lib.charge_dtype) == (torch.float32, torch.float32)
+    # the Adams mover takes neither the flag nor double arrays in FP32 mode
+    d = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
+    e, b = lib.fields_uniform((0, 0, 0), (0, 0, 1.0))
+    dG = torch.zeros(lib.n_edges, dtype=torch.float32, device="cuda")
+    Q = torch.zeros(lib.n_nodes, dtype=torch.float32, device="cuda")
+    assert _adams_status(lib, e, b, d, dG, Q, F.FP_CHARGE_CHANGE) == F.FP_EINVAL
+    assert _adams_status(lib, e, b, d, dG, Q, 0) == F.FP_OK
+    lib.set_charge_precision(F.FP_FP64)
+    assert _adams_status(lib, e, b, d, dG, Q.double(), 0) == F.FP_EINVAL
+    assert lib.status() == F.FP_OK
+    lib.close()
+    lib = F.FemPic(m.xyz, m.tets, F.FP_FP64)        # an FP64 context keeps double arrays
+    assert lib.charge_dtype == torch.float64
+    lib.set_charge_precision(F.FP_FP64)
+    with pytest.raises(F.FemPicError):
+        lib.set_charge_precision(F.FP_FP32)
+    lib.close()
+
+
+def test_charge_change_shortens_the_projection():
+    """Four field steps of 16^3 x 6 tets with 10 electrons per tet: float arrays with the
+    end-point charge (the default), double arrays with the end-point charge, and float dG with
+    a double Q carried from step to step by the charge change.  Every step reaches 1e-10; the
+    Gauss-law projection, whose right-hand side is the continuity residual, takes fewer
+    iterations the closer continuity holds."""
+    wl = I.config(2, 1.0, mesh_n=16)
+    its = {}
+    for mode in ("fp32", "fp64", "change"):
+        lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
+        if mode == "fp64":
+            lib.set_deposit_precision(F.FP_FP64)
+        if mode == "change":
+            lib.set_charge_precision(F.FP_FP64)
+        flags = F.FP_CHARGE_CHANGE if mode == "change" else 0
+        F.fem_pic_field_setup(lib.h, wl.dt)
+        s0 = wl.species[0]
+        d = lib.species(s0.cell, s0.X, s0.V, s0.q, s0.m, s0.w)
+        e, b = lib.fields_uniform((0, 0, 0), wl.B0)
+        Q = torch.zeros(lib.n_nodes, dtype=lib.charge_dtype, device="cuda")
+        lib.deposit_charge(d, Q)
+        st, _ = F.fem_pic_field_initial(lib.h, Q, e, tol=1e-10)
+        assert st == F.FP_OK
+        E_prev, E_next = e.clone(), torch.empty_like(e)
+        dG = torch.zeros(lib.n_edges, dtype=lib.deposit_dtype, device="cuda")
+        dGp = torch.zeros_like(dG)
+        g = []
+        for _ in range(4):
+            lib.push_deposit(e, b, d, wl.dt, dG, Q, flags=flags)
+            st, info = F.fem_pic_field_step(lib.h, E_prev, e, E_next, b, dG, dGp, Q, tol=1e-10)
+            assert st == F.FP_OK and info[1]["rel_res"] <= 1e-10
+            g.append(info[1]["iters"])
+            E_prev, e, E_next = e, E_next, E_prev
+            dGp, dG = dG, dGp
+        assert lib.status() == F.FP_OK
+        if mode == "change":       # Q carried by the changes equals the charge of the particles
+            Qd = torch.zeros_like(Q)
+            lib.deposit_charge(d, Qd)
+            ref = _np(Qd)
+            assert np.abs(_np(Q) - ref).max() <= 1e-5 * np.abs(ref).max()
+        its[mode] = np.mean(g[1:])
+        lib.close()
+    print("Gauss-law projection iterations per step:", its)
+    assert its["change"] < 0.8 * its["fp32"], its

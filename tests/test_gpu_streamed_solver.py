@@ -4,9 +4,9 @@ At 96^3 x 6 tets (6.3M edges, 0.9M nodes) neither FP32 operator fits in shared m
 inner solves stream them from HBM (with the 16-bit column encoding when the library is built
 with FP_COL16=1).  Both systems of Sec. IV.B (Eq. reducedWaveEqn, discreteGauss) are solved for
 seeded right-hand sides to 1e-10 with the Jacobi and with the learned preconditioner (a head
-set to a mild symmetric correction of Jacobi, applied on the same streamed pattern).  The FP64 residual of each solution is then formed on the CPU with the library's own
-operators (pinned to the oracle's by test_gpu_fields.py::test_operators_match_oracle): a
-wrongly read column would leave the inner solves unable to reduce the true residual.
+set to a mild symmetric correction of Jacobi, applied on the same streamed pattern).  The FP64
+residual of each solution is then formed on the CPU with the library's own operators (pinned
+to the oracle's by test_gpu_fields.py::test_operators_match_oracle): a wrongly read column would leave the inner solves unable to reduce the true residual.
 """
 import numpy as np
 import pytest
