@@ -53,12 +53,13 @@ def parse():
     ap.add_argument("--mesh", type=int, default=0,
                     help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
                          "particles per tet and displacement per step in cells (profiling cases)")
-    ap.add_argument("--deposits", default="fp32", choices=["fp32", "fp64", "change"],
-                    help="deposit arrays: fp32 (float dG and Q, the end-point charge), fp64 (double dG and Q: "
-                         "the FP32 contributions added with FP64 atomics; at 96^3 it cut the Gauss-law "
-                         "projection from 121 to 104 inner iterations but slowed the push and walk by 0.6 ms) "
-                         "or change (float dG, double Q carried from step to step by the charge change of "
-                         "each particle, FP_CHARGE_CHANGE)")
+    ap.add_argument("--deposits", default="change", choices=["change", "fp32", "fp64"],
+                    help="deposit arrays: change (float dG, double Q carried from step to step by each "
+                         "particle's charge change, FP_CHARGE_CHANGE; at 96^3 with Chebyshev-Jacobi solves it "
+                         "cut the Gauss-law projection from 32.7 to 17.9 inner iterations, 6.1 -> 3.4 ms, for "
+                         "0.16 ms more push and walk), fp32 (float dG and Q, the end-point charge) or fp64 "
+                         "(double dG and Q: 121 -> 104 learned projection iterations, push and walk 0.6 ms "
+                         "slower)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="steps between cell sorts (0: the workload's own: 2 for the drifting beam, whose cell "
                          "order decays fastest, 10 otherwise; negative: never)")

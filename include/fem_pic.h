@@ -207,6 +207,9 @@ fp_status fem_pic_particles_to_global(fem_pic_t* ctx, int64_t n, const int32_t* 
  * removed particle with a finite start subtracts its start charge): a Q that holds the
  * charge of the start positions (fem_pic_deposit_charge, or the previous step) becomes the
  * charge of the end positions.  dG is zeroed unless FP_ACCUMULATE, as without the flag.
+ * (A particle absorbed by a PEC wall leaves its charge on the wall's nodes, in this step as
+ * without the flag, and a carried Q keeps it there in later steps; wall nodes are fixed in
+ * the Gauss-law solve, so the field step does not read it.)
  * The change equals D0^T dG exactly in real arithmetic (the continuity equation of
  * Sec. II.A), so FP32 rounding touches only the change, not the node charges.
  * Particle arrays are updated in place.  Asynchronous.

@@ -274,11 +274,22 @@ def test_charge_change_shortens_the_projection():
             E_prev, e, E_next = e, E_next, E_prev
             dGp, dG = dG, dGp
         assert lib.status() == F.FP_OK
-        if mode == "change":       # Q carried by the changes equals the charge of the particles
+        if mode == "change":
+            # Q carried by the changes equals the charge of the particles on interior nodes; a
+            # particle absorbed by a PEC wall leaves its charge on the wall nodes (fixed in the
+            # Gauss-law solve), which a fresh deposit of the live particles does not see
+            T = F.fem_pic_topology(lib.h)
+            wall = np.zeros(lib.n_nodes, bool)
+            for k in range(4):
+                on = T["tet_neigh"][:, k] < 0
+                for j in range(4):
+                    if j != k:        # face k is the one opposite vertex k
+                        wall[T["tet_nodes"][on, j]] = True
+            assert 0 < wall.sum() < lib.n_nodes
             Qd = torch.zeros_like(Q)
             lib.deposit_charge(d, Qd)
-            ref = _np(Qd)
-            assert np.abs(_np(Q) - ref).max() <= 1e-5 * np.abs(ref).max()
+            ref = _np(Qd)[~wall]
+            assert np.abs(_np(Q)[~wall] - ref).max() <= 1e-5 * np.abs(ref).max()
         its[mode] = np.mean(g[1:])
         lib.close()
     print("Gauss-law projection iterations per step:", its)
