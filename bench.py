@@ -53,13 +53,13 @@ def parse():
     ap.add_argument("--mesh", type=int, default=0,
                     help="mesh resolution n of the workload's n^3 x 6 cube instead of its own, with the same "
                          "particles per tet and displacement per step in cells (profiling cases)")
-    ap.add_argument("--deposits", default="change", choices=["change", "fp32", "fp64"],
+    ap.add_argument("--deposits", default="change", choices=["change", "change64", "fp32", "fp64"],
                     help="deposit arrays: change (float dG, double Q carried from step to step by each "
                          "particle's charge change, FP_CHARGE_CHANGE; at 96^3 with Chebyshev-Jacobi solves it "
                          "cut the Gauss-law projection from 32.7 to 17.9 inner iterations, 6.1 -> 3.4 ms, for "
                          "0.16 ms more push and walk), fp32 (float dG and Q, the end-point charge) or fp64 "
                          "(double dG and Q: 121 -> 104 learned projection iterations, push and walk 0.6 ms "
-                         "slower)")
+                         "slower); change64 is change with a double dG as well")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="steps between cell sorts (0: the workload's own: 2 for the drifting beam, whose cell "
                          "order decays fastest, 10 otherwise; negative: never)")
@@ -305,7 +305,7 @@ def peak_hbm():
 
 def set_deposits(args, lib, F):
     """The deposit arrays' element types for the --deposits choice."""
-    if args.deposits == "fp64":
+    if args.deposits in ("fp64", "change64"):
         lib.set_deposit_precision(F.FP_FP64)
     elif args.deposits == "change":
         lib.set_charge_precision(F.FP_FP64)
@@ -335,7 +335,7 @@ def learned_protocol(args, dev):
         wl = I.config(idx)
         lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
         set_deposits(args, lib, F)
-        cflag = F.FP_CHARGE_CHANGE if args.deposits == "change" else 0
+        cflag = F.FP_CHARGE_CHANGE if args.deposits.startswith("change") else 0
         sizes = lib.sizes
         sps = []
         for s_ in wl.species:
@@ -522,7 +522,7 @@ def run_gpu(args):
         ev[wall] = 0.0
         e.copy_(torch.as_tensor(ev, device=dev))
     set_deposits(args, lib, F)
-    cflag = F.FP_CHARGE_CHANGE if args.deposits == "change" else 0
+    cflag = F.FP_CHARGE_CHANGE if args.deposits.startswith("change") else 0
     DEP, DQ = lib.deposit_dtype, lib.charge_dtype
     dG = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)       # dG^{n+1/2}
     dG_prev = torch.zeros(sizes["n_edges"], dtype=DEP, device=dev)  # dG^{n-1/2}
@@ -1301,6 +1301,8 @@ def run_gpu(args):
                        "deposits": {"fp64": "double dG and Q (FP32 contributions added with FP64 atomics)",
                                     "change": "float dG (FP32 atomics); double Q carried from step to step, each "
                                               "particle's FP32 charge change added with FP64 atomics",
+                                    "change64": "double dG (FP64 atomics); double Q carried from step to step, "
+                                                "each particle's FP32 charge change added with FP64 atomics",
                                     "fp32": "float dG and Q (FP32 atomics)"}[args.deposits],
                        "l2": "flushed between timed steps: 256 MB written, then another 256 MB read (outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -65,14 +65,17 @@ def _np(t):
 
 
 # 1,200,000 sorted: the run-summing staged kernel; 50,001: the grid-stride kernel; 50,000
-# sorted with float Q: the staged kernel with float arrays; FP64: the FP64 context's push.
-# At |v| dt = 0.15 on an 8^3 cube (cells 0.125 wide) most particles cross faces (the FP64
-# walk) and some reach the walls.
-@pytest.mark.parametrize("prec,npart,sort,q64", [(F.FP_FP32, 1_200_000, True, True),
-                                                 (F.FP_FP32, 50_001, False, True),
-                                                 (F.FP_FP32, 50_000, True, False),
-                                                 (F.FP_FP64, 50_001, False, True)])
-def test_charge_change_matches_oracle(prec, npart, sort, q64):
+# sorted with float Q, and with double dG and Q: the staged kernel with those arrays; FP64: the
+# FP64 context's push.  At |v| dt = 0.15 on an 8^3 cube (cells 0.125 wide) most particles cross
+# faces (the FP64 walk) and some reach the walls.
+@pytest.mark.parametrize("prec,npart,sort,arrays", [(F.FP_FP32, 1_200_000, True, "Q"),
+                                                    (F.FP_FP32, 50_001, False, "Q"),
+                                                    (F.FP_FP32, 50_000, True, "none"),
+                                                    (F.FP_FP32, 50_000, True, "dG+Q"),
+                                                    (F.FP_FP64, 50_001, False, "dG+Q")])
+def test_charge_change_matches_oracle(prec, npart, sort, arrays):
+    """`arrays`: which deposit arrays are double."""
+    q64 = arrays != "none"
     m = I.cube_mesh(8, 1.0, 0.1, seed=1)
     orc = O.Oracle(m.xyz, m.tets)
     sp = I.uniform_species(m, npart, 3, 0.15, -1.0, 1.0, 0.7)
@@ -82,10 +85,12 @@ def test_charge_change_matches_oracle(prec, npart, sort, q64):
     ed = torch.as_tensor(e, device="cuda")
     bd = torch.as_tensor(b, device="cuda")
     lib = F.FemPic(m.xyz, m.tets, prec)
-    if prec == F.FP_FP32 and q64:
+    if prec == F.FP_FP32 and arrays == "Q":
         lib.set_charge_precision(F.FP_FP64)
+    if prec == F.FP_FP32 and arrays == "dG+Q":
+        lib.set_deposit_precision(F.FP_FP64)
     RG, RQ = lib.deposit_dtype, lib.charge_dtype
-    assert RG == lib.real
+    assert RG == (torch.float64 if arrays == "dG+Q" else torch.float32)
     assert RQ == (torch.float64 if q64 else torch.float32)
     d0 = _state(lib, sp, sort)
     cell0 = d0.cell.cpu().numpy().copy()
@@ -130,6 +135,8 @@ def test_charge_change_matches_oracle(prec, npart, sort, q64):
     res = _resid(lib, dG1, Q1, Q0, bd)
     if prec == F.FP_FP64:
         assert res[0] <= 1e-12 * res[1]
+    elif arrays == "dG+Q":       # FP32 terms summed in FP64 on both sides
+        assert res[0] <= 1e-6 * res[1]
     elif q64:
         # against float arrays: the end-point charge summed in FP32 (the default)
         lib.set_charge_precision(F.FP_FP32)
@@ -241,19 +248,19 @@ def test_charge_precision_settings_and_refusals():
 
 def test_charge_change_shortens_the_projection():
     """Four field steps of 16^3 x 6 tets with 10 electrons per tet: float arrays with the
-    end-point charge (the default), double arrays with the end-point charge, and float dG with
-    a double Q carried from step to step by the charge change.  Every step reaches 1e-10; the
+    end-point charge, double arrays with the end-point charge, and a double Q carried from step
+    to step by the charge change beside a float and a double dG.  Every step reaches 1e-10; the
     Gauss-law projection, whose right-hand side is the continuity residual, takes fewer
     iterations the closer continuity holds."""
     wl = I.config(2, 1.0, mesh_n=16)
     its = {}
-    for mode in ("fp32", "fp64", "change"):
+    for mode in ("fp32", "fp64", "change", "change64"):
         lib = F.FemPic(wl.mesh.xyz, wl.mesh.tets, F.FP_FP32)
-        if mode == "fp64":
+        if mode in ("fp64", "change64"):
             lib.set_deposit_precision(F.FP_FP64)
         if mode == "change":
             lib.set_charge_precision(F.FP_FP64)
-        flags = F.FP_CHARGE_CHANGE if mode == "change" else 0
+        flags = F.FP_CHARGE_CHANGE if mode.startswith("change") else 0
         F.fem_pic_field_setup(lib.h, wl.dt)
         s0 = wl.species[0]
         d = lib.species(s0.cell, s0.X, s0.V, s0.q, s0.m, s0.w)
@@ -274,7 +281,7 @@ def test_charge_change_shortens_the_projection():
             E_prev, e, E_next = e, E_next, E_prev
             dGp, dG = dG, dGp
         assert lib.status() == F.FP_OK
-        if mode == "change":
+        if mode.startswith("change"):
             # Q carried by the changes equals the charge of the particles on interior nodes; a
             # particle absorbed by a PEC wall leaves its charge on the wall nodes (fixed in the
             # Gauss-law solve), which a fresh deposit of the live particles does not see
@@ -293,4 +300,4 @@ def test_charge_change_shortens_the_projection():
         its[mode] = np.mean(g[1:])
         lib.close()
     print("Gauss-law projection iterations per step:", its)
-    assert its["change"] < 0.8 * its["fp32"], its
+    assert its["change"] < 0.8 * its["fp32"] and its["change64"] < 0.8 * its["fp32"], its
