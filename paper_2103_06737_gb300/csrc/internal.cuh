@@ -190,6 +190,20 @@ __device__ __forceinline__ float d2f(double d) {
     return __uint_as_float(r | sign);
 }
 
+// A deposit contribution in the element type of its array: a float goes into a double array
+// through f2d (so a float subnormal contribution, below 1.2e-38 in magnitude, adds zero);
+// a double (FP64 mode) or a float into a float array is passed as it is.
+template <typename D>
+__device__ __forceinline__ D dep_cast(float x) {
+    if constexpr (sizeof(D) == 8) return f2d(x);
+    else return x;
+}
+template <typename D>
+__device__ __forceinline__ D dep_cast(double x) {
+    static_assert(sizeof(D) == 8, "double contributions go into double arrays");
+    return x;
+}
+
 // x < 0 strictly (and not NaN-with-sign), from the bit pattern
 __device__ __forceinline__ bool neg_strict(double x) {
     const long long b = __double_as_longlong(x);

@@ -170,14 +170,15 @@ __device__ __forceinline__ void deposit_piece(const TetTopo& T, const double la[
     Real val[6];
     piece_values<Real>(la, lx, qw, val);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], (D)val[k]);
+    for (int k = 0; k < 6; ++k) atomicAdd(dG + T.edge[k], dep_cast<D>(val[k]));
 }
 
 template <typename Real, typename D = Real>
 __device__ __forceinline__ void deposit_charge(const TetTopo& T, const double l[4], double qw,
                                                D* __restrict__ Q) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(Q + T.node[k], (D)(to_real<Real>(qw) * to_real<Real>(l[k])));
+    for (int k = 0; k < 4; ++k)
+        atomicAdd(Q + T.node[k], dep_cast<D>(to_real<Real>(qw) * to_real<Real>(l[k])));
 }
 
 // Sum `v[0..NV)` over each run of equal `key` in lane order; the first lane of a run
@@ -833,7 +834,7 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             if (cc && finite_bits(l[0]) && finite_bits(l[1]) && finite_bits(l[2]) && finite_bits(l[3])) {
                 ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)(-w * l[k]));
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], dep_cast<DQ>(-w * l[k]));
             }
         } else if (r3 == kFastStay) {
             deposit_values(w, l, d, agg, cc);
@@ -845,9 +846,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
             if (!aggregate) {
                 ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (DG)agg[k]);
+                for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], dep_cast<DG>(agg[k]));
 #pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)agg[6 + k]);
+                for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], dep_cast<DQ>(agg[6 + k]));
             }
         } else {
             slow = true;
@@ -860,9 +861,9 @@ __device__ __forceinline__ bool fast_particle(const TetHot* __restrict__ hot, co
         if (((heads >> lane) & 1u) && key >= 0) {
             ids_of(hot, rec, rec_lo, in_win, c, H);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], (DG)agg[k]);
+            for (int k = 0; k < 6; ++k) atomicAdd(dG + H.edge[k], dep_cast<DG>(agg[k]));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (DQ)agg[6 + k]);
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], dep_cast<DQ>(agg[6 + k]));
         }
     }
     return slow;
@@ -1358,16 +1359,16 @@ __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const 
         e03 = __ldg(r + 1);
         e45 = __ldg(r + 2);
     }
-    atomicAdd(dG + e03.x, (DG)(w * a[0]));
-    atomicAdd(dG + e03.y, (DG)(w * a[1]));
-    atomicAdd(dG + e03.z, (DG)(w * a[2]));
-    atomicAdd(dG + e03.w, (DG)(w * a[3]));
-    atomicAdd(dG + e45.x, (DG)(w * a[4]));
-    atomicAdd(dG + e45.y, (DG)(w * a[5]));
-    atomicAdd(Q + nd.x, (DQ)(w * a[6]));
-    atomicAdd(Q + nd.y, (DQ)(w * a[7]));
-    atomicAdd(Q + nd.z, (DQ)(w * a[8]));
-    atomicAdd(Q + nd.w, (DQ)(w * a[9]));
+    atomicAdd(dG + e03.x, dep_cast<DG>(w * a[0]));
+    atomicAdd(dG + e03.y, dep_cast<DG>(w * a[1]));
+    atomicAdd(dG + e03.z, dep_cast<DG>(w * a[2]));
+    atomicAdd(dG + e03.w, dep_cast<DG>(w * a[3]));
+    atomicAdd(dG + e45.x, dep_cast<DG>(w * a[4]));
+    atomicAdd(dG + e45.y, dep_cast<DG>(w * a[5]));
+    atomicAdd(Q + nd.x, dep_cast<DQ>(w * a[6]));
+    atomicAdd(Q + nd.y, dep_cast<DQ>(w * a[7]));
+    atomicAdd(Q + nd.z, dep_cast<DQ>(w * a[8]));
+    atomicAdd(Q + nd.w, dep_cast<DQ>(w * a[9]));
 }
 
 // a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, and l_k + d_k,
@@ -1912,7 +1913,7 @@ __global__ void __launch_bounds__(256) k_deposit_charge32(const TetHot* __restri
         warp_run_reduce<float, 4>(c, v, &heads, &end);
         if (((heads >> lane) & 1u) && c >= 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], (D)v[k]);
+            for (int k = 0; k < 4; ++k) atomicAdd(Q + H.node[k], dep_cast<D>(v[k]));
         }
     }
 }
