@@ -1359,16 +1359,19 @@ __device__ __forceinline__ void run_flush(const TetHot* __restrict__ hot, const 
         e03 = __ldg(r + 1);
         e45 = __ldg(r + 2);
     }
-    atomicAdd(dG + e03.x, dep_cast<DG>(w * a[0]));
-    atomicAdd(dG + e03.y, dep_cast<DG>(w * a[1]));
-    atomicAdd(dG + e03.z, dep_cast<DG>(w * a[2]));
-    atomicAdd(dG + e03.w, dep_cast<DG>(w * a[3]));
-    atomicAdd(dG + e45.x, dep_cast<DG>(w * a[4]));
-    atomicAdd(dG + e45.y, dep_cast<DG>(w * a[5]));
-    atomicAdd(Q + nd.x, dep_cast<DQ>(w * a[6]));
-    atomicAdd(Q + nd.y, dep_cast<DQ>(w * a[7]));
-    atomicAdd(Q + nd.z, dep_cast<DQ>(w * a[8]));
-    atomicAdd(Q + nd.w, dep_cast<DQ>(w * a[9]));
+    // Here the conversion into a double array is the hardware one: the run kernel issues few
+    // of them (once per run), has FP64 pipe to spare, and the integer form's extra instructions
+    // cost it 4% (2.06 against 1.99 ms for both 96^3 species); the walk, FP64-bound, uses dep_cast.
+    atomicAdd(dG + e03.x, (DG)(w * a[0]));
+    atomicAdd(dG + e03.y, (DG)(w * a[1]));
+    atomicAdd(dG + e03.z, (DG)(w * a[2]));
+    atomicAdd(dG + e03.w, (DG)(w * a[3]));
+    atomicAdd(dG + e45.x, (DG)(w * a[4]));
+    atomicAdd(dG + e45.y, (DG)(w * a[5]));
+    atomicAdd(Q + nd.x, (DQ)(w * a[6]));
+    atomicAdd(Q + nd.y, (DQ)(w * a[7]));
+    atomicAdd(Q + nd.z, (DQ)(w * a[8]));
+    atomicAdd(Q + nd.w, (DQ)(w * a[9]));
 }
 
 // a += the 10 deposit values of a piece without the weight (l_i d_j - l_j d_i, and l_k + d_k,

