@@ -305,7 +305,8 @@ fp_status fem_pic_sort_columns(fem_pic_t* ctx, const fp_particles* src, fp_parti
  *   out[4], out[5] = as out[0], out[1] over interior nodes only (charge absorbed by a
  *            PEC wall in an earlier step leaves the particle set, so over several
  *            steps continuity is checked where the field solve uses it).
- * dG, Q_new, Q_old have the deposit precision (fem_pic_deposit_precision); b is double.  Any
+ * dG has the deposit precision (fem_pic_deposit_precision), Q_new and Q_old the charge
+ * precision (fem_pic_charge_precision); b is double.  Any
  * input may be NULL (its entries are then 0).  out is device double[6].  Asynchronous.
  */
 fp_status fem_pic_residuals(fem_pic_t* ctx, const void* dG, const void* Q_new, const void* Q_old,
@@ -388,7 +389,7 @@ fp_status fem_pic_field_solve(fem_pic_t* ctx, int system, const double* rhs, dou
  *   3. Faraday: b <- b - dt D1 (E^{n+1} + E^n)/2 (skipped if b is NULL).
  * E_prev = E^{n-1}, E_cur = E^n (device double [N_e]); E_next receives E^{n+1} (distinct
  * buffer); dG_half = dG^{n+1/2} (the deposit of the push that used E^n), dG_prev =
- * dG^{n-1/2} (NULL = 0), Q_new = Q^{n+1} (deposit precision).  info[2] (host, may be
+ * dG^{n-1/2} (NULL = 0), Q_new = Q^{n+1} (charge precision).  info[2] (host, may be
  * NULL): the Newmark and Gauss solves; with info, FP_ENOCONV if either missed tol.
  */
 fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double* E_cur, double* E_next,
@@ -398,7 +399,8 @@ fp_status fem_pic_field_step(fem_pic_t* ctx, const double* E_prev, const double*
 
 /*
  * Initial field: E (device double [N_e]) with D0^T M E + Q = 0 at interior nodes and no
- * solenoidal part (the Gauss-law projection of E = 0), CG to ||r|| <= tol ||Q||.
+ * solenoidal part (the Gauss-law projection of E = 0), CG to ||r|| <= tol ||Q||.  Q has the
+ * charge precision (fem_pic_charge_precision).
  */
 fp_status fem_pic_field_initial(fem_pic_t* ctx, const void* Q, double* E, double tol, int max_iter,
                                 fp_solve_info* info, void* stream);
@@ -454,7 +456,7 @@ fp_status fem_pic_wave_step(fem_pic_mfem_t* m, const double* E_prev, const doubl
  * Gauss-law residual g = D0^T [*eps] E + Q (Eq. discreteGauss) on the free nodes, in FP64:
  * out[0] = max |g_n|, out[1] = max over the same nodes of |Q_n| + sum over incident edges of
  * |([*eps] E)_e| (the scale).  Natural boundary: g less (sum Q / sum alpha) alpha, the net
- * charge the zero-mean constraint spreads.  E device double [N_e], Q deposit precision [N_n]
+ * charge the zero-mean constraint spreads.  E device double [N_e], Q charge precision [N_n]
  * (NULL = 0), out device double [2].  Asynchronous.
  */
 fp_status fem_pic_mfem_gauss_residual(fem_pic_mfem_t* m, const double* E, const void* Q, double* out,
