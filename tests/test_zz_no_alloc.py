@@ -36,28 +36,39 @@ def _entry():
 
 
 # 50,001 particles: the grid-stride kernel (n not a multiple of 4); 50,000: the staged
-# pipeline, which both entry points pick for aligned state
-@pytest.mark.parametrize("npart", [50_001, 50_000])
-def test_static_push_matches_allocating_push_on_two_calls(npart):
+# pipeline, which both entry points pick for aligned state; and the staged pipeline with the
+# charge-change deposit into a double Q carried over both calls
+@pytest.mark.parametrize("npart,change", [(50_001, False), (50_000, False), (50_000, True)])
+def test_static_push_matches_allocating_push_on_two_calls(npart, change):
     F, push_static = _entry()
     m = I.cube_mesh(8, 1.0, 0.1, seed=1)
     sp = I.uniform_species(m, npart, 3, 0.15, -1.0, 1.0, 0.7)
     lib = F.FemPic(m.xyz, m.tets, F.FP_FP32)
+    if change:
+        lib.set_charge_precision(F.FP_FP64)
+    RQ = lib.charge_dtype
+    flags = F.FP_CHARGE_CHANGE if change else 0
     rng = np.random.default_rng(7)
     e = torch.as_tensor(rng.uniform(-0.2, 0.2, lib.n_edges), device="cuda")
     b = torch.as_tensor(rng.uniform(-0.5, 0.5, lib.n_faces), device="cuda")
     ref = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
     new = lib.species(sp.cell, sp.X, sp.V, sp.q, sp.m, sp.w)
     stream = torch.cuda.current_stream().cuda_stream
+    if change:      # both start from the charge of the start positions and carry it
+        Q_ref = torch.zeros(lib.n_nodes, dtype=RQ, device="cuda")
+        lib.deposit_charge(ref, Q_ref)
+        Q_new = Q_ref.clone()
     for call in range(2):
         dG_ref = torch.empty(lib.n_edges, dtype=torch.float32, device="cuda")
-        Q_ref = torch.empty(lib.n_nodes, dtype=torch.float32, device="cuda")
-        lib.push_deposit(e, b, ref, 1.0, dG_ref, Q_ref)
+        if not change:
+            Q_ref = torch.empty(lib.n_nodes, dtype=RQ, device="cuda")
+        lib.push_deposit(e, b, ref, 1.0, dG_ref, Q_ref, flags=flags)
         dG_new = torch.full((lib.n_edges,), 7.0, dtype=torch.float32, device="cuda")
-        Q_new = torch.full((lib.n_nodes,), 7.0, dtype=torch.float32, device="cuda")
+        if not change:
+            Q_new = torch.full((lib.n_nodes,), 7.0, dtype=RQ, device="cuda")
         pa = new.abi()
         st = push_static(lib.h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(b.data_ptr()), ctypes.byref(pa),
-                         1.0, 64, ctypes.c_void_p(dG_new.data_ptr()), ctypes.c_void_p(Q_new.data_ptr()), 0,
+                         1.0, 64, ctypes.c_void_p(dG_new.data_ptr()), ctypes.c_void_p(Q_new.data_ptr()), flags,
                          ctypes.c_void_p(stream))
         assert st == F.FP_OK, F.fem_pic_last_error(lib.h)
         assert lib.status() == F.FP_OK
