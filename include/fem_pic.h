@@ -122,10 +122,11 @@ fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]);
  *   FP_FP64: double arrays.  The particle arithmetic stays FP32: each particle's
  *            contributions, and the fast push's sums over a run of particles in one tet, are
  *            formed in FP32 and added into the arrays with FP64 atomics.  The arrays then keep
- *            charge continuity (D0^T dG against the change of Q) about a hundred times closer
- *            than FP32 arrays, whose atomic sums round at the scale of each entry's total,
- *            and the Gauss-law projection of the field step, which corrects exactly that
- *            residual, needs correspondingly fewer iterations.
+ *            charge continuity (D0^T dG against the change of Q) about ten times closer than
+ *            FP32 arrays, whose atomic sums round at the scale of each entry's total, and the
+ *            Gauss-law projection of the field step, which corrects exactly that residual,
+ *            needs fewer iterations.  The charge change into a double Q (FP_CHARGE_CHANGE,
+ *            fem_pic_set_charge_precision) keeps it closer still, with float dG.
  * An FP64 context always deposits in FP64 (FP_FP64 accepted, FP_FP32 -> FP_EINVAL).  The FP32
  * Adams mover (fem_pic_push_deposit_adams) takes FP32 deposits only (FP_EINVAL otherwise).
  * FP_FP32 sets Q back to float as well (see fem_pic_set_charge_precision).
