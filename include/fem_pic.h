@@ -125,7 +125,9 @@ fp_status fem_pic_sizes(const fem_pic_t* ctx, int64_t sizes[5]);
  *            charge continuity (D0^T dG against the change of Q) about ten times closer than
  *            FP32 arrays, whose atomic sums round at the scale of each entry's total, and the
  *            Gauss-law projection of the field step, which corrects exactly that residual,
- *            needs fewer iterations.  The charge change into a double Q (FP_CHARGE_CHANGE,
+ *            needs fewer iterations.  (A float contribution below 1.2e-38 in magnitude, a
+ *            subnormal, may add zero: some kernels widen floats through their bit patterns.)
+ *            The charge change into a double Q (FP_CHARGE_CHANGE,
  *            fem_pic_set_charge_precision) keeps it closer still, with float dG.
  * An FP64 context always deposits in FP64 (FP_FP64 accepted, FP_FP32 -> FP_EINVAL).  The FP32
  * Adams mover (fem_pic_push_deposit_adams) takes FP32 deposits only (FP_EINVAL otherwise).
